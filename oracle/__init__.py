@@ -1,0 +1,214 @@
+"""CPU oracle for SCPL video retargeting -- TEST INFRASTRUCTURE ONLY.
+
+A plain single-threaded C statement of the method (``scpl_oracle.c``) with a
+numpy/ctypes wrapper.  Only the test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may load it.  The product library never
+imports, links or calls anything here, and this module never imports the
+product package.
+
+Each wrapper names the passage of the paper (arXiv 1903.03180) it follows; the
+readings taken where the paper is silent are listed at the top of the C file.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "scpl_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+# Default parameters used across the tests and benchmarks (Sec. 3.2: alpha in
+# [0.15, 0.25]; Sec. 3.3 weights are integers here).
+ALPHA = 0.20
+T_MAX = 128
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fused multiply-add contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    build()
+    lib = ctypes.CDLL(_LIB)
+    P = ctypes.c_void_p
+    i32, i64, dbl = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    lib.orc_luma.argtypes = [P, i32, i32, P]
+    lib.orc_sobel.argtypes = [P, i32, i32, P]
+    lib.orc_motion.argtypes = [P, i32, i32, i32, P]
+    lib.orc_energy.argtypes = [P, i32, i32, i32, i32, i32, P]
+    lib.orc_dp.argtypes = [P, i32, i32, P, P, P]
+    lib.orc_select.argtypes = [P, P, i32, i32, P]
+    lib.orc_backtrack.argtypes = [P, i32, i32, i32, P]
+    lib.orc_isqrt.argtypes = [ctypes.c_uint64]
+    lib.orc_isqrt.restype = ctypes.c_uint64
+    lib.orc_asde_sum.argtypes = [P, i32, i32, i32, P]
+    lib.orc_threshold.argtypes = [i32, i64, i32, i32, dbl]
+    lib.orc_threshold.restype = dbl
+    lib.orc_exceeds.argtypes = [i64, i32, i64, i32, i32, dbl]
+    lib.orc_scan.argtypes = [P, i32, i32, i32, dbl, i32, i32, i64, P, P]
+    lib.orc_carve_buffer.argtypes = [P, P, i32, i32, i32, i32, i32, i32, i32, P, P, P]
+    lib.orc_carve.argtypes = [P, i32, i32, i32, i32, i32, i32, i32, dbl, i32, i32, i32, P, P, P, P]
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc):
+    if rc != 0:
+        raise RuntimeError(f"oracle error {rc}")
+
+
+def luma(rgb: np.ndarray) -> np.ndarray:
+    """Integer BT.601 luma of an [H,W,3] uint8 frame (Sec. 3.3 energy input)."""
+    rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
+    H, W = rgb.shape[:2]
+    Y = np.empty((H, W), np.uint8)
+    _check(_load().orc_luma(_ptr(rgb), H, W, _ptr(Y)))
+    return Y
+
+
+def sobel(Y: np.ndarray) -> np.ndarray:
+    """|Gx|+|Gy| Sobel gradient with replicate border (Sec. 3.3)."""
+    Y = np.ascontiguousarray(Y, dtype=np.uint8)
+    H, W = Y.shape
+    G = np.empty((H, W), np.int32)
+    _check(_load().orc_sobel(_ptr(Y), H, W, _ptr(G)))
+    return G
+
+
+def motion(frames: np.ndarray) -> np.ndarray:
+    """D_t = |Y_t - Y_{t-1}|, D_0 = 0 (Sec. 3.3).  frames [T,H,W,3]."""
+    frames = np.ascontiguousarray(frames, dtype=np.uint8)
+    T, H, W = frames.shape[:3]
+    D = np.empty((T, H, W), np.uint8)
+    _check(_load().orc_motion(_ptr(frames), T, H, W, _ptr(D)))
+    return D
+
+
+def energy(frames: np.ndarray, wg: int = 1, wm: int = 2) -> np.ndarray:
+    """e_t = wg*Sobel(Y_t) + wm*D_t for every frame (Sec. 3.3).  [T,H,W] int32."""
+    frames = np.ascontiguousarray(frames, dtype=np.uint8)
+    T, H, W = frames.shape[:3]
+    e = np.empty((T, H, W), np.int32)
+    _check(_load().orc_energy(_ptr(frames), T, H, W, wg, wm, _ptr(e)))
+    return e
+
+
+def dp(E: np.ndarray):
+    """Eq. 4 with parental labels: returns (CE int64, labels int32, dir uint8)."""
+    E = np.ascontiguousarray(E, dtype=np.int32)
+    H, W = E.shape
+    CE = np.empty((H, W), np.int64)
+    L = np.empty((H, W), np.int32)
+    d = np.empty((H, W), np.uint8)
+    _check(_load().orc_dp(_ptr(E), H, W, _ptr(CE), _ptr(L), _ptr(d)))
+    return CE, L, d
+
+
+def select(ce_last: np.ndarray, lab_last: np.ndarray, cap: int) -> np.ndarray:
+    """Eq. 6 per-parent argmin, then the `cap` lowest by (CE, column)."""
+    ce_last = np.ascontiguousarray(ce_last, dtype=np.int64)
+    lab_last = np.ascontiguousarray(lab_last, dtype=np.int32)
+    W = ce_last.shape[0]
+    cols = np.empty(max(W, 1), np.int32)
+    n = _load().orc_select(_ptr(ce_last), _ptr(lab_last), W, cap, _ptr(cols))
+    if n < 0:
+        raise RuntimeError(f"oracle error {-n}")
+    return cols[:n].copy()
+
+
+def backtrack(d: np.ndarray, end_col: int) -> np.ndarray:
+    """Follow the recorded indicators up from (H-1, end_col) (Sec. 3.1)."""
+    d = np.ascontiguousarray(d, dtype=np.uint8)
+    H, W = d.shape
+    path = np.empty(H, np.int32)
+    _check(_load().orc_backtrack(_ptr(d), H, W, end_col, _ptr(path)))
+    return path
+
+
+def isqrt(x: int) -> int:
+    return int(_load().orc_isqrt(x))
+
+
+def asde_sum(e: np.ndarray) -> int:
+    """A = sum_ij floor(256*sqrt(n*S2 - S1^2)) over n maps [n,H,W] (Eq. 7-8)."""
+    e = np.ascontiguousarray(e, dtype=np.int32)
+    n, H, W = e.shape
+    out = np.zeros(1, np.int64)
+    _check(_load().orc_asde_sum(_ptr(e), n, H, W, _ptr(out)))
+    return int(out[0])
+
+
+def threshold(n: int, M: int, H: int, W: int, alpha: float = ALPHA) -> float:
+    """256*alpha*M*sqrt(n-1)*H*W, the scaled phi(n) of Eq. 9."""
+    return float(_load().orc_threshold(n, M, H, W, alpha))
+
+
+def exceeds(A: int, n: int, M: int, H: int, W: int, alpha: float = ALPHA) -> bool:
+    return bool(_load().orc_exceeds(A, n, M, H, W, alpha))
+
+
+def scan(e: np.ndarray, alpha: float = ALPHA, t_max: int = T_MAX, maxval_mode: int = 0,
+         maxval_theory: int = 0) -> np.ndarray:
+    """Buffer boundaries of the dynamic spatiotemporal buffer (Sec. 3.2).
+
+    Returns starts (int32, length n_buffers+1, last entry T)."""
+    e = np.ascontiguousarray(e, dtype=np.int32)
+    T, H, W = e.shape
+    starts = np.empty(T + 1, np.int32)
+    nb = np.zeros(1, np.int32)
+    _check(_load().orc_scan(_ptr(e), T, H, W, alpha, t_max, maxval_mode, maxval_theory,
+                            _ptr(starts), _ptr(nb)))
+    return starts[: nb[0] + 1].copy()
+
+
+def carve_buffer(frames: np.ndarray, D: np.ndarray, target: int, k: int, wg: int = 1,
+                 wm: int = 2):
+    """Carve one fixed buffer (Sec. 3.1/3.2).  Returns (out, seams, k_eff list)."""
+    frames = np.ascontiguousarray(frames, dtype=np.uint8)
+    D = np.ascontiguousarray(D, dtype=np.uint8)
+    Tb, H, W0 = frames.shape[:3]
+    out = np.empty((Tb, H, target, 3), np.uint8)
+    seams = np.empty((max(W0 - target, 1), H), np.int16)
+    keff = np.zeros(max(W0 - target, 1), np.int32)
+    n = _load().orc_carve_buffer(_ptr(frames), _ptr(D), Tb, H, W0, target, k, wg, wm, _ptr(out),
+                                 _ptr(seams), _ptr(keff))
+    if n < 0:
+        raise RuntimeError(f"oracle error {-n}")
+    return out, seams[: W0 - target].copy(), keff[:n].copy()
+
+
+def carve(frames: np.ndarray, target: int, k: int, wg: int = 1, wm: int = 2,
+          alpha: float = ALPHA, t_max: int = T_MAX, use_buffer: bool = True,
+          maxval_mode: int = 0):
+    """Whole clip: energy, buffer scan, per-buffer carving.
+
+    Returns (out [T,H,target,3], starts [n_buffers+1], seams [n_buffers, W0-target, H])."""
+    frames = np.ascontiguousarray(frames, dtype=np.uint8)
+    T, H, W0 = frames.shape[:3]
+    out = np.empty((T, H, target, 3), np.uint8)
+    starts = np.empty(T + 1, np.int32)
+    nb = np.zeros(1, np.int32)
+    seams = np.empty((T, max(W0 - target, 1), H), np.int16)
+    _check(_load().orc_carve(_ptr(frames), T, H, W0, target, k, wg, wm, alpha, t_max,
+                             int(use_buffer), maxval_mode, _ptr(out), _ptr(starts), _ptr(nb),
+                             _ptr(seams)))
+    n = int(nb[0])
+    return out, starts[: n + 1].copy(), seams[:n, : W0 - target].copy()
