@@ -355,24 +355,34 @@ int orc_carve_buffer(const uint8_t *frames, const uint8_t *D, int Tb, int H, int
                 if (seams) seams[(long)(removed + s) * H + i] = (int16_t)orig[p];
             }
         }
-        /* delete the marked pixels row by row from every carved array */
+        /* delete the marked pixels row by row from every carved array; the
+         * arrays are compacted in place, frame by frame in storage order, so
+         * no write ever lands ahead of the next read */
         int Wn = W - k_eff;
         for (int i = 0; i < H; ++i) {
             int q = 0;
             for (int j = 0; j < W; ++j) {
                 long p = (long)i * W + j;
                 if (kill[p]) continue;
-                long pn = (long)i * Wn + q;
-                orig[pn] = orig[p];
-                for (int t = 0; t < Tb; ++t) {
+                orig[(long)i * Wn + q] = orig[p];
+                ++q;
+            }
+            if (q != Wn) { rc = -ORC_EINVAL; goto done; } /* every row narrows by k_eff */
+        }
+        for (int t = 0; t < Tb; ++t) {
+            for (int i = 0; i < H; ++i) {
+                int q = 0;
+                for (int j = 0; j < W; ++j) {
+                    long p = (long)i * W + j;
+                    if (kill[p]) continue;
+                    long pn = (long)i * Wn + q;
                     const uint8_t *src = rgb + 3 * ((long)t * hw + p);
                     uint8_t *dst = rgb + 3 * ((long)t * H * Wn + pn);
                     dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2];
                     dm[(long)t * H * Wn + pn] = dm[(long)t * hw + p];
+                    ++q;
                 }
-                ++q;
             }
-            if (q != Wn) { rc = -ORC_EINVAL; goto done; } /* every row narrows by k_eff */
         }
         if (k_eff_out) k_eff_out[iters] = k_eff;
         W = Wn;

@@ -1,0 +1,372 @@
+"""Pins for the CPU oracle: each test checks it against something other than
+itself -- closed forms, library routines, brute force, a textbook classic seam
+carver, a hand-worked example, invariants that the paper's Sec. 3.1 argument
+fixes.  No GPU is needed."""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+from tests import textbook as tb
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- luma (R1)
+def test_luma_grey_is_exact(orc):
+    # the integer coefficients sum to 256, so a grey pixel keeps its value
+    v = np.arange(256, dtype=np.uint8)
+    rgb = np.stack([v, v, v], -1)[None]
+    assert np.array_equal(orc.luma(rgb)[0], v)
+
+
+def test_luma_within_one_of_float_bt601(orc):
+    r = np.random.default_rng(0)
+    rgb = r.integers(0, 256, (64, 97, 3), dtype=np.uint8)
+    rgb[0, :8] = [[255, 0, 0], [0, 255, 0], [0, 0, 255], [255, 255, 0], [0, 255, 255],
+                  [255, 0, 255], [255, 255, 255], [0, 0, 0]]
+    y = orc.luma(rgb).astype(np.float64)
+    assert np.max(np.abs(y - tb.luma_bt601_float(rgb))) <= 1.0
+
+
+# ------------------------------------------------------------- Sobel (R2)
+def test_sobel_closed_forms(orc):
+    H, W = 7, 9
+    assert not orc.sobel(np.full((H, W), 77, np.uint8)).any()
+    ramp = np.tile(np.arange(W, dtype=np.uint8) * 3, (H, 1))
+    G = orc.sobel(ramp)
+    assert (G[:, 1:-1] == 8 * 3).all() and (G[:, 0] == 4 * 3).all() and (G[:, -1] == 4 * 3).all()
+    G = orc.sobel(np.ascontiguousarray(ramp.T))
+    assert (G[1:-1] == 24).all() and (G[0] == 12).all() and (G[-1] == 12).all()
+    step = np.zeros((H, W), np.uint8)
+    step[:, 4:] = 50
+    G = orc.sobel(step)
+    assert (G[:, 3] == 200).all() and (G[:, 4] == 200).all()
+    assert not np.delete(G, [3, 4], axis=1).any()
+
+
+def test_sobel_matches_scipy(orc):
+    r = np.random.default_rng(1)
+    for H, W in [(1, 1), (1, 5), (5, 1), (2, 2), (13, 31), (40, 17)]:
+        Y = r.integers(0, 256, (H, W), dtype=np.uint8)
+        assert np.array_equal(orc.sobel(Y), tb.sobel_scipy(Y))
+
+
+# ------------------------------------------------------ motion energy (R3)
+def test_motion_and_blend_hand_case(orc):
+    f = np.zeros((3, 4, 6, 3), np.uint8)
+    f[0], f[1], f[2] = 10, 30, 25
+    assert np.array_equal(orc.motion(f)[:, 0, 0], [0, 20, 5])
+    e = orc.energy(f, wg=1, wm=2)
+    assert np.array_equal(e[:, 2, 3], [0, 40, 10])
+    e = orc.energy(f, wg=1, wm=0)
+    assert not e.any()
+
+
+def test_energy_matches_scipy(orc):
+    r = np.random.default_rng(2)
+    f = r.integers(0, 256, (4, 11, 23, 3), dtype=np.uint8)
+    for wg, wm in [(1, 0), (1, 2), (2, 3)]:
+        ref = tb.energy_scipy(f, wg, wm, orc.luma)
+        assert np.array_equal(orc.energy(f, wg, wm), ref)
+
+
+# ------------------------------------------------ DP, labels, ties (R4-R5)
+def _load_golden(name):
+    blocks, cur = {}, None
+    with open(os.path.join(GOLDEN, name)) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line[0].isalpha():
+                cur = line
+                blocks[cur] = []
+            else:
+                blocks[cur].append([int(x) for x in line.split()])
+    return {k: np.array(v) for k, v in blocks.items()}
+
+
+def test_dp_hand_worked_example(orc):
+    g = _load_golden("dp_3x5.txt")
+    CE, L, d = orc.dp(g["energy"])
+    assert np.array_equal(CE, g["ce"])
+    assert np.array_equal(L, g["labels"])
+    assert np.array_equal(d, g["dir"])
+    assert np.array_equal(orc.select(CE[-1], L[-1], 1), g["select_k1"][0])
+    assert np.array_equal(orc.select(CE[-1], L[-1], 2), g["select_k2"][0])
+    assert np.array_equal(orc.backtrack(d, 1), g["seam_from_1"][0])
+    assert np.array_equal(orc.backtrack(d, 4), g["seam_from_4"][0])
+
+
+@pytest.mark.parametrize("H,W,vmax,seed", [(1, 4, 3, 0), (2, 3, 2, 1), (4, 5, 3, 2), (5, 6, 2, 3),
+                                          (5, 6, 9, 4), (3, 6, 0, 5), (5, 4, 1, 6)])
+def test_dp_brute_force(orc, H, W, vmax, seed):
+    """CE(H-1, j) is the least cost of all seams ending at j; the traced path is
+    the lexicographically least (c_{H-2}, ..., c_0) among them; its row-0
+    column is the label (Eq. 4, Eq. 5, lowest-column tie reading)."""
+    r = np.random.default_rng(seed)
+    E = r.integers(0, vmax + 1, (H, W)).astype(np.int32)
+    CE, L, d = orc.dp(E)
+    best = {}
+    for path in tb.all_seams(H, W):
+        cost = int(sum(E[i, c] for i, c in enumerate(path)))
+        key = (cost, tuple(reversed(path[:-1])))
+        j = path[-1]
+        if j not in best or key < best[j][0]:
+            best[j] = (key, path)
+    for j in range(W):
+        (cost, _), path = best[j]
+        assert CE[-1, j] == cost
+        assert L[-1, j] == path[0]
+        assert tuple(orc.backtrack(d, j)) == path
+
+
+def test_labels_non_decreasing_and_seams_disjoint(orc):
+    """Sec. 3.1: paths never cross, so labels are sorted along every row and
+    the traced seams of different parents share no pixel (Eq. 5)."""
+    r = np.random.default_rng(7)
+    for trial in range(20):
+        H, W = int(r.integers(1, 40)), int(r.integers(1, 60))
+        E = r.integers(0, int(r.integers(1, 50)), (H, W)).astype(np.int32)
+        CE, L, d = orc.dp(E)
+        assert (np.diff(L, axis=1) >= 0).all()
+        cols = orc.select(CE[-1], L[-1], W)
+        assert len(cols) == len(np.unique(L[-1]))
+        paths = np.array([orc.backtrack(d, c) for c in cols])
+        for i in range(H):
+            assert len(np.unique(paths[:, i])) == len(cols)
+        assert (np.abs(np.diff(paths, axis=1)) <= 1).all()
+
+
+# --------------------------------------------------------- selection (R6)
+def test_select_k1_is_global_argmin(orc):
+    r = np.random.default_rng(8)
+    for _ in range(30):
+        H, W = int(r.integers(1, 20)), int(r.integers(1, 40))
+        E = r.integers(0, 5, (H, W)).astype(np.int32)
+        CE, L, _ = orc.dp(E)
+        M, _ = tb.classic_dp(E)
+        assert np.array_equal(CE, M)
+        assert orc.select(CE[-1], L[-1], 1)[0] == int(np.argmin(M[-1]))
+
+
+def test_select_per_parent_minimum(orc):
+    r = np.random.default_rng(9)
+    for _ in range(30):
+        H, W = int(r.integers(1, 25)), int(r.integers(2, 50))
+        E = r.integers(0, 4, (H, W)).astype(np.int32)
+        CE, L, _ = orc.dp(E)
+        cols = orc.select(CE[-1], L[-1], W)
+        # every parent appears once, with the least (CE, column) of its children
+        for c in cols:
+            same = np.nonzero(L[-1] == L[-1, c])[0]
+            assert c == same[np.lexsort((same, CE[-1, same]))][0]
+        keys = [(CE[-1, c], c) for c in cols]
+        assert keys == sorted(keys)
+        for cap in range(1, len(cols) + 2):
+            assert np.array_equal(orc.select(CE[-1], L[-1], cap), cols[:cap])
+
+
+# ------------------------------------------- whole carve vs textbook SC (R9)
+def test_k1_single_frame_equals_classic_seam_carving(orc):
+    """With k = 1 and one frame, SCPL is classic Avidan-Shamir seam carving."""
+    from paper_1903_03180_gb300 import synth
+    f = synth.still_frame(36, 48, seed=11, n_rects=4)
+    n = 12
+    ref, ref_seams = tb.classic_seam_carve(f, n, lambda im: tb.sobel_scipy(orc.luma(im)))
+    out, starts, seams = orc.carve(f[None], 48 - n, 1, wg=1, wm=0, use_buffer=False)
+    assert np.array_equal(out[0], ref)
+    assert np.array_equal(seams[0], ref_seams)
+
+
+def test_k1_per_frame_raw_video_equals_classic(orc):
+    from paper_1903_03180_gb300 import synth
+    c = synth.clip(3, 24, 40, seed=12)
+    out, starts, seams = orc.carve(c, 34, 1, wg=1, wm=0, use_buffer=False)
+    assert np.array_equal(starts, [0, 1, 2, 3])
+    for t in range(3):
+        ref, _ = tb.classic_seam_carve(c[t], 6, lambda im: tb.sobel_scipy(orc.luma(im)))
+        assert np.array_equal(out[t], ref)
+
+
+def _check_carve_invariants(frames, out, starts, seams, target):
+    T, H, W0 = frames.shape[:3]
+    for b in range(len(starts) - 1):
+        sb = seams[b]                                   # [W0-target, H] original columns
+        for i in range(H):
+            assert len(np.unique(sb[:, i])) == W0 - target   # disjoint, every row narrows
+        for t in range(starts[b], starts[b + 1]):
+            for i in range(H):
+                keep = np.delete(frames[t, i], sb[:, i], axis=0)
+                assert np.array_equal(out[t, i], keep)
+
+
+def _current_columns(seams_b, H, W0):
+    """Convert removal-order original columns into the column each pixel had
+    at the time of its removal."""
+    removed = [[] for _ in range(H)]
+    cur = np.empty_like(seams_b)
+    for s in range(seams_b.shape[0]):
+        for i in range(H):
+            o = int(seams_b[s, i])
+            cur[s, i] = o - sum(1 for x in removed[i] if x < o)
+        for i in range(H):
+            removed[i].append(int(seams_b[s, i]))
+    return cur
+
+
+def test_multi_seam_invariants(orc):
+    from paper_1903_03180_gb300 import synth
+    c = synth.clip(6, 30, 52, seed=13)
+    target = 36
+    out, starts, seams = orc.carve(c, target, 5, wg=1, wm=2, t_max=4)
+    assert starts[0] == 0 and starts[-1] == 6 and (np.diff(starts) <= 4).all()
+    _check_carve_invariants(c, out, starts, seams, target)
+    for b in range(len(starts) - 1):
+        cur = _current_columns(seams[b], 30, 52)
+        # every seam is 8-connected at the width it was removed at
+        assert (np.abs(np.diff(cur, axis=1)) <= 1).all()
+
+
+def test_kbig_removes_one_seam_per_parent(orc):
+    from paper_1903_03180_gb300 import synth
+    f = synth.still_frame(20, 40, seed=14, n_rects=3)
+    D = np.zeros((1, 20, 40), np.uint8)
+    out, seams, keff = orc.carve_buffer(f[None], D, 30, 1000, wg=1, wm=0)
+    E = orc.energy(f[None], 1, 0)[0]
+    CE, L, d = orc.dp(E)
+    assert keff[0] == min(len(np.unique(L[-1])), 10)
+    assert keff.sum() == 10
+
+
+# ----------------------------------------------------- buffer, ASDE (R7)
+def test_isqrt_exact(orc):
+    r = np.random.default_rng(15)
+    xs = [0, 1, 2, 3, 4, 15, 16, 17, 2 ** 52 - 1, 2 ** 52, 2 ** 53 + 1, (2 ** 31 - 1) ** 2,
+          (2 ** 31 - 1) ** 2 - 1, (10 ** 8) ** 2 + 10 ** 8]
+    xs += [int(v) for v in r.integers(0, 2 ** 62, 200, dtype=np.int64)]
+    for x in xs:
+        assert orc.isqrt(x) == math.isqrt(x)
+
+
+def test_threshold_is_eq9(orc):
+    """Eq. 9 in its printed form equals the scaled threshold / (256*n*H*W)."""
+    for n in range(1, 40):
+        for M in [1, 255, 2550, 7777]:
+            for alpha in [0.15, 0.2, 0.25]:
+                mv = float(M)
+                phi = alpha * math.sqrt(((mv - mv / n) ** 2 + (n - 1) * (mv / n) ** 2) / n)
+                thr = orc.threshold(n, M, 6, 9, alpha)
+                assert thr / (256 * n * 6 * 9) == pytest.approx(phi, rel=1e-12, abs=1e-12)
+
+
+def test_asde_matches_numpy_std(orc):
+    """A/(256*n*H*W) is Eq. 7 (mean of Eq. 8's population STD) up to the
+    1/256 floor of each pixel's term."""
+    r = np.random.default_rng(16)
+    for n in [1, 2, 3, 7, 16]:
+        e = r.integers(0, 2551, (n, 9, 13)).astype(np.int32)
+        A = orc.asde_sum(e)
+        asde = float(np.mean(np.std(e.astype(np.float64), axis=0)))
+        approx = A / (256.0 * n * e.shape[1] * e.shape[2])
+        assert asde - 1.0 / (256 * n) - 1e-9 <= approx <= asde + 1e-9
+
+
+def test_fig4_worst_case_construction(orc):
+    """Fig. 4: n-1 frames of the lowest energy then one of the highest.  Each
+    pixel's STD is then M*sqrt(n-1)/n, so ASDE = phi(n)/alpha exactly."""
+    H, W, M = 5, 7, 2550
+    for n in range(2, 30):
+        e = np.zeros((n, H, W), np.int32)
+        e[-1] = M
+        A = orc.asde_sum(e)
+        assert A == H * W * math.isqrt(65536 * M * M * (n - 1))
+        assert orc.exceeds(A, n, M, H, W, 0.2)
+        assert not orc.exceeds(A, n, M, H, W, 1.0)     # floor never exceeds alpha = 1
+        st = orc.scan(e, alpha=0.2)
+        assert np.array_equal(st, [0, n - 1, n])           # the spike starts a new buffer
+
+
+def test_constant_clip_fills_to_t_max(orc):
+    e = np.full((70, 4, 6), 123, np.int32)
+    assert np.array_equal(orc.scan(e, t_max=16), [0, 16, 32, 48, 64, 70])
+    assert np.array_equal(orc.scan(e[:1], t_max=16), [0, 1])
+    assert np.array_equal(orc.scan(e, t_max=1), np.arange(71))
+
+
+def _scan_float_reference(e, alpha, t_max):
+    """Sec. 3.2 with Eq. 7-9 in floating point as printed (np.std, Eq. 9's
+    unsimplified form).  Returns the starts and the smallest relative margin."""
+    T = e.shape[0]
+    starts, start, margin = [], 0, np.inf
+    buf = []
+    for f in range(T):
+        cand = buf + [e[f]]
+        n = len(cand)
+        if n >= 2:
+            asde = float(np.mean(np.std(np.array(cand, np.float64), axis=0)))
+            M = float(np.max(cand))
+            phi = alpha * math.sqrt(((M - M / n) ** 2 + (n - 1) * (M / n) ** 2) / n)
+            margin = min(margin, abs(asde - phi) / max(phi, 1e-9))
+            if asde > phi:
+                starts.append(start)
+                start, buf = f, [e[f]]
+                continue
+        buf = cand
+        if len(buf) == t_max:
+            starts.append(start)
+            start, buf = f + 1, []
+    if buf:
+        starts.append(start)
+    return starts + [T], margin
+
+
+def test_scan_matches_float_reading_of_eq7_9(orc):
+    r = np.random.default_rng(17)
+    checked = 0
+    for trial in range(40):
+        T, H, W = int(r.integers(2, 14)), int(r.integers(2, 8)), int(r.integers(2, 8))
+        base = r.integers(0, 600, (H, W))
+        jitter = int(r.integers(1, 400))
+        e = np.stack([base + r.integers(0, jitter, (H, W)) * (r.random() < 0.3)
+                      for _ in range(T)]).astype(np.int32)
+        ref, margin = _scan_float_reference(e, 0.2, 6)
+        if margin < 1e-3:
+            continue
+        assert list(orc.scan(e, alpha=0.2, t_max=6)) == ref
+        checked += 1
+    assert checked >= 20
+
+
+def test_maxval_theoretical_mode(orc):
+    # with M fixed at the theoretical maximum the bar is higher than with the
+    # running maximum, so the spike of the Fig. 4 construction (M = 100) stays
+    e = np.zeros((6, 3, 3), np.int32)
+    e[-1] = 100
+    assert np.array_equal(orc.scan(e, maxval_mode=0), [0, 5, 6])
+    assert np.array_equal(orc.scan(e, maxval_mode=1, maxval_theory=2550), [0, 6])
+
+
+def test_buffer_carves_same_seams_from_every_frame(orc):
+    """Sec. 3.2: one seam set per buffer, applied to all of its frames."""
+    from paper_1903_03180_gb300 import synth
+    c = synth.clip(8, 24, 40, seed=18, pan=0, noise=0)
+    out, starts, seams = orc.carve(c, 30, 4, t_max=8)
+    _check_carve_invariants(c, out, starts, seams, 30)
+    e = orc.energy(c)
+    assert np.array_equal(starts, orc.scan(e, t_max=8))
+
+
+def test_new_buffer_keeps_its_first_frames_maximum(orc):
+    """After a flush the frame that starts the new buffer is part of it, so its
+    maximum energy is the new buffer's maxval (Eq. 9's maxval over the buffer).
+    Frames 0-2 are zero, frame 3 spikes to 2550 and starts buffer 2, frame 4
+    drops to 2100: with maxval 2550 the drop (STD sum 450*H*W) stays under
+    0.2*2550*H*W = 510*H*W, so frame 4 joins; a maxval of 2100 would flush it."""
+    e = np.zeros((5, 3, 4), np.int32)
+    e[3], e[4] = 2550, 2100
+    assert np.array_equal(orc.scan(e, alpha=0.2), [0, 3, 5])
