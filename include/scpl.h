@@ -1,0 +1,175 @@
+/*
+ * scpl.h -- C ABI of libscpl, GB300 (sm_103a) video retargeting by Seam
+ * Carving with Parental Labeling (SCPL), arXiv 1903.03180.
+ *
+ * Conventions shared by every entry point:
+ *  - Pointers marked [device] are CUDA device pointers owned by the caller;
+ *    pointers marked [host] are ordinary host memory owned by the caller.
+ *    The library never frees caller memory.  The library owns its own
+ *    workspaces, grows them on demand and frees them in scpl_destroy.
+ *  - Frames are uint8 RGB, layout [T][H][W][3], contiguous (HWC).
+ *  - Work is issued on the handle's stream.  Entry points that return results
+ *    to [host] pointers synchronise that stream before returning; the others
+ *    return as soon as the work is queued.
+ *  - Every entry point returns an scpl_status; nothing throws.  On a non-zero
+ *    status scpl_last_error() describes it.  After SCPL_EINVAL, SCPL_ENOMEM,
+ *    SCPL_EOVERFLOW or SCPL_ETIMEOUT the handle stays usable.  After
+ *    SCPL_ECUDA it is usable unless the CUDA context itself was lost.
+ *  - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef SCPL_H
+#define SCPL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct scpl_ctx *scpl_handle;
+
+typedef enum {
+    SCPL_OK = 0,
+    SCPL_EINVAL = 1,    /* bad argument (sizes, pointers, parameters)          */
+    SCPL_ENOMEM = 2,    /* a workspace could not be allocated                  */
+    SCPL_ECUDA = 3,     /* a CUDA call failed                                  */
+    SCPL_ETIMEOUT = 4,  /* a bounded device-side wait ran out                  */
+    SCPL_EOVERFLOW = 5  /* the sizes could overflow the exact integer sums     */
+} scpl_status;
+
+/* Parameters of the method.
+ *  alpha        Eq. 9's alpha (the paper's useful range is [0.15, 0.25]).
+ *  wg, wm       integer weights of the gradient and motion energies,
+ *               e = wg*|Sobel(Y)|_1 + wm*|Y_t - Y_{t-1}| (Sec. 3.3).
+ *  t_max        cap on frames per spatiotemporal buffer (1 <= t_max <= 1024).
+ *  use_buffer   0: every frame is its own buffer (per-frame SCPL; with k = 1
+ *               this is classic seam carving frame by frame).
+ *  maxval_mode  Eq. 9's maxval: 0 = running maximum of the buffered energy
+ *               maps, 1 = the energy function's maximum 255*(8*wg + wm).     */
+typedef struct {
+    double alpha;
+    int wg, wm;
+    int t_max;
+    int use_buffer;
+    int maxval_mode;
+} scpl_params;
+
+/* Fill p with the defaults: alpha 0.20, wg 1, wm 2, t_max 128, buffer on,
+ * maxval_mode 0. */
+void scpl_default_params(scpl_params *p);
+
+/* Create a handle bound to the current CUDA device and to `stream`
+ * (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ * Returns SCPL_EINVAL for a NULL out or invalid parameters. */
+scpl_status scpl_create(const scpl_params *p, void *stream, scpl_handle *out);
+
+/* Rebind the handle to another stream of the same device. */
+scpl_status scpl_set_stream(scpl_handle h, void *stream);
+
+/* Release every workspace of the handle.  NULL is accepted. */
+void scpl_destroy(scpl_handle h);
+
+/* Text of the last error on this handle ("" if none).  The string lives until
+ * the next call on the handle. */
+const char *scpl_last_error(scpl_handle h);
+
+/* Per-frame energy of a clip (Sec. 3.3): integer BT.601 luma
+ * Y = (77R + 150G + 29B + 128) >> 8, Sobel gradient |Gx| + |Gy| with a
+ * replicate border, frame difference D_t = |Y_t - Y_{t-1}| with D_0 = 0,
+ * e_t = wg*G_t + wm*D_t.
+ *   frames  [device] uint8 [T][H][W][3]
+ *   energy  [device] int32 [T][H][W], written
+ * Asynchronous.  SCPL_EINVAL if T, H or W < 1 or a pointer is NULL. */
+scpl_status scpl_energy(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                        int32_t *energy);
+
+/* Spatiotemporal buffer boundaries of a clip (Sec. 3.2, Eq. 7-9).  Frames
+ * join the open buffer one by one; a frame whose joining would make the
+ * buffer's ASDE exceed phi(n) starts the next buffer instead; a buffer is also
+ * closed at t_max frames and at the end of the clip.  The comparison is made
+ * exactly: A = sum_ij floor(256*sqrt(n*S2_ij - S1_ij^2)) (S1, S2 the sums of
+ * e and e^2 over the buffer) against 256*alpha*M*sqrt(n-1)*H*W in IEEE double.
+ *   frames        [device] uint8 [T][H][W][3]
+ *   buffer_starts [host] int32 [T+1]: first frame of each buffer, then T
+ *   n_buffers     [host] receives the number of buffers
+ * Synchronises the stream.  SCPL_ETIMEOUT if the device-wide per-frame
+ * reduction waited longer than its limit (the handle stays usable). */
+scpl_status scpl_scan(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                      int32_t *buffer_starts, int *n_buffers);
+
+/* One SCPL iteration on an energy map (Sec. 3.1, Eq. 4-6): the cumulative
+ * energy DP carrying each pixel's row-0 parent (lowest column on ties), the
+ * least-(CE, column) child of every parent, the k_eff = min(k, #parents)
+ * lowest of those by (CE, column), traced back through the recorded
+ * directions.
+ *   energy  [device] int32 [H][W], values >= 0, column sums < 2^31
+ *   cols    [device] int16 [k][H]: cols[s][i] = column of seam s in row i,
+ *           seams in rank order; rows s >= k_eff are left untouched
+ *   k_eff   [host] receives the number of seams found
+ * Synchronises the stream. */
+scpl_status scpl_seams(scpl_handle h, const int32_t *energy, int H, int W, int k,
+                       int16_t *cols, int *k_eff);
+
+/* Retarget a clip to width target_W (Sec. 3): energy, buffer scan, then for
+ * every buffer repeated SCPL iterations on the summed energy of its frames
+ * (the gradient recomputed on the carved frames, the motion term carved
+ * along), each removing k_eff = min(k, W - target_W, #parents) disjoint seams
+ * from every frame of the buffer, until the width is target_W.
+ *   frames         [device] uint8 [T][H][W][3]
+ *   out            [device] uint8 [T][H][target_W][3], written
+ *   buffer_starts  [host] int32 [T+1] or NULL
+ *   n_buffers      [host] or NULL
+ *   seams          [device] int16 [n_buffers][W - target_W][H] or NULL: for
+ *                  every buffer, the original column of every removed pixel,
+ *                  seams in removal order (iteration, then rank)
+ * Limits: 1 <= T, 1 <= H <= 65535, 2 <= target_W <= W <= 8192, 1 <= k;
+ * 255*(8*wg + wm)*min(T, t_max)*H < 2^31 and t_max*(255*(8*wg+wm))^2 < 2^32
+ * (else SCPL_EOVERFLOW).  Synchronises the stream (the buffer count decides
+ * the launch shapes). */
+scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W, int target_W,
+                       int k, uint8_t *out, int32_t *buffer_starts, int *n_buffers,
+                       int16_t *seams);
+
+/* scpl_carve on host memory: copies frames in and out on the handle's stream
+ * through library-owned device buffers (page-locked host memory makes the
+ * copies asynchronous and fast; pageable memory works too).
+ *   frames [host] uint8 [T][H][W][3]   out [host] uint8 [T][H][target_W][3]
+ *   seams  [host] int16 [n_buffers][W - target_W][H] or NULL (size it for T
+ *          buffers when the count is not known in advance) */
+scpl_status scpl_carve_host(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                            int target_W, int k, uint8_t *out, int32_t *buffer_starts,
+                            int *n_buffers, int16_t *seams);
+
+/* Per-kernel accounting of the handle's launches (not part of the paper: a
+ * measurement aid).  While profiling is on, every kernel launch of the handle
+ * is bracketed by CUDA events on the handle's stream, and every scpl_carve
+ * call adds its kernels' algorithmic bytes (the bytes the method has to move,
+ * by the model stated beside each kernel in the library's design notes).
+ *   scpl_set_profiling(h, 1) clears the counters and turns accounting on;
+ *   scpl_set_profiling(h, 0) turns it off.
+ *   scpl_get_stats synchronises the stream and fills *out. */
+typedef struct {
+    char name[32];
+    long long launches;
+    double ms;       /* summed event-timed duration of those launches       */
+    double bytes;    /* summed algorithmic bytes of those launches          */
+} scpl_kernel_stat;
+
+typedef struct {
+    int n_buffers;              /* of the last scpl_carve call              */
+    int iterations_max;         /* most SCPL iterations of any of its buffers */
+    long long iterations_total; /* summed over its buffers                   */
+    double carved_px;           /* sum over its buffers and iterations of
+                                   H * (width before the iteration)         */
+    int n_kernels;
+    scpl_kernel_stat kernel[8];
+} scpl_stats;
+
+scpl_status scpl_set_profiling(scpl_handle h, int on);
+scpl_status scpl_get_stats(scpl_handle h, scpl_stats *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SCPL_H */

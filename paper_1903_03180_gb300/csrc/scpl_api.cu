@@ -1,0 +1,574 @@
+// C ABI of libscpl (declared in include/scpl.h): argument checks, workspace
+// management and the host-side order of launches.  All arithmetic of the
+// method runs in the kernels of scan.cu and carve.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "scpl.h"
+#include "scpl_internal.cuh"
+
+using namespace scpl;
+
+namespace {
+
+// A grow-only device allocation.
+struct DevBuf {
+    void *p = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= n) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e == cudaSuccess) n = bytes;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// A grow-only page-locked host allocation.
+struct HostBuf {
+    void *p = nullptr;
+    size_t n = 0;
+    cudaError_t ensure(size_t bytes) {
+        if (bytes <= n) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+        cudaError_t e = cudaMallocHost(&p, bytes);
+        if (e == cudaSuccess) n = bytes;
+        return e;
+    }
+    void release() {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        n = 0;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+constexpr unsigned long long SPIN_LIMIT_NS = 2000000000ull;   // 2 s per device-wide wait
+
+// Kernel kinds for the per-kernel accounting.
+enum KernelId { K_SCAN, K_ENERGY_INIT, K_ENERGY_ITER, K_DP_SELECT, K_GATHER, K_IDENTITY,
+                K_ENERGY_API, K_COUNT };
+const char *const kKernelNames[K_COUNT] = {"k_scan", "k_energy_init", "k_energy_iter",
+                                           "k_dp_select", "k_gather", "k_identity_O",
+                                           "k_energy_api"};
+
+// Event-bracketed launches while profiling is on.
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<std::pair<int, size_t>> marks;   // kernel id, index of its start event
+    double ms[K_COUNT] = {};
+    long long launches[K_COUNT] = {};
+    double bytes[K_COUNT] = {};
+    cudaEvent_t next() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void clear() {
+        used = 0;
+        marks.clear();
+        for (int i = 0; i < K_COUNT; ++i) { ms[i] = 0; launches[i] = 0; bytes[i] = 0; }
+    }
+};
+
+long round_up(long v, long m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+struct scpl_ctx {
+    scpl_params p;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    std::string err;
+    // scan
+    DevBuf Y, D, ering, S1, S2, partA, partM, count, starts, nbuf, errw;
+    // carving
+    DevBuf E, SD, O, dirs, rem, st, bof;
+    // host-memory entry point staging
+    DevBuf in_frames, out_frames, seams_dev;
+    DevBuf klog;
+    HostBuf h_small;   // starts + n_buffers + states readback
+    Profiler prof;
+    // summary of the last scpl_carve call
+    int last_nb = 0, last_iter_max = 0;
+    long long last_iter_total = 0;
+    double last_carved_px = 0;
+};
+
+namespace {
+
+scpl_status fail(scpl_ctx *h, scpl_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    return s;
+}
+
+#define SCPL_CUDA(h, call)                                                                 \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            scpl_status s_ = (e_ == cudaErrorMemoryAllocation) ? SCPL_ENOMEM : SCPL_ECUDA; \
+            return fail(h, s_, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,  \
+                        __LINE__);                                                         \
+        }                                                                                  \
+    } while (0)
+
+// Runs `launch` bracketed by events when profiling is on.
+template <class F>
+cudaError_t timed(scpl_ctx *h, int id, F launch) {
+    if (!h->prof.on) return launch();
+    cudaEvent_t a = h->prof.next(), b = h->prof.next();
+    if (!a || !b) return launch();
+    cudaEventRecord(a, h->stream);
+    cudaError_t e = launch();
+    cudaEventRecord(b, h->stream);
+    h->prof.marks.push_back({id, h->prof.used - 2});
+    return e;
+}
+
+scpl_status check_params(const scpl_params *p) {
+    if (!p) return SCPL_EINVAL;
+    if (!(p->alpha >= 0.0) || p->alpha > 1e6) return SCPL_EINVAL;
+    if (p->wg < 0 || p->wm < 0 || p->wg + p->wm == 0) return SCPL_EINVAL;
+    if (p->t_max < 1 || p->t_max > 1024) return SCPL_EINVAL;
+    if (p->maxval_mode != 0 && p->maxval_mode != 1) return SCPL_EINVAL;
+    return SCPL_OK;
+}
+
+long long energy_max(const scpl_params &p) { return 255LL * (8LL * p.wg + p.wm); }
+
+int effective_tmax(const scpl_params &p) { return p.use_buffer ? p.t_max : 1; }
+
+// Overflow limits of the exact integer arithmetic: the DP keys hold a
+// column's cumulative energy in 32 bits, S2 holds t_max * e^2 in 32 bits and
+// the scan keeps e in 16 bits.
+scpl_status check_overflow(scpl_ctx *h, int T, int H) {
+    long long em = energy_max(h->p);
+    long long tb = std::min<long long>(T, effective_tmax(h->p));
+    if (em >= 65536) return fail(h, SCPL_EOVERFLOW, "energy maximum %lld exceeds 16 bits", em);
+    if (em * tb * H >= (1LL << 31))
+        return fail(h, SCPL_EOVERFLOW, "cumulative energy %lld*%lld*%d can exceed 2^31", em, tb,
+                    H);
+    if ((long long)effective_tmax(h->p) * em * em >= (1LL << 32))
+        return fail(h, SCPL_EOVERFLOW, "t_max*emax^2 can exceed 2^32");
+    return SCPL_OK;
+}
+
+// Runs the buffer scan; leaves Y, D (original luma / motion) in the handle and
+// the starts on the host.
+scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
+                     std::vector<int> &starts) {
+    const long ypitch = round_up(W, 16);
+    const long hw = (long)H * W;
+    int gerr = 0;
+    int G = scan_grid_size(H, W, &gerr);
+    if (gerr || G < 1) return fail(h, SCPL_ECUDA, "scan occupancy query failed (%d)", gerr);
+    SCPL_CUDA(h, h->Y.ensure((size_t)T * H * ypitch));
+    SCPL_CUDA(h, h->D.ensure((size_t)T * H * ypitch));
+    SCPL_CUDA(h, h->ering.ensure((size_t)2 * hw * sizeof(uint16_t)));
+    SCPL_CUDA(h, h->S1.ensure((size_t)hw * sizeof(uint32_t)));
+    SCPL_CUDA(h, h->S2.ensure((size_t)hw * sizeof(uint32_t)));
+    SCPL_CUDA(h, h->partA.ensure((size_t)T * G * sizeof(long long)));
+    SCPL_CUDA(h, h->partM.ensure((size_t)T * G * sizeof(int)));
+    SCPL_CUDA(h, h->count.ensure((size_t)T * sizeof(unsigned)));
+    SCPL_CUDA(h, h->starts.ensure((size_t)(T + 1) * sizeof(int)));
+    SCPL_CUDA(h, h->nbuf.ensure(sizeof(int)));
+    SCPL_CUDA(h, h->errw.ensure(sizeof(int)));
+    SCPL_CUDA(h, h->h_small.ensure((size_t)(T + 4) * sizeof(int)));
+    cudaStream_t s = h->stream;
+    SCPL_CUDA(h, cudaMemsetAsync(h->count.p, 0, (size_t)T * sizeof(unsigned), s));
+    SCPL_CUDA(h, cudaMemsetAsync(h->S1.p, 0, (size_t)hw * sizeof(uint32_t), s));
+    SCPL_CUDA(h, cudaMemsetAsync(h->S2.p, 0, (size_t)hw * sizeof(uint32_t), s));
+    SCPL_CUDA(h, cudaMemsetAsync(h->errw.p, 0, sizeof(int), s));
+    ScanArgs a;
+    a.rgb = frames; a.T = T; a.H = H; a.W = W; a.ypitch = ypitch;
+    a.Y = h->Y.as<uint8_t>(); a.D = h->D.as<uint8_t>();
+    a.ering = h->ering.as<uint16_t>();
+    a.S1 = h->S1.as<uint32_t>(); a.S2 = h->S2.as<uint32_t>();
+    a.partA = h->partA.as<long long>(); a.partM = h->partM.as<int>();
+    a.count = h->count.as<unsigned>();
+    a.starts = h->starts.as<int>(); a.n_buffers = h->nbuf.as<int>();
+    a.err = h->errw.as<int>();
+    a.wg = h->p.wg; a.wm = h->p.wm; a.alpha = h->p.alpha;
+    a.t_max = effective_tmax(h->p); a.maxval_mode = h->p.maxval_mode;
+    a.maxval_theory = energy_max(h->p);
+    a.spin_limit_ns = SPIN_LIMIT_NS;
+    SCPL_CUDA(h, timed(h, K_SCAN, [&] { return launch_scan(a, G, s); }));
+    if (h->prof.on) h->prof.bytes[K_SCAN] += 28.0 * hw * T;
+    int *hs = h->h_small.as<int>();
+    SCPL_CUDA(h, cudaMemcpyAsync(hs, h->errw.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCPL_CUDA(h, cudaMemcpyAsync(hs + 1, h->nbuf.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SCPL_CUDA(h, cudaMemcpyAsync(hs + 2, h->starts.p, (size_t)(T + 1) * sizeof(int),
+                                 cudaMemcpyDeviceToHost, s));
+    SCPL_CUDA(h, cudaStreamSynchronize(s));
+    if (hs[0] == DEV_ETIMEOUT)
+        return fail(h, SCPL_ETIMEOUT, "buffer scan: a device-wide wait exceeded %llu ns",
+                    SPIN_LIMIT_NS);
+    int nb = hs[1];
+    if (nb < 1 || nb > T) return fail(h, SCPL_ECUDA, "buffer scan returned %d buffers", nb);
+    starts.assign(hs + 2, hs + 2 + nb + 1);
+    return SCPL_OK;
+}
+
+// Workspace of the carving stage for nb buffers.
+scpl_status carve_ws(scpl_ctx *h, int nb, int H, int W0, int kcap, CarveWs &ws,
+                     int klog_stride = 1) {
+    ws.H = H;
+    ws.W0 = W0;
+    ws.pitch = round_up(W0, 32);
+    ws.plane = (long)H * ws.pitch;
+    ws.ngroups = (W0 + 31) / 32;
+    ws.kcap = std::max(kcap, 1);
+    SCPL_CUDA(h, h->E.ensure((size_t)nb * 2 * ws.plane * sizeof(int32_t)));
+    SCPL_CUDA(h, h->SD.ensure((size_t)nb * 2 * ws.plane * sizeof(int32_t)));
+    SCPL_CUDA(h, h->O.ensure((size_t)nb * 2 * ws.plane * sizeof(uint16_t)));
+    SCPL_CUDA(h, h->dirs.ensure((size_t)nb * H * ws.ngroups * 2 * sizeof(uint32_t)));
+    SCPL_CUDA(h, h->rem.ensure((size_t)nb * H * ws.kcap * sizeof(uint16_t)));
+    SCPL_CUDA(h, h->st.ensure((size_t)nb * sizeof(BufState)));
+    SCPL_CUDA(h, h->klog.ensure((size_t)nb * std::max(klog_stride, 1) * sizeof(int)));
+    ws.klog = h->klog.as<int>();
+    ws.klog_stride = std::max(klog_stride, 1);
+    ws.E = h->E.as<int32_t>();
+    ws.SD = h->SD.as<int32_t>();
+    ws.O = h->O.as<uint16_t>();
+    ws.dirs = h->dirs.as<uint32_t>();
+    ws.rem = h->rem.as<uint16_t>();
+    ws.st = h->st.as<BufState>();
+    ws.Y = h->Y.as<uint8_t>();
+    ws.D = h->D.as<uint8_t>();
+    ws.ypitch = round_up(W0, 16);
+    ws.wg = h->p.wg;
+    ws.wm = h->p.wm;
+    if (dp_select_smem_bytes(W0) > 227 * 1024)
+        return fail(h, SCPL_EINVAL, "width %d exceeds the DP's shared-memory row limit", W0);
+    return SCPL_OK;
+}
+
+scpl_status check_frames(scpl_ctx *h, const void *frames, int T, int H, int W) {
+    if (!h) return SCPL_EINVAL;
+    if (!frames) return fail(h, SCPL_EINVAL, "frames is NULL");
+    if (T < 1 || H < 1 || W < 1) return fail(h, SCPL_EINVAL, "T=%d H=%d W=%d must be >= 1", T, H, W);
+    if (H > 65535) return fail(h, SCPL_EINVAL, "H=%d exceeds 65535", H);
+    if (W > 8192) return fail(h, SCPL_EINVAL, "W=%d exceeds 8192", W);
+    return SCPL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void scpl_default_params(scpl_params *p) {
+    if (!p) return;
+    p->alpha = 0.20;
+    p->wg = 1;
+    p->wm = 2;
+    p->t_max = 128;
+    p->use_buffer = 1;
+    p->maxval_mode = 0;
+}
+
+scpl_status scpl_create(const scpl_params *p, void *stream, scpl_handle *out) {
+    if (!out) return SCPL_EINVAL;
+    *out = nullptr;
+    scpl_params def;
+    scpl_default_params(&def);
+    if (!p) p = &def;
+    if (check_params(p) != SCPL_OK) return SCPL_EINVAL;
+    scpl_ctx *h = new (std::nothrow) scpl_ctx();
+    if (!h) return SCPL_ENOMEM;
+    h->p = *p;
+    h->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&h->device) != cudaSuccess) {
+        delete h;
+        return SCPL_ECUDA;
+    }
+    *out = h;
+    return SCPL_OK;
+}
+
+scpl_status scpl_set_stream(scpl_handle h, void *stream) {
+    if (!h) return SCPL_EINVAL;
+    h->stream = (cudaStream_t)stream;
+    return SCPL_OK;
+}
+
+void scpl_destroy(scpl_handle h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    DevBuf *bufs[] = {&h->Y, &h->D, &h->ering, &h->S1, &h->S2, &h->partA, &h->partM,
+                      &h->count, &h->starts, &h->nbuf, &h->errw, &h->E, &h->SD, &h->O,
+                      &h->dirs, &h->rem, &h->st, &h->bof, &h->in_frames, &h->out_frames,
+                      &h->seams_dev, &h->klog};
+    for (DevBuf *b : bufs) b->release();
+    for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+    h->h_small.release();
+    delete h;
+}
+
+const char *scpl_last_error(scpl_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+scpl_status scpl_energy(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                        int32_t *energy) {
+    scpl_status s = check_frames(h, frames, T, H, W);
+    if (s != SCPL_OK) return s;
+    if (!energy) return fail(h, SCPL_EINVAL, "energy is NULL");
+    SCPL_CUDA(h, timed(h, K_ENERGY_API, [&] {
+                  return launch_energy_api(frames, T, H, W, h->p.wg, h->p.wm, energy, h->stream);
+              }));
+    if (h->prof.on) h->prof.bytes[K_ENERGY_API] += 7.0 * T * H * W;
+    return SCPL_OK;
+}
+
+scpl_status scpl_scan(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                      int32_t *buffer_starts, int *n_buffers) {
+    scpl_status s = check_frames(h, frames, T, H, W);
+    if (s != SCPL_OK) return s;
+    if ((s = check_overflow(h, T, H)) != SCPL_OK) return s;
+    std::vector<int> starts;
+    if ((s = run_scan(h, frames, T, H, W, starts)) != SCPL_OK) return s;
+    if (buffer_starts) std::copy(starts.begin(), starts.end(), buffer_starts);
+    if (n_buffers) *n_buffers = (int)starts.size() - 1;
+    return SCPL_OK;
+}
+
+scpl_status scpl_seams(scpl_handle h, const int32_t *energy, int H, int W, int k, int16_t *cols,
+                       int *k_eff) {
+    scpl_status s = check_frames(h, energy, 1, H, W);
+    if (s != SCPL_OK) return s;
+    if (!cols || !k_eff) return fail(h, SCPL_EINVAL, "cols and k_eff must not be NULL");
+    if (k < 1) return fail(h, SCPL_EINVAL, "k=%d must be >= 1", k);
+    CarveWs ws;
+    int kc = std::min(k, W);
+    if ((s = carve_ws(h, 1, H, W, kc, ws)) != SCPL_OK) return s;
+    cudaStream_t st = h->stream;
+    SCPL_CUDA(h, cudaMemcpy2DAsync(ws.E, ws.pitch * sizeof(int32_t), energy,
+                                   (size_t)W * sizeof(int32_t), (size_t)W * sizeof(int32_t), H,
+                                   cudaMemcpyDeviceToDevice, st));
+    SCPL_CUDA(h, timed(h, K_IDENTITY, [&] { return launch_identity_O(ws, 1, st); }));
+    SCPL_CUDA(h, h->h_small.ensure(64 + sizeof(BufState)));
+    BufState *hb = reinterpret_cast<BufState *>(h->h_small.as<char>() + 64);
+    SCPL_CUDA(h, cudaStreamSynchronize(st));   // the staging area is reused below
+    *hb = BufState{0, 1, W, 0, 0, 0, W - kc, 0};
+    SCPL_CUDA(h, cudaMemcpyAsync(ws.st, hb, sizeof(BufState), cudaMemcpyHostToDevice, st));
+    SCPL_CUDA(h, timed(h, K_DP_SELECT, [&] { return launch_dp_select(ws, 1, k, cols, 0, st); }));
+    SCPL_CUDA(h, cudaMemcpyAsync(hb, ws.st, sizeof(BufState), cudaMemcpyDeviceToHost, st));
+    SCPL_CUDA(h, cudaStreamSynchronize(st));
+    *k_eff = hb->k_eff;
+    return SCPL_OK;
+}
+
+scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W, int target_W,
+                       int k, uint8_t *out, int32_t *buffer_starts, int *n_buffers,
+                       int16_t *seams) {
+    scpl_status s = check_frames(h, frames, T, H, W);
+    if (s != SCPL_OK) return s;
+    if (!out) return fail(h, SCPL_EINVAL, "out is NULL");
+    if (target_W < 2 || target_W > W)
+        return fail(h, SCPL_EINVAL, "target_W=%d must be in [2, W=%d]", target_W, W);
+    if (k < 1) return fail(h, SCPL_EINVAL, "k=%d must be >= 1", k);
+    if ((s = check_overflow(h, T, H)) != SCPL_OK) return s;
+
+    std::vector<int> starts;
+    if ((s = run_scan(h, frames, T, H, W, starts)) != SCPL_OK) return s;
+    const int nb = (int)starts.size() - 1;
+    const int remove = W - target_W;
+    CarveWs ws;
+    if ((s = carve_ws(h, nb, H, W, std::min(k, std::max(remove, 1)), ws, remove)) != SCPL_OK)
+        return s;
+    cudaStream_t st = h->stream;
+
+    // per-buffer states and the frame -> buffer map
+    SCPL_CUDA(h, h->bof.ensure((size_t)T * sizeof(int)));
+    size_t need = 64 + (size_t)nb * sizeof(BufState) + (size_t)T * sizeof(int) +
+                  (size_t)nb * std::max(remove, 1) * sizeof(int);
+    SCPL_CUDA(h, h->h_small.ensure(need));
+    BufState *hb = reinterpret_cast<BufState *>(h->h_small.as<char>() + 64);
+    int *hbof = reinterpret_cast<int *>(hb + nb);
+    int *hklog = hbof + T;
+    for (int b = 0; b < nb; ++b) {
+        hb[b] = BufState{starts[b], starts[b + 1] - starts[b], W, 0, 0, 0, target_W, 0};
+        for (int t = starts[b]; t < starts[b + 1]; ++t) hbof[t] = b;
+    }
+    SCPL_CUDA(h, cudaMemcpyAsync(ws.st, hb, (size_t)nb * sizeof(BufState),
+                                 cudaMemcpyHostToDevice, st));
+    SCPL_CUDA(h, cudaMemcpyAsync(h->bof.p, hbof, (size_t)T * sizeof(int), cudaMemcpyHostToDevice,
+                                 st));
+    const long seam_stride = (long)remove * H;
+
+    if (remove == 0) {
+        SCPL_CUDA(h, timed(h, K_IDENTITY, [&] { return launch_identity_O(ws, nb, st); }));
+    } else {
+        SCPL_CUDA(h, timed(h, K_ENERGY_INIT, [&] { return launch_energy_init(ws, nb, st); }));
+        int iters = (remove + k - 1) / k;
+        for (int guard = 0; guard <= remove; ++guard) {
+            for (int q = 0; q < iters; ++q) {
+                SCPL_CUDA(h, timed(h, K_DP_SELECT, [&] {
+                              return launch_dp_select(ws, nb, k, seams, seam_stride, st);
+                          }));
+                SCPL_CUDA(h, timed(h, K_ENERGY_ITER, [&] { return launch_energy_iter(ws, nb, st); }));
+            }
+            SCPL_CUDA(h, cudaMemcpyAsync(hb, ws.st, (size_t)nb * sizeof(BufState),
+                                         cudaMemcpyDeviceToHost, st));
+            SCPL_CUDA(h, cudaStreamSynchronize(st));
+            int max_rem = 0, min_k = k;
+            for (int b = 0; b < nb; ++b) {
+                int Wc = hb[b].W - hb[b].k_eff;
+                int r = Wc - target_W;
+                if (r > 0) {
+                    max_rem = std::max(max_rem, r);
+                    min_k = std::min(min_k, std::max(hb[b].k_eff, 1));
+                }
+            }
+            if (max_rem == 0) break;
+            iters = (max_rem + min_k - 1) / min_k;
+        }
+    }
+    SCPL_CUDA(h, timed(h, K_GATHER, [&] {
+                  return launch_gather(ws, frames, T, h->bof.as<int>(), target_W, out, st);
+              }));
+
+    // iteration summary (and the algorithmic bytes while profiling)
+    h->last_nb = nb;
+    h->last_iter_max = 0;
+    h->last_iter_total = 0;
+    h->last_carved_px = 0;
+    if (remove > 0) {
+        SCPL_CUDA(h, cudaMemcpyAsync(hklog, ws.klog, (size_t)nb * remove * sizeof(int),
+                                     cudaMemcpyDeviceToHost, st));
+        SCPL_CUDA(h, cudaStreamSynchronize(st));
+        for (int b = 0; b < nb; ++b) {
+            const double Tb = hb[b].nt;
+            int Wc = W, it = 0;
+            while (Wc > target_W && it < remove) {
+                const int ke = hklog[(long)b * remove + it];
+                const int Wn = Wc - ke;
+                h->last_carved_px += (double)H * Wc;
+                if (h->prof.on) {
+                    // DP: E read, direction planes written and read, lists written
+                    h->prof.bytes[K_DP_SELECT] += H * (4.0 * Wc + 0.5 * Wc + 4.0 * ke);
+                    // energy: carved luma of every frame, O and SD read at the old
+                    // width and written at the new one, E written, lists read
+                    if (Wn > target_W)
+                        h->prof.bytes[K_ENERGY_ITER] +=
+                            H * (Tb * Wn + 6.0 * Wc + 10.0 * Wn + 2.0 * ke);
+                    else
+                        h->prof.bytes[K_ENERGY_ITER] += H * (2.0 * Wc + 2.0 * Wn + 2.0 * ke);
+                }
+                Wc = Wn;
+                ++it;
+            }
+            h->last_iter_max = std::max(h->last_iter_max, it);
+            h->last_iter_total += it;
+            if (h->prof.on)   // first iteration: luma and motion of every frame, O, SD, E out
+                h->prof.bytes[K_ENERGY_INIT] += H * (2.0 * Tb * W + 10.0 * W);
+        }
+    }
+    if (h->prof.on) {
+        h->prof.bytes[K_GATHER] += (double)H * target_W * (6.0 * T + 2.0 * nb);
+        if (remove == 0) h->prof.bytes[K_IDENTITY] += 2.0 * H * W * nb;
+    }
+    if (n_buffers || buffer_starts) SCPL_CUDA(h, cudaStreamSynchronize(st));
+    if (buffer_starts) std::copy(starts.begin(), starts.end(), buffer_starts);
+    if (n_buffers) *n_buffers = nb;
+    return SCPL_OK;
+}
+
+scpl_status scpl_carve_host(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                            int target_W, int k, uint8_t *out, int32_t *buffer_starts,
+                            int *n_buffers, int16_t *seams) {
+    scpl_status s = check_frames(h, frames, T, H, W);
+    if (s != SCPL_OK) return s;
+    if (!out) return fail(h, SCPL_EINVAL, "out is NULL");
+    if (target_W < 2 || target_W > W)
+        return fail(h, SCPL_EINVAL, "target_W=%d must be in [2, W=%d]", target_W, W);
+    const size_t in_bytes = (size_t)T * H * W * 3;
+    const size_t out_bytes = (size_t)T * H * target_W * 3;
+    const size_t seam_bytes = (size_t)T * (W - target_W) * H * sizeof(int16_t);
+    SCPL_CUDA(h, h->in_frames.ensure(in_bytes));
+    SCPL_CUDA(h, h->out_frames.ensure(out_bytes));
+    if (seams) SCPL_CUDA(h, h->seams_dev.ensure(std::max<size_t>(seam_bytes, 2)));
+    cudaStream_t st = h->stream;
+    SCPL_CUDA(h, cudaMemcpyAsync(h->in_frames.p, frames, in_bytes, cudaMemcpyHostToDevice, st));
+    int nb = 0;
+    std::vector<int> starts(T + 1);
+    s = scpl_carve(h, h->in_frames.as<uint8_t>(), T, H, W, target_W, k,
+                   h->out_frames.as<uint8_t>(), starts.data(), &nb,
+                   seams ? h->seams_dev.as<int16_t>() : nullptr);
+    if (s != SCPL_OK) return s;
+    SCPL_CUDA(h, cudaMemcpyAsync(out, h->out_frames.p, out_bytes, cudaMemcpyDeviceToHost, st));
+    if (seams)
+        SCPL_CUDA(h, cudaMemcpyAsync(seams, h->seams_dev.p,
+                                     (size_t)nb * (W - target_W) * H * sizeof(int16_t),
+                                     cudaMemcpyDeviceToHost, st));
+    SCPL_CUDA(h, cudaStreamSynchronize(st));
+    if (buffer_starts) std::copy(starts.begin(), starts.begin() + nb + 1, buffer_starts);
+    if (n_buffers) *n_buffers = nb;
+    return SCPL_OK;
+}
+
+scpl_status scpl_set_profiling(scpl_handle h, int on) {
+    if (!h) return SCPL_EINVAL;
+    if (on) {
+        SCPL_CUDA(h, cudaStreamSynchronize(h->stream));
+        h->prof.clear();
+    }
+    h->prof.on = on != 0;
+    return SCPL_OK;
+}
+
+scpl_status scpl_get_stats(scpl_handle h, scpl_stats *out) {
+    if (!h || !out) return SCPL_EINVAL;
+    SCPL_CUDA(h, cudaStreamSynchronize(h->stream));
+    Profiler &pr = h->prof;
+    for (auto &m : pr.marks) {
+        float ms = 0.f;
+        SCPL_CUDA(h, cudaEventElapsedTime(&ms, pr.pool[m.second], pr.pool[m.second + 1]));
+        pr.ms[m.first] += ms;
+        pr.launches[m.first] += 1;
+    }
+    pr.marks.clear();
+    pr.used = 0;
+    std::memset(out, 0, sizeof *out);
+    out->n_buffers = h->last_nb;
+    out->iterations_max = h->last_iter_max;
+    out->iterations_total = h->last_iter_total;
+    out->carved_px = h->last_carved_px;
+    int n = 0;
+    for (int i = 0; i < K_COUNT && n < 8; ++i) {
+        if (pr.launches[i] == 0 && pr.bytes[i] == 0) continue;
+        scpl_kernel_stat &ks = out->kernel[n++];
+        std::snprintf(ks.name, sizeof ks.name, "%s", kKernelNames[i]);
+        ks.launches = pr.launches[i];
+        ks.ms = pr.ms[i];
+        ks.bytes = pr.bytes[i];
+    }
+    out->n_kernels = n;
+    return SCPL_OK;
+}
+
+}  // extern "C"

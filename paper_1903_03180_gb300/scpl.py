@@ -1,0 +1,272 @@
+"""Thin ctypes binding over libscpl's C ABI (include/scpl.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels.  Device buffers are torch CUDA tensors (torch supplies device memory
+and streams), host buffers are numpy arrays or CPU tensors.  The library is
+loaded on first use; a missing library raises instead of falling back to
+anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libscpl.so")
+_lib = None
+
+SCPL_OK, SCPL_EINVAL, SCPL_ENOMEM, SCPL_ECUDA, SCPL_ETIMEOUT, SCPL_EOVERFLOW = range(6)
+STATUS_NAMES = {0: "SCPL_OK", 1: "SCPL_EINVAL", 2: "SCPL_ENOMEM", 3: "SCPL_ECUDA",
+                4: "SCPL_ETIMEOUT", 5: "SCPL_EOVERFLOW"}
+
+# every symbol the header declares, with (restype, argtypes)
+_P, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+
+
+class Params(ctypes.Structure):
+    """scpl_params (Sec. 3.2 alpha, Sec. 3.3 weights, buffer cap and mode)."""
+    _fields_ = [("alpha", ctypes.c_double), ("wg", ctypes.c_int), ("wm", ctypes.c_int),
+                ("t_max", ctypes.c_int), ("use_buffer", ctypes.c_int),
+                ("maxval_mode", ctypes.c_int)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong),
+                ("ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_buffers", ctypes.c_int), ("iterations_max", ctypes.c_int),
+                ("iterations_total", ctypes.c_longlong), ("carved_px", ctypes.c_double),
+                ("n_kernels", ctypes.c_int), ("kernel", KernelStat * 8)]
+
+
+SIGNATURES = {
+    "scpl_default_params": (None, [ctypes.POINTER(Params)]),
+    "scpl_create": (_I, [ctypes.POINTER(Params), _P, ctypes.POINTER(_P)]),
+    "scpl_set_stream": (_I, [_P, _P]),
+    "scpl_destroy": (None, [_P]),
+    "scpl_last_error": (ctypes.c_char_p, [_P]),
+    "scpl_energy": (_I, [_P, _P, _I, _I, _I, _P]),
+    "scpl_scan": (_I, [_P, _P, _I, _I, _I, _P, _P]),
+    "scpl_seams": (_I, [_P, _P, _I, _I, _I, _P, _P]),
+    "scpl_carve": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
+    "scpl_carve_host": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
+    "scpl_set_profiling": (_I, [_P, _I]),
+    "scpl_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
+}
+
+
+class SCPLError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load(path: str = LIB_PATH):
+    """Load libscpl.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None and path == LIB_PATH:
+        return _lib
+    if not os.path.exists(path):
+        raise OSError(f"{path} is missing: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path == LIB_PATH:
+        _lib = lib
+    return lib
+
+
+def _check(h, status):
+    if status != SCPL_OK:
+        msg = load().scpl_last_error(h) if h else b""
+        raise SCPLError(status, (msg or b"").decode(errors="replace"))
+
+
+def _dev_ptr(t, dtype, ndim=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dims")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_ptr(a, dtype, name="array"):
+    if hasattr(a, "numpy"):            # CPU torch tensor
+        a = a.numpy()
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"{name} must be a contiguous {np.dtype(dtype)} array")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def scpl_default_params() -> Params:
+    p = Params()
+    load().scpl_default_params(ctypes.byref(p))
+    return p
+
+
+def scpl_create(params: Params | None = None, stream=None):
+    """Create a handle on the current CUDA device.  `stream` is a
+    torch.cuda.Stream, an integer cudaStream_t, or None (torch's current
+    stream)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    h = ctypes.c_void_p()
+    st = load().scpl_create(ctypes.byref(params) if params is not None else None,
+                            ctypes.c_void_p(sp), ctypes.byref(h))
+    if st != SCPL_OK:
+        raise SCPLError(st, "scpl_create failed")
+    return h
+
+
+def scpl_set_stream(h, stream):
+    sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(h, load().scpl_set_stream(h, ctypes.c_void_p(sp)))
+
+
+def scpl_destroy(h):
+    load().scpl_destroy(h)
+
+
+def scpl_last_error(h) -> str:
+    return (load().scpl_last_error(h) or b"").decode(errors="replace")
+
+
+def scpl_energy(h, frames, energy):
+    """frames: cuda uint8 [T,H,W,3]; energy: cuda int32 [T,H,W] (written)."""
+    import torch
+    fp = _dev_ptr(frames, torch.uint8, 4, "frames")
+    T, H, W, _ = frames.shape
+    ep = _dev_ptr(energy, torch.int32, 3, "energy")
+    if tuple(energy.shape) != (T, H, W):
+        raise ValueError("energy must be [T,H,W]")
+    _check(h, load().scpl_energy(h, fp, T, H, W, ep))
+
+
+def scpl_scan(h, frames) -> np.ndarray:
+    """Buffer starts (int32, n_buffers + 1 entries, last = T)."""
+    import torch
+    fp = _dev_ptr(frames, torch.uint8, 4, "frames")
+    T, H, W, _ = frames.shape
+    starts = np.zeros(T + 1, np.int32)
+    nb = ctypes.c_int()
+    _check(h, load().scpl_scan(h, fp, T, H, W, starts.ctypes.data_as(_P), ctypes.byref(nb)))
+    return starts[: nb.value + 1].copy()
+
+
+def scpl_seams(h, energy, k: int, cols) -> int:
+    """energy: cuda int32 [H,W]; cols: cuda int16 [k,H] (written).  Returns k_eff."""
+    import torch
+    ep = _dev_ptr(energy, torch.int32, 2, "energy")
+    H, W = energy.shape
+    cp = _dev_ptr(cols, torch.int16, 2, "cols")
+    if cols.shape[0] < k or cols.shape[1] != H:
+        raise ValueError("cols must be [k,H]")
+    ke = ctypes.c_int()
+    _check(h, load().scpl_seams(h, ep, H, W, k, cp, ctypes.byref(ke)))
+    return ke.value
+
+
+def scpl_carve(h, frames, target_W: int, k: int, out, seams=None) -> np.ndarray:
+    """frames: cuda uint8 [T,H,W,3]; out: cuda uint8 [T,H,target_W,3];
+    seams: optional cuda int16 [>=n_buffers, W-target_W, H].  Returns the
+    buffer starts."""
+    import torch
+    fp = _dev_ptr(frames, torch.uint8, 4, "frames")
+    T, H, W, _ = frames.shape
+    op = _dev_ptr(out, torch.uint8, 4, "out")
+    if tuple(out.shape) != (T, H, target_W, 3):
+        raise ValueError("out must be [T,H,target_W,3]")
+    sp = None
+    if seams is not None:
+        sp = _dev_ptr(seams, torch.int16, 3, "seams")
+        if seams.shape[1] != W - target_W or seams.shape[2] != H:
+            raise ValueError("seams must be [n_buffers, W-target_W, H]")
+    starts = np.zeros(T + 1, np.int32)
+    nb = ctypes.c_int()
+    _check(h, load().scpl_carve(h, fp, T, H, W, target_W, k, op, starts.ctypes.data_as(_P),
+                                ctypes.byref(nb), sp))
+    return starts[: nb.value + 1].copy()
+
+
+def scpl_carve_host(h, frames, target_W: int, k: int, out, seams=None) -> np.ndarray:
+    """Host-memory form: frames uint8 [T,H,W,3], out uint8 [T,H,target_W,3],
+    seams optional int16 [T, W-target_W, H] (numpy or CPU tensors)."""
+    T, H, W, _ = frames.shape
+    fp = _host_ptr(frames, np.uint8, "frames")
+    op = _host_ptr(out, np.uint8, "out")
+    if tuple(out.shape) != (T, H, target_W, 3):
+        raise ValueError("out must be [T,H,target_W,3]")
+    sp = None if seams is None else _host_ptr(seams, np.int16, "seams")
+    starts = np.zeros(T + 1, np.int32)
+    nb = ctypes.c_int()
+    _check(h, load().scpl_carve_host(h, fp, T, H, W, target_W, k, op, starts.ctypes.data_as(_P),
+                                     ctypes.byref(nb), sp))
+    return starts[: nb.value + 1].copy()
+
+
+def scpl_set_profiling(h, on: bool):
+    _check(h, load().scpl_set_profiling(h, int(on)))
+
+
+def scpl_get_stats(h) -> dict:
+    """Per-kernel launches, event-timed milliseconds and algorithmic bytes,
+    plus the iteration summary of the last carve."""
+    st = Stats()
+    _check(h, load().scpl_get_stats(h, ctypes.byref(st)))
+    kernels = {}
+    for i in range(st.n_kernels):
+        k = st.kernel[i]
+        kernels[k.name.decode()] = {"launches": int(k.launches), "ms": float(k.ms),
+                                    "bytes": float(k.bytes)}
+    return {"n_buffers": st.n_buffers, "iterations_max": st.iterations_max,
+            "iterations_total": int(st.iterations_total), "carved_px": float(st.carved_px),
+            "kernels": kernels}
+
+
+class Retargeter:
+    """Owns one handle; carve() allocates outputs with torch on the frames'
+    device."""
+
+    def __init__(self, alpha: float = 0.20, wg: int = 1, wm: int = 2, t_max: int = 128,
+                 use_buffer: bool = True, maxval_mode: int = 0, stream=None):
+        p = scpl_default_params()
+        p.alpha, p.wg, p.wm, p.t_max = alpha, wg, wm, t_max
+        p.use_buffer, p.maxval_mode = int(use_buffer), maxval_mode
+        self.params = p
+        self.h = scpl_create(p, stream)
+
+    def carve(self, frames, target_W: int, k: int, with_seams: bool = False):
+        import torch
+        T, H, W, _ = frames.shape
+        out = torch.empty((T, H, target_W, 3), dtype=torch.uint8, device=frames.device)
+        seams = None
+        if with_seams:
+            seams = torch.empty((T, W - target_W, H), dtype=torch.int16, device=frames.device)
+        starts = scpl_carve(self.h, frames, target_W, k, out, seams)
+        if seams is not None:
+            seams = seams[: len(starts) - 1]
+        return out, starts, seams
+
+    def close(self):
+        if self.h is not None:
+            scpl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

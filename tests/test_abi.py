@@ -1,0 +1,63 @@
+"""The C-ABI library builds, loads without a GPU and exports every symbol that
+include/scpl.h declares; the binding declares exactly those symbols."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "scpl.h")) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(scpl_[a-z_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1903_03180_gb300 import build, scpl
+    build.build()
+    return scpl.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ["scpl_create", "scpl_energy", "scpl_carve", "scpl_destroy", "scpl_scan",
+                 "scpl_seams", "scpl_carve_host", "scpl_last_error"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_the_header(lib):
+    from paper_1903_03180_gb300 import scpl
+    assert sorted(scpl.SIGNATURES) == _declared()
+
+
+def test_default_params_host_only(lib):
+    from paper_1903_03180_gb300 import scpl
+    p = scpl.scpl_default_params()
+    assert (p.alpha, p.wg, p.wm, p.t_max, p.use_buffer, p.maxval_mode) == (0.2, 1, 2, 128, 1, 0)
+
+
+def test_null_handle_is_rejected_without_a_gpu(lib):
+    from paper_1903_03180_gb300 import scpl
+    assert lib.scpl_energy(None, None, 1, 1, 1, None) == scpl.SCPL_EINVAL
+    assert lib.scpl_carve(None, None, 1, 1, 4, 2, 1, None, None, None, None) == scpl.SCPL_EINVAL
+    assert lib.scpl_create(None, None, None) == scpl.SCPL_EINVAL
+    lib.scpl_destroy(None)
+    assert lib.scpl_last_error(None) == b"null handle"
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_1903_03180_gb300 import scpl
+    with pytest.raises(OSError):
+        scpl.load(str(tmp_path / "libscpl.so"))

@@ -1,0 +1,238 @@
+"""GPU parity: the CUDA library, called through its C ABI, against the CPU
+oracle on the same seeded inputs.  Every output of the method is integer
+(energies, buffer boundaries, seam columns, carved bytes), so the bar is
+equality (tolerance 0)."""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1903_03180_gb300 import scpl
+    return scpl
+
+
+@pytest.fixture(scope="module")
+def synth():
+    from paper_1903_03180_gb300 import synth as s
+    return s
+
+
+def _carve_gpu(lib, frames, target, k, **params):
+    r = lib.Retargeter(**params)
+    out, starts, seams = r.carve(torch.from_numpy(frames).cuda(), target, k, with_seams=True)
+    torch.cuda.synchronize()
+    res = out.cpu().numpy(), starts, seams.cpu().numpy()
+    r.close()
+    return res
+
+
+def _carve_both(orc, lib, frames, target, k, wg=1, wm=2, t_max=128, use_buffer=True,
+                maxval_mode=0, alpha=0.2):
+    ref = orc.carve(frames, target, k, wg=wg, wm=wm, alpha=alpha, t_max=t_max,
+                    use_buffer=use_buffer, maxval_mode=maxval_mode)
+    got = _carve_gpu(lib, frames, target, k, alpha=alpha, wg=wg, wm=wm, t_max=t_max,
+                     use_buffer=use_buffer, maxval_mode=maxval_mode)
+    return ref, got
+
+
+def _assert_same(ref, got):
+    ref_out, ref_starts, ref_seams = ref
+    out, starts, seams = got
+    assert np.array_equal(starts, ref_starts), (starts, ref_starts)
+    assert seams.shape == ref_seams.shape
+    for b in range(len(starts) - 1):
+        assert np.array_equal(seams[b], ref_seams[b]), f"seams of buffer {b} differ"
+    assert np.array_equal(out, ref_out)
+
+
+# ------------------------------------------------------------------ energy
+@pytest.mark.parametrize("T,H,W", [(1, 1, 1), (2, 1, 7), (3, 5, 1), (3, 17, 33), (4, 40, 130)])
+def test_energy_random(orc, lib, T, H, W):
+    r = np.random.default_rng(T * 1000 + H * 10 + W)
+    f = r.integers(0, 256, (T, H, W, 3), dtype=np.uint8)
+    for wg, wm in [(1, 0), (1, 2), (3, 5)]:
+        h = lib.scpl_create(lib.Params(0.2, wg, wm, 128, 1, 0))
+        e = torch.empty((T, H, W), dtype=torch.int32, device="cuda")
+        lib.scpl_energy(h, torch.from_numpy(f).cuda(), e)
+        torch.cuda.synchronize()
+        lib.scpl_destroy(h)
+        assert np.array_equal(e.cpu().numpy(), orc.energy(f, wg, wm))
+
+
+def test_energy_clip(orc, lib, synth):
+    f = synth.clip(5, 360, 640, seed=21)
+    h = lib.scpl_create()
+    e = torch.empty(f.shape[:3], dtype=torch.int32, device="cuda")
+    lib.scpl_energy(h, torch.from_numpy(f).cuda(), e)
+    torch.cuda.synchronize()
+    lib.scpl_destroy(h)
+    assert np.array_equal(e.cpu().numpy(), orc.energy(f))
+
+
+# --------------------------------------------------------------------- scan
+@pytest.mark.parametrize("T,H,W,seed,t_max", [(1, 8, 8, 1, 128), (10, 9, 70, 2, 4),
+                                              (64, 360, 640, 0x5C9 ^ 2, 128),
+                                              (40, 61, 97, 3, 16), (30, 24, 40, 4, 1)])
+def test_scan(orc, lib, synth, T, H, W, seed, t_max):
+    f = synth.clip(T, H, W, seed=seed, cuts=(5, 12) if T >= 30 else None)
+    h = lib.scpl_create(lib.Params(0.2, 1, 2, t_max, 1, 0))
+    starts = lib.scpl_scan(h, torch.from_numpy(f).cuda())
+    lib.scpl_destroy(h)
+    assert np.array_equal(starts, orc.scan(orc.energy(f), t_max=t_max))
+
+
+def test_scan_maxval_theoretical(orc, lib, synth):
+    f = synth.clip(20, 32, 48, seed=5, cuts=(4, 9))
+    h = lib.scpl_create(lib.Params(0.05, 1, 2, 128, 1, 1))
+    starts = lib.scpl_scan(h, torch.from_numpy(f).cuda())
+    lib.scpl_destroy(h)
+    assert np.array_equal(starts, orc.scan(orc.energy(f), alpha=0.05, maxval_mode=1,
+                                           maxval_theory=255 * 10))
+
+
+# ------------------------------------------------------- one SCPL iteration
+@pytest.mark.parametrize("H,W,vmax,k", [(1, 1, 5, 1), (1, 9, 3, 4), (2, 2, 0, 2), (7, 3, 2, 3),
+                                        (33, 31, 4, 8), (50, 1025, 9, 16), (64, 2049, 1, 32),
+                                        (20, 700, 0, 700), (300, 1920, 2550, 32)])
+def test_seams(orc, lib, H, W, vmax, k):
+    r = np.random.default_rng(H * 7 + W)
+    E = r.integers(0, vmax + 1, (H, W)).astype(np.int32)
+    CE, L, d = orc.dp(E)
+    ref_cols = orc.select(CE[-1], L[-1], k)
+    h = lib.scpl_create()
+    cols = torch.full((k, H), -1, dtype=torch.int16, device="cuda")
+    ke = lib.scpl_seams(h, torch.from_numpy(E).cuda(), k, cols)
+    lib.scpl_destroy(h)
+    assert ke == len(ref_cols)
+    got = cols.cpu().numpy()
+    for s, c in enumerate(ref_cols):
+        assert np.array_equal(got[s], orc.backtrack(d, int(c))), f"seam {s}"
+
+
+# -------------------------------------------------------------------- carve
+def test_carve_still_320x240(orc, lib, synth):
+    """Single 320x240 frame, gradient energy only, 32 seams with k = 8."""
+    f = synth.workload_still_320x240()
+    ref, got = _carve_both(orc, lib, f, 288, 8, wg=1, wm=0, use_buffer=False)
+    _assert_same(ref, got)
+
+
+@pytest.mark.parametrize("T,H,W,target,k,t_max,seed", [
+    (1, 1, 3, 2, 1, 128, 1),       # one row, narrowest
+    (1, 5, 9, 9, 4, 128, 2),       # nothing to remove
+    (2, 7, 40, 20, 64, 128, 3),    # k larger than the parents
+    (6, 48, 80, 64, 4, 4, 4),      # several buffers
+    (9, 33, 129, 100, 1, 3, 5),    # k = 1, ragged width
+    (12, 70, 300, 210, 16, 128, 6),
+    (5, 1, 600, 300, 32, 2, 7),    # H = 1: every column its own parent
+])
+def test_carve_small(orc, lib, synth, T, H, W, target, k, t_max, seed):
+    f = synth.clip(T, H, W, seed=seed)
+    ref, got = _carve_both(orc, lib, f, target, k, t_max=t_max)
+    _assert_same(ref, got)
+
+
+def test_carve_flat_frames_ties(orc, lib):
+    """All-equal energy: every DP choice is a tie (lowest column wins)."""
+    f = np.full((3, 20, 50, 3), 128, np.uint8)
+    ref, got = _carve_both(orc, lib, f, 30, 8)
+    _assert_same(ref, got)
+
+
+def test_carve_raw_classic_per_frame(orc, lib, synth):
+    f = synth.clip(4, 40, 64, seed=8)
+    ref, got = _carve_both(orc, lib, f, 50, 1, use_buffer=False)
+    _assert_same(ref, got)
+
+
+def test_carve_clip_640x360(orc, lib, synth):
+    """64-frame 640x360 clip, motion energy, buffer on, 160 seams, k = 16."""
+    f = synth.workload_clip_640x360()
+    ref, got = _carve_both(orc, lib, f, 480, 16)
+    _assert_same(ref, got)
+
+
+def test_carve_host_matches_device(orc, lib, synth):
+    f = synth.clip(7, 50, 90, seed=9)
+    out_d, starts_d, seams_d = _carve_gpu(lib, f, 70, 5)
+    h = lib.scpl_create()
+    out_h = np.empty((7, 50, 70, 3), np.uint8)
+    seams_h = np.empty((7, 20, 50), np.int16)
+    starts_h = lib.scpl_carve_host(h, f, 70, 5, out_h, seams_h)
+    lib.scpl_destroy(h)
+    assert np.array_equal(starts_h, starts_d)
+    assert np.array_equal(out_h, out_d)
+    assert np.array_equal(seams_h[: len(starts_h) - 1], seams_d)
+
+
+def test_repeat_calls_identical(lib, synth):
+    f = torch.from_numpy(synth.clip(10, 64, 100, seed=10)).cuda()
+    r = lib.Retargeter()
+    a = r.carve(f, 80, 8, with_seams=True)
+    b = r.carve(f, 80, 8, with_seams=True)
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], b[0]) and torch.equal(a[2], b[2])
+    assert np.array_equal(a[1], b[1])
+    r.close()
+
+
+def test_errors(lib):
+    h = lib.scpl_create()
+    f = torch.zeros((1, 4, 4, 3), dtype=torch.uint8, device="cuda")
+    out = torch.zeros((1, 4, 5, 3), dtype=torch.uint8, device="cuda")
+    with pytest.raises(lib.SCPLError):
+        lib.scpl_carve(h, f, 5, 1, out)
+    st = lib.load().scpl_carve(h, f.data_ptr(), 1, 4, 4, 5, 1, out.data_ptr(), None, None, None)
+    assert st == lib.SCPL_EINVAL and "target_W" in lib.scpl_last_error(h)
+    st = lib.load().scpl_carve(h, f.data_ptr(), 1, 4, 4, 3, 0, out.data_ptr(), None, None, None)
+    assert st == lib.SCPL_EINVAL
+    lib.scpl_destroy(h)
+    # a huge height overflows the 32-bit cumulative energy
+    h = lib.scpl_create(lib.Params(0.2, 1, 2, 128, 1, 0))
+    big = torch.zeros((1, 1, 1, 3), dtype=torch.uint8, device="cuda")
+    st = lib.load().scpl_scan(h, big.data_ptr(), 128, 65535, 1, None, None)
+    assert st == lib.SCPL_EOVERFLOW
+    lib.scpl_destroy(h)
+
+
+# ------------------------------------------- full-size 1080p, sampled parity
+@pytest.mark.slow
+def test_carve_1080p_full_size_sampled(orc, lib, synth):
+    """The 300-frame 1920x1080 workload in the same launch configuration the
+    benchmark times: buffer boundaries compared with the oracle's scan, every
+    buffer checked by the carving invariants (disjoint seams, output = input
+    minus the seams' pixels), and the shortest buffer carved by the oracle
+    and compared byte for byte."""
+    f = synth.workload_clip_1080p()
+    T, H, W = f.shape[:3]
+    target, k = 1344, 32
+    out, starts, seams = _carve_gpu(lib, f, target, k)
+    e = orc.energy(f)
+    assert np.array_equal(starts, orc.scan(e))
+    del e
+    for b in range(len(starts) - 1):
+        sb = seams[b].astype(np.int64)
+        srt = np.sort(sb, axis=0)
+        assert (np.diff(srt, axis=0) > 0).all(), "seams overlap"
+        for t in (starts[b], starts[b + 1] - 1):
+            keep = np.ones((H, W), bool)
+            keep[np.arange(H)[None, :].repeat(sb.shape[0], 0), sb] = False
+            assert np.array_equal(out[t], f[t][keep].reshape(H, target, 3))
+    b = int(np.argmin(np.diff(starts)))
+    t0, t1 = starts[b], starts[b + 1]
+    D = orc.motion(f[max(t0 - 1, 0):t1])[1 if t0 > 0 else 0:]
+    ref_out, ref_seams, _ = orc.carve_buffer(f[t0:t1], D, target, k)
+    assert np.array_equal(seams[b], ref_seams)
+    assert np.array_equal(out[t0:t1], ref_out)
