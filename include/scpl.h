@@ -140,6 +140,30 @@ scpl_status scpl_carve_host(scpl_handle h, const uint8_t *frames, int T, int H, 
                             int target_W, int k, uint8_t *out, int32_t *buffer_starts,
                             int *n_buffers, int16_t *seams);
 
+/* scpl_seams without any memory allocation.  The paper has no counterpart:
+ * this exists for callers that must not allocate device memory -- code that is
+ * recording a CUDA graph (allocation is not allowed during stream capture), a
+ * real-time frame loop that cannot take cudaMalloc's implicit synchronisation
+ * of the device, or a host application that hands out all device memory from
+ * its own fixed pool.  It computes exactly what scpl_seams computes (one SCPL
+ * iteration: Eq. 4 DP with parental labels, Eq. 6 per-parent argmin, the
+ * k_eff lowest children traced back), needs no handle, and calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   energy  [device] int32 [H][W], read in place
+ *   cols    [device] int16 [k][H], written as by scpl_seams
+ *   k_eff   [host] receives the number of seams found
+ *   stream  cudaStream_t as void* (NULL = legacy default stream)
+ * Its scratch is one fixed array of about 10 MiB in device memory, reserved on
+ * every GPU that loads the library and held until the process exits.  Limits
+ * (else SCPL_EINVAL): H*W <= 2^21, W <= 4096, k <= 64.  The first call on a
+ * device looks up the array's device address (once per device, with that
+ * device current); make that first call before any stream capture.  All calls
+ * share the one array: calls whose work overlaps on the GPU (other streams,
+ * other threads) race and give wrong seams, so serialise them.  Synchronises
+ * `stream` before returning.  SCPL_ECUDA if a CUDA call fails. */
+scpl_status scpl_seams_noalloc(const int32_t *energy, int H, int W, int k, int16_t *cols,
+                               int *k_eff, void *stream);
+
 /* Per-kernel accounting of the handle's launches (not part of the paper: a
  * measurement aid).  While profiling is on, every kernel launch of the handle
  * is bracketed by CUDA events on the handle's stream, and every scpl_carve

@@ -54,6 +54,7 @@ SIGNATURES = {
     "scpl_seams": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "scpl_carve": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
     "scpl_carve_host": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
+    "scpl_seams_noalloc": (_I, [_P, _I, _I, _I, _P, _P, _P]),
     "scpl_set_profiling": (_I, [_P, _I]),
     "scpl_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
 }
@@ -215,6 +216,27 @@ def scpl_carve_host(h, frames, target_W: int, k: int, out, seams=None) -> np.nda
     _check(h, load().scpl_carve_host(h, fp, T, H, W, target_W, k, op, starts.ctypes.data_as(_P),
                                      ctypes.byref(nb), sp))
     return starts[: nb.value + 1].copy()
+
+
+def scpl_seams_noalloc(energy, k: int, cols, stream=None) -> int:
+    """scpl_seams for callers that may not allocate device memory: works in
+    the library's fixed scratch array (H*W <= 2^21, W <= 4096, k <= 64).
+    energy: cuda int32 [H,W]; cols: cuda int16 [k,H] (written).  Returns k_eff."""
+    import torch
+    ep = _dev_ptr(energy, torch.int32, 2, "energy")
+    H, W = energy.shape
+    cp = _dev_ptr(cols, torch.int16, 2, "cols")
+    if cols.shape[0] < k or cols.shape[1] != H:
+        raise ValueError("cols must be [k,H]")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    ke = ctypes.c_int()
+    st = load().scpl_seams_noalloc(ep, H, W, k, cp, ctypes.byref(ke), ctypes.c_void_p(sp))
+    if st != SCPL_OK:
+        raise SCPLError(st, "scpl_seams_noalloc failed (sizes beyond its fixed scratch "
+                            "give SCPL_EINVAL)")
+    return ke.value
 
 
 def scpl_set_profiling(h, on: bool):
