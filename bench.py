@@ -41,9 +41,11 @@ WORKLOADS = {
 SEEDS = {"clip_1080p_300f": 0x5C9 ^ 3, "clip_360p_64f": 0x5C9 ^ 2, "still_240p": 0x5C9 ^ 1}
 
 
-def make_frames(name: str, rank: int = 0) -> np.ndarray:
+def make_frames(name: str, rank: int = 0, frames: int = 0) -> np.ndarray:
     from paper_1903_03180_gb300 import synth
     T, H, W, _, _, gen, _, _ = WORKLOADS[name]
+    if frames:
+        T = min(T, frames)
     seed = SEEDS[name] + 7919 * rank
     if gen is None:
         return synth.still_frame(H, W, seed)[None]
@@ -179,7 +181,8 @@ def run_native(args) -> None:
 
     name = args.workload
     T, H, W, target, k, _, (wg, wm), use_buffer = WORKLOADS[name]
-    frames_np = make_frames(name, rank)
+    frames_np = make_frames(name, rank, args.frames)
+    T = frames_np.shape[0]
     frames = torch.from_numpy(frames_np).cuda()
     out = torch.empty((T, H, target, 3), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
@@ -278,7 +281,7 @@ def run_native(args) -> None:
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": name, "T": T, "H": H, "W": W, "target_W": target, "k": k,
+            "config": {"workload": name if not args.frames else f"{name}[:{T}]", "T": T, "H": H, "W": W, "target_W": target, "k": k,
                        "seams": W - target, "wg": wg, "wm": wm, "alpha": 0.2,
                        "use_buffer": use_buffer, "buffers": stats["n_buffers"],
                        "mean_buffer_frames": round(T / max(stats["n_buffers"], 1), 2),
@@ -316,6 +319,8 @@ def main():
                     help="frames of the workload the oracle carves per reference step")
     ap.add_argument("--cpu-frames", type=int, default=16,
                     help="frames of the workload the oracle carves for cpu_baseline")
+    ap.add_argument("--frames", type=int, default=0,
+                    help="carve only the first N frames of the workload (smaller profiling case)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

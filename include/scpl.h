@@ -153,7 +153,7 @@ scpl_status scpl_carve_host(scpl_handle h, const uint8_t *frames, int T, int H, 
  *   cols    [device] int16 [k][H], written as by scpl_seams
  *   k_eff   [host] receives the number of seams found
  *   stream  cudaStream_t as void* (NULL = legacy default stream)
- * Its scratch is one fixed array of about 10 MiB in device memory, reserved on
+ * Its scratch is one fixed array of about 9 MiB in device memory, reserved on
  * every GPU that loads the library and held until the process exits.  Limits
  * (else SCPL_EINVAL): H*W <= 2^21, W <= 4096, k <= 64.  The first call on a
  * device looks up the array's device address (once per device, with that

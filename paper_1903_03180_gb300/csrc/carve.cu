@@ -1,16 +1,23 @@
 // SCPL carving of fixed spatiotemporal buffers (Sec. 3.1 and 3.2).
 //
+// Per buffer:
+//   k_energy_init  first iteration: E = sum_t wg*Sobel(Y_t) + SDo, with
+//                  SDo = wm * sum_t D_t kept at original coordinates, O = id.
 // Per buffer and iteration:
-//   k_dp_select  one CTA per buffer: the cumulative-energy DP of Eq. 4 with
-//                packed keys (CE << 32 | dir << 24 | parent label), the
-//                per-parent argmin of Eq. 6, the k_eff lowest children, and
-//                the trace back through the recorded directions into per-row
-//                sorted removal lists.
-//   k_energy     many CTAs per buffer: the origin map O and the summed motion
-//                energy SD are compacted by the removal lists, and the summed
-//                energy of the next iteration, E = sum_t wg*Sobel(carved Y_t) +
-//                SD, is rebuilt by gathering every frame's original luma
-//                through O (the luma itself is never rewritten).
+//   k_dp           one CTA per buffer: the cumulative-energy DP of Eq. 4 with
+//                  each lane holding 4 (or 8) consecutive columns in
+//                  registers, the parent label carried along (Eq. 5), the
+//                  per-parent argmin of Eq. 6, the k_eff lowest children and
+//                  the trace back through the recorded directions into
+//                  per-row sorted removal lists.
+//   k_update       many CTAs per buffer: O and E are compacted by the removal
+//                  lists; only carved pixels whose 3x3 neighbourhood changed
+//                  get their summed gradient recomputed from the frames'
+//                  original luma (gathered through O).  A pixel whose old
+//                  column q has no removed pixel within columns q-2..q+2 in
+//                  rows i-1..i+1 keeps exactly its old neighbourhood (every
+//                  seam moves at most one column per row), so its summed
+//                  energy is the old one.
 // After the last iteration k_gather copies every output pixel's colour from
 // its original column.
 #include "scpl_internal.cuh"
@@ -19,25 +26,14 @@ namespace scpl {
 
 namespace {
 
-constexpr int EN_RB = 8;      // rows per k_energy CTA
-constexpr int EN_CW = 256;    // carved columns per k_energy CTA (= threads)
-constexpr int DP_THREADS = 1024;
-constexpr int DP_PF = 8;      // rows of energy prefetched ahead of the DP
+constexpr int EN_RB = 8;       // rows per k_energy_init CTA
+constexpr int EN_CW = 256;     // columns per k_energy_init CTA (= threads)
+constexpr int UP_THREADS = 256;
+constexpr int DP_MAX_WARPS = 32;
+constexpr int DP_PF = 4;       // rows of energy prefetched ahead of the DP
+constexpr uint32_t INF32 = 0xFFFFFFFFu;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
-
-// Committed view of a buffer's state (applies a pending iteration).
-__device__ __forceinline__ void committed(const BufState &s, int &W, int &slot, int &removed) {
-    if (s.k_eff > 0) {
-        W = s.W - s.k_eff;
-        slot = s.slot ^ 1;
-        removed = s.removed + s.k_eff;
-    } else {
-        W = s.W;
-        slot = s.slot;
-        removed = s.removed;
-    }
-}
 
 // Source column (at the old width) of carved column p, given the ascending
 // removal list r[0..k) of the row: p + #{m : r[m] - m <= p}.
@@ -50,115 +46,281 @@ __device__ __forceinline__ int src_col(const uint16_t *__restrict__ r, int k, in
     return p + lo;
 }
 
+// #{m : r[m] < q} for an ascending list.
+__device__ __forceinline__ int count_less(const uint16_t *__restrict__ r, int k, int q) {
+    int lo = 0, hi = k;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if ((int)r[mid] < q) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int sobel_l1(int a00, int a01, int a02, int a10, int a12, int a20,
+                                        int a21, int a22) {
+    int gx = (a02 + 2 * a12 + a22) - (a00 + 2 * a10 + a20);
+    int gy = (a20 + 2 * a21 + a22) - (a00 + 2 * a01 + a02);
+    return abs(gx) + abs(gy);
+}
+
 // ---------------------------------------------------------------------------
-// k_energy: grid (ceil(W0/EN_CW), ceil(H/EN_RB), nb), EN_CW threads.
-// init = 1: first iteration (O = identity, SD = wm * sum_t D_t), writes slot 0.
-// init = 0: applies the pending removal lists, writes slot ^ 1.
-template <bool INIT>
-__global__ void __launch_bounds__(EN_CW) k_energy(CarveWs ws) {
+// k_energy_init: grid (ceil(W0/EN_CW), ceil(H/EN_RB), nb), EN_CW threads.
+__global__ void __launch_bounds__(EN_CW) k_energy_init(CarveWs ws) {
     const int b = blockIdx.z;
     const BufState st = ws.st[b];
-    int Wn, s_in = 0, s_out = 0, keff = 0;
-    if (INIT) {
-        Wn = ws.W0;
-    } else {
-        keff = st.k_eff;
-        if (keff == 0) return;
-        Wn = st.W - keff;
-        s_in = st.slot;
-        s_out = s_in ^ 1;
-    }
-    const bool need_e = INIT || Wn > st.target;
-    const int p0 = blockIdx.x * EN_CW;
-    const int i0 = blockIdx.y * EN_RB;
-    if (p0 >= Wn || i0 >= ws.H) return;
-
-    __shared__ uint16_t Os[EN_RB + 2][EN_CW + 2];
-    const int tid = threadIdx.x;
-    const int H = ws.H;
-    const long plane = ws.plane, pitch = ws.pitch;
-    const uint16_t *Oin = ws.O + ((long)b * 2 + s_in) * plane;
-    uint16_t *Oout = ws.O + ((long)b * 2 + s_out) * plane;
-    const uint16_t *rem = ws.rem + (long)b * H * ws.kcap;
-
-    for (int q = tid; q < (EN_RB + 2) * (EN_CW + 2); q += EN_CW) {
-        int r = q / (EN_CW + 2), c = q % (EN_CW + 2);
-        int gi = clampi(i0 + r - 1, 0, H - 1);
-        int pc = clampi(p0 + c - 1, 0, Wn - 1);
-        uint16_t o;
-        if (INIT) o = (uint16_t)pc;
-        else o = Oin[(long)gi * pitch + src_col(rem + (long)gi * ws.kcap, keff, pc)];
-        Os[r][c] = o;
-    }
-    __syncthreads();
-
-    const int p = p0 + tid;
-    const bool col_ok = p < Wn;
-    const int32_t *SDin = ws.SD + ((long)b * 2 + s_in) * plane;
-    int32_t *SDout = ws.SD + ((long)b * 2 + s_out) * plane;
+    const int W0 = ws.W0, H = ws.H;
+    const int p0 = blockIdx.x * EN_CW, i0 = blockIdx.y * EN_RB;
+    const int tid = threadIdx.x, p = p0 + tid;
+    if (p >= W0) return;
+    const long pitch = ws.pitch, plane = ws.plane;
+    uint16_t *O = ws.O + (long)b * 2 * plane;
+    int32_t *SDo = ws.SD + (long)b * plane;
+    int32_t *E = ws.E + (long)b * 2 * plane;
     int32_t eacc[EN_RB];
 #pragma unroll
     for (int r = 0; r < EN_RB; ++r) {
         eacc[r] = 0;
-        int i = i0 + r;
-        if (col_ok && i < H) {
-            Oout[(long)i * pitch + p] = Os[r + 1][tid + 1];
-            if (need_e) {
-                int sd = 0;
-                if (INIT) {
-                    for (int t = st.t0; t < st.t0 + st.nt; ++t)
-                        sd += ws.D[((long)t * H + i) * ws.ypitch + p];
-                    sd *= ws.wm;
-                } else {
-                    sd = SDin[(long)i * pitch + src_col(rem + (long)i * ws.kcap, keff, p)];
-                }
-                SDout[(long)i * pitch + p] = sd;
-                eacc[r] = sd;
-            }
+        const int i = i0 + r;
+        if (i < H) {
+            O[(long)i * pitch + p] = (uint16_t)p;
+            int sd = 0;
+            for (int t = st.t0; t < st.t0 + st.nt; ++t)
+                sd += ws.D[((long)t * H + i) * ws.ypitch + p];
+            sd *= ws.wm;
+            SDo[(long)i * pitch + p] = sd;
+            eacc[r] = sd;
         }
     }
-    if (!need_e || !col_ok) return;
-
+    const int pl = max(p - 1, 0), pr = min(p + 1, W0 - 1);
     for (int t = st.t0; t < st.t0 + st.nt; ++t) {
         const uint8_t *Yt = ws.Y + (long)t * H * ws.ypitch;
 #pragma unroll
         for (int r = 0; r < EN_RB; ++r) {
-            int i = i0 + r;
+            const int i = i0 + r;
             if (i < H) {
                 const uint8_t *ru = Yt + (long)clampi(i - 1, 0, H - 1) * ws.ypitch;
                 const uint8_t *rc = Yt + (long)i * ws.ypitch;
                 const uint8_t *rd = Yt + (long)clampi(i + 1, 0, H - 1) * ws.ypitch;
-                int a00 = __ldg(ru + Os[r][tid]), a01 = __ldg(ru + Os[r][tid + 1]),
-                    a02 = __ldg(ru + Os[r][tid + 2]);
-                int a10 = __ldg(rc + Os[r + 1][tid]), a12 = __ldg(rc + Os[r + 1][tid + 2]);
-                int a20 = __ldg(rd + Os[r + 2][tid]), a21 = __ldg(rd + Os[r + 2][tid + 1]),
-                    a22 = __ldg(rd + Os[r + 2][tid + 2]);
-                int gx = (a02 + 2 * a12 + a22) - (a00 + 2 * a10 + a20);
-                int gy = (a20 + 2 * a21 + a22) - (a00 + 2 * a01 + a02);
-                eacc[r] += ws.wg * (abs(gx) + abs(gy));
+                eacc[r] += ws.wg * sobel_l1(__ldg(ru + pl), __ldg(ru + p), __ldg(ru + pr),
+                                            __ldg(rc + pl), __ldg(rc + pr), __ldg(rd + pl),
+                                            __ldg(rd + p), __ldg(rd + pr));
             }
         }
     }
-    int32_t *Eout = ws.E + ((long)b * 2 + s_out) * plane;
 #pragma unroll
     for (int r = 0; r < EN_RB; ++r) {
-        int i = i0 + r;
-        if (i < H) Eout[(long)i * pitch + p] = eacc[r];
+        const int i = i0 + r;
+        if (i < H) E[(long)i * pitch + p] = eacc[r];
     }
 }
 
 // ---------------------------------------------------------------------------
-// k_dp_select: one CTA of DP_THREADS per buffer; thread tid owns the columns
-// tid + m*DP_THREADS, m < MPT.
+// k_update: grid (ceil(H/RB), nb), UP_THREADS threads, dynamic shared memory
+// (see update_smem_bytes).
+//   1. O and E are compacted: each thread gathers 8 consecutive output pixels
+//      (all loads first) and writes them as vectors.
+//   2. The changed pixels of the rows are marked in a bitmap and listed.
+//   3. Each changed pixel's 3x3 original columns are looked up once; then
+//      (pixel, 8-frame group) work items add up the Sobel gradients of the
+//      frames' original luma in shared memory; E is written from the sums.
+constexpr int UP_FG = 8;   // frames per work item of the recompute
+
+__global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ int s_cnt;
+    const int b = blockIdx.y;
+    const BufState st = ws.st[b];
+    const int keff = st.k_eff;
+    if (keff == 0) return;
+    const int Wc = st.W, Wn = Wc - keff;
+    const int s_in = st.slot, s_out = s_in ^ 1;
+    const bool need_e = Wn > st.target;
+    const int H = ws.H, i0 = blockIdx.x * RB;
+    if (i0 >= H) return;
+    const int nrows = min(RB, H - i0);
+    const int tid = threadIdx.x;
+    const long pitch = ws.pitch, plane = ws.plane;
+    const int kcap = ws.kcap;
+    const int nwords0 = (ws.W0 + 31) >> 5;
+    const int list_cap = RB * min(ws.W0, 15 * kcap);
+    uint16_t *rl = reinterpret_cast<uint16_t *>(smraw);   // [RB+2][kcap] lists of rows i0-1..i0+RB
+    size_t off = ((size_t)(RB + 2) * kcap * 2 + 15) & ~(size_t)15;
+    uint32_t *bm = reinterpret_cast<uint32_t *>(smraw + off);   // [RB][nwords0]
+    off += (size_t)RB * nwords0 * 4;
+    uint32_t *list = reinterpret_cast<uint32_t *>(smraw + off);  // [list_cap] (row << 16 | old column)
+    off += (size_t)list_cap * 4;
+    int *acc = reinterpret_cast<int *>(smraw + off);             // [list_cap]
+    off += (size_t)list_cap * 4;
+    uint16_t *ocs = reinterpret_cast<uint16_t *>(smraw + off);   // [list_cap][9]
+    const uint16_t *rem = ws.rem + (long)b * H * kcap;
+
+    for (int x = tid; x < (RB + 2) * keff; x += UP_THREADS) {
+        const int r = x / keff, m = x - r * keff;
+        const int gi = clampi(i0 + r - 1, 0, H - 1);
+        rl[r * kcap + m] = rem[(long)gi * kcap + m];
+    }
+    for (int x = tid; x < nrows * nwords0; x += UP_THREADS) bm[x] = 0;
+    if (tid == 0) s_cnt = 0;
+    __syncthreads();
+
+    // 1. compaction of the origin map and of the summed energy
+    const uint16_t *__restrict__ Oin = ws.O + ((long)b * 2 + s_in) * plane;
+    uint16_t *__restrict__ Oout = ws.O + ((long)b * 2 + s_out) * plane;
+    const int32_t *__restrict__ Ein = ws.E + ((long)b * 2 + s_in) * plane;
+    int32_t *__restrict__ Eout = ws.E + ((long)b * 2 + s_out) * plane;
+    const int chunks = (Wn + 7) >> 3;
+    for (int x = tid; x < nrows * chunks; x += UP_THREADS) {
+        const int r = x / chunks, p0 = (x - r * chunks) * 8;
+        const long roff = (long)(i0 + r) * pitch;
+        const uint16_t *rr = rl + (r + 1) * kcap;
+        int m = 0;
+        {   // removals at or before the source of p0
+            int lo = 0, hi = keff;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if ((int)rr[mid] - mid <= p0) lo = mid + 1; else hi = mid;
+            }
+            m = lo;
+        }
+        int src[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int p = p0 + j;
+            while (m < keff && (int)rr[m] - m <= p) ++m;
+            src[j] = min(p + m, Wc - 1);
+        }
+        uint16_t ov[8];
+        int ev[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) ov[j] = Oin[roff + src[j]];
+        if (need_e) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) ev[j] = __ldcg(Ein + roff + src[j]);
+        }
+        if (p0 + 8 <= Wn) {
+            uint4 o4;
+            o4.x = (uint32_t)ov[0] | ((uint32_t)ov[1] << 16);
+            o4.y = (uint32_t)ov[2] | ((uint32_t)ov[3] << 16);
+            o4.z = (uint32_t)ov[4] | ((uint32_t)ov[5] << 16);
+            o4.w = (uint32_t)ov[6] | ((uint32_t)ov[7] << 16);
+            *reinterpret_cast<uint4 *>(Oout + roff + p0) = o4;
+            if (need_e) {
+                *reinterpret_cast<int4 *>(Eout + roff + p0) = make_int4(ev[0], ev[1], ev[2], ev[3]);
+                *reinterpret_cast<int4 *>(Eout + roff + p0 + 4) =
+                    make_int4(ev[4], ev[5], ev[6], ev[7]);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (p0 + j < Wn) {
+                    Oout[roff + p0 + j] = ov[j];
+                    if (need_e) Eout[roff + p0 + j] = ev[j];
+                }
+            }
+        }
+    }
+    if (!need_e) return;
+
+    // 2. old columns within 2 of a removed pixel in rows i-1, i, i+1
+    const int per_row = 15 * keff;
+    for (int x = tid; x < nrows * per_row; x += UP_THREADS) {
+        const int r = x / per_row, y = x - r * per_row;
+        const int a = y / (5 * keff), z = y - a * 5 * keff;
+        const int mm = z / 5, d = z - mm * 5 - 2;
+        const int c = (int)rl[(r + a) * kcap + mm] + d;
+        if (c >= 0 && c < Wc) atomicOr(&bm[r * nwords0 + (c >> 5)], 1u << (c & 31));
+    }
+    __syncthreads();
+    for (int x = tid; x < nrows * keff; x += UP_THREADS) {
+        const int r = x / keff, mm = x - r * keff;
+        const int c = rl[(r + 1) * kcap + mm];
+        atomicAnd(&bm[r * nwords0 + (c >> 5)], ~(1u << (c & 31)));
+    }
+    __syncthreads();
+    const int nwords = (Wc + 31) >> 5;
+    for (int x = tid; x < nrows * nwords; x += UP_THREADS) {
+        const int r = x / nwords, wd = x - r * nwords;
+        uint32_t bits = bm[r * nwords0 + wd];
+        while (bits) {
+            const int bit = __ffs(bits) - 1;
+            bits &= bits - 1;
+            list[atomicAdd(&s_cnt, 1)] = ((uint32_t)r << 16) | (uint32_t)(wd * 32 + bit);
+        }
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    if (tid == 0 && ws.dirty_count) atomicAdd(ws.dirty_count + b, (unsigned long long)cnt);
+
+    // 3. exact recompute of the changed pixels from every frame's original luma
+    for (int e = tid; e < cnt; e += UP_THREADS) {
+        const int r = (int)(list[e] >> 16), q = (int)(list[e] & 0xFFFFu);
+        const int i = i0 + r;
+        const int p = q - count_less(rl + (r + 1) * kcap, keff, q);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int gi = clampi(i + a - 1, 0, H - 1);
+            const uint16_t *rr = rl + (r + a) * kcap;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int x = clampi(p + c - 1, 0, Wn - 1);
+                ocs[e * 9 + a * 3 + c] = Oin[(long)gi * pitch + src_col(rr, keff, x)];
+            }
+        }
+        acc[e] = 0;
+    }
+    __syncthreads();
+    const int ngroups = (st.nt + UP_FG - 1) / UP_FG;
+    const long fstride = (long)H * ws.ypitch;
+    for (int x = tid; x < cnt * ngroups; x += UP_THREADS) {
+        const int e = x % cnt, fg = x / cnt;
+        const int r = (int)(list[e] >> 16);
+        const int i = i0 + r;
+        const long r0 = (long)clampi(i - 1, 0, H - 1) * ws.ypitch;
+        const long r1 = (long)i * ws.ypitch;
+        const long r2 = (long)clampi(i + 1, 0, H - 1) * ws.ypitch;
+        const uint16_t *oc = ocs + e * 9;
+        const int t_begin = fg * UP_FG, t_end = min(t_begin + UP_FG, st.nt);
+        const uint8_t *Yt = ws.Y + (long)(st.t0 + t_begin) * fstride;
+        int sum = 0;
+#pragma unroll 4
+        for (int t = t_begin; t < t_end; ++t, Yt += fstride) {
+            sum += sobel_l1(__ldg(Yt + r0 + oc[0]), __ldg(Yt + r0 + oc[1]), __ldg(Yt + r0 + oc[2]),
+                            __ldg(Yt + r1 + oc[3]), __ldg(Yt + r1 + oc[5]), __ldg(Yt + r2 + oc[6]),
+                            __ldg(Yt + r2 + oc[7]), __ldg(Yt + r2 + oc[8]));
+        }
+        atomicAdd(&acc[e], sum);
+    }
+    __syncthreads();
+    const int32_t *SDo = ws.SD + (long)b * plane;
+    for (int e = tid; e < cnt; e += UP_THREADS) {
+        const int r = (int)(list[e] >> 16), q = (int)(list[e] & 0xFFFFu);
+        const int i = i0 + r;
+        const int p = q - count_less(rl + (r + 1) * kcap, keff, q);
+        Eout[(long)i * pitch + p] = ws.wg * acc[e] + SDo[(long)i * pitch + ocs[e * 9 + 4]];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_dp: one CTA of 32*NW threads per buffer.  Lane l of warp w holds the V
+// consecutive columns base = (32w + l)*V .. base+V-1 of the current DP row:
+// their cumulative energy (u32) and parent label.  A row step takes the left
+// and right neighbours from the adjacent lanes (shuffles) or, at a warp's
+// edge, from the neighbouring warp's boundary slot of the previous row.
 //
-// Shared memory: keys[2][W0 + 2] (sentinels at both ends) and cand[W0], all
-// uint64; the same bytes are reused by the selection and the trace back.
-template <int MPT>
-__global__ void __launch_bounds__(DP_THREADS, 1)
-k_dp_select(CarveWs ws, int k, int16_t *seams, long seam_stride) {
-    extern __shared__ uint64_t sm[];
+// Ties: the candidates are compared j-1, j, j+1 with a strict "<", so the
+// lowest column wins among equal cumulative energies (the tie reading of
+// Eq. 4 that makes paths non-crossing).
+//
+// Directions: 2 bits per pixel, one u32 word per 4 rows x 4 columns:
+// word [i/4][j/4], bits 8*(i%4) + 2*(j%4).
+template <int V>
+__global__ void __launch_bounds__(DP_MAX_WARPS * 32, 1)
+k_dp(CarveWs ws, int k, int16_t *seams, long seam_stride, int band_blocks) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ uint32_t bnd_c[2][DP_MAX_WARPS][2], bnd_l[2][DP_MAX_WARPS][2];
     __shared__ int s_W, s_slot, s_removed, s_target, s_active, s_cnt;
-    const int b = blockIdx.x, tid = threadIdx.x;
+    const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int NT = blockDim.x, NW = NT >> 5;
     const int H = ws.H;
     if (tid == 0) {
         BufState st = ws.st[b];
@@ -173,149 +335,200 @@ k_dp_select(CarveWs ws, int k, int16_t *seams, long seam_stride) {
     if (!s_active) return;
     const int W = s_W;
     const int32_t *E = ws.E + ((long)b * 2 + s_slot) * ws.plane;
-    uint32_t *dirs = ws.dirs + (long)b * H * ws.ngroups * 2;
-    uint64_t *keysA = sm, *keysB = sm + (ws.W0 + 2), *cand = sm + 2 * (ws.W0 + 2);
     const long pitch = ws.pitch;
-    const int lane = tid & 31;
+    const int base = (w * 32 + lane) * V;
+    const int dstride = ws.dstride;
+    uint32_t *dirs = ws.dirs + (long)b * ws.dbuf;
+    const bool vec = ((pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(E) & 15) == 0);
 
-    // row 0: CE = E, label = column, direction byte 0
+    auto loadE = [&](int i, int (&dst)[V]) {
 #pragma unroll
-    for (int m = 0; m < MPT; ++m) {
-        int j = tid + m * DP_THREADS;
-        if (j < W) keysA[j + 1] = ((uint64_t)(uint32_t)E[j] << 32) | (uint32_t)j;
-    }
-    if (tid == 0) { keysA[0] = keysA[W + 1] = keysB[0] = keysB[W + 1] = KEY_INF; }
-
-    int ereg[DP_PF][MPT];
+        for (int v = 0; v < V; ++v) dst[v] = 0;
+        if (i < H && base < W) {
+            const int32_t *row = E + (long)i * pitch + base;
+            if (vec && base + V <= pitch) {
 #pragma unroll
-    for (int u = 0; u < DP_PF; ++u)
+                for (int v4 = 0; v4 < V; v4 += 4) {
+                    const int4 q = __ldcg(reinterpret_cast<const int4 *>(row + v4));
+                    dst[v4] = q.x; dst[v4 + 1] = q.y; dst[v4 + 2] = q.z; dst[v4 + 3] = q.w;
+                }
+            } else {
 #pragma unroll
-        for (int m = 0; m < MPT; ++m) {
-            int j = tid + m * DP_THREADS, i = 1 + u;
-            ereg[u][m] = (i < H && j < W) ? E[(long)i * pitch + j] : 0;
+                for (int v = 0; v < V; ++v)
+                    if (base + v < W) dst[v] = __ldcg(row + v);
+            }
         }
+    };
+
+    uint32_t cost[V], lab[V];
+    bool valid[V];
+    {
+        int e0[V];
+        loadE(0, e0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            valid[v] = base + v < W;
+            cost[v] = valid[v] ? (uint32_t)e0[v] : INF32;
+            lab[v] = (uint32_t)(base + v);
+        }
+    }
+    if (lane == 0) { bnd_c[0][w][0] = cost[0]; bnd_l[0][w][0] = lab[0]; }
+    if (lane == 31) { bnd_c[0][w][1] = cost[V - 1]; bnd_l[0][w][1] = lab[V - 1]; }
+    int ering[DP_PF][V];
+#pragma unroll
+    for (int u = 0; u < DP_PF; ++u) loadE(1 + u, ering[u]);
+    uint32_t dw[V / 4];
+#pragma unroll
+    for (int g = 0; g < V / 4; ++g) dw[g] = 0;
+    const bool store_dirs = base < ws.W0;
     __syncthreads();
 
-    // rows 1..H-1 (Eq. 4); among equal CE the lowest column wins because the
-    // direction byte (0 = j-1, 1 = j, 2 = j+1) is the next key field
     for (int ib = 1; ib < H; ib += DP_PF) {
 #pragma unroll
         for (int u = 0; u < DP_PF; ++u) {
             const int i = ib + u;
             if (i < H) {
-                const uint64_t *cur = ((i - 1) & 1) ? keysB : keysA;
-                uint64_t *nxt = (i & 1) ? keysB : keysA;
-#pragma unroll
-                for (int m = 0; m < MPT; ++m) {
-                    const int j = tid + m * DP_THREADS;
-                    uint32_t d = 0;
-                    if (j < W) {
-                        uint64_t k0 = cur[j], k1 = cur[j + 1] | (1ull << 24),
-                                 k2 = cur[j + 2] | (2ull << 24);
-                        uint64_t mn = k0 < k1 ? k0 : k1;
-                        mn = mn < k2 ? mn : k2;
-                        d = (uint32_t)(mn >> 24) & 3u;
-                        nxt[j + 1] = (mn & ~KEY_DIR_MASK) + ((uint64_t)(uint32_t)ereg[u][m] << 32);
-                    }
-                    // direction bit planes of this warp's 32 columns
-                    unsigned lo = __ballot_sync(0xffffffffu, d & 1u);
-                    unsigned hi = __ballot_sync(0xffffffffu, (d >> 1) & 1u);
-                    const int g = (tid >> 5) + m * (DP_THREADS / 32);
-                    if (lane == 0 && g * 32 < W) {
-                        uint32_t *dst = dirs + ((long)i * ws.ngroups + g) * 2;
-                        dst[0] = lo;
-                        dst[1] = hi;
-                    }
-                    const int ip = i + DP_PF;
-                    ereg[u][m] = (ip < H && j < W) ? E[(long)ip * pitch + j] : 0;
+                const int sp = (i - 1) & 1;
+                uint32_t lc = __shfl_up_sync(0xffffffffu, cost[V - 1], 1);
+                uint32_t ll = __shfl_up_sync(0xffffffffu, lab[V - 1], 1);
+                uint32_t rc = __shfl_down_sync(0xffffffffu, cost[0], 1);
+                uint32_t rl = __shfl_down_sync(0xffffffffu, lab[0], 1);
+                if (lane == 0) {
+                    lc = w > 0 ? bnd_c[sp][w - 1][1] : INF32;
+                    ll = w > 0 ? bnd_l[sp][w - 1][1] : 0u;
                 }
+                if (lane == 31) {
+                    rc = w < NW - 1 ? bnd_c[sp][w + 1][0] : INF32;
+                    rl = w < NW - 1 ? bnd_l[sp][w + 1][0] : 0u;
+                }
+                uint32_t nc[V], nl[V];
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const uint32_t c0 = v == 0 ? lc : cost[v - 1];
+                    const uint32_t l0 = v == 0 ? ll : lab[v - 1];
+                    const uint32_t c2 = v == V - 1 ? rc : cost[v + 1];
+                    const uint32_t l2 = v == V - 1 ? rl : lab[v + 1];
+                    uint32_t m = c0, l = l0, d = 0;
+                    if (cost[v] < m) { m = cost[v]; l = lab[v]; d = 1; }
+                    if (c2 < m) { m = c2; l = l2; d = 2; }
+                    nc[v] = valid[v] ? m + (uint32_t)ering[u][v] : INF32;
+                    nl[v] = l;
+                    dw[v >> 2] |= d << (8 * (i & 3) + 2 * (v & 3));
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) { cost[v] = nc[v]; lab[v] = nl[v]; }
+                if ((i & 3) == 3 || i == H - 1) {
+                    if (store_dirs) {
+#pragma unroll
+                        for (int g = 0; g < V / 4; ++g)
+                            if (base + 4 * g < ws.W0)
+                                dirs[(long)(i >> 2) * dstride + (base >> 2) + g] = dw[g];
+                    }
+#pragma unroll
+                    for (int g = 0; g < V / 4; ++g) dw[g] = 0;
+                }
+                if (lane == 0) { bnd_c[i & 1][w][0] = cost[0]; bnd_l[i & 1][w][0] = lab[0]; }
+                if (lane == 31) { bnd_c[i & 1][w][1] = cost[V - 1]; bnd_l[i & 1][w][1] = lab[V - 1]; }
+                loadE(i + DP_PF, ering[u]);
                 __syncthreads();
             }
         }
     }
-    const uint64_t *last = ((H - 1) & 1) ? keysB : keysA;
-    uint64_t *segmin = ((H - 1) & 1) ? keysA : keysB;   // the other row buffer
 
     // ---- Eq. 6: least (CE, column) child of every parent --------------------
-    for (int j = tid; j < W; j += DP_THREADS) segmin[j] = KEY_INF;
+    const int W0 = ws.W0;
+    uint64_t *segmin = reinterpret_cast<uint64_t *>(smraw);   // [W0]
+    uint64_t *cand = segmin + W0;                             // [W0]
+    int *sel = reinterpret_cast<int *>(cand + W0);            // [W0]
+    int *pos = sel + W0;                                      // [W0]
+    uint32_t *band = reinterpret_cast<uint32_t *>(pos + W0);  // [2][band_blocks*dstride]
+    for (int j = tid; j < W; j += NT) segmin[j] = ~0ull;
     __syncthreads();
-    for (int j = tid; j < W; j += DP_THREADS) {
-        uint64_t key = last[j + 1];
-        uint32_t lab = (uint32_t)key & LABEL_MASK;
-        atomicMin((unsigned long long *)&segmin[lab],
-                  (unsigned long long)((key & 0xFFFFFFFF00000000ull) | (uint32_t)j));
+    {
+        // runs of equal labels inside the lane's columns, one atomic per run
+        uint64_t run = ~0ull;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            if (valid[v]) {
+                const uint64_t key = ((uint64_t)cost[v] << 32) | (uint32_t)(base + v);
+                run = key < run ? key : run;
+                const bool last_of_run = (v == V - 1) || !valid[v + 1] || lab[v + 1] != lab[v];
+                if (last_of_run) {
+                    atomicMin(reinterpret_cast<unsigned long long *>(&segmin[lab[v]]),
+                              (unsigned long long)run);
+                    run = ~0ull;
+                }
+            }
+        }
     }
     __syncthreads();
-    for (int a = tid; a < W; a += DP_THREADS) {
-        uint64_t v = segmin[a];
-        if (v != KEY_INF) cand[atomicAdd(&s_cnt, 1)] = v;
+    for (int a = tid; a < W; a += NT) {
+        const uint64_t v = segmin[a];
+        if (v != ~0ull) cand[atomicAdd(&s_cnt, 1)] = v;
     }
     __syncthreads();
     const int n = s_cnt;
     int keff = min(k, W - s_target);
     keff = min(keff, n);
-    // rank by (CE, column): keys are distinct because the columns are.  The
-    // row buffers (`last`, `segmin`) are dead now; sel/pos reuse keysA.
-    int *sel = (int *)keysA;            // [keff] end columns in rank order
-    int *pos = sel + W;                 // [keff] rank among the seams by column
-#pragma unroll
-    for (int m = 0; m < MPT; ++m) {
-        const int c = tid + m * DP_THREADS;
-        if (c < n) {
-            const uint64_t v = cand[c];
-            int r = 0;
-            for (int c2 = 0; c2 < n; ++c2) r += cand[c2] < v;
-            if (r < keff) sel[r] = (int)(uint32_t)v;
-        }
+    for (int c = tid; c < n; c += NT) {
+        const uint64_t v = cand[c];
+        int r = 0;
+        for (int c2 = 0; c2 < n; ++c2) r += cand[c2] < v;
+        if (r < keff) sel[r] = (int)(uint32_t)v;
     }
     __syncthreads();
-    for (int r = tid; r < keff; r += DP_THREADS) {
-        int c = sel[r], q = 0;
+    for (int r = tid; r < keff; r += NT) {
+        const int c = sel[r];
+        int q = 0;
         for (int r2 = 0; r2 < keff; ++r2) q += sel[r2] < c;
         pos[r] = q;
     }
     __syncthreads();
 
-    // ---- trace back (Sec. 3.1), bands of direction rows staged in smem ------
-    // staging area: keysB + cand region, (W0 + 2 + W0) * 8 bytes
-    uint32_t *band = (uint32_t *)keysB;
-    const long band_words = ((long)(ws.W0 + 2) + ws.W0) * 2;   // uint32 words available
-    const int row_words = ws.ngroups * 2;
-    int BR = (int)(band_words / row_words);
-    if (BR > H) BR = H;
+    // ---- trace back (Sec. 3.1): bands of direction rows staged in shared
+    // memory, the next band loaded by the non-walking warps meanwhile --------
+    const int nblk = (H + 3) >> 2;
+    const int nbands = (nblk + band_blocks - 1) / band_blocks;
+    const int band_words = band_blocks * dstride;
+    const int wt = min(((keff + 31) >> 5) << 5, NT);   // walker threads, whole warps
+    const bool loaders = wt < NT;
     const uint16_t *Ocur = ws.O + ((long)b * 2 + s_slot) * ws.plane;
     uint16_t *rem = ws.rem + (long)b * H * ws.kcap;
-    int col = 0, mypos = 0;
-    if (tid < keff) { col = sel[tid]; mypos = pos[tid]; }
-    for (int top = H; top > 0; top -= BR) {
-        const int lo = max(top - BR, 0);
-        __syncthreads();
-        const long nw = (long)(top - lo) * row_words;
-        const uint32_t *srcw = dirs + (long)lo * row_words;
-        for (long w = tid; w < nw; w += DP_THREADS) band[w] = __ldcg(srcw + w);
-        __syncthreads();
-        if (tid < keff) {
-            for (int i = top - 1; i >= lo; --i) {
+    auto load_band = [&](int q, int t_begin, int t_step) {
+        const int bhi = nblk - q * band_blocks;
+        const int blo = max(bhi - band_blocks, 0);
+        const int nwd = (bhi - blo) * dstride;
+        const uint32_t *src = dirs + (long)blo * dstride;
+        uint32_t *dst = band + (q & 1) * band_words;
+        for (int x = t_begin; x < nwd; x += t_step) dst[x] = __ldcg(src + x);
+    };
+    load_band(0, tid, NT);
+    __syncthreads();
+    // sel[s] holds seam s's column at the current row while it is traced
+    for (int q = 0; q < nbands; ++q) {
+        if (q + 1 < nbands && loaders && tid >= wt) load_band(q + 1, tid - wt, NT - wt);
+        const int bhi = nblk - q * band_blocks;
+        const int blo = max(bhi - band_blocks, 0);
+        const uint32_t *cur = band + (q & 1) * band_words;
+        const int top = min(bhi * 4, H);
+        for (int sidx = tid; sidx < keff; sidx += NT) {
+            int col = sel[sidx];
+            const int mypos = pos[sidx];
+            for (int i = top - 1; i >= blo * 4; --i) {
                 rem[(long)i * ws.kcap + mypos] = (uint16_t)col;
                 if (seams)
-                    seams[(long)b * seam_stride + (long)(s_removed + tid) * H + i] =
+                    seams[(long)b * seam_stride + (long)(s_removed + sidx) * H + i] =
                         (int16_t)Ocur[(long)i * pitch + col];
-                if (i > 0 && i > lo) {
-                    const uint32_t *wrow = band + (long)(i - lo) * row_words + (col >> 5) * 2;
-                    int d = (int)((wrow[0] >> (col & 31)) & 1u) |
-                            (int)(((wrow[1] >> (col & 31)) & 1u) << 1);
+                if (i > 0) {
+                    const uint32_t word = cur[((i >> 2) - blo) * dstride + (col >> 2)];
+                    const int d = (int)((word >> (8 * (i & 3) + 2 * (col & 3))) & 3u);
                     col += d - 1;
                 }
             }
-            if (lo > 0) {
-                // the step from row lo to row lo-1 needs row lo's directions,
-                // which are in this band (row index 0)
-                const uint32_t *wrow = band + (col >> 5) * 2;
-                int d = (int)((wrow[0] >> (col & 31)) & 1u) |
-                        (int)(((wrow[1] >> (col & 31)) & 1u) << 1);
-                col += d - 1;
-            }
+            sel[sidx] = col;
         }
+        if (q + 1 < nbands && !loaders) load_band(q + 1, tid, NT);
+        __syncthreads();
     }
     if (tid == 0) {
         const int it = ws.st[b].iters;
@@ -355,39 +568,75 @@ __global__ void k_gather(CarveWs ws, const uint8_t *__restrict__ rgb, const int 
     }
 }
 
-template <int MPT>
+int dp_lanes_cols(int W0) { return W0 <= 4096 ? 4 : 8; }
+
+template <int V>
 cudaError_t launch_dp_t(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                         cudaStream_t s) {
-    size_t smem = dp_select_smem_bytes(ws.W0);
-    cudaError_t e = cudaFuncSetAttribute(k_dp_select<MPT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int band_blocks = 0;
+    size_t smem = dp_smem_bytes(ws.W0, ws.H, &band_blocks);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_dp<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_dp_select<MPT><<<nb, DP_THREADS, smem, s>>>(ws, k, seams, seam_stride);
+    const int nw = (ws.W0 + 32 * V - 1) / (32 * V);
+    k_dp<V><<<nb, 32 * nw, smem, s>>>(ws, k, seams, seam_stride, band_blocks);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t dp_select_smem_bytes(int W0) { return ((size_t)(W0 + 2) * 2 + W0) * sizeof(uint64_t); }
+// Dynamic shared memory of k_dp: segmin, cand (u64), sel, pos (int) over W0
+// columns, plus two bands of direction words, as many 4-row blocks as fit.
+size_t dp_smem_bytes(int W0, int H, int *band_blocks) {
+    const size_t fixed = (size_t)W0 * 24;
+    const size_t limit = 227 * 1024 - 4096;   // minus the static shared memory
+    const size_t dstride = (size_t)(W0 + 3) / 4;
+    size_t budget = limit > fixed ? limit - fixed : 0;
+    if (budget > 64 * 1024) budget = 64 * 1024;
+    int bb = (int)(budget / (2 * dstride * 4));
+    const int nblk = (H + 3) / 4;
+    if (bb > nblk) bb = nblk;
+    if (bb < 1) bb = 1;
+    *band_blocks = bb;
+    return fixed + 2 * (size_t)bb * dstride * 4;
+}
+
+// Rows per k_update CTA and its dynamic shared memory.
+size_t update_smem_bytes(int W0, int kcap, int *rows) {
+    const size_t per_row_list = (size_t)(W0 < 15 * kcap ? W0 : 15 * kcap);
+    const size_t nwords0 = (size_t)(W0 + 31) / 32;
+    int rb = 4;
+    size_t bytes = 0;
+    for (; rb >= 1; --rb) {
+        bytes = (((size_t)(rb + 2) * kcap * 2 + 15) & ~(size_t)15) + (size_t)rb * nwords0 * 4 +
+                (size_t)rb * per_row_list * (4 + 4 + 18);
+        if (bytes <= 200 * 1024) break;
+    }
+    if (rb < 1) rb = 1;
+    *rows = rb;
+    return bytes;
+}
 
 cudaError_t launch_energy_init(const CarveWs &ws, int nb, cudaStream_t s) {
     dim3 grid((ws.W0 + EN_CW - 1) / EN_CW, (ws.H + EN_RB - 1) / EN_RB, nb);
-    k_energy<true><<<grid, EN_CW, 0, s>>>(ws);
+    k_energy_init<<<grid, EN_CW, 0, s>>>(ws);
     return cudaGetLastError();
 }
 
-cudaError_t launch_energy_iter(const CarveWs &ws, int nb, cudaStream_t s) {
-    dim3 grid((ws.W0 + EN_CW - 1) / EN_CW, (ws.H + EN_RB - 1) / EN_RB, nb);
-    k_energy<false><<<grid, EN_CW, 0, s>>>(ws);
+cudaError_t launch_update(const CarveWs &ws, int nb, cudaStream_t s) {
+    int rb = 8;
+    size_t smem = update_smem_bytes(ws.W0, ws.kcap, &rb);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((ws.H + rb - 1) / rb, nb);
+    k_update<<<grid, UP_THREADS, smem, s>>>(ws, rb);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dp_select(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                              cudaStream_t s) {
-    int mpt = (ws.W0 + DP_THREADS - 1) / DP_THREADS;
-    if (mpt <= 1) return launch_dp_t<1>(ws, nb, k, seams, seam_stride, s);
-    if (mpt <= 2) return launch_dp_t<2>(ws, nb, k, seams, seam_stride, s);
-    if (mpt <= 4) return launch_dp_t<4>(ws, nb, k, seams, seam_stride, s);
+    if (dp_lanes_cols(ws.W0) == 4) return launch_dp_t<4>(ws, nb, k, seams, seam_stride, s);
     return launch_dp_t<8>(ws, nb, k, seams, seam_stride, s);
 }
 

@@ -1,0 +1,638 @@
+// k_dpc: one SCPL iteration (Sec. 3.1, Eq. 4-6) of a buffer on a thread-block
+// cluster.
+//
+// DP (Eq. 4 with parental labels, Eq. 5).  Warp g of the cluster owns the 96
+// columns [96g, 96g+96) and holds a 128-column window [96g-16, 96g+112) in
+// registers, 4 consecutive columns per lane.  A row step needs only the
+// neighbours in the adjacent lanes (shuffles); the window's outer columns go
+// stale one column per row (trapezoid), so after 16 rows exactly the owned
+// columns are still exact.  Then every warp publishes the 16 owned columns at
+// each of its edges in shared memory, the cluster synchronises once, and each
+// warp refreshes its 16-column halos from its neighbours (same CTA: shared
+// memory; neighbouring CTA: distributed shared memory).  No barrier is taken
+// inside the 16 rows.  The energy rows reach shared memory through TMA bulk
+// copies, four 16-row stages ahead of the DP, one copy per row.
+//
+// Columns outside [0, W) carry energy 2^31: a real cumulative energy is below
+// 2^31 (checked on the host), so the column next to a real one always ends up
+// at 2^31 or more and is never chosen, whatever lies further out.  Among equal
+// cumulative energies the lowest column wins (candidates compared j-1, j, j+1
+// with a strict "<"), which keeps paths non-crossing.
+//
+// Every pixel carries (label << 16 | anchor): the label is the row-0 column of
+// its path (Eq. 5); the anchor is the path's column at the first row of the
+// current trace-back band of rj rows.  At each band's last row the anchors of
+// the owned columns are stored (J), so the trace back can jump a whole band in
+// one look-up.
+//
+// Selection (Eq. 6): each CTA min-reduces (CE << 32 | column) per label over
+// its owned last-row columns and pushes the short list of its parents' minima
+// into CTA 0, which merges them, ranks them and keeps the k_eff lowest.
+//
+// Trace back: CTA 0 follows every selected seam from band to band through J
+// and the band-first-row directions (both bulk-copied into shared memory) and
+// records the seam's column at every band's last row; then each CTA walks all
+// seams through its share of the bands at once (one thread per seam and band),
+// the bands' directions bulk-copied into shared memory, and writes the
+// per-row removal lists.
+#include <cooperative_groups.h>
+
+#include <type_traits>
+
+#include "scpl_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace scpl {
+
+namespace {
+
+constexpr int DPC_WPC = 4;                       // warps per CTA
+constexpr int DPC_V = 4;                         // columns per lane
+constexpr int DPC_R = 16;                        // rows between halo refreshes (= TMA stage)
+constexpr int DPC_OWW = 32 * DPC_V - 2 * DPC_R;  // owned columns per warp: 96
+constexpr int DPC_CW = DPC_WPC * DPC_OWW + 2 * DPC_R;   // columns of a CTA's window: 416
+constexpr int DPC_NST = 4;                       // energy stages in flight
+constexpr int DPC_LMAX = DPC_WPC * DPC_OWW;      // parents a CTA can report: 384
+constexpr size_t DPC_RING = (size_t)DPC_NST * DPC_R * DPC_CW * 4;
+constexpr size_t DPC_STAGE_BUDGET = 96 * 1024;   // trace-back staging
+constexpr uint32_t BIG = 0x80000000u;            // energy of columns outside [0, W)
+constexpr uint32_t INF32 = 0xFFFFFFFFu;
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+
+__host__ __device__ inline size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
+
+// Shared-memory layout after the DP (aliases the energy ring).
+struct PostLayout {
+    size_t segmin, lkeys, llabs, lcnt, cand, sel, pos, js, ds, end;
+    __host__ __device__ PostLayout(int W0, int C, int kcap, int nb, int jstride, int dstride) {
+        size_t o = 0;
+        segmin = o; o = al16(o + (size_t)W0 * 8);
+        lkeys = o;  o = al16(o + (size_t)C * DPC_LMAX * 8);
+        llabs = o;  o = al16(o + (size_t)C * DPC_LMAX * 4);
+        lcnt = o;   o = al16(o + (size_t)C * 4);
+        cand = o;   o = al16(o + (size_t)W0 * 8);
+        sel = o;    o = al16(o + (size_t)kcap * 4);
+        pos = o;    o = al16(o + (size_t)kcap * 4);
+        js = o;     o = al16(o + (size_t)nb * jstride * 2);
+        ds = o;     o = al16(o + (size_t)nb * dstride * 4);
+        end = o;
+    }
+};
+
+// Trace-back walk layout (aliases everything before it).
+struct WalkLayout {
+    size_t stage, cur, pos, end;
+    __host__ __device__ WalkLayout(int kcap, int nbq_max) {
+        stage = 0;
+        cur = al16(DPC_STAGE_BUDGET);
+        pos = al16(cur + (size_t)nbq_max * kcap * 4);
+        end = al16(pos + (size_t)kcap * 4);
+    }
+};
+
+__global__ void __launch_bounds__(DPC_WPC * 32, 1)
+k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    // halo inboxes: [parity][warp][value], filled by the neighbouring warps
+    __shared__ uint32_t inLc[2][DPC_WPC][16], inLl[2][DPC_WPC][16];
+    __shared__ uint32_t inRc[2][DPC_WPC][16], inRl[2][DPC_WPC][16];
+    __shared__ __align__(8) uint64_t mbar[DPC_NST + 2];
+    __shared__ int s_cnt, s_keff;
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int C = (int)cluster.num_blocks();
+    const int crank = (int)cluster.block_rank();
+    const int b = blockIdx.x / C;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int NT = blockDim.x;
+    const int g = crank * DPC_WPC + w;
+    const int nwarps = C * DPC_WPC;
+    const int H = ws.H, W0 = ws.W0, RJ = ws.rj, NB = ws.nbands;
+
+    const BufState st0 = ws.st[b];
+    int W, slot, removed;
+    committed(st0, W, slot, removed);
+    if (W <= st0.target) {
+        if (crank == 0 && tid == 0) {
+            BufState st = st0;
+            st.W = W; st.slot = slot; st.removed = removed; st.k_eff = 0;
+            ws.st[b] = st;
+        }
+        return;
+    }
+
+    const int32_t *E = ws.E + ((long)b * 2 + slot) * ws.plane;
+    const long pitch = ws.pitch;
+    const int c_lo = crank * DPC_WPC * DPC_OWW - DPC_R;     // first column of the CTA window
+    const int woff = w * DPC_OWW + lane * DPC_V;             // lane's offset in the window
+    const int cbase = c_lo + woff;                           // lane's first column
+    const bool owner = lane >= DPC_R / DPC_V && lane < 32 - DPC_R / DPC_V;
+    const int dstride = ws.dstride;
+    uint32_t *dirs = ws.dirs + (long)b * ws.dbuf;
+    uint16_t *J = ws.J + (long)b * NB * ws.jstride;
+    uint32_t *Dfirst = ws.Dfirst + (long)b * NB * dstride;
+
+    // ---- energy ring: stage s holds rows 1+16s .. 16+16s ----------------------
+    uint32_t *ring = reinterpret_cast<uint32_t *>(smraw);
+    const int cp_lo = max(c_lo, 0), cp_hi = (int)min((long)(c_lo + DPC_CW), pitch);
+    const unsigned row_bytes = cp_hi > cp_lo ? (unsigned)(cp_hi - cp_lo) * 4u : 0u;
+    const int nstages = (H - 1 + DPC_R - 1) / DPC_R;
+    auto issue_stage = [&](int s) {   // thread 0 only
+        if (s >= nstages) return;
+        const int r0 = 1 + s * DPC_R, r1 = min(r0 + DPC_R, H);
+        uint64_t *mb = &mbar[s % DPC_NST];
+        mbar_expect_tx(mb, row_bytes * (unsigned)(r1 - r0));
+        if (row_bytes) {
+            uint32_t *dst = ring + (size_t)(s % DPC_NST) * DPC_R * DPC_CW + (cp_lo - c_lo);
+            for (int r = r0; r < r1; ++r)
+                bulk_g2s(dst + (size_t)(r - r0) * DPC_CW, E + (long)r * pitch + cp_lo, row_bytes,
+                         mb);
+        }
+    };
+    if (tid == 0) {
+        for (int i = 0; i < DPC_NST + 2; ++i) mbar_init(&mbar[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int s = 0; s < DPC_NST; ++s) issue_stage(s);
+
+    // ---- row 0 ----------------------------------------------------------------
+    uint32_t cost[DPC_V], lab[DPC_V];
+#pragma unroll
+    for (int v = 0; v < DPC_V; ++v) {
+        const int c = cbase + v;
+        cost[v] = (c >= 0 && c < W) ? (uint32_t)__ldcg(E + c) : BIG;
+        const uint32_t cc = (uint32_t)c & 0xFFFFu;
+        lab[v] = (cc << 16) | cc;
+    }
+    if (H == 1 && owner) {
+#pragma unroll
+        for (int v = 0; v < DPC_V; ++v) {
+            const int c = cbase + v;
+            if (c >= 0 && c < W0) J[c] = (uint16_t)(lab[v] & 0xFFFFu);
+        }
+    }
+    uint32_t dw = 0;
+    bool valid[DPC_V];
+#pragma unroll
+    for (int v = 0; v < DPC_V; ++v) valid[v] = cbase + v >= 0 && cbase + v < W;
+    cluster.sync();   // every CTA has read the buffer state and initialised its barriers
+
+    // ---- rows 1 .. H-1, one 16-row TMA stage at a time ------------------------
+    // Stage s holds rows 16s+1 .. 16s+16; its last row is where the halos are
+    // refreshed.  Band boundaries are multiples of 16, so a band's first row is
+    // always a stage's last row (ro = 15) and its last row is ro = 14.
+    // Directions are kept per 16-row group G (rows 16G .. 16G+15) as one uint4
+    // per 4 columns: component b holds rows 16G+4b .. 16G+4b+3, 2 bits each.
+    uint32_t wq0 = 0, wq1 = 0, wq2 = 0, wq3 = 0;   // the current group's block words
+    auto store_group = [&](int G) {
+        if (owner && cbase >= 0 && cbase < W0) {
+            reinterpret_cast<uint4 *>(dirs)[(long)G * dstride + (cbase >> 2)] =
+                make_uint4(wq0, wq1, wq2, wq3);
+            if (((16 * G) % RJ) == 0) Dfirst[(long)((16 * G) / RJ) * dstride + (cbase >> 2)] = wq0;
+        }
+        wq0 = wq1 = wq2 = wq3 = 0;
+    };
+    auto stage_rows = [&](int s, auto guarded) {
+        constexpr bool GUARD = decltype(guarded)::value;
+        const uint32_t *rs = ring + (size_t)(s % DPC_NST) * DPC_R * DPC_CW + woff;
+        const int ibase = 1 + DPC_R * s;
+        const bool band_edge = ((ibase + DPC_R - 1) % RJ) == 0;   // row 16s+16 starts a band
+#pragma unroll
+        for (int ro = 0; ro < DPC_R; ++ro) {
+            const int i = ibase + ro;
+            if (!GUARD || i < H) {
+                const uint4 ev = *reinterpret_cast<const uint4 *>(rs + ro * DPC_CW);
+                const uint32_t e[DPC_V] = {valid[0] ? ev.x : BIG, valid[1] ? ev.y : BIG,
+                                           valid[2] ? ev.z : BIG, valid[3] ? ev.w : BIG};
+                const uint32_t lc = __shfl_up_sync(0xffffffffu, cost[DPC_V - 1], 1);
+                const uint32_t ll = __shfl_up_sync(0xffffffffu, lab[DPC_V - 1], 1);
+                const uint32_t rc = __shfl_down_sync(0xffffffffu, cost[0], 1);
+                const uint32_t rl = __shfl_down_sync(0xffffffffu, lab[0], 1);
+                uint32_t nc[DPC_V], nl[DPC_V], dbyte = 0;
+#pragma unroll
+                for (int v = 0; v < DPC_V; ++v) {
+                    const uint32_t c0 = v == 0 ? lc : cost[v - 1];
+                    const uint32_t l0 = v == 0 ? ll : lab[v - 1];
+                    const uint32_t c2 = v == DPC_V - 1 ? rc : cost[v + 1];
+                    const uint32_t l2 = v == DPC_V - 1 ? rl : lab[v + 1];
+                    // the cost chain is two integer mins; the first index that
+                    // attains the minimum (lowest column) is chosen off the chain
+                    const uint32_t m = min(min(c0, cost[v]), c2);
+                    const bool p0 = c0 == m, p1 = cost[v] == m;
+                    nc[v] = m + e[v];
+                    nl[v] = p0 ? l0 : (p1 ? lab[v] : l2);
+                    dbyte |= (p0 ? 0u : (p1 ? 1u : 2u)) << (2 * v);
+                }
+#pragma unroll
+                for (int v = 0; v < DPC_V; ++v) { cost[v] = nc[v]; lab[v] = nl[v]; }
+                if (ro == DPC_R - 1 && band_edge) {
+#pragma unroll
+                    for (int v = 0; v < DPC_V; ++v)
+                        lab[v] = (lab[v] & 0xFFFF0000u) | ((uint32_t)(cbase + v) & 0xFFFFu);
+                }
+                dw |= dbyte << (8 * ((1 + ro) & 3));
+                if (((1 + ro) & 3) == 3) {   // row i closes a 4-row block
+                    if (ro == 2) wq0 = dw;
+                    if (ro == 6) wq1 = dw;
+                    if (ro == 10) wq2 = dw;
+                    if (ro == 14) { wq3 = dw; }
+                    dw = 0;
+                    if (ro == 14) store_group(s);   // rows 16s .. 16s+15 are complete
+                }
+                if (ro == DPC_R - 2 && band_edge && owner) {   // a band's last row
+                    uint16_t *Jrow = J + (long)(i / RJ) * ws.jstride;
+#pragma unroll
+                    for (int v = 0; v < DPC_V; ++v) {
+                        const int c = cbase + v;
+                        if (c >= 0 && c < W0) Jrow[c] = (uint16_t)(lab[v] & 0xFFFFu);
+                    }
+                }
+            }
+        }
+    };
+    for (int s = 0; s < nstages; ++s) {
+        mbar_wait(&mbar[s % DPC_NST], (unsigned)(s / DPC_NST) & 1u, ws.err, WAIT_NS);
+        const int ibase = 1 + DPC_R * s;
+        if (ibase + DPC_R - 1 < H) stage_rows(s, std::false_type{});
+        else stage_rows(s, std::true_type{});
+        const int ilast = ibase + DPC_R - 1;   // the stage's last row
+        if (ilast < H - 1) {
+            // the slot of stage s is refilled with stage s+NST once every warp
+            // of this CTA is past it; account its bytes now
+            if (tid == 0 && s + DPC_NST < nstages) {
+                const int r0 = 1 + (s + DPC_NST) * DPC_R, r1 = min(r0 + DPC_R, H);
+                mbar_expect_tx(&mbar[s % DPC_NST], row_bytes * (unsigned)(r1 - r0));
+            }
+            // push the owned edge strips into the neighbours' inboxes (remote
+            // stores across CTAs), synchronise, then read the own inboxes
+            const int par = s & 1;
+            if (lane >= 24 && lane < 28 && g + 1 < nwarps) {
+                uint32_t *dc, *dl;
+                if (w < DPC_WPC - 1) {
+                    dc = &inLc[par][w + 1][0];
+                    dl = &inLl[par][w + 1][0];
+                } else {
+                    dc = cluster.map_shared_rank(&inLc[par][0][0], crank + 1);
+                    dl = cluster.map_shared_rank(&inLl[par][0][0], crank + 1);
+                }
+#pragma unroll
+                for (int v = 0; v < DPC_V; ++v) {
+                    dc[(lane - 24) * 4 + v] = cost[v];
+                    dl[(lane - 24) * 4 + v] = lab[v];
+                }
+            }
+            if (lane >= 4 && lane < 8 && g > 0) {
+                uint32_t *dc, *dl;
+                if (w > 0) {
+                    dc = &inRc[par][w - 1][0];
+                    dl = &inRl[par][w - 1][0];
+                } else {
+                    dc = cluster.map_shared_rank(&inRc[par][DPC_WPC - 1][0], crank - 1);
+                    dl = cluster.map_shared_rank(&inRl[par][DPC_WPC - 1][0], crank - 1);
+                }
+#pragma unroll
+                for (int v = 0; v < DPC_V; ++v) {
+                    dc[(lane - 4) * 4 + v] = cost[v];
+                    dl[(lane - 4) * 4 + v] = lab[v];
+                }
+            }
+            cluster.sync();
+            // refill: each warp's lane 0 copies a quarter of the stage's rows
+            if (lane == 0 && s + DPC_NST < nstages && row_bytes) {
+                const int sn = s + DPC_NST;
+                const int r0 = 1 + sn * DPC_R, r1 = min(r0 + DPC_R, H);
+                uint32_t *dst = ring + (size_t)(sn % DPC_NST) * DPC_R * DPC_CW + (cp_lo - c_lo);
+                for (int r = r0 + w * (DPC_R / DPC_WPC);
+                     r < min(r0 + (w + 1) * (DPC_R / DPC_WPC), r1); ++r)
+                    bulk_g2s(dst + (size_t)(r - r0) * DPC_CW, E + (long)r * pitch + cp_lo,
+                             row_bytes, &mbar[sn % DPC_NST]);
+            }
+            if (lane < 4) {
+#pragma unroll
+                for (int v = 0; v < DPC_V; ++v) {
+                    cost[v] = g == 0 ? INF32 : inLc[par][w][lane * 4 + v];
+                    lab[v] = inLl[par][w][lane * 4 + v];
+                }
+            }
+            if (lane >= 28) {
+#pragma unroll
+                for (int v = 0; v < DPC_V; ++v) {
+                    cost[v] = g == nwarps - 1 ? INF32 : inRc[par][w][(lane - 28) * 4 + v];
+                    lab[v] = inRl[par][w][(lane - 28) * 4 + v];
+                }
+            }
+        }
+    }
+    // the last row: a partial 4-row block, group and band are stored here
+    if (H > 1) {
+        const int il = H - 1;
+        if ((il & 15) != 15) {
+            if ((il & 3) != 3) {
+                const int bq = (il >> 2) & 3;
+                if (bq == 0) wq0 = dw;
+                if (bq == 1) wq1 = dw;
+                if (bq == 2) wq2 = dw;
+                if (bq == 3) wq3 = dw;
+            }
+            store_group(il >> 4);
+        }
+        if ((il % RJ) != RJ - 1 && owner) {
+            uint16_t *Jrow = J + (long)(il / RJ) * ws.jstride;
+#pragma unroll
+            for (int v = 0; v < DPC_V; ++v) {
+                const int c = cbase + v;
+                if (c >= 0 && c < W0) Jrow[c] = (uint16_t)(lab[v] & 0xFFFFu);
+            }
+        }
+    }
+    // directions, anchors and band rows are read back through the async proxy
+    fence_proxy_async();
+    cluster.sync();   // every CTA is done with its energy ring
+
+    // ---- Eq. 6: per-parent minima -------------------------------------------------
+    const PostLayout PL(W0, C, ws.kcap, NB, ws.jstride, dstride);
+    uint64_t *segmin = reinterpret_cast<uint64_t *>(smraw + PL.segmin);
+    uint64_t *lkeys = reinterpret_cast<uint64_t *>(smraw + PL.lkeys);
+    uint32_t *llabs = reinterpret_cast<uint32_t *>(smraw + PL.llabs);
+    int *lcnt = reinterpret_cast<int *>(smraw + PL.lcnt);
+    for (int j = tid; j < W; j += NT) segmin[j] = ~0ull;
+    if (tid == 0) s_cnt = 0;
+    __syncthreads();
+    if (owner) {
+        uint64_t run = ~0ull;
+#pragma unroll
+        for (int v = 0; v < DPC_V; ++v) {
+            const int c = cbase + v;
+            if (c >= 0 && c < W) {
+                const uint64_t key = ((uint64_t)cost[v] << 32) | (uint32_t)c;
+                run = key < run ? key : run;
+                const bool last = v == DPC_V - 1 || c + 1 >= W ||
+                                  (lab[v + (v < DPC_V - 1)] >> 16) != (lab[v] >> 16);
+                if (last) {
+                    atomicMin(reinterpret_cast<unsigned long long *>(&segmin[lab[v] >> 16]),
+                              (unsigned long long)run);
+                    run = ~0ull;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (crank != 0) {
+        // push this CTA's parents' minima into CTA 0's list for this rank
+        uint64_t *rk = cluster.map_shared_rank(lkeys, 0) + (size_t)crank * DPC_LMAX;
+        uint32_t *rl = cluster.map_shared_rank(llabs, 0) + (size_t)crank * DPC_LMAX;
+        for (int a = tid; a < W; a += NT) {
+            const uint64_t v = segmin[a];
+            if (v != ~0ull) {
+                const int idx = atomicAdd(&s_cnt, 1);
+                if (idx < DPC_LMAX) { rk[idx] = v; rl[idx] = (uint32_t)a; }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) *cluster.map_shared_rank(lcnt + crank, 0) = min(s_cnt, DPC_LMAX);
+    }
+    cluster.sync();
+
+    int *dpx = ws.dpx + (long)b * (1 + ws.kcap);
+    uint16_t *colbot = ws.colbot + (long)b * NB * ws.kcap;
+    if (crank == 0) {
+        uint64_t *cand = reinterpret_cast<uint64_t *>(smraw + PL.cand);
+        int *sel = reinterpret_cast<int *>(smraw + PL.sel);
+        int *pos = reinterpret_cast<int *>(smraw + PL.pos);
+        uint16_t *Js = reinterpret_cast<uint16_t *>(smraw + PL.js);
+        uint32_t *Ds = reinterpret_cast<uint32_t *>(smraw + PL.ds);
+        const unsigned jbytes = (unsigned)NB * ws.jstride * 2u;
+        const unsigned dbytes = (unsigned)NB * dstride * 4u;
+        if (tid == 0) {
+            mbar_expect_tx(&mbar[DPC_NST], jbytes + dbytes);
+            bulk_g2s(Js, J, jbytes, &mbar[DPC_NST]);
+            bulk_g2s(Ds, Dfirst, dbytes, &mbar[DPC_NST]);
+        }
+        for (int r = 1; r < C; ++r) {
+            const int n = lcnt[r];
+            for (int x = tid; x < n; x += NT)
+                atomicMin(reinterpret_cast<unsigned long long *>(
+                              &segmin[llabs[(size_t)r * DPC_LMAX + x]]),
+                          (unsigned long long)lkeys[(size_t)r * DPC_LMAX + x]);
+        }
+        __syncthreads();
+        for (int a = tid; a < W; a += NT) {
+            const uint64_t v = segmin[a];
+            if (v != ~0ull) cand[atomicAdd(&s_cnt, 1)] = v;
+        }
+        __syncthreads();
+        const int n = s_cnt;
+        int keff = min(k, W - st0.target);
+        keff = min(keff, n);
+        for (int c = tid; c < n; c += NT) {
+            const uint64_t v = cand[c];
+            int r = 0;
+            for (int c2 = 0; c2 < n; ++c2) r += cand[c2] < v;
+            if (r < keff) sel[r] = (int)(uint32_t)v;
+        }
+        __syncthreads();
+        for (int r = tid; r < keff; r += NT) {
+            const int c = sel[r];
+            int q = 0;
+            for (int r2 = 0; r2 < keff; ++r2) q += sel[r2] < c;
+            pos[r] = q;
+            dpx[1 + r] = q;
+        }
+        if (tid == 0) {
+            dpx[0] = keff;
+            s_keff = keff;
+        }
+        mbar_wait(&mbar[DPC_NST], 0u, ws.err, WAIT_NS);
+        // each seam's column at every band's last row, band by band upwards
+        for (int s = tid; s < keff; s += NT) {
+            int col = sel[s];
+            for (int q = NB - 1; q >= 0; --q) {
+                colbot[(long)q * ws.kcap + s] = (uint16_t)col;
+                const int top = Js[(long)q * ws.jstride + col];
+                if (q > 0) {
+                    const int r0 = q * RJ;
+                    const uint32_t word = Ds[(long)q * dstride + (top >> 2)];
+                    col = top + (int)((word >> (8 * (r0 & 3) + 2 * (top & 3))) & 3u) - 1;
+                }
+            }
+        }
+    }
+    cluster.sync();
+
+    // ---- trace back: every CTA walks all seams through its bands at once -------
+    const int keff = __ldcg(dpx);
+    const int q0 = (crank * NB) / C, q1 = ((crank + 1) * NB) / C, nbq = q1 - q0;
+    const WalkLayout WL(ws.kcap, (NB + C - 1) / C);
+    uint32_t *stage = reinterpret_cast<uint32_t *>(smraw + WL.stage);
+    int *cur = reinterpret_cast<int *>(smraw + WL.cur);
+    int *pos_s = reinterpret_cast<int *>(smraw + WL.pos);
+    const uint16_t *Ocur = ws.O + ((long)b * 2 + slot) * ws.plane;
+    uint16_t *rem = ws.rem + (long)b * H * ws.kcap;
+    if (nbq > 0) {
+        for (int s = tid; s < keff; s += NT) pos_s[s] = __ldcg(dpx + 1 + s);
+        for (int x = tid; x < nbq * keff; x += NT) {
+            const int qq = x / keff, s = x - qq * keff;
+            cur[x] = __ldcg(colbot + (long)(q0 + qq) * ws.kcap + s);
+        }
+        const int gpb = RJ / 16;   // 16-row direction groups of a full band
+        int cb = (int)(DPC_STAGE_BUDGET / ((size_t)nbq * dstride * 16));
+        cb = max(1, min(cb, gpb));
+        const int rounds = (gpb + cb - 1) / cb;
+        for (int j = 0; j < rounds; ++j) {
+            __syncthreads();   // the previous round's staging is consumed
+            if (tid == 0) {
+                unsigned total = 0;
+                for (int qq = 0; qq < nbq; ++qq) {
+                    const int q = q0 + qq;
+                    const int glo = q * gpb, ghi = (min((q + 1) * RJ, H) + 15) >> 4;
+                    const int shi = ghi - j * cb, slo = max(glo, shi - cb);
+                    if (shi > slo) total += (unsigned)(shi - slo) * dstride * 16u;
+                }
+                mbar_expect_tx(&mbar[DPC_NST + 1], total);
+                for (int qq = 0; qq < nbq; ++qq) {
+                    const int q = q0 + qq;
+                    const int glo = q * gpb, ghi = (min((q + 1) * RJ, H) + 15) >> 4;
+                    const int shi = ghi - j * cb, slo = max(glo, shi - cb);
+                    if (shi > slo)
+                        bulk_g2s(stage + (size_t)qq * cb * dstride * 4,
+                                 dirs + (long)slo * dstride * 4,
+                                 (unsigned)(shi - slo) * dstride * 16u, &mbar[DPC_NST + 1]);
+                }
+            }
+            mbar_wait(&mbar[DPC_NST + 1], (unsigned)j & 1u, ws.err, WAIT_NS);
+            for (int x = tid; x < nbq * keff; x += NT) {
+                const int qq = x / keff, s = x - qq * keff;
+                const int q = q0 + qq;
+                const int rtop = q * RJ, rend = min((q + 1) * RJ, H);
+                const int glo = q * gpb, ghi = (rend + 15) >> 4;
+                const int shi = ghi - j * cb, slo = max(glo, shi - cb);
+                if (shi <= slo) continue;
+                const int i_hi = min(shi * 16, rend) - 1, i_lo = max(slo * 16, rtop);
+                const uint32_t *sq = stage + (size_t)qq * cb * dstride * 4;
+                int col = cur[x];
+                const int mypos = pos_s[s];
+                for (int i = i_hi; i >= i_lo; --i) {
+                    rem[(long)i * ws.kcap + mypos] = (uint16_t)col;
+                    if (seams)
+                        seams[(long)b * seam_stride + (long)(removed + s) * H + i] =
+                            (int16_t)Ocur[(long)i * pitch + col];
+                    if (i > rtop) {
+                        const uint32_t word =
+                            sq[((size_t)((i >> 4) - slo) * dstride + (col >> 2)) * 4 + ((i >> 2) & 3)];
+                        col += (int)((word >> (8 * (i & 3) + 2 * (col & 3))) & 3u) - 1;
+                    }
+                }
+                cur[x] = col;
+            }
+        }
+    }
+
+    if (crank == 0 && tid == 0) {
+        BufState st = st0;
+        st.W = W; st.slot = slot; st.removed = removed;
+        st.k_eff = s_keff;
+        const int it = st0.iters;
+        if (it < ws.klog_stride) ws.klog[(long)b * ws.klog_stride + it] = s_keff;
+        st.iters = it + 1;
+        ws.st[b] = st;
+    }
+}
+
+size_t dpc_smem(int W0, int H, int rj, int kcap, int C) {
+    const int nb = (H + rj - 1) / rj;
+    const int jstride = (W0 + 7) & ~7;
+    const int dstride = (((W0 + 3) / 4) + 3) & ~3;
+    const PostLayout PL(W0, C, kcap, nb, jstride, dstride);
+    const WalkLayout WL(kcap, (nb + C - 1) / C);
+    size_t m = DPC_RING;
+    m = PL.end > m ? PL.end : m;
+    m = WL.end > m ? WL.end : m;
+    return m;
+}
+
+}  // namespace
+
+bool dpc_plan(int W0, int H, int *ctas, int *rj, size_t *smem) {
+    const int nwarps = (W0 + DPC_OWW - 1) / DPC_OWW;
+    const int C = (nwarps + DPC_WPC - 1) / DPC_WPC;
+    if (C > 16) return false;
+    // about four bands per CTA: the walk then takes ~rj rows per CTA
+    int r = (H + 4 * C - 1) / (4 * C);
+    r = ((r + 15) / 16) * 16;
+    if (r < 16) r = 16;
+    size_t bytes = dpc_smem(W0, H, r, W0, C);
+    while (bytes > 220 * 1024 && r < H) {
+        r += 16;
+        bytes = dpc_smem(W0, H, r, W0, C);
+    }
+    if (bytes > 220 * 1024) return false;
+    *ctas = C;
+    *rj = r;
+    *smem = bytes;
+    return true;
+}
+
+bool dpc_available(int W0, int H) {
+    int C = 0, rj = 0;
+    size_t smem = 0;
+    if (!dpc_plan(W0, H, &C, &rj, &smem)) return false;
+    if (cudaFuncSetAttribute(k_dpc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return false;
+    if (C > 8 &&
+        cudaFuncSetAttribute(k_dpc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess)
+        return false;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(DPC_WPC * 32);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_dpc, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return clusters > 0;
+}
+
+cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
+                       cudaStream_t s) {
+    int C = 0, rj = 0;
+    size_t smem = 0;
+    if (!dpc_plan(ws.W0, ws.H, &C, &rj, &smem) || rj != ws.rj) return cudaErrorInvalidValue;
+    smem = dpc_smem(ws.W0, ws.H, ws.rj, ws.kcap, C);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_dpc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (C > 8) {
+        e = cudaFuncSetAttribute(k_dpc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nb * C);
+    cfg.blockDim = dim3(DPC_WPC * 32);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_dpc, ws, k, seams, seam_stride);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+}  // namespace scpl

@@ -35,18 +35,19 @@ constexpr int NA_MAX_K = 64;
 
 constexpr size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
-// Scratch layout: origin map O (u16 per pixel), direction bit planes
-// (two u32 per row and 32-column group), removal lists (u16 [H][k]),
+// Scratch layout: origin map O (u16 per pixel), DP directions (one u32 per
+// 4x4 pixel block, rows of ceil(W/4) words padded to a multiple of 4),
+// removal lists (u16 [H][k]),
 // buffer state and the k_eff log.
 constexpr size_t NA_O_BYTES = align256(NA_MAX_PIXELS * sizeof(uint16_t));
 constexpr size_t NA_DIRS_BYTES =
-    align256((size_t)(NA_MAX_PIXELS / 32 + 2L * 65536) * 2 * sizeof(uint32_t));
+    align256((size_t)(NA_MAX_PIXELS / 16 + NA_MAX_H + NA_MAX_W / 4 + 4) * sizeof(uint32_t));
 constexpr size_t NA_REM_BYTES = align256((size_t)NA_MAX_PIXELS * sizeof(uint16_t));
 constexpr size_t NA_ST_BYTES = align256(sizeof(BufState) + sizeof(int));
 constexpr size_t NA_OFF_DIRS = NA_O_BYTES;
 constexpr size_t NA_OFF_REM = NA_OFF_DIRS + NA_DIRS_BYTES;
 constexpr size_t NA_OFF_ST = NA_OFF_REM + NA_REM_BYTES;
-constexpr size_t NA_SCRATCH_BYTES = NA_OFF_ST + NA_ST_BYTES;   // about 10 MiB
+constexpr size_t NA_SCRATCH_BYTES = NA_OFF_ST + NA_ST_BYTES;   // about 9 MiB
 
 __device__ __align__(256) unsigned char g_scratch[NA_SCRATCH_BYTES];
 
@@ -101,7 +102,17 @@ extern "C" scpl_status scpl_seams_noalloc(const int32_t *energy, int H, int W, i
     ws.W0 = W;
     ws.pitch = W;                       // the caller's map is read in place
     ws.plane = (long)H * W;
-    ws.ngroups = (W + 31) / 32;
+    ws.dstride = (((W + 3) / 4) + 3) & ~3;
+    ws.dbuf = (long)((H + 3) / 4) * ws.dstride;
+    ws.dirty_count = nullptr;
+    ws.err = nullptr;
+    ws.J = nullptr;
+    ws.Dfirst = nullptr;
+    ws.colbot = nullptr;
+    ws.dpx = nullptr;
+    ws.rj = 0;
+    ws.nbands = 0;
+    ws.jstride = 0;
     ws.kcap = kc;
     ws.E = const_cast<int32_t *>(energy);
     ws.SD = nullptr;

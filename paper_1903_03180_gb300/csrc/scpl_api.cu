@@ -64,8 +64,8 @@ constexpr unsigned long long SPIN_LIMIT_NS = 2000000000ull;   // 2 s per device-
 // Kernel kinds for the per-kernel accounting.
 enum KernelId { K_SCAN, K_ENERGY_INIT, K_ENERGY_ITER, K_DP_SELECT, K_GATHER, K_IDENTITY,
                 K_ENERGY_API, K_COUNT };
-const char *const kKernelNames[K_COUNT] = {"k_scan", "k_energy_init", "k_energy_iter",
-                                           "k_dp_select", "k_gather", "k_identity_O",
+const char *const kKernelNames[K_COUNT] = {"k_scan", "k_energy_init", "k_update",
+                                           "k_dp", "k_gather", "k_identity_O",
                                            "k_energy_api"};
 
 // Event-bracketed launches while profiling is on.
@@ -107,7 +107,10 @@ struct scpl_ctx {
     DevBuf E, SD, O, dirs, rem, st, bof;
     // host-memory entry point staging
     DevBuf in_frames, out_frames, seams_dev;
-    DevBuf klog;
+    DevBuf klog, dirty, J, colbot, dpx, Dfirst;
+    // cluster-DP availability per (W0, H) last checked
+    int dpc_W0 = -1, dpc_H = -1;
+    bool dpc_ok = false;
     HostBuf h_small;   // starts + n_buffers + states readback
     Profiler prof;
     // summary of the last scpl_carve call
@@ -242,12 +245,19 @@ scpl_status carve_ws(scpl_ctx *h, int nb, int H, int W0, int kcap, CarveWs &ws,
     ws.W0 = W0;
     ws.pitch = round_up(W0, 32);
     ws.plane = (long)H * ws.pitch;
-    ws.ngroups = (W0 + 31) / 32;
+    ws.dstride = (((W0 + 3) / 4) + 3) & ~3;
+    ws.dbuf = (long)((H + 15) / 16) * 4 * ws.dstride;
+    ws.jstride = (W0 + 7) & ~7;
+    ws.Dfirst = nullptr;
+    SCPL_CUDA(h, h->errw.ensure(sizeof(int)));
+    ws.err = h->errw.as<int>();
     ws.kcap = std::max(kcap, 1);
     SCPL_CUDA(h, h->E.ensure((size_t)nb * 2 * ws.plane * sizeof(int32_t)));
-    SCPL_CUDA(h, h->SD.ensure((size_t)nb * 2 * ws.plane * sizeof(int32_t)));
+    SCPL_CUDA(h, h->SD.ensure((size_t)nb * ws.plane * sizeof(int32_t)));
     SCPL_CUDA(h, h->O.ensure((size_t)nb * 2 * ws.plane * sizeof(uint16_t)));
-    SCPL_CUDA(h, h->dirs.ensure((size_t)nb * H * ws.ngroups * 2 * sizeof(uint32_t)));
+    SCPL_CUDA(h, h->dirs.ensure((size_t)nb * ws.dbuf * sizeof(uint32_t)));
+    SCPL_CUDA(h, h->dirty.ensure((size_t)nb * sizeof(unsigned long long)));
+    ws.dirty_count = h->dirty.as<unsigned long long>();
     SCPL_CUDA(h, h->rem.ensure((size_t)nb * H * ws.kcap * sizeof(uint16_t)));
     SCPL_CUDA(h, h->st.ensure((size_t)nb * sizeof(BufState)));
     SCPL_CUDA(h, h->klog.ensure((size_t)nb * std::max(klog_stride, 1) * sizeof(int)));
@@ -264,8 +274,36 @@ scpl_status carve_ws(scpl_ctx *h, int nb, int H, int W0, int kcap, CarveWs &ws,
     ws.ypitch = round_up(W0, 16);
     ws.wg = h->p.wg;
     ws.wm = h->p.wm;
-    if (dp_select_smem_bytes(W0) > 227 * 1024)
-        return fail(h, SCPL_EINVAL, "width %d exceeds the DP's shared-memory row limit", W0);
+    int bb = 0, rb = 0;
+    if (dp_smem_bytes(W0, H, &bb) > 227 * 1024 - 4096 ||
+        update_smem_bytes(W0, ws.kcap, &rb) > 200 * 1024)
+        return fail(h, SCPL_EINVAL, "width %d exceeds the shared-memory limits", W0);
+    // cluster DP tables (used when the GPU can co-schedule the cluster)
+    if (h->dpc_W0 != W0 || h->dpc_H != H) {
+        h->dpc_ok = dpc_available(W0, H);
+        h->dpc_W0 = W0;
+        h->dpc_H = H;
+    }
+    ws.rj = 0;
+    ws.nbands = 0;
+    ws.J = nullptr;
+    ws.colbot = nullptr;
+    ws.dpx = nullptr;
+    if (h->dpc_ok) {
+        int C = 0, rj = 0;
+        size_t smem = 0;
+        dpc_plan(W0, H, &C, &rj, &smem);
+        ws.rj = rj;
+        ws.nbands = (H + rj - 1) / rj;
+        SCPL_CUDA(h, h->J.ensure((size_t)nb * ws.nbands * ws.jstride * sizeof(uint16_t)));
+        SCPL_CUDA(h, h->Dfirst.ensure((size_t)nb * ws.nbands * ws.dstride * sizeof(uint32_t)));
+        ws.Dfirst = h->Dfirst.as<uint32_t>();
+        SCPL_CUDA(h, h->colbot.ensure((size_t)nb * ws.nbands * ws.kcap * sizeof(uint16_t)));
+        SCPL_CUDA(h, h->dpx.ensure((size_t)nb * (1 + ws.kcap) * sizeof(int)));
+        ws.J = h->J.as<uint16_t>();
+        ws.colbot = h->colbot.as<uint16_t>();
+        ws.dpx = h->dpx.as<int>();
+    }
     return SCPL_OK;
 }
 
@@ -323,7 +361,8 @@ void scpl_destroy(scpl_handle h) {
     DevBuf *bufs[] = {&h->Y, &h->D, &h->ering, &h->S1, &h->S2, &h->partA, &h->partM,
                       &h->count, &h->starts, &h->nbuf, &h->errw, &h->E, &h->SD, &h->O,
                       &h->dirs, &h->rem, &h->st, &h->bof, &h->in_frames, &h->out_frames,
-                      &h->seams_dev, &h->klog};
+                      &h->seams_dev, &h->klog, &h->dirty, &h->J, &h->colbot, &h->dpx,
+                      &h->Dfirst};
     for (DevBuf *b : bufs) b->release();
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
     h->h_small.release();
@@ -366,6 +405,7 @@ scpl_status scpl_seams(scpl_handle h, const int32_t *energy, int H, int W, int k
     int kc = std::min(k, W);
     if ((s = carve_ws(h, 1, H, W, kc, ws)) != SCPL_OK) return s;
     cudaStream_t st = h->stream;
+    SCPL_CUDA(h, cudaMemsetAsync(ws.err, 0, sizeof(int), st));
     SCPL_CUDA(h, cudaMemcpy2DAsync(ws.E, ws.pitch * sizeof(int32_t), energy,
                                    (size_t)W * sizeof(int32_t), (size_t)W * sizeof(int32_t), H,
                                    cudaMemcpyDeviceToDevice, st));
@@ -375,9 +415,16 @@ scpl_status scpl_seams(scpl_handle h, const int32_t *energy, int H, int W, int k
     SCPL_CUDA(h, cudaStreamSynchronize(st));   // the staging area is reused below
     *hb = BufState{0, 1, W, 0, 0, 0, W - kc, 0};
     SCPL_CUDA(h, cudaMemcpyAsync(ws.st, hb, sizeof(BufState), cudaMemcpyHostToDevice, st));
-    SCPL_CUDA(h, timed(h, K_DP_SELECT, [&] { return launch_dp_select(ws, 1, k, cols, 0, st); }));
+    SCPL_CUDA(h, timed(h, K_DP_SELECT, [&] {
+                  return ws.J ? launch_dpc(ws, 1, k, cols, 0, st)
+                              : launch_dp_select(ws, 1, k, cols, 0, st);
+              }));
     SCPL_CUDA(h, cudaMemcpyAsync(hb, ws.st, sizeof(BufState), cudaMemcpyDeviceToHost, st));
+    int *herr = reinterpret_cast<int *>(h->h_small.as<char>());
+    SCPL_CUDA(h, cudaMemcpyAsync(herr, ws.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     SCPL_CUDA(h, cudaStreamSynchronize(st));
+    if (*herr == DEV_ETIMEOUT)
+        return fail(h, SCPL_ETIMEOUT, "a bounded device-side wait ran out in the DP");
     *k_eff = hb->k_eff;
     return SCPL_OK;
 }
@@ -405,7 +452,8 @@ scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W
     // per-buffer states and the frame -> buffer map
     SCPL_CUDA(h, h->bof.ensure((size_t)T * sizeof(int)));
     size_t need = 64 + (size_t)nb * sizeof(BufState) + (size_t)T * sizeof(int) +
-                  (size_t)nb * std::max(remove, 1) * sizeof(int);
+                  (size_t)nb * std::max(remove, 1) * sizeof(int) + 8 +
+                  (size_t)nb * sizeof(unsigned long long);
     SCPL_CUDA(h, h->h_small.ensure(need));
     BufState *hb = reinterpret_cast<BufState *>(h->h_small.as<char>() + 64);
     int *hbof = reinterpret_cast<int *>(hb + nb);
@@ -420,6 +468,7 @@ scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W
                                  st));
     const long seam_stride = (long)remove * H;
 
+    SCPL_CUDA(h, cudaMemsetAsync(ws.dirty_count, 0, (size_t)nb * sizeof(unsigned long long), st));
     if (remove == 0) {
         SCPL_CUDA(h, timed(h, K_IDENTITY, [&] { return launch_identity_O(ws, nb, st); }));
     } else {
@@ -428,9 +477,10 @@ scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W
         for (int guard = 0; guard <= remove; ++guard) {
             for (int q = 0; q < iters; ++q) {
                 SCPL_CUDA(h, timed(h, K_DP_SELECT, [&] {
-                              return launch_dp_select(ws, nb, k, seams, seam_stride, st);
+                              return ws.J ? launch_dpc(ws, nb, k, seams, seam_stride, st)
+                                          : launch_dp_select(ws, nb, k, seams, seam_stride, st);
                           }));
-                SCPL_CUDA(h, timed(h, K_ENERGY_ITER, [&] { return launch_energy_iter(ws, nb, st); }));
+                SCPL_CUDA(h, timed(h, K_ENERGY_ITER, [&] { return launch_update(ws, nb, st); }));
             }
             SCPL_CUDA(h, cudaMemcpyAsync(hb, ws.st, (size_t)nb * sizeof(BufState),
                                          cudaMemcpyDeviceToHost, st));
@@ -458,7 +508,12 @@ scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W
     h->last_iter_total = 0;
     h->last_carved_px = 0;
     if (remove > 0) {
+        unsigned long long *hdirty = reinterpret_cast<unsigned long long *>(
+            h->h_small.as<char>() + 64 + (((size_t)nb * sizeof(BufState) + (size_t)T * sizeof(int) +
+                                           (size_t)nb * remove * sizeof(int) + 7) & ~(size_t)7));
         SCPL_CUDA(h, cudaMemcpyAsync(hklog, ws.klog, (size_t)nb * remove * sizeof(int),
+                                     cudaMemcpyDeviceToHost, st));
+        SCPL_CUDA(h, cudaMemcpyAsync(hdirty, ws.dirty_count, (size_t)nb * sizeof(unsigned long long),
                                      cudaMemcpyDeviceToHost, st));
         SCPL_CUDA(h, cudaStreamSynchronize(st));
         for (int b = 0; b < nb; ++b) {
@@ -469,30 +524,37 @@ scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W
                 const int Wn = Wc - ke;
                 h->last_carved_px += (double)H * Wc;
                 if (h->prof.on) {
-                    // DP: E read, direction planes written and read, lists written
-                    h->prof.bytes[K_DP_SELECT] += H * (4.0 * Wc + 0.5 * Wc + 4.0 * ke);
-                    // energy: carved luma of every frame, O and SD read at the old
-                    // width and written at the new one, E written, lists read
+                    // DP: E read, directions written and read back, lists written
+                    h->prof.bytes[K_DP_SELECT] += H * (4.5 * Wc + 2.0 * ke);
+                    // update: O and E read (gathered) and written at the new width,
+                    // the removal lists of each row and its two neighbours
                     if (Wn > target_W)
-                        h->prof.bytes[K_ENERGY_ITER] +=
-                            H * (Tb * Wn + 6.0 * Wc + 10.0 * Wn + 2.0 * ke);
+                        h->prof.bytes[K_ENERGY_ITER] += H * (12.0 * Wn + 6.0 * ke);
                     else
-                        h->prof.bytes[K_ENERGY_ITER] += H * (2.0 * Wc + 2.0 * Wn + 2.0 * ke);
+                        h->prof.bytes[K_ENERGY_ITER] += H * (4.0 * Wn + 6.0 * ke);
                 }
                 Wc = Wn;
                 ++it;
             }
             h->last_iter_max = std::max(h->last_iter_max, it);
             h->last_iter_total += it;
-            if (h->prof.on)   // first iteration: luma and motion of every frame, O, SD, E out
+            if (h->prof.on) {
+                // first iteration: luma and motion of every frame, O, SDo, E out
                 h->prof.bytes[K_ENERGY_INIT] += H * (2.0 * Tb * W + 10.0 * W);
+                // recomputed pixels: 3 luma bytes of every frame, SDo read, E write
+                h->prof.bytes[K_ENERGY_ITER] += (double)hdirty[b] * (3.0 * Tb + 8.0);
+            }
         }
     }
     if (h->prof.on) {
         h->prof.bytes[K_GATHER] += (double)H * target_W * (6.0 * T + 2.0 * nb);
         if (remove == 0) h->prof.bytes[K_IDENTITY] += 2.0 * H * W * nb;
     }
-    if (n_buffers || buffer_starts) SCPL_CUDA(h, cudaStreamSynchronize(st));
+    int *herr = reinterpret_cast<int *>(h->h_small.as<char>());
+    SCPL_CUDA(h, cudaMemcpyAsync(herr, ws.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SCPL_CUDA(h, cudaStreamSynchronize(st));
+    if (*herr == DEV_ETIMEOUT)
+        return fail(h, SCPL_ETIMEOUT, "a bounded device-side wait ran out while carving");
     if (buffer_starts) std::copy(starts.begin(), starts.end(), buffer_starts);
     if (n_buffers) *n_buffers = nb;
     return SCPL_OK;

@@ -29,17 +29,92 @@ struct BufState {
     int iters;       // iterations selected so far
 };
 
+#ifdef __CUDACC__
+// ---- TMA bulk copies and mbarriers (inline PTX) ------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long globaltimer_now() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count)
+                 : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// Global -> this CTA's shared memory; bytes and both addresses 16-byte aligned.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes,
+                                         uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait for an mbarrier phase: after `limit_ns` the status word gets
+// DEV_ETIMEOUT and the caller continues (its data is then invalid; the host
+// reports the error), so no wait can hang the GPU.
+__device__ __forceinline__ bool mbar_wait(uint64_t *mbar, unsigned parity, int *err,
+                                          unsigned long long limit_ns) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    const unsigned long long t0 = globaltimer_now();
+    while (!mbar_try_wait(mbar, parity)) {
+        if (globaltimer_now() - t0 > limit_ns) {
+            if (err) atomicExch(err, DEV_ETIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Committed view of a buffer's state (applies a pending iteration).
+__device__ __forceinline__ void committed(const BufState &s, int &W, int &slot, int &removed) {
+    if (s.k_eff > 0) {
+        W = s.W - s.k_eff;
+        slot = s.slot ^ 1;
+        removed = s.removed + s.k_eff;
+    } else {
+        W = s.W;
+        slot = s.slot;
+        removed = s.removed;
+    }
+}
+#endif
+
 // Arrays of one clip's carving, all in device memory.
 struct CarveWs {
     int H, W0;          // clip height and original width
     long pitch;         // elements per row of E / SD / O (>= W0)
     long plane;         // H * pitch
-    int ngroups;        // ceil(W0 / 32): 32-column groups of the direction bit planes
+    int dstride;        // direction words per 4-row block: ceil(W0 / 4) rounded up to 4
+    long dbuf;          // direction words per buffer: ceil(H / 16) * 4 * dstride
     int kcap;           // capacity of a row's removal list
     int32_t *E;         // [nb][2][plane]  summed energy of the buffer
-    int32_t *SD;        // [nb][2][plane]  summed, carved motion energy wm * sum_t D_t
+    int32_t *SD;        // [nb][plane]     wm * sum_t D_t at original coordinates
     uint16_t *O;        // [nb][2][plane]  original column of each carved pixel
-    uint32_t *dirs;     // [nb][H][ngroups][2] DP directions as two bit planes
+    uint32_t *dirs;     // [nb][dbuf] DP directions, 2 bits per pixel, one word per 4x4 block
     uint16_t *rem;      // [nb][H][kcap]   columns removed in a row, ascending
     BufState *st;       // [nb]
     int *klog;          // [nb][klog_stride] k_eff of every iteration
@@ -48,6 +123,17 @@ struct CarveWs {
     const uint8_t *D;   // [T][H][ypitch]  motion map of every frame
     long ypitch;
     int wg, wm;
+    unsigned long long *dirty_count;   // [nb] pixels recomputed by k_update (or NULL)
+    // cluster DP (k_dpc) only
+    int rj;             // rows per trace-back band
+    int nbands;         // ceil(H / rj)
+    uint16_t *J;        // [nb][nbands][W0]  column at the band's first row of the path
+                        //                   through (band's last row, j)
+    uint16_t *colbot;   // [nb][nbands][kcap] column of each seam at each band's last row
+    int *dpx;           // [nb][1 + kcap]     k_eff, then each seam's rank by column
+    int jstride;        // row stride of J (W0 rounded up to 8)
+    uint32_t *Dfirst;   // [nb][nbands][dstride] direction words of every band's first row
+    int *err;           // device status word (bounded waits)
 };
 
 // Scan (Sec. 3.2) arguments.
@@ -78,12 +164,19 @@ int scan_grid_size(int H, int W, int *err_out);
 cudaError_t launch_scan(const ScanArgs &a, int grid, cudaStream_t s);
 
 cudaError_t launch_energy_init(const CarveWs &ws, int nb, cudaStream_t s);
-cudaError_t launch_energy_iter(const CarveWs &ws, int nb, cudaStream_t s);
+cudaError_t launch_update(const CarveWs &ws, int nb, cudaStream_t s);
 cudaError_t launch_dp_select(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                              cudaStream_t s);
+// Cluster DP: plan (CTAs per cluster, band rows, shared memory) for a width and
+// height; returns false if this GPU cannot run it (then use launch_dp_select).
+bool dpc_plan(int W0, int H, int *ctas, int *rj, size_t *smem);
+bool dpc_available(int W0, int H);
+cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
+                       cudaStream_t s);
 cudaError_t launch_identity_O(const CarveWs &ws, int nb, cudaStream_t s);
 cudaError_t launch_gather(const CarveWs &ws, const uint8_t *rgb, int T, const int *buf_of_frame,
                           int target, uint8_t *out, cudaStream_t s);
-size_t dp_select_smem_bytes(int W0);
+size_t dp_smem_bytes(int W0, int H, int *band_blocks);
+size_t update_smem_bytes(int W0, int kcap, int *rows);
 
 }  // namespace scpl

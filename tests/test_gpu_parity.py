@@ -105,7 +105,8 @@ def test_scan_maxval_theoretical(orc, lib, synth):
 # ------------------------------------------------------- one SCPL iteration
 @pytest.mark.parametrize("H,W,vmax,k", [(1, 1, 5, 1), (1, 9, 3, 4), (2, 2, 0, 2), (7, 3, 2, 3),
                                         (33, 31, 4, 8), (50, 1025, 9, 16), (64, 2049, 1, 32),
-                                        (20, 700, 0, 700), (300, 1920, 2550, 32)])
+                                        (20, 700, 0, 700), (300, 1920, 2550, 32),
+                                        (70, 5000, 40, 24), (40, 7000, 9, 16)])
 def test_seams(orc, lib, H, W, vmax, k):
     r = np.random.default_rng(H * 7 + W)
     E = r.integers(0, vmax + 1, (H, W)).astype(np.int32)
