@@ -92,19 +92,40 @@ __global__ void __launch_bounds__(EN_CW) k_energy_init(CarveWs ws) {
         }
     }
     const int pl = max(p - 1, 0), pr = min(p + 1, W0 - 1);
-    for (int t = st.t0; t < st.t0 + st.nt; ++t) {
-        const uint8_t *Yt = ws.Y + (long)t * H * ws.ypitch;
+    // frames innermost copy of the luma: 16 frames per uint4
+    uint32_t fq[EN_RB][4];
+#pragma unroll
+    for (int r = 0; r < EN_RB; ++r) fq[r][0] = fq[r][1] = fq[r][2] = fq[r][3] = 0;
+    uint8_t *yfm = ws.Yfm + st.yfm;
+    for (int tb = 0; tb < st.tp; tb += 16) {
+#pragma unroll
+        for (int tt = 0; tt < 16; ++tt) {
+            const int t = tb + tt;
+            if (t < st.nt) {
+                const uint8_t *Yt = ws.Y + (long)(st.t0 + t) * H * ws.ypitch;
+#pragma unroll
+                for (int r = 0; r < EN_RB; ++r) {
+                    const int i = i0 + r;
+                    if (i < H) {
+                        const uint8_t *ru = Yt + (long)clampi(i - 1, 0, H - 1) * ws.ypitch;
+                        const uint8_t *rc = Yt + (long)i * ws.ypitch;
+                        const uint8_t *rd = Yt + (long)clampi(i + 1, 0, H - 1) * ws.ypitch;
+                        const int yc = __ldg(rc + p);
+                        eacc[r] += ws.wg * sobel_l1(__ldg(ru + pl), __ldg(ru + p), __ldg(ru + pr),
+                                                    __ldg(rc + pl), __ldg(rc + pr), __ldg(rd + pl),
+                                                    __ldg(rd + p), __ldg(rd + pr));
+                        fq[r][tt >> 2] |= (uint32_t)yc << (8 * (tt & 3));
+                    }
+                }
+            }
+        }
 #pragma unroll
         for (int r = 0; r < EN_RB; ++r) {
             const int i = i0 + r;
-            if (i < H) {
-                const uint8_t *ru = Yt + (long)clampi(i - 1, 0, H - 1) * ws.ypitch;
-                const uint8_t *rc = Yt + (long)i * ws.ypitch;
-                const uint8_t *rd = Yt + (long)clampi(i + 1, 0, H - 1) * ws.ypitch;
-                eacc[r] += ws.wg * sobel_l1(__ldg(ru + pl), __ldg(ru + p), __ldg(ru + pr),
-                                            __ldg(rc + pl), __ldg(rc + pr), __ldg(rd + pl),
-                                            __ldg(rd + p), __ldg(rd + pr));
-            }
+            if (i < H)
+                *reinterpret_cast<uint4 *>(yfm + ((long)i * W0 + p) * st.tp + tb) =
+                    make_uint4(fq[r][0], fq[r][1], fq[r][2], fq[r][3]);
+            fq[r][0] = fq[r][1] = fq[r][2] = fq[r][3] = 0;
         }
     }
 #pragma unroll
@@ -120,10 +141,8 @@ __global__ void __launch_bounds__(EN_CW) k_energy_init(CarveWs ws) {
 //   1. O and E are compacted: each thread gathers 8 consecutive output pixels
 //      (all loads first) and writes them as vectors.
 //   2. The changed pixels of the rows are marked in a bitmap and listed.
-//   3. Each changed pixel's 3x3 original columns are looked up once; then
-//      (pixel, 8-frame group) work items add up the Sobel gradients of the
-//      frames' original luma in shared memory; E is written from the sums.
-constexpr int UP_FG = 8;   // frames per work item of the recompute
+//   3. Each changed pixel's summed gradient is recomputed from the frame-minor
+//      luma copy written by k_energy_init.
 
 __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -148,10 +167,6 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
     uint32_t *bm = reinterpret_cast<uint32_t *>(smraw + off);   // [RB][nwords0]
     off += (size_t)RB * nwords0 * 4;
     uint32_t *list = reinterpret_cast<uint32_t *>(smraw + off);  // [list_cap] (row << 16 | old column)
-    off += (size_t)list_cap * 4;
-    int *acc = reinterpret_cast<int *>(smraw + off);             // [list_cap]
-    off += (size_t)list_cap * 4;
-    uint16_t *ocs = reinterpret_cast<uint16_t *>(smraw + off);   // [list_cap][9]
     const uint16_t *rem = ws.rem + (long)b * H * kcap;
 
     for (int x = tid; x < (RB + 2) * keff; x += UP_THREADS) {
@@ -251,11 +266,18 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
     const int cnt = s_cnt;
     if (tid == 0 && ws.dirty_count) atomicAdd(ws.dirty_count + b, (unsigned long long)cnt);
 
-    // 3. exact recompute of the changed pixels from every frame's original luma
+    // 3. exact recompute of the changed pixels: every frame's Sobel gradient
+    //    from the frame-minor luma copy, 16 frames per vector load, bytes
+    //    widened to 16-bit lanes and |P - N| taken with packed max/min
+    const int32_t *SDo = ws.SD + (long)b * plane;
+    const uint8_t *yfm = ws.Yfm + st.yfm;
+    const int tp = st.tp;
     for (int e = tid; e < cnt; e += UP_THREADS) {
         const int r = (int)(list[e] >> 16), q = (int)(list[e] & 0xFFFFu);
         const int i = i0 + r;
         const int p = q - count_less(rl + (r + 1) * kcap, keff, q);
+        const uint4 *nb[3][3];
+        int ocenter = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const int gi = clampi(i + a - 1, 0, H - 1);
@@ -263,40 +285,40 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const int x = clampi(p + c - 1, 0, Wn - 1);
-                ocs[e * 9 + a * 3 + c] = Oin[(long)gi * pitch + src_col(rr, keff, x)];
+                const int o = Oin[(long)gi * pitch + src_col(rr, keff, x)];
+                if (a == 1 && c == 1) ocenter = o;
+                nb[a][c] = reinterpret_cast<const uint4 *>(yfm + ((long)gi * ws.W0 + o) * tp);
             }
         }
-        acc[e] = 0;
-    }
-    __syncthreads();
-    const int ngroups = (st.nt + UP_FG - 1) / UP_FG;
-    const long fstride = (long)H * ws.ypitch;
-    for (int x = tid; x < cnt * ngroups; x += UP_THREADS) {
-        const int e = x % cnt, fg = x / cnt;
-        const int r = (int)(list[e] >> 16);
-        const int i = i0 + r;
-        const long r0 = (long)clampi(i - 1, 0, H - 1) * ws.ypitch;
-        const long r1 = (long)i * ws.ypitch;
-        const long r2 = (long)clampi(i + 1, 0, H - 1) * ws.ypitch;
-        const uint16_t *oc = ocs + e * 9;
-        const int t_begin = fg * UP_FG, t_end = min(t_begin + UP_FG, st.nt);
-        const uint8_t *Yt = ws.Y + (long)(st.t0 + t_begin) * fstride;
-        int sum = 0;
-#pragma unroll 4
-        for (int t = t_begin; t < t_end; ++t, Yt += fstride) {
-            sum += sobel_l1(__ldg(Yt + r0 + oc[0]), __ldg(Yt + r0 + oc[1]), __ldg(Yt + r0 + oc[2]),
-                            __ldg(Yt + r1 + oc[3]), __ldg(Yt + r1 + oc[5]), __ldg(Yt + r2 + oc[6]),
-                            __ldg(Yt + r2 + oc[7]), __ldg(Yt + r2 + oc[8]));
+        int acc = 0;
+        for (int f = 0; f < tp / 16; ++f) {
+            const uint4 v00 = __ldg(nb[0][0] + f), v01 = __ldg(nb[0][1] + f), v02 = __ldg(nb[0][2] + f);
+            const uint4 v10 = __ldg(nb[1][0] + f), v12 = __ldg(nb[1][2] + f);
+            const uint4 v20 = __ldg(nb[2][0] + f), v21 = __ldg(nb[2][1] + f), v22 = __ldg(nb[2][2] + f);
+            const uint32_t w00[4] = {v00.x, v00.y, v00.z, v00.w}, w01[4] = {v01.x, v01.y, v01.z, v01.w};
+            const uint32_t w02[4] = {v02.x, v02.y, v02.z, v02.w}, w10[4] = {v10.x, v10.y, v10.z, v10.w};
+            const uint32_t w12[4] = {v12.x, v12.y, v12.z, v12.w}, w20[4] = {v20.x, v20.y, v20.z, v20.w};
+            const uint32_t w21[4] = {v21.x, v21.y, v21.z, v21.w}, w22[4] = {v22.x, v22.y, v22.z, v22.w};
+            uint32_t packed = 0;   // two 16-bit lane sums, at most 8 * 2040 each
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const uint32_t sel = h ? 0x4342u : 0x4140u;   // bytes (2,3) or (0,1) -> u16 lanes
+                    const uint32_t a00 = __byte_perm(w00[k], 0, sel), a01 = __byte_perm(w01[k], 0, sel);
+                    const uint32_t a02 = __byte_perm(w02[k], 0, sel), a10 = __byte_perm(w10[k], 0, sel);
+                    const uint32_t a12 = __byte_perm(w12[k], 0, sel), a20 = __byte_perm(w20[k], 0, sel);
+                    const uint32_t a21 = __byte_perm(w21[k], 0, sel), a22 = __byte_perm(w22[k], 0, sel);
+                    const uint32_t gxp = a02 + 2u * a12 + a22, gxn = a00 + 2u * a10 + a20;
+                    const uint32_t gyp = a20 + 2u * a21 + a22, gyn = a00 + 2u * a01 + a02;
+                    const uint32_t gx = __vimax3_u16x2(gxp, gxn, 0u) - __vimin3_u16x2(gxp, gxn, 0xFFFFFFFFu);
+                    const uint32_t gy = __vimax3_u16x2(gyp, gyn, 0u) - __vimin3_u16x2(gyp, gyn, 0xFFFFFFFFu);
+                    packed += gx + gy;
+                }
+            }
+            acc += (int)(packed & 0xFFFFu) + (int)(packed >> 16);
         }
-        atomicAdd(&acc[e], sum);
-    }
-    __syncthreads();
-    const int32_t *SDo = ws.SD + (long)b * plane;
-    for (int e = tid; e < cnt; e += UP_THREADS) {
-        const int r = (int)(list[e] >> 16), q = (int)(list[e] & 0xFFFFu);
-        const int i = i0 + r;
-        const int p = q - count_less(rl + (r + 1) * kcap, keff, q);
-        Eout[(long)i * pitch + p] = ws.wg * acc[e] + SDo[(long)i * pitch + ocs[e * 9 + 4]];
+        Eout[(long)i * pitch + p] = ws.wg * acc + SDo[(long)i * pitch + ocenter];
     }
 }
 
@@ -609,7 +631,7 @@ size_t update_smem_bytes(int W0, int kcap, int *rows) {
     size_t bytes = 0;
     for (; rb >= 1; --rb) {
         bytes = (((size_t)(rb + 2) * kcap * 2 + 15) & ~(size_t)15) + (size_t)rb * nwords0 * 4 +
-                (size_t)rb * per_row_list * (4 + 4 + 18);
+                (size_t)rb * per_row_list * 4;
         if (bytes <= 200 * 1024) break;
     }
     if (rb < 1) rb = 1;

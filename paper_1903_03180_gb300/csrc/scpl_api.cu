@@ -107,7 +107,7 @@ struct scpl_ctx {
     DevBuf E, SD, O, dirs, rem, st, bof;
     // host-memory entry point staging
     DevBuf in_frames, out_frames, seams_dev;
-    DevBuf klog, dirty, J, colbot, dpx, Dfirst;
+    DevBuf klog, dirty, J, colbot, dpx, Dfirst, Yfm;
     // cluster-DP availability per (W0, H) last checked
     int dpc_W0 = -1, dpc_H = -1;
     bool dpc_ok = false;
@@ -249,6 +249,7 @@ scpl_status carve_ws(scpl_ctx *h, int nb, int H, int W0, int kcap, CarveWs &ws,
     ws.dbuf = (long)((H + 15) / 16) * 4 * ws.dstride;
     ws.jstride = (W0 + 7) & ~7;
     ws.Dfirst = nullptr;
+    ws.Yfm = nullptr;
     SCPL_CUDA(h, h->errw.ensure(sizeof(int)));
     ws.err = h->errw.as<int>();
     ws.kcap = std::max(kcap, 1);
@@ -362,7 +363,7 @@ void scpl_destroy(scpl_handle h) {
                       &h->count, &h->starts, &h->nbuf, &h->errw, &h->E, &h->SD, &h->O,
                       &h->dirs, &h->rem, &h->st, &h->bof, &h->in_frames, &h->out_frames,
                       &h->seams_dev, &h->klog, &h->dirty, &h->J, &h->colbot, &h->dpx,
-                      &h->Dfirst};
+                      &h->Dfirst, &h->Yfm};
     for (DevBuf *b : bufs) b->release();
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
     h->h_small.release();
@@ -413,7 +414,7 @@ scpl_status scpl_seams(scpl_handle h, const int32_t *energy, int H, int W, int k
     SCPL_CUDA(h, h->h_small.ensure(64 + sizeof(BufState)));
     BufState *hb = reinterpret_cast<BufState *>(h->h_small.as<char>() + 64);
     SCPL_CUDA(h, cudaStreamSynchronize(st));   // the staging area is reused below
-    *hb = BufState{0, 1, W, 0, 0, 0, W - kc, 0};
+    *hb = BufState{0, 1, W, 0, 0, 0, W - kc, 0, 0, 0, 0};
     SCPL_CUDA(h, cudaMemcpyAsync(ws.st, hb, sizeof(BufState), cudaMemcpyHostToDevice, st));
     SCPL_CUDA(h, timed(h, K_DP_SELECT, [&] {
                   return ws.J ? launch_dpc(ws, 1, k, cols, 0, st)
@@ -458,10 +459,16 @@ scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W
     BufState *hb = reinterpret_cast<BufState *>(h->h_small.as<char>() + 64);
     int *hbof = reinterpret_cast<int *>(hb + nb);
     int *hklog = hbof + T;
+    long long yfm_total = 0;
     for (int b = 0; b < nb; ++b) {
-        hb[b] = BufState{starts[b], starts[b + 1] - starts[b], W, 0, 0, 0, target_W, 0};
+        const int nt = starts[b + 1] - starts[b];
+        const int tp = (nt + 15) & ~15;
+        hb[b] = BufState{starts[b], nt, W, 0, 0, 0, target_W, 0, tp, 0, yfm_total};
+        yfm_total += (long long)H * W * tp;
         for (int t = starts[b]; t < starts[b + 1]; ++t) hbof[t] = b;
     }
+    SCPL_CUDA(h, h->Yfm.ensure((size_t)std::max<long long>(yfm_total, 16)));
+    ws.Yfm = h->Yfm.as<uint8_t>();
     SCPL_CUDA(h, cudaMemcpyAsync(ws.st, hb, (size_t)nb * sizeof(BufState),
                                  cudaMemcpyHostToDevice, st));
     SCPL_CUDA(h, cudaMemcpyAsync(h->bof.p, hbof, (size_t)T * sizeof(int), cudaMemcpyHostToDevice,

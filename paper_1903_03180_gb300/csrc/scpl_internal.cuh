@@ -27,6 +27,9 @@ struct BufState {
     int slot;        // slot of E / SD / O that holds width W
     int target;      // target width
     int iters;       // iterations selected so far
+    int tp;          // frames of the frame-minor luma copy (nt rounded up to 16)
+    int pad;
+    long long yfm;   // byte offset of this buffer's frame-minor luma copy
 };
 
 #ifdef __CUDACC__
@@ -124,6 +127,7 @@ struct CarveWs {
     long ypitch;
     int wg, wm;
     unsigned long long *dirty_count;   // [nb] pixels recomputed by k_update (or NULL)
+    uint8_t *Yfm;       // per buffer [H][W0][tp] original luma, frames innermost
     // cluster DP (k_dpc) only
     int rj;             // rows per trace-back band
     int nbands;         // ceil(H / rj)
