@@ -612,7 +612,7 @@ cudaError_t launch_dp_t(const CarveWs &ws, int nb, int k, int16_t *seams, long s
 size_t dp_smem_bytes(int W0, int H, int *band_blocks) {
     const size_t fixed = (size_t)W0 * 24;
     const size_t limit = 227 * 1024 - 4096;   // minus the static shared memory
-    const size_t dstride = (size_t)(W0 + 3) / 4;
+    const size_t dstride = (((size_t)(W0 + 3) / 4) + 3) & ~(size_t)3;   // as CarveWs::dstride
     size_t budget = limit > fixed ? limit - fixed : 0;
     if (budget > 64 * 1024) budget = 64 * 1024;
     int bb = (int)(budget / (2 * dstride * 4));

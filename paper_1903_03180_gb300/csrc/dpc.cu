@@ -49,12 +49,15 @@ namespace {
 
 constexpr int DPC_WPC = 4;                       // warps per CTA
 constexpr int DPC_V = 4;                         // columns per lane
-constexpr int DPC_R = 16;                        // rows between halo refreshes (= TMA stage)
-constexpr int DPC_OWW = 32 * DPC_V - 2 * DPC_R;  // owned columns per warp: 96
-constexpr int DPC_CW = DPC_WPC * DPC_OWW + 2 * DPC_R;   // columns of a CTA's window: 416
+constexpr int DPC_S = 16;                        // rows per TMA stage of the energy ring
+constexpr int DPC_R = 32;                        // rows between halo refreshes (= halo width)
+constexpr int DPC_SPR = DPC_R / DPC_S;           // stages per refresh
+constexpr int DPC_HL = DPC_R / DPC_V;            // halo lanes on each side of a warp: 8
+constexpr int DPC_OWW = 32 * DPC_V - 2 * DPC_R;  // owned columns per warp: 64
+constexpr int DPC_CW = DPC_WPC * DPC_OWW + 2 * DPC_R;   // columns of a CTA's window: 320
 constexpr int DPC_NST = 4;                       // energy stages in flight
 constexpr int DPC_LMAX = DPC_WPC * DPC_OWW;      // parents a CTA can report: 384
-constexpr size_t DPC_RING = (size_t)DPC_NST * DPC_R * DPC_CW * 4;
+constexpr size_t DPC_RING = (size_t)DPC_NST * DPC_S * DPC_CW * 4;
 constexpr size_t DPC_STAGE_BUDGET = 96 * 1024;   // trace-back staging
 constexpr uint32_t BIG = 0x80000000u;            // energy of columns outside [0, W)
 constexpr uint32_t INF32 = 0xFFFFFFFFu;
@@ -95,8 +98,8 @@ __global__ void __launch_bounds__(DPC_WPC * 32, 1)
 k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
     extern __shared__ __align__(128) unsigned char smraw[];
     // halo inboxes: [parity][warp][value], filled by the neighbouring warps
-    __shared__ uint32_t inLc[2][DPC_WPC][16], inLl[2][DPC_WPC][16];
-    __shared__ uint32_t inRc[2][DPC_WPC][16], inRl[2][DPC_WPC][16];
+    __shared__ uint32_t inLc[2][DPC_WPC][DPC_R], inLl[2][DPC_WPC][DPC_R];
+    __shared__ uint32_t inRc[2][DPC_WPC][DPC_R], inRl[2][DPC_WPC][DPC_R];
     __shared__ __align__(8) uint64_t mbar[DPC_NST + 2];
     __shared__ int s_cnt, s_keff;
 
@@ -127,7 +130,7 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
     const int c_lo = crank * DPC_WPC * DPC_OWW - DPC_R;     // first column of the CTA window
     const int woff = w * DPC_OWW + lane * DPC_V;             // lane's offset in the window
     const int cbase = c_lo + woff;                           // lane's first column
-    const bool owner = lane >= DPC_R / DPC_V && lane < 32 - DPC_R / DPC_V;
+    const bool owner = lane >= DPC_HL && lane < 32 - DPC_HL;
     const int dstride = ws.dstride;
     uint32_t *dirs = ws.dirs + (long)b * ws.dbuf;
     uint16_t *J = ws.J + (long)b * NB * ws.jstride;
@@ -137,14 +140,14 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
     uint32_t *ring = reinterpret_cast<uint32_t *>(smraw);
     const int cp_lo = max(c_lo, 0), cp_hi = (int)min((long)(c_lo + DPC_CW), pitch);
     const unsigned row_bytes = cp_hi > cp_lo ? (unsigned)(cp_hi - cp_lo) * 4u : 0u;
-    const int nstages = (H - 1 + DPC_R - 1) / DPC_R;
+    const int nstages = (H - 1 + DPC_S - 1) / DPC_S;
     auto issue_stage = [&](int s) {   // thread 0 only
         if (s >= nstages) return;
-        const int r0 = 1 + s * DPC_R, r1 = min(r0 + DPC_R, H);
+        const int r0 = 1 + s * DPC_S, r1 = min(r0 + DPC_S, H);
         uint64_t *mb = &mbar[s % DPC_NST];
         mbar_expect_tx(mb, row_bytes * (unsigned)(r1 - r0));
         if (row_bytes) {
-            uint32_t *dst = ring + (size_t)(s % DPC_NST) * DPC_R * DPC_CW + (cp_lo - c_lo);
+            uint32_t *dst = ring + (size_t)(s % DPC_NST) * DPC_S * DPC_CW + (cp_lo - c_lo);
             for (int r = r0; r < r1; ++r)
                 bulk_g2s(dst + (size_t)(r - r0) * DPC_CW, E + (long)r * pitch + cp_lo, row_bytes,
                          mb);
@@ -197,11 +200,11 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
     };
     auto stage_rows = [&](int s, auto guarded) {
         constexpr bool GUARD = decltype(guarded)::value;
-        const uint32_t *rs = ring + (size_t)(s % DPC_NST) * DPC_R * DPC_CW + woff;
-        const int ibase = 1 + DPC_R * s;
-        const bool band_edge = ((ibase + DPC_R - 1) % RJ) == 0;   // row 16s+16 starts a band
+        const uint32_t *rs = ring + (size_t)(s % DPC_NST) * DPC_S * DPC_CW + woff;
+        const int ibase = 1 + DPC_S * s;
+        const bool band_edge = ((ibase + DPC_S - 1) % RJ) == 0;   // row 16s+16 starts a band
 #pragma unroll
-        for (int ro = 0; ro < DPC_R; ++ro) {
+        for (int ro = 0; ro < DPC_S; ++ro) {
             const int i = ibase + ro;
             if (!GUARD || i < H) {
                 const uint4 ev = *reinterpret_cast<const uint4 *>(rs + ro * DPC_CW);
@@ -220,7 +223,7 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
                     const uint32_t l2 = v == DPC_V - 1 ? rl : lab[v + 1];
                     // the cost chain is two integer mins; the first index that
                     // attains the minimum (lowest column) is chosen off the chain
-                    const uint32_t m = min(min(c0, cost[v]), c2);
+                    const uint32_t m = __vimin3_u32(c0, cost[v], c2);
                     const bool p0 = c0 == m, p1 = cost[v] == m;
                     nc[v] = m + e[v];
                     nl[v] = p0 ? l0 : (p1 ? lab[v] : l2);
@@ -228,7 +231,7 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
                 }
 #pragma unroll
                 for (int v = 0; v < DPC_V; ++v) { cost[v] = nc[v]; lab[v] = nl[v]; }
-                if (ro == DPC_R - 1 && band_edge) {
+                if (ro == DPC_S - 1 && band_edge) {
 #pragma unroll
                     for (int v = 0; v < DPC_V; ++v)
                         lab[v] = (lab[v] & 0xFFFF0000u) | ((uint32_t)(cbase + v) & 0xFFFFu);
@@ -242,7 +245,7 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
                     dw = 0;
                     if (ro == 14) store_group(s);   // rows 16s .. 16s+15 are complete
                 }
-                if (ro == DPC_R - 2 && band_edge && owner) {   // a band's last row
+                if (ro == DPC_S - 2 && band_edge && owner) {   // a band's last row
                     uint16_t *Jrow = J + (long)(i / RJ) * ws.jstride;
 #pragma unroll
                     for (int v = 0; v < DPC_V; ++v) {
@@ -255,21 +258,26 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
     };
     for (int s = 0; s < nstages; ++s) {
         mbar_wait(&mbar[s % DPC_NST], (unsigned)(s / DPC_NST) & 1u, ws.err, WAIT_NS);
-        const int ibase = 1 + DPC_R * s;
-        if (ibase + DPC_R - 1 < H) stage_rows(s, std::false_type{});
+        const int ibase = 1 + DPC_S * s;
+        if (ibase + DPC_S - 1 < H) stage_rows(s, std::false_type{});
         else stage_rows(s, std::true_type{});
-        const int ilast = ibase + DPC_R - 1;   // the stage's last row
-        if (ilast < H - 1) {
-            // the slot of stage s is refilled with stage s+NST once every warp
-            // of this CTA is past it; account its bytes now
-            if (tid == 0 && s + DPC_NST < nstages) {
-                const int r0 = 1 + (s + DPC_NST) * DPC_R, r1 = min(r0 + DPC_R, H);
-                mbar_expect_tx(&mbar[s % DPC_NST], row_bytes * (unsigned)(r1 - r0));
+        const int ilast = ibase + DPC_S - 1;   // the stage's last row
+        if ((s + 1) % DPC_SPR == 0 && ilast < H - 1) {
+            // the slots of the stages just finished are refilled once every
+            // warp of this CTA is past them; account their bytes now
+            if (tid == 0) {
+                for (int k = 0; k < DPC_SPR; ++k) {
+                    const int sn = s - k + DPC_NST;
+                    if (sn < nstages) {
+                        const int r0 = 1 + sn * DPC_S, r1 = min(r0 + DPC_S, H);
+                        mbar_expect_tx(&mbar[sn % DPC_NST], row_bytes * (unsigned)(r1 - r0));
+                    }
+                }
             }
             // push the owned edge strips into the neighbours' inboxes (remote
             // stores across CTAs), synchronise, then read the own inboxes
-            const int par = s & 1;
-            if (lane >= 24 && lane < 28 && g + 1 < nwarps) {
+            const int par = (s / DPC_SPR) & 1;
+            if (lane >= 32 - 2 * DPC_HL && lane < 32 - DPC_HL && g + 1 < nwarps) {
                 uint32_t *dc, *dl;
                 if (w < DPC_WPC - 1) {
                     dc = &inLc[par][w + 1][0];
@@ -278,13 +286,14 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
                     dc = cluster.map_shared_rank(&inLc[par][0][0], crank + 1);
                     dl = cluster.map_shared_rank(&inLl[par][0][0], crank + 1);
                 }
+                const int o = (lane - (32 - 2 * DPC_HL)) * DPC_V;
 #pragma unroll
                 for (int v = 0; v < DPC_V; ++v) {
-                    dc[(lane - 24) * 4 + v] = cost[v];
-                    dl[(lane - 24) * 4 + v] = lab[v];
+                    dc[o + v] = cost[v];
+                    dl[o + v] = lab[v];
                 }
             }
-            if (lane >= 4 && lane < 8 && g > 0) {
+            if (lane >= DPC_HL && lane < 2 * DPC_HL && g > 0) {
                 uint32_t *dc, *dl;
                 if (w > 0) {
                     dc = &inRc[par][w - 1][0];
@@ -293,35 +302,40 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
                     dc = cluster.map_shared_rank(&inRc[par][DPC_WPC - 1][0], crank - 1);
                     dl = cluster.map_shared_rank(&inRl[par][DPC_WPC - 1][0], crank - 1);
                 }
+                const int o = (lane - DPC_HL) * DPC_V;
 #pragma unroll
                 for (int v = 0; v < DPC_V; ++v) {
-                    dc[(lane - 4) * 4 + v] = cost[v];
-                    dl[(lane - 4) * 4 + v] = lab[v];
+                    dc[o + v] = cost[v];
+                    dl[o + v] = lab[v];
                 }
             }
             cluster.sync();
-            // refill: each warp's lane 0 copies a quarter of the stage's rows
-            if (lane == 0 && s + DPC_NST < nstages && row_bytes) {
-                const int sn = s + DPC_NST;
-                const int r0 = 1 + sn * DPC_R, r1 = min(r0 + DPC_R, H);
-                uint32_t *dst = ring + (size_t)(sn % DPC_NST) * DPC_R * DPC_CW + (cp_lo - c_lo);
-                for (int r = r0 + w * (DPC_R / DPC_WPC);
-                     r < min(r0 + (w + 1) * (DPC_R / DPC_WPC), r1); ++r)
-                    bulk_g2s(dst + (size_t)(r - r0) * DPC_CW, E + (long)r * pitch + cp_lo,
-                             row_bytes, &mbar[sn % DPC_NST]);
-            }
-            if (lane < 4) {
-#pragma unroll
-                for (int v = 0; v < DPC_V; ++v) {
-                    cost[v] = g == 0 ? INF32 : inLc[par][w][lane * 4 + v];
-                    lab[v] = inLl[par][w][lane * 4 + v];
+            // refill: the warps' lane 0 share the copies of the freed stages
+            if (lane == 0 && row_bytes) {
+                for (int k = 0; k < DPC_SPR; ++k) {
+                    const int sn = s - k + DPC_NST;
+                    if (sn >= nstages) continue;
+                    const int r0 = 1 + sn * DPC_S, r1 = min(r0 + DPC_S, H);
+                    uint32_t *dst =
+                        ring + (size_t)(sn % DPC_NST) * DPC_S * DPC_CW + (cp_lo - c_lo);
+                    for (int r = r0 + w * (DPC_S / DPC_WPC);
+                         r < min(r0 + (w + 1) * (DPC_S / DPC_WPC), r1); ++r)
+                        bulk_g2s(dst + (size_t)(r - r0) * DPC_CW, E + (long)r * pitch + cp_lo,
+                                 row_bytes, &mbar[sn % DPC_NST]);
                 }
             }
-            if (lane >= 28) {
+            if (lane < DPC_HL) {
 #pragma unroll
                 for (int v = 0; v < DPC_V; ++v) {
-                    cost[v] = g == nwarps - 1 ? INF32 : inRc[par][w][(lane - 28) * 4 + v];
-                    lab[v] = inRl[par][w][(lane - 28) * 4 + v];
+                    cost[v] = g == 0 ? INF32 : inLc[par][w][lane * DPC_V + v];
+                    lab[v] = inLl[par][w][lane * DPC_V + v];
+                }
+            }
+            if (lane >= 32 - DPC_HL) {
+#pragma unroll
+                for (int v = 0; v < DPC_V; ++v) {
+                    cost[v] = g == nwarps - 1 ? INF32 : inRc[par][w][(lane - (32 - DPC_HL)) * DPC_V + v];
+                    lab[v] = inRl[par][w][(lane - (32 - DPC_HL)) * DPC_V + v];
                 }
             }
         }
@@ -569,6 +583,10 @@ bool dpc_plan(int W0, int H, int *ctas, int *rj, size_t *smem) {
         bytes = dpc_smem(W0, H, r, W0, C);
     }
     if (bytes > 220 * 1024) return false;
+    // the walk stages at least one 16-row group of every band a CTA owns
+    const int nbands = (H + r - 1) / r;
+    const size_t dstride = (size_t)((((W0 + 3) / 4) + 3) & ~3);
+    if ((size_t)((nbands + C - 1) / C) * dstride * 16 > DPC_STAGE_BUDGET) return false;
     *ctas = C;
     *rj = r;
     *smem = bytes;
