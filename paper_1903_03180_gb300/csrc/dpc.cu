@@ -5,13 +5,14 @@
 // columns [96g, 96g+96) and holds a 128-column window [96g-16, 96g+112) in
 // registers, 4 consecutive columns per lane.  A row step needs only the
 // neighbours in the adjacent lanes (shuffles); the window's outer columns go
-// stale one column per row (trapezoid), so after 16 rows exactly the owned
-// columns are still exact.  Then every warp publishes the 16 owned columns at
-// each of its edges in shared memory, the cluster synchronises once, and each
-// warp refreshes its 16-column halos from its neighbours (same CTA: shared
-// memory; neighbouring CTA: distributed shared memory).  No barrier is taken
-// inside the 16 rows.  The energy rows reach shared memory through TMA bulk
-// copies, four 16-row stages ahead of the DP, one copy per row.
+// stale one column per row (trapezoid), so after 32 rows exactly the owned
+// columns are still exact.  Then every warp sends the 32 owned columns at each
+// of its edges straight into its neighbours' inboxes with st.async (shared or
+// distributed shared memory), which completes on the receiving warp's
+// mbarrier, and refreshes its own 32-column halos from its inbox.  Warps are
+// coupled only to their two neighbours; the DP loop takes no CTA or cluster
+// barrier.  Each warp's energy rows arrive by TMA tensor copies (one
+// 16-row x 128-column box per stage) into its own four-stage ring.
 //
 // Columns outside [0, W) carry energy 2^31: a real cumulative energy is below
 // 2^31 (checked on the host), so the column next to a real one always ends up
@@ -36,6 +37,8 @@
 // the bands' directions bulk-copied into shared memory, and writes the
 // per-row removal lists.
 #include <cooperative_groups.h>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 #include <type_traits>
 
@@ -54,10 +57,11 @@ constexpr int DPC_R = 32;                        // rows between halo refreshes 
 constexpr int DPC_SPR = DPC_R / DPC_S;           // stages per refresh
 constexpr int DPC_HL = DPC_R / DPC_V;            // halo lanes on each side of a warp: 8
 constexpr int DPC_OWW = 32 * DPC_V - 2 * DPC_R;  // owned columns per warp: 64
-constexpr int DPC_CW = DPC_WPC * DPC_OWW + 2 * DPC_R;   // columns of a CTA's window: 320
 constexpr int DPC_NST = 4;                       // energy stages in flight
 constexpr int DPC_LMAX = DPC_WPC * DPC_OWW;      // parents a CTA can report: 384
-constexpr size_t DPC_RING = (size_t)DPC_NST * DPC_S * DPC_CW * 4;
+constexpr int DPC_WW = 32 * DPC_V;               // columns of a warp's window: 128
+constexpr size_t DPC_WSLOT = (size_t)DPC_S * DPC_WW * 4;   // one warp's stage: 8 KB
+constexpr size_t DPC_RING = (size_t)DPC_WPC * DPC_NST * DPC_WSLOT;
 constexpr size_t DPC_STAGE_BUDGET = 96 * 1024;   // trace-back staging
 constexpr uint32_t BIG = 0x80000000u;            // energy of columns outside [0, W)
 constexpr uint32_t INF32 = 0xFFFFFFFFu;
@@ -94,13 +98,63 @@ struct WalkLayout {
     }
 };
 
+__device__ __forceinline__ uint32_t mapa_u32(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+// 16 bytes into (possibly another CTA's) shared memory, completing on that
+// CTA's mbarrier.
+__device__ __forceinline__ void st_async_v4(uint32_t raddr, const uint32_t (&v)[4], uint32_t rmbar) {
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::
+            "r"(raddr),
+        "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(rmbar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, int x, int y, int z,
+                                            uint64_t *mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(mbar))
+        : "memory");
+}
+// Bounded wait with cluster-scope acquire (data written by other CTAs).
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t *mbar, unsigned parity, int *err,
+                                                  unsigned long long limit_ns) {
+    auto try_once = [&]() {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_u32(mbar)), "r"(parity)
+            : "memory");
+        return ok != 0;
+    };
+    if (try_once()) return true;
+    if (err && *(volatile int *)err != DEV_OK) return false;   // an earlier wait gave up
+    const unsigned long long t0 = globaltimer_now();
+    while (!try_once()) {
+        if (globaltimer_now() - t0 > limit_ns) {
+            if (err) atomicExch(err, DEV_ETIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
 __global__ void __launch_bounds__(DPC_WPC * 32, 1)
-k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
+k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams,
+      long seam_stride) {
     extern __shared__ __align__(128) unsigned char smraw[];
     // halo inboxes: [parity][warp][value], filled by the neighbouring warps
-    __shared__ uint32_t inLc[2][DPC_WPC][DPC_R], inLl[2][DPC_WPC][DPC_R];
-    __shared__ uint32_t inRc[2][DPC_WPC][DPC_R], inRl[2][DPC_WPC][DPC_R];
-    __shared__ __align__(8) uint64_t mbar[DPC_NST + 2];
+    __shared__ __align__(16) uint32_t inLc[2][DPC_WPC][DPC_R], inLl[2][DPC_WPC][DPC_R];
+    __shared__ __align__(16) uint32_t inRc[2][DPC_WPC][DPC_R], inRl[2][DPC_WPC][DPC_R];
+    __shared__ __align__(8) uint64_t mring[DPC_WPC][DPC_NST];   // per-warp energy stages
+    __shared__ __align__(8) uint64_t minbox[DPC_WPC][2];        // per-warp halo inboxes
+    __shared__ __align__(8) uint64_t mbar[2];                    // trace-back copies
     __shared__ int s_cnt, s_keff;
 
     cg::cluster_group cluster = cg::this_cluster();
@@ -127,39 +181,40 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
 
     const int32_t *E = ws.E + ((long)b * 2 + slot) * ws.plane;
     const long pitch = ws.pitch;
-    const int c_lo = crank * DPC_WPC * DPC_OWW - DPC_R;     // first column of the CTA window
-    const int woff = w * DPC_OWW + lane * DPC_V;             // lane's offset in the window
-    const int cbase = c_lo + woff;                           // lane's first column
+    const int cbase = g * DPC_OWW - DPC_R + lane * DPC_V;   // lane's first column
     const bool owner = lane >= DPC_HL && lane < 32 - DPC_HL;
     const int dstride = ws.dstride;
     uint32_t *dirs = ws.dirs + (long)b * ws.dbuf;
     uint16_t *J = ws.J + (long)b * NB * ws.jstride;
     uint32_t *Dfirst = ws.Dfirst + (long)b * NB * dstride;
 
-    // ---- energy ring: stage s holds rows 1+16s .. 16+16s ----------------------
-    uint32_t *ring = reinterpret_cast<uint32_t *>(smraw);
-    const int cp_lo = max(c_lo, 0), cp_hi = (int)min((long)(c_lo + DPC_CW), pitch);
-    const unsigned row_bytes = cp_hi > cp_lo ? (unsigned)(cp_hi - cp_lo) * 4u : 0u;
+    // ---- per-warp energy ring: stage s holds rows 1+16s .. 16+16s of the
+    //      warp's 128-column window ---------------------------------------------
+    uint32_t *wring = reinterpret_cast<uint32_t *>(smraw) + (size_t)w * DPC_NST * DPC_S * DPC_WW;
+    const int wx = g * DPC_OWW - DPC_R;   // first column of the warp's window
+    const int zplane = b * 2 + slot;
     const int nstages = (H - 1 + DPC_S - 1) / DPC_S;
-    auto issue_stage = [&](int s) {   // thread 0 only
+    auto issue = [&](int s) {   // lane 0 of the warp
         if (s >= nstages) return;
-        const int r0 = 1 + s * DPC_S, r1 = min(r0 + DPC_S, H);
-        uint64_t *mb = &mbar[s % DPC_NST];
-        mbar_expect_tx(mb, row_bytes * (unsigned)(r1 - r0));
-        if (row_bytes) {
-            uint32_t *dst = ring + (size_t)(s % DPC_NST) * DPC_S * DPC_CW + (cp_lo - c_lo);
-            for (int r = r0; r < r1; ++r)
-                bulk_g2s(dst + (size_t)(r - r0) * DPC_CW, E + (long)r * pitch + cp_lo, row_bytes,
-                         mb);
-        }
+        uint64_t *mb = &mring[w][s % DPC_NST];
+        mbar_expect_tx(mb, (unsigned)DPC_WSLOT);
+        tma_load_3d(wring + (size_t)(s % DPC_NST) * DPC_S * DPC_WW, &tmE, wx, 1 + s * DPC_S,
+                    zplane, mb);
     };
-    if (tid == 0) {
-        for (int i = 0; i < DPC_NST + 2; ++i) mbar_init(&mbar[i], 1);
+    // halo bytes a warp receives per refresh: 32 costs and 32 labels per neighbour
+    const unsigned in_bytes =
+        (g > 0 ? 2u * DPC_R * 4u : 0u) + (g + 1 < nwarps ? 2u * DPC_R * 4u : 0u);
+    if (lane == 0) {
+        for (int i = 0; i < DPC_NST; ++i) mbar_init(&mring[w][i], 1);
+        mbar_init(&minbox[w][0], 1);
+        mbar_init(&minbox[w][1], 1);
+        if (w == 0) { mbar_init(&mbar[0], 1); mbar_init(&mbar[1], 1); }
         fence_mbar_init();
+        mbar_expect_tx(&minbox[w][0], in_bytes);   // refreshes 0 and 1
+        mbar_expect_tx(&minbox[w][1], in_bytes);
+        for (int s2 = 0; s2 < DPC_NST; ++s2) issue(s2);
     }
-    __syncthreads();
-    if (tid == 0)
-        for (int s = 0; s < DPC_NST; ++s) issue_stage(s);
+    __syncwarp();
 
     // ---- row 0 ----------------------------------------------------------------
     uint32_t cost[DPC_V], lab[DPC_V];
@@ -200,14 +255,14 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
     };
     auto stage_rows = [&](int s, auto guarded) {
         constexpr bool GUARD = decltype(guarded)::value;
-        const uint32_t *rs = ring + (size_t)(s % DPC_NST) * DPC_S * DPC_CW + woff;
+        const uint32_t *rs = wring + (size_t)(s % DPC_NST) * DPC_S * DPC_WW + lane * DPC_V;
         const int ibase = 1 + DPC_S * s;
         const bool band_edge = ((ibase + DPC_S - 1) % RJ) == 0;   // row 16s+16 starts a band
 #pragma unroll
         for (int ro = 0; ro < DPC_S; ++ro) {
             const int i = ibase + ro;
             if (!GUARD || i < H) {
-                const uint4 ev = *reinterpret_cast<const uint4 *>(rs + ro * DPC_CW);
+                const uint4 ev = *reinterpret_cast<const uint4 *>(rs + ro * DPC_WW);
                 const uint32_t e[DPC_V] = {valid[0] ? ev.x : BIG, valid[1] ? ev.y : BIG,
                                            valid[2] ? ev.z : BIG, valid[3] ? ev.w : BIG};
                 const uint32_t lc = __shfl_up_sync(0xffffffffu, cost[DPC_V - 1], 1);
@@ -257,73 +312,32 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
         }
     };
     for (int s = 0; s < nstages; ++s) {
-        mbar_wait(&mbar[s % DPC_NST], (unsigned)(s / DPC_NST) & 1u, ws.err, WAIT_NS);
+        mbar_wait(&mring[w][s % DPC_NST], (unsigned)(s / DPC_NST) & 1u, ws.err, WAIT_NS);
         const int ibase = 1 + DPC_S * s;
         if (ibase + DPC_S - 1 < H) stage_rows(s, std::false_type{});
         else stage_rows(s, std::true_type{});
+        __syncwarp();
+        if (lane == 0) issue(s + DPC_NST);   // the warp is done with this slot
         const int ilast = ibase + DPC_S - 1;   // the stage's last row
         if ((s + 1) % DPC_SPR == 0 && ilast < H - 1) {
-            // the slots of the stages just finished are refilled once every
-            // warp of this CTA is past them; account their bytes now
-            if (tid == 0) {
-                for (int k = 0; k < DPC_SPR; ++k) {
-                    const int sn = s - k + DPC_NST;
-                    if (sn < nstages) {
-                        const int r0 = 1 + sn * DPC_S, r1 = min(r0 + DPC_S, H);
-                        mbar_expect_tx(&mbar[sn % DPC_NST], row_bytes * (unsigned)(r1 - r0));
-                    }
-                }
-            }
-            // push the owned edge strips into the neighbours' inboxes (remote
-            // stores across CTAs), synchronise, then read the own inboxes
-            const int par = (s / DPC_SPR) & 1;
+            // refresh e: send the owned edge strips to the neighbours' inboxes,
+            // then wait for the own inbox and reload the halos from it
+            const int e = (s + 1) / DPC_SPR - 1, par = e & 1;
             if (lane >= 32 - 2 * DPC_HL && lane < 32 - DPC_HL && g + 1 < nwarps) {
-                uint32_t *dc, *dl;
-                if (w < DPC_WPC - 1) {
-                    dc = &inLc[par][w + 1][0];
-                    dl = &inLl[par][w + 1][0];
-                } else {
-                    dc = cluster.map_shared_rank(&inLc[par][0][0], crank + 1);
-                    dl = cluster.map_shared_rank(&inLl[par][0][0], crank + 1);
-                }
+                const int tg = g + 1, tr = tg / DPC_WPC, tw = tg % DPC_WPC;
                 const int o = (lane - (32 - 2 * DPC_HL)) * DPC_V;
-#pragma unroll
-                for (int v = 0; v < DPC_V; ++v) {
-                    dc[o + v] = cost[v];
-                    dl[o + v] = lab[v];
-                }
+                const uint32_t mb = mapa_u32(smem_u32(&minbox[tw][par]), tr);
+                st_async_v4(mapa_u32(smem_u32(&inLc[par][tw][o]), tr), cost, mb);
+                st_async_v4(mapa_u32(smem_u32(&inLl[par][tw][o]), tr), lab, mb);
             }
             if (lane >= DPC_HL && lane < 2 * DPC_HL && g > 0) {
-                uint32_t *dc, *dl;
-                if (w > 0) {
-                    dc = &inRc[par][w - 1][0];
-                    dl = &inRl[par][w - 1][0];
-                } else {
-                    dc = cluster.map_shared_rank(&inRc[par][DPC_WPC - 1][0], crank - 1);
-                    dl = cluster.map_shared_rank(&inRl[par][DPC_WPC - 1][0], crank - 1);
-                }
+                const int tg = g - 1, tr = tg / DPC_WPC, tw = tg % DPC_WPC;
                 const int o = (lane - DPC_HL) * DPC_V;
-#pragma unroll
-                for (int v = 0; v < DPC_V; ++v) {
-                    dc[o + v] = cost[v];
-                    dl[o + v] = lab[v];
-                }
+                const uint32_t mb = mapa_u32(smem_u32(&minbox[tw][par]), tr);
+                st_async_v4(mapa_u32(smem_u32(&inRc[par][tw][o]), tr), cost, mb);
+                st_async_v4(mapa_u32(smem_u32(&inRl[par][tw][o]), tr), lab, mb);
             }
-            cluster.sync();
-            // refill: the warps' lane 0 share the copies of the freed stages
-            if (lane == 0 && row_bytes) {
-                for (int k = 0; k < DPC_SPR; ++k) {
-                    const int sn = s - k + DPC_NST;
-                    if (sn >= nstages) continue;
-                    const int r0 = 1 + sn * DPC_S, r1 = min(r0 + DPC_S, H);
-                    uint32_t *dst =
-                        ring + (size_t)(sn % DPC_NST) * DPC_S * DPC_CW + (cp_lo - c_lo);
-                    for (int r = r0 + w * (DPC_S / DPC_WPC);
-                         r < min(r0 + (w + 1) * (DPC_S / DPC_WPC), r1); ++r)
-                        bulk_g2s(dst + (size_t)(r - r0) * DPC_CW, E + (long)r * pitch + cp_lo,
-                                 row_bytes, &mbar[sn % DPC_NST]);
-                }
-            }
+            mbar_wait_cluster(&minbox[w][par], (unsigned)(e >> 1) & 1u, ws.err, WAIT_NS);
             if (lane < DPC_HL) {
 #pragma unroll
                 for (int v = 0; v < DPC_V; ++v) {
@@ -338,6 +352,8 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
                     lab[v] = inRl[par][w][(lane - (32 - DPC_HL)) * DPC_V + v];
                 }
             }
+            __syncwarp();
+            if (lane == 0) mbar_expect_tx(&minbox[w][par], in_bytes);   // arm refresh e+2
         }
     }
     // the last row: a partial 4-row block, group and band are stored here
@@ -421,9 +437,9 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
         const unsigned jbytes = (unsigned)NB * ws.jstride * 2u;
         const unsigned dbytes = (unsigned)NB * dstride * 4u;
         if (tid == 0) {
-            mbar_expect_tx(&mbar[DPC_NST], jbytes + dbytes);
-            bulk_g2s(Js, J, jbytes, &mbar[DPC_NST]);
-            bulk_g2s(Ds, Dfirst, dbytes, &mbar[DPC_NST]);
+            mbar_expect_tx(&mbar[0], jbytes + dbytes);
+            bulk_g2s(Js, J, jbytes, &mbar[0]);
+            bulk_g2s(Ds, Dfirst, dbytes, &mbar[0]);
         }
         for (int r = 1; r < C; ++r) {
             const int n = lcnt[r];
@@ -459,17 +475,21 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
             dpx[0] = keff;
             s_keff = keff;
         }
-        mbar_wait(&mbar[DPC_NST], 0u, ws.err, WAIT_NS);
+        mbar_wait(&mbar[0], 0u, ws.err, WAIT_NS);
         // each seam's column at every band's last row, band by band upwards
+        // (columns are checked against [0, W): a table entry outside it can
+        // only come from a fault, which is reported instead of followed)
         for (int s = tid; s < keff; s += NT) {
             int col = sel[s];
             for (int q = NB - 1; q >= 0; --q) {
                 colbot[(long)q * ws.kcap + s] = (uint16_t)col;
-                const int top = Js[(long)q * ws.jstride + col];
+                int top = Js[(long)q * ws.jstride + col];
+                if (top >= W) { atomicExch(ws.err, DEV_EINTERNAL); top = W - 1; }
                 if (q > 0) {
                     const int r0 = q * RJ;
                     const uint32_t word = Ds[(long)q * dstride + (top >> 2)];
                     col = top + (int)((word >> (8 * (r0 & 3) + 2 * (top & 3))) & 3u) - 1;
+                    if (col < 0 || col >= W) { atomicExch(ws.err, DEV_EINTERNAL); col = min(max(col, 0), W - 1); }
                 }
             }
         }
@@ -505,7 +525,7 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
                     const int shi = ghi - j * cb, slo = max(glo, shi - cb);
                     if (shi > slo) total += (unsigned)(shi - slo) * dstride * 16u;
                 }
-                mbar_expect_tx(&mbar[DPC_NST + 1], total);
+                mbar_expect_tx(&mbar[1], total);
                 for (int qq = 0; qq < nbq; ++qq) {
                     const int q = q0 + qq;
                     const int glo = q * gpb, ghi = (min((q + 1) * RJ, H) + 15) >> 4;
@@ -513,10 +533,10 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
                     if (shi > slo)
                         bulk_g2s(stage + (size_t)qq * cb * dstride * 4,
                                  dirs + (long)slo * dstride * 4,
-                                 (unsigned)(shi - slo) * dstride * 16u, &mbar[DPC_NST + 1]);
+                                 (unsigned)(shi - slo) * dstride * 16u, &mbar[1]);
                 }
             }
-            mbar_wait(&mbar[DPC_NST + 1], (unsigned)j & 1u, ws.err, WAIT_NS);
+            mbar_wait(&mbar[1], (unsigned)j & 1u, ws.err, WAIT_NS);
             for (int x = tid; x < nbq * keff; x += NT) {
                 const int qq = x / keff, s = x - qq * keff;
                 const int q = q0 + qq;
@@ -527,6 +547,7 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
                 const int i_hi = min(shi * 16, rend) - 1, i_lo = max(slo * 16, rtop);
                 const uint32_t *sq = stage + (size_t)qq * cb * dstride * 4;
                 int col = cur[x];
+                if (col >= W) { atomicExch(ws.err, DEV_EINTERNAL); col = W - 1; }
                 const int mypos = pos_s[s];
                 for (int i = i_hi; i >= i_lo; --i) {
                     rem[(long)i * ws.kcap + mypos] = (uint16_t)col;
@@ -537,6 +558,7 @@ k_dpc(CarveWs ws, int k, int16_t *seams, long seam_stride) {
                         const uint32_t word =
                             sq[((size_t)((i >> 4) - slo) * dstride + (col >> 2)) * 4 + ((i >> 2) & 3)];
                         col += (int)((word >> (8 * (i & 3) + 2 * (col & 3))) & 3u) - 1;
+                        if (col < 0 || col >= W) { atomicExch(ws.err, DEV_EINTERNAL); col = min(max(col, 0), W - 1); }
                     }
                 }
                 cur[x] = col;
@@ -567,6 +589,37 @@ size_t dpc_smem(int W0, int H, int rj, int kcap, int C) {
     return m;
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once.
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 3-D view of E ([nb*2 planes][H][pitch] int32) with 16-row x 128-column boxes.
+bool make_energy_map(const CarveWs &ws, int nb, CUtensorMap *m) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)ws.pitch, (cuuint64_t)ws.H, (cuuint64_t)nb * 2};
+    const cuuint64_t strides[2] = {(cuuint64_t)ws.pitch * 4, (cuuint64_t)ws.plane * 4};
+    const cuuint32_t box[3] = {DPC_WW, DPC_S, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, ws.E, dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 }  // namespace
 
 bool dpc_plan(int W0, int H, int *ctas, int *rj, size_t *smem) {
@@ -594,6 +647,7 @@ bool dpc_plan(int W0, int H, int *ctas, int *rj, size_t *smem) {
 }
 
 bool dpc_available(int W0, int H) {
+    if (!encode_tiled()) return false;
     int C = 0, rj = 0;
     size_t smem = 0;
     if (!dpc_plan(W0, H, &C, &rj, &smem)) return false;
@@ -648,7 +702,9 @@ cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long se
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_dpc, ws, k, seams, seam_stride);
+    CUtensorMap tm;
+    if (!make_energy_map(ws, nb, &tm)) return cudaErrorInvalidValue;
+    e = cudaLaunchKernelEx(&cfg, k_dpc, tm, ws, k, seams, seam_stride);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

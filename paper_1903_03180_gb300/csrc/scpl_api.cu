@@ -426,6 +426,8 @@ scpl_status scpl_seams(scpl_handle h, const int32_t *energy, int H, int W, int k
     SCPL_CUDA(h, cudaStreamSynchronize(st));
     if (*herr == DEV_ETIMEOUT)
         return fail(h, SCPL_ETIMEOUT, "a bounded device-side wait ran out in the DP");
+    if (*herr != DEV_OK)
+        return fail(h, SCPL_ECUDA, "internal consistency check failed on the device (%d)", *herr);
     *k_eff = hb->k_eff;
     return SCPL_OK;
 }
@@ -562,6 +564,8 @@ scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W
     SCPL_CUDA(h, cudaStreamSynchronize(st));
     if (*herr == DEV_ETIMEOUT)
         return fail(h, SCPL_ETIMEOUT, "a bounded device-side wait ran out while carving");
+    if (*herr != DEV_OK)
+        return fail(h, SCPL_ECUDA, "internal consistency check failed on the device (%d)", *herr);
     if (buffer_starts) std::copy(starts.begin(), starts.end(), buffer_starts);
     if (n_buffers) *n_buffers = nb;
     return SCPL_OK;

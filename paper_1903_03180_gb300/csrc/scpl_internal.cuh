@@ -14,6 +14,7 @@ constexpr uint32_t LABEL_MASK = 0xFFFFFFu;         // 24-bit parent label of a D
 // Status words written by kernels (mirror scpl_status).
 constexpr int DEV_OK = 0;
 constexpr int DEV_ETIMEOUT = 4;
+constexpr int DEV_EINTERNAL = 6;   // an internal table held an out-of-range column
 
 // Per-buffer carving state, one per spatiotemporal buffer, in device memory.
 // An iteration's seams are selected by k_dp_select (k_eff > 0 = "pending");
@@ -82,6 +83,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, unsigned parity) {
 __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, unsigned parity, int *err,
                                           unsigned long long limit_ns) {
     if (mbar_try_wait(mbar, parity)) return true;
+    if (err && *(volatile int *)err != DEV_OK) return false;   // an earlier wait gave up
     const unsigned long long t0 = globaltimer_now();
     while (!mbar_try_wait(mbar, parity)) {
         if (globaltimer_now() - t0 > limit_ns) {
