@@ -192,6 +192,92 @@ typedef struct {
 scpl_status scpl_set_profiling(scpl_handle h, int on);
 scpl_status scpl_get_stats(scpl_handle h, scpl_stats *out);
 
+/* ------------------------------------------------------------------------
+ * Many clips at once: batching and serving.  The paper carves one video at a
+ * time (Sec. 3, 4); it has no counterpart for these entry points.  They run
+ * the same kernels as scpl_carve, with every stage launched once for all the
+ * clips that are at that stage, and give each clip the same result as
+ * scpl_carve gives it alone.
+ *
+ * A job retargets one clip of T frames from H x W to target_H x target_W.
+ * A smaller width is reached by vertical seams (Sec. 3.1); a smaller height
+ * by horizontal seams, i.e. the same method on the transposed frames
+ * (Sec. 2: seams are vertical or horizontal).  When both shrink the width is
+ * carved first.  k is the cap on seams per iteration, as in scpl_carve.
+ *  frames  [T][H][W][3]                 device, or host when on_host != 0
+ *  out     [T][target_H][target_W][3]   device, or host when on_host != 0
+ *  buffer_starts  [host] or NULL, T+1 entries: the spatiotemporal buffers of
+ *          the first pass (as scpl_carve returns them), written when that
+ *          pass's scan completes
+ *  n_buffers, status  written by the library (status = this job's result)
+ * The caller keeps frames, out and buffer_starts valid and unchanged until
+ * the job has completed.  Host frames should be page-locked for the copies
+ * to overlap other work (pageable memory works, synchronously). */
+typedef struct {
+    const uint8_t *frames;
+    int T, H, W;
+    int target_W, target_H;
+    int k;
+    int on_host;
+    uint8_t *out;
+    int32_t *buffer_starts;
+    int n_buffers;
+    int status;
+} scpl_job;
+
+/* Carve every job; returns when all have completed (host-synchronous).  The
+ * work starts after everything queued before on the handle's stream.
+ * Returns SCPL_OK if every job succeeded, else the first failing job's status
+ * (each job's own result is in jobs[i].status; a job with bad arguments
+ * fails alone with SCPL_EINVAL). */
+scpl_status scpl_carve_batch(scpl_handle h, scpl_job *jobs, int n_jobs);
+
+/* Device memory one job holds while it runs, as admission counts it: the
+ * copies of host frames and outputs, the transposed frames of a horizontal
+ * pass, the luma and motion maps, the scan state and the carving workspace of
+ * one spatiotemporal buffer.  Each further buffer the scan finds adds
+ * scpl_job_footprint_per_buffer bytes when it is found.  0 for an invalid job. */
+size_t scpl_job_footprint(const scpl_params *p, const scpl_job *job);
+size_t scpl_job_footprint_per_buffer(const scpl_job *job);
+
+/* A server: continuous batching of retarget jobs on one GPU.
+ *  scpl_server_create   hbm_budget = bytes of device memory the admitted jobs
+ *                       may hold (0: 90 % of the free memory at creation).
+ *  scpl_server_submit   queue a job (the struct is copied; its buffers must
+ *                       stay valid until completion).  *ticket identifies it.
+ *  scpl_server_progress admit queued jobs in arrival order while their
+ *                       footprint fits the budget, and launch the next stage
+ *                       of every admitted job whose previous stage finished.
+ *                       Jobs admitted while others run share the GPU with
+ *                       them.  wait != 0: if nothing could be launched, block
+ *                       until some work in flight finishes.
+ *  scpl_server_poll     up to max completed jobs since the last poll: their
+ *                       tickets and statuses; returns how many.
+ *  scpl_server_drain    progress until every submitted job has completed.
+ * A server is not thread-safe: one host thread drives it. */
+typedef struct scpl_server_s *scpl_server;
+
+typedef struct {
+    long long submitted, completed, failed;
+    int queued, active;
+    long long scan_waves;        /* multi-clip scan launches                   */
+    long long groups;            /* carving groups (clips of one size per wave) */
+    long long chunks;            /* DP + update chunks launched as CUDA graphs */
+    long long graphs_built;
+    long long kernel_launches;   /* kernels of this library, graph nodes included */
+    size_t reserved_bytes, peak_reserved_bytes, budget_bytes;
+} scpl_server_stats;
+
+scpl_status scpl_server_create(const scpl_params *p, size_t hbm_budget, void *stream,
+                               scpl_server *out);
+scpl_status scpl_server_submit(scpl_server s, const scpl_job *job, long long *ticket);
+scpl_status scpl_server_progress(scpl_server s, int wait, int *n_active, int *n_queued);
+int scpl_server_poll(scpl_server s, long long *tickets, int *statuses, int max);
+scpl_status scpl_server_drain(scpl_server s);
+scpl_status scpl_server_get_stats(scpl_server s, scpl_server_stats *out);
+const char *scpl_server_last_error(scpl_server s);
+void scpl_server_destroy(scpl_server s);
+
 #ifdef __cplusplus
 }
 #endif

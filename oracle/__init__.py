@@ -212,3 +212,30 @@ def carve(frames: np.ndarray, target: int, k: int, wg: int = 1, wm: int = 2,
                              _ptr(seams)))
     n = int(nb[0])
     return out, starts[: n + 1].copy(), seams[:n, : W0 - target].copy()
+
+
+def carve_job(frames: np.ndarray, target_W: int, target_H: int, k: int, wg: int = 1,
+              wm: int = 2, alpha: float = ALPHA, t_max: int = T_MAX, use_buffer: bool = True,
+              maxval_mode: int = 0):
+    """A retarget job to target_H x target_W.  Seams are vertical or horizontal
+    (Sec. 2).  The width is carved first with vertical seams (``carve``).  The
+    height is then carved as vertical seams of the transposed result, with its
+    own buffer scan, and transposed back.
+
+    Returns (out [T,target_H,target_W,3], starts of the first pass)."""
+    frames = np.ascontiguousarray(frames, dtype=np.uint8)
+    T, H, W = frames.shape[:3]
+    out, starts = frames, None
+    kw = dict(wg=wg, wm=wm, alpha=alpha, t_max=t_max, use_buffer=use_buffer,
+              maxval_mode=maxval_mode)
+    if target_W < W:
+        out, starts, _ = carve(out, target_W, k, **kw)
+    if target_H < H:
+        tr = np.ascontiguousarray(out.transpose(0, 2, 1, 3))
+        o2, s2, _ = carve(tr, target_H, k, **kw)
+        if starts is None:
+            starts = s2
+        out = np.ascontiguousarray(o2.transpose(0, 2, 1, 3))
+    if starts is None:
+        starts = np.array([0, T], np.int32)
+    return out, starts

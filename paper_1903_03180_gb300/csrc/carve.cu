@@ -20,6 +20,9 @@
 //                  energy is the old one.
 // After the last iteration k_gather copies every output pixel's colour from
 // its original column.
+#include <map>
+#include <mutex>
+
 #include "scpl_internal.cuh"
 
 namespace scpl {
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(DP_MAX_WARPS * 32, 1)
 k_dp(CarveWs ws, int k, int16_t *seams, long seam_stride, int band_blocks) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ uint32_t bnd_c[2][DP_MAX_WARPS][2], bnd_l[2][DP_MAX_WARPS][2];
-    __shared__ int s_W, s_slot, s_removed, s_target, s_active, s_cnt;
+    __shared__ int s_W, s_slot, s_removed, s_target, s_active, s_cnt, s_k;
     const int b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int NT = blockDim.x, NW = NT >> 5;
     const int H = ws.H;
@@ -351,6 +354,7 @@ k_dp(CarveWs ws, int k, int16_t *seams, long seam_stride, int band_blocks) {
         ws.st[b] = st;
         s_W = st.W; s_slot = st.slot; s_removed = st.removed; s_target = st.target;
         s_active = st.W > st.target;
+        s_k = st.k > 0 ? st.k : k;
         s_cnt = 0;
     }
     __syncthreads();
@@ -490,7 +494,7 @@ k_dp(CarveWs ws, int k, int16_t *seams, long seam_stride, int band_blocks) {
     }
     __syncthreads();
     const int n = s_cnt;
-    int keff = min(k, W - s_target);
+    int keff = min(s_k, W - s_target);
     keff = min(keff, n);
     for (int c = tid; c < n; c += NT) {
         const uint64_t v = cand[c];
@@ -590,6 +594,57 @@ __global__ void k_gather(CarveWs ws, const uint8_t *__restrict__ rgb, const int 
     }
 }
 
+// Final colour gather of frames listed in a table (frames of several clips
+// that share one (H, W0) workspace).  grid (H, frames).
+__global__ void k_gather_frames(CarveWs ws, const GatherFrame *__restrict__ tab) {
+    const int i = blockIdx.x;
+    const GatherFrame g = tab[blockIdx.y];
+    int W, slot, removed;
+    committed(ws.st[g.b], W, slot, removed);
+    if (W != g.target) {   // carving did not reach the target: report, copy nothing
+        if (i == 0 && threadIdx.x == 0) atomicExch(ws.err, DEV_EINTERNAL);
+        return;
+    }
+    const uint16_t *O = ws.O + ((long)g.b * 2 + slot) * ws.plane + (long)i * ws.pitch;
+    const uint8_t *src = g.src + (long)i * ws.W0 * 3;
+    uint8_t *dst = g.dst + (long)i * g.target * 3;
+    for (int p = threadIdx.x; p < g.target; p += blockDim.x) {
+        const int o = O[p];
+        dst[p * 3 + 0] = src[o * 3 + 0];
+        dst[p * 3 + 1] = src[o * 3 + 1];
+        dst[p * 3 + 2] = src[o * 3 + 2];
+    }
+}
+
+// dst[t][j][i] = src[t][i][j] for RGB pixels: [T][H][W][3] -> [T][W][H][3].
+// 32x32 pixel tiles through shared memory, grid (ceil(W/32), ceil(H/32), T).
+__global__ void __launch_bounds__(256) k_transpose_rgb(const uint8_t *__restrict__ src, int H,
+                                                       int W, uint8_t *__restrict__ dst) {
+    __shared__ uint8_t tile[32][32 * 3 + 4];
+    const int j0 = blockIdx.x * 32, i0 = blockIdx.y * 32;
+    const long frame = (long)blockIdx.z * H * W * 3;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + r, j = j0 + tx;
+        if (i < H && j < W) {
+            const uint8_t *p = src + frame + ((long)i * W + j) * 3;
+            tile[r][tx * 3 + 0] = p[0];
+            tile[r][tx * 3 + 1] = p[1];
+            tile[r][tx * 3 + 2] = p[2];
+        }
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int j = j0 + r, i = i0 + tx;   // output row j, column i
+        if (i < H && j < W) {
+            uint8_t *q = dst + frame + ((long)j * H + i) * 3;
+            q[0] = tile[tx][r * 3 + 0];
+            q[1] = tile[tx][r * 3 + 1];
+            q[2] = tile[tx][r * 3 + 2];
+        }
+    }
+}
+
 int dp_lanes_cols(int W0) { return W0 <= 4096 ? 4 : 8; }
 
 template <int V>
@@ -598,7 +653,7 @@ cudaError_t launch_dp_t(const CarveWs &ws, int nb, int k, int16_t *seams, long s
     int band_blocks = 0;
     size_t smem = dp_smem_bytes(ws.W0, ws.H, &band_blocks);
     cudaError_t e =
-        cudaFuncSetAttribute(k_dp<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        raise_dyn_smem((const void *)k_dp<V>, smem);
     if (e != cudaSuccess) return e;
     const int nw = (ws.W0 + 32 * V - 1) / (32 * V);
     k_dp<V><<<nb, 32 * nw, smem, s>>>(ws, k, seams, seam_stride, band_blocks);
@@ -649,7 +704,7 @@ cudaError_t launch_update(const CarveWs &ws, int nb, cudaStream_t s) {
     int rb = 8;
     size_t smem = update_smem_bytes(ws.W0, ws.kcap, &rb);
     cudaError_t e =
-        cudaFuncSetAttribute(k_update, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        raise_dyn_smem((const void *)k_update, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((ws.H + rb - 1) / rb, nb);
     k_update<<<grid, UP_THREADS, smem, s>>>(ws, rb);
@@ -671,6 +726,91 @@ cudaError_t launch_gather(const CarveWs &ws, const uint8_t *rgb, int T, const in
                           int target, uint8_t *out, cudaStream_t s) {
     k_gather<<<dim3(ws.H, T), 256, 0, s>>>(ws, rgb, buf_of_frame, target, out);
     return cudaGetLastError();
+}
+
+cudaError_t launch_gather_frames(const CarveWs &ws, const GatherFrame *tab, int nframes,
+                                 cudaStream_t s) {
+    for (int f0 = 0; f0 < nframes; f0 += 65535) {
+        const int n = nframes - f0 < 65535 ? nframes - f0 : 65535;
+        k_gather_frames<<<dim3(ws.H, n), 256, 0, s>>>(ws, tab + f0);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_rgb(const uint8_t *src, int T, int H, int W, uint8_t *dst,
+                                 cudaStream_t s) {
+    for (int t0 = 0; t0 < T; t0 += 65535) {
+        const int n = T - t0 < 65535 ? T - t0 : 65535;
+        const long off = (long)t0 * H * W * 3;
+        k_transpose_rgb<<<dim3((W + 31) / 32, (H + 31) / 32, n), 256, 0, s>>>(src + off, H, W,
+                                                                              dst + off);
+    }
+    return cudaGetLastError();
+}
+
+namespace {
+size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+}  // namespace
+
+cudaError_t raise_dyn_smem(const void *func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> limit;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cur = limit[std::make_pair(dev, func)];
+    if (bytes <= cur) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cur = bytes;
+    return e;
+}
+
+size_t carve_ws_assign(CarveWs &ws, int nb, int klog_stride, bool dpc, char *base) {
+    const int H = ws.H, W0 = ws.W0;
+    ws.pitch = (W0 + 31) / 32 * 32;
+    ws.plane = (long)H * ws.pitch;
+    ws.dstride = (((W0 + 3) / 4) + 3) & ~3;
+    ws.dbuf = (long)((H + 15) / 16) * 4 * ws.dstride;
+    ws.jstride = (W0 + 7) & ~7;
+    ws.kcap = ws.kcap < 1 ? 1 : ws.kcap;
+    ws.klog_stride = klog_stride < 1 ? 1 : klog_stride;
+    ws.rj = 0;
+    ws.nbands = 0;
+    if (dpc) {
+        int C = 0, rj = 0;
+        size_t smem = 0;
+        if (!dpc_plan(W0, H, &C, &rj, &smem)) dpc = false;
+        else {
+            ws.rj = rj;
+            ws.nbands = (H + rj - 1) / rj;
+        }
+    }
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off += al256(bytes < 1 ? 1 : bytes);
+        return base ? base + o : nullptr;
+    };
+    ws.E = reinterpret_cast<int32_t *>(take((size_t)nb * 2 * ws.plane * 4));
+    ws.SD = reinterpret_cast<int32_t *>(take((size_t)nb * ws.plane * 4));
+    ws.O = reinterpret_cast<uint16_t *>(take((size_t)nb * 2 * ws.plane * 2));
+    ws.dirs = reinterpret_cast<uint32_t *>(take((size_t)nb * ws.dbuf * 4));
+    ws.dirty_count = reinterpret_cast<unsigned long long *>(take((size_t)nb * 8));
+    ws.rem = reinterpret_cast<uint16_t *>(take((size_t)nb * H * ws.kcap * 2));
+    ws.st = reinterpret_cast<BufState *>(take((size_t)nb * sizeof(BufState)));
+    ws.klog = reinterpret_cast<int *>(take((size_t)nb * ws.klog_stride * 4));
+    ws.J = nullptr;
+    ws.Dfirst = nullptr;
+    ws.colbot = nullptr;
+    ws.dpx = nullptr;
+    if (dpc) {
+        ws.J = reinterpret_cast<uint16_t *>(take((size_t)nb * ws.nbands * ws.jstride * 2));
+        ws.Dfirst = reinterpret_cast<uint32_t *>(take((size_t)nb * ws.nbands * ws.dstride * 4));
+        ws.colbot = reinterpret_cast<uint16_t *>(take((size_t)nb * ws.nbands * ws.kcap * 2));
+        ws.dpx = reinterpret_cast<int *>(take((size_t)nb * (1 + ws.kcap) * 4));
+    }
+    return off;
 }
 
 }  // namespace scpl

@@ -455,7 +455,7 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
         }
         __syncthreads();
         const int n = s_cnt;
-        int keff = min(k, W - st0.target);
+        int keff = min(st0.k > 0 ? st0.k : k, W - st0.target);
         keff = min(keff, n);
         for (int c = tid; c < n; c += NT) {
             const uint64_t v = cand[c];
@@ -651,9 +651,7 @@ bool dpc_available(int W0, int H) {
     int C = 0, rj = 0;
     size_t smem = 0;
     if (!dpc_plan(W0, H, &C, &rj, &smem)) return false;
-    if (cudaFuncSetAttribute(k_dpc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return false;
+    if (raise_dyn_smem((const void *)k_dpc, smem) != cudaSuccess) return false;
     if (C > 8 &&
         cudaFuncSetAttribute(k_dpc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
             cudaSuccess)
@@ -683,8 +681,7 @@ cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long se
     size_t smem = 0;
     if (!dpc_plan(ws.W0, ws.H, &C, &rj, &smem) || rj != ws.rj) return cudaErrorInvalidValue;
     smem = dpc_smem(ws.W0, ws.H, ws.rj, ws.kcap, C);
-    cudaError_t e =
-        cudaFuncSetAttribute(k_dpc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = raise_dyn_smem((const void *)k_dpc, smem);
     if (e != cudaSuccess) return e;
     if (C > 8) {
         e = cudaFuncSetAttribute(k_dpc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);

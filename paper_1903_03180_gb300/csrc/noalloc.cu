@@ -78,7 +78,7 @@ __global__ void k_noalloc_reset(BufState *st, int *klog, int W, int target) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         BufState s;
         s.t0 = 0; s.nt = 1; s.W = W; s.k_eff = 0; s.removed = 0; s.slot = 0;
-        s.target = target; s.iters = 0; s.tp = 0; s.pad = 0; s.yfm = 0;
+        s.target = target; s.iters = 0; s.tp = 0; s.k = 0; s.yfm = 0;
         *st = s;
         *klog = 0;
     }

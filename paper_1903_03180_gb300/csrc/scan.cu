@@ -13,6 +13,9 @@
 //       publishes its partial A_t = sum floor(sqrt(65536 (n S2 - S1^2))) with
 //       frame t added, plus the partial maximum of e_t.
 // Step (1) of frame t overlaps the device-wide reduction of frame t-1.
+//
+// Several clips can share one launch: a table gives each clip its own range
+// of CTAs, and the waits and reductions above then run among that range only.
 #include "scpl_internal.cuh"
 
 namespace scpl {
@@ -162,7 +165,7 @@ __device__ bool wait_and_decide(const ScanArgs &a, int t, int G, DecState &s, in
                 A += __shfl_xor_sync(0xffffffffu, A, o);
                 m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
             }
-            if (lane == 0) *dec_out = decide(s, A, m, t, a, blockIdx.x == 0);
+            if (lane == 0) *dec_out = decide(s, A, m, t, a, blockIdx.x == (unsigned)a.cta0);
         }
         if (lane == 0) s_ok = ok;
     }
@@ -170,15 +173,30 @@ __device__ bool wait_and_decide(const ScanArgs &a, int t, int G, DecState &s, in
     return s_ok != 0;
 }
 
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs a) {
+// One clip per launch (tab == NULL, every CTA works on a0) or one clip per
+// range of CTAs (clip of CTA x = tab[block_clip[x]], CTAs [cta0, cta0 + G)).
+__global__ void __launch_bounds__(SCAN_THREADS)
+k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ block_clip) {
+    __shared__ ScanArgs a;
     __shared__ uint8_t lum[TR + 2][TC + 2];
     __shared__ long long red_a[SCAN_THREADS / 32];
     __shared__ int red_m[SCAN_THREADS / 32];
     __shared__ DecState st;
     __shared__ int s_dec;
 
-    const int G = gridDim.x;
     const int tid = threadIdx.x;
+    if (tid == 0) {
+        if (tab) {
+            a = tab[block_clip[blockIdx.x]];
+        } else {
+            a = a0;
+            a.cta0 = 0;
+            a.G = gridDim.x;
+        }
+    }
+    __syncthreads();
+    const int G = a.G;
+    const int lb = blockIdx.x - a.cta0;   // CTA index within the clip's range
     const int tiles_x = (a.W + TC - 1) / TC;
     const int ntiles = ((a.H + TR - 1) / TR) * tiles_x;
     const long hw = (long)a.H * a.W;
@@ -193,7 +211,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs a) {
         const uint8_t *f = a.rgb + (long)t * hw * 3;
         uint16_t *ecur = a.ering + (long)(t & 1) * hw;
         int emax = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += G) {
+        for (int tile = lb; tile < ntiles; tile += G) {
             int r0 = (tile / tiles_x) * TR, c0 = (tile % tiles_x) * TC;
             for (int q = tid; q < (TR + 2) * (TC + 2); q += SCAN_THREADS) {
                 int r = q / (TC + 2), c = q % (TC + 2);
@@ -232,14 +250,16 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs a) {
         // ---- (3) fold e_{t-1} into S1/S2, partial A_t ------------------------
         const uint16_t *eprev = a.ering + (long)((t + 1) & 1) * hw;
         unsigned long long acc = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += G) {
+        for (int tile = lb; tile < ntiles; tile += G) {
             int r0 = (tile / tiles_x) * TR, c0 = (tile % tiles_x) * TC;
             for (int q = tid; q < TR * TC; q += SCAN_THREADS) {
                 int gi = r0 + q / TC, gj = c0 + q % TC;
                 if (gi < a.H && gj < a.W) {
                     long p = (long)gi * a.W + gj;
-                    uint32_t s1 = a.S1[p], s2 = a.S2[p];
+                    uint32_t s1 = 0, s2 = 0;   // the sums start at zero (no memset)
                     if (t > 0) {
+                        s1 = a.S1[p];
+                        s2 = a.S2[p];
                         uint32_t ep = eprev[p];
                         if (dec == DEC_JOIN) { s1 += ep; s2 += ep * ep; }
                         else if (dec == DEC_FLUSH) { s1 = ep; s2 = ep * ep; }
@@ -267,8 +287,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs a) {
             long long A = 0;
             int m = 0;
             for (int w = 0; w < SCAN_THREADS / 32; ++w) { A += red_a[w]; m = max(m, red_m[w]); }
-            a.partA[(long)t * G + blockIdx.x] = A;
-            a.partM[(long)t * G + blockIdx.x] = m;
+            a.partA[(long)t * G + lb] = A;
+            a.partM[(long)t * G + lb] = m;
             __threadfence();
             atomicAdd(&a.count[t], 1u);
         }
@@ -277,7 +297,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(ScanArgs a) {
 
     // decision for the last frame, then close the open buffer
     if (!wait_and_decide(a, a.T - 1, G, st, &s_dec)) return;
-    if (blockIdx.x == 0 && tid == 0) {
+    if (lb == 0 && tid == 0) {
         int nb = st.nb;
         if (st.n > 0) a.starts[nb++] = st.start;
         a.starts[nb] = a.T;
@@ -313,9 +333,32 @@ int scan_grid_size(int H, int W, int *err_out) {
 
 cudaError_t launch_scan(const ScanArgs &a, int grid, cudaStream_t s) {
     ScanArgs copy = a;
-    void *args[] = {&copy};
+    const ScanArgs *tab = nullptr;
+    const int *bc = nullptr;
+    void *args[] = {&copy, &tab, &bc};
     return cudaLaunchCooperativeKernel((const void *)k_scan, dim3(grid), dim3(SCAN_THREADS), args,
                                        0, s);
 }
+
+cudaError_t launch_scan_multi(const ScanArgs *tab, const int *block_clip, int grid,
+                              cudaStream_t s) {
+    ScanArgs none{};
+    void *args[] = {&none, &tab, &block_clip};
+    return cudaLaunchCooperativeKernel((const void *)k_scan, dim3(grid), dim3(SCAN_THREADS), args,
+                                       0, s);
+}
+
+int scan_capacity(int *err_out) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan, SCAN_THREADS, 0);
+    if (e != cudaSuccess) { *err_out = (int)e; return 0; }
+    *err_out = 0;
+    return sms * per_sm;
+}
+
+int scan_tiles(int H, int W) { return ((H + TR - 1) / TR) * ((W + TC - 1) / TC); }
 
 }  // namespace scpl

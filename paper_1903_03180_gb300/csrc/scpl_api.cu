@@ -103,11 +103,11 @@ struct scpl_ctx {
     std::string err;
     // scan
     DevBuf Y, D, ering, S1, S2, partA, partM, count, starts, nbuf, errw;
-    // carving
-    DevBuf E, SD, O, dirs, rem, st, bof;
+    // carving: one slab for every array of the carving workspace
+    DevBuf cws, bof;
     // host-memory entry point staging
     DevBuf in_frames, out_frames, seams_dev;
-    DevBuf klog, dirty, J, colbot, dpx, Dfirst, Yfm;
+    DevBuf Yfm;
     // cluster-DP availability per (W0, H) last checked
     int dpc_W0 = -1, dpc_H = -1;
     bool dpc_ok = false;
@@ -205,8 +205,6 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     SCPL_CUDA(h, h->h_small.ensure((size_t)(T + 4) * sizeof(int)));
     cudaStream_t s = h->stream;
     SCPL_CUDA(h, cudaMemsetAsync(h->count.p, 0, (size_t)T * sizeof(unsigned), s));
-    SCPL_CUDA(h, cudaMemsetAsync(h->S1.p, 0, (size_t)hw * sizeof(uint32_t), s));
-    SCPL_CUDA(h, cudaMemsetAsync(h->S2.p, 0, (size_t)hw * sizeof(uint32_t), s));
     SCPL_CUDA(h, cudaMemsetAsync(h->errw.p, 0, sizeof(int), s));
     ScanArgs a;
     a.rgb = frames; a.T = T; a.H = H; a.W = W; a.ypitch = ypitch;
@@ -238,43 +236,15 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     return SCPL_OK;
 }
 
-// Workspace of the carving stage for nb buffers.
+// Workspace of the carving stage for nb buffers (one grow-only slab).
 scpl_status carve_ws(scpl_ctx *h, int nb, int H, int W0, int kcap, CarveWs &ws,
                      int klog_stride = 1) {
+    ws = CarveWs{};
     ws.H = H;
     ws.W0 = W0;
-    ws.pitch = round_up(W0, 32);
-    ws.plane = (long)H * ws.pitch;
-    ws.dstride = (((W0 + 3) / 4) + 3) & ~3;
-    ws.dbuf = (long)((H + 15) / 16) * 4 * ws.dstride;
-    ws.jstride = (W0 + 7) & ~7;
-    ws.Dfirst = nullptr;
-    ws.Yfm = nullptr;
+    ws.kcap = std::max(kcap, 1);
     SCPL_CUDA(h, h->errw.ensure(sizeof(int)));
     ws.err = h->errw.as<int>();
-    ws.kcap = std::max(kcap, 1);
-    SCPL_CUDA(h, h->E.ensure((size_t)nb * 2 * ws.plane * sizeof(int32_t)));
-    SCPL_CUDA(h, h->SD.ensure((size_t)nb * ws.plane * sizeof(int32_t)));
-    SCPL_CUDA(h, h->O.ensure((size_t)nb * 2 * ws.plane * sizeof(uint16_t)));
-    SCPL_CUDA(h, h->dirs.ensure((size_t)nb * ws.dbuf * sizeof(uint32_t)));
-    SCPL_CUDA(h, h->dirty.ensure((size_t)nb * sizeof(unsigned long long)));
-    ws.dirty_count = h->dirty.as<unsigned long long>();
-    SCPL_CUDA(h, h->rem.ensure((size_t)nb * H * ws.kcap * sizeof(uint16_t)));
-    SCPL_CUDA(h, h->st.ensure((size_t)nb * sizeof(BufState)));
-    SCPL_CUDA(h, h->klog.ensure((size_t)nb * std::max(klog_stride, 1) * sizeof(int)));
-    ws.klog = h->klog.as<int>();
-    ws.klog_stride = std::max(klog_stride, 1);
-    ws.E = h->E.as<int32_t>();
-    ws.SD = h->SD.as<int32_t>();
-    ws.O = h->O.as<uint16_t>();
-    ws.dirs = h->dirs.as<uint32_t>();
-    ws.rem = h->rem.as<uint16_t>();
-    ws.st = h->st.as<BufState>();
-    ws.Y = h->Y.as<uint8_t>();
-    ws.D = h->D.as<uint8_t>();
-    ws.ypitch = round_up(W0, 16);
-    ws.wg = h->p.wg;
-    ws.wm = h->p.wm;
     int bb = 0, rb = 0;
     if (dp_smem_bytes(W0, H, &bb) > 227 * 1024 - 4096 ||
         update_smem_bytes(W0, ws.kcap, &rb) > 200 * 1024)
@@ -285,26 +255,14 @@ scpl_status carve_ws(scpl_ctx *h, int nb, int H, int W0, int kcap, CarveWs &ws,
         h->dpc_W0 = W0;
         h->dpc_H = H;
     }
-    ws.rj = 0;
-    ws.nbands = 0;
-    ws.J = nullptr;
-    ws.colbot = nullptr;
-    ws.dpx = nullptr;
-    if (h->dpc_ok) {
-        int C = 0, rj = 0;
-        size_t smem = 0;
-        dpc_plan(W0, H, &C, &rj, &smem);
-        ws.rj = rj;
-        ws.nbands = (H + rj - 1) / rj;
-        SCPL_CUDA(h, h->J.ensure((size_t)nb * ws.nbands * ws.jstride * sizeof(uint16_t)));
-        SCPL_CUDA(h, h->Dfirst.ensure((size_t)nb * ws.nbands * ws.dstride * sizeof(uint32_t)));
-        ws.Dfirst = h->Dfirst.as<uint32_t>();
-        SCPL_CUDA(h, h->colbot.ensure((size_t)nb * ws.nbands * ws.kcap * sizeof(uint16_t)));
-        SCPL_CUDA(h, h->dpx.ensure((size_t)nb * (1 + ws.kcap) * sizeof(int)));
-        ws.J = h->J.as<uint16_t>();
-        ws.colbot = h->colbot.as<uint16_t>();
-        ws.dpx = h->dpx.as<int>();
-    }
+    const size_t bytes = carve_ws_assign(ws, nb, klog_stride, h->dpc_ok, nullptr);
+    SCPL_CUDA(h, h->cws.ensure(bytes));
+    carve_ws_assign(ws, nb, klog_stride, h->dpc_ok, h->cws.as<char>());
+    ws.Y = h->Y.as<uint8_t>();
+    ws.D = h->D.as<uint8_t>();
+    ws.ypitch = round_up(W0, 16);
+    ws.wg = h->p.wg;
+    ws.wm = h->p.wm;
     return SCPL_OK;
 }
 
@@ -360,10 +318,8 @@ void scpl_destroy(scpl_handle h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     DevBuf *bufs[] = {&h->Y, &h->D, &h->ering, &h->S1, &h->S2, &h->partA, &h->partM,
-                      &h->count, &h->starts, &h->nbuf, &h->errw, &h->E, &h->SD, &h->O,
-                      &h->dirs, &h->rem, &h->st, &h->bof, &h->in_frames, &h->out_frames,
-                      &h->seams_dev, &h->klog, &h->dirty, &h->J, &h->colbot, &h->dpx,
-                      &h->Dfirst, &h->Yfm};
+                      &h->count, &h->starts, &h->nbuf, &h->errw, &h->cws, &h->bof,
+                      &h->in_frames, &h->out_frames, &h->seams_dev, &h->Yfm};
     for (DevBuf *b : bufs) b->release();
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
     h->h_small.release();
@@ -601,6 +557,16 @@ scpl_status scpl_carve_host(scpl_handle h, const uint8_t *frames, int T, int H, 
     SCPL_CUDA(h, cudaStreamSynchronize(st));
     if (buffer_starts) std::copy(starts.begin(), starts.begin() + nb + 1, buffer_starts);
     if (n_buffers) *n_buffers = nb;
+    return SCPL_OK;
+}
+
+scpl_status scpl_carve_batch(scpl_handle h, scpl_job *jobs, int n_jobs) {
+    if (!h) return SCPL_EINVAL;
+    if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(h, SCPL_EINVAL, "bad job list");
+    if (n_jobs == 0) return SCPL_OK;
+    std::string err;
+    scpl_status s = engine_run_batch(h->p, h->stream, jobs, n_jobs, err);
+    if (s != SCPL_OK) return fail(h, s, "%s", err.c_str());
     return SCPL_OK;
 }
 

@@ -29,7 +29,7 @@ struct BufState {
     int target;      // target width
     int iters;       // iterations selected so far
     int tp;          // frames of the frame-minor luma copy (nt rounded up to 16)
-    int pad;
+    int k;           // seams per iteration of this buffer (0: the launch's k)
     long long yfm;   // byte offset of this buffer's frame-minor luma copy
 };
 
@@ -161,6 +161,7 @@ struct ScanArgs {
     int t_max, maxval_mode;
     long long maxval_theory;
     unsigned long long spin_limit_ns;
+    int cta0, G;            // the clip's CTAs in a multi-clip launch
 };
 
 // Launchers (return the CUDA error of the launch).
@@ -168,6 +169,12 @@ cudaError_t launch_energy_api(const uint8_t *rgb, int T, int H, int W, int wg, i
                               int32_t *energy, cudaStream_t s);
 int scan_grid_size(int H, int W, int *err_out);
 cudaError_t launch_scan(const ScanArgs &a, int grid, cudaStream_t s);
+// Several clips in one cooperative launch: tab (device) holds each clip's
+// arguments with its CTA range, block_clip (device) the clip of every CTA.
+cudaError_t launch_scan_multi(const ScanArgs *tab, const int *block_clip, int grid,
+                              cudaStream_t s);
+int scan_capacity(int *err_out);   // co-resident scan CTAs on this GPU
+int scan_tiles(int H, int W);      // 8x64 tiles of one frame
 
 cudaError_t launch_energy_init(const CarveWs &ws, int nb, cudaStream_t s);
 cudaError_t launch_update(const CarveWs &ws, int nb, cudaStream_t s);
@@ -182,6 +189,36 @@ cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long se
 cudaError_t launch_identity_O(const CarveWs &ws, int nb, cudaStream_t s);
 cudaError_t launch_gather(const CarveWs &ws, const uint8_t *rgb, int T, const int *buf_of_frame,
                           int target, uint8_t *out, cudaStream_t s);
+// One frame of a batched colour gather: out rows of frame `dst` from `src`
+// (both [H][*][3], device) through the origin map of buffer b.
+struct GatherFrame {
+    const uint8_t *src;
+    uint8_t *dst;
+    int b;
+    int target;
+};
+cudaError_t launch_gather_frames(const CarveWs &ws, const GatherFrame *tab, int nframes,
+                                 cudaStream_t s);
+// [T][H][W][3] -> [T][W][H][3]
+cudaError_t launch_transpose_rgb(const uint8_t *src, int T, int H, int W, uint8_t *dst,
+                                 cudaStream_t s);
+// Carving workspace of nb buffers in one slab: sets ws's geometry (from ws.H,
+// ws.W0, ws.kcap) and, when base is not NULL, its array pointers into base.
+// Returns the slab size in bytes.  dpc: also the cluster-DP tables.
+size_t carve_ws_assign(CarveWs &ws, int nb, int klog_stride, bool dpc, char *base);
+}  // namespace scpl
+
+#include <string>
+#include "scpl.h"
+
+namespace scpl {
+// scpl_carve_batch's engine (engine.cu).
+scpl_status engine_run_batch(const scpl_params &p, cudaStream_t stream, scpl_job *jobs,
+                             int n_jobs, std::string &err);
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device.  It never lowers the limit, so a CUDA graph captured earlier
+// with a larger launch of the same kernel stays launchable.
+cudaError_t raise_dyn_smem(const void *func, size_t bytes);
 size_t dp_smem_bytes(int W0, int H, int *band_blocks);
 size_t update_smem_bytes(int W0, int kcap, int *rows);
 

@@ -43,6 +43,25 @@ class Stats(ctypes.Structure):
                 ("n_kernels", ctypes.c_int), ("kernel", KernelStat * 8)]
 
 
+class Job(ctypes.Structure):
+    """scpl_job: one clip to retarget in a batch or through a server."""
+    _fields_ = [("frames", ctypes.c_void_p), ("T", ctypes.c_int), ("H", ctypes.c_int),
+                ("W", ctypes.c_int), ("target_W", ctypes.c_int), ("target_H", ctypes.c_int),
+                ("k", ctypes.c_int), ("on_host", ctypes.c_int), ("out", ctypes.c_void_p),
+                ("buffer_starts", ctypes.c_void_p), ("n_buffers", ctypes.c_int),
+                ("status", ctypes.c_int)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong),
+                ("failed", ctypes.c_longlong), ("queued", ctypes.c_int), ("active", ctypes.c_int),
+                ("scan_waves", ctypes.c_longlong), ("groups", ctypes.c_longlong),
+                ("chunks", ctypes.c_longlong), ("graphs_built", ctypes.c_longlong),
+                ("kernel_launches", ctypes.c_longlong), ("reserved_bytes", ctypes.c_size_t),
+                ("peak_reserved_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t)]
+
+
+_LL = ctypes.c_longlong
 SIGNATURES = {
     "scpl_default_params": (None, [ctypes.POINTER(Params)]),
     "scpl_create": (_I, [ctypes.POINTER(Params), _P, ctypes.POINTER(_P)]),
@@ -57,6 +76,17 @@ SIGNATURES = {
     "scpl_seams_noalloc": (_I, [_P, _I, _I, _I, _P, _P, _P]),
     "scpl_set_profiling": (_I, [_P, _I]),
     "scpl_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
+    "scpl_carve_batch": (_I, [_P, ctypes.POINTER(Job), _I]),
+    "scpl_job_footprint": (ctypes.c_size_t, [ctypes.POINTER(Params), ctypes.POINTER(Job)]),
+    "scpl_job_footprint_per_buffer": (ctypes.c_size_t, [ctypes.POINTER(Job)]),
+    "scpl_server_create": (_I, [ctypes.POINTER(Params), ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
+    "scpl_server_submit": (_I, [_P, ctypes.POINTER(Job), ctypes.POINTER(_LL)]),
+    "scpl_server_progress": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "scpl_server_poll": (_I, [_P, ctypes.POINTER(_LL), ctypes.POINTER(_I), _I]),
+    "scpl_server_drain": (_I, [_P]),
+    "scpl_server_get_stats": (_I, [_P, ctypes.POINTER(ServerStats)]),
+    "scpl_server_last_error": (ctypes.c_char_p, [_P]),
+    "scpl_server_destroy": (None, [_P]),
 }
 
 
@@ -286,6 +316,119 @@ class Retargeter:
         if self.h is not None:
             scpl_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- batching
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def make_job(frames, target_W: int, target_H: int, k: int, out, starts=None) -> Job:
+    """A Job over torch CUDA tensors (device job) or numpy arrays (host job).
+    frames [T,H,W,3] uint8, out [T,target_H,target_W,3] uint8, starts an
+    optional int32 numpy array of T+1 entries for the buffer starts."""
+    import torch
+    j = Job()
+    T, H, W, _ = frames.shape
+    if isinstance(frames, torch.Tensor):
+        j.frames = _dev_ptr(frames, torch.uint8, 4, "frames")
+        j.out = _dev_ptr(out, torch.uint8, 4, "out")
+        j.on_host = 0
+    else:
+        j.frames = _host_ptr(frames, np.uint8, "frames")
+        j.out = _host_ptr(out, np.uint8, "out")
+        j.on_host = 1
+    if tuple(out.shape) != (T, target_H, target_W, 3):
+        raise ValueError("out must be [T,target_H,target_W,3]")
+    j.T, j.H, j.W = T, H, W
+    j.target_W, j.target_H, j.k = target_W, target_H, k
+    j.buffer_starts = None if starts is None else _host_ptr(starts, np.int32, "starts")
+    return j
+
+
+def scpl_job_footprint(params: Params | None, job: Job) -> int:
+    return int(load().scpl_job_footprint(ctypes.byref(params) if params is not None else None,
+                                         ctypes.byref(job)))
+
+
+def scpl_job_footprint_per_buffer(job: Job) -> int:
+    return int(load().scpl_job_footprint_per_buffer(ctypes.byref(job)))
+
+
+def scpl_carve_batch(h, jobs: list[Job]) -> list[tuple[int, int]]:
+    """Carve every job in one batched run; returns (status, n_buffers) per job
+    and raises if any job failed (after all have completed)."""
+    arr = (Job * len(jobs))(*jobs)
+    st = load().scpl_carve_batch(h, arr, len(jobs))
+    res = [(arr[i].status, arr[i].n_buffers) for i in range(len(jobs))]
+    _check(h, st)
+    return res
+
+
+class Server:
+    """Continuous batching of retarget jobs (scpl_server_*).  Tensors and
+    arrays of a submitted job are kept referenced here until it completes."""
+
+    def __init__(self, params: Params | None = None, hbm_budget: int = 0, stream=None):
+        self.lib = load()
+        self.s = ctypes.c_void_p()
+        st = self.lib.scpl_server_create(ctypes.byref(params) if params is not None else None,
+                                         ctypes.c_size_t(hbm_budget),
+                                         ctypes.c_void_p(_stream_ptr(stream)),
+                                         ctypes.byref(self.s))
+        if st != SCPL_OK:
+            raise SCPLError(st, "scpl_server_create failed")
+        self._keep: dict[int, tuple] = {}
+
+    def _err(self, st):
+        if st != SCPL_OK:
+            msg = self.lib.scpl_server_last_error(self.s) or b""
+            raise SCPLError(st, msg.decode(errors="replace"))
+
+    def submit(self, frames, target_W: int, target_H: int, k: int, out, starts=None) -> int:
+        job = make_job(frames, target_W, target_H, k, out, starts)
+        t = ctypes.c_longlong()
+        self._err(self.lib.scpl_server_submit(self.s, ctypes.byref(job), ctypes.byref(t)))
+        self._keep[t.value] = (frames, out, starts, job)
+        return t.value
+
+    def progress(self, wait: bool = False) -> tuple[int, int]:
+        a, q = ctypes.c_int(), ctypes.c_int()
+        self._err(self.lib.scpl_server_progress(self.s, int(wait), ctypes.byref(a),
+                                                ctypes.byref(q)))
+        return a.value, q.value
+
+    def poll(self, max_n: int = 1024) -> list[tuple[int, int]]:
+        tk = (ctypes.c_longlong * max_n)()
+        ss = (ctypes.c_int * max_n)()
+        n = self.lib.scpl_server_poll(self.s, tk, ss, max_n)
+        done = [(int(tk[i]), int(ss[i])) for i in range(n)]
+        for t, _ in done:
+            self._keep.pop(t, None)
+        return done
+
+    def drain(self):
+        self._err(self.lib.scpl_server_drain(self.s))
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        self._err(self.lib.scpl_server_get_stats(self.s, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.s:
+            self.lib.scpl_server_destroy(self.s)
+            self.s = ctypes.c_void_p()
+            self._keep.clear()
 
     def __del__(self):
         try:

@@ -61,3 +61,22 @@ def test_missing_library_fails_loudly(tmp_path):
     from paper_1903_03180_gb300 import scpl
     with pytest.raises(OSError):
         scpl.load(str(tmp_path / "libscpl.so"))
+
+
+def test_job_footprint_host_only(lib):
+    """Admission's footprint is host arithmetic (no GPU): the luma and motion
+    maps plus the frame-minor luma copy at least, the host copies on top for a
+    host job, and 0 for an invalid job."""
+    from paper_1903_03180_gb300 import scpl
+    j = scpl.Job()
+    j.frames, j.out = 1, 1   # never dereferenced
+    j.T, j.H, j.W, j.target_W, j.target_H, j.k = 32, 1080, 1920, 1440, 1080, 32
+    fp = scpl.scpl_job_footprint(None, j)
+    assert fp >= 3 * 32 * 1080 * 1920
+    j.on_host = 1
+    assert scpl.scpl_job_footprint(None, j) == fp + 32 * 1080 * (1920 + 1440) * 3
+    assert scpl.scpl_job_footprint_per_buffer(j) > 1080 * 1920 * 16
+    j.target_H = 823   # both dimensions: a second pass on the transposed clip
+    assert scpl.scpl_job_footprint(None, j) > fp
+    j.target_W = 1921
+    assert scpl.scpl_job_footprint(None, j) == 0

@@ -370,3 +370,35 @@ def test_new_buffer_keeps_its_first_frames_maximum(orc):
     e = np.zeros((5, 3, 4), np.int32)
     e[3], e[4] = 2550, 2100
     assert np.array_equal(orc.scan(e, alpha=0.2), [0, 3, 5])
+
+
+# ------------------------------------------------ C12: horizontal seams (Sec. 2)
+def test_carve_job_height_is_classic_horizontal_seam_carving(orc):
+    """k = 1, one frame, gradient energy: the job's height pass removes the
+    same pixels as a horizontal seam carver written column by column."""
+    from paper_1903_03180_gb300 import synth
+    f = synth.clip(1, 18, 26, seed=31)
+    out, starts = orc.carve_job(f, 26, 13, 1, wm=0, use_buffer=False)
+    ref = tb.classic_horizontal_seam_carve(f[0], 5, lambda im: tb.sobel_scipy(orc.luma(im)))
+    assert out.shape == (1, 13, 26, 3)
+    assert np.array_equal(out[0], ref)
+    assert list(starts) == [0, 1]
+
+
+def test_carve_job_both_is_width_then_height(orc):
+    """Both dimensions: classic vertical seams first, then horizontal ones."""
+    from paper_1903_03180_gb300 import synth
+    f = synth.clip(1, 16, 22, seed=32)
+    efn = lambda im: tb.sobel_scipy(orc.luma(im))
+    out, _ = orc.carve_job(f, 17, 12, 1, wm=0, use_buffer=False)
+    mid, _ = tb.classic_seam_carve(f[0], 5, efn)
+    ref = tb.classic_horizontal_seam_carve(mid, 4, efn)
+    assert np.array_equal(out[0], ref)
+
+
+def test_carve_job_width_only_is_carve(orc):
+    from paper_1903_03180_gb300 import synth
+    f = synth.clip(5, 20, 40, seed=33)
+    out, starts = orc.carve_job(f, 30, 20, 4, t_max=3)
+    ref, ref_starts, _ = orc.carve(f, 30, 4, t_max=3)
+    assert np.array_equal(out, ref) and np.array_equal(starts, ref_starts)

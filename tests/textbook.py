@@ -87,6 +87,37 @@ def classic_seam_carve(frame: np.ndarray, n_remove: int, energy_fn):
     return img, np.array(seams, np.int64).reshape(n_remove, H)
 
 
+def classic_horizontal_seam_carve(frame: np.ndarray, n_remove: int, energy_fn):
+    """Horizontal seams written in their own orientation: the cumulative energy
+    runs left to right over columns, M[i,j] = E[i,j] + min(M[i-1..i+1, j-1]),
+    ties to the lowest row.  A seam has one pixel per column, and removing it
+    moves the pixels below it up by one.  Returns the [H-n_remove, W, 3] frame."""
+    img = frame.copy()
+    for _ in range(n_remove):
+        E = energy_fn(img).astype(np.int64)
+        H, W = E.shape
+        M = E.copy()
+        back = np.zeros((H, W), np.int64)
+        inf = np.iinfo(np.int64).max // 4
+        for j in range(1, W):
+            prev = M[:, j - 1]
+            up = np.concatenate([[inf], prev[:-1]])
+            down = np.concatenate([prev[1:], [inf]])
+            stack = np.stack([up, prev, down])
+            idx = np.argmin(stack, axis=0)
+            M[:, j] += stack[idx, np.arange(H)]
+            back[:, j] = np.arange(H) + idx - 1
+        path = np.empty(W, np.int64)
+        path[-1] = int(np.argmin(M[:, -1]))
+        for j in range(W - 1, 0, -1):
+            path[j - 1] = back[path[j], j]
+        out = np.empty((H - 1, W, 3), img.dtype)
+        for j in range(W):
+            out[:, j] = np.delete(img[:, j], path[j], axis=0)
+        img = out
+    return img
+
+
 def all_seams(H: int, W: int):
     """Every vertical 8-connected seam as a tuple of columns (row 0 .. H-1)."""
     for c0 in range(W):
