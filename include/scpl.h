@@ -226,7 +226,9 @@ typedef struct {
 } scpl_job;
 
 /* Carve every job; returns when all have completed (host-synchronous).  The
- * work starts after everything queued before on the handle's stream.
+ * work starts after everything queued before on the handle's stream.  The
+ * handle keeps the engine and its device memory pool between calls (freed by
+ * scpl_destroy).
  * Returns SCPL_OK if every job succeeded, else the first failing job's status
  * (each job's own result is in jobs[i].status; a job with bad arguments
  * fails alone with SCPL_EINVAL). */
@@ -267,6 +269,10 @@ typedef struct {
     long long kernel_launches;   /* kernels of this library, graph nodes included */
     size_t reserved_bytes, peak_reserved_bytes, budget_bytes;
 } scpl_server_stats;
+
+/* Counters of the handle's batch engine (zeros before the first
+ * scpl_carve_batch): scan waves, groups, graph chunks, kernel launches. */
+scpl_status scpl_batch_stats(scpl_handle h, scpl_server_stats *out);
 
 scpl_status scpl_server_create(const scpl_params *p, size_t hbm_budget, void *stream,
                                scpl_server *out);

@@ -22,7 +22,7 @@
 //          their target width become no-ops in later launches.
 //   gather one launch per group for the colour frames of all its passes, then
 //          transposes for horizontal passes and the copy back for host jobs.
-// Each group runs on its own stream, so groups of different sizes, and jobs
+// Each group runs on one of 16 streams, so groups of different sizes, and jobs
 // admitted while others are carving, overlap on the GPU.
 //
 // Memory: every allocation is stream-ordered from the engine's own pool.  A
@@ -48,7 +48,7 @@ using namespace scpl;
 
 namespace {
 
-constexpr int N_STREAMS = 8;
+constexpr int N_STREAMS = 16;
 constexpr int MAX_CHUNK = 16;
 constexpr unsigned long long SPIN_NS = 2000000000ull;   // bounded device-wide waits
 
@@ -420,7 +420,13 @@ scpl_status admit(Srv *s, bool *any) {
 scpl_status launch_wave(Srv *s) {
     if (s->pending_scan.empty()) return SCPL_OK;
     std::unique_ptr<Wave> W(new Wave());
-    const int cap = s->scan_cap;
+    // a cooperative launch starts only when all its CTAs fit at once: while
+    // groups are carving, a wave takes half the GPU so that it can start
+    // beside them instead of waiting for the whole GPU to drain
+    bool carving = false;
+    for (auto &g : s->groups)
+        if (g && g->phase == 2) carving = true;
+    const int cap = carving ? std::max(1, s->scan_cap / 2) : s->scan_cap;
     std::vector<int> take, rest;
     for (int pid : s->pending_scan) ((int)take.size() < cap ? take : rest).push_back(pid);
     s->pending_scan = rest;
@@ -913,6 +919,8 @@ scpl_status reap_jobs(Srv *s, bool *any) {
     return SCPL_OK;
 }
 
+void compact(Srv *s);
+
 // One scheduling round.  *any = something was launched or completed.
 scpl_status round(Srv *s, bool *any) {
     scpl_status st;
@@ -985,6 +993,7 @@ scpl_status round(Srv *s, bool *any) {
         if ((st = launch_wave(s)) != SCPL_OK) return st;
         *any = true;
     }
+    compact(s);
     return SCPL_OK;
 }
 
@@ -1009,6 +1018,26 @@ scpl_status wait_some(Srv *s) {
 }
 
 int count_queued(Srv *s) { return (int)s->queue.size(); }
+
+// With nothing queued, active or in flight, the records of finished jobs are
+// dropped so that a long-running server does not grow (tickets stay unique).
+void compact(Srv *s) {
+    if (s->active_jobs != 0 || !s->queue.empty() || !s->pending_scan.empty()) return;
+    for (auto &G : s->groups)
+        if (G->phase != 3) return;
+    for (auto &W : s->waves)
+        if (!W->done) return;
+    for (auto &G : s->groups)
+        if (G->ev) cudaEventDestroy(G->ev);
+    for (auto &W : s->waves)
+        if (W->ev) cudaEventDestroy(W->ev);
+    for (auto &P : s->passes)
+        if (P.ready) cudaEventDestroy(P.ready);
+    s->groups.clear();
+    s->waves.clear();
+    s->passes.clear();
+    s->jobs.clear();
+}
 
 scpl_status create(const scpl_params *p, size_t budget, void *stream, Srv **out) {
     scpl_params def;
@@ -1152,28 +1181,51 @@ scpl_status drain(Srv *s) {
 
 }  // namespace
 
+extern "C" scpl_status scpl_server_get_stats(scpl_server s, scpl_server_stats *out);
+
 namespace scpl {
 
-// scpl_carve_batch: one engine for the call, every job submitted at once.
-scpl_status engine_run_batch(const scpl_params &p, cudaStream_t stream, scpl_job *jobs,
-                             int n_jobs, std::string &err) {
-    Srv *s = nullptr;
-    scpl_status st = create(&p, 0, stream, &s);
-    if (st != SCPL_OK) {
-        err = "could not create the batch engine";
-        return st;
+// scpl_carve_batch: the handle's engine (created on first use and kept, with
+// its memory pool, until the handle is destroyed), every job submitted at once.
+scpl_status engine_run_batch(scpl_server_s **eng, const scpl_params &p, cudaStream_t stream,
+                             scpl_job *jobs, int n_jobs, std::string &err) {
+    scpl_status st = SCPL_OK;
+    if (!*eng) {
+        st = create(&p, 0, stream, eng);
+        if (st != SCPL_OK) {
+            err = "could not create the batch engine";
+            return st;
+        }
+    }
+    Srv *s = *eng;
+    s->user = stream;
+    if (s->broken) {
+        err = "the batch engine hit a CUDA error earlier: " + s->err;
+        return SCPL_ECUDA;
     }
     for (int i = 0; i < n_jobs && st == SCPL_OK; ++i) st = submit(s, &jobs[i], &jobs[i], nullptr);
     if (st == SCPL_OK) st = drain(s);
-    if (st != SCPL_OK) err = s->err;
-    destroy(s);
-    if (st != SCPL_OK) return st;
+    s->completed.clear();
+    if (st != SCPL_OK) {
+        err = s->err;
+        return st;
+    }
     for (int i = 0; i < n_jobs; ++i)
         if (jobs[i].status != SCPL_OK) {
             err = "job " + std::to_string(i) + " failed";
             return (scpl_status)jobs[i].status;
         }
     return SCPL_OK;
+}
+
+void engine_destroy(scpl_server_s *eng) { destroy(eng); }
+
+scpl_status engine_stats(scpl_server_s *eng, scpl_server_stats *out) {
+    if (!eng) {
+        std::memset(out, 0, sizeof *out);
+        return SCPL_OK;
+    }
+    return scpl_server_get_stats(eng, out);
 }
 
 }  // namespace scpl

@@ -113,6 +113,7 @@ struct scpl_ctx {
     bool dpc_ok = false;
     HostBuf h_small;   // starts + n_buffers + states readback
     Profiler prof;
+    scpl_server_s *engine = nullptr;   // scpl_carve_batch's engine (created on first use)
     // summary of the last scpl_carve call
     int last_nb = 0, last_iter_max = 0;
     long long last_iter_total = 0;
@@ -321,6 +322,7 @@ void scpl_destroy(scpl_handle h) {
                       &h->count, &h->starts, &h->nbuf, &h->errw, &h->cws, &h->bof,
                       &h->in_frames, &h->out_frames, &h->seams_dev, &h->Yfm};
     for (DevBuf *b : bufs) b->release();
+    engine_destroy(h->engine);
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
     h->h_small.release();
     delete h;
@@ -565,9 +567,14 @@ scpl_status scpl_carve_batch(scpl_handle h, scpl_job *jobs, int n_jobs) {
     if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(h, SCPL_EINVAL, "bad job list");
     if (n_jobs == 0) return SCPL_OK;
     std::string err;
-    scpl_status s = engine_run_batch(h->p, h->stream, jobs, n_jobs, err);
+    scpl_status s = engine_run_batch(&h->engine, h->p, h->stream, jobs, n_jobs, err);
     if (s != SCPL_OK) return fail(h, s, "%s", err.c_str());
     return SCPL_OK;
+}
+
+scpl_status scpl_batch_stats(scpl_handle h, scpl_server_stats *out) {
+    if (!h || !out) return SCPL_EINVAL;
+    return engine_stats(h->engine, out);
 }
 
 scpl_status scpl_set_profiling(scpl_handle h, int on) {

@@ -212,9 +212,11 @@ size_t carve_ws_assign(CarveWs &ws, int nb, int klog_stride, bool dpc, char *bas
 #include "scpl.h"
 
 namespace scpl {
-// scpl_carve_batch's engine (engine.cu).
-scpl_status engine_run_batch(const scpl_params &p, cudaStream_t stream, scpl_job *jobs,
-                             int n_jobs, std::string &err);
+// scpl_carve_batch's engine (engine.cu), owned by a handle.
+scpl_status engine_run_batch(scpl_server_s **eng, const scpl_params &p, cudaStream_t stream,
+                             scpl_job *jobs, int n_jobs, std::string &err);
+void engine_destroy(scpl_server_s *eng);
+scpl_status engine_stats(scpl_server_s *eng, scpl_server_stats *out);
 // Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
 // current device.  It never lowers the limit, so a CUDA graph captured earlier
 // with a larger launch of the same kernel stays launchable.

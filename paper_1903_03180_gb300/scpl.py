@@ -79,6 +79,7 @@ SIGNATURES = {
     "scpl_carve_batch": (_I, [_P, ctypes.POINTER(Job), _I]),
     "scpl_job_footprint": (ctypes.c_size_t, [ctypes.POINTER(Params), ctypes.POINTER(Job)]),
     "scpl_job_footprint_per_buffer": (ctypes.c_size_t, [ctypes.POINTER(Job)]),
+    "scpl_batch_stats": (_I, [_P, ctypes.POINTER(ServerStats)]),
     "scpl_server_create": (_I, [ctypes.POINTER(Params), ctypes.c_size_t, _P, ctypes.POINTER(_P)]),
     "scpl_server_submit": (_I, [_P, ctypes.POINTER(Job), ctypes.POINTER(_LL)]),
     "scpl_server_progress": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
@@ -372,6 +373,12 @@ def scpl_carve_batch(h, jobs: list[Job]) -> list[tuple[int, int]]:
     res = [(arr[i].status, arr[i].n_buffers) for i in range(len(jobs))]
     _check(h, st)
     return res
+
+
+def scpl_batch_stats(h) -> dict:
+    st = ServerStats()
+    _check(h, load().scpl_batch_stats(h, ctypes.byref(st)))
+    return {f: getattr(st, f) for f, _ in ServerStats._fields_}
 
 
 class Server:

@@ -159,3 +159,35 @@ def workload_clip_640x360(seed: int = SEED_BASE ^ 2, T: int = 64) -> np.ndarray:
 def workload_clip_1080p(seed: int = SEED_BASE ^ 3, T: int = 300) -> np.ndarray:
     """300-frame 1920x1080 clip with hard scene cuts every 60-120 frames."""
     return clip(T, 1080, 1920, seed, cuts=(60, 120))
+
+
+BATCH_SIZES = ((240, 426), (360, 640), (720, 1280), (1080, 1920))
+BATCH_ASPECTS = ("1:1", "4:3", "21:9")
+
+
+def batch_spec(n_clips: int = 256, T: int = 32, seed: int = SEED_BASE ^ 4):
+    """The batched workload's job list, without frames: for clip c a dict with
+    its size (H, W drawn uniformly from BATCH_SIZES), target aspect (uniform
+    over 1:1, 4:3, 21:9), target size and k, and the seed of its frames.
+    1:1 and 4:3 keep the height and cut the width to round(H * aspect); 21:9
+    keeps the width and cuts the height to round(W * 9 / 21) (horizontal
+    seams).  k = 16 up to 640 columns wide, 32 above."""
+    r = _rng(seed)
+    out = []
+    for c in range(n_clips):
+        H, W = BATCH_SIZES[int(r.integers(0, len(BATCH_SIZES)))]
+        aspect = BATCH_ASPECTS[int(r.integers(0, len(BATCH_ASPECTS)))]
+        if aspect == "21:9":
+            tw, th = W, int(round(W * 9 / 21))
+        else:
+            num, den = (1, 1) if aspect == "1:1" else (4, 3)
+            tw, th = int(round(H * num / den)), H
+        out.append({"clip": c, "T": T, "H": H, "W": W, "aspect": aspect, "target_W": tw,
+                    "target_H": th, "k": 16 if W <= 640 else 32,
+                    "seed": (seed * 1000003 + c) & 0xFFFFFFFF})
+    return out
+
+
+def batch_clip(spec: dict) -> np.ndarray:
+    """Frames of one clip of the batched workload (one scene, no cuts)."""
+    return clip(spec["T"], spec["H"], spec["W"], spec["seed"])

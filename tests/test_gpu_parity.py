@@ -237,3 +237,26 @@ def test_carve_1080p_full_size_sampled(orc, lib, synth):
     ref_out, ref_seams, _ = orc.carve_buffer(f[t0:t1], D, target, k)
     assert np.array_equal(seams[b], ref_seams)
     assert np.array_equal(out[t0:t1], ref_out)
+
+
+# ------------------------------------------------- 3840x2160 (serving sizes)
+def test_seams_3840x2160(orc, lib):
+    """The widest serving size: a 15-CTA cluster per buffer."""
+    r = np.random.default_rng(2160)
+    E = r.integers(0, 2551, (2160, 3840)).astype(np.int32)
+    CE, L, d = orc.dp(E)
+    ref_cols = orc.select(CE[-1], L[-1], 64)
+    h = lib.scpl_create()
+    cols = torch.full((64, 2160), -1, dtype=torch.int16, device="cuda")
+    ke = lib.scpl_seams(h, torch.from_numpy(E).cuda(), 64, cols)
+    lib.scpl_destroy(h)
+    assert ke == len(ref_cols)
+    got = cols.cpu().numpy()
+    for s, c in enumerate(ref_cols):
+        assert np.array_equal(got[s], orc.backtrack(d, int(c))), f"seam {s}"
+
+
+def test_carve_3840x2160(orc, lib, synth):
+    f = synth.clip(3, 2160, 3840, seed=61)
+    ref, got = _carve_both(orc, lib, f, 3840 - 96, 64)
+    _assert_same(ref, got)
