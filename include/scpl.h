@@ -97,6 +97,17 @@ scpl_status scpl_energy(scpl_handle h, const uint8_t *frames, int T, int H, int 
 scpl_status scpl_scan(scpl_handle h, const uint8_t *frames, int T, int H, int W,
                       int32_t *buffer_starts, int *n_buffers);
 
+/* scpl_scan plus the integers each decision used (diagnostic): for every
+ * frame t, A[t] = sum over pixels of floor(sqrt(65536 (n S2 - S1^2))) with
+ * frame t added to the open buffer (Eq. 7-8 scaled by 256 n), and emax[t] =
+ * the maximum energy of frame t (Eq. 9's maxval is the running maximum of
+ * these, or the theoretical one).
+ *   A     [host] int64 [T]
+ *   emax  [host] int32 [T]
+ * Synchronises the stream. */
+scpl_status scpl_scan_stats(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                            int32_t *buffer_starts, int *n_buffers, int64_t *A, int32_t *emax);
+
 /* One SCPL iteration on an energy map (Sec. 3.1, Eq. 4-6): the cumulative
  * energy DP carrying each pixel's row-0 parent (lowest column on ties), the
  * least-(CE, column) child of every parent, the k_eff = min(k, #parents)

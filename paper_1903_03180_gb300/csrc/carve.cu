@@ -68,6 +68,9 @@ __device__ __forceinline__ int sobel_l1(int a00, int a01, int a02, int a10, int 
 
 // ---------------------------------------------------------------------------
 // k_energy_init: grid (ceil(W0/EN_CW), ceil(H/EN_RB), nb), EN_CW threads.
+// Writes the identity origin map, SDo = wm * sum_t D_t, the frame-minor luma
+// copy and E = sum_t e_t.  The scan hands over E for most buffers (st.e0 >= 0);
+// for the others the gradient of every frame is summed here.
 __global__ void __launch_bounds__(EN_CW) k_energy_init(CarveWs ws) {
     const int b = blockIdx.z;
     const BufState st = ws.st[b];
@@ -76,6 +79,7 @@ __global__ void __launch_bounds__(EN_CW) k_energy_init(CarveWs ws) {
     const int tid = threadIdx.x, p = p0 + tid;
     if (p >= W0) return;
     const long pitch = ws.pitch, plane = ws.plane;
+    const bool have_e = st.e0 >= 0;
     uint16_t *O = ws.O + (long)b * 2 * plane;
     int32_t *SDo = ws.SD + (long)b * plane;
     int32_t *E = ws.E + (long)b * 2 * plane;
@@ -91,7 +95,7 @@ __global__ void __launch_bounds__(EN_CW) k_energy_init(CarveWs ws) {
                 sd += ws.D[((long)t * H + i) * ws.ypitch + p];
             sd *= ws.wm;
             SDo[(long)i * pitch + p] = sd;
-            eacc[r] = sd;
+            eacc[r] = have_e ? __ldg(ws.E0 + st.e0 + (long)i * W0 + p) : sd;
         }
     }
     const int pl = max(p - 1, 0), pr = min(p + 1, W0 - 1);
@@ -110,13 +114,16 @@ __global__ void __launch_bounds__(EN_CW) k_energy_init(CarveWs ws) {
                 for (int r = 0; r < EN_RB; ++r) {
                     const int i = i0 + r;
                     if (i < H) {
-                        const uint8_t *ru = Yt + (long)clampi(i - 1, 0, H - 1) * ws.ypitch;
                         const uint8_t *rc = Yt + (long)i * ws.ypitch;
-                        const uint8_t *rd = Yt + (long)clampi(i + 1, 0, H - 1) * ws.ypitch;
                         const int yc = __ldg(rc + p);
-                        eacc[r] += ws.wg * sobel_l1(__ldg(ru + pl), __ldg(ru + p), __ldg(ru + pr),
-                                                    __ldg(rc + pl), __ldg(rc + pr), __ldg(rd + pl),
-                                                    __ldg(rd + p), __ldg(rd + pr));
+                        if (!have_e) {
+                            const uint8_t *ru = Yt + (long)clampi(i - 1, 0, H - 1) * ws.ypitch;
+                            const uint8_t *rd = Yt + (long)clampi(i + 1, 0, H - 1) * ws.ypitch;
+                            eacc[r] += ws.wg * sobel_l1(__ldg(ru + pl), __ldg(ru + p),
+                                                        __ldg(ru + pr), __ldg(rc + pl),
+                                                        __ldg(rc + pr), __ldg(rd + pl),
+                                                        __ldg(rd + p), __ldg(rd + pr));
+                        }
                         fq[r][tt >> 2] |= (uint32_t)yc << (8 * (tt & 3));
                     }
                 }

@@ -96,11 +96,15 @@ struct PassDims {
 // Bytes of one pass's scan state (freed with its wave) and of one carving
 // buffer (item) of the pass.
 size_t scan_state_bytes(const PassDims &d) {
-    const size_t hw = (size_t)d.H * d.W;
+    const size_t spx = (size_t)scan_state_px(d.H, d.W);
     const size_t G = (size_t)scan_tiles(d.H, d.W);
-    return a256(2 * hw * 2) + 2 * a256(hw * 4) + a256((size_t)d.T * G * 12) +
+    return a256(2 * spx * 2) + 2 * a256(spx * 4) + a256((size_t)d.T * G * 12) +
            a256((size_t)(d.T + 1) * 4) + a256((size_t)d.T * 4 + 8);
 }
+// Buffers of a pass whose summed energy the scan keeps (more are summed by
+// k_energy_init from the luma and motion maps).
+int e0_planes(const PassDims &d) { return std::min(d.T, 4); }
+size_t e0_bytes(const PassDims &d) { return a256((size_t)e0_planes(d) * d.H * d.W * 4); }
 size_t item_bytes(const PassDims &d, int kcap) {
     CarveWs ws{};
     ws.H = d.H;
@@ -113,7 +117,8 @@ size_t pass_bytes(const PassDims &d, int k) {
     const size_t ypool = 2 * (size_t)d.T * d.H * yp;
     const size_t yfm = (size_t)d.H * d.W * rup(d.T, 16);
     const int kcap = std::max(1, std::min(k, d.W - d.target));
-    return ypool + scan_state_bytes(d) + item_bytes(d, kcap) + yfm + (size_t)d.T * 32;
+    return ypool + e0_bytes(d) + scan_state_bytes(d) + item_bytes(d, kcap) + yfm +
+           (size_t)d.T * 32;
 }
 
 // The passes of a job: width first, then height on the transposed frames.
@@ -202,6 +207,7 @@ struct Pass {
     cudaEvent_t ready = nullptr;   // src complete (null: ordered on the main stream)
     int group = -1;
     int frame_off = 0;
+    long long e0_off = 0;       // element offset of its summed-energy planes
     int nb = 0, item0 = 0;
     std::vector<int> starts;
     size_t group_share = 0;     // bytes of its group attributed to this pass
@@ -467,6 +473,13 @@ scpl_status launch_wave(Srv *s) {
     for (int g : W->groups) {
         Group &G = *s->groups[g];
         G.ypool_bytes = 2 * (size_t)G.T_total * G.H * G.ypitch;
+        size_t e0 = 0;   // summed-energy planes follow the luma and motion maps
+        for (int pid : G.passes) {
+            Pass &P = s->passes[pid];
+            P.e0_off = (long long)(e0 / 4);
+            e0 += e0_bytes(P.d);
+        }
+        G.ypool_bytes += e0;
         void *p = nullptr;
         SRV_CUDA(s, dalloc(s, &p, G.ypool_bytes, m));
         G.ypool = static_cast<uint8_t *>(p);
@@ -541,12 +554,13 @@ scpl_status launch_wave(Srv *s) {
         a.ypitch = Gr.ypitch;
         a.Y = Gr.ypool + (size_t)P.frame_off * P.d.H * Gr.ypitch;
         a.D = Gr.ypool + ((size_t)Gr.T_total + P.frame_off) * P.d.H * Gr.ypitch;
+        const size_t spx = (size_t)scan_state_px(P.d.H, P.d.W);
         a.ering = reinterpret_cast<uint16_t *>(q);
-        q += a256(2 * hw * 2);
+        q += a256(2 * spx * 2);
         a.S1 = reinterpret_cast<uint32_t *>(q);
-        q += a256(hw * 4);
+        q += a256(spx * 4);
         a.S2 = reinterpret_cast<uint32_t *>(q);
-        q += a256(hw * 4);
+        q += a256(spx * 4);
         a.partA = reinterpret_cast<long long *>(q);
         a.partM = reinterpret_cast<int *>(q + (size_t)P.d.T * G[i] * 8);
         q += a256((size_t)P.d.T * scan_tiles(P.d.H, P.d.W) * 12);
@@ -564,6 +578,12 @@ scpl_status launch_wave(Srv *s) {
         a.spin_limit_ns = SPIN_NS;
         a.cta0 = cta;
         a.G = G[i];
+        a.E0 = reinterpret_cast<int32_t *>(Gr.ypool + 2 * (size_t)Gr.T_total * Gr.H * Gr.ypitch) +
+               P.e0_off;
+        a.nbcap = e0_planes(P.d);
+        a.e0_plane = (long)hw;
+        a.A_out = nullptr;
+        a.M_out = nullptr;
         tab[i] = a;
         for (int c = 0; c < G[i]; ++c) bc[cta + c] = i;
         cta += G[i];
@@ -731,6 +751,7 @@ scpl_status setup_group(Srv *s, int gid) {
     ws.wg = s->p.wg;
     ws.wm = s->p.wm;
     ws.Yfm = reinterpret_cast<uint8_t *>(G.slab + yfm_off);
+    ws.E0 = reinterpret_cast<const int32_t *>(G.ypool + 2 * (size_t)G.T_total * G.H * G.ypitch);
     // share of the group's memory per pass (by frames)
     for (int pid : ok) {
         Pass &P = s->passes[pid];
@@ -751,7 +772,10 @@ scpl_status setup_group(Srv *s, int gid) {
         for (int b = 0; b < P.nb; ++b) {
             const int t0 = P.starts[b], nt = P.starts[b + 1] - t0;
             const int tp = (int)rup(nt, 16);
-            hst[P.item0 + b] = BufState{P.frame_off + t0, nt, G.W, 0, 0, 0, tgt, 0, tp, P.k, yfm};
+            const long long e0 =
+                b < e0_planes(P.d) ? P.e0_off + (long long)b * G.H * G.W : -1;
+            hst[P.item0 + b] =
+                BufState{P.frame_off + t0, nt, G.W, 0, 0, 0, tgt, 0, tp, P.k, yfm, e0};
             yfm += (long long)G.H * G.W * tp;
             for (int t = t0; t < t0 + nt; ++t) {
                 GatherFrame gf;

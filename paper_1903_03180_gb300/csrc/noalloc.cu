@@ -78,7 +78,7 @@ __global__ void k_noalloc_reset(BufState *st, int *klog, int W, int target) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
         BufState s;
         s.t0 = 0; s.nt = 1; s.W = W; s.k_eff = 0; s.removed = 0; s.slot = 0;
-        s.target = target; s.iters = 0; s.tp = 0; s.k = 0; s.yfm = 0;
+        s.target = target; s.iters = 0; s.tp = 0; s.k = 0; s.yfm = 0; s.e0 = -1;
         *st = s;
         *klog = 0;
     }
@@ -106,6 +106,7 @@ extern "C" scpl_status scpl_seams_noalloc(const int32_t *energy, int H, int W, i
     ws.dbuf = (long)((H + 3) / 4) * ws.dstride;
     ws.dirty_count = nullptr;
     ws.Yfm = nullptr;
+    ws.E0 = nullptr;
     ws.err = nullptr;
     ws.J = nullptr;
     ws.Dfirst = nullptr;

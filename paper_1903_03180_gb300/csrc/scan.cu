@@ -2,16 +2,20 @@
 // (Sec. 3.2, Eq. 7-9).
 //
 // k_scan is one persistent cooperative launch over the whole clip.  Each CTA
-// owns a fixed set of 8x64 pixel tiles.  For every frame t it
-//   (1) computes luma, the Sobel gradient, the frame difference and the energy
-//       e_t of its tiles (independent of any buffer decision) and writes Y_t,
-//       D_t and e_t;
+// owns a fixed set of 8x128 pixel tiles for the whole clip, and each thread a
+// quad of 4 pixels in every tile.  For every frame t it
+//   (1) computes luma, the Sobel gradient (4 pixels at once in u16x2 lanes),
+//       the frame difference and the energy e_t of its tiles (independent of
+//       any buffer decision) and writes Y_t and D_t; e_t stays in registers
+//       when the CTA owns at most MAXT tiles;
 //   (2) waits until every CTA has published its partial sums for frame t-1,
 //       reduces them and takes the buffer decision for t-1 (every CTA takes
 //       the same decision from the same integers);
 //   (3) folds e_{t-1} into its running sums S1, S2 as that decision says, and
 //       publishes its partial A_t = sum floor(sqrt(65536 (n S2 - S1^2))) with
-//       frame t added, plus the partial maximum of e_t.
+//       frame t added, plus the partial maximum of e_t.  When the decision
+//       closes a buffer, S1 (its summed energy, the uniform energy map of
+//       Sec. 3.2) is written out for the carving stage.
 // Step (1) of frame t overlaps the device-wide reduction of frame t-1.
 //
 // Several clips can share one launch: a table gives each clip its own range
@@ -22,7 +26,8 @@ namespace scpl {
 
 namespace {
 
-constexpr int TR = 8, TC = 64, SCAN_THREADS = 256;
+constexpr int TR = 8, TC = 128, SCAN_THREADS = 256;
+constexpr int LUMW = TC + 8;   // luma tile row: TC + 2 columns, padded to whole words
 enum { DEC_JOIN = 0, DEC_FLUSH = 1, DEC_CLOSE = 2 };
 
 __device__ __forceinline__ int luma_px(const uint8_t *p) {
@@ -30,15 +35,6 @@ __device__ __forceinline__ int luma_px(const uint8_t *p) {
 }
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
-
-// floor(sqrt(x)) for x < 2^62: a single-precision estimate corrected exactly
-// with integer arithmetic.
-__device__ __forceinline__ unsigned long long isqrt_u64(unsigned long long x) {
-    unsigned long long s = (unsigned long long)__fsqrt_rn(__ull2float_rn(x));
-    while (s * s > x) --s;
-    while ((s + 1) * (s + 1) <= x) ++s;
-    return s;
-}
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
     unsigned v;
@@ -165,7 +161,14 @@ __device__ bool wait_and_decide(const ScanArgs &a, int t, int G, DecState &s, in
                 A += __shfl_xor_sync(0xffffffffu, A, o);
                 m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
             }
-            if (lane == 0) *dec_out = decide(s, A, m, t, a, blockIdx.x == (unsigned)a.cta0);
+            if (lane == 0) {
+                const bool first = blockIdx.x == (unsigned)a.cta0;
+                if (first && a.A_out) {
+                    a.A_out[t] = A;
+                    a.M_out[t] = m;
+                }
+                *dec_out = decide(s, A, m, t, a, first);
+            }
         }
         if (lane == 0) s_ok = ok;
     }
@@ -173,14 +176,87 @@ __device__ bool wait_and_decide(const ScanArgs &a, int t, int G, DecState &s, in
     return s_ok != 0;
 }
 
+// floor(sqrt(x)) for x < 2^53 without loops: a single-precision estimate
+// (off by a few units at most), one Newton step on the exact integer residual,
+// then a final correction by one.  Every float operation is correctly rounded.
+__device__ __forceinline__ uint32_t isqrt53(unsigned long long x) {
+    const float sf = __fsqrt_rn(__ull2float_rn(x));
+    const uint32_t r0 = __float2uint_rz(sf);
+    const long long R = (long long)x - (long long)r0 * (long long)r0;
+    const float d = __fmul_rn(__ll2float_rn(R), __fdiv_rn(0.5f, __uint2float_rn(r0 > 0 ? r0 : 1)));
+    unsigned long long r = (unsigned long long)((long long)r0 + __float2ll_rd(d));
+    r -= (r * r > x) ? 1ull : 0ull;
+    r += ((r + 1) * (r + 1) <= x) ? 1ull : 0ull;
+    return (uint32_t)r;
+}
+
+// Packed u16x2 helpers for the 4 pixels of a thread: lane 0 = pixels 0 and 2,
+// lane 1 = pixels 1 and 3 of a luma quad.
+__device__ __forceinline__ uint32_t even16(uint32_t q) { return __byte_perm(q, 0, 0x4240); }
+__device__ __forceinline__ uint32_t odd16(uint32_t q) { return __byte_perm(q, 0, 0x4341); }
+
+// Sobel |Gx| + |Gy| of 4 consecutive pixels from three luma rows.  Each row is
+// two aligned words holding the columns c-1 .. c+6 (bytes 0..7); the pixels
+// are columns c .. c+3.  Returns (G of pixels 0, 2) and (G of pixels 1, 3).
+__device__ __forceinline__ void sobel4(uint32_t u0, uint32_t u1, uint32_t m0, uint32_t m1,
+                                       uint32_t d0, uint32_t d1, uint32_t &g02, uint32_t &g13) {
+    // left, centre and right neighbours of the 4 pixels in each row
+    const uint32_t uL = u0, uC = __funnelshift_r(u0, u1, 8), uR = __funnelshift_r(u0, u1, 16);
+    const uint32_t mL = m0, mR = __funnelshift_r(m0, m1, 16);
+    const uint32_t dL = d0, dC = __funnelshift_r(d0, d1, 8), dR = __funnelshift_r(d0, d1, 16);
+    // the per-lane sums stay below 2^16, so packed adds cannot carry across lanes
+    const uint32_t lE = even16(uL) + 2 * even16(mL) + even16(dL);
+    const uint32_t rE = even16(uR) + 2 * even16(mR) + even16(dR);
+    const uint32_t tE = even16(uL) + 2 * even16(uC) + even16(uR);
+    const uint32_t bE = even16(dL) + 2 * even16(dC) + even16(dR);
+    g02 = __vabsdiffu2(rE, lE) + __vabsdiffu2(bE, tE);
+    const uint32_t lO = odd16(uL) + 2 * odd16(mL) + odd16(dL);
+    const uint32_t rO = odd16(uR) + 2 * odd16(mR) + odd16(dR);
+    const uint32_t tO = odd16(uL) + 2 * odd16(uC) + odd16(uR);
+    const uint32_t bO = odd16(dL) + 2 * odd16(dC) + odd16(dR);
+    g13 = __vabsdiffu2(rO, lO) + __vabsdiffu2(bO, tO);
+}
+
+// Per-CTA tile ownership: CTA lb of a clip owns tiles lb, lb + G, ... for the
+// whole clip.  Up to MAXT tiles the previous frame's energy and luma of its
+// pixels stay in registers; beyond that they go through global memory.
+constexpr int MAXT = 4;
+
+struct TileCtx {
+    int r0, c0;      // tile origin
+    int row, col;    // this thread's row and first column
+    int nvalid;      // valid pixels of the quad (0..4)
+};
+
+__device__ __forceinline__ TileCtx tile_ctx(const ScanArgs &a, int tile, int tiles_x, int tid) {
+    TileCtx c;
+    c.r0 = (tile / tiles_x) * TR;
+    c.c0 = (tile % tiles_x) * TC;
+    c.row = c.r0 + (tid >> 5);
+    c.col = c.c0 + 4 * (tid & 31);
+    c.nvalid = c.row < a.H ? max(0, min(4, a.W - c.col)) : 0;
+    return c;
+}
+
+// Luma of the tile and its one-pixel frame (replicated at the image border)
+// into lum[r][j] = Y(r0 - 1 + r, c0 - 1 + j).
+__device__ __forceinline__ void load_luma(const ScanArgs &a, const uint8_t *f, int r0, int c0,
+                                          uint8_t (*lum)[LUMW]) {
+    for (int q = threadIdx.x; q < (TR + 2) * (TC + 2); q += SCAN_THREADS) {
+        const int r = q / (TC + 2), c = q - r * (TC + 2);
+        const int gi = clampi(r0 + r - 1, 0, a.H - 1), gj = clampi(c0 + c - 1, 0, a.W - 1);
+        lum[r][c] = (uint8_t)luma_px(f + ((long)gi * a.W + gj) * 3);
+    }
+}
+
 // One clip per launch (tab == NULL, every CTA works on a0) or one clip per
 // range of CTAs (clip of CTA x = tab[block_clip[x]], CTAs [cta0, cta0 + G)).
-__global__ void __launch_bounds__(SCAN_THREADS)
+__global__ void __launch_bounds__(SCAN_THREADS, 4)
 k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ block_clip) {
     __shared__ ScanArgs a;
-    __shared__ uint8_t lum[TR + 2][TC + 2];
-    __shared__ long long red_a[SCAN_THREADS / 32];
-    __shared__ int red_m[SCAN_THREADS / 32];
+    __shared__ __align__(16) uint8_t lum[TR + 2][LUMW];
+    __shared__ unsigned long long red_a[SCAN_THREADS / 32];
+    __shared__ uint32_t red_m[SCAN_THREADS / 32];
     __shared__ DecState st;
     __shared__ int s_dec;
 
@@ -193,51 +269,137 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
             a.cta0 = 0;
             a.G = gridDim.x;
         }
+        st.n = 0; st.M = 0; st.start = 0; st.nb = 0;
+        s_dec = DEC_JOIN;
     }
     __syncthreads();
     const int G = a.G;
     const int lb = blockIdx.x - a.cta0;   // CTA index within the clip's range
     const int tiles_x = (a.W + TC - 1) / TC;
     const int ntiles = ((a.H + TR - 1) / TR) * tiles_x;
-    const long hw = (long)a.H * a.W;
-    if (tid == 0) {
-        st.n = 0; st.M = 0; st.start = 0; st.nb = 0;
-        s_dec = DEC_JOIN;
-    }
-    __syncthreads();
+    const int mine = lb < ntiles ? (ntiles - 1 - lb) / G + 1 : 0;
+    const bool resident = mine <= MAXT;
+    const long hw3 = (long)a.H * a.W * 3;
+    const long yplane = (long)a.H * a.ypitch;
+
+    // registers of the resident path: energy (u16x2 pairs) and luma quad of the
+    // previous and the current frame for each owned tile
+    uint32_t ep02[MAXT], ep13[MAXT], yp[MAXT], ec02[MAXT], ec13[MAXT];
+#pragma unroll
+    for (int k = 0; k < MAXT; ++k) ep02[k] = ep13[k] = yp[k] = ec02[k] = ec13[k] = 0;
+
+    // phase A of one tile: energy of frame t, luma and motion written out
+    auto phase_a = [&](int t, int tile, uint32_t &e02, uint32_t &e13, uint32_t &yprev,
+                       uint32_t &emax2) {
+        const TileCtx c = tile_ctx(a, tile, tiles_x, tid);
+        const uint8_t *f = a.rgb + (long)t * hw3;
+        load_luma(a, f, c.r0, c.c0, lum);
+        __syncthreads();
+        const int rr = tid >> 5, cc = 4 * (tid & 31);
+        const uint32_t *L0 = reinterpret_cast<const uint32_t *>(&lum[rr][cc]);
+        const uint32_t *L1 = reinterpret_cast<const uint32_t *>(&lum[rr + 1][cc]);
+        const uint32_t *L2 = reinterpret_cast<const uint32_t *>(&lum[rr + 2][cc]);
+        uint32_t g02, g13;
+        sobel4(L0[0], L0[1], L1[0], L1[1], L2[0], L2[1], g02, g13);
+        const uint32_t ycur = __funnelshift_r(L1[0], L1[1], 8);
+        uint32_t yprv = yprev;
+        if (!resident && t > 0 && c.nvalid > 0)
+            yprv = *reinterpret_cast<const uint32_t *>(a.Y + (long)(t - 1) * yplane +
+                                                       (long)c.row * a.ypitch + c.col);
+        const uint32_t dq = t > 0 ? __vabsdiffu4(ycur, yprv) : 0u;
+        e02 = (uint32_t)a.wg * g02 + (uint32_t)a.wm * even16(dq);
+        e13 = (uint32_t)a.wg * g13 + (uint32_t)a.wm * odd16(dq);
+        if (c.nvalid > 0) {
+            // invalid pixels of a ragged quad do not count towards the maximum
+            const uint32_t m02 = c.nvalid >= 3 ? e02 : (e02 & 0xFFFFu);
+            const uint32_t m13 = c.nvalid >= 4 ? e13 : (c.nvalid >= 2 ? (e13 & 0xFFFFu) : 0u);
+            emax2 = __vmaxu2(emax2, __vmaxu2(m02, m13));
+            const long yo = (long)t * yplane + (long)c.row * a.ypitch + c.col;
+            *reinterpret_cast<uint32_t *>(a.Y + yo) = ycur;
+            *reinterpret_cast<uint32_t *>(a.D + yo) = dq;
+        }
+        yprev = ycur;
+        __syncthreads();   // lum is reused by the next tile
+    };
+
+    // phase B of one tile: fold e_{t-1} into S1/S2 as the decision says, add
+    // e_t, accumulate floor(sqrt(65536 (n S2 - S1^2))) of the valid pixels
+    auto phase_b = [&](int t, int tile, int dec, int n1, int nb_closed, uint32_t pe02,
+                       uint32_t pe13, uint32_t ce02, uint32_t ce13, unsigned long long &acc) {
+        const TileCtx c = tile_ctx(a, tile, tiles_x, tid);
+        const long sidx = (long)tile * SCAN_THREADS + tid;
+        uint4 s1 = make_uint4(0, 0, 0, 0), s2 = make_uint4(0, 0, 0, 0);
+        if (t > 0) {
+            s1 = reinterpret_cast<const uint4 *>(a.S1)[sidx];
+            s2 = reinterpret_cast<const uint4 *>(a.S2)[sidx];
+            const uint32_t ep[4] = {pe02 & 0xFFFFu, pe13 & 0xFFFFu, pe02 >> 16, pe13 >> 16};
+            uint32_t *S1v = &s1.x, *S2v = &s2.x;
+            // the buffer that the decision closed: its summed energy
+            const bool closing = dec != DEC_JOIN && a.E0 && nb_closed - 1 < a.nbcap;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                if (closing && v < c.nvalid)
+                    a.E0[(long)(nb_closed - 1) * a.e0_plane + (long)c.row * a.W + c.col + v] =
+                        (int32_t)(dec == DEC_CLOSE ? S1v[v] + ep[v] : S1v[v]);
+                if (dec == DEC_JOIN) { S1v[v] += ep[v]; S2v[v] += ep[v] * ep[v]; }
+                else if (dec == DEC_FLUSH) { S1v[v] = ep[v]; S2v[v] = ep[v] * ep[v]; }
+                else { S1v[v] = 0; S2v[v] = 0; }
+            }
+        }
+        reinterpret_cast<uint4 *>(a.S1)[sidx] = s1;
+        reinterpret_cast<uint4 *>(a.S2)[sidx] = s2;
+        const uint32_t ec[4] = {ce02 & 0xFFFFu, ce13 & 0xFFFFu, ce02 >> 16, ce13 >> 16};
+        const uint32_t *S1v = &s1.x, *S2v = &s2.x;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            if (v < c.nvalid) {
+                const unsigned long long a1 = S1v[v] + ec[v];
+                const unsigned long long a2 = (unsigned long long)S2v[v] + ec[v] * ec[v];
+                const unsigned long long Q = (unsigned long long)n1 * a2 - a1 * a1;
+                acc += isqrt53(Q << 16);
+            }
+        }
+    };
+
+    // the CTA's partial sums of frame t
+    auto publish = [&](int t, unsigned long long acc, uint32_t emax2) {
+        uint32_t em = max(emax2 & 0xFFFFu, emax2 >> 16);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+        }
+        if ((tid & 31) == 0) { red_a[tid >> 5] = acc; red_m[tid >> 5] = em; }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long A = 0;
+            uint32_t m = 0;
+            for (int w = 0; w < SCAN_THREADS / 32; ++w) { A += red_a[w]; m = max(m, red_m[w]); }
+            a.partA[(long)t * G + lb] = (long long)A;
+            a.partM[(long)t * G + lb] = (int)m;
+            __threadfence();
+            atomicAdd(&a.count[t], 1u);
+        }
+        __syncthreads();
+    };
+
+    uint16_t *ering = a.ering;   // non-resident path: [2][ntiles][256][4]
+    const long eslot = (long)ntiles * SCAN_THREADS * 4;
 
     for (int t = 0; t < a.T; ++t) {
         // ---- (1) energy of frame t on this CTA's tiles ----------------------
-        const uint8_t *f = a.rgb + (long)t * hw * 3;
-        uint16_t *ecur = a.ering + (long)(t & 1) * hw;
-        int emax = 0;
-        for (int tile = lb; tile < ntiles; tile += G) {
-            int r0 = (tile / tiles_x) * TR, c0 = (tile % tiles_x) * TC;
-            for (int q = tid; q < (TR + 2) * (TC + 2); q += SCAN_THREADS) {
-                int r = q / (TC + 2), c = q % (TC + 2);
-                int gi = clampi(r0 + r - 1, 0, a.H - 1), gj = clampi(c0 + c - 1, 0, a.W - 1);
-                lum[r][c] = (uint8_t)luma_px(f + ((long)gi * a.W + gj) * 3);
+        uint32_t emax2 = 0;
+        if (resident) {
+#pragma unroll
+            for (int k = 0; k < MAXT; ++k)
+                if (k < mine) phase_a(t, lb + k * G, ec02[k], ec13[k], yp[k], emax2);
+        } else {
+            for (int k = 0; k < mine; ++k) {
+                uint32_t e02, e13, ydummy = 0;
+                phase_a(t, lb + k * G, e02, e13, ydummy, emax2);
+                const long sidx = (long)(lb + k * G) * SCAN_THREADS + tid;
+                reinterpret_cast<uint2 *>(ering + (long)(t & 1) * eslot)[sidx] = make_uint2(e02, e13);
             }
-            __syncthreads();
-            for (int q = tid; q < TR * TC; q += SCAN_THREADS) {
-                int r = q / TC, c = q % TC;
-                int gi = r0 + r, gj = c0 + c;
-                if (gi < a.H && gj < a.W) {
-                    int g = sobel3(lum[r][c], lum[r][c + 1], lum[r][c + 2], lum[r + 1][c],
-                                   lum[r + 1][c + 2], lum[r + 2][c], lum[r + 2][c + 1],
-                                   lum[r + 2][c + 2]);
-                    int y = lum[r + 1][c + 1];
-                    long yo = (long)t * a.H * a.ypitch + (long)gi * a.ypitch + gj;
-                    int d = 0;
-                    if (t > 0) d = abs(y - (int)a.Y[yo - (long)a.H * a.ypitch]);
-                    int e = a.wg * g + a.wm * d;
-                    a.Y[yo] = (uint8_t)y;
-                    a.D[yo] = (uint8_t)d;
-                    ecur[(long)gi * a.W + gj] = (uint16_t)e;
-                    emax = max(emax, e);
-                }
-            }
-            __syncthreads();
         }
 
         // ---- (2) buffer decision for frame t-1 -------------------------------
@@ -246,57 +408,77 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
         }
         const int dec = s_dec;
         const int n1 = st.n + 1;
+        const int nbc = st.nb;
 
         // ---- (3) fold e_{t-1} into S1/S2, partial A_t ------------------------
-        const uint16_t *eprev = a.ering + (long)((t + 1) & 1) * hw;
         unsigned long long acc = 0;
-        for (int tile = lb; tile < ntiles; tile += G) {
-            int r0 = (tile / tiles_x) * TR, c0 = (tile % tiles_x) * TC;
-            for (int q = tid; q < TR * TC; q += SCAN_THREADS) {
-                int gi = r0 + q / TC, gj = c0 + q % TC;
-                if (gi < a.H && gj < a.W) {
-                    long p = (long)gi * a.W + gj;
-                    uint32_t s1 = 0, s2 = 0;   // the sums start at zero (no memset)
-                    if (t > 0) {
-                        s1 = a.S1[p];
-                        s2 = a.S2[p];
-                        uint32_t ep = eprev[p];
-                        if (dec == DEC_JOIN) { s1 += ep; s2 += ep * ep; }
-                        else if (dec == DEC_FLUSH) { s1 = ep; s2 = ep * ep; }
-                        else { s1 = 0; s2 = 0; }
-                    }
-                    uint32_t ec = ecur[p];
-                    unsigned long long a1 = s1 + ec;
-                    unsigned long long a2 = (unsigned long long)s2 + ec * ec;
-                    unsigned long long Q = (unsigned long long)n1 * a2 - a1 * a1;
-                    acc += isqrt_u64(Q << 16);
-                    a.S1[p] = s1;
-                    a.S2[p] = s2;
+        if (resident) {
+#pragma unroll
+            for (int k = 0; k < MAXT; ++k)
+                if (k < mine) {
+                    phase_b(t, lb + k * G, dec, n1, nbc, ep02[k], ep13[k], ec02[k], ec13[k], acc);
+                    ep02[k] = ec02[k];
+                    ep13[k] = ec13[k];
                 }
+        } else {
+            for (int k = 0; k < mine; ++k) {
+                const long sidx = (long)(lb + k * G) * SCAN_THREADS + tid;
+                const uint2 cur = reinterpret_cast<const uint2 *>(ering + (long)(t & 1) * eslot)[sidx];
+                uint2 prv = make_uint2(0, 0);
+                if (t > 0)
+                    prv = reinterpret_cast<const uint2 *>(ering + (long)((t + 1) & 1) * eslot)[sidx];
+                phase_b(t, lb + k * G, dec, n1, nbc, prv.x, prv.y, cur.x, cur.y, acc);
             }
         }
-        // block reduction of (acc, emax)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-        }
-        if ((tid & 31) == 0) { red_a[tid >> 5] = (long long)acc; red_m[tid >> 5] = emax; }
-        __syncthreads();
-        if (tid == 0) {
-            long long A = 0;
-            int m = 0;
-            for (int w = 0; w < SCAN_THREADS / 32; ++w) { A += red_a[w]; m = max(m, red_m[w]); }
-            a.partA[(long)t * G + lb] = A;
-            a.partM[(long)t * G + lb] = m;
-            __threadfence();
-            atomicAdd(&a.count[t], 1u);
-        }
-        __syncthreads();
+        publish(t, acc, emax2);
     }
 
     // decision for the last frame, then close the open buffer
     if (!wait_and_decide(a, a.T - 1, G, st, &s_dec)) return;
+    const int dec = s_dec;
+    // summed energy of the buffers this last decision closed or left open
+    if (a.E0) {
+        for (int k = 0; k < mine; ++k) {
+            const int tile = lb + k * G;
+            const TileCtx c = tile_ctx(a, tile, tiles_x, tid);
+            if (c.nvalid == 0) continue;
+            uint32_t pe02, pe13;
+            if (resident) {
+                // registers hold e_{T-1}; pick the tile's entry without dynamic indexing
+                pe02 = ep02[0]; pe13 = ep13[0];
+#pragma unroll
+                for (int q = 1; q < MAXT; ++q)
+                    if (q == k) { pe02 = ep02[q]; pe13 = ep13[q]; }
+            } else {
+                const long sidx = (long)tile * SCAN_THREADS + tid;
+                const uint2 v = reinterpret_cast<const uint2 *>(
+                    ering + (long)((a.T - 1) & 1) * eslot)[sidx];
+                pe02 = v.x; pe13 = v.y;
+            }
+            const long sidx = (long)tile * SCAN_THREADS + tid;
+            const uint4 s1 = reinterpret_cast<const uint4 *>(a.S1)[sidx];
+            const uint32_t ep[4] = {pe02 & 0xFFFFu, pe13 & 0xFFFFu, pe02 >> 16, pe13 >> 16};
+            const uint32_t S1v[4] = {s1.x, s1.y, s1.z, s1.w};
+            // JOIN: the open buffer ends with frame T-1.  FLUSH: the previous
+            // buffer closed before T-1, which is a buffer of its own.  CLOSE:
+            // the buffer ending with T-1 closed at t_max.
+            const int nb = st.nb;   // buffers closed so far (after this decision)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                if (v >= c.nvalid) continue;
+                const long px = (long)c.row * a.W + c.col + v;
+                if (dec == DEC_JOIN) {
+                    if (nb < a.nbcap) a.E0[(long)nb * a.e0_plane + px] = (int32_t)(S1v[v] + ep[v]);
+                } else if (dec == DEC_FLUSH) {
+                    if (nb - 1 < a.nbcap) a.E0[(long)(nb - 1) * a.e0_plane + px] = (int32_t)S1v[v];
+                    if (nb < a.nbcap) a.E0[(long)nb * a.e0_plane + px] = (int32_t)ep[v];
+                } else {
+                    if (nb - 1 < a.nbcap)
+                        a.E0[(long)(nb - 1) * a.e0_plane + px] = (int32_t)(S1v[v] + ep[v]);
+                }
+            }
+        }
+    }
     if (lb == 0 && tid == 0) {
         int nb = st.nb;
         if (st.n > 0) a.starts[nb++] = st.start;
@@ -360,5 +542,7 @@ int scan_capacity(int *err_out) {
 }
 
 int scan_tiles(int H, int W) { return ((H + TR - 1) / TR) * ((W + TC - 1) / TC); }
+
+long scan_state_px(int H, int W) { return (long)scan_tiles(H, W) * TR * TC; }
 
 }  // namespace scpl

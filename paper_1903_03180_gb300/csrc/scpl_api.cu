@@ -102,7 +102,8 @@ struct scpl_ctx {
     int device = 0;
     std::string err;
     // scan
-    DevBuf Y, D, ering, S1, S2, partA, partM, count, starts, nbuf, errw;
+    DevBuf Y, D, ering, S1, S2, partA, partM, count, starts, nbuf, errw, E0;
+    int e0cap = 0;   // summed-energy planes the last scan could write
     // carving: one slab for every array of the carving workspace
     DevBuf cws, bof;
     // host-memory entry point staging
@@ -183,10 +184,14 @@ scpl_status check_overflow(scpl_ctx *h, int T, int H) {
     return SCPL_OK;
 }
 
-// Runs the buffer scan; leaves Y, D (original luma / motion) in the handle and
-// the starts on the host.
+constexpr int E0_PLANES = 16;   // buffers whose summed energy the scan keeps
+
+// Runs the buffer scan; leaves Y, D (original luma / motion) and the summed
+// energy of the first E0_PLANES buffers in the handle and the starts on the
+// host.  A and M (host, or NULL) receive every frame's A_t and maximum e_t.
 scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
-                     std::vector<int> &starts) {
+                     std::vector<int> &starts, bool keep_e0, long long *A = nullptr,
+                     int *M = nullptr) {
     const long ypitch = round_up(W, 16);
     const long hw = (long)H * W;
     int gerr = 0;
@@ -194,9 +199,13 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     if (gerr || G < 1) return fail(h, SCPL_ECUDA, "scan occupancy query failed (%d)", gerr);
     SCPL_CUDA(h, h->Y.ensure((size_t)T * H * ypitch));
     SCPL_CUDA(h, h->D.ensure((size_t)T * H * ypitch));
-    SCPL_CUDA(h, h->ering.ensure((size_t)2 * hw * sizeof(uint16_t)));
-    SCPL_CUDA(h, h->S1.ensure((size_t)hw * sizeof(uint32_t)));
-    SCPL_CUDA(h, h->S2.ensure((size_t)hw * sizeof(uint32_t)));
+    const size_t spx = (size_t)scan_state_px(H, W);
+    SCPL_CUDA(h, h->ering.ensure(2 * spx * sizeof(uint16_t)));
+    SCPL_CUDA(h, h->S1.ensure(spx * sizeof(uint32_t)));
+    SCPL_CUDA(h, h->S2.ensure(spx * sizeof(uint32_t)));
+    h->e0cap = keep_e0 ? std::min(T, E0_PLANES) : 0;
+    if (h->e0cap) SCPL_CUDA(h, h->E0.ensure((size_t)h->e0cap * hw * sizeof(int32_t)));
+    if (A) SCPL_CUDA(h, h->partA.ensure((size_t)T * G * sizeof(long long) + (size_t)T * 12));
     SCPL_CUDA(h, h->partA.ensure((size_t)T * G * sizeof(long long)));
     SCPL_CUDA(h, h->partM.ensure((size_t)T * G * sizeof(int)));
     SCPL_CUDA(h, h->count.ensure((size_t)T * sizeof(unsigned)));
@@ -220,6 +229,15 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     a.t_max = effective_tmax(h->p); a.maxval_mode = h->p.maxval_mode;
     a.maxval_theory = energy_max(h->p);
     a.spin_limit_ns = SPIN_LIMIT_NS;
+    a.E0 = h->e0cap ? h->E0.as<int32_t>() : nullptr;
+    a.nbcap = h->e0cap;
+    a.e0_plane = hw;
+    a.A_out = nullptr;
+    a.M_out = nullptr;
+    if (A) {   // diagnostics after the partial sums in the same allocation
+        a.A_out = reinterpret_cast<long long *>(h->partA.as<char>() + (size_t)T * G * 8);
+        a.M_out = reinterpret_cast<int *>(a.A_out + T);
+    }
     SCPL_CUDA(h, timed(h, K_SCAN, [&] { return launch_scan(a, G, s); }));
     if (h->prof.on) h->prof.bytes[K_SCAN] += 28.0 * hw * T;
     int *hs = h->h_small.as<int>();
@@ -234,6 +252,11 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     int nb = hs[1];
     if (nb < 1 || nb > T) return fail(h, SCPL_ECUDA, "buffer scan returned %d buffers", nb);
     starts.assign(hs + 2, hs + 2 + nb + 1);
+    if (A) {
+        SCPL_CUDA(h, cudaMemcpyAsync(A, a.A_out, (size_t)T * 8, cudaMemcpyDeviceToHost, s));
+        SCPL_CUDA(h, cudaMemcpyAsync(M, a.M_out, (size_t)T * 4, cudaMemcpyDeviceToHost, s));
+        SCPL_CUDA(h, cudaStreamSynchronize(s));
+    }
     return SCPL_OK;
 }
 
@@ -319,7 +342,7 @@ void scpl_destroy(scpl_handle h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
     DevBuf *bufs[] = {&h->Y, &h->D, &h->ering, &h->S1, &h->S2, &h->partA, &h->partM,
-                      &h->count, &h->starts, &h->nbuf, &h->errw, &h->cws, &h->bof,
+                      &h->count, &h->starts, &h->nbuf, &h->errw, &h->E0, &h->cws, &h->bof,
                       &h->in_frames, &h->out_frames, &h->seams_dev, &h->Yfm};
     for (DevBuf *b : bufs) b->release();
     engine_destroy(h->engine);
@@ -348,7 +371,22 @@ scpl_status scpl_scan(scpl_handle h, const uint8_t *frames, int T, int H, int W,
     if (s != SCPL_OK) return s;
     if ((s = check_overflow(h, T, H)) != SCPL_OK) return s;
     std::vector<int> starts;
-    if ((s = run_scan(h, frames, T, H, W, starts)) != SCPL_OK) return s;
+    if ((s = run_scan(h, frames, T, H, W, starts, false)) != SCPL_OK) return s;
+    if (buffer_starts) std::copy(starts.begin(), starts.end(), buffer_starts);
+    if (n_buffers) *n_buffers = (int)starts.size() - 1;
+    return SCPL_OK;
+}
+
+scpl_status scpl_scan_stats(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                            int32_t *buffer_starts, int *n_buffers, int64_t *A, int32_t *emax) {
+    scpl_status s = check_frames(h, frames, T, H, W);
+    if (s != SCPL_OK) return s;
+    if (!A || !emax) return fail(h, SCPL_EINVAL, "A and emax must not be NULL");
+    if ((s = check_overflow(h, T, H)) != SCPL_OK) return s;
+    std::vector<int> starts;
+    std::vector<long long> a(T);
+    if ((s = run_scan(h, frames, T, H, W, starts, false, a.data(), emax)) != SCPL_OK) return s;
+    for (int t = 0; t < T; ++t) A[t] = a[t];
     if (buffer_starts) std::copy(starts.begin(), starts.end(), buffer_starts);
     if (n_buffers) *n_buffers = (int)starts.size() - 1;
     return SCPL_OK;
@@ -372,7 +410,7 @@ scpl_status scpl_seams(scpl_handle h, const int32_t *energy, int H, int W, int k
     SCPL_CUDA(h, h->h_small.ensure(64 + sizeof(BufState)));
     BufState *hb = reinterpret_cast<BufState *>(h->h_small.as<char>() + 64);
     SCPL_CUDA(h, cudaStreamSynchronize(st));   // the staging area is reused below
-    *hb = BufState{0, 1, W, 0, 0, 0, W - kc, 0, 0, 0, 0};
+    *hb = BufState{0, 1, W, 0, 0, 0, W - kc, 0, 0, 0, 0, -1};
     SCPL_CUDA(h, cudaMemcpyAsync(ws.st, hb, sizeof(BufState), cudaMemcpyHostToDevice, st));
     SCPL_CUDA(h, timed(h, K_DP_SELECT, [&] {
                   return ws.J ? launch_dpc(ws, 1, k, cols, 0, st)
@@ -402,7 +440,7 @@ scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W
     if ((s = check_overflow(h, T, H)) != SCPL_OK) return s;
 
     std::vector<int> starts;
-    if ((s = run_scan(h, frames, T, H, W, starts)) != SCPL_OK) return s;
+    if ((s = run_scan(h, frames, T, H, W, starts, true)) != SCPL_OK) return s;
     const int nb = (int)starts.size() - 1;
     const int remove = W - target_W;
     CarveWs ws;
@@ -423,12 +461,14 @@ scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W
     for (int b = 0; b < nb; ++b) {
         const int nt = starts[b + 1] - starts[b];
         const int tp = (nt + 15) & ~15;
-        hb[b] = BufState{starts[b], nt, W, 0, 0, 0, target_W, 0, tp, 0, yfm_total};
+        const long long e0 = b < h->e0cap ? (long long)b * H * W : -1;
+        hb[b] = BufState{starts[b], nt, W, 0, 0, 0, target_W, 0, tp, 0, yfm_total, e0};
         yfm_total += (long long)H * W * tp;
         for (int t = starts[b]; t < starts[b + 1]; ++t) hbof[t] = b;
     }
     SCPL_CUDA(h, h->Yfm.ensure((size_t)std::max<long long>(yfm_total, 16)));
     ws.Yfm = h->Yfm.as<uint8_t>();
+    ws.E0 = h->E0.as<int32_t>();
     SCPL_CUDA(h, cudaMemcpyAsync(ws.st, hb, (size_t)nb * sizeof(BufState),
                                  cudaMemcpyHostToDevice, st));
     SCPL_CUDA(h, cudaMemcpyAsync(h->bof.p, hbof, (size_t)T * sizeof(int), cudaMemcpyHostToDevice,

@@ -31,6 +31,8 @@ struct BufState {
     int tp;          // frames of the frame-minor luma copy (nt rounded up to 16)
     int k;           // seams per iteration of this buffer (0: the launch's k)
     long long yfm;   // byte offset of this buffer's frame-minor luma copy
+    long long e0;    // element offset in CarveWs::E0 of the summed energy the
+                     // scan wrote for this buffer, -1: none (k_energy_init sums)
 };
 
 #ifdef __CUDACC__
@@ -140,6 +142,7 @@ struct CarveWs {
     int jstride;        // row stride of J (W0 rounded up to 8)
     uint32_t *Dfirst;   // [nb][nbands][dstride] direction words of every band's first row
     int *err;           // device status word (bounded waits)
+    const int32_t *E0;  // summed energy planes [H][W0] from the scan (see BufState::e0)
 };
 
 // Scan (Sec. 3.2) arguments.
@@ -148,8 +151,8 @@ struct ScanArgs {
     int T, H, W;
     long ypitch;
     uint8_t *Y, *D;         // [T][H][ypitch]
-    uint16_t *ering;        // [2][H*W] energy of the last two frames
-    uint32_t *S1, *S2;      // [H*W] sums of e and e^2 over the open buffer
+    uint16_t *ering;        // [2][scan_state_px] energy of the last two frames (tile-major)
+    uint32_t *S1, *S2;      // [scan_state_px] sums of e and e^2 over the open buffer (tile-major)
     long long *partA;       // [T][G] per-CTA partial ASDE sums
     int *partM;             // [T][G] per-CTA partial energy maxima
     unsigned *count;        // [T] CTAs that published frame t
@@ -162,6 +165,11 @@ struct ScanArgs {
     long long maxval_theory;
     unsigned long long spin_limit_ns;
     int cta0, G;            // the clip's CTAs in a multi-clip launch
+    int32_t *E0;            // [nbcap][H][W] summed energy of each closed buffer (or NULL)
+    int nbcap;
+    long e0_plane;          // H * W
+    long long *A_out;       // [T] A_t of every frame (diagnostic, or NULL)
+    int *M_out;             // [T] maximum e_t of every frame (diagnostic)
 };
 
 // Launchers (return the CUDA error of the launch).
@@ -174,7 +182,8 @@ cudaError_t launch_scan(const ScanArgs &a, int grid, cudaStream_t s);
 cudaError_t launch_scan_multi(const ScanArgs *tab, const int *block_clip, int grid,
                               cudaStream_t s);
 int scan_capacity(int *err_out);   // co-resident scan CTAs on this GPU
-int scan_tiles(int H, int W);      // 8x64 tiles of one frame
+int scan_tiles(int H, int W);      // 8x128 tiles of one frame
+long scan_state_px(int H, int W);  // pixels of the tile-major scan state
 
 cudaError_t launch_energy_init(const CarveWs &ws, int nb, cudaStream_t s);
 cudaError_t launch_update(const CarveWs &ws, int nb, cudaStream_t s);

@@ -70,6 +70,7 @@ SIGNATURES = {
     "scpl_last_error": (ctypes.c_char_p, [_P]),
     "scpl_energy": (_I, [_P, _P, _I, _I, _I, _P]),
     "scpl_scan": (_I, [_P, _P, _I, _I, _I, _P, _P]),
+    "scpl_scan_stats": (_I, [_P, _P, _I, _I, _I, _P, _P, _P, _P]),
     "scpl_seams": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "scpl_carve": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
     "scpl_carve_host": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
@@ -196,6 +197,20 @@ def scpl_scan(h, frames) -> np.ndarray:
     nb = ctypes.c_int()
     _check(h, load().scpl_scan(h, fp, T, H, W, starts.ctypes.data_as(_P), ctypes.byref(nb)))
     return starts[: nb.value + 1].copy()
+
+
+def scpl_scan_stats(h, frames):
+    """(buffer starts, A_t int64 [T], emax_t int32 [T]) as the scan computed them."""
+    import torch
+    fp = _dev_ptr(frames, torch.uint8, 4, "frames")
+    T, H, W, _ = frames.shape
+    starts = np.zeros(T + 1, np.int32)
+    A = np.zeros(T, np.int64)
+    M = np.zeros(T, np.int32)
+    nb = ctypes.c_int()
+    _check(h, load().scpl_scan_stats(h, fp, T, H, W, starts.ctypes.data_as(_P), ctypes.byref(nb),
+                                     A.ctypes.data_as(_P), M.ctypes.data_as(_P)))
+    return starts[: nb.value + 1].copy(), A, M
 
 
 def scpl_seams(h, energy, k: int, cols) -> int:

@@ -260,3 +260,44 @@ def test_carve_3840x2160(orc, lib, synth):
     f = synth.clip(3, 2160, 3840, seed=61)
     ref, got = _carve_both(orc, lib, f, 3840 - 96, 64)
     _assert_same(ref, got)
+
+
+# ------------------------------------ the integers behind every scan decision
+def _oracle_A(orc, e, starts, t_max):
+    """A_t of every frame from the oracle's energy and buffers: the sum over
+    the buffer that was open when frame t arrived, frame t included."""
+    T = e.shape[0]
+    A = np.zeros(T, np.int64)
+    bstart = {int(s): b for b, s in enumerate(starts[:-1])}
+    for b in range(len(starts) - 1):
+        s0, s1 = int(starts[b]), int(starts[b + 1])
+        for t in range(s0, s1):
+            lo = s0
+            if t == s0 and b > 0 and (s0 - int(starts[b - 1])) < t_max:
+                lo = int(starts[b - 1])   # frame t was tested against the previous buffer
+            A[t] = orc.asde_sum(e[lo:t + 1])
+    return A
+
+
+@pytest.mark.parametrize("T,H,W,seed,t_max,cuts", [(40, 61, 300, 71, 128, (8, 14)),
+                                                     (30, 200, 1000, 72, 7, (5, 9)),
+                                                     (12, 1080, 1920, 73, 128, (5, 7)),
+                                                     (6, 17, 5, 74, 2, None)])
+def test_scan_stats_every_frame(orc, lib, synth, T, H, W, seed, t_max, cuts):
+    f = synth.clip(T, H, W, seed=seed, cuts=cuts)
+    e = orc.energy(f)
+    h = lib.scpl_create(lib.Params(0.2, 1, 2, t_max, 1, 0))
+    starts, A, M = lib.scpl_scan_stats(h, torch.from_numpy(f).cuda())
+    lib.scpl_destroy(h)
+    ref_starts = orc.scan(e, t_max=t_max)
+    assert np.array_equal(starts, ref_starts)
+    assert np.array_equal(M, e.reshape(T, -1).max(axis=1))
+    assert np.array_equal(A, _oracle_A(orc, e, ref_starts, t_max))
+
+
+def test_carve_more_buffers_than_kept_sums(orc, lib, synth):
+    """t_max = 2 over 40 frames: 20 buffers, more than the scan keeps summed
+    energy for, so k_energy_init sums the rest itself."""
+    f = synth.clip(40, 30, 64, seed=75)
+    ref, got = _carve_both(orc, lib, f, 50, 4, t_max=2)
+    _assert_same(ref, got)
