@@ -29,8 +29,7 @@ namespace scpl {
 
 namespace {
 
-constexpr int EN_RB = 8;       // rows per k_energy_init CTA
-constexpr int EN_CW = 256;     // columns per k_energy_init CTA (= threads)
+constexpr int EN_QT = 128;     // threads (4-column quads) per k_energy_init CTA
 constexpr int UP_THREADS = 256;
 constexpr int DP_MAX_WARPS = 32;
 constexpr int DP_PF = 4;       // rows of energy prefetched ahead of the DP
@@ -67,82 +66,95 @@ __device__ __forceinline__ int sobel_l1(int a00, int a01, int a02, int a10, int 
 }
 
 // ---------------------------------------------------------------------------
-// k_energy_init: grid (ceil(W0/EN_CW), ceil(H/EN_RB), nb), EN_CW threads.
-// Writes the identity origin map, SDo = wm * sum_t D_t, the frame-minor luma
-// copy and E = sum_t e_t.  The scan hands over E for most buffers (st.e0 >= 0);
-// for the others the gradient of every frame is summed here.
-__global__ void __launch_bounds__(EN_CW) k_energy_init(CarveWs ws) {
+// k_energy_init: grid (ceil(W0 / (4 * EN_QT)), H, nb), EN_QT threads; every
+// thread owns a quad of 4 columns of one row of one buffer.  It writes the
+// identity origin map, SDo = wm * sum_t D_t, the frame-minor luma copy (16
+// frames per uint4 and pixel, frames past the buffer zero) and E = sum_t e_t.
+// The scan hands over E for most buffers (st.e0 >= 0); for the others the
+// gradient of every frame is summed here.
+__device__ __forceinline__ void transpose4x4(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
+                                             uint32_t &p0, uint32_t &p1, uint32_t &p2,
+                                             uint32_t &p3) {
+    // w_f = (pixel 0..3 of frame f)  ->  p_j = (frames 0..3 of pixel j)
+    const uint32_t t0 = __byte_perm(w0, w1, 0x5140), t1 = __byte_perm(w2, w3, 0x5140);
+    const uint32_t t2 = __byte_perm(w0, w1, 0x7362), t3 = __byte_perm(w2, w3, 0x7362);
+    p0 = __byte_perm(t0, t1, 0x5410);
+    p1 = __byte_perm(t0, t1, 0x7632);
+    p2 = __byte_perm(t2, t3, 0x5410);
+    p3 = __byte_perm(t2, t3, 0x7632);
+}
+
+__global__ void __launch_bounds__(EN_QT) k_energy_init(CarveWs ws) {
     const int b = blockIdx.z;
     const BufState st = ws.st[b];
     const int W0 = ws.W0, H = ws.H;
-    const int p0 = blockIdx.x * EN_CW, i0 = blockIdx.y * EN_RB;
-    const int tid = threadIdx.x, p = p0 + tid;
-    if (p >= W0) return;
+    const int i = blockIdx.y;
+    const int c = 4 * (blockIdx.x * EN_QT + threadIdx.x);
+    if (c >= W0) return;
+    const int nv = min(4, W0 - c);   // valid columns of the quad
     const long pitch = ws.pitch, plane = ws.plane;
-    const bool have_e = st.e0 >= 0;
-    uint16_t *O = ws.O + (long)b * 2 * plane;
-    int32_t *SDo = ws.SD + (long)b * plane;
-    int32_t *E = ws.E + (long)b * 2 * plane;
-    int32_t eacc[EN_RB];
-#pragma unroll
-    for (int r = 0; r < EN_RB; ++r) {
-        eacc[r] = 0;
-        const int i = i0 + r;
-        if (i < H) {
-            O[(long)i * pitch + p] = (uint16_t)p;
-            int sd = 0;
-            for (int t = st.t0; t < st.t0 + st.nt; ++t)
-                sd += ws.D[((long)t * H + i) * ws.ypitch + p];
-            sd *= ws.wm;
-            SDo[(long)i * pitch + p] = sd;
-            eacc[r] = have_e ? __ldg(ws.E0 + st.e0 + (long)i * W0 + p) : sd;
-        }
-    }
-    const int pl = max(p - 1, 0), pr = min(p + 1, W0 - 1);
-    // frames innermost copy of the luma: 16 frames per uint4
-    uint32_t fq[EN_RB][4];
-#pragma unroll
-    for (int r = 0; r < EN_RB; ++r) fq[r][0] = fq[r][1] = fq[r][2] = fq[r][3] = 0;
-    uint8_t *yfm = ws.Yfm + st.yfm;
+    const long yrow = (long)i * ws.ypitch + c;
+    const long fstride = (long)H * ws.ypitch;
+    const uint8_t *Yb = ws.Y + (long)st.t0 * fstride + yrow;
+    const uint8_t *Db = ws.D + (long)st.t0 * fstride + yrow;
+    uint8_t *yfm = ws.Yfm + st.yfm + ((long)i * W0 + c) * st.tp;
+    uint32_t sd02 = 0, sd13 = 0;   // sum of D, pixels (0, 2) and (1, 3) in u16 lanes
     for (int tb = 0; tb < st.tp; tb += 16) {
+        uint32_t q[4][4];   // q[j][g]: frames tb + 4g .. tb + 4g + 3 of pixel j
 #pragma unroll
-        for (int tt = 0; tt < 16; ++tt) {
-            const int t = tb + tt;
-            if (t < st.nt) {
-                const uint8_t *Yt = ws.Y + (long)(st.t0 + t) * H * ws.ypitch;
+        for (int g = 0; g < 4; ++g) {
+            uint32_t w[4];
 #pragma unroll
-                for (int r = 0; r < EN_RB; ++r) {
-                    const int i = i0 + r;
-                    if (i < H) {
-                        const uint8_t *rc = Yt + (long)i * ws.ypitch;
-                        const int yc = __ldg(rc + p);
-                        if (!have_e) {
-                            const uint8_t *ru = Yt + (long)clampi(i - 1, 0, H - 1) * ws.ypitch;
-                            const uint8_t *rd = Yt + (long)clampi(i + 1, 0, H - 1) * ws.ypitch;
-                            eacc[r] += ws.wg * sobel_l1(__ldg(ru + pl), __ldg(ru + p),
-                                                        __ldg(ru + pr), __ldg(rc + pl),
-                                                        __ldg(rc + pr), __ldg(rd + pl),
-                                                        __ldg(rd + p), __ldg(rd + pr));
-                        }
-                        fq[r][tt >> 2] |= (uint32_t)yc << (8 * (tt & 3));
-                    }
+            for (int f = 0; f < 4; ++f) {
+                const int t = tb + 4 * g + f;
+                w[f] = 0;
+                if (t < st.nt) {
+                    w[f] = __ldg(reinterpret_cast<const uint32_t *>(Yb + (long)t * fstride));
+                    const uint32_t d = __ldg(reinterpret_cast<const uint32_t *>(Db + (long)t * fstride));
+                    sd02 += __byte_perm(d, 0, 0x4240);
+                    sd13 += __byte_perm(d, 0, 0x4341);
                 }
             }
+            transpose4x4(w[0], w[1], w[2], w[3], q[0][g], q[1][g], q[2][g], q[3][g]);
         }
 #pragma unroll
-        for (int r = 0; r < EN_RB; ++r) {
-            const int i = i0 + r;
-            if (i < H)
-                *reinterpret_cast<uint4 *>(yfm + ((long)i * W0 + p) * st.tp + tb) =
-                    make_uint4(fq[r][0], fq[r][1], fq[r][2], fq[r][3]);
-            fq[r][0] = fq[r][1] = fq[r][2] = fq[r][3] = 0;
+        for (int j = 0; j < 4; ++j)
+            if (j < nv)
+                *reinterpret_cast<uint4 *>(yfm + (long)j * st.tp + tb) =
+                    make_uint4(q[j][0], q[j][1], q[j][2], q[j][3]);
+    }
+    const int sd[4] = {(int)(sd02 & 0xFFFFu) * ws.wm, (int)(sd13 & 0xFFFFu) * ws.wm,
+                       (int)(sd02 >> 16) * ws.wm, (int)(sd13 >> 16) * ws.wm};
+    int e[4] = {sd[0], sd[1], sd[2], sd[3]};
+    if (st.e0 >= 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j < nv) e[j] = __ldg(ws.E0 + st.e0 + (long)i * W0 + c + j);
+    } else {
+        // no sum from the scan: add the gradient of every frame
+        for (int t = 0; t < st.nt; ++t) {
+            const uint8_t *Yt = ws.Y + (long)(st.t0 + t) * fstride;
+            const uint8_t *ru = Yt + (long)clampi(i - 1, 0, H - 1) * ws.ypitch;
+            const uint8_t *rc = Yt + (long)i * ws.ypitch;
+            const uint8_t *rd = Yt + (long)clampi(i + 1, 0, H - 1) * ws.ypitch;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                if (j >= nv) continue;
+                const int p = c + j, pl = max(p - 1, 0), pr = min(p + 1, W0 - 1);
+                e[j] += ws.wg * sobel_l1(__ldg(ru + pl), __ldg(ru + p), __ldg(ru + pr),
+                                         __ldg(rc + pl), __ldg(rc + pr), __ldg(rd + pl),
+                                         __ldg(rd + p), __ldg(rd + pr));
+            }
         }
     }
-#pragma unroll
-    for (int r = 0; r < EN_RB; ++r) {
-        const int i = i0 + r;
-        if (i < H) E[(long)i * pitch + p] = eacc[r];
-    }
+    uint16_t *O = ws.O + (long)b * 2 * plane + (long)i * pitch + c;
+    int32_t *SDo = ws.SD + (long)b * plane + (long)i * pitch + c;
+    int32_t *E = ws.E + (long)b * 2 * plane + (long)i * pitch + c;
+    // pitch is a multiple of 32 and c of 4: whole quads are aligned vectors
+    *reinterpret_cast<uint2 *>(O) = make_uint2((uint32_t)c | ((uint32_t)(c + 1) << 16),
+                                               (uint32_t)(c + 2) | ((uint32_t)(c + 3) << 16));
+    *reinterpret_cast<int4 *>(SDo) = make_int4(sd[0], sd[1], sd[2], sd[3]);
+    *reinterpret_cast<int4 *>(E) = make_int4(e[0], e[1], e[2], e[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -583,6 +595,40 @@ __global__ void k_identity_O(CarveWs ws) {
     }
 }
 
+// One output row of the colour gather: dst[p] = src[O[p]] for p < target.
+// Every thread moves quads of 4 pixels: 4 origins in one load, 12 bytes out as
+// three words when the row is word-aligned.
+__device__ __forceinline__ void gather_row(const uint16_t *__restrict__ O,
+                                           const uint8_t *__restrict__ src,
+                                           uint8_t *__restrict__ dst, int target) {
+    const bool words = ((reinterpret_cast<uintptr_t>(dst) & 3) == 0);
+    for (int p = 4 * threadIdx.x; p < target; p += 4 * blockDim.x) {
+        const uint2 o4 = *reinterpret_cast<const uint2 *>(O + p);   // O rows are 8-byte aligned
+        const int o[4] = {(int)(o4.x & 0xFFFF), (int)(o4.x >> 16), (int)(o4.y & 0xFFFF),
+                          (int)(o4.y >> 16)};
+        const int n = min(4, target - p);
+        if (n == 4 && words) {
+            uint32_t b[12];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                b[3 * j + 0] = src[o[j] * 3 + 0];
+                b[3 * j + 1] = src[o[j] * 3 + 1];
+                b[3 * j + 2] = src[o[j] * 3 + 2];
+            }
+            uint32_t *d = reinterpret_cast<uint32_t *>(dst + p * 3);
+            d[0] = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
+            d[1] = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
+            d[2] = b[8] | (b[9] << 8) | (b[10] << 16) | (b[11] << 24);
+        } else {
+            for (int j = 0; j < n; ++j) {
+                dst[(p + j) * 3 + 0] = src[o[j] * 3 + 0];
+                dst[(p + j) * 3 + 1] = src[o[j] * 3 + 1];
+                dst[(p + j) * 3 + 2] = src[o[j] * 3 + 2];
+            }
+        }
+    }
+}
+
 // Final colour gather: out[t][i][p] = rgb[t][i][O[i][p]].  grid (H, T).
 __global__ void k_gather(CarveWs ws, const uint8_t *__restrict__ rgb, const int *buf_of_frame,
                          int target, uint8_t *__restrict__ out) {
@@ -591,14 +637,8 @@ __global__ void k_gather(CarveWs ws, const uint8_t *__restrict__ rgb, const int 
     int W, slot, removed;
     committed(ws.st[b], W, slot, removed);
     const uint16_t *O = ws.O + ((long)b * 2 + slot) * ws.plane + (long)i * ws.pitch;
-    const uint8_t *src = rgb + ((long)t * ws.H + i) * ws.W0 * 3;
-    uint8_t *dst = out + ((long)t * ws.H + i) * (long)target * 3;
-    for (int p = threadIdx.x; p < target; p += blockDim.x) {
-        int o = O[p];
-        dst[p * 3 + 0] = src[o * 3 + 0];
-        dst[p * 3 + 1] = src[o * 3 + 1];
-        dst[p * 3 + 2] = src[o * 3 + 2];
-    }
+    gather_row(O, rgb + ((long)t * ws.H + i) * ws.W0 * 3,
+               out + ((long)t * ws.H + i) * (long)target * 3, target);
 }
 
 // Final colour gather of frames listed in a table (frames of several clips
@@ -613,14 +653,7 @@ __global__ void k_gather_frames(CarveWs ws, const GatherFrame *__restrict__ tab)
         return;
     }
     const uint16_t *O = ws.O + ((long)g.b * 2 + slot) * ws.plane + (long)i * ws.pitch;
-    const uint8_t *src = g.src + (long)i * ws.W0 * 3;
-    uint8_t *dst = g.dst + (long)i * g.target * 3;
-    for (int p = threadIdx.x; p < g.target; p += blockDim.x) {
-        const int o = O[p];
-        dst[p * 3 + 0] = src[o * 3 + 0];
-        dst[p * 3 + 1] = src[o * 3 + 1];
-        dst[p * 3 + 2] = src[o * 3 + 2];
-    }
+    gather_row(O, g.src + (long)i * ws.W0 * 3, g.dst + (long)i * g.target * 3, g.target);
 }
 
 // dst[t][j][i] = src[t][i][j] for RGB pixels: [T][H][W][3] -> [T][W][H][3].
@@ -702,8 +735,8 @@ size_t update_smem_bytes(int W0, int kcap, int *rows) {
 }
 
 cudaError_t launch_energy_init(const CarveWs &ws, int nb, cudaStream_t s) {
-    dim3 grid((ws.W0 + EN_CW - 1) / EN_CW, (ws.H + EN_RB - 1) / EN_RB, nb);
-    k_energy_init<<<grid, EN_CW, 0, s>>>(ws);
+    dim3 grid((ws.W0 + 4 * EN_QT - 1) / (4 * EN_QT), ws.H, nb);
+    k_energy_init<<<grid, EN_QT, 0, s>>>(ws);
     return cudaGetLastError();
 }
 

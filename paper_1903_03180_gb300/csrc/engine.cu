@@ -98,8 +98,9 @@ struct PassDims {
 size_t scan_state_bytes(const PassDims &d) {
     const size_t spx = (size_t)scan_state_px(d.H, d.W);
     const size_t G = (size_t)scan_tiles(d.H, d.W);
-    return a256(2 * spx * 2) + 2 * a256(spx * 4) + a256((size_t)d.T * G * 12) +
-           a256((size_t)(d.T + 1) * 4) + a256((size_t)d.T * 4 + 8);
+    (void)G;
+    return a256(2 * spx * 2) + 2 * a256(spx * 4) + a256((size_t)(d.T + 1) * 4) +
+           a256((size_t)d.T * 16 + 8);
 }
 // Buffers of a pass whose summed energy the scan keeps (more are summed by
 // k_energy_init from the luma and motion maps).
@@ -504,14 +505,15 @@ scpl_status launch_wave(Srv *s) {
         total += G[i];
     }
 
-    // per-pass scan state in one slab: counts and status words first (zeroed)
+    // per-pass scan state in one slab: status words, then per frame the A_t
+    // and maximum accumulators and the arrival counts (all zeroed)
     std::vector<size_t> off(n);
-    size_t o = a256((size_t)n * 8);   // [n] err words, then counts
+    size_t o = a256((size_t)n * 8);   // [n] err words
     std::vector<size_t> cnt_off(n);
     size_t cnt_bytes = 0;
     for (int i = 0; i < n; ++i) {
-        cnt_off[i] = cnt_bytes;
-        cnt_bytes += (size_t)s->passes[take[i]].d.T * 4;
+        cnt_off[i] = cnt_bytes;   // A [T] int64, M [T] int32, count [T] uint32
+        cnt_bytes += (size_t)s->passes[take[i]].d.T * 16;
     }
     const size_t zero_bytes = a256(o + cnt_bytes);
     o = zero_bytes;
@@ -561,13 +563,13 @@ scpl_status launch_wave(Srv *s) {
         q += a256(spx * 4);
         a.S2 = reinterpret_cast<uint32_t *>(q);
         q += a256(spx * 4);
-        a.partA = reinterpret_cast<long long *>(q);
-        a.partM = reinterpret_cast<int *>(q + (size_t)P.d.T * G[i] * 8);
-        q += a256((size_t)P.d.T * scan_tiles(P.d.H, P.d.W) * 12);
+        char *acc = base + a256((size_t)n * 8) + cnt_off[i];
+        a.partA = reinterpret_cast<long long *>(acc);
+        a.partM = reinterpret_cast<int *>(acc + (size_t)P.d.T * 8);
+        a.count = reinterpret_cast<unsigned *>(acc + (size_t)P.d.T * 12);
         a.starts = reinterpret_cast<int *>(q);
         q += a256((size_t)(P.d.T + 1) * 4);
         a.n_buffers = reinterpret_cast<int *>(q);
-        a.count = reinterpret_cast<unsigned *>(base + a256((size_t)n * 8) + cnt_off[i]);
         a.err = reinterpret_cast<int *>(base + (size_t)i * 8);
         a.wg = s->p.wg;
         a.wm = s->p.wm;

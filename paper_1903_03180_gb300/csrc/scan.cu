@@ -127,9 +127,9 @@ __device__ int decide(DecState &s, long long A, long long emax, int t, const Sca
     return DEC_JOIN;
 }
 
-// Warp 0 waits for every CTA's partials of frame t, reduces them and decides.
-// Returns false (and sets the status word) if the wait ran out of time or
-// another CTA gave up.
+// Warp 0 waits until every CTA of the clip has added its partial sums of frame
+// t to the clip's accumulators, then decides.  Returns false (and sets the
+// status word) if the wait ran out of time or another CTA gave up.
 __device__ bool wait_and_decide(const ScanArgs &a, int t, int G, DecState &s, int *dec_out) {
     __shared__ int s_ok;
     if (threadIdx.x < 32) {
@@ -148,27 +148,17 @@ __device__ bool wait_and_decide(const ScanArgs &a, int t, int G, DecState &s, in
             }
         }
         ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (ok) {
+        if (ok && lane == 0) {
             __threadfence();
-            long long A = 0;
-            int m = 0;
-            for (int c = lane; c < G; c += 32) {
-                A += __ldcg(&a.partA[(long)t * G + c]);
-                m = max(m, __ldcg(&a.partM[(long)t * G + c]));
+            const long long A = (long long)__ldcg(
+                reinterpret_cast<const unsigned long long *>(&a.partA[t]));
+            const int m = __ldcg(&a.partM[t]);
+            const bool first = blockIdx.x == (unsigned)a.cta0;
+            if (first && a.A_out) {
+                a.A_out[t] = A;
+                a.M_out[t] = m;
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                A += __shfl_xor_sync(0xffffffffu, A, o);
-                m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-            }
-            if (lane == 0) {
-                const bool first = blockIdx.x == (unsigned)a.cta0;
-                if (first && a.A_out) {
-                    a.A_out[t] = A;
-                    a.M_out[t] = m;
-                }
-                *dec_out = decide(s, A, m, t, a, first);
-            }
+            *dec_out = decide(s, A, m, t, a, first);
         }
         if (lane == 0) s_ok = ok;
     }
@@ -217,10 +207,13 @@ __device__ __forceinline__ void sobel4(uint32_t u0, uint32_t u1, uint32_t m0, ui
     g13 = __vabsdiffu2(rO, lO) + __vabsdiffu2(bO, tO);
 }
 
-// Per-CTA tile ownership: CTA lb of a clip owns tiles lb, lb + G, ... for the
-// whole clip.  Up to MAXT tiles the previous frame's energy and luma of its
-// pixels stay in registers; beyond that they go through global memory.
+// Tile ownership: CTA lb of a clip owns the contiguous tiles
+// [lb * tpc, (lb + 1) * tpc) for the whole clip, tpc = ceil(tiles / G).  Up to
+// MAXT tiles the CTA keeps S1 and S2 of its pixels in shared memory and the
+// previous frame's energy and luma in registers; beyond that they live in
+// global memory.
 constexpr int MAXT = 4;
+constexpr size_t SCAN_SMEM = (size_t)MAXT * SCAN_THREADS * 2 * sizeof(uint4);   // 32 KB
 
 struct TileCtx {
     int r0, c0;      // tile origin
@@ -238,14 +231,54 @@ __device__ __forceinline__ TileCtx tile_ctx(const ScanArgs &a, int tile, int til
     return c;
 }
 
+__device__ __forceinline__ uint32_t luma4(uint32_t w0, uint32_t w1, uint32_t w2) {
+    // 12 bytes = pixels p0..p3 as R G B R | G B R G | B R G B
+    const uint32_t y0 = (77u * (w0 & 0xFF) + 150u * ((w0 >> 8) & 0xFF) + 29u * ((w0 >> 16) & 0xFF) + 128u) >> 8;
+    const uint32_t y1 = (77u * (w0 >> 24) + 150u * (w1 & 0xFF) + 29u * ((w1 >> 8) & 0xFF) + 128u) >> 8;
+    const uint32_t y2 = (77u * ((w1 >> 16) & 0xFF) + 150u * (w1 >> 24) + 29u * (w2 & 0xFF) + 128u) >> 8;
+    const uint32_t y3 = (77u * ((w2 >> 8) & 0xFF) + 150u * ((w2 >> 16) & 0xFF) + 29u * (w2 >> 24) + 128u) >> 8;
+    return y0 | (y1 << 8) | (y2 << 16) | (y3 << 24);
+}
+
 // Luma of the tile and its one-pixel frame (replicated at the image border)
-// into lum[r][j] = Y(r0 - 1 + r, c0 - 1 + j).
+// into lum[r][j] = Y(r0 - 1 + r, c0 - 1 + j).  With W a multiple of 4 every
+// 4-pixel quad is three aligned words of RGB; otherwise pixel by pixel.
 __device__ __forceinline__ void load_luma(const ScanArgs &a, const uint8_t *f, int r0, int c0,
                                           uint8_t (*lum)[LUMW]) {
-    for (int q = threadIdx.x; q < (TR + 2) * (TC + 2); q += SCAN_THREADS) {
-        const int r = q / (TC + 2), c = q - r * (TC + 2);
-        const int gi = clampi(r0 + r - 1, 0, a.H - 1), gj = clampi(c0 + c - 1, 0, a.W - 1);
-        lum[r][c] = (uint8_t)luma_px(f + ((long)gi * a.W + gj) * 3);
+    const int tid = threadIdx.x;
+    if ((a.W & 3) == 0 && (reinterpret_cast<uintptr_t>(a.rgb) & 3) == 0) {
+        // body and top/bottom frame rows: (TR + 2) rows x 32 quads
+        for (int q = tid; q < (TR + 2) * 32; q += SCAN_THREADS) {
+            const int r = q >> 5, x = q & 31;
+            const int gi = clampi(r0 + r - 1, 0, a.H - 1);
+            const int gj = c0 + 4 * x;
+            uint32_t y = 0;
+            if (gj < a.W) {
+                const uint32_t *w =
+                    reinterpret_cast<const uint32_t *>(f + ((long)gi * a.W + gj) * 3);
+                y = luma4(__ldg(w), __ldg(w + 1), __ldg(w + 2));
+            } else {   // past the right edge: replicate the last column
+                y = luma_px(f + ((long)gi * a.W + a.W - 1) * 3) * 0x01010101u;
+            }
+            // columns c0 + 4x .. c0 + 4x + 3 sit at lum[r][1 + 4x ..]: unaligned by one
+            lum[r][1 + 4 * x] = (uint8_t)y;
+            lum[r][2 + 4 * x] = (uint8_t)(y >> 8);
+            lum[r][3 + 4 * x] = (uint8_t)(y >> 16);
+            lum[r][4 + 4 * x] = (uint8_t)(y >> 24);
+        }
+        // left and right frame columns
+        if (tid < 2 * (TR + 2)) {
+            const int r = tid >> 1, side = tid & 1;
+            const int gi = clampi(r0 + r - 1, 0, a.H - 1);
+            const int gj = clampi(side ? c0 + TC : c0 - 1, 0, a.W - 1);
+            lum[r][side ? TC + 1 : 0] = (uint8_t)luma_px(f + ((long)gi * a.W + gj) * 3);
+        }
+    } else {
+        for (int q = tid; q < (TR + 2) * (TC + 2); q += SCAN_THREADS) {
+            const int r = q / (TC + 2), c = q - r * (TC + 2);
+            const int gi = clampi(r0 + r - 1, 0, a.H - 1), gj = clampi(c0 + c - 1, 0, a.W - 1);
+            lum[r][c] = (uint8_t)luma_px(f + ((long)gi * a.W + gj) * 3);
+        }
     }
 }
 
@@ -253,6 +286,7 @@ __device__ __forceinline__ void load_luma(const ScanArgs &a, const uint8_t *f, i
 // range of CTAs (clip of CTA x = tab[block_clip[x]], CTAs [cta0, cta0 + G)).
 __global__ void __launch_bounds__(SCAN_THREADS, 4)
 k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ block_clip) {
+    extern __shared__ __align__(16) uint4 sstate[];   // [MAXT][2][SCAN_THREADS] S1, S2
     __shared__ ScanArgs a;
     __shared__ __align__(16) uint8_t lum[TR + 2][LUMW];
     __shared__ unsigned long long red_a[SCAN_THREADS / 32];
@@ -277,8 +311,10 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
     const int lb = blockIdx.x - a.cta0;   // CTA index within the clip's range
     const int tiles_x = (a.W + TC - 1) / TC;
     const int ntiles = ((a.H + TR - 1) / TR) * tiles_x;
-    const int mine = lb < ntiles ? (ntiles - 1 - lb) / G + 1 : 0;
-    const bool resident = mine <= MAXT;
+    const int tpc = (ntiles + G - 1) / G;
+    const int first = lb * tpc;
+    const int mine = max(0, min(tpc, ntiles - first));
+    const bool resident = tpc <= MAXT;
     const long hw3 = (long)a.H * a.W * 3;
     const long yplane = (long)a.H * a.ypitch;
 
@@ -324,14 +360,22 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
 
     // phase B of one tile: fold e_{t-1} into S1/S2 as the decision says, add
     // e_t, accumulate floor(sqrt(65536 (n S2 - S1^2))) of the valid pixels
-    auto phase_b = [&](int t, int tile, int dec, int n1, int nb_closed, uint32_t pe02,
+    auto phase_b = [&](int t, int tile, int slot, int dec, int n1, int nb_closed, uint32_t pe02,
                        uint32_t pe13, uint32_t ce02, uint32_t ce13, unsigned long long &acc) {
         const TileCtx c = tile_ctx(a, tile, tiles_x, tid);
-        const long sidx = (long)tile * SCAN_THREADS + tid;
+        uint4 *S1p, *S2p;
+        if (resident) {
+            S1p = &sstate[(slot * 2) * SCAN_THREADS + tid];
+            S2p = &sstate[(slot * 2 + 1) * SCAN_THREADS + tid];
+        } else {
+            const long sidx = (long)tile * SCAN_THREADS + tid;
+            S1p = reinterpret_cast<uint4 *>(a.S1) + sidx;
+            S2p = reinterpret_cast<uint4 *>(a.S2) + sidx;
+        }
         uint4 s1 = make_uint4(0, 0, 0, 0), s2 = make_uint4(0, 0, 0, 0);
         if (t > 0) {
-            s1 = reinterpret_cast<const uint4 *>(a.S1)[sidx];
-            s2 = reinterpret_cast<const uint4 *>(a.S2)[sidx];
+            s1 = *S1p;
+            s2 = *S2p;
             const uint32_t ep[4] = {pe02 & 0xFFFFu, pe13 & 0xFFFFu, pe02 >> 16, pe13 >> 16};
             uint32_t *S1v = &s1.x, *S2v = &s2.x;
             // the buffer that the decision closed: its summed energy
@@ -346,8 +390,8 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
                 else { S1v[v] = 0; S2v[v] = 0; }
             }
         }
-        reinterpret_cast<uint4 *>(a.S1)[sidx] = s1;
-        reinterpret_cast<uint4 *>(a.S2)[sidx] = s2;
+        *S1p = s1;
+        *S2p = s2;
         const uint32_t ec[4] = {ce02 & 0xFFFFu, ce13 & 0xFFFFu, ce02 >> 16, ce13 >> 16};
         const uint32_t *S1v = &s1.x, *S2v = &s2.x;
 #pragma unroll
@@ -361,7 +405,7 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
         }
     };
 
-    // the CTA's partial sums of frame t
+    // the CTA's partial sums of frame t into the clip's accumulators
     auto publish = [&](int t, unsigned long long acc, uint32_t emax2) {
         uint32_t em = max(emax2 & 0xFFFFu, emax2 >> 16);
 #pragma unroll
@@ -375,8 +419,8 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
             unsigned long long A = 0;
             uint32_t m = 0;
             for (int w = 0; w < SCAN_THREADS / 32; ++w) { A += red_a[w]; m = max(m, red_m[w]); }
-            a.partA[(long)t * G + lb] = (long long)A;
-            a.partM[(long)t * G + lb] = (int)m;
+            atomicAdd(reinterpret_cast<unsigned long long *>(&a.partA[t]), A);
+            atomicMax(&a.partM[t], (int)m);
             __threadfence();
             atomicAdd(&a.count[t], 1u);
         }
@@ -392,12 +436,12 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
         if (resident) {
 #pragma unroll
             for (int k = 0; k < MAXT; ++k)
-                if (k < mine) phase_a(t, lb + k * G, ec02[k], ec13[k], yp[k], emax2);
+                if (k < mine) phase_a(t, first + k, ec02[k], ec13[k], yp[k], emax2);
         } else {
             for (int k = 0; k < mine; ++k) {
                 uint32_t e02, e13, ydummy = 0;
-                phase_a(t, lb + k * G, e02, e13, ydummy, emax2);
-                const long sidx = (long)(lb + k * G) * SCAN_THREADS + tid;
+                phase_a(t, first + k, e02, e13, ydummy, emax2);
+                const long sidx = (long)(first + k) * SCAN_THREADS + tid;
                 reinterpret_cast<uint2 *>(ering + (long)(t & 1) * eslot)[sidx] = make_uint2(e02, e13);
             }
         }
@@ -416,18 +460,18 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
 #pragma unroll
             for (int k = 0; k < MAXT; ++k)
                 if (k < mine) {
-                    phase_b(t, lb + k * G, dec, n1, nbc, ep02[k], ep13[k], ec02[k], ec13[k], acc);
+                    phase_b(t, first + k, k, dec, n1, nbc, ep02[k], ep13[k], ec02[k], ec13[k], acc);
                     ep02[k] = ec02[k];
                     ep13[k] = ec13[k];
                 }
         } else {
             for (int k = 0; k < mine; ++k) {
-                const long sidx = (long)(lb + k * G) * SCAN_THREADS + tid;
+                const long sidx = (long)(first + k) * SCAN_THREADS + tid;
                 const uint2 cur = reinterpret_cast<const uint2 *>(ering + (long)(t & 1) * eslot)[sidx];
                 uint2 prv = make_uint2(0, 0);
                 if (t > 0)
                     prv = reinterpret_cast<const uint2 *>(ering + (long)((t + 1) & 1) * eslot)[sidx];
-                phase_b(t, lb + k * G, dec, n1, nbc, prv.x, prv.y, cur.x, cur.y, acc);
+                phase_b(t, first + k, 0, dec, n1, nbc, prv.x, prv.y, cur.x, cur.y, acc);
             }
         }
         publish(t, acc, emax2);
@@ -438,31 +482,31 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
     const int dec = s_dec;
     // summed energy of the buffers this last decision closed or left open
     if (a.E0) {
+        const int nb = st.nb;   // buffers closed so far (after this decision)
         for (int k = 0; k < mine; ++k) {
-            const int tile = lb + k * G;
+            const int tile = first + k;
             const TileCtx c = tile_ctx(a, tile, tiles_x, tid);
             if (c.nvalid == 0) continue;
-            uint32_t pe02, pe13;
+            uint32_t pe02 = 0, pe13 = 0;
+            uint4 s1;
             if (resident) {
                 // registers hold e_{T-1}; pick the tile's entry without dynamic indexing
-                pe02 = ep02[0]; pe13 = ep13[0];
 #pragma unroll
-                for (int q = 1; q < MAXT; ++q)
+                for (int q = 0; q < MAXT; ++q)
                     if (q == k) { pe02 = ep02[q]; pe13 = ep13[q]; }
+                s1 = sstate[(k * 2) * SCAN_THREADS + tid];
             } else {
                 const long sidx = (long)tile * SCAN_THREADS + tid;
                 const uint2 v = reinterpret_cast<const uint2 *>(
                     ering + (long)((a.T - 1) & 1) * eslot)[sidx];
                 pe02 = v.x; pe13 = v.y;
+                s1 = reinterpret_cast<const uint4 *>(a.S1)[sidx];
             }
-            const long sidx = (long)tile * SCAN_THREADS + tid;
-            const uint4 s1 = reinterpret_cast<const uint4 *>(a.S1)[sidx];
             const uint32_t ep[4] = {pe02 & 0xFFFFu, pe13 & 0xFFFFu, pe02 >> 16, pe13 >> 16};
             const uint32_t S1v[4] = {s1.x, s1.y, s1.z, s1.w};
             // JOIN: the open buffer ends with frame T-1.  FLUSH: the previous
             // buffer closed before T-1, which is a buffer of its own.  CLOSE:
             // the buffer ending with T-1 closed at t_max.
-            const int nb = st.nb;   // buffers closed so far (after this decision)
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 if (v >= c.nvalid) continue;
@@ -498,19 +542,14 @@ cudaError_t launch_energy_api(const uint8_t *rgb, int T, int H, int W, int wg, i
     return cudaGetLastError();
 }
 
-// Co-resident CTAs for the cooperative scan: all SMs' worth, capped by the
-// number of tiles of a frame.
+// Co-resident CTAs for the cooperative scan: all SMs' worth, lowered so that
+// every CTA owns the same number of tiles.
 int scan_grid_size(int H, int W, int *err_out) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan, SCAN_THREADS, 0);
-    if (e != cudaSuccess) { *err_out = (int)e; return 0; }
-    *err_out = 0;
-    long ntiles = (long)((H + TR - 1) / TR) * ((W + TC - 1) / TC);
-    long g = (long)sms * per_sm;
-    return (int)(g < ntiles ? g : ntiles);
+    const int cap = scan_capacity(err_out);
+    if (*err_out || cap < 1) return 0;
+    const long ntiles = (long)((H + TR - 1) / TR) * ((W + TC - 1) / TC);
+    const long tpc = (ntiles + cap - 1) / cap;
+    return (int)((ntiles + tpc - 1) / tpc);
 }
 
 cudaError_t launch_scan(const ScanArgs &a, int grid, cudaStream_t s) {
@@ -518,16 +557,22 @@ cudaError_t launch_scan(const ScanArgs &a, int grid, cudaStream_t s) {
     const ScanArgs *tab = nullptr;
     const int *bc = nullptr;
     void *args[] = {&copy, &tab, &bc};
+    cudaError_t e = cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SCAN_SMEM);
+    if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((const void *)k_scan, dim3(grid), dim3(SCAN_THREADS), args,
-                                       0, s);
+                                       SCAN_SMEM, s);
 }
 
 cudaError_t launch_scan_multi(const ScanArgs *tab, const int *block_clip, int grid,
                               cudaStream_t s) {
     ScanArgs none{};
     void *args[] = {&none, &tab, &block_clip};
+    cudaError_t e = cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SCAN_SMEM);
+    if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((const void *)k_scan, dim3(grid), dim3(SCAN_THREADS), args,
-                                       0, s);
+                                       SCAN_SMEM, s);
 }
 
 int scan_capacity(int *err_out) {
@@ -535,7 +580,11 @@ int scan_capacity(int *err_out) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan, SCAN_THREADS, 0);
+        e = cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)SCAN_SMEM);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan, SCAN_THREADS,
+                                                          SCAN_SMEM);
     if (e != cudaSuccess) { *err_out = (int)e; return 0; }
     *err_out = 0;
     return sms * per_sm;

@@ -205,9 +205,7 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     SCPL_CUDA(h, h->S2.ensure(spx * sizeof(uint32_t)));
     h->e0cap = keep_e0 ? std::min(T, E0_PLANES) : 0;
     if (h->e0cap) SCPL_CUDA(h, h->E0.ensure((size_t)h->e0cap * hw * sizeof(int32_t)));
-    if (A) SCPL_CUDA(h, h->partA.ensure((size_t)T * G * sizeof(long long) + (size_t)T * 12));
-    SCPL_CUDA(h, h->partA.ensure((size_t)T * G * sizeof(long long)));
-    SCPL_CUDA(h, h->partM.ensure((size_t)T * G * sizeof(int)));
+    SCPL_CUDA(h, h->partA.ensure((size_t)T * 24));   // A_t, then M_t, then diagnostics
     SCPL_CUDA(h, h->count.ensure((size_t)T * sizeof(unsigned)));
     SCPL_CUDA(h, h->starts.ensure((size_t)(T + 1) * sizeof(int)));
     SCPL_CUDA(h, h->nbuf.ensure(sizeof(int)));
@@ -215,13 +213,15 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     SCPL_CUDA(h, h->h_small.ensure((size_t)(T + 4) * sizeof(int)));
     cudaStream_t s = h->stream;
     SCPL_CUDA(h, cudaMemsetAsync(h->count.p, 0, (size_t)T * sizeof(unsigned), s));
+    SCPL_CUDA(h, cudaMemsetAsync(h->partA.p, 0, (size_t)T * 12, s));
     SCPL_CUDA(h, cudaMemsetAsync(h->errw.p, 0, sizeof(int), s));
     ScanArgs a;
     a.rgb = frames; a.T = T; a.H = H; a.W = W; a.ypitch = ypitch;
     a.Y = h->Y.as<uint8_t>(); a.D = h->D.as<uint8_t>();
     a.ering = h->ering.as<uint16_t>();
     a.S1 = h->S1.as<uint32_t>(); a.S2 = h->S2.as<uint32_t>();
-    a.partA = h->partA.as<long long>(); a.partM = h->partM.as<int>();
+    a.partA = h->partA.as<long long>();
+    a.partM = reinterpret_cast<int *>(h->partA.as<char>() + (size_t)T * 8);
     a.count = h->count.as<unsigned>();
     a.starts = h->starts.as<int>(); a.n_buffers = h->nbuf.as<int>();
     a.err = h->errw.as<int>();
@@ -234,9 +234,9 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     a.e0_plane = hw;
     a.A_out = nullptr;
     a.M_out = nullptr;
-    if (A) {   // diagnostics after the partial sums in the same allocation
-        a.A_out = reinterpret_cast<long long *>(h->partA.as<char>() + (size_t)T * G * 8);
-        a.M_out = reinterpret_cast<int *>(a.A_out + T);
+    if (A) {   // diagnostics after the accumulators in the same allocation
+        a.A_out = reinterpret_cast<long long *>(h->partA.as<char>() + (size_t)T * 16);
+        a.M_out = reinterpret_cast<int *>(h->partA.as<char>() + (size_t)T * 12);
     }
     SCPL_CUDA(h, timed(h, K_SCAN, [&] { return launch_scan(a, G, s); }));
     if (h->prof.on) h->prof.bytes[K_SCAN] += 28.0 * hw * T;

@@ -153,8 +153,8 @@ struct ScanArgs {
     uint8_t *Y, *D;         // [T][H][ypitch]
     uint16_t *ering;        // [2][scan_state_px] energy of the last two frames (tile-major)
     uint32_t *S1, *S2;      // [scan_state_px] sums of e and e^2 over the open buffer (tile-major)
-    long long *partA;       // [T][G] per-CTA partial ASDE sums
-    int *partM;             // [T][G] per-CTA partial energy maxima
+    long long *partA;       // [T] A_t accumulated over the clip's CTAs (zeroed)
+    int *partM;             // [T] maximum e_t over the clip's CTAs (zeroed)
     unsigned *count;        // [T] CTAs that published frame t
     int *starts;            // [T+1] buffer starts (device)
     int *n_buffers;         // device scalar
