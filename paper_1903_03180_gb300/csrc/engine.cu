@@ -99,8 +99,8 @@ size_t scan_state_bytes(const PassDims &d) {
     const size_t spx = (size_t)scan_state_px(d.H, d.W);
     const size_t G = (size_t)scan_tiles(d.H, d.W);
     (void)G;
-    return a256(2 * spx * 2) + 2 * a256(spx * 4) + a256((size_t)(d.T + 1) * 4) +
-           a256((size_t)d.T * 16 + 8);
+    return a256((size_t)SCAN_FW * spx * 2) + 2 * a256(spx * 4) + a256((size_t)(d.T + 1) * 4) +
+           a256((size_t)d.T * (8 * SCAN_FW + 8) + 8);
 }
 // Buffers of a pass whose summed energy the scan keeps (more are summed by
 // k_energy_init from the luma and motion maps).
@@ -512,8 +512,8 @@ scpl_status launch_wave(Srv *s) {
     std::vector<size_t> cnt_off(n);
     size_t cnt_bytes = 0;
     for (int i = 0; i < n; ++i) {
-        cnt_off[i] = cnt_bytes;   // A [T] int64, M [T] int32, count [T] uint32
-        cnt_bytes += (size_t)s->passes[take[i]].d.T * 16;
+        cnt_off[i] = cnt_bytes;   // A [T][SCAN_FW] int64, M [T] int32, count [T] uint32
+        cnt_bytes += (size_t)s->passes[take[i]].d.T * (8 * SCAN_FW + 8);
     }
     const size_t zero_bytes = a256(o + cnt_bytes);
     o = zero_bytes;
@@ -558,15 +558,15 @@ scpl_status launch_wave(Srv *s) {
         a.D = Gr.ypool + ((size_t)Gr.T_total + P.frame_off) * P.d.H * Gr.ypitch;
         const size_t spx = (size_t)scan_state_px(P.d.H, P.d.W);
         a.ering = reinterpret_cast<uint16_t *>(q);
-        q += a256(2 * spx * 2);
+        q += a256((size_t)SCAN_FW * spx * 2);
         a.S1 = reinterpret_cast<uint32_t *>(q);
         q += a256(spx * 4);
         a.S2 = reinterpret_cast<uint32_t *>(q);
         q += a256(spx * 4);
         char *acc = base + a256((size_t)n * 8) + cnt_off[i];
         a.partA = reinterpret_cast<long long *>(acc);
-        a.partM = reinterpret_cast<int *>(acc + (size_t)P.d.T * 8);
-        a.count = reinterpret_cast<unsigned *>(acc + (size_t)P.d.T * 12);
+        a.partM = reinterpret_cast<int *>(acc + (size_t)P.d.T * 8 * SCAN_FW);
+        a.count = reinterpret_cast<unsigned *>(acc + (size_t)P.d.T * (8 * SCAN_FW + 4));
         a.starts = reinterpret_cast<int *>(q);
         q += a256((size_t)(P.d.T + 1) * 4);
         a.n_buffers = reinterpret_cast<int *>(q);

@@ -2,21 +2,16 @@
 // (Sec. 3.2, Eq. 7-9).
 //
 // k_scan is one persistent cooperative launch over the whole clip.  Each CTA
-// owns a fixed set of 8x128 pixel tiles for the whole clip, and each thread a
-// quad of 4 pixels in every tile.  For every frame t it
-//   (1) computes luma, the Sobel gradient (4 pixels at once in u16x2 lanes),
-//       the frame difference and the energy e_t of its tiles (independent of
-//       any buffer decision) and writes Y_t and D_t; e_t stays in registers
-//       when the CTA owns at most MAXT tiles;
-//   (2) waits until every CTA has published its partial sums for frame t-1,
-//       reduces them and takes the buffer decision for t-1 (every CTA takes
-//       the same decision from the same integers);
-//   (3) folds e_{t-1} into its running sums S1, S2 as that decision says, and
-//       publishes its partial A_t = sum floor(sqrt(65536 (n S2 - S1^2))) with
-//       frame t added, plus the partial maximum of e_t.  When the decision
-//       closes a buffer, S1 (its summed energy, the uniform energy map of
-//       Sec. 3.2) is written out for the carving stage.
-// Step (1) of frame t overlaps the device-wide reduction of frame t-1.
+// owns a fixed block of 8x128 pixel tiles for the whole clip, and each thread
+// a quad of 4 pixels in every tile.  For every frame it computes luma, the
+// Sobel gradient (4 pixels at once in u16x2 lanes), the frame difference and
+// the energy e_t (written out as Y_t and D_t), folds e_t into the running sums
+// S1, S2 of the open buffer and adds its share of
+// A_t = sum floor(sqrt(65536 (n S2 - S1^2))) to the clip's accumulator.  The
+// decisions of Eq. 9 need every CTA's share, so frames are taken in rounds
+// with one device-wide wait per round (see k_scan below).  When a decision
+// closes a buffer, its S1 (the summed energy, the uniform energy map of
+// Sec. 3.2) is written out for the carving stage.
 //
 // Several clips can share one launch: a table gives each clip its own range
 // of CTAs, and the waits and reductions above then run among that range only.
@@ -127,57 +122,39 @@ __device__ int decide(DecState &s, long long A, long long emax, int t, const Sca
     return DEC_JOIN;
 }
 
-// Warp 0 waits until every CTA of the clip has added its partial sums of frame
-// t to the clip's accumulators, then decides.  Returns false (and sets the
-// status word) if the wait ran out of time or another CTA gave up.
-__device__ bool wait_and_decide(const ScanArgs &a, int t, int G, DecState &s, int *dec_out) {
-    __shared__ int s_ok;
-    if (threadIdx.x < 32) {
-        int lane = threadIdx.x;
-        int ok = 1;
-        if (lane == 0) {
-            unsigned long long t0 = globaltimer_ns();
-            while (ld_acquire_u32(&a.count[t]) < (unsigned)G) {
-                if (*(volatile int *)a.err != DEV_OK) { ok = 0; break; }
-                if (globaltimer_ns() - t0 > a.spin_limit_ns) {
-                    atomicCAS(a.err, DEV_OK, DEV_ETIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
-            }
+// Thread 0 waits until every CTA of the clip has published round r.  Returns
+// false (and sets the status word) if the wait ran out of time or another CTA
+// gave up.
+__device__ bool wait_round(const ScanArgs &a, int r, int G) {
+    if (ld_acquire_u32(&a.count[r]) >= (unsigned)G) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (ld_acquire_u32(&a.count[r]) < (unsigned)G) {
+        if (*(volatile int *)a.err != DEV_OK) return false;
+        if (globaltimer_ns() - t0 > a.spin_limit_ns) {
+            atomicCAS(a.err, DEV_OK, DEV_ETIMEOUT);
+            return false;
         }
-        ok = __shfl_sync(0xffffffffu, ok, 0);
-        if (ok && lane == 0) {
-            __threadfence();
-            const long long A = (long long)__ldcg(
-                reinterpret_cast<const unsigned long long *>(&a.partA[t]));
-            const int m = __ldcg(&a.partM[t]);
-            const bool first = blockIdx.x == (unsigned)a.cta0;
-            if (first && a.A_out) {
-                a.A_out[t] = A;
-                a.M_out[t] = m;
-            }
-            *dec_out = decide(s, A, m, t, a, first);
-        }
-        if (lane == 0) s_ok = ok;
+        __nanosleep(32);
     }
-    __syncthreads();
-    return s_ok != 0;
+    return true;
 }
 
-// floor(sqrt(x)) for x < 2^53 without loops: a single-precision estimate
-// (off by a few units at most), one Newton step on the exact integer residual,
-// then a final correction by one.  Every float operation is correctly rounded.
+// floor(sqrt(x)) for x < 2^53 without loops.  A hardware square-root
+// estimate (relative error below 2^-22) is off by a few units at most; one
+// Newton step on the exact integer residual, with an approximate reciprocal,
+// lands within one of the answer, and a final exact correction by one each
+// way settles it.  Only the correction decides the result, so the estimates
+// need no particular rounding.
 __device__ __forceinline__ uint32_t isqrt53(unsigned long long x) {
-    const float sf = __fsqrt_rn(__ull2float_rn(x));
-    const uint32_t r0 = __float2uint_rz(sf);
-    const long long R = (long long)x - (long long)r0 * (long long)r0;
-    const float d = __fmul_rn(__ll2float_rn(R), __fdiv_rn(0.5f, __uint2float_rn(r0 > 0 ? r0 : 1)));
-    unsigned long long r = (unsigned long long)((long long)r0 + __float2ll_rd(d));
-    r -= (r * r > x) ? 1ull : 0ull;
-    r += ((r + 1) * (r + 1) <= x) ? 1ull : 0ull;
-    return (uint32_t)r;
+    const float xf = __ull2float_rz(x);
+    const float r0f = xf > 0.0f ? xf * rsqrtf(xf) : 0.0f;
+    const uint32_t r0 = __float2uint_rz(r0f);
+    const long long R = (long long)x - (long long)((unsigned long long)r0 * r0);
+    const float d = __ll2float_rz(R) * __frcp_rz(2.0f * fmaxf(r0f, 1.0f));
+    uint32_t r = r0 + (uint32_t)__float2int_rd(d);
+    r -= ((unsigned long long)r * r > x) ? 1u : 0u;
+    r += ((unsigned long long)(r + 1) * (r + 1) <= x) ? 1u : 0u;
+    return r;
 }
 
 // Packed u16x2 helpers for the 4 pixels of a thread: lane 0 = pixels 0 and 2,
@@ -223,20 +200,23 @@ struct TileCtx {
 
 __device__ __forceinline__ TileCtx tile_ctx(const ScanArgs &a, int tile, int tiles_x, int tid) {
     TileCtx c;
-    c.r0 = (tile / tiles_x) * TR;
-    c.c0 = (tile % tiles_x) * TC;
+    const int ty = tile / tiles_x;
+    c.r0 = ty * TR;
+    c.c0 = (tile - ty * tiles_x) * TC;
     c.row = c.r0 + (tid >> 5);
     c.col = c.c0 + 4 * (tid & 31);
     c.nvalid = c.row < a.H ? max(0, min(4, a.W - c.col)) : 0;
     return c;
 }
 
+// Luma of 4 pixels from their 12 RGB bytes (R G B R | G B R G | B R G B):
+// one byte dot product per pixel with the weights (77, 150, 29, 0).
 __device__ __forceinline__ uint32_t luma4(uint32_t w0, uint32_t w1, uint32_t w2) {
-    // 12 bytes = pixels p0..p3 as R G B R | G B R G | B R G B
-    const uint32_t y0 = (77u * (w0 & 0xFF) + 150u * ((w0 >> 8) & 0xFF) + 29u * ((w0 >> 16) & 0xFF) + 128u) >> 8;
-    const uint32_t y1 = (77u * (w0 >> 24) + 150u * (w1 & 0xFF) + 29u * ((w1 >> 8) & 0xFF) + 128u) >> 8;
-    const uint32_t y2 = (77u * ((w1 >> 16) & 0xFF) + 150u * (w1 >> 24) + 29u * (w2 & 0xFF) + 128u) >> 8;
-    const uint32_t y3 = (77u * ((w2 >> 8) & 0xFF) + 150u * ((w2 >> 16) & 0xFF) + 29u * (w2 >> 24) + 128u) >> 8;
+    constexpr uint32_t K = 77u | (150u << 8) | (29u << 16);
+    const uint32_t y0 = __dp4a(w0, K, 128u) >> 8;
+    const uint32_t y1 = __dp4a(__byte_perm(w0, w1, 0x0543), K, 128u) >> 8;
+    const uint32_t y2 = __dp4a(__byte_perm(w1, w2, 0x0432), K, 128u) >> 8;
+    const uint32_t y3 = __dp4a(w2 >> 8, K, 128u) >> 8;
     return y0 | (y1 << 8) | (y2 << 16) | (y3 << 24);
 }
 
@@ -284,6 +264,16 @@ __device__ __forceinline__ void load_luma(const ScanArgs &a, const uint8_t *f, i
 
 // One clip per launch (tab == NULL, every CTA works on a0) or one clip per
 // range of CTAs (clip of CTA x = tab[block_clip[x]], CTAs [cta0, cta0 + G)).
+//
+// Rounds: a round takes the next frames [t, w] (at most SCAN_FW, never past
+// the frame where the open buffer reaches t_max, never past T - 1) and folds
+// each into S1/S2 as if it joined the open buffer, publishing every frame's
+// A_t.  After one device-wide wait every CTA replays the decisions of Eq. 9 in
+// frame order on the same integers.  Up to the first frame that exceeds the
+// threshold the guess was right.  At that frame f a new buffer starts: the
+// closed buffer's sum is S1 minus the energies of frames f..w, S1/S2 restart
+// from e_f, and the next round re-evaluates frames f+1..w from their stored
+// energies.
 __global__ void __launch_bounds__(SCAN_THREADS, 4)
 k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ block_clip) {
     extern __shared__ __align__(16) uint4 sstate[];   // [MAXT][2][SCAN_THREADS] S1, S2
@@ -292,7 +282,8 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
     __shared__ unsigned long long red_a[SCAN_THREADS / 32];
     __shared__ uint32_t red_m[SCAN_THREADS / 32];
     __shared__ DecState st;
-    __shared__ int s_dec;
+    __shared__ int s_ok, s_ndec, s_last;
+    __shared__ uint32_t s_rc[64];   // origins (r0 << 16 | c0) of the CTA's first 64 tiles
 
     const int tid = threadIdx.x;
     if (tid == 0) {
@@ -304,7 +295,6 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
             a.G = gridDim.x;
         }
         st.n = 0; st.M = 0; st.start = 0; st.nb = 0;
-        s_dec = DEC_JOIN;
     }
     __syncthreads();
     const int G = a.G;
@@ -317,17 +307,33 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
     const bool resident = tpc <= MAXT;
     const long hw3 = (long)a.H * a.W * 3;
     const long yplane = (long)a.H * a.ypitch;
-
-    // registers of the resident path: energy (u16x2 pairs) and luma quad of the
-    // previous and the current frame for each owned tile
-    uint32_t ep02[MAXT], ep13[MAXT], yp[MAXT], ec02[MAXT], ec13[MAXT];
+    const long eslot = (long)ntiles * SCAN_THREADS;   // uint2 entries per ring slot
+    uint2 *ering = reinterpret_cast<uint2 *>(a.ering);  // [SCAN_FW][ntiles][256] e quads
+    for (int k = tid; k < min(mine, 64); k += SCAN_THREADS) {
+        const int ty = (first + k) / tiles_x;
+        s_rc[k] = ((uint32_t)(ty * TR) << 16) | (uint32_t)((first + k - ty * tiles_x) * TC);
+    }
+    __syncthreads();
+    // the geometry of the CTA's k-th tile for this thread
+    auto ctx = [&](int k) {
+        if (k >= 64) return tile_ctx(a, first + k, tiles_x, tid);
+        TileCtx c;
+        c.r0 = (int)(s_rc[k] >> 16);
+        c.c0 = (int)(s_rc[k] & 0xFFFFu);
+        c.row = c.r0 + (tid >> 5);
+        c.col = c.c0 + 4 * (tid & 31);
+        c.nvalid = c.row < a.H ? max(0, min(4, a.W - c.col)) : 0;
+        return c;
+    };
+    uint32_t yp[MAXT];   // resident path: previous frame's luma quad per tile
 #pragma unroll
-    for (int k = 0; k < MAXT; ++k) ep02[k] = ep13[k] = yp[k] = ec02[k] = ec13[k] = 0;
+    for (int k = 0; k < MAXT; ++k) yp[k] = 0;
 
-    // phase A of one tile: energy of frame t, luma and motion written out
-    auto phase_a = [&](int t, int tile, uint32_t &e02, uint32_t &e13, uint32_t &yprev,
-                       uint32_t &emax2) {
-        const TileCtx c = tile_ctx(a, tile, tiles_x, tid);
+    // energy of frame t on one tile: luma and motion written out, the e quad
+    // (u16x2 pairs) stored in the ring
+    auto phase_a = [&](int t, int k, uint32_t &yprev, uint32_t &emax2) {
+        const int tile = first + k;
+        const TileCtx c = ctx(k);
         const uint8_t *f = a.rgb + (long)t * hw3;
         load_luma(a, f, c.r0, c.c0, lum);
         __syncthreads();
@@ -343,8 +349,8 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
             yprv = *reinterpret_cast<const uint32_t *>(a.Y + (long)(t - 1) * yplane +
                                                        (long)c.row * a.ypitch + c.col);
         const uint32_t dq = t > 0 ? __vabsdiffu4(ycur, yprv) : 0u;
-        e02 = (uint32_t)a.wg * g02 + (uint32_t)a.wm * even16(dq);
-        e13 = (uint32_t)a.wg * g13 + (uint32_t)a.wm * odd16(dq);
+        const uint32_t e02 = (uint32_t)a.wg * g02 + (uint32_t)a.wm * even16(dq);
+        const uint32_t e13 = (uint32_t)a.wg * g13 + (uint32_t)a.wm * odd16(dq);
         if (c.nvalid > 0) {
             // invalid pixels of a ragged quad do not count towards the maximum
             const uint32_t m02 = c.nvalid >= 3 ? e02 : (e02 & 0xFFFFu);
@@ -354,60 +360,52 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
             *reinterpret_cast<uint32_t *>(a.Y + yo) = ycur;
             *reinterpret_cast<uint32_t *>(a.D + yo) = dq;
         }
+        ering[(long)(t % SCAN_FW) * eslot + (long)tile * SCAN_THREADS + tid] = make_uint2(e02, e13);
         yprev = ycur;
         __syncthreads();   // lum is reused by the next tile
     };
 
-    // phase B of one tile: fold e_{t-1} into S1/S2 as the decision says, add
-    // e_t, accumulate floor(sqrt(65536 (n S2 - S1^2))) of the valid pixels
-    auto phase_b = [&](int t, int tile, int slot, int dec, int n1, int nb_closed, uint32_t pe02,
-                       uint32_t pe13, uint32_t ce02, uint32_t ce13, unsigned long long &acc) {
-        const TileCtx c = tile_ctx(a, tile, tiles_x, tid);
-        uint4 *S1p, *S2p;
+    auto state_ptrs = [&](int k, int tile, uint4 *&S1p, uint4 *&S2p) {
         if (resident) {
-            S1p = &sstate[(slot * 2) * SCAN_THREADS + tid];
-            S2p = &sstate[(slot * 2 + 1) * SCAN_THREADS + tid];
+            S1p = &sstate[(k * 2) * SCAN_THREADS + tid];
+            S2p = &sstate[(k * 2 + 1) * SCAN_THREADS + tid];
         } else {
             const long sidx = (long)tile * SCAN_THREADS + tid;
             S1p = reinterpret_cast<uint4 *>(a.S1) + sidx;
             S2p = reinterpret_cast<uint4 *>(a.S2) + sidx;
         }
+    };
+
+    // fold frame t into S1/S2 of one tile (restart when `fresh`) and add its
+    // floor(sqrt(65536 (n S2 - S1^2))) over the valid pixels to acc
+    auto fold = [&](int t, int k, int tile, bool fresh, int n1, unsigned long long &acc) {
+        const TileCtx c = ctx(k);
+        uint4 *S1p, *S2p;
+        state_ptrs(k, tile, S1p, S2p);
+        const uint2 e = ering[(long)(t % SCAN_FW) * eslot + (long)tile * SCAN_THREADS + tid];
+        const uint32_t ev[4] = {e.x & 0xFFFFu, e.y & 0xFFFFu, e.x >> 16, e.y >> 16};
         uint4 s1 = make_uint4(0, 0, 0, 0), s2 = make_uint4(0, 0, 0, 0);
-        if (t > 0) {
+        if (!fresh) {
             s1 = *S1p;
             s2 = *S2p;
-            const uint32_t ep[4] = {pe02 & 0xFFFFu, pe13 & 0xFFFFu, pe02 >> 16, pe13 >> 16};
-            uint32_t *S1v = &s1.x, *S2v = &s2.x;
-            // the buffer that the decision closed: its summed energy
-            const bool closing = dec != DEC_JOIN && a.E0 && nb_closed - 1 < a.nbcap;
+        }
+        uint32_t *S1v = &s1.x, *S2v = &s2.x;
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                if (closing && v < c.nvalid)
-                    a.E0[(long)(nb_closed - 1) * a.e0_plane + (long)c.row * a.W + c.col + v] =
-                        (int32_t)(dec == DEC_CLOSE ? S1v[v] + ep[v] : S1v[v]);
-                if (dec == DEC_JOIN) { S1v[v] += ep[v]; S2v[v] += ep[v] * ep[v]; }
-                else if (dec == DEC_FLUSH) { S1v[v] = ep[v]; S2v[v] = ep[v] * ep[v]; }
-                else { S1v[v] = 0; S2v[v] = 0; }
+        for (int v = 0; v < 4; ++v) {
+            S1v[v] += ev[v];
+            S2v[v] += ev[v] * ev[v];
+            if (v < c.nvalid) {
+                const unsigned long long Q =
+                    (unsigned long long)n1 * S2v[v] - (unsigned long long)S1v[v] * S1v[v];
+                acc += isqrt53(Q << 16);
             }
         }
         *S1p = s1;
         *S2p = s2;
-        const uint32_t ec[4] = {ce02 & 0xFFFFu, ce13 & 0xFFFFu, ce02 >> 16, ce13 >> 16};
-        const uint32_t *S1v = &s1.x, *S2v = &s2.x;
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            if (v < c.nvalid) {
-                const unsigned long long a1 = S1v[v] + ec[v];
-                const unsigned long long a2 = (unsigned long long)S2v[v] + ec[v] * ec[v];
-                const unsigned long long Q = (unsigned long long)n1 * a2 - a1 * a1;
-                acc += isqrt53(Q << 16);
-            }
-        }
     };
 
-    // the CTA's partial sums of frame t into the clip's accumulators
-    auto publish = [&](int t, unsigned long long acc, uint32_t emax2) {
-        uint32_t em = max(emax2 & 0xFFFFu, emax2 >> 16);
+    // block sum of acc and maximum of emax2 (thread 0 receives them)
+    auto block_reduce = [&](unsigned long long &acc, uint32_t &em) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             acc += __shfl_xor_sync(0xffffffffu, acc, o);
@@ -419,110 +417,131 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
             unsigned long long A = 0;
             uint32_t m = 0;
             for (int w = 0; w < SCAN_THREADS / 32; ++w) { A += red_a[w]; m = max(m, red_m[w]); }
-            atomicAdd(reinterpret_cast<unsigned long long *>(&a.partA[t]), A);
-            atomicMax(&a.partM[t], (int)m);
-            __threadfence();
-            atomicAdd(&a.count[t], 1u);
+            acc = A;
+            em = m;
         }
         __syncthreads();
     };
 
-    uint16_t *ering = a.ering;   // non-resident path: [2][ntiles][256][4]
-    const long eslot = (long)ntiles * SCAN_THREADS * 4;
-
-    for (int t = 0; t < a.T; ++t) {
-        // ---- (1) energy of frame t on this CTA's tiles ----------------------
-        uint32_t emax2 = 0;
-        if (resident) {
-#pragma unroll
-            for (int k = 0; k < MAXT; ++k)
-                if (k < mine) phase_a(t, first + k, ec02[k], ec13[k], yp[k], emax2);
-        } else {
-            for (int k = 0; k < mine; ++k) {
-                uint32_t e02, e13, ydummy = 0;
-                phase_a(t, first + k, e02, e13, ydummy, emax2);
-                const long sidx = (long)(first + k) * SCAN_THREADS + tid;
-                reinterpret_cast<uint2 *>(ering + (long)(t & 1) * eslot)[sidx] = make_uint2(e02, e13);
-            }
-        }
-
-        // ---- (2) buffer decision for frame t-1 -------------------------------
-        if (t > 0) {
-            if (!wait_and_decide(a, t - 1, G, st, &s_dec)) return;
-        }
-        const int dec = s_dec;
-        const int n1 = st.n + 1;
-        const int nbc = st.nb;
-
-        // ---- (3) fold e_{t-1} into S1/S2, partial A_t ------------------------
-        unsigned long long acc = 0;
-        if (resident) {
-#pragma unroll
-            for (int k = 0; k < MAXT; ++k)
-                if (k < mine) {
-                    phase_b(t, first + k, k, dec, n1, nbc, ep02[k], ep13[k], ec02[k], ec13[k], acc);
-                    ep02[k] = ec02[k];
-                    ep13[k] = ec13[k];
-                }
-        } else {
-            for (int k = 0; k < mine; ++k) {
-                const long sidx = (long)(first + k) * SCAN_THREADS + tid;
-                const uint2 cur = reinterpret_cast<const uint2 *>(ering + (long)(t & 1) * eslot)[sidx];
-                uint2 prv = make_uint2(0, 0);
-                if (t > 0)
-                    prv = reinterpret_cast<const uint2 *>(ering + (long)((t + 1) & 1) * eslot)[sidx];
-                phase_b(t, first + k, 0, dec, n1, nbc, prv.x, prv.y, cur.x, cur.y, acc);
-            }
-        }
-        publish(t, acc, emax2);
-    }
-
-    // decision for the last frame, then close the open buffer
-    if (!wait_and_decide(a, a.T - 1, G, st, &s_dec)) return;
-    const int dec = s_dec;
-    // summed energy of the buffers this last decision closed or left open
-    if (a.E0) {
-        const int nb = st.nb;   // buffers closed so far (after this decision)
+    // summed energy of buffer bi (the E0 plane) for the valid pixels of my tiles:
+    // S1 minus the ring energies of frames [g0, g1)
+    auto write_e0 = [&](int bi, int g0, int g1) {
+        if (!a.E0 || bi >= a.nbcap) return;
         for (int k = 0; k < mine; ++k) {
             const int tile = first + k;
-            const TileCtx c = tile_ctx(a, tile, tiles_x, tid);
+            const TileCtx c = ctx(k);
             if (c.nvalid == 0) continue;
-            uint32_t pe02 = 0, pe13 = 0;
-            uint4 s1;
-            if (resident) {
-                // registers hold e_{T-1}; pick the tile's entry without dynamic indexing
-#pragma unroll
-                for (int q = 0; q < MAXT; ++q)
-                    if (q == k) { pe02 = ep02[q]; pe13 = ep13[q]; }
-                s1 = sstate[(k * 2) * SCAN_THREADS + tid];
-            } else {
-                const long sidx = (long)tile * SCAN_THREADS + tid;
-                const uint2 v = reinterpret_cast<const uint2 *>(
-                    ering + (long)((a.T - 1) & 1) * eslot)[sidx];
-                pe02 = v.x; pe13 = v.y;
-                s1 = reinterpret_cast<const uint4 *>(a.S1)[sidx];
+            uint4 *S1p, *S2p;
+            state_ptrs(k, tile, S1p, S2p);
+            uint4 s1 = *S1p;
+            uint32_t *S1v = &s1.x;
+            for (int g = g0; g < g1; ++g) {
+                const uint2 e = ering[(long)(g % SCAN_FW) * eslot + (long)tile * SCAN_THREADS + tid];
+                S1v[0] -= e.x & 0xFFFFu;
+                S1v[1] -= e.y & 0xFFFFu;
+                S1v[2] -= e.x >> 16;
+                S1v[3] -= e.y >> 16;
             }
-            const uint32_t ep[4] = {pe02 & 0xFFFFu, pe13 & 0xFFFFu, pe02 >> 16, pe13 >> 16};
-            const uint32_t S1v[4] = {s1.x, s1.y, s1.z, s1.w};
-            // JOIN: the open buffer ends with frame T-1.  FLUSH: the previous
-            // buffer closed before T-1, which is a buffer of its own.  CLOSE:
-            // the buffer ending with T-1 closed at t_max.
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                if (v >= c.nvalid) continue;
-                const long px = (long)c.row * a.W + c.col + v;
-                if (dec == DEC_JOIN) {
-                    if (nb < a.nbcap) a.E0[(long)nb * a.e0_plane + px] = (int32_t)(S1v[v] + ep[v]);
-                } else if (dec == DEC_FLUSH) {
-                    if (nb - 1 < a.nbcap) a.E0[(long)(nb - 1) * a.e0_plane + px] = (int32_t)S1v[v];
-                    if (nb < a.nbcap) a.E0[(long)nb * a.e0_plane + px] = (int32_t)ep[v];
+            for (int v = 0; v < 4; ++v)
+                if (v < c.nvalid)
+                    a.E0[(long)bi * a.e0_plane + (long)c.row * a.W + c.col + v] = (int32_t)S1v[v];
+        }
+    };
+
+    int t = 0, horizon = 0, r = 0;
+    while (t < a.T) {
+        // the round's frames: up to SCAN_FW, ending where the open buffer
+        // would reach t_max, and at the clip end
+        const int n0 = st.n;
+        int w = min(t + SCAN_FW - 1, a.T - 1);
+        w = min(w, t + (a.t_max - n0) - 1);
+        for (int f = t; f <= w; ++f) {
+            uint32_t emax2 = 0;
+            const bool fresh_frame = f >= horizon;
+            if (fresh_frame) {
+                if (resident) {
+#pragma unroll
+                    for (int k = 0; k < MAXT; ++k)
+                        if (k < mine) phase_a(f, k, yp[k], emax2);
                 } else {
-                    if (nb - 1 < a.nbcap)
-                        a.E0[(long)(nb - 1) * a.e0_plane + px] = (int32_t)(S1v[v] + ep[v]);
+                    for (int k = 0; k < mine; ++k) {
+                        uint32_t ydummy = 0;
+                        phase_a(f, k, ydummy, emax2);
+                    }
                 }
             }
+            unsigned long long acc = 0;
+            const bool fresh = n0 == 0 && f == t;   // the open buffer starts here
+            const int n1 = n0 + (f - t) + 1;
+            if (resident) {
+#pragma unroll
+                for (int k = 0; k < MAXT; ++k)
+                    if (k < mine) fold(f, k, first + k, fresh, n1, acc);
+            } else {
+                for (int k = 0; k < mine; ++k) fold(f, k, first + k, fresh, n1, acc);
+            }
+            uint32_t em = max(emax2 & 0xFFFFu, emax2 >> 16);
+            block_reduce(acc, em);
+            if (tid == 0) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(&a.partA[(long)r * SCAN_FW + (f - t)]),
+                          acc);
+                if (fresh_frame) atomicMax(&a.partM[f], (int)em);
+            }
         }
+        horizon = max(horizon, w + 1);
+        // publish the round, wait for the clip's other CTAs, replay decisions
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(&a.count[r], 1u);
+            int ok = wait_round(a, r, G) ? 1 : 0;
+            int ndec = 0, last = DEC_JOIN;
+            if (ok) {
+                __threadfence();
+                const bool lead = lb == 0;
+                for (int f = t; f <= w; ++f) {
+                    const long long A = (long long)__ldcg(reinterpret_cast<const unsigned long long *>(
+                        &a.partA[(long)r * SCAN_FW + (f - t)]));
+                    const int m = __ldcg(&a.partM[f]);
+                    if (lead && a.A_out) {
+                        a.A_out[f] = A;
+                        a.M_out[f] = m;
+                    }
+                    last = decide(st, A, m, f, a, lead);
+                    ++ndec;
+                    if (last == DEC_FLUSH) break;
+                }
+            }
+            s_ok = ok;
+            s_ndec = ndec;
+            s_last = last;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        const int fend = t + s_ndec;   // first frame not yet decided
+        if (s_last == DEC_FLUSH) {
+            // frame fend-1 starts a new buffer: the closed one is S1 minus the
+            // energies of frames fend-1..w; S1/S2 restart from e_{fend-1}
+            const int f = fend - 1;
+            write_e0(st.nb - 1, f, w + 1);
+            for (int k = 0; k < mine; ++k) {
+                const int tile = first + k;
+                uint4 *S1p, *S2p;
+                state_ptrs(k, tile, S1p, S2p);
+                const uint2 e = ering[(long)(f % SCAN_FW) * eslot + (long)tile * SCAN_THREADS + tid];
+                const uint32_t ev[4] = {e.x & 0xFFFFu, e.y & 0xFFFFu, e.x >> 16, e.y >> 16};
+                *S1p = make_uint4(ev[0], ev[1], ev[2], ev[3]);
+                *S2p = make_uint4(ev[0] * ev[0], ev[1] * ev[1], ev[2] * ev[2], ev[3] * ev[3]);
+            }
+        } else if (s_last == DEC_CLOSE) {
+            write_e0(st.nb - 1, w + 1, w + 1);   // the buffer ending with frame w
+        }
+        __syncthreads();
+        t = fend;
+        ++r;
     }
+    // the buffer still open at the clip end
+    if (st.n > 0) write_e0(st.nb, a.T, a.T);
     if (lb == 0 && tid == 0) {
         int nb = st.nb;
         if (st.n > 0) a.starts[nb++] = st.start;

@@ -200,12 +200,14 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     SCPL_CUDA(h, h->Y.ensure((size_t)T * H * ypitch));
     SCPL_CUDA(h, h->D.ensure((size_t)T * H * ypitch));
     const size_t spx = (size_t)scan_state_px(H, W);
-    SCPL_CUDA(h, h->ering.ensure(2 * spx * sizeof(uint16_t)));
+    SCPL_CUDA(h, h->ering.ensure((size_t)SCAN_FW * spx * sizeof(uint16_t)));
     SCPL_CUDA(h, h->S1.ensure(spx * sizeof(uint32_t)));
     SCPL_CUDA(h, h->S2.ensure(spx * sizeof(uint32_t)));
     h->e0cap = keep_e0 ? std::min(T, E0_PLANES) : 0;
     if (h->e0cap) SCPL_CUDA(h, h->E0.ensure((size_t)h->e0cap * hw * sizeof(int32_t)));
-    SCPL_CUDA(h, h->partA.ensure((size_t)T * 24));   // A_t, then M_t, then diagnostics
+    // per-round A_t [T][SCAN_FW], frame maxima [T], then the diagnostics M_t, A_t
+    const size_t accb = (size_t)T * SCAN_FW * 8;
+    SCPL_CUDA(h, h->partA.ensure(accb + (size_t)T * 16));
     SCPL_CUDA(h, h->count.ensure((size_t)T * sizeof(unsigned)));
     SCPL_CUDA(h, h->starts.ensure((size_t)(T + 1) * sizeof(int)));
     SCPL_CUDA(h, h->nbuf.ensure(sizeof(int)));
@@ -213,7 +215,7 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     SCPL_CUDA(h, h->h_small.ensure((size_t)(T + 4) * sizeof(int)));
     cudaStream_t s = h->stream;
     SCPL_CUDA(h, cudaMemsetAsync(h->count.p, 0, (size_t)T * sizeof(unsigned), s));
-    SCPL_CUDA(h, cudaMemsetAsync(h->partA.p, 0, (size_t)T * 12, s));
+    SCPL_CUDA(h, cudaMemsetAsync(h->partA.p, 0, accb + (size_t)T * 4, s));
     SCPL_CUDA(h, cudaMemsetAsync(h->errw.p, 0, sizeof(int), s));
     ScanArgs a;
     a.rgb = frames; a.T = T; a.H = H; a.W = W; a.ypitch = ypitch;
@@ -221,7 +223,7 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     a.ering = h->ering.as<uint16_t>();
     a.S1 = h->S1.as<uint32_t>(); a.S2 = h->S2.as<uint32_t>();
     a.partA = h->partA.as<long long>();
-    a.partM = reinterpret_cast<int *>(h->partA.as<char>() + (size_t)T * 8);
+    a.partM = reinterpret_cast<int *>(h->partA.as<char>() + accb);
     a.count = h->count.as<unsigned>();
     a.starts = h->starts.as<int>(); a.n_buffers = h->nbuf.as<int>();
     a.err = h->errw.as<int>();
@@ -235,8 +237,8 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     a.A_out = nullptr;
     a.M_out = nullptr;
     if (A) {   // diagnostics after the accumulators in the same allocation
-        a.A_out = reinterpret_cast<long long *>(h->partA.as<char>() + (size_t)T * 16);
-        a.M_out = reinterpret_cast<int *>(h->partA.as<char>() + (size_t)T * 12);
+        a.M_out = reinterpret_cast<int *>(h->partA.as<char>() + accb + (size_t)T * 4);
+        a.A_out = reinterpret_cast<long long *>(h->partA.as<char>() + accb + (size_t)T * 8);
     }
     SCPL_CUDA(h, timed(h, K_SCAN, [&] { return launch_scan(a, G, s); }));
     if (h->prof.on) h->prof.bytes[K_SCAN] += 28.0 * hw * T;

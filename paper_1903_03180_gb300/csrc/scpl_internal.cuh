@@ -145,17 +145,19 @@ struct CarveWs {
     const int32_t *E0;  // summed energy planes [H][W0] from the scan (see BufState::e0)
 };
 
+constexpr int SCAN_FW = 8;   // frames per round of the buffer scan
+
 // Scan (Sec. 3.2) arguments.
 struct ScanArgs {
     const uint8_t *rgb;     // [T][H][W][3]
     int T, H, W;
     long ypitch;
     uint8_t *Y, *D;         // [T][H][ypitch]
-    uint16_t *ering;        // [2][scan_state_px] energy of the last two frames (tile-major)
+    uint16_t *ering;        // [SCAN_FW][scan_state_px] energy of the frames of a round (tile-major)
     uint32_t *S1, *S2;      // [scan_state_px] sums of e and e^2 over the open buffer (tile-major)
-    long long *partA;       // [T] A_t accumulated over the clip's CTAs (zeroed)
+    long long *partA;       // [T][SCAN_FW] A_t of each round's frames over the clip's CTAs (zeroed)
     int *partM;             // [T] maximum e_t over the clip's CTAs (zeroed)
-    unsigned *count;        // [T] CTAs that published frame t
+    unsigned *count;        // [T] CTAs that published round r (zeroed)
     int *starts;            // [T+1] buffer starts (device)
     int *n_buffers;         // device scalar
     int *err;               // device status word
