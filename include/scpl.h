@@ -204,6 +204,38 @@ scpl_status scpl_set_profiling(scpl_handle h, int on);
 scpl_status scpl_get_stats(scpl_handle h, scpl_stats *out);
 
 /* ------------------------------------------------------------------------
+ * Autotuning (no counterpart in the paper).  Per frame size (H, W, in carving
+ * orientation) the carving kernels have choices that change only the time:
+ * the cluster DP's halo depth R (16: 96 columns a warp, a halo exchange every
+ * 16 rows; 32: 64 columns a warp, an exchange every 32 rows), the single-CTA
+ * DP instead of the cluster, and the rows per update CTA.  A process-wide
+ * table holds one choice per size; scpl_carve, scpl_carve_batch and servers
+ * use it when an entry exists, and the defaults (R = 32, the most update rows
+ * that fit) otherwise. */
+typedef struct {
+    int H, W;
+    int dpc_halo;        /* 16 or 32: the cluster DP's R; 0: the single-CTA DP        */
+    int update_rows;     /* rows per update CTA: 1, 2 or 4                              */
+    float dp_us_r32, dp_us_r16, dp_us_single;   /* measured DP times, us (< 0: unusable) */
+    float up_us[3];      /* measured update times with 1, 2 and 4 rows, us              */
+} scpl_tuning;
+
+/* Measure every choice for (H, W) with k seams per iteration on a scratch
+ * workspace (synthetic energy, allocated and freed here) on the handle's
+ * stream, record the fastest in the table and return the measurements in
+ * *out (may be NULL).  Synchronises the stream. */
+scpl_status scpl_tune(scpl_handle h, int H, int W, int k, scpl_tuning *out);
+/* Record a known choice (e.g. from a file the caller keeps); the measured
+ * fields are not used.  SCPL_EINVAL for an unknown halo or row count. */
+scpl_status scpl_tuning_set(const scpl_tuning *t);
+/* The recorded choice for (H, W): SCPL_OK, or SCPL_EINVAL if there is none. */
+scpl_status scpl_tuning_get(int H, int W, scpl_tuning *out);
+void scpl_tuning_clear(void);
+/* on != 0: scpl_carve and scpl_carve_batch tune every size they meet for the
+ * first time (once per process) before carving it. */
+scpl_status scpl_set_autotune(scpl_handle h, int on);
+
+/* ------------------------------------------------------------------------
  * Many clips at once: batching and serving.  The paper carves one video at a
  * time (Sec. 3, 4); it has no counterpart for these entry points.  They run
  * the same kernels as scpl_carve, with every stage launched once for all the
@@ -288,6 +320,8 @@ scpl_status scpl_batch_stats(scpl_handle h, scpl_server_stats *out);
 scpl_status scpl_server_create(const scpl_params *p, size_t hbm_budget, void *stream,
                                scpl_server *out);
 scpl_status scpl_server_submit(scpl_server s, const scpl_job *job, long long *ticket);
+/* on != 0: tune every frame size the first time a job of that size is carved. */
+scpl_status scpl_server_set_autotune(scpl_server s, int on);
 scpl_status scpl_server_progress(scpl_server s, int wait, int *n_active, int *n_queued);
 int scpl_server_poll(scpl_server s, long long *tickets, int *statuses, int max);
 scpl_status scpl_server_drain(scpl_server s);

@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
         for (int j = 0; j < 8; ++j) ov[j] = Oin[roff + src[j]];
         if (need_e) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) ev[j] = __ldcg(Ein + roff + src[j]);
+            for (int j = 0; j < 8; ++j) ev[j] = __ldg(Ein + roff + src[j]);   // read-only here
         }
         if (p0 + 8 <= Wn) {
             uint4 o4;
@@ -718,6 +718,14 @@ size_t dp_smem_bytes(int W0, int H, int *band_blocks) {
     return fixed + 2 * (size_t)bb * dstride * 4;
 }
 
+// Dynamic shared memory of a k_update CTA of `rb` rows.
+size_t update_smem_bytes_rows(int W0, int kcap, int rb) {
+    const size_t per_row_list = (size_t)(W0 < 15 * kcap ? W0 : 15 * kcap);
+    const size_t nwords0 = (size_t)(W0 + 31) / 32;
+    return (((size_t)(rb + 2) * kcap * 2 + 15) & ~(size_t)15) + (size_t)rb * nwords0 * 4 +
+           (size_t)rb * per_row_list * 4;
+}
+
 // Rows per k_update CTA and its dynamic shared memory.
 size_t update_smem_bytes(int W0, int kcap, int *rows) {
     const size_t per_row_list = (size_t)(W0 < 15 * kcap ? W0 : 15 * kcap);
@@ -743,6 +751,10 @@ cudaError_t launch_energy_init(const CarveWs &ws, int nb, cudaStream_t s) {
 cudaError_t launch_update(const CarveWs &ws, int nb, cudaStream_t s) {
     int rb = 8;
     size_t smem = update_smem_bytes(ws.W0, ws.kcap, &rb);
+    if (ws.up_rows >= 1 && ws.up_rows < rb) {
+        rb = ws.up_rows;
+        smem = update_smem_bytes_rows(ws.W0, ws.kcap, rb);
+    }
     cudaError_t e =
         raise_dyn_smem((const void *)k_update, smem);
     if (e != cudaSuccess) return e;
@@ -820,12 +832,14 @@ size_t carve_ws_assign(CarveWs &ws, int nb, int klog_stride, bool dpc, char *bas
     if (dpc) {
         int C = 0, rj = 0;
         size_t smem = 0;
-        if (!dpc_plan(W0, H, &C, &rj, &smem)) dpc = false;
+        if (ws.dpc_r != 16 && ws.dpc_r != 32) ws.dpc_r = 32;
+        if (!dpc_plan(W0, H, ws.dpc_r, &C, &rj, &smem)) dpc = false;
         else {
             ws.rj = rj;
             ws.nbands = (H + rj - 1) / rj;
         }
     }
+    if (!dpc) ws.dpc_r = 0;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;

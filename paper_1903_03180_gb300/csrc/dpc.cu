@@ -53,13 +53,14 @@ namespace {
 constexpr int DPC_WPC = 4;                       // warps per CTA
 constexpr int DPC_V = 4;                         // columns per lane
 constexpr int DPC_S = 16;                        // rows per TMA stage of the energy ring
-constexpr int DPC_R = 32;                        // rows between halo refreshes (= halo width)
-constexpr int DPC_SPR = DPC_R / DPC_S;           // stages per refresh
-constexpr int DPC_HL = DPC_R / DPC_V;            // halo lanes on each side of a warp: 8
-constexpr int DPC_OWW = 32 * DPC_V - 2 * DPC_R;  // owned columns per warp: 64
+// The halo depth R (16 or 32, a template parameter of k_dpc) is also the
+// number of rows between halo refreshes.  A warp's window is always 128
+// columns, so it owns 128 - 2R of them (96 or 64): R trades the exchange
+// frequency against the columns per warp.
 constexpr int DPC_NST = 4;                       // energy stages in flight
-constexpr int DPC_LMAX = DPC_WPC * DPC_OWW;      // parents a CTA can report: 384
 constexpr int DPC_WW = 32 * DPC_V;               // columns of a warp's window: 128
+__host__ __device__ constexpr int dpc_oww(int R) { return DPC_WW - 2 * R; }
+__host__ __device__ constexpr int dpc_lmax(int R) { return DPC_WPC * dpc_oww(R); }
 constexpr size_t DPC_WSLOT = (size_t)DPC_S * DPC_WW * 4;   // one warp's stage: 8 KB
 constexpr size_t DPC_RING = (size_t)DPC_WPC * DPC_NST * DPC_WSLOT;
 constexpr size_t DPC_STAGE_BUDGET = 96 * 1024;   // trace-back staging
@@ -72,7 +73,8 @@ __host__ __device__ inline size_t al16(size_t v) { return (v + 15) & ~(size_t)15
 // Shared-memory layout after the DP (aliases the energy ring).
 struct PostLayout {
     size_t segmin, lkeys, llabs, lcnt, cand, sel, pos, js, ds, end;
-    __host__ __device__ PostLayout(int W0, int C, int kcap, int nb, int jstride, int dstride) {
+    __host__ __device__ PostLayout(int W0, int C, int kcap, int nb, int jstride, int dstride,
+                                   int DPC_LMAX) {
         size_t o = 0;
         segmin = o; o = al16(o + (size_t)W0 * 8);
         lkeys = o;  o = al16(o + (size_t)C * DPC_LMAX * 8);
@@ -145,9 +147,15 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t *mbar, unsigned parit
     return true;
 }
 
+template <int R>
 __global__ void __launch_bounds__(DPC_WPC * 32, 1)
 k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams,
       long seam_stride) {
+    constexpr int DPC_R = R;                      // rows between halo refreshes (= halo width)
+    constexpr int DPC_SPR = DPC_R / DPC_S;        // stages per refresh
+    constexpr int DPC_HL = DPC_R / DPC_V;         // halo lanes on each side of a warp
+    constexpr int DPC_OWW = dpc_oww(R);           // owned columns per warp
+    constexpr int DPC_LMAX = dpc_lmax(R);         // parents a CTA can report
     extern __shared__ __align__(128) unsigned char smraw[];
     // halo inboxes: [parity][warp][value], filled by the neighbouring warps
     __shared__ __align__(16) uint32_t inLc[2][DPC_WPC][DPC_R], inLl[2][DPC_WPC][DPC_R];
@@ -383,7 +391,7 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
     cluster.sync();   // every CTA is done with its energy ring
 
     // ---- Eq. 6: per-parent minima -------------------------------------------------
-    const PostLayout PL(W0, C, ws.kcap, NB, ws.jstride, dstride);
+    const PostLayout PL(W0, C, ws.kcap, NB, ws.jstride, dstride, DPC_LMAX);
     uint64_t *segmin = reinterpret_cast<uint64_t *>(smraw + PL.segmin);
     uint64_t *lkeys = reinterpret_cast<uint64_t *>(smraw + PL.lkeys);
     uint32_t *llabs = reinterpret_cast<uint32_t *>(smraw + PL.llabs);
@@ -577,11 +585,11 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
     }
 }
 
-size_t dpc_smem(int W0, int H, int rj, int kcap, int C) {
+size_t dpc_smem(int W0, int H, int rj, int kcap, int C, int R) {
     const int nb = (H + rj - 1) / rj;
     const int jstride = (W0 + 7) & ~7;
     const int dstride = (((W0 + 3) / 4) + 3) & ~3;
-    const PostLayout PL(W0, C, kcap, nb, jstride, dstride);
+    const PostLayout PL(W0, C, kcap, nb, jstride, dstride, dpc_lmax(R));
     const WalkLayout WL(kcap, (nb + C - 1) / C);
     size_t m = DPC_RING;
     m = PL.end > m ? PL.end : m;
@@ -622,18 +630,19 @@ bool make_energy_map(const CarveWs &ws, int nb, CUtensorMap *m) {
 
 }  // namespace
 
-bool dpc_plan(int W0, int H, int *ctas, int *rj, size_t *smem) {
-    const int nwarps = (W0 + DPC_OWW - 1) / DPC_OWW;
+bool dpc_plan(int W0, int H, int R, int *ctas, int *rj, size_t *smem) {
+    if (R != 16 && R != 32) return false;
+    const int nwarps = (W0 + dpc_oww(R) - 1) / dpc_oww(R);
     const int C = (nwarps + DPC_WPC - 1) / DPC_WPC;
     if (C > 16) return false;
     // about four bands per CTA: the walk then takes ~rj rows per CTA
     int r = (H + 4 * C - 1) / (4 * C);
     r = ((r + 15) / 16) * 16;
     if (r < 16) r = 16;
-    size_t bytes = dpc_smem(W0, H, r, W0, C);
+    size_t bytes = dpc_smem(W0, H, r, W0, C, R);
     while (bytes > 220 * 1024 && r < H) {
         r += 16;
-        bytes = dpc_smem(W0, H, r, W0, C);
+        bytes = dpc_smem(W0, H, r, W0, C, R);
     }
     if (bytes > 220 * 1024) return false;
     // the walk stages at least one 16-row group of every band a CTA owns
@@ -646,14 +655,16 @@ bool dpc_plan(int W0, int H, int *ctas, int *rj, size_t *smem) {
     return true;
 }
 
-bool dpc_available(int W0, int H) {
-    if (!encode_tiled()) return false;
+namespace {
+
+template <int R>
+bool dpc_available_t(int W0, int H) {
     int C = 0, rj = 0;
     size_t smem = 0;
-    if (!dpc_plan(W0, H, &C, &rj, &smem)) return false;
-    if (raise_dyn_smem((const void *)k_dpc, smem) != cudaSuccess) return false;
+    if (!dpc_plan(W0, H, R, &C, &rj, &smem)) return false;
+    if (raise_dyn_smem((const void *)k_dpc<R>, smem) != cudaSuccess) return false;
     if (C > 8 &&
-        cudaFuncSetAttribute(k_dpc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        cudaFuncSetAttribute(k_dpc<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
             cudaSuccess)
         return false;
     cudaLaunchConfig_t cfg = {};
@@ -668,23 +679,24 @@ bool dpc_available(int W0, int H) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, k_dpc, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_dpc<R>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     return clusters > 0;
 }
 
-cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
-                       cudaStream_t s) {
+template <int R>
+cudaError_t launch_dpc_t(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
+                         cudaStream_t s) {
     int C = 0, rj = 0;
     size_t smem = 0;
-    if (!dpc_plan(ws.W0, ws.H, &C, &rj, &smem) || rj != ws.rj) return cudaErrorInvalidValue;
-    smem = dpc_smem(ws.W0, ws.H, ws.rj, ws.kcap, C);
-    cudaError_t e = raise_dyn_smem((const void *)k_dpc, smem);
+    if (!dpc_plan(ws.W0, ws.H, R, &C, &rj, &smem) || rj != ws.rj) return cudaErrorInvalidValue;
+    smem = dpc_smem(ws.W0, ws.H, ws.rj, ws.kcap, C, R);
+    cudaError_t e = raise_dyn_smem((const void *)k_dpc<R>, smem);
     if (e != cudaSuccess) return e;
     if (C > 8) {
-        e = cudaFuncSetAttribute(k_dpc, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(k_dpc<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
@@ -701,9 +713,23 @@ cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long se
     cfg.numAttrs = 1;
     CUtensorMap tm;
     if (!make_energy_map(ws, nb, &tm)) return cudaErrorInvalidValue;
-    e = cudaLaunchKernelEx(&cfg, k_dpc, tm, ws, k, seams, seam_stride);
+    e = cudaLaunchKernelEx(&cfg, k_dpc<R>, tm, ws, k, seams, seam_stride);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
+}
+
+}  // namespace
+
+bool dpc_available(int W0, int H, int R) {
+    if (!encode_tiled()) return false;
+    return R == 16 ? dpc_available_t<16>(W0, H) : R == 32 ? dpc_available_t<32>(W0, H) : false;
+}
+
+cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
+                       cudaStream_t s) {
+    if (ws.dpc_r == 16) return launch_dpc_t<16>(ws, nb, k, seams, seam_stride, s);
+    if (ws.dpc_r == 32) return launch_dpc_t<32>(ws, nb, k, seams, seam_stride, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace scpl

@@ -274,6 +274,7 @@ struct scpl_server_s {
     long long next_ticket = 1;
     scpl_server_stats st{};
     int active_jobs = 0;
+    bool autotune = false;
 };
 
 namespace {
@@ -309,11 +310,11 @@ void add_reserved(Srv *s, long long delta) {
     s->peak = std::max(s->peak, s->reserved);
 }
 
-bool dpc_ok(Srv *s, int W, int H) {
-    auto key = std::make_pair(W, H);
+bool dpc_ok(Srv *s, int W, int H, int R) {
+    auto key = std::make_pair(W, H * 64 + R);
     auto it = s->dpc_cache.find(key);
     if (it != s->dpc_cache.end()) return it->second;
-    bool ok = dpc_available(W, H);
+    bool ok = dpc_available(W, H, R);
     s->dpc_cache[key] = ok;
     return ok;
 }
@@ -693,12 +694,17 @@ scpl_status setup_group(Srv *s, int gid) {
         G.phase = 3;
         return SCPL_OK;
     }
-    G.dpc = dpc_ok(s, G.W, G.H);
     CarveWs &ws = G.ws;
     ws = CarveWs{};
     ws.H = G.H;
     ws.W0 = G.W;
     ws.kcap = kcap;
+    ws.dpc_r = 32;
+    bool use_dpc = true;
+    if (s->autotune && !tuning_lookup(G.H, G.W, nullptr))
+        tune_class(G.H, G.W, kcap, G.stream, nullptr);   // on failure: the defaults
+    tuning_apply(G.H, G.W, ws, &use_dpc);
+    G.dpc = use_dpc && dpc_ok(s, G.W, G.H, ws.dpc_r);
     const size_t ws_bytes = carve_ws_assign(ws, nb, klog, G.dpc, nullptr);
     // frames of every item, the gather table and the frame-minor luma
     long long yfm_total = 0;
@@ -1214,7 +1220,7 @@ namespace scpl {
 // scpl_carve_batch: the handle's engine (created on first use and kept, with
 // its memory pool, until the handle is destroyed), every job submitted at once.
 scpl_status engine_run_batch(scpl_server_s **eng, const scpl_params &p, cudaStream_t stream,
-                             scpl_job *jobs, int n_jobs, std::string &err) {
+                             bool autotune, scpl_job *jobs, int n_jobs, std::string &err) {
     scpl_status st = SCPL_OK;
     if (!*eng) {
         st = create(&p, 0, stream, eng);
@@ -1225,6 +1231,7 @@ scpl_status engine_run_batch(scpl_server_s **eng, const scpl_params &p, cudaStre
     }
     Srv *s = *eng;
     s->user = stream;
+    s->autotune = autotune;
     if (s->broken) {
         err = "the batch engine hit a CUDA error earlier: " + s->err;
         return SCPL_ECUDA;
@@ -1285,6 +1292,12 @@ scpl_status scpl_server_create(const scpl_params *p, size_t hbm_budget, void *st
 scpl_status scpl_server_submit(scpl_server s, const scpl_job *job, long long *ticket) {
     if (!s) return SCPL_EINVAL;
     return submit(s, job, nullptr, ticket);
+}
+
+scpl_status scpl_server_set_autotune(scpl_server s, int on) {
+    if (!s) return SCPL_EINVAL;
+    s->autotune = on != 0;
+    return SCPL_OK;
 }
 
 scpl_status scpl_server_progress(scpl_server s, int wait, int *n_active, int *n_queued) {

@@ -109,9 +109,10 @@ struct scpl_ctx {
     // host-memory entry point staging
     DevBuf in_frames, out_frames, seams_dev;
     DevBuf Yfm;
-    // cluster-DP availability per (W0, H) last checked
-    int dpc_W0 = -1, dpc_H = -1;
+    // cluster-DP availability per (W0, H, halo) last checked
+    int dpc_W0 = -1, dpc_H = -1, dpc_R = -1;
     bool dpc_ok = false;
+    bool autotune = false;
     HostBuf h_small;   // starts + n_buffers + states readback
     Profiler prof;
     scpl_server_s *engine = nullptr;   // scpl_carve_batch's engine (created on first use)
@@ -275,15 +276,25 @@ scpl_status carve_ws(scpl_ctx *h, int nb, int H, int W0, int kcap, CarveWs &ws,
     if (dp_smem_bytes(W0, H, &bb) > 227 * 1024 - 4096 ||
         update_smem_bytes(W0, ws.kcap, &rb) > 200 * 1024)
         return fail(h, SCPL_EINVAL, "width %d exceeds the shared-memory limits", W0);
+    // the tuned choice for this size (halo depth or the single-CTA DP, update
+    // rows), measured first if autotuning is on; R = 32 otherwise
+    ws.dpc_r = 32;
+    ws.up_rows = 0;
+    bool use_dpc = true;
+    if (h->autotune && !tuning_lookup(H, W0, nullptr))
+        tune_class(H, W0, ws.kcap, h->stream, nullptr);   // on failure: the defaults
+    tuning_apply(H, W0, ws, &use_dpc);
     // cluster DP tables (used when the GPU can co-schedule the cluster)
-    if (h->dpc_W0 != W0 || h->dpc_H != H) {
-        h->dpc_ok = dpc_available(W0, H);
+    if (h->dpc_W0 != W0 || h->dpc_H != H || h->dpc_R != ws.dpc_r) {
+        h->dpc_ok = dpc_available(W0, H, ws.dpc_r);
         h->dpc_W0 = W0;
         h->dpc_H = H;
+        h->dpc_R = ws.dpc_r;
     }
-    const size_t bytes = carve_ws_assign(ws, nb, klog_stride, h->dpc_ok, nullptr);
+    const bool dpc = use_dpc && h->dpc_ok;
+    const size_t bytes = carve_ws_assign(ws, nb, klog_stride, dpc, nullptr);
     SCPL_CUDA(h, h->cws.ensure(bytes));
-    carve_ws_assign(ws, nb, klog_stride, h->dpc_ok, h->cws.as<char>());
+    carve_ws_assign(ws, nb, klog_stride, dpc, h->cws.as<char>());
     ws.Y = h->Y.as<uint8_t>();
     ws.D = h->D.as<uint8_t>();
     ws.ypitch = round_up(W0, 16);
@@ -609,7 +620,7 @@ scpl_status scpl_carve_batch(scpl_handle h, scpl_job *jobs, int n_jobs) {
     if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return fail(h, SCPL_EINVAL, "bad job list");
     if (n_jobs == 0) return SCPL_OK;
     std::string err;
-    scpl_status s = engine_run_batch(&h->engine, h->p, h->stream, jobs, n_jobs, err);
+    scpl_status s = engine_run_batch(&h->engine, h->p, h->stream, h->autotune, jobs, n_jobs, err);
     if (s != SCPL_OK) return fail(h, s, "%s", err.c_str());
     return SCPL_OK;
 }
@@ -617,6 +628,36 @@ scpl_status scpl_carve_batch(scpl_handle h, scpl_job *jobs, int n_jobs) {
 scpl_status scpl_batch_stats(scpl_handle h, scpl_server_stats *out) {
     if (!h || !out) return SCPL_EINVAL;
     return engine_stats(h->engine, out);
+}
+
+scpl_status scpl_tune(scpl_handle h, int H, int W, int k, scpl_tuning *out) {
+    if (!h) return SCPL_EINVAL;
+    if (H < 1 || H > 65535 || W < 4 || W > 8192 || k < 1)
+        return fail(h, SCPL_EINVAL, "cannot tune H=%d W=%d k=%d", H, W, k);
+    scpl_status s = tune_class(H, W, k, h->stream, out);
+    if (s != SCPL_OK) return fail(h, s, "tuning H=%d W=%d failed", H, W);
+    return SCPL_OK;
+}
+
+scpl_status scpl_tuning_set(const scpl_tuning *t) {
+    if (!t || t->H < 1 || t->W < 1) return SCPL_EINVAL;
+    if (t->dpc_halo != 0 && t->dpc_halo != 16 && t->dpc_halo != 32) return SCPL_EINVAL;
+    if (t->update_rows != 1 && t->update_rows != 2 && t->update_rows != 4) return SCPL_EINVAL;
+    tuning_store(*t);
+    return SCPL_OK;
+}
+
+scpl_status scpl_tuning_get(int H, int W, scpl_tuning *out) {
+    if (!out) return SCPL_EINVAL;
+    return tuning_lookup(H, W, out) ? SCPL_OK : SCPL_EINVAL;
+}
+
+void scpl_tuning_clear(void) { tuning_clear(); }
+
+scpl_status scpl_set_autotune(scpl_handle h, int on) {
+    if (!h) return SCPL_EINVAL;
+    h->autotune = on != 0;
+    return SCPL_OK;
 }
 
 scpl_status scpl_set_profiling(scpl_handle h, int on) {

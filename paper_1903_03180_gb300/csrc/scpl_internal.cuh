@@ -141,6 +141,8 @@ struct CarveWs {
     int *dpx;           // [nb][1 + kcap]     k_eff, then each seam's rank by column
     int jstride;        // row stride of J (W0 rounded up to 8)
     uint32_t *Dfirst;   // [nb][nbands][dstride] direction words of every band's first row
+    int dpc_r;          // halo depth of the cluster DP (16 or 32); 0: the single-CTA DP
+    int up_rows;        // rows per k_update CTA (1, 2 or 4); 0: the largest that fits
     int *err;           // device status word (bounded waits)
     const int32_t *E0;  // summed energy planes [H][W0] from the scan (see BufState::e0)
 };
@@ -191,10 +193,11 @@ cudaError_t launch_energy_init(const CarveWs &ws, int nb, cudaStream_t s);
 cudaError_t launch_update(const CarveWs &ws, int nb, cudaStream_t s);
 cudaError_t launch_dp_select(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                              cudaStream_t s);
-// Cluster DP: plan (CTAs per cluster, band rows, shared memory) for a width and
-// height; returns false if this GPU cannot run it (then use launch_dp_select).
-bool dpc_plan(int W0, int H, int *ctas, int *rj, size_t *smem);
-bool dpc_available(int W0, int H);
+// Cluster DP with halo depth R (16 or 32): plan (CTAs per cluster, band rows,
+// shared memory) for a width and height; returns false if this GPU cannot run
+// it (then use launch_dp_select).  launch_dpc uses ws.dpc_r.
+bool dpc_plan(int W0, int H, int R, int *ctas, int *rj, size_t *smem);
+bool dpc_available(int W0, int H, int R);
 cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                        cudaStream_t s);
 cudaError_t launch_identity_O(const CarveWs &ws, int nb, cudaStream_t s);
@@ -223,9 +226,16 @@ size_t carve_ws_assign(CarveWs &ws, int nb, int klog_stride, bool dpc, char *bas
 #include "scpl.h"
 
 namespace scpl {
+// Autotuning table (tune.cu): the measured choice per (H, W).
+bool tuning_lookup(int H, int W, scpl_tuning *out);
+void tuning_store(const scpl_tuning &t);
+void tuning_clear();
+void tuning_apply(int H, int W, CarveWs &ws, bool *use_dpc);
+scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out);
+
 // scpl_carve_batch's engine (engine.cu), owned by a handle.
 scpl_status engine_run_batch(scpl_server_s **eng, const scpl_params &p, cudaStream_t stream,
-                             scpl_job *jobs, int n_jobs, std::string &err);
+                             bool autotune, scpl_job *jobs, int n_jobs, std::string &err);
 void engine_destroy(scpl_server_s *eng);
 scpl_status engine_stats(scpl_server_s *eng, scpl_server_stats *out);
 // Raises a kernel's dynamic shared-memory limit to at least `bytes` on the

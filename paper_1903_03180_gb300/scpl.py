@@ -61,6 +61,14 @@ class ServerStats(ctypes.Structure):
                 ("peak_reserved_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t)]
 
 
+class Tuning(ctypes.Structure):
+    """scpl_tuning: the kernel choices for one frame size and their times."""
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("dpc_halo", ctypes.c_int),
+                ("update_rows", ctypes.c_int), ("dp_us_r32", ctypes.c_float),
+                ("dp_us_r16", ctypes.c_float), ("dp_us_single", ctypes.c_float),
+                ("up_us", ctypes.c_float * 3)]
+
+
 _LL = ctypes.c_longlong
 SIGNATURES = {
     "scpl_default_params": (None, [ctypes.POINTER(Params)]),
@@ -78,6 +86,12 @@ SIGNATURES = {
     "scpl_set_profiling": (_I, [_P, _I]),
     "scpl_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
     "scpl_carve_batch": (_I, [_P, ctypes.POINTER(Job), _I]),
+    "scpl_tune": (_I, [_P, _I, _I, _I, ctypes.POINTER(Tuning)]),
+    "scpl_tuning_set": (_I, [ctypes.POINTER(Tuning)]),
+    "scpl_tuning_get": (_I, [_I, _I, ctypes.POINTER(Tuning)]),
+    "scpl_tuning_clear": (None, []),
+    "scpl_set_autotune": (_I, [_P, _I]),
+    "scpl_server_set_autotune": (_I, [_P, _I]),
     "scpl_job_footprint": (ctypes.c_size_t, [ctypes.POINTER(Params), ctypes.POINTER(Job)]),
     "scpl_job_footprint_per_buffer": (ctypes.c_size_t, [ctypes.POINTER(Job)]),
     "scpl_batch_stats": (_I, [_P, ctypes.POINTER(ServerStats)]),
@@ -371,6 +385,42 @@ def make_job(frames, target_W: int, target_H: int, k: int, out, starts=None) -> 
     return j
 
 
+def _tuning_dict(t: Tuning) -> dict:
+    return {"H": t.H, "W": t.W, "dpc_halo": t.dpc_halo, "update_rows": t.update_rows,
+            "dp_us": {"r32": t.dp_us_r32, "r16": t.dp_us_r16, "single": t.dp_us_single},
+            "update_us": {1: t.up_us[0], 2: t.up_us[1], 4: t.up_us[2]}}
+
+
+def scpl_tune(h, H: int, W: int, k: int) -> dict:
+    """Measure the kernel choices for (H, W) and record the fastest."""
+    t = Tuning()
+    _check(h, load().scpl_tune(h, H, W, k, ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def scpl_tuning_set(H: int, W: int, dpc_halo: int, update_rows: int):
+    t = Tuning()
+    t.H, t.W, t.dpc_halo, t.update_rows = H, W, dpc_halo, update_rows
+    st = load().scpl_tuning_set(ctypes.byref(t))
+    if st != SCPL_OK:
+        raise SCPLError(st, "scpl_tuning_set: halo must be 0, 16 or 32 and rows 1, 2 or 4")
+
+
+def scpl_tuning_get(H: int, W: int) -> dict | None:
+    t = Tuning()
+    if load().scpl_tuning_get(H, W, ctypes.byref(t)) != SCPL_OK:
+        return None
+    return _tuning_dict(t)
+
+
+def scpl_tuning_clear():
+    load().scpl_tuning_clear()
+
+
+def scpl_set_autotune(h, on: bool):
+    _check(h, load().scpl_set_autotune(h, int(on)))
+
+
 def scpl_job_footprint(params: Params | None, job: Job) -> int:
     return int(load().scpl_job_footprint(ctypes.byref(params) if params is not None else None,
                                          ctypes.byref(job)))
@@ -422,6 +472,9 @@ class Server:
         self._err(self.lib.scpl_server_submit(self.s, ctypes.byref(job), ctypes.byref(t)))
         self._keep[t.value] = (frames, out, starts, job)
         return t.value
+
+    def set_autotune(self, on: bool):
+        self._err(self.lib.scpl_server_set_autotune(self.s, int(on)))
 
     def progress(self, wait: bool = False) -> tuple[int, int]:
         a, q = ctypes.c_int(), ctypes.c_int()

@@ -80,3 +80,17 @@ def test_job_footprint_host_only(lib):
     assert scpl.scpl_job_footprint(None, j) > fp
     j.target_W = 1921
     assert scpl.scpl_job_footprint(None, j) == 0
+
+
+def test_tuning_table_host_only(lib):
+    from paper_1903_03180_gb300 import scpl
+    scpl.scpl_tuning_clear()
+    assert scpl.scpl_tuning_get(10, 20) is None
+    scpl.scpl_tuning_set(10, 20, 16, 2)
+    assert scpl.scpl_tuning_get(10, 20)["dpc_halo"] == 16
+    with pytest.raises(scpl.SCPLError):
+        scpl.scpl_tuning_set(10, 20, 8, 2)
+    with pytest.raises(scpl.SCPLError):
+        scpl.scpl_tuning_set(10, 20, 32, 3)
+    scpl.scpl_tuning_clear()
+    assert scpl.scpl_tuning_get(10, 20) is None
