@@ -346,6 +346,7 @@ def run_batch(args) -> None:
              for i, sp in enumerate(specs)]
     frames = sum(sp["T"] for sp in specs)
     h = scpl.scpl_create()
+    scpl.scpl_set_autotune(h, True)   # every size is tuned once, during the warm-up
     for _ in range(max(args.warmup, 0)):
         scpl.scpl_carve_batch(h, jobs)
     st0 = scpl.scpl_batch_stats(h)
@@ -383,6 +384,11 @@ def run_batch(args) -> None:
             "identical_output": bool(identical),
             "engine_per_step": {k: (st1[k] - st0[k]) / steps for k in
                                 ("scan_waves", "groups", "chunks", "kernel_launches")},
+            "tuning": {f"{hh}x{w}": scpl.scpl_tuning_get(hh, w) for hh, w in
+                       sorted({(sp["H"], sp["W"]) for sp in specs} |
+                              {(sp["W"] if sp["target_H"] < sp["H"] else sp["H"],
+                                sp["H"] if sp["target_H"] < sp["H"] else sp["W"])
+                               for sp in specs})},
             "gpu_launches": int((st1["kernel_launches"] - st0["kernel_launches"]) / steps),
             "clocks": clk}
     print(json.dumps(line), flush=True)
@@ -419,6 +425,10 @@ def run_serve(args) -> None:
 
     results = []
     srv = scpl.Server()
+    # tune the four sizes before the sweep (what a server does at start-up)
+    th = scpl.scpl_create()
+    tuning = {f"{W}x{H}": scpl.scpl_tune(th, H, W, k) for H, W, k in sizes}
+    scpl.scpl_destroy(th)
     rates = [float(x) for x in args.rates.split(",")]
     for ri, rate in enumerate(rates):
         r = np.random.default_rng(1000 + ri)
@@ -471,6 +481,8 @@ def run_serve(args) -> None:
                                           "groups", "chunks", "graphs_built",
                                           "kernel_launches", "peak_reserved_bytes",
                                           "budget_bytes")},
+            "tuning": {k: {"dpc_halo": v["dpc_halo"], "update_rows": v["update_rows"]}
+                       for k, v in tuning.items()},
             "gpu_launches": int(st["kernel_launches"])}
     print(json.dumps(line), flush=True)
 

@@ -701,9 +701,7 @@ scpl_status setup_group(Srv *s, int gid) {
     ws.kcap = kcap;
     ws.dpc_r = 32;
     bool use_dpc = true;
-    if (s->autotune && !tuning_lookup(G.H, G.W, nullptr))
-        tune_class(G.H, G.W, kcap, G.stream, nullptr);   // on failure: the defaults
-    tuning_apply(G.H, G.W, ws, &use_dpc);
+    tuning_apply(G.H, G.W, ws, &use_dpc);   // sizes were tuned when their wave finished
     G.dpc = use_dpc && dpc_ok(s, G.W, G.H, ws.dpc_r);
     const size_t ws_bytes = carve_ws_assign(ws, nb, klog, G.dpc, nullptr);
     // frames of every item, the gather table and the frame-minor luma
@@ -988,6 +986,18 @@ scpl_status round(Srv *s, bool *any) {
         W.slab = nullptr;
         s->pinned.put(W.h);
         W.h = Pinned{};
+        // new sizes are tuned before this wave's groups start carving, so that
+        // the measurements see only what was already running
+        if (s->autotune)
+            for (int g : W.groups) {
+                const Group &G = *s->groups[g];
+                if (tuning_lookup(G.H, G.W, nullptr)) continue;
+                int kcap = 1;
+                for (int pid : G.passes)
+                    kcap = std::max(kcap, std::min(s->passes[pid].k,
+                                                   s->passes[pid].d.W - s->passes[pid].d.target));
+                tune_class(G.H, G.W, kcap, s->main, nullptr);   // on failure: the defaults
+            }
         for (int g : W.groups)
             if ((st = setup_group(s, g)) != SCPL_OK) return st;
     }
