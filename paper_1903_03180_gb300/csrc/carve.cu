@@ -629,10 +629,11 @@ __device__ __forceinline__ void gather_row(const uint16_t *__restrict__ O,
     }
 }
 
-// Final colour gather: out[t][i][p] = rgb[t][i][O[i][p]].  grid (H, T).
+// Final colour gather: out[t][i][p] = rgb[t][i][O[i][p]].  grid (H, frames),
+// frame t = t0 + blockIdx.y.
 __global__ void k_gather(CarveWs ws, const uint8_t *__restrict__ rgb, const int *buf_of_frame,
-                         int target, uint8_t *__restrict__ out) {
-    const int i = blockIdx.x, t = blockIdx.y;
+                         int target, uint8_t *__restrict__ out, int t0) {
+    const int i = blockIdx.x, t = t0 + blockIdx.y;
     const int b = buf_of_frame[t];
     int W, slot, removed;
     committed(ws.st[b], W, slot, removed);
@@ -774,10 +775,19 @@ cudaError_t launch_identity_O(const CarveWs &ws, int nb, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_gather_range(const CarveWs &ws, const uint8_t *rgb, int t0, int nt,
+                                const int *buf_of_frame, int target, uint8_t *out,
+                                cudaStream_t s) {
+    for (int f = 0; f < nt; f += 65535) {
+        const int n = nt - f < 65535 ? nt - f : 65535;
+        k_gather<<<dim3(ws.H, n), 256, 0, s>>>(ws, rgb, buf_of_frame, target, out, t0 + f);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather(const CarveWs &ws, const uint8_t *rgb, int T, const int *buf_of_frame,
                           int target, uint8_t *out, cudaStream_t s) {
-    k_gather<<<dim3(ws.H, T), 256, 0, s>>>(ws, rgb, buf_of_frame, target, out);
-    return cudaGetLastError();
+    return launch_gather_range(ws, rgb, 0, T, buf_of_frame, target, out, s);
 }
 
 cudaError_t launch_gather_frames(const CarveWs &ws, const GatherFrame *tab, int nframes,

@@ -459,6 +459,29 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
         for (int f = t; f <= w; ++f) {
             uint32_t emax2 = 0;
             const bool fresh_frame = f >= horizon;
+            if (fresh_frame && a.ready) {
+                // frame f may still be on its way from the host: wait (bounded)
+                // until the copy stream has raised the counter past its chunk
+                if (tid == 0) {
+                    const unsigned need = (unsigned)(f / a.ready_frames) + 1u;
+                    int ok = 1;
+                    if (ld_acquire_u32(a.ready) < need) {
+                        const unsigned long long t0 = globaltimer_ns();
+                        while (ld_acquire_u32(a.ready) < need) {
+                            if (*(volatile int *)a.err != DEV_OK) { ok = 0; break; }
+                            if (globaltimer_ns() - t0 > a.spin_limit_ns) {
+                                atomicCAS(a.err, DEV_OK, DEV_ETIMEOUT);
+                                ok = 0;
+                                break;
+                            }
+                            __nanosleep(256);
+                        }
+                    }
+                    s_ok = ok;
+                }
+                __syncthreads();
+                if (!s_ok) return;
+            }
             if (fresh_frame) {
                 if (resident) {
 #pragma unroll

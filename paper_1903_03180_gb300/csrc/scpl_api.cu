@@ -1,6 +1,8 @@
 // C ABI of libscpl (declared in include/scpl.h): argument checks, workspace
 // management and the host-side order of launches.  All arithmetic of the
 // method runs in the kernels of scan.cu and carve.cu.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -113,6 +115,10 @@ struct scpl_ctx {
     int dpc_W0 = -1, dpc_H = -1, dpc_R = -1;
     bool dpc_ok = false;
     bool autotune = false;
+    // host-memory path: copy stream, side stream for early gathers, the
+    // arrival counter of the frames and its driver entry point
+    cudaStream_t cstream = nullptr, gstream = nullptr;
+    DevBuf ready;
     HostBuf h_small;   // starts + n_buffers + states readback
     Profiler prof;
     scpl_server_s *engine = nullptr;   // scpl_carve_batch's engine (created on first use)
@@ -144,17 +150,21 @@ scpl_status fail(scpl_ctx *h, scpl_status s, const char *fmt, ...) {
         }                                                                                  \
     } while (0)
 
-// Runs `launch` bracketed by events when profiling is on.
+// Runs `launch` (issued on stream s) bracketed by events when profiling is on.
 template <class F>
-cudaError_t timed(scpl_ctx *h, int id, F launch) {
+cudaError_t timed_on(scpl_ctx *h, int id, cudaStream_t s, F launch) {
     if (!h->prof.on) return launch();
     cudaEvent_t a = h->prof.next(), b = h->prof.next();
     if (!a || !b) return launch();
-    cudaEventRecord(a, h->stream);
+    cudaEventRecord(a, s);
     cudaError_t e = launch();
-    cudaEventRecord(b, h->stream);
+    cudaEventRecord(b, s);
     h->prof.marks.push_back({id, h->prof.used - 2});
     return e;
+}
+template <class F>
+cudaError_t timed(scpl_ctx *h, int id, F launch) {
+    return timed_on(h, id, h->stream, launch);
 }
 
 scpl_status check_params(const scpl_params *p) {
@@ -192,7 +202,7 @@ constexpr int E0_PLANES = 16;   // buffers whose summed energy the scan keeps
 // host.  A and M (host, or NULL) receive every frame's A_t and maximum e_t.
 scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
                      std::vector<int> &starts, bool keep_e0, long long *A = nullptr,
-                     int *M = nullptr) {
+                     int *M = nullptr, const unsigned *ready = nullptr, int ready_frames = 1) {
     const long ypitch = round_up(W, 16);
     const long hw = (long)H * W;
     int gerr = 0;
@@ -237,6 +247,8 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     a.e0_plane = hw;
     a.A_out = nullptr;
     a.M_out = nullptr;
+    a.ready = ready;
+    a.ready_frames = ready_frames;
     if (A) {   // diagnostics after the accumulators in the same allocation
         a.M_out = reinterpret_cast<int *>(h->partA.as<char>() + accb + (size_t)T * 4);
         a.A_out = reinterpret_cast<long long *>(h->partA.as<char>() + accb + (size_t)T * 8);
@@ -314,6 +326,215 @@ scpl_status check_frames(scpl_ctx *h, const void *frames, int T, int H, int W) {
 
 }  // namespace
 
+namespace {
+
+// cuStreamWriteValue32 from the driver, looked up once (NULL if unavailable).
+PFN_cuStreamWriteValue32_v11070 stream_write_value() {
+    static PFN_cuStreamWriteValue32_v11070 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuStreamWriteValue32", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuStreamWriteValue32_v11070>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// scpl_carve with two options of the host-memory path: `ready` (frames still
+// arriving, see ScanArgs::ready) and `host_out` (every buffer's output frames
+// are gathered as soon as the buffer is carved and copied to host_out on the
+// copy stream while the other buffers carve on).
+scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, int target_W,
+                      int k, uint8_t *out, int32_t *buffer_starts, int *n_buffers,
+                      int16_t *seams, const unsigned *ready, int ready_frames,
+                      uint8_t *host_out) {
+    scpl_status s = check_frames(h, frames, T, H, W);
+    if (s != SCPL_OK) return s;
+    if (!out) return fail(h, SCPL_EINVAL, "out is NULL");
+    if (target_W < 2 || target_W > W)
+        return fail(h, SCPL_EINVAL, "target_W=%d must be in [2, W=%d]", target_W, W);
+    if (k < 1) return fail(h, SCPL_EINVAL, "k=%d must be >= 1", k);
+    if ((s = check_overflow(h, T, H)) != SCPL_OK) return s;
+
+    std::vector<int> starts;
+    if ((s = run_scan(h, frames, T, H, W, starts, true, nullptr, nullptr, ready, ready_frames)) != SCPL_OK) return s;
+    const int nb = (int)starts.size() - 1;
+    const int remove = W - target_W;
+    CarveWs ws;
+    if ((s = carve_ws(h, nb, H, W, std::min(k, std::max(remove, 1)), ws, remove)) != SCPL_OK)
+        return s;
+    cudaStream_t st = h->stream;
+
+    // per-buffer states and the frame -> buffer map
+    SCPL_CUDA(h, h->bof.ensure((size_t)T * sizeof(int)));
+    size_t need = 64 + (size_t)nb * sizeof(BufState) + (size_t)T * sizeof(int) +
+                  (size_t)nb * std::max(remove, 1) * sizeof(int) + 8 +
+                  (size_t)nb * sizeof(unsigned long long);
+    SCPL_CUDA(h, h->h_small.ensure(need));
+    BufState *hb = reinterpret_cast<BufState *>(h->h_small.as<char>() + 64);
+    int *hbof = reinterpret_cast<int *>(hb + nb);
+    int *hklog = hbof + T;
+    long long yfm_total = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int nt = starts[b + 1] - starts[b];
+        const int tp = (nt + 15) & ~15;
+        const long long e0 = b < h->e0cap ? (long long)b * H * W : -1;
+        hb[b] = BufState{starts[b], nt, W, 0, 0, 0, target_W, 0, tp, 0, yfm_total, e0};
+        yfm_total += (long long)H * W * tp;
+        for (int t = starts[b]; t < starts[b + 1]; ++t) hbof[t] = b;
+    }
+    SCPL_CUDA(h, h->Yfm.ensure((size_t)std::max<long long>(yfm_total, 16)));
+    ws.Yfm = h->Yfm.as<uint8_t>();
+    ws.E0 = h->E0.as<int32_t>();
+    SCPL_CUDA(h, cudaMemcpyAsync(ws.st, hb, (size_t)nb * sizeof(BufState),
+                                 cudaMemcpyHostToDevice, st));
+    SCPL_CUDA(h, cudaMemcpyAsync(h->bof.p, hbof, (size_t)T * sizeof(int), cudaMemcpyHostToDevice,
+                                 st));
+    const long seam_stride = (long)remove * H;
+
+    SCPL_CUDA(h, cudaMemsetAsync(ws.dirty_count, 0, (size_t)nb * sizeof(unsigned long long), st));
+    // host path: gather buffer b on the side stream once carved, then copy its
+    // frames to the host on the copy stream
+    std::vector<char> gathered(nb, 0);
+    cudaEvent_t ev_carved = nullptr, ev_gathered = nullptr;
+    if (host_out) {
+        SCPL_CUDA(h, cudaEventCreateWithFlags(&ev_carved, cudaEventDisableTiming));
+        SCPL_CUDA(h, cudaEventCreateWithFlags(&ev_gathered, cudaEventDisableTiming));
+    }
+    struct EvGuard {
+        cudaEvent_t a, b;
+        ~EvGuard() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev_guard{ev_carved, ev_gathered};
+    const size_t frame_out = (size_t)H * target_W * 3;
+    auto gather_out = [&](int b) -> scpl_status {
+        const int t0 = starts[b], nt = starts[b + 1] - starts[b];
+        SCPL_CUDA(h, cudaEventRecord(ev_carved, st));
+        SCPL_CUDA(h, cudaStreamWaitEvent(h->gstream, ev_carved, 0));
+        SCPL_CUDA(h, timed_on(h, K_GATHER, h->gstream, [&] {
+                      return launch_gather_range(ws, frames, t0, nt, h->bof.as<int>(), target_W,
+                                                 out, h->gstream);
+                  }));
+        SCPL_CUDA(h, cudaEventRecord(ev_gathered, h->gstream));
+        SCPL_CUDA(h, cudaStreamWaitEvent(h->cstream, ev_gathered, 0));
+        SCPL_CUDA(h, cudaMemcpyAsync(host_out + (size_t)t0 * frame_out, out + (size_t)t0 * frame_out,
+                                     (size_t)nt * frame_out, cudaMemcpyDeviceToHost, h->cstream));
+        gathered[b] = 1;
+        return SCPL_OK;
+    };
+    if (remove == 0) {
+        SCPL_CUDA(h, timed(h, K_IDENTITY, [&] { return launch_identity_O(ws, nb, st); }));
+    } else {
+        SCPL_CUDA(h, timed(h, K_ENERGY_INIT, [&] { return launch_energy_init(ws, nb, st); }));
+        int iters = (remove + k - 1) / k;
+        for (int guard = 0; guard <= remove; ++guard) {
+            for (int q = 0; q < iters; ++q) {
+                SCPL_CUDA(h, timed(h, K_DP_SELECT, [&] {
+                              return ws.J ? launch_dpc(ws, nb, k, seams, seam_stride, st)
+                                          : launch_dp_select(ws, nb, k, seams, seam_stride, st);
+                          }));
+                SCPL_CUDA(h, timed(h, K_ENERGY_ITER, [&] { return launch_update(ws, nb, st); }));
+            }
+            SCPL_CUDA(h, cudaMemcpyAsync(hb, ws.st, (size_t)nb * sizeof(BufState),
+                                         cudaMemcpyDeviceToHost, st));
+            SCPL_CUDA(h, cudaStreamSynchronize(st));
+            if (host_out)   // buffers that reached the target: gather and send them now
+                for (int b = 0; b < nb; ++b)
+                    if (!gathered[b] && hb[b].W - hb[b].k_eff <= target_W) {
+                        if ((s = gather_out(b)) != SCPL_OK) return s;
+                    }
+            int max_rem = 0, min_k = k;
+            for (int b = 0; b < nb; ++b) {
+                int Wc = hb[b].W - hb[b].k_eff;
+                int r = Wc - target_W;
+                if (r > 0) {
+                    max_rem = std::max(max_rem, r);
+                    min_k = std::min(min_k, std::max(hb[b].k_eff, 1));
+                }
+            }
+            if (max_rem == 0) break;
+            iters = (max_rem + min_k - 1) / min_k;
+        }
+    }
+    if (host_out) {
+        for (int b = 0; b < nb; ++b)
+            if (!gathered[b] && (s = gather_out(b)) != SCPL_OK) return s;
+    } else {
+        SCPL_CUDA(h, timed(h, K_GATHER, [&] {
+                      return launch_gather(ws, frames, T, h->bof.as<int>(), target_W, out, st);
+                  }));
+    }
+
+    // iteration summary (and the algorithmic bytes while profiling)
+    h->last_nb = nb;
+    h->last_iter_max = 0;
+    h->last_iter_total = 0;
+    h->last_carved_px = 0;
+    if (remove > 0) {
+        unsigned long long *hdirty = reinterpret_cast<unsigned long long *>(
+            h->h_small.as<char>() + 64 + (((size_t)nb * sizeof(BufState) + (size_t)T * sizeof(int) +
+                                           (size_t)nb * remove * sizeof(int) + 7) & ~(size_t)7));
+        SCPL_CUDA(h, cudaMemcpyAsync(hklog, ws.klog, (size_t)nb * remove * sizeof(int),
+                                     cudaMemcpyDeviceToHost, st));
+        SCPL_CUDA(h, cudaMemcpyAsync(hdirty, ws.dirty_count, (size_t)nb * sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToHost, st));
+        SCPL_CUDA(h, cudaStreamSynchronize(st));
+        for (int b = 0; b < nb; ++b) {
+            const double Tb = hb[b].nt;
+            int Wc = W, it = 0;
+            while (Wc > target_W && it < remove) {
+                const int ke = hklog[(long)b * remove + it];
+                const int Wn = Wc - ke;
+                h->last_carved_px += (double)H * Wc;
+                if (h->prof.on) {
+                    // DP: E read, directions written and read back, lists written
+                    h->prof.bytes[K_DP_SELECT] += H * (4.5 * Wc + 2.0 * ke);
+                    // update: O and E read (gathered) and written at the new width,
+                    // the removal lists of each row and its two neighbours
+                    if (Wn > target_W)
+                        h->prof.bytes[K_ENERGY_ITER] += H * (12.0 * Wn + 6.0 * ke);
+                    else
+                        h->prof.bytes[K_ENERGY_ITER] += H * (4.0 * Wn + 6.0 * ke);
+                }
+                Wc = Wn;
+                ++it;
+            }
+            h->last_iter_max = std::max(h->last_iter_max, it);
+            h->last_iter_total += it;
+            if (h->prof.on) {
+                // first iteration: luma and motion of every frame, O, SDo, E out
+                h->prof.bytes[K_ENERGY_INIT] += H * (2.0 * Tb * W + 10.0 * W);
+                // recomputed pixels: 3 luma bytes of every frame, SDo read, E write
+                h->prof.bytes[K_ENERGY_ITER] += (double)hdirty[b] * (3.0 * Tb + 8.0);
+            }
+        }
+    }
+    if (h->prof.on) {
+        h->prof.bytes[K_GATHER] += (double)H * target_W * (6.0 * T + 2.0 * nb);
+        if (remove == 0) h->prof.bytes[K_IDENTITY] += 2.0 * H * W * nb;
+    }
+    int *herr = reinterpret_cast<int *>(h->h_small.as<char>());
+    SCPL_CUDA(h, cudaMemcpyAsync(herr, ws.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SCPL_CUDA(h, cudaStreamSynchronize(st));
+    if (*herr == DEV_ETIMEOUT)
+        return fail(h, SCPL_ETIMEOUT, "a bounded device-side wait ran out while carving");
+    if (*herr != DEV_OK)
+        return fail(h, SCPL_ECUDA, "internal consistency check failed on the device (%d)", *herr);
+    if (buffer_starts) std::copy(starts.begin(), starts.end(), buffer_starts);
+    if (n_buffers) *n_buffers = nb;
+    return SCPL_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void scpl_default_params(scpl_params *p) {
@@ -359,6 +580,9 @@ void scpl_destroy(scpl_handle h) {
                       &h->in_frames, &h->out_frames, &h->seams_dev, &h->Yfm};
     for (DevBuf *b : bufs) b->release();
     engine_destroy(h->engine);
+    if (h->cstream) cudaStreamDestroy(h->cstream);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
+    h->ready.release();
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
     h->h_small.release();
     delete h;
@@ -444,142 +668,8 @@ scpl_status scpl_seams(scpl_handle h, const int32_t *energy, int H, int W, int k
 scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W, int target_W,
                        int k, uint8_t *out, int32_t *buffer_starts, int *n_buffers,
                        int16_t *seams) {
-    scpl_status s = check_frames(h, frames, T, H, W);
-    if (s != SCPL_OK) return s;
-    if (!out) return fail(h, SCPL_EINVAL, "out is NULL");
-    if (target_W < 2 || target_W > W)
-        return fail(h, SCPL_EINVAL, "target_W=%d must be in [2, W=%d]", target_W, W);
-    if (k < 1) return fail(h, SCPL_EINVAL, "k=%d must be >= 1", k);
-    if ((s = check_overflow(h, T, H)) != SCPL_OK) return s;
-
-    std::vector<int> starts;
-    if ((s = run_scan(h, frames, T, H, W, starts, true)) != SCPL_OK) return s;
-    const int nb = (int)starts.size() - 1;
-    const int remove = W - target_W;
-    CarveWs ws;
-    if ((s = carve_ws(h, nb, H, W, std::min(k, std::max(remove, 1)), ws, remove)) != SCPL_OK)
-        return s;
-    cudaStream_t st = h->stream;
-
-    // per-buffer states and the frame -> buffer map
-    SCPL_CUDA(h, h->bof.ensure((size_t)T * sizeof(int)));
-    size_t need = 64 + (size_t)nb * sizeof(BufState) + (size_t)T * sizeof(int) +
-                  (size_t)nb * std::max(remove, 1) * sizeof(int) + 8 +
-                  (size_t)nb * sizeof(unsigned long long);
-    SCPL_CUDA(h, h->h_small.ensure(need));
-    BufState *hb = reinterpret_cast<BufState *>(h->h_small.as<char>() + 64);
-    int *hbof = reinterpret_cast<int *>(hb + nb);
-    int *hklog = hbof + T;
-    long long yfm_total = 0;
-    for (int b = 0; b < nb; ++b) {
-        const int nt = starts[b + 1] - starts[b];
-        const int tp = (nt + 15) & ~15;
-        const long long e0 = b < h->e0cap ? (long long)b * H * W : -1;
-        hb[b] = BufState{starts[b], nt, W, 0, 0, 0, target_W, 0, tp, 0, yfm_total, e0};
-        yfm_total += (long long)H * W * tp;
-        for (int t = starts[b]; t < starts[b + 1]; ++t) hbof[t] = b;
-    }
-    SCPL_CUDA(h, h->Yfm.ensure((size_t)std::max<long long>(yfm_total, 16)));
-    ws.Yfm = h->Yfm.as<uint8_t>();
-    ws.E0 = h->E0.as<int32_t>();
-    SCPL_CUDA(h, cudaMemcpyAsync(ws.st, hb, (size_t)nb * sizeof(BufState),
-                                 cudaMemcpyHostToDevice, st));
-    SCPL_CUDA(h, cudaMemcpyAsync(h->bof.p, hbof, (size_t)T * sizeof(int), cudaMemcpyHostToDevice,
-                                 st));
-    const long seam_stride = (long)remove * H;
-
-    SCPL_CUDA(h, cudaMemsetAsync(ws.dirty_count, 0, (size_t)nb * sizeof(unsigned long long), st));
-    if (remove == 0) {
-        SCPL_CUDA(h, timed(h, K_IDENTITY, [&] { return launch_identity_O(ws, nb, st); }));
-    } else {
-        SCPL_CUDA(h, timed(h, K_ENERGY_INIT, [&] { return launch_energy_init(ws, nb, st); }));
-        int iters = (remove + k - 1) / k;
-        for (int guard = 0; guard <= remove; ++guard) {
-            for (int q = 0; q < iters; ++q) {
-                SCPL_CUDA(h, timed(h, K_DP_SELECT, [&] {
-                              return ws.J ? launch_dpc(ws, nb, k, seams, seam_stride, st)
-                                          : launch_dp_select(ws, nb, k, seams, seam_stride, st);
-                          }));
-                SCPL_CUDA(h, timed(h, K_ENERGY_ITER, [&] { return launch_update(ws, nb, st); }));
-            }
-            SCPL_CUDA(h, cudaMemcpyAsync(hb, ws.st, (size_t)nb * sizeof(BufState),
-                                         cudaMemcpyDeviceToHost, st));
-            SCPL_CUDA(h, cudaStreamSynchronize(st));
-            int max_rem = 0, min_k = k;
-            for (int b = 0; b < nb; ++b) {
-                int Wc = hb[b].W - hb[b].k_eff;
-                int r = Wc - target_W;
-                if (r > 0) {
-                    max_rem = std::max(max_rem, r);
-                    min_k = std::min(min_k, std::max(hb[b].k_eff, 1));
-                }
-            }
-            if (max_rem == 0) break;
-            iters = (max_rem + min_k - 1) / min_k;
-        }
-    }
-    SCPL_CUDA(h, timed(h, K_GATHER, [&] {
-                  return launch_gather(ws, frames, T, h->bof.as<int>(), target_W, out, st);
-              }));
-
-    // iteration summary (and the algorithmic bytes while profiling)
-    h->last_nb = nb;
-    h->last_iter_max = 0;
-    h->last_iter_total = 0;
-    h->last_carved_px = 0;
-    if (remove > 0) {
-        unsigned long long *hdirty = reinterpret_cast<unsigned long long *>(
-            h->h_small.as<char>() + 64 + (((size_t)nb * sizeof(BufState) + (size_t)T * sizeof(int) +
-                                           (size_t)nb * remove * sizeof(int) + 7) & ~(size_t)7));
-        SCPL_CUDA(h, cudaMemcpyAsync(hklog, ws.klog, (size_t)nb * remove * sizeof(int),
-                                     cudaMemcpyDeviceToHost, st));
-        SCPL_CUDA(h, cudaMemcpyAsync(hdirty, ws.dirty_count, (size_t)nb * sizeof(unsigned long long),
-                                     cudaMemcpyDeviceToHost, st));
-        SCPL_CUDA(h, cudaStreamSynchronize(st));
-        for (int b = 0; b < nb; ++b) {
-            const double Tb = hb[b].nt;
-            int Wc = W, it = 0;
-            while (Wc > target_W && it < remove) {
-                const int ke = hklog[(long)b * remove + it];
-                const int Wn = Wc - ke;
-                h->last_carved_px += (double)H * Wc;
-                if (h->prof.on) {
-                    // DP: E read, directions written and read back, lists written
-                    h->prof.bytes[K_DP_SELECT] += H * (4.5 * Wc + 2.0 * ke);
-                    // update: O and E read (gathered) and written at the new width,
-                    // the removal lists of each row and its two neighbours
-                    if (Wn > target_W)
-                        h->prof.bytes[K_ENERGY_ITER] += H * (12.0 * Wn + 6.0 * ke);
-                    else
-                        h->prof.bytes[K_ENERGY_ITER] += H * (4.0 * Wn + 6.0 * ke);
-                }
-                Wc = Wn;
-                ++it;
-            }
-            h->last_iter_max = std::max(h->last_iter_max, it);
-            h->last_iter_total += it;
-            if (h->prof.on) {
-                // first iteration: luma and motion of every frame, O, SDo, E out
-                h->prof.bytes[K_ENERGY_INIT] += H * (2.0 * Tb * W + 10.0 * W);
-                // recomputed pixels: 3 luma bytes of every frame, SDo read, E write
-                h->prof.bytes[K_ENERGY_ITER] += (double)hdirty[b] * (3.0 * Tb + 8.0);
-            }
-        }
-    }
-    if (h->prof.on) {
-        h->prof.bytes[K_GATHER] += (double)H * target_W * (6.0 * T + 2.0 * nb);
-        if (remove == 0) h->prof.bytes[K_IDENTITY] += 2.0 * H * W * nb;
-    }
-    int *herr = reinterpret_cast<int *>(h->h_small.as<char>());
-    SCPL_CUDA(h, cudaMemcpyAsync(herr, ws.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    SCPL_CUDA(h, cudaStreamSynchronize(st));
-    if (*herr == DEV_ETIMEOUT)
-        return fail(h, SCPL_ETIMEOUT, "a bounded device-side wait ran out while carving");
-    if (*herr != DEV_OK)
-        return fail(h, SCPL_ECUDA, "internal consistency check failed on the device (%d)", *herr);
-    if (buffer_starts) std::copy(starts.begin(), starts.end(), buffer_starts);
-    if (n_buffers) *n_buffers = nb;
-    return SCPL_OK;
+    return carve_run(h, frames, T, H, W, target_W, k, out, buffer_starts, n_buffers, seams,
+                     nullptr, 1, nullptr);
 }
 
 scpl_status scpl_carve_host(scpl_handle h, const uint8_t *frames, int T, int H, int W,
@@ -590,21 +680,54 @@ scpl_status scpl_carve_host(scpl_handle h, const uint8_t *frames, int T, int H, 
     if (!out) return fail(h, SCPL_EINVAL, "out is NULL");
     if (target_W < 2 || target_W > W)
         return fail(h, SCPL_EINVAL, "target_W=%d must be in [2, W=%d]", target_W, W);
-    const size_t in_bytes = (size_t)T * H * W * 3;
-    const size_t out_bytes = (size_t)T * H * target_W * 3;
+    const size_t frame_in = (size_t)H * W * 3;
+    const size_t in_bytes = (size_t)T * frame_in;
     const size_t seam_bytes = (size_t)T * (W - target_W) * H * sizeof(int16_t);
     SCPL_CUDA(h, h->in_frames.ensure(in_bytes));
-    SCPL_CUDA(h, h->out_frames.ensure(out_bytes));
+    SCPL_CUDA(h, h->out_frames.ensure((size_t)T * H * target_W * 3));
     if (seams) SCPL_CUDA(h, h->seams_dev.ensure(std::max<size_t>(seam_bytes, 2)));
+    if (!h->cstream) SCPL_CUDA(h, cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
+    if (!h->gstream) SCPL_CUDA(h, cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
     cudaStream_t st = h->stream;
-    SCPL_CUDA(h, cudaMemcpyAsync(h->in_frames.p, frames, in_bytes, cudaMemcpyHostToDevice, st));
+    // The frames go up in chunks on the copy stream; after each chunk a
+    // stream memory operation raises the arrival counter, and the scan reads a
+    // frame only once its chunk has arrived.  The carved frames come back per
+    // buffer as the buffers finish.
+    PFN_cuStreamWriteValue32_v11070 write_value = stream_write_value();
+    const unsigned *ready = nullptr;
+    constexpr int CHUNK = 8;
+    SCPL_CUDA(h, h->ready.ensure(sizeof(unsigned)));
+    SCPL_CUDA(h, cudaMemsetAsync(h->ready.p, 0, sizeof(unsigned), st));
+    cudaEvent_t ev = nullptr;
+    SCPL_CUDA(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    SCPL_CUDA(h, cudaEventRecord(ev, st));
+    SCPL_CUDA(h, cudaStreamWaitEvent(h->cstream, ev, 0));   // no copy before the reset
+    cudaEventDestroy(ev);
+    if (write_value) {
+        for (int c = 0; c * CHUNK < T; ++c) {
+            const int f0 = c * CHUNK, nf = std::min(CHUNK, T - f0);
+            SCPL_CUDA(h, cudaMemcpyAsync(h->in_frames.as<uint8_t>() + f0 * frame_in,
+                                         frames + f0 * frame_in, (size_t)nf * frame_in,
+                                         cudaMemcpyHostToDevice, h->cstream));
+            if (write_value(reinterpret_cast<CUstream>(h->cstream),
+                            reinterpret_cast<CUdeviceptr>(h->ready.p), (cuuint32_t)(c + 1),
+                            CU_STREAM_WRITE_VALUE_DEFAULT) != CUDA_SUCCESS)
+                return fail(h, SCPL_ECUDA, "cuStreamWriteValue32 failed");
+        }
+        ready = h->ready.as<unsigned>();
+    } else {   // no stream memory operations: copy everything first
+        SCPL_CUDA(h, cudaMemcpyAsync(h->in_frames.p, frames, in_bytes, cudaMemcpyHostToDevice, st));
+    }
     int nb = 0;
     std::vector<int> starts(T + 1);
-    s = scpl_carve(h, h->in_frames.as<uint8_t>(), T, H, W, target_W, k,
-                   h->out_frames.as<uint8_t>(), starts.data(), &nb,
-                   seams ? h->seams_dev.as<int16_t>() : nullptr);
+    s = carve_run(h, h->in_frames.as<uint8_t>(), T, H, W, target_W, k,
+                  h->out_frames.as<uint8_t>(), starts.data(), &nb,
+                  seams ? h->seams_dev.as<int16_t>() : nullptr, ready, CHUNK, out);
+    cudaError_t e1 = cudaStreamSynchronize(h->cstream);
+    cudaError_t e2 = cudaStreamSynchronize(h->gstream);
     if (s != SCPL_OK) return s;
-    SCPL_CUDA(h, cudaMemcpyAsync(out, h->out_frames.p, out_bytes, cudaMemcpyDeviceToHost, st));
+    SCPL_CUDA(h, e1);
+    SCPL_CUDA(h, e2);
     if (seams)
         SCPL_CUDA(h, cudaMemcpyAsync(seams, h->seams_dev.p,
                                      (size_t)nb * (W - target_W) * H * sizeof(int16_t),

@@ -174,6 +174,10 @@ struct ScanArgs {
     long e0_plane;          // H * W
     long long *A_out;       // [T] A_t of every frame (diagnostic, or NULL)
     int *M_out;             // [T] maximum e_t of every frame (diagnostic)
+    // frames still arriving (or NULL): frame f may be read once *ready exceeds
+    // f / ready_frames; a copy stream raises it after every chunk it copies
+    const unsigned *ready;
+    int ready_frames;
 };
 
 // Launchers (return the CUDA error of the launch).
@@ -203,6 +207,10 @@ cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long se
 cudaError_t launch_identity_O(const CarveWs &ws, int nb, cudaStream_t s);
 cudaError_t launch_gather(const CarveWs &ws, const uint8_t *rgb, int T, const int *buf_of_frame,
                           int target, uint8_t *out, cudaStream_t s);
+// The colour gather of frames [t0, t0 + nt) only.
+cudaError_t launch_gather_range(const CarveWs &ws, const uint8_t *rgb, int t0, int nt,
+                                const int *buf_of_frame, int target, uint8_t *out,
+                                cudaStream_t s);
 // One frame of a batched colour gather: out rows of frame `dst` from `src`
 // (both [H][*][3], device) through the origin map of buffer b.
 struct GatherFrame {

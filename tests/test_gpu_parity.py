@@ -301,3 +301,19 @@ def test_carve_more_buffers_than_kept_sums(orc, lib, synth):
     f = synth.clip(40, 30, 64, seed=75)
     ref, got = _carve_both(orc, lib, f, 50, 4, t_max=2)
     _assert_same(ref, got)
+
+
+def test_carve_host_pipelined_matches_oracle(orc, lib, synth):
+    """37 frames arrive in 5 chunks while the scan runs; buffers are gathered
+    and sent back as each finishes.  Same bytes as the oracle."""
+    f = synth.clip(37, 60, 130, seed=95, cuts=(6, 11))
+    ref_out, ref_starts, ref_seams = orc.carve(f, 100, 8)
+    h = lib.scpl_create()
+    src = torch.from_numpy(f).pin_memory().numpy()
+    out = torch.zeros((37, 60, 100, 3), dtype=torch.uint8).pin_memory().numpy()
+    seams = np.zeros((37, 30, 60), np.int16)
+    starts = lib.scpl_carve_host(h, src, 100, 8, out, seams)
+    lib.scpl_destroy(h)
+    assert np.array_equal(starts, ref_starts)
+    assert np.array_equal(seams[: len(starts) - 1], ref_seams)
+    assert np.array_equal(out, ref_out)
