@@ -501,7 +501,8 @@ scpl_status launch_wave(Srv *s) {
     for (int i = 0; i < n; ++i) {
         const Pass &P = s->passes[take[i]];
         int g = 1 + (int)((double)(cap - n) * work[i] / std::max(wsum, 1.0));
-        g = std::min(g, scan_tiles(P.d.H, P.d.W));
+        const int tw = scan_tile_warps();
+        g = std::min(g, (scan_tiles(P.d.H, P.d.W) + tw - 1) / tw);   // a tile per warp at most
         G[i] = std::max(g, 1);
         total += G[i];
     }

@@ -21,8 +21,7 @@ namespace scpl {
 
 namespace {
 
-constexpr int TR = 8, TC = 128, SCAN_THREADS = 256;
-constexpr int LUMW = TC + 8;   // luma tile row: TC + 2 columns, padded to whole words
+constexpr int TR = 8, TC = 128, SCAN_THREADS = 128;
 enum { DEC_JOIN = 0, DEC_FLUSH = 1, DEC_CLOSE = 2 };
 
 __device__ __forceinline__ int luma_px(const uint8_t *p) {
@@ -35,6 +34,11 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -150,7 +154,7 @@ __device__ __forceinline__ uint32_t isqrt53(unsigned long long x) {
     const float r0f = xf > 0.0f ? xf * rsqrtf(xf) : 0.0f;
     const uint32_t r0 = __float2uint_rz(r0f);
     const long long R = (long long)x - (long long)((unsigned long long)r0 * r0);
-    const float d = __ll2float_rz(R) * __frcp_rz(2.0f * fmaxf(r0f, 1.0f));
+    const float d = __fdividef(__ll2float_rz(R), 2.0f * fmaxf(r0f, 1.0f));   // approximate
     uint32_t r = r0 + (uint32_t)__float2int_rd(d);
     r -= ((unsigned long long)r * r > x) ? 1u : 0u;
     r += ((unsigned long long)(r + 1) * (r + 1) <= x) ? 1u : 0u;
@@ -161,6 +165,14 @@ __device__ __forceinline__ uint32_t isqrt53(unsigned long long x) {
 // lane 1 = pixels 1 and 3 of a luma quad.
 __device__ __forceinline__ uint32_t even16(uint32_t q) { return __byte_perm(q, 0, 0x4240); }
 __device__ __forceinline__ uint32_t odd16(uint32_t q) { return __byte_perm(q, 0, 0x4341); }
+// |x - y| and max(x, y) per 16-bit lane with the DPX three-way max/min (the
+// per-lane difference max - min is never negative, so no borrow crosses lanes)
+__device__ __forceinline__ uint32_t absdiff16(uint32_t x, uint32_t y) {
+    return __vimax3_u16x2(x, y, 0u) - __vimin3_u16x2(x, y, 0xFFFFFFFFu);
+}
+__device__ __forceinline__ uint32_t max16(uint32_t x, uint32_t y, uint32_t z) {
+    return __vimax3_u16x2(x, y, z);
+}
 
 // Sobel |Gx| + |Gy| of 4 consecutive pixels from three luma rows.  Each row is
 // two aligned words holding the columns c-1 .. c+6 (bytes 0..7); the pixels
@@ -176,38 +188,22 @@ __device__ __forceinline__ void sobel4(uint32_t u0, uint32_t u1, uint32_t m0, ui
     const uint32_t rE = even16(uR) + 2 * even16(mR) + even16(dR);
     const uint32_t tE = even16(uL) + 2 * even16(uC) + even16(uR);
     const uint32_t bE = even16(dL) + 2 * even16(dC) + even16(dR);
-    g02 = __vabsdiffu2(rE, lE) + __vabsdiffu2(bE, tE);
+    g02 = absdiff16(rE, lE) + absdiff16(bE, tE);
     const uint32_t lO = odd16(uL) + 2 * odd16(mL) + odd16(dL);
     const uint32_t rO = odd16(uR) + 2 * odd16(mR) + odd16(dR);
     const uint32_t tO = odd16(uL) + 2 * odd16(uC) + odd16(uR);
     const uint32_t bO = odd16(dL) + 2 * odd16(dC) + odd16(dR);
-    g13 = __vabsdiffu2(rO, lO) + __vabsdiffu2(bO, tO);
+    g13 = absdiff16(rO, lO) + absdiff16(bO, tO);
 }
 
-// Tile ownership: CTA lb of a clip owns the contiguous tiles
-// [lb * tpc, (lb + 1) * tpc) for the whole clip, tpc = ceil(tiles / G).  Up to
-// MAXT tiles the CTA keeps S1 and S2 of its pixels in shared memory and the
-// previous frame's energy and luma in registers; beyond that they live in
-// global memory.
-constexpr int MAXT = 4;
-constexpr size_t SCAN_SMEM = (size_t)MAXT * SCAN_THREADS * 2 * sizeof(uint4);   // 32 KB
-
-struct TileCtx {
-    int r0, c0;      // tile origin
-    int row, col;    // this thread's row and first column
-    int nvalid;      // valid pixels of the quad (0..4)
-};
-
-__device__ __forceinline__ TileCtx tile_ctx(const ScanArgs &a, int tile, int tiles_x, int tid) {
-    TileCtx c;
-    const int ty = tile / tiles_x;
-    c.r0 = ty * TR;
-    c.c0 = (tile - ty * tiles_x) * TC;
-    c.row = c.r0 + (tid >> 5);
-    c.col = c.c0 + 4 * (tid & 31);
-    c.nvalid = c.row < a.H ? max(0, min(4, a.W - c.col)) : 0;
-    return c;
-}
+// Tile ownership: a tile is 8 rows x 128 columns and belongs to one warp for
+// the whole clip; lane l holds columns 4l .. 4l+3 of every row of it.  Warp gw
+// of a clip (CTA lb, warp w: gw = lb * SCAN_WARPS + w) owns the tiles
+// [gw * tpw, (gw + 1) * tpw), tpw = ceil(tiles / warps).  With one tile a warp
+// the running sums S1, S2 of its pixels stay in shared memory and the previous
+// frame's luma in registers ("resident"); with more they live in global memory.
+constexpr int SCAN_WARPS = SCAN_THREADS / 32;
+constexpr size_t SCAN_SMEM = (size_t)SCAN_WARPS * TR * 2 * 32 * sizeof(uint4);   // 32 KB
 
 // Luma of 4 pixels from their 12 RGB bytes (R G B R | G B R G | B R G B):
 // one byte dot product per pixel with the weights (77, 150, 29, 0).
@@ -218,48 +214,6 @@ __device__ __forceinline__ uint32_t luma4(uint32_t w0, uint32_t w1, uint32_t w2)
     const uint32_t y2 = __dp4a(__byte_perm(w1, w2, 0x0432), K, 128u) >> 8;
     const uint32_t y3 = __dp4a(w2 >> 8, K, 128u) >> 8;
     return y0 | (y1 << 8) | (y2 << 16) | (y3 << 24);
-}
-
-// Luma of the tile and its one-pixel frame (replicated at the image border)
-// into lum[r][j] = Y(r0 - 1 + r, c0 - 1 + j).  With W a multiple of 4 every
-// 4-pixel quad is three aligned words of RGB; otherwise pixel by pixel.
-__device__ __forceinline__ void load_luma(const ScanArgs &a, const uint8_t *f, int r0, int c0,
-                                          uint8_t (*lum)[LUMW]) {
-    const int tid = threadIdx.x;
-    if ((a.W & 3) == 0 && (reinterpret_cast<uintptr_t>(a.rgb) & 3) == 0) {
-        // body and top/bottom frame rows: (TR + 2) rows x 32 quads
-        for (int q = tid; q < (TR + 2) * 32; q += SCAN_THREADS) {
-            const int r = q >> 5, x = q & 31;
-            const int gi = clampi(r0 + r - 1, 0, a.H - 1);
-            const int gj = c0 + 4 * x;
-            uint32_t y = 0;
-            if (gj < a.W) {
-                const uint32_t *w =
-                    reinterpret_cast<const uint32_t *>(f + ((long)gi * a.W + gj) * 3);
-                y = luma4(__ldg(w), __ldg(w + 1), __ldg(w + 2));
-            } else {   // past the right edge: replicate the last column
-                y = luma_px(f + ((long)gi * a.W + a.W - 1) * 3) * 0x01010101u;
-            }
-            // columns c0 + 4x .. c0 + 4x + 3 sit at lum[r][1 + 4x ..]: unaligned by one
-            lum[r][1 + 4 * x] = (uint8_t)y;
-            lum[r][2 + 4 * x] = (uint8_t)(y >> 8);
-            lum[r][3 + 4 * x] = (uint8_t)(y >> 16);
-            lum[r][4 + 4 * x] = (uint8_t)(y >> 24);
-        }
-        // left and right frame columns
-        if (tid < 2 * (TR + 2)) {
-            const int r = tid >> 1, side = tid & 1;
-            const int gi = clampi(r0 + r - 1, 0, a.H - 1);
-            const int gj = clampi(side ? c0 + TC : c0 - 1, 0, a.W - 1);
-            lum[r][side ? TC + 1 : 0] = (uint8_t)luma_px(f + ((long)gi * a.W + gj) * 3);
-        }
-    } else {
-        for (int q = tid; q < (TR + 2) * (TC + 2); q += SCAN_THREADS) {
-            const int r = q / (TC + 2), c = q - r * (TC + 2);
-            const int gi = clampi(r0 + r - 1, 0, a.H - 1), gj = clampi(c0 + c - 1, 0, a.W - 1);
-            lum[r][c] = (uint8_t)luma_px(f + ((long)gi * a.W + gj) * 3);
-        }
-    }
 }
 
 // One clip per launch (tab == NULL, every CTA works on a0) or one clip per
@@ -274,18 +228,16 @@ __device__ __forceinline__ void load_luma(const ScanArgs &a, const uint8_t *f, i
 // closed buffer's sum is S1 minus the energies of frames f..w, S1/S2 restart
 // from e_f, and the next round re-evaluates frames f+1..w from their stored
 // energies.
-__global__ void __launch_bounds__(SCAN_THREADS, 4)
+__global__ void __launch_bounds__(SCAN_THREADS, 5)
 k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ block_clip) {
-    extern __shared__ __align__(16) uint4 sstate[];   // [MAXT][2][SCAN_THREADS] S1, S2
+    extern __shared__ __align__(16) uint4 sstate[];   // [SCAN_WARPS][TR][2][32] S1, S2
     __shared__ ScanArgs a;
-    __shared__ __align__(16) uint8_t lum[TR + 2][LUMW];
-    __shared__ unsigned long long red_a[SCAN_THREADS / 32];
-    __shared__ uint32_t red_m[SCAN_THREADS / 32];
+    __shared__ unsigned long long red_a[SCAN_WARPS];
+    __shared__ uint32_t red_m[SCAN_WARPS];
     __shared__ DecState st;
     __shared__ int s_ok, s_ndec, s_last;
-    __shared__ uint32_t s_rc[64];   // origins (r0 << 16 | c0) of the CTA's first 64 tiles
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) {
         if (tab) {
             a = tab[block_clip[blockIdx.x]];
@@ -297,93 +249,61 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
         st.n = 0; st.M = 0; st.start = 0; st.nb = 0;
     }
     __syncthreads();
+    // the clip's arguments live in shared memory; the hot loops use register
+    // copies (shared loads there could not be hoisted past the state stores)
+    const int H = a.H, W = a.W, T = a.T;
+    const uint32_t wg = (uint32_t)a.wg, wm = (uint32_t)a.wm;
+    const long ypitch = a.ypitch;
+    const uint8_t *__restrict__ rgb = a.rgb;
+    uint8_t *__restrict__ Yo = a.Y;
+    uint8_t *__restrict__ Do = a.D;
+    uint32_t *S1g = a.S1, *S2g = a.S2;
+    int32_t *E0 = a.E0;
+    const int nbcap = a.nbcap;
+    const long e0_plane = a.e0_plane;
+    const unsigned *ready = a.ready;
+    const int ready_frames = a.ready_frames;
     const int G = a.G;
     const int lb = blockIdx.x - a.cta0;   // CTA index within the clip's range
-    const int tiles_x = (a.W + TC - 1) / TC;
-    const int ntiles = ((a.H + TR - 1) / TR) * tiles_x;
-    const int tpc = (ntiles + G - 1) / G;
-    const int first = lb * tpc;
-    const int mine = max(0, min(tpc, ntiles - first));
-    const bool resident = tpc <= MAXT;
-    const long hw3 = (long)a.H * a.W * 3;
-    const long yplane = (long)a.H * a.ypitch;
-    const long eslot = (long)ntiles * SCAN_THREADS;   // uint2 entries per ring slot
-    uint2 *ering = reinterpret_cast<uint2 *>(a.ering);  // [SCAN_FW][ntiles][256] e quads
-    for (int k = tid; k < min(mine, 64); k += SCAN_THREADS) {
-        const int ty = (first + k) / tiles_x;
-        s_rc[k] = ((uint32_t)(ty * TR) << 16) | (uint32_t)((first + k - ty * tiles_x) * TC);
-    }
-    __syncthreads();
-    // the geometry of the CTA's k-th tile for this thread
-    auto ctx = [&](int k) {
-        if (k >= 64) return tile_ctx(a, first + k, tiles_x, tid);
-        TileCtx c;
-        c.r0 = (int)(s_rc[k] >> 16);
-        c.c0 = (int)(s_rc[k] & 0xFFFFu);
-        c.row = c.r0 + (tid >> 5);
-        c.col = c.c0 + 4 * (tid & 31);
-        c.nvalid = c.row < a.H ? max(0, min(4, a.W - c.col)) : 0;
-        return c;
-    };
-    uint32_t yp[MAXT];   // resident path: previous frame's luma quad per tile
+    const int tiles_x = (W + TC - 1) / TC;
+    const int ntiles = ((H + TR - 1) / TR) * tiles_x;
+    const int nwarps = G * SCAN_WARPS;
+    const int tpw = (ntiles + nwarps - 1) / nwarps;
+    const int gw = lb * SCAN_WARPS + w;
+    const int first = gw * tpw;
+    const int mine = max(0, min(tpw, ntiles - first));
+    const bool resident = tpw <= 1;
+    const bool words = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(rgb) & 3) == 0;
+    const bool pf_ok = (reinterpret_cast<uintptr_t>(rgb) & 15) == 0;   // prefetch needs 16-byte bases
+    const long hw3 = (long)H * W * 3;
+    const long yplane = (long)H * ypitch;
+    const long eslot = (long)ntiles * TR * 32;           // uint2 entries per ring slot
+    uint2 *ering = reinterpret_cast<uint2 *>(a.ering);  // [SCAN_FW][ntiles][TR][32] e quads
+    uint32_t yp[TR];   // resident path: previous frame's luma quad of every row
 #pragma unroll
-    for (int k = 0; k < MAXT; ++k) yp[k] = 0;
+    for (int r = 0; r < TR; ++r) yp[r] = 0;
 
-    // energy of frame t on one tile: luma and motion written out, the e quad
-    // (u16x2 pairs) stored in the ring
-    auto phase_a = [&](int t, int k, uint32_t &yprev, uint32_t &emax2) {
-        const int tile = first + k;
-        const TileCtx c = ctx(k);
-        const uint8_t *f = a.rgb + (long)t * hw3;
-        load_luma(a, f, c.r0, c.c0, lum);
-        __syncthreads();
-        const int rr = tid >> 5, cc = 4 * (tid & 31);
-        const uint32_t *L0 = reinterpret_cast<const uint32_t *>(&lum[rr][cc]);
-        const uint32_t *L1 = reinterpret_cast<const uint32_t *>(&lum[rr + 1][cc]);
-        const uint32_t *L2 = reinterpret_cast<const uint32_t *>(&lum[rr + 2][cc]);
-        uint32_t g02, g13;
-        sobel4(L0[0], L0[1], L1[0], L1[1], L2[0], L2[1], g02, g13);
-        const uint32_t ycur = __funnelshift_r(L1[0], L1[1], 8);
-        uint32_t yprv = yprev;
-        if (!resident && t > 0 && c.nvalid > 0)
-            yprv = *reinterpret_cast<const uint32_t *>(a.Y + (long)(t - 1) * yplane +
-                                                       (long)c.row * a.ypitch + c.col);
-        const uint32_t dq = t > 0 ? __vabsdiffu4(ycur, yprv) : 0u;
-        const uint32_t e02 = (uint32_t)a.wg * g02 + (uint32_t)a.wm * even16(dq);
-        const uint32_t e13 = (uint32_t)a.wg * g13 + (uint32_t)a.wm * odd16(dq);
-        if (c.nvalid > 0) {
-            // invalid pixels of a ragged quad do not count towards the maximum
-            const uint32_t m02 = c.nvalid >= 3 ? e02 : (e02 & 0xFFFFu);
-            const uint32_t m13 = c.nvalid >= 4 ? e13 : (c.nvalid >= 2 ? (e13 & 0xFFFFu) : 0u);
-            emax2 = __vmaxu2(emax2, __vmaxu2(m02, m13));
-            const long yo = (long)t * yplane + (long)c.row * a.ypitch + c.col;
-            *reinterpret_cast<uint32_t *>(a.Y + yo) = ycur;
-            *reinterpret_cast<uint32_t *>(a.D + yo) = dq;
-        }
-        ering[(long)(t % SCAN_FW) * eslot + (long)tile * SCAN_THREADS + tid] = make_uint2(e02, e13);
-        yprev = ycur;
-        __syncthreads();   // lum is reused by the next tile
-    };
-
-    auto state_ptrs = [&](int k, int tile, uint4 *&S1p, uint4 *&S2p) {
+    auto state_ptrs = [&](int tile, int r, uint4 *&S1p, uint4 *&S2p) {
         if (resident) {
-            S1p = &sstate[(k * 2) * SCAN_THREADS + tid];
-            S2p = &sstate[(k * 2 + 1) * SCAN_THREADS + tid];
+            S1p = &sstate[((w * TR + r) * 2) * 32 + lane];
+            S2p = &sstate[((w * TR + r) * 2 + 1) * 32 + lane];
         } else {
-            const long sidx = (long)tile * SCAN_THREADS + tid;
-            S1p = reinterpret_cast<uint4 *>(a.S1) + sidx;
-            S2p = reinterpret_cast<uint4 *>(a.S2) + sidx;
+            const long sidx = ((long)tile * TR + r) * 32 + lane;
+            S1p = reinterpret_cast<uint4 *>(S1g) + sidx;
+            S2p = reinterpret_cast<uint4 *>(S2g) + sidx;
         }
     };
+    auto ering_at = [&](int f, int tile, int r) -> uint2 & {
+        return ering[(long)(f % SCAN_FW) * eslot + ((long)tile * TR + r) * 32 + lane];
+    };
 
-    // fold frame t into S1/S2 of one tile (restart when `fresh`) and add its
-    // floor(sqrt(65536 (n S2 - S1^2))) over the valid pixels to acc
-    auto fold = [&](int t, int k, int tile, bool fresh, int n1, unsigned long long &acc) {
-        const TileCtx c = ctx(k);
+    // fold one row's energy quad into S1/S2 (restart when `fresh`) and add
+    // floor(sqrt(65536 (n S2 - S1^2))) of its valid pixels to acc
+    auto fold = [&](int tile, int r, uint32_t e02, uint32_t e13, int nv, bool fresh, int n1,
+                    unsigned long long &acc) {
         uint4 *S1p, *S2p;
-        state_ptrs(k, tile, S1p, S2p);
-        const uint2 e = ering[(long)(t % SCAN_FW) * eslot + (long)tile * SCAN_THREADS + tid];
-        const uint32_t ev[4] = {e.x & 0xFFFFu, e.y & 0xFFFFu, e.x >> 16, e.y >> 16};
+        state_ptrs(tile, r, S1p, S2p);
+        const uint32_t ev[4] = {e02 & 0xFFFFu, e13 & 0xFFFFu, e02 >> 16, e13 >> 16};
         uint4 s1 = make_uint4(0, 0, 0, 0), s2 = make_uint4(0, 0, 0, 0);
         if (!fresh) {
             s1 = *S1p;
@@ -394,7 +314,7 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
         for (int v = 0; v < 4; ++v) {
             S1v[v] += ev[v];
             S2v[v] += ev[v] * ev[v];
-            if (v < c.nvalid) {
+            if (v < nv) {
                 const unsigned long long Q =
                     (unsigned long long)n1 * S2v[v] - (unsigned long long)S1v[v] * S1v[v];
                 acc += isqrt53(Q << 16);
@@ -404,19 +324,132 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
         *S2p = s2;
     };
 
-    // block sum of acc and maximum of emax2 (thread 0 receives them)
+    // frame f on one tile: (fresh_frame) the energy of every row from the RGB
+    // frame, luma and motion written out, the energy kept in the ring; then
+    // every row folded into the running sums.  Rows are software-pipelined:
+    // the raw bytes of row i+2 are loaded while row i is computed.
+    auto tile_frame = [&](int f, int tile, bool fresh_frame, bool fresh, int n1,
+                          unsigned long long &acc, uint32_t &emax2) {
+        const int ty = tile / tiles_x;
+        const int r0 = ty * TR, c0 = (tile - ty * tiles_x) * TC;
+        const int col = c0 + 4 * lane;
+        const int nvq = max(0, min(4, W - col));
+        if (!fresh_frame) {
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+                const int nv = r0 + r < H ? nvq : 0;
+                const uint2 e = ering_at(f, tile, r);
+                fold(tile, r, e.x, e.y, nv, fresh, n1, acc);
+            }
+            return;
+        }
+        const uint8_t *fr = rgb + (long)f * hw3;
+        // the tile's rows of the next frame into L2 now, so that its loads
+        // wait for L2 instead of DRAM; ranges rounded inwards to 16 bytes
+        // and kept inside the clip
+        if (pf_ok && lane < TR + 2 && f + 1 < T) {
+            const int row = clampi(r0 - 1 + lane, 0, H - 1);
+            const long base = ((long)(f + 1) * H + row) * W * 3;
+            const long lo = (base + 3L * max(c0 - 1, 0)) & ~15L;
+            const long hi = (base + 3L * min(c0 + TC + 1, W)) & ~15L;
+            if (hi > lo) prefetch_l2(rgb + lo, (unsigned)(hi - lo));
+        }
+        const bool fastq = words && col + 3 < W;
+        const int ecol = lane == 0 ? max(c0 - 1, 0) : min(c0 + TC, W - 1);
+        // raw bytes of one row: the quad's 3 RGB words (or, off the fast path,
+        // its luma already packed in w0) and the edge pixel of lanes 0 and 31
+        struct Raw { uint32_t w0, w1, w2, e0, e1, e2; };
+        auto fetch = [&](int row) {
+            Raw x;
+            const uint8_t *rp = fr + (long)clampi(row, 0, H - 1) * W * 3;
+            if (fastq) {
+                const uint32_t *w = reinterpret_cast<const uint32_t *>(rp + col * 3);
+                x.w0 = __ldg(w);
+                x.w1 = __ldg(w + 1);
+                x.w2 = __ldg(w + 2);
+            } else {
+                x.w0 = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    x.w0 |= (uint32_t)luma_px(rp + min(col + j, W - 1) * 3) << (8 * j);
+                x.w1 = x.w2 = 0;
+            }
+            x.e0 = x.e1 = x.e2 = 0;
+            if (lane == 0 || lane == 31) {
+                const uint8_t *ep = rp + ecol * 3;
+                x.e0 = __ldg(ep);
+                x.e1 = __ldg(ep + 1);
+                x.e2 = __ldg(ep + 2);
+            }
+            return x;
+        };
+        // luma quad and its 8-byte window from raw bytes (shuffles: all lanes)
+        auto window = [&](const Raw &x, uint32_t &q, uint32_t &u0, uint32_t &u1) {
+            q = fastq ? luma4(x.w0, x.w1, x.w2) : x.w0;
+            const uint32_t ey = (77u * x.e0 + 150u * x.e1 + 29u * x.e2 + 128u) >> 8;
+            uint32_t lq = __shfl_up_sync(0xffffffffu, q, 1);
+            uint32_t rq = __shfl_down_sync(0xffffffffu, q, 1);
+            if (lane == 0) lq = ey << 24;
+            if (lane == 31) rq = ey;
+            u0 = __byte_perm(lq, q, 0x6543);
+            u1 = __byte_perm(q, rq, 0x0043);
+        };
+        uint32_t qa, qb, a0, a1, b0, b1;
+        {
+            const Raw xa = fetch(r0 - 1), xb = fetch(r0);
+            Raw xc = fetch(r0 + 1);
+            window(xa, qa, a0, a1);
+            window(xb, qb, b0, b1);
+#pragma unroll
+            for (int r = 0; r < TR; ++r) {
+                const int i = r0 + r;
+                const Raw xn = fetch(i + 2);   // two rows ahead
+                uint32_t qc, c0w, c1w;
+                window(xc, qc, c0w, c1w);
+                uint32_t g02, g13;
+                sobel4(a0, a1, b0, b1, c0w, c1w, g02, g13);
+                uint32_t yprv = yp[r];
+                const int nv = i < H ? nvq : 0;
+                if (!resident && f > 0 && nv > 0)
+                    yprv = *reinterpret_cast<const uint32_t *>(Yo + (long)(f - 1) * yplane +
+                                                               (long)i * ypitch + col);
+                // motion |Y_t - Y_{t-1}| on the u16 halves the energy uses
+                const uint32_t d02 = f > 0 ? absdiff16(even16(qb), even16(yprv)) : 0u;
+                const uint32_t d13 = f > 0 ? absdiff16(odd16(qb), odd16(yprv)) : 0u;
+                const uint32_t dq = __byte_perm(d02, d13, 0x6240);   // back to 4 bytes
+                const uint32_t e02 = wg * g02 + wm * d02;
+                const uint32_t e13 = wg * g13 + wm * d13;
+                if (nv > 0) {
+                    // invalid pixels of a ragged quad do not count towards the maximum
+                    const uint32_t m02 = nv >= 3 ? e02 : (e02 & 0xFFFFu);
+                    const uint32_t m13 = nv >= 4 ? e13 : (nv >= 2 ? (e13 & 0xFFFFu) : 0u);
+                    emax2 = max16(emax2, m02, m13);
+                    const long yo = (long)f * yplane + (long)i * ypitch + col;
+                    *reinterpret_cast<uint32_t *>(Yo + yo) = qb;
+                    *reinterpret_cast<uint32_t *>(Do + yo) = dq;
+                }
+                ering_at(f, tile, r) = make_uint2(e02, e13);
+                yp[r] = qb;
+                fold(tile, r, e02, e13, nv, fresh, n1, acc);
+                a0 = b0; a1 = b1; b0 = c0w; b1 = c1w; qb = qc;
+                xc = xn;
+            }
+        }
+    };
+
+    // block sum of acc and maximum of em (thread 0 receives them)
     auto block_reduce = [&](unsigned long long &acc, uint32_t &em) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             acc += __shfl_xor_sync(0xffffffffu, acc, o);
             em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
         }
-        if ((tid & 31) == 0) { red_a[tid >> 5] = acc; red_m[tid >> 5] = em; }
+        if (lane == 0) { red_a[w] = acc; red_m[w] = em; }
         __syncthreads();
         if (tid == 0) {
             unsigned long long A = 0;
             uint32_t m = 0;
-            for (int w = 0; w < SCAN_THREADS / 32; ++w) { A += red_a[w]; m = max(m, red_m[w]); }
+            for (int q = 0; q < SCAN_WARPS; ++q) { A += red_a[q]; m = max(m, red_m[q]); }
             acc = A;
             em = m;
         }
@@ -426,48 +459,52 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
     // summed energy of buffer bi (the E0 plane) for the valid pixels of my tiles:
     // S1 minus the ring energies of frames [g0, g1)
     auto write_e0 = [&](int bi, int g0, int g1) {
-        if (!a.E0 || bi >= a.nbcap) return;
+        if (!E0 || bi >= nbcap) return;
         for (int k = 0; k < mine; ++k) {
             const int tile = first + k;
-            const TileCtx c = ctx(k);
-            if (c.nvalid == 0) continue;
-            uint4 *S1p, *S2p;
-            state_ptrs(k, tile, S1p, S2p);
-            uint4 s1 = *S1p;
-            uint32_t *S1v = &s1.x;
-            for (int g = g0; g < g1; ++g) {
-                const uint2 e = ering[(long)(g % SCAN_FW) * eslot + (long)tile * SCAN_THREADS + tid];
-                S1v[0] -= e.x & 0xFFFFu;
-                S1v[1] -= e.y & 0xFFFFu;
-                S1v[2] -= e.x >> 16;
-                S1v[3] -= e.y >> 16;
-            }
+            const int ty = tile / tiles_x;
+            const int r0 = ty * TR, col = (tile - ty * tiles_x) * TC + 4 * lane;
+            const int nvq = max(0, min(4, W - col));
+            for (int r = 0; r < TR; ++r) {
+                if (r0 + r >= H || nvq == 0) continue;
+                uint4 *S1p, *S2p;
+                state_ptrs(tile, r, S1p, S2p);
+                uint4 s1 = *S1p;
+                uint32_t *S1v = &s1.x;
+                for (int g = g0; g < g1; ++g) {
+                    const uint2 e = ering_at(g, tile, r);
+                    S1v[0] -= e.x & 0xFFFFu;
+                    S1v[1] -= e.y & 0xFFFFu;
+                    S1v[2] -= e.x >> 16;
+                    S1v[3] -= e.y >> 16;
+                }
 #pragma unroll
-            for (int v = 0; v < 4; ++v)
-                if (v < c.nvalid)
-                    a.E0[(long)bi * a.e0_plane + (long)c.row * a.W + c.col + v] = (int32_t)S1v[v];
+                for (int v = 0; v < 4; ++v)
+                    if (v < nvq)
+                        E0[(long)bi * e0_plane + (long)(r0 + r) * W + col + v] =
+                            (int32_t)S1v[v];
+            }
         }
     };
 
-    int t = 0, horizon = 0, r = 0;
-    while (t < a.T) {
+    int t = 0, horizon = 0, rnd = 0;
+    while (t < T) {
         // the round's frames: up to SCAN_FW, ending where the open buffer
         // would reach t_max, and at the clip end
         const int n0 = st.n;
-        int w = min(t + SCAN_FW - 1, a.T - 1);
-        w = min(w, t + (a.t_max - n0) - 1);
-        for (int f = t; f <= w; ++f) {
-            uint32_t emax2 = 0;
+        int wend = min(t + SCAN_FW - 1, T - 1);
+        wend = min(wend, t + (a.t_max - n0) - 1);
+        for (int f = t; f <= wend; ++f) {
             const bool fresh_frame = f >= horizon;
-            if (fresh_frame && a.ready) {
+            if (fresh_frame && ready) {
                 // frame f may still be on its way from the host: wait (bounded)
                 // until the copy stream has raised the counter past its chunk
                 if (tid == 0) {
-                    const unsigned need = (unsigned)(f / a.ready_frames) + 1u;
+                    const unsigned need = (unsigned)(f / ready_frames) + 1u;
                     int ok = 1;
-                    if (ld_acquire_u32(a.ready) < need) {
+                    if (ld_acquire_u32(ready) < need) {
                         const unsigned long long t0 = globaltimer_ns();
-                        while (ld_acquire_u32(a.ready) < need) {
+                        while (ld_acquire_u32(ready) < need) {
                             if (*(volatile int *)a.err != DEV_OK) { ok = 0; break; }
                             if (globaltimer_ns() - t0 > a.spin_limit_ns) {
                                 atomicCAS(a.err, DEV_OK, DEV_ETIMEOUT);
@@ -482,49 +519,33 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
                 __syncthreads();
                 if (!s_ok) return;
             }
-            if (fresh_frame) {
-                if (resident) {
-#pragma unroll
-                    for (int k = 0; k < MAXT; ++k)
-                        if (k < mine) phase_a(f, k, yp[k], emax2);
-                } else {
-                    for (int k = 0; k < mine; ++k) {
-                        uint32_t ydummy = 0;
-                        phase_a(f, k, ydummy, emax2);
-                    }
-                }
-            }
             unsigned long long acc = 0;
+            uint32_t emax2 = 0;
             const bool fresh = n0 == 0 && f == t;   // the open buffer starts here
             const int n1 = n0 + (f - t) + 1;
-            if (resident) {
-#pragma unroll
-                for (int k = 0; k < MAXT; ++k)
-                    if (k < mine) fold(f, k, first + k, fresh, n1, acc);
-            } else {
-                for (int k = 0; k < mine; ++k) fold(f, k, first + k, fresh, n1, acc);
-            }
+            for (int k = 0; k < mine; ++k) tile_frame(f, first + k, fresh_frame, fresh, n1, acc, emax2);
             uint32_t em = max(emax2 & 0xFFFFu, emax2 >> 16);
             block_reduce(acc, em);
             if (tid == 0) {
-                atomicAdd(reinterpret_cast<unsigned long long *>(&a.partA[(long)r * SCAN_FW + (f - t)]),
+                atomicAdd(reinterpret_cast<unsigned long long *>(
+                              &a.partA[(long)rnd * SCAN_FW + (f - t)]),
                           acc);
                 if (fresh_frame) atomicMax(&a.partM[f], (int)em);
             }
         }
-        horizon = max(horizon, w + 1);
+        horizon = max(horizon, wend + 1);
         // publish the round, wait for the clip's other CTAs, replay decisions
         if (tid == 0) {
             __threadfence();
-            atomicAdd(&a.count[r], 1u);
-            int ok = wait_round(a, r, G) ? 1 : 0;
+            atomicAdd(&a.count[rnd], 1u);
+            int ok = wait_round(a, rnd, G) ? 1 : 0;
             int ndec = 0, last = DEC_JOIN;
             if (ok) {
                 __threadfence();
                 const bool lead = lb == 0;
-                for (int f = t; f <= w; ++f) {
+                for (int f = t; f <= wend; ++f) {
                     const long long A = (long long)__ldcg(reinterpret_cast<const unsigned long long *>(
-                        &a.partA[(long)r * SCAN_FW + (f - t)]));
+                        &a.partA[(long)rnd * SCAN_FW + (f - t)]));
                     const int m = __ldcg(&a.partM[f]);
                     if (lead && a.A_out) {
                         a.A_out[f] = A;
@@ -544,31 +565,33 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
         const int fend = t + s_ndec;   // first frame not yet decided
         if (s_last == DEC_FLUSH) {
             // frame fend-1 starts a new buffer: the closed one is S1 minus the
-            // energies of frames fend-1..w; S1/S2 restart from e_{fend-1}
+            // energies of frames fend-1..wend; S1/S2 restart from e_{fend-1}
             const int f = fend - 1;
-            write_e0(st.nb - 1, f, w + 1);
+            write_e0(st.nb - 1, f, wend + 1);
             for (int k = 0; k < mine; ++k) {
                 const int tile = first + k;
-                uint4 *S1p, *S2p;
-                state_ptrs(k, tile, S1p, S2p);
-                const uint2 e = ering[(long)(f % SCAN_FW) * eslot + (long)tile * SCAN_THREADS + tid];
-                const uint32_t ev[4] = {e.x & 0xFFFFu, e.y & 0xFFFFu, e.x >> 16, e.y >> 16};
-                *S1p = make_uint4(ev[0], ev[1], ev[2], ev[3]);
-                *S2p = make_uint4(ev[0] * ev[0], ev[1] * ev[1], ev[2] * ev[2], ev[3] * ev[3]);
+                for (int r = 0; r < TR; ++r) {
+                    uint4 *S1p, *S2p;
+                    state_ptrs(tile, r, S1p, S2p);
+                    const uint2 e = ering_at(f, tile, r);
+                    const uint32_t ev[4] = {e.x & 0xFFFFu, e.y & 0xFFFFu, e.x >> 16, e.y >> 16};
+                    *S1p = make_uint4(ev[0], ev[1], ev[2], ev[3]);
+                    *S2p = make_uint4(ev[0] * ev[0], ev[1] * ev[1], ev[2] * ev[2], ev[3] * ev[3]);
+                }
             }
         } else if (s_last == DEC_CLOSE) {
-            write_e0(st.nb - 1, w + 1, w + 1);   // the buffer ending with frame w
+            write_e0(st.nb - 1, wend + 1, wend + 1);   // the buffer ending with frame wend
         }
         __syncthreads();
         t = fend;
-        ++r;
+        ++rnd;
     }
     // the buffer still open at the clip end
-    if (st.n > 0) write_e0(st.nb, a.T, a.T);
+    if (st.n > 0) write_e0(st.nb, T, T);
     if (lb == 0 && tid == 0) {
         int nb = st.nb;
         if (st.n > 0) a.starts[nb++] = st.start;
-        a.starts[nb] = a.T;
+        a.starts[nb] = T;
         *a.n_buffers = nb;
     }
 }
@@ -585,13 +608,13 @@ cudaError_t launch_energy_api(const uint8_t *rgb, int T, int H, int W, int wg, i
 }
 
 // Co-resident CTAs for the cooperative scan: all SMs' worth, lowered so that
-// every CTA owns the same number of tiles.
+// every warp owns the same number of tiles.
 int scan_grid_size(int H, int W, int *err_out) {
     const int cap = scan_capacity(err_out);
     if (*err_out || cap < 1) return 0;
     const long ntiles = (long)((H + TR - 1) / TR) * ((W + TC - 1) / TC);
-    const long tpc = (ntiles + cap - 1) / cap;
-    return (int)((ntiles + tpc - 1) / tpc);
+    const long tpw = (ntiles + (long)cap * SCAN_WARPS - 1) / ((long)cap * SCAN_WARPS);
+    return (int)((ntiles + tpw * SCAN_WARPS - 1) / (tpw * SCAN_WARPS));
 }
 
 cudaError_t launch_scan(const ScanArgs &a, int grid, cudaStream_t s) {
@@ -633,6 +656,7 @@ int scan_capacity(int *err_out) {
 }
 
 int scan_tiles(int H, int W) { return ((H + TR - 1) / TR) * ((W + TC - 1) / TC); }
+int scan_tile_warps() { return SCAN_WARPS; }
 
 long scan_state_px(int H, int W) { return (long)scan_tiles(H, W) * TR * TC; }
 

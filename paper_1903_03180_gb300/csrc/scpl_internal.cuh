@@ -191,6 +191,7 @@ cudaError_t launch_scan_multi(const ScanArgs *tab, const int *block_clip, int gr
                               cudaStream_t s);
 int scan_capacity(int *err_out);   // co-resident scan CTAs on this GPU
 int scan_tiles(int H, int W);      // 8x128 tiles of one frame
+int scan_tile_warps();             // tile-owning warps per scan CTA
 long scan_state_px(int H, int W);  // pixels of the tile-major scan state
 
 cudaError_t launch_energy_init(const CarveWs &ws, int nb, cudaStream_t s);
