@@ -141,12 +141,18 @@ scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W
                        int k, uint8_t *out, int32_t *buffer_starts, int *n_buffers,
                        int16_t *seams);
 
-/* scpl_carve on host memory: copies frames in and out on the handle's stream
- * through library-owned device buffers (page-locked host memory makes the
- * copies asynchronous and fast; pageable memory works too).
+/* scpl_carve on host memory, through library-owned device buffers.  The
+ * copies overlap the work: frames go up in chunks of 8 on a copy stream and
+ * the buffer scan reads each chunk as soon as it has arrived (a stream memory
+ * operation raises a device counter after every chunk; the scan's wait for it
+ * is bounded and ends in SCPL_ETIMEOUT); every spatiotemporal buffer is
+ * gathered and copied back as soon as it is carved, while the others carve
+ * on.  Page-locked host memory makes the copies asynchronous; pageable memory
+ * works too, without the overlap.
  *   frames [host] uint8 [T][H][W][3]   out [host] uint8 [T][H][target_W][3]
  *   seams  [host] int16 [n_buffers][W - target_W][H] or NULL (size it for T
- *          buffers when the count is not known in advance) */
+ *          buffers when the count is not known in advance)
+ * Synchronises before returning. */
 scpl_status scpl_carve_host(scpl_handle h, const uint8_t *frames, int T, int H, int W,
                             int target_W, int k, uint8_t *out, int32_t *buffer_starts,
                             int *n_buffers, int16_t *seams);
@@ -207,16 +213,19 @@ scpl_status scpl_get_stats(scpl_handle h, scpl_stats *out);
  * Autotuning (no counterpart in the paper).  Per frame size (H, W, in carving
  * orientation) the carving kernels have choices that change only the time:
  * the cluster DP's halo depth R (16: 96 columns a warp, a halo exchange every
- * 16 rows; 32: 64 columns a warp, an exchange every 32 rows), the single-CTA
- * DP instead of the cluster, and the rows per update CTA.  A process-wide
+ * 16 rows; 32: 64 columns a warp, an exchange every 32 rows), its warps per
+ * CTA (4 or 8, i.e. how many CTAs carve one frame), the single-CTA DP instead
+ * of the cluster, and the rows per update CTA.  A process-wide
  * table holds one choice per size; scpl_carve, scpl_carve_batch and servers
  * use it when an entry exists, and the defaults (R = 32, the most update rows
  * that fit) otherwise. */
 typedef struct {
     int H, W;
     int dpc_halo;        /* 16 or 32: the cluster DP's R; 0: the single-CTA DP        */
+    int dpc_warps;       /* warps per cluster-DP CTA: 4 or 8 (8 halves the CTAs a frame) */
     int update_rows;     /* rows per update CTA: 1, 2 or 4                              */
-    float dp_us_r32, dp_us_r16, dp_us_single;   /* measured DP times, us (< 0: unusable) */
+    float dp_us[5];      /* measured DP times, us (< 0: unusable): R32 x 4 warps, R16 x 4,
+                            R32 x 8, R16 x 8, the single-CTA DP                        */
     float up_us[3];      /* measured update times with 1, 2 and 4 rows, us              */
 } scpl_tuning;
 

@@ -50,19 +50,23 @@ namespace scpl {
 
 namespace {
 
-constexpr int DPC_WPC = 4;                       // warps per CTA
 constexpr int DPC_V = 4;                         // columns per lane
 constexpr int DPC_S = 16;                        // rows per TMA stage of the energy ring
 // The halo depth R (16 or 32, a template parameter of k_dpc) is also the
 // number of rows between halo refreshes.  A warp's window is always 128
 // columns, so it owns 128 - 2R of them (96 or 64): R trades the exchange
 // frequency against the columns per warp.
-constexpr int DPC_NST = 4;                       // energy stages in flight
 constexpr int DPC_WW = 32 * DPC_V;               // columns of a warp's window: 128
 __host__ __device__ constexpr int dpc_oww(int R) { return DPC_WW - 2 * R; }
-__host__ __device__ constexpr int dpc_lmax(int R) { return DPC_WPC * dpc_oww(R); }
+// Warps per CTA (4 or 8, the other template parameter): with 8 the cluster
+// needs half the CTAs and two warps share an SM sub-partition, each warp's
+// energy ring then holding 2 stages instead of 4 to fit shared memory.
+__host__ __device__ constexpr int dpc_nst(int WPC) { return WPC == 8 ? 2 : 4; }
+__host__ __device__ constexpr int dpc_lmax(int R, int WPC) { return WPC * dpc_oww(R); }
 constexpr size_t DPC_WSLOT = (size_t)DPC_S * DPC_WW * 4;   // one warp's stage: 8 KB
-constexpr size_t DPC_RING = (size_t)DPC_WPC * DPC_NST * DPC_WSLOT;
+__host__ __device__ constexpr size_t dpc_ring(int WPC) {
+    return (size_t)WPC * dpc_nst(WPC) * DPC_WSLOT;
+}
 constexpr size_t DPC_STAGE_BUDGET = 96 * 1024;   // trace-back staging
 constexpr uint32_t BIG = 0x80000000u;            // energy of columns outside [0, W)
 constexpr uint32_t INF32 = 0xFFFFFFFFu;
@@ -147,15 +151,17 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t *mbar, unsigned parit
     return true;
 }
 
-template <int R>
-__global__ void __launch_bounds__(DPC_WPC * 32, 1)
+template <int R, int WPC>
+__global__ void __launch_bounds__(WPC * 32, 1)
 k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams,
       long seam_stride) {
+    constexpr int DPC_WPC = WPC;                  // warps per CTA
+    constexpr int DPC_NST = dpc_nst(WPC);         // energy stages in flight per warp
     constexpr int DPC_R = R;                      // rows between halo refreshes (= halo width)
     constexpr int DPC_SPR = DPC_R / DPC_S;        // stages per refresh
     constexpr int DPC_HL = DPC_R / DPC_V;         // halo lanes on each side of a warp
     constexpr int DPC_OWW = dpc_oww(R);           // owned columns per warp
-    constexpr int DPC_LMAX = dpc_lmax(R);         // parents a CTA can report
+    constexpr int DPC_LMAX = dpc_lmax(R, WPC);    // parents a CTA can report
     extern __shared__ __align__(128) unsigned char smraw[];
     // halo inboxes: [parity][warp][value], filled by the neighbouring warps
     __shared__ __align__(16) uint32_t inLc[2][DPC_WPC][DPC_R], inLl[2][DPC_WPC][DPC_R];
@@ -585,13 +591,13 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
     }
 }
 
-size_t dpc_smem(int W0, int H, int rj, int kcap, int C, int R) {
+size_t dpc_smem(int W0, int H, int rj, int kcap, int C, int R, int WPC) {
     const int nb = (H + rj - 1) / rj;
     const int jstride = (W0 + 7) & ~7;
     const int dstride = (((W0 + 3) / 4) + 3) & ~3;
-    const PostLayout PL(W0, C, kcap, nb, jstride, dstride, dpc_lmax(R));
+    const PostLayout PL(W0, C, kcap, nb, jstride, dstride, dpc_lmax(R, WPC));
     const WalkLayout WL(kcap, (nb + C - 1) / C);
-    size_t m = DPC_RING;
+    size_t m = dpc_ring(WPC);
     m = PL.end > m ? PL.end : m;
     m = WL.end > m ? WL.end : m;
     return m;
@@ -630,19 +636,19 @@ bool make_energy_map(const CarveWs &ws, int nb, CUtensorMap *m) {
 
 }  // namespace
 
-bool dpc_plan(int W0, int H, int R, int *ctas, int *rj, size_t *smem) {
-    if (R != 16 && R != 32) return false;
+bool dpc_plan(int W0, int H, int R, int WPC, int *ctas, int *rj, size_t *smem) {
+    if ((R != 16 && R != 32) || (WPC != 4 && WPC != 8)) return false;
     const int nwarps = (W0 + dpc_oww(R) - 1) / dpc_oww(R);
-    const int C = (nwarps + DPC_WPC - 1) / DPC_WPC;
+    const int C = (nwarps + WPC - 1) / WPC;
     if (C > 16) return false;
     // about four bands per CTA: the walk then takes ~rj rows per CTA
     int r = (H + 4 * C - 1) / (4 * C);
     r = ((r + 15) / 16) * 16;
     if (r < 16) r = 16;
-    size_t bytes = dpc_smem(W0, H, r, W0, C, R);
+    size_t bytes = dpc_smem(W0, H, r, W0, C, R, WPC);
     while (bytes > 220 * 1024 && r < H) {
         r += 16;
-        bytes = dpc_smem(W0, H, r, W0, C, R);
+        bytes = dpc_smem(W0, H, r, W0, C, R, WPC);
     }
     if (bytes > 220 * 1024) return false;
     // the walk stages at least one 16-row group of every band a CTA owns
@@ -657,19 +663,19 @@ bool dpc_plan(int W0, int H, int R, int *ctas, int *rj, size_t *smem) {
 
 namespace {
 
-template <int R>
+template <int R, int WPC>
 bool dpc_available_t(int W0, int H) {
     int C = 0, rj = 0;
     size_t smem = 0;
-    if (!dpc_plan(W0, H, R, &C, &rj, &smem)) return false;
-    if (raise_dyn_smem((const void *)k_dpc<R>, smem) != cudaSuccess) return false;
+    if (!dpc_plan(W0, H, R, WPC, &C, &rj, &smem)) return false;
+    if (raise_dyn_smem((const void *)k_dpc<R, WPC>, smem) != cudaSuccess) return false;
     if (C > 8 &&
-        cudaFuncSetAttribute(k_dpc<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+        cudaFuncSetAttribute(k_dpc<R, WPC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
             cudaSuccess)
         return false;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C);
-    cfg.blockDim = dim3(DPC_WPC * 32);
+    cfg.blockDim = dim3(WPC * 32);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -679,29 +685,30 @@ bool dpc_available_t(int W0, int H) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, k_dpc<R>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_dpc<R, WPC>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     return clusters > 0;
 }
 
-template <int R>
+template <int R, int WPC>
 cudaError_t launch_dpc_t(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                          cudaStream_t s) {
     int C = 0, rj = 0;
     size_t smem = 0;
-    if (!dpc_plan(ws.W0, ws.H, R, &C, &rj, &smem) || rj != ws.rj) return cudaErrorInvalidValue;
-    smem = dpc_smem(ws.W0, ws.H, ws.rj, ws.kcap, C, R);
-    cudaError_t e = raise_dyn_smem((const void *)k_dpc<R>, smem);
+    if (!dpc_plan(ws.W0, ws.H, R, WPC, &C, &rj, &smem) || rj != ws.rj)
+        return cudaErrorInvalidValue;
+    smem = dpc_smem(ws.W0, ws.H, ws.rj, ws.kcap, C, R, WPC);
+    cudaError_t e = raise_dyn_smem((const void *)k_dpc<R, WPC>, smem);
     if (e != cudaSuccess) return e;
     if (C > 8) {
-        e = cudaFuncSetAttribute(k_dpc<R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(k_dpc<R, WPC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nb * C);
-    cfg.blockDim = dim3(DPC_WPC * 32);
+    cfg.blockDim = dim3(WPC * 32);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -713,22 +720,27 @@ cudaError_t launch_dpc_t(const CarveWs &ws, int nb, int k, int16_t *seams, long 
     cfg.numAttrs = 1;
     CUtensorMap tm;
     if (!make_energy_map(ws, nb, &tm)) return cudaErrorInvalidValue;
-    e = cudaLaunchKernelEx(&cfg, k_dpc<R>, tm, ws, k, seams, seam_stride);
+    e = cudaLaunchKernelEx(&cfg, k_dpc<R, WPC>, tm, ws, k, seams, seam_stride);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 }  // namespace
 
-bool dpc_available(int W0, int H, int R) {
+bool dpc_available(int W0, int H, int R, int WPC) {
     if (!encode_tiled()) return false;
-    return R == 16 ? dpc_available_t<16>(W0, H) : R == 32 ? dpc_available_t<32>(W0, H) : false;
+    if (WPC == 4) return R == 16 ? dpc_available_t<16, 4>(W0, H) : R == 32 && dpc_available_t<32, 4>(W0, H);
+    if (WPC == 8) return R == 16 ? dpc_available_t<16, 8>(W0, H) : R == 32 && dpc_available_t<32, 8>(W0, H);
+    return false;
 }
 
 cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                        cudaStream_t s) {
-    if (ws.dpc_r == 16) return launch_dpc_t<16>(ws, nb, k, seams, seam_stride, s);
-    if (ws.dpc_r == 32) return launch_dpc_t<32>(ws, nb, k, seams, seam_stride, s);
+    const int wpc = ws.dpc_wpc == 8 ? 8 : 4;
+    if (ws.dpc_r == 16 && wpc == 4) return launch_dpc_t<16, 4>(ws, nb, k, seams, seam_stride, s);
+    if (ws.dpc_r == 32 && wpc == 4) return launch_dpc_t<32, 4>(ws, nb, k, seams, seam_stride, s);
+    if (ws.dpc_r == 16 && wpc == 8) return launch_dpc_t<16, 8>(ws, nb, k, seams, seam_stride, s);
+    if (ws.dpc_r == 32 && wpc == 8) return launch_dpc_t<32, 8>(ws, nb, k, seams, seam_stride, s);
     return cudaErrorInvalidValue;
 }
 

@@ -310,11 +310,11 @@ void add_reserved(Srv *s, long long delta) {
     s->peak = std::max(s->peak, s->reserved);
 }
 
-bool dpc_ok(Srv *s, int W, int H, int R) {
-    auto key = std::make_pair(W, H * 64 + R);
+bool dpc_ok(Srv *s, int W, int H, int R, int WPC) {
+    auto key = std::make_pair(W, (H * 64 + R) * 16 + WPC);
     auto it = s->dpc_cache.find(key);
     if (it != s->dpc_cache.end()) return it->second;
-    bool ok = dpc_available(W, H, R);
+    bool ok = dpc_available(W, H, R, WPC);
     s->dpc_cache[key] = ok;
     return ok;
 }
@@ -701,9 +701,10 @@ scpl_status setup_group(Srv *s, int gid) {
     ws.W0 = G.W;
     ws.kcap = kcap;
     ws.dpc_r = 32;
+    ws.dpc_wpc = 4;
     bool use_dpc = true;
     tuning_apply(G.H, G.W, ws, &use_dpc);   // sizes were tuned when their wave finished
-    G.dpc = use_dpc && dpc_ok(s, G.W, G.H, ws.dpc_r);
+    G.dpc = use_dpc && dpc_ok(s, G.W, G.H, ws.dpc_r, ws.dpc_wpc);
     const size_t ws_bytes = carve_ws_assign(ws, nb, klog, G.dpc, nullptr);
     // frames of every item, the gather table and the frame-minor luma
     long long yfm_total = 0;

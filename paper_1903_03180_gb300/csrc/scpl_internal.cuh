@@ -142,6 +142,7 @@ struct CarveWs {
     int jstride;        // row stride of J (W0 rounded up to 8)
     uint32_t *Dfirst;   // [nb][nbands][dstride] direction words of every band's first row
     int dpc_r;          // halo depth of the cluster DP (16 or 32); 0: the single-CTA DP
+    int dpc_wpc;        // warps per cluster-DP CTA (4 or 8; 0 means 4)
     int up_rows;        // rows per k_update CTA (1, 2 or 4); 0: the largest that fits
     int *err;           // device status word (bounded waits)
     const int32_t *E0;  // summed energy planes [H][W0] from the scan (see BufState::e0)
@@ -198,11 +199,12 @@ cudaError_t launch_energy_init(const CarveWs &ws, int nb, cudaStream_t s);
 cudaError_t launch_update(const CarveWs &ws, int nb, cudaStream_t s);
 cudaError_t launch_dp_select(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                              cudaStream_t s);
-// Cluster DP with halo depth R (16 or 32): plan (CTAs per cluster, band rows,
-// shared memory) for a width and height; returns false if this GPU cannot run
-// it (then use launch_dp_select).  launch_dpc uses ws.dpc_r.
-bool dpc_plan(int W0, int H, int R, int *ctas, int *rj, size_t *smem);
-bool dpc_available(int W0, int H, int R);
+// Cluster DP with halo depth R (16 or 32) and WPC warps per CTA (4 or 8):
+// plan (CTAs per cluster, band rows, shared memory) for a width and height;
+// returns false if this GPU cannot run it (then use launch_dp_select).
+// launch_dpc uses ws.dpc_r and ws.dpc_wpc.
+bool dpc_plan(int W0, int H, int R, int WPC, int *ctas, int *rj, size_t *smem);
+bool dpc_available(int W0, int H, int R, int WPC);
 cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                        cudaStream_t s);
 cudaError_t launch_identity_O(const CarveWs &ws, int nb, cudaStream_t s);

@@ -89,6 +89,7 @@ void tuning_apply(int H, int W, CarveWs &ws, bool *use_dpc) {
         *use_dpc = false;
     } else {
         ws.dpc_r = t.dpc_halo;
+        ws.dpc_wpc = t.dpc_warps;
     }
     ws.up_rows = t.update_rows;
 }
@@ -101,6 +102,7 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
     t.H = H;
     t.W = W;
     t.dpc_halo = 32;
+    t.dpc_warps = 4;
     t.update_rows = 0;
     const int tp = 16;   // frames of the scratch buffer
     CarveWs ws{};
@@ -108,15 +110,18 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
     ws.W0 = W;
     ws.kcap = kcap;
     ws.dpc_r = 32;
+    ws.dpc_wpc = 4;
     Scratch sc;
     // one slab big enough for the layout of every candidate (E, SD and O come
     // first and sit at the same offsets in all of them)
     size_t bytes = 0;
-    for (int R : {16, 32, 0}) {
-        CarveWs c = ws;
-        c.dpc_r = R;
-        bytes = std::max(bytes, carve_ws_assign(c, 1, remove, R != 0, nullptr));
-    }
+    for (int R : {16, 32, 0})
+        for (int wpc : {4, 8}) {
+            CarveWs c = ws;
+            c.dpc_r = R;
+            c.dpc_wpc = wpc;
+            bytes = std::max(bytes, carve_ws_assign(c, 1, remove, R != 0, nullptr));
+        }
     if (cudaMalloc(&sc.slab, bytes) != cudaSuccess) return SCPL_ENOMEM;
     const long yfm_bytes = (long)H * W * tp;
     if (cudaMalloc(&sc.yfm, (size_t)yfm_bytes) != cudaSuccess) return SCPL_ENOMEM;
@@ -146,12 +151,13 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
     };
     const int reps = 3;
     // time one DP candidate (the state is reset before every run)
-    auto time_dp = [&](int kind) -> float {   // 16, 32: cluster DP halo; 0: single CTA
+    auto time_dp = [&](int kind, int wpc) -> float {   // kind 16, 32: cluster halo; 0: one CTA
         CarveWs v = ws;
         v.dpc_r = kind;
-        if (kind != 0 && !dpc_available(W, H, kind)) return -1.0f;
+        v.dpc_wpc = wpc;
+        if (kind != 0 && !dpc_available(W, H, kind, wpc)) return -1.0f;
         carve_ws_assign(v, 1, remove, kind != 0, static_cast<char *>(sc.slab));
-        if (kind != 0 && v.dpc_r != kind) return -1.0f;
+        if (kind != 0 && (v.dpc_r != kind || v.dpc_wpc != wpc)) return -1.0f;
         if (kind == 0) {
             int bb = 0;
             if (dp_smem_bytes(W, H, &bb) > 227 * 1024 - 4096) return -1.0f;
@@ -173,29 +179,28 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
         }
         return best * 1000.0f;
     };
-    t.dp_us_r32 = time_dp(32);
-    t.dp_us_r16 = time_dp(16);
-    t.dp_us_single = time_dp(0);
+    const int kinds[5] = {32, 16, 32, 16, 0}, warps[5] = {4, 4, 8, 8, 4};
+    for (int i = 0; i < 5; ++i) t.dp_us[i] = time_dp(kinds[i], warps[i]);
     // the fastest DP; then leave one pending iteration for the update timing
     float best = 1e30f;
-    const float cand[3] = {t.dp_us_r32, t.dp_us_r16, t.dp_us_single};
-    const int kinds[3] = {32, 16, 0};
-    for (int i = 0; i < 3; ++i)
-        if (cand[i] > 0.0f && cand[i] < best) {
-            best = cand[i];
+    for (int i = 0; i < 5; ++i)
+        if (t.dp_us[i] > 0.0f && t.dp_us[i] < best) {
+            best = t.dp_us[i];
             t.dpc_halo = kinds[i];
+            t.dpc_warps = warps[i];
         }
     scpl_status result = SCPL_OK;
     if (best >= 1e29f) {
         result = SCPL_ECUDA;
     } else {
         CarveWs v = ws;   // any exact DP leaves the same pending iteration
-        v.dpc_r = t.dp_us_r32 > 0 ? 32 : 0;
+        v.dpc_r = t.dp_us[0] > 0 ? 32 : 0;
+        v.dpc_wpc = 4;
         carve_ws_assign(v, 1, remove, v.dpc_r != 0, static_cast<char *>(sc.slab));
         cudaError_t e = reset();
         if (e == cudaSuccess)
-            e = t.dp_us_r32 > 0 ? launch_dpc(v, 1, k, nullptr, 0, s)
-                                : launch_dp_select(v, 1, k, nullptr, 0, s);
+            e = t.dp_us[0] > 0 ? launch_dpc(v, 1, k, nullptr, 0, s)
+                               : launch_dp_select(v, 1, k, nullptr, 0, s);
         if (e != cudaSuccess) result = SCPL_ECUDA;
         const int rows[3] = {1, 2, 4};
         float ubest = 1e30f;

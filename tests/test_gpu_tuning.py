@@ -30,14 +30,14 @@ def synth():
     return s
 
 
-CHOICES = [(32, 4), (32, 1), (16, 2), (16, 4), (0, 1), (0, 4)]
+CHOICES = [(32, 4, 4), (32, 1, 8), (16, 2, 4), (16, 4, 8), (0, 1, 4), (0, 4, 4)]
 
 
-@pytest.mark.parametrize("halo,rows", CHOICES)
+@pytest.mark.parametrize("halo,rows,warps", CHOICES)
 @pytest.mark.parametrize("T,H,W,target,k,seed", [(6, 70, 300, 220, 16, 81),
                                                  (4, 50, 1000, 900, 32, 82)])
-def test_every_choice_is_exact(orc, lib, synth, halo, rows, T, H, W, target, k, seed):
-    lib.scpl_tuning_set(H, W, halo, rows)
+def test_every_choice_is_exact(orc, lib, synth, halo, rows, warps, T, H, W, target, k, seed):
+    lib.scpl_tuning_set(H, W, halo, rows, warps)
     f = synth.clip(T, H, W, seed=seed, cuts=(2, 3))
     ref_out, ref_starts, ref_seams = orc.carve(f, target, k)
     r = lib.Retargeter()
@@ -54,7 +54,7 @@ def test_tune_measures_and_records(lib):
     h = lib.scpl_create()
     t = lib.scpl_tune(h, 1080, 1920, 32)
     lib.scpl_destroy(h)
-    assert t["dp_us"]["r32"] > 0 and t["dp_us"]["r16"] > 0
+    assert all(t["dp_us"][k] > 0 for k in ("r32w4", "r16w4", "r32w8", "r16w8"))
     assert all(v > 0 for v in t["update_us"].values())
     assert t["dpc_halo"] in (0, 16, 32) and t["update_rows"] in (1, 2, 4)
     rec = lib.scpl_tuning_get(1080, 1920)
