@@ -275,13 +275,32 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
     }
     __syncthreads();
     const int nwords = (Wc + 31) >> 5;
-    for (int x = tid; x < nrows * nwords; x += UP_THREADS) {
-        const int r = x / nwords, wd = x - r * nwords;
-        uint32_t bits = bm[r * nwords0 + wd];
+    const int lane = tid & 31;
+    // every warp reserves room for all its words' bits with one atomic
+    for (int x0 = tid - lane; x0 < nrows * nwords; x0 += UP_THREADS) {
+        const int x = x0 + lane;
+        uint32_t bits = 0;
+        int r = 0, wd = 0;
+        if (x < nrows * nwords) {
+            r = x / nwords;
+            wd = x - r * nwords;
+            bits = bm[r * nwords0 + wd];
+        }
+        const int n = __popc(bits);
+        int pre = n;   // inclusive prefix over the warp
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, pre, o);
+            if (lane >= o) pre += y;
+        }
+        int base = 0;
+        if (lane == 31) base = atomicAdd(&s_cnt, pre);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        int pos = base + pre - n;
         while (bits) {
             const int bit = __ffs(bits) - 1;
             bits &= bits - 1;
-            list[atomicAdd(&s_cnt, 1)] = ((uint32_t)r << 16) | (uint32_t)(wd * 32 + bit);
+            list[pos++] = ((uint32_t)r << 16) | (uint32_t)(wd * 32 + bit);
         }
     }
     __syncthreads();
@@ -304,10 +323,28 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
         for (int a = 0; a < 3; ++a) {
             const int gi = clampi(i + a - 1, 0, H - 1);
             const uint16_t *rr = rl + (r + a) * kcap;
+            // source columns of x-1, x, x+1 (clamped): one search, then steps
+            // over the removals that fall between consecutive columns
+            const int xl = max(p - 1, 0), xr = min(p + 1, Wn - 1);
+            int m = 0;
+            {
+                int lo = 0, hi = keff;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if ((int)rr[mid] - mid <= xl) lo = mid + 1; else hi = mid;
+                }
+                m = lo;
+            }
+            int src[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const int x = clampi(p + c - 1, 0, Wn - 1);
-                const int o = Oin[(long)gi * pitch + src_col(rr, keff, x)];
+                const int x = c == 0 ? xl : (c == 1 ? min(p, Wn - 1) : xr);
+                while (m < keff && (int)rr[m] - m <= x) ++m;
+                src[c] = x + m;
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int o = Oin[(long)gi * pitch + src[c]];
                 if (a == 1 && c == 1) ocenter = o;
                 nb[a][c] = reinterpret_cast<const uint4 *>(yfm + ((long)gi * ws.W0 + o) * tp);
             }
