@@ -169,6 +169,8 @@ __global__ void __launch_bounds__(EN_QT) k_energy_init(CarveWs ws) {
 __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int s_cnt;
+    pdl_launch_dependents();
+    pdl_wait();   // the DP's selection and removal lists
     const int b = blockIdx.y;
     const BufState st = ws.st[b];
     const int keff = st.k_eff;
@@ -796,8 +798,18 @@ cudaError_t launch_update(const CarveWs &ws, int nb, cudaStream_t s) {
     cudaError_t e =
         raise_dyn_smem((const void *)k_update, smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((ws.H + rb - 1) / rb, nb);
-    k_update<<<grid, UP_THREADS, smem, s>>>(ws, rb);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((ws.H + rb - 1) / rb, nb);
+    cfg.blockDim = dim3(UP_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_update, ws, rb);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

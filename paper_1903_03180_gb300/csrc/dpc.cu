@@ -181,6 +181,8 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
     const int nwarps = C * DPC_WPC;
     const int H = ws.H, W0 = ws.W0, RJ = ws.rj, NB = ws.nbands;
 
+    pdl_launch_dependents();
+    pdl_wait();   // the previous update's carved energy and state
     const BufState st0 = ws.st[b];
     int W, slot, removed;
     committed(st0, W, slot, removed);
@@ -711,13 +713,15 @@ cudaError_t launch_dpc_t(const CarveWs &ws, int nb, int k, int16_t *seams, long 
     cfg.blockDim = dim3(WPC * 32);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     CUtensorMap tm;
     if (!make_energy_map(ws, nb, &tm)) return cudaErrorInvalidValue;
     e = cudaLaunchKernelEx(&cfg, k_dpc<R, WPC>, tm, ws, k, seams, seam_stride);

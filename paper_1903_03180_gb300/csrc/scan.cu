@@ -21,7 +21,8 @@ namespace scpl {
 
 namespace {
 
-constexpr int TR = 8, TC = 128, SCAN_THREADS = 128;
+constexpr int TR = 8, TC = 128, SCAN_THREADS = 256;
+constexpr int LUMW = TC + 8;   // luma tile row: TC + 2 columns, padded to whole words
 enum { DEC_JOIN = 0, DEC_FLUSH = 1, DEC_CLOSE = 2 };
 
 __device__ __forceinline__ int luma_px(const uint8_t *p) {
@@ -34,11 +35,6 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
-}
-
-// Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
-__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -165,13 +161,18 @@ __device__ __forceinline__ uint32_t isqrt53(unsigned long long x) {
 // lane 1 = pixels 1 and 3 of a luma quad.
 __device__ __forceinline__ uint32_t even16(uint32_t q) { return __byte_perm(q, 0, 0x4240); }
 __device__ __forceinline__ uint32_t odd16(uint32_t q) { return __byte_perm(q, 0, 0x4341); }
-// |x - y| and max(x, y) per 16-bit lane with the DPX three-way max/min (the
+// |x - y| and max(x, y, z) per 16-bit lane with the DPX three-way max/min (the
 // per-lane difference max - min is never negative, so no borrow crosses lanes)
 __device__ __forceinline__ uint32_t absdiff16(uint32_t x, uint32_t y) {
     return __vimax3_u16x2(x, y, 0u) - __vimin3_u16x2(x, y, 0xFFFFFFFFu);
 }
 __device__ __forceinline__ uint32_t max16(uint32_t x, uint32_t y, uint32_t z) {
     return __vimax3_u16x2(x, y, z);
+}
+
+// Bulk prefetch of [p, p + bytes) into L2 (p and bytes multiples of 16).
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
 // Sobel |Gx| + |Gy| of 4 consecutive pixels from three luma rows.  Each row is
@@ -196,14 +197,30 @@ __device__ __forceinline__ void sobel4(uint32_t u0, uint32_t u1, uint32_t m0, ui
     g13 = absdiff16(rO, lO) + absdiff16(bO, tO);
 }
 
-// Tile ownership: a tile is 8 rows x 128 columns and belongs to one warp for
-// the whole clip; lane l holds columns 4l .. 4l+3 of every row of it.  Warp gw
-// of a clip (CTA lb, warp w: gw = lb * SCAN_WARPS + w) owns the tiles
-// [gw * tpw, (gw + 1) * tpw), tpw = ceil(tiles / warps).  With one tile a warp
-// the running sums S1, S2 of its pixels stay in shared memory and the previous
-// frame's luma in registers ("resident"); with more they live in global memory.
-constexpr int SCAN_WARPS = SCAN_THREADS / 32;
-constexpr size_t SCAN_SMEM = (size_t)SCAN_WARPS * TR * 2 * 32 * sizeof(uint4);   // 32 KB
+// Tile ownership: CTA lb of a clip owns the contiguous tiles
+// [lb * tpc, (lb + 1) * tpc) for the whole clip, tpc = ceil(tiles / G).  Up to
+// MAXT tiles the CTA keeps S1 and S2 of its pixels in shared memory and the
+// previous frame's energy and luma in registers; beyond that they live in
+// global memory.
+constexpr int MAXT = 4;
+constexpr size_t SCAN_SMEM = (size_t)MAXT * SCAN_THREADS * 2 * sizeof(uint4);   // 32 KB
+
+struct TileCtx {
+    int r0, c0;      // tile origin
+    int row, col;    // this thread's row and first column
+    int nvalid;      // valid pixels of the quad (0..4)
+};
+
+__device__ __forceinline__ TileCtx tile_ctx(int H, int W, int tile, int tiles_x, int tid) {
+    TileCtx c;
+    const int ty = tile / tiles_x;
+    c.r0 = ty * TR;
+    c.c0 = (tile - ty * tiles_x) * TC;
+    c.row = c.r0 + (tid >> 5);
+    c.col = c.c0 + 4 * (tid & 31);
+    c.nvalid = c.row < H ? max(0, min(4, W - c.col)) : 0;
+    return c;
+}
 
 // Luma of 4 pixels from their 12 RGB bytes (R G B R | G B R G | B R G B):
 // one byte dot product per pixel with the weights (77, 150, 29, 0).
@@ -214,6 +231,48 @@ __device__ __forceinline__ uint32_t luma4(uint32_t w0, uint32_t w1, uint32_t w2)
     const uint32_t y2 = __dp4a(__byte_perm(w1, w2, 0x0432), K, 128u) >> 8;
     const uint32_t y3 = __dp4a(w2 >> 8, K, 128u) >> 8;
     return y0 | (y1 << 8) | (y2 << 16) | (y3 << 24);
+}
+
+// Luma of the tile and its one-pixel frame (replicated at the image border)
+// into lum[r][j] = Y(r0 - 1 + r, c0 - 1 + j).  With W a multiple of 4 every
+// 4-pixel quad is three aligned words of RGB; otherwise pixel by pixel.
+__device__ __forceinline__ void load_luma(int H, int W, bool words, const uint8_t *f, int r0,
+                                          int c0, uint8_t (*lum)[LUMW]) {
+    const int tid = threadIdx.x;
+    if (words) {
+        // body and top/bottom frame rows: (TR + 2) rows x 32 quads
+        for (int q = tid; q < (TR + 2) * 32; q += SCAN_THREADS) {
+            const int r = q >> 5, x = q & 31;
+            const int gi = clampi(r0 + r - 1, 0, H - 1);
+            const int gj = c0 + 4 * x;
+            uint32_t y = 0;
+            if (gj < W) {
+                const uint32_t *w =
+                    reinterpret_cast<const uint32_t *>(f + ((long)gi * W + gj) * 3);
+                y = luma4(__ldg(w), __ldg(w + 1), __ldg(w + 2));
+            } else {   // past the right edge: replicate the last column
+                y = luma_px(f + ((long)gi * W + W - 1) * 3) * 0x01010101u;
+            }
+            // columns c0 + 4x .. c0 + 4x + 3 sit at lum[r][1 + 4x ..]: unaligned by one
+            lum[r][1 + 4 * x] = (uint8_t)y;
+            lum[r][2 + 4 * x] = (uint8_t)(y >> 8);
+            lum[r][3 + 4 * x] = (uint8_t)(y >> 16);
+            lum[r][4 + 4 * x] = (uint8_t)(y >> 24);
+        }
+        // left and right frame columns
+        if (tid < 2 * (TR + 2)) {
+            const int r = tid >> 1, side = tid & 1;
+            const int gi = clampi(r0 + r - 1, 0, H - 1);
+            const int gj = clampi(side ? c0 + TC : c0 - 1, 0, W - 1);
+            lum[r][side ? TC + 1 : 0] = (uint8_t)luma_px(f + ((long)gi * W + gj) * 3);
+        }
+    } else {
+        for (int q = tid; q < (TR + 2) * (TC + 2); q += SCAN_THREADS) {
+            const int r = q / (TC + 2), c = q - r * (TC + 2);
+            const int gi = clampi(r0 + r - 1, 0, H - 1), gj = clampi(c0 + c - 1, 0, W - 1);
+            lum[r][c] = (uint8_t)luma_px(f + ((long)gi * W + gj) * 3);
+        }
+    }
 }
 
 // One clip per launch (tab == NULL, every CTA works on a0) or one clip per
@@ -228,12 +287,364 @@ __device__ __forceinline__ uint32_t luma4(uint32_t w0, uint32_t w1, uint32_t w2)
 // closed buffer's sum is S1 minus the energies of frames f..w, S1/S2 restart
 // from e_f, and the next round re-evaluates frames f+1..w from their stored
 // energies.
-__global__ void __launch_bounds__(SCAN_THREADS, 5)
+__global__ void __launch_bounds__(SCAN_THREADS, 4)
 k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ block_clip) {
-    extern __shared__ __align__(16) uint4 sstate[];   // [SCAN_WARPS][TR][2][32] S1, S2
+    extern __shared__ __align__(16) uint4 sstate[];   // [MAXT][2][SCAN_THREADS] S1, S2
     __shared__ ScanArgs a;
-    __shared__ unsigned long long red_a[SCAN_WARPS];
-    __shared__ uint32_t red_m[SCAN_WARPS];
+    __shared__ __align__(16) uint8_t lum[TR + 2][LUMW];
+    __shared__ unsigned long long red_a[SCAN_THREADS / 32];
+    __shared__ uint32_t red_m[SCAN_THREADS / 32];
+    __shared__ DecState st;
+    __shared__ int s_ok, s_ndec, s_last;
+    __shared__ uint32_t s_rc[64];   // origins (r0 << 16 | c0) of the CTA's first 64 tiles
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        if (tab) {
+            a = tab[block_clip[blockIdx.x]];
+        } else {
+            a = a0;
+            a.cta0 = 0;
+            a.G = gridDim.x;
+        }
+        st.n = 0; st.M = 0; st.start = 0; st.nb = 0;
+    }
+    __syncthreads();
+    // the clip's arguments live in shared memory; the hot loops use register
+    // copies (shared loads there could not be hoisted past the tile stores)
+    const int H = a.H, W = a.W, T = a.T;
+    const uint32_t wg = (uint32_t)a.wg, wm = (uint32_t)a.wm;
+    const long ypitch = a.ypitch;
+    const uint8_t *__restrict__ rgb = a.rgb;
+    uint8_t *__restrict__ Yo = a.Y;
+    uint8_t *__restrict__ Do = a.D;
+    uint32_t *S1g = a.S1, *S2g = a.S2;
+    int32_t *E0 = a.E0;
+    const int nbcap = a.nbcap;
+    const long e0_plane = a.e0_plane;
+    const unsigned *ready = a.ready;
+    const int ready_frames = a.ready_frames;
+    const bool words = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(rgb) & 3) == 0;
+    const int G = a.G;
+    const int lb = blockIdx.x - a.cta0;   // CTA index within the clip's range
+    const int tiles_x = (W + TC - 1) / TC;
+    const int ntiles = ((H + TR - 1) / TR) * tiles_x;
+    const int tpc = (ntiles + G - 1) / G;
+    const int first = lb * tpc;
+    const int mine = max(0, min(tpc, ntiles - first));
+    const bool resident = tpc <= MAXT;
+    const long hw3 = (long)H * W * 3;
+    const long yplane = (long)H * ypitch;
+    const bool pf_ok = (reinterpret_cast<uintptr_t>(rgb) & 15) == 0;   // prefetch needs 16-byte bases
+    const long eslot = (long)ntiles * SCAN_THREADS;   // uint2 entries per ring slot
+    uint2 *ering = reinterpret_cast<uint2 *>(a.ering);  // [SCAN_FW][ntiles][256] e quads
+    for (int k = tid; k < min(mine, 64); k += SCAN_THREADS) {
+        const int ty = (first + k) / tiles_x;
+        s_rc[k] = ((uint32_t)(ty * TR) << 16) | (uint32_t)((first + k - ty * tiles_x) * TC);
+    }
+    __syncthreads();
+    // the geometry of the CTA's k-th tile for this thread
+    auto ctx = [&](int k) {
+        if (k >= 64) return tile_ctx(H, W, first + k, tiles_x, tid);
+        TileCtx c;
+        c.r0 = (int)(s_rc[k] >> 16);
+        c.c0 = (int)(s_rc[k] & 0xFFFFu);
+        c.row = c.r0 + (tid >> 5);
+        c.col = c.c0 + 4 * (tid & 31);
+        c.nvalid = c.row < H ? max(0, min(4, W - c.col)) : 0;
+        return c;
+    };
+    uint32_t yp[MAXT];   // resident path: previous frame's luma quad per tile
+#pragma unroll
+    for (int k = 0; k < MAXT; ++k) yp[k] = 0;
+
+    // energy of frame t on one tile: luma and motion written out, the e quad
+    // (u16x2 pairs) stored in the ring
+    auto phase_a = [&](int t, int k, uint32_t &yprev, uint32_t &emax2) {
+        const int tile = first + k;
+        const TileCtx c = ctx(k);
+        const uint8_t *f = rgb + (long)t * hw3;
+        // the tile's rows of the next frame into L2 now, so that its loads
+        // wait for L2 instead of DRAM; ranges rounded inwards to 16 bytes
+        // and kept inside the clip
+        if (pf_ok && tid < TR + 2 && t + 1 < T) {
+            const int row = clampi(c.r0 - 1 + tid, 0, H - 1);
+            const long base = ((long)(t + 1) * H + row) * W * 3;
+            const long lo = (base + 3L * max(c.c0 - 1, 0)) & ~15L;
+            const long hi = (base + 3L * min(c.c0 + TC + 1, W)) & ~15L;
+            if (hi > lo) prefetch_l2(rgb + lo, (unsigned)(hi - lo));
+        }
+        load_luma(H, W, words, f, c.r0, c.c0, lum);
+        __syncthreads();
+        const int rr = tid >> 5, cc = 4 * (tid & 31);
+        const uint32_t *L0 = reinterpret_cast<const uint32_t *>(&lum[rr][cc]);
+        const uint32_t *L1 = reinterpret_cast<const uint32_t *>(&lum[rr + 1][cc]);
+        const uint32_t *L2 = reinterpret_cast<const uint32_t *>(&lum[rr + 2][cc]);
+        uint32_t g02, g13;
+        sobel4(L0[0], L0[1], L1[0], L1[1], L2[0], L2[1], g02, g13);
+        const uint32_t ycur = __funnelshift_r(L1[0], L1[1], 8);
+        uint32_t yprv = yprev;
+        if (!resident && t > 0 && c.nvalid > 0)
+            yprv = *reinterpret_cast<const uint32_t *>(Yo + (long)(t - 1) * yplane +
+                                                       (long)c.row * ypitch + c.col);
+        // motion |Y_t - Y_{t-1}| on the u16 halves the energy uses
+        const uint32_t d02 = t > 0 ? absdiff16(even16(ycur), even16(yprv)) : 0u;
+        const uint32_t d13 = t > 0 ? absdiff16(odd16(ycur), odd16(yprv)) : 0u;
+        const uint32_t dq = __byte_perm(d02, d13, 0x6240);   // back to 4 bytes
+        const uint32_t e02 = wg * g02 + wm * d02;
+        const uint32_t e13 = wg * g13 + wm * d13;
+        if (c.nvalid > 0) {
+            // invalid pixels of a ragged quad do not count towards the maximum
+            const uint32_t m02 = c.nvalid >= 3 ? e02 : (e02 & 0xFFFFu);
+            const uint32_t m13 = c.nvalid >= 4 ? e13 : (c.nvalid >= 2 ? (e13 & 0xFFFFu) : 0u);
+            emax2 = max16(emax2, m02, m13);
+            const long yo = (long)t * yplane + (long)c.row * ypitch + c.col;
+            *reinterpret_cast<uint32_t *>(Yo + yo) = ycur;
+            *reinterpret_cast<uint32_t *>(Do + yo) = dq;
+        }
+        ering[(long)(t % SCAN_FW) * eslot + (long)tile * SCAN_THREADS + tid] = make_uint2(e02, e13);
+        yprev = ycur;
+        __syncthreads();   // lum is reused by the next tile
+    };
+
+    auto state_ptrs = [&](int k, int tile, uint4 *&S1p, uint4 *&S2p) {
+        if (resident) {
+            S1p = &sstate[(k * 2) * SCAN_THREADS + tid];
+            S2p = &sstate[(k * 2 + 1) * SCAN_THREADS + tid];
+        } else {
+            const long sidx = (long)tile * SCAN_THREADS + tid;
+            S1p = reinterpret_cast<uint4 *>(S1g) + sidx;
+            S2p = reinterpret_cast<uint4 *>(S2g) + sidx;
+        }
+    };
+
+    // fold frame t into S1/S2 of one tile (restart when `fresh`) and add its
+    // floor(sqrt(65536 (n S2 - S1^2))) over the valid pixels to acc
+    auto fold = [&](int t, int k, int tile, bool fresh, int n1, unsigned long long &acc) {
+        const TileCtx c = ctx(k);
+        uint4 *S1p, *S2p;
+        state_ptrs(k, tile, S1p, S2p);
+        const uint2 e = ering[(long)(t % SCAN_FW) * eslot + (long)tile * SCAN_THREADS + tid];
+        const uint32_t ev[4] = {e.x & 0xFFFFu, e.y & 0xFFFFu, e.x >> 16, e.y >> 16};
+        uint4 s1 = make_uint4(0, 0, 0, 0), s2 = make_uint4(0, 0, 0, 0);
+        if (!fresh) {
+            s1 = *S1p;
+            s2 = *S2p;
+        }
+        uint32_t *S1v = &s1.x, *S2v = &s2.x;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            S1v[v] += ev[v];
+            S2v[v] += ev[v] * ev[v];
+            if (v < c.nvalid) {
+                const unsigned long long Q =
+                    (unsigned long long)n1 * S2v[v] - (unsigned long long)S1v[v] * S1v[v];
+                acc += isqrt53(Q << 16);
+            }
+        }
+        *S1p = s1;
+        *S2p = s2;
+    };
+
+    // block sum of acc and maximum of emax2 (thread 0 receives them)
+    auto block_reduce = [&](unsigned long long &acc, uint32_t &em) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+        }
+        if ((tid & 31) == 0) { red_a[tid >> 5] = acc; red_m[tid >> 5] = em; }
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long A = 0;
+            uint32_t m = 0;
+            for (int w = 0; w < SCAN_THREADS / 32; ++w) { A += red_a[w]; m = max(m, red_m[w]); }
+            acc = A;
+            em = m;
+        }
+        __syncthreads();
+    };
+
+    // summed energy of buffer bi (the E0 plane) for the valid pixels of my tiles:
+    // S1 minus the ring energies of frames [g0, g1)
+    auto write_e0 = [&](int bi, int g0, int g1) {
+        if (!E0 || bi >= nbcap) return;
+        for (int k = 0; k < mine; ++k) {
+            const int tile = first + k;
+            const TileCtx c = ctx(k);
+            if (c.nvalid == 0) continue;
+            uint4 *S1p, *S2p;
+            state_ptrs(k, tile, S1p, S2p);
+            uint4 s1 = *S1p;
+            uint32_t *S1v = &s1.x;
+            for (int g = g0; g < g1; ++g) {
+                const uint2 e = ering[(long)(g % SCAN_FW) * eslot + (long)tile * SCAN_THREADS + tid];
+                S1v[0] -= e.x & 0xFFFFu;
+                S1v[1] -= e.y & 0xFFFFu;
+                S1v[2] -= e.x >> 16;
+                S1v[3] -= e.y >> 16;
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+                if (v < c.nvalid)
+                    E0[(long)bi * e0_plane + (long)c.row * W + c.col + v] = (int32_t)S1v[v];
+        }
+    };
+
+    int t = 0, horizon = 0, r = 0;
+    while (t < T) {
+        // the round's frames: up to SCAN_FW, ending where the open buffer
+        // would reach t_max, and at the clip end
+        const int n0 = st.n;
+        int w = min(t + SCAN_FW - 1, T - 1);
+        w = min(w, t + (a.t_max - n0) - 1);
+        for (int f = t; f <= w; ++f) {
+            uint32_t emax2 = 0;
+            const bool fresh_frame = f >= horizon;
+            if (fresh_frame && ready) {
+                // frame f may still be on its way from the host: wait (bounded)
+                // until the copy stream has raised the counter past its chunk
+                if (tid == 0) {
+                    const unsigned need = (unsigned)(f / ready_frames) + 1u;
+                    int ok = 1;
+                    if (ld_acquire_u32(ready) < need) {
+                        const unsigned long long t0 = globaltimer_ns();
+                        while (ld_acquire_u32(ready) < need) {
+                            if (*(volatile int *)a.err != DEV_OK) { ok = 0; break; }
+                            if (globaltimer_ns() - t0 > a.spin_limit_ns) {
+                                atomicCAS(a.err, DEV_OK, DEV_ETIMEOUT);
+                                ok = 0;
+                                break;
+                            }
+                            __nanosleep(256);
+                        }
+                    }
+                    s_ok = ok;
+                }
+                __syncthreads();
+                if (!s_ok) return;
+            }
+            if (fresh_frame) {
+                if (resident) {
+#pragma unroll
+                    for (int k = 0; k < MAXT; ++k)
+                        if (k < mine) phase_a(f, k, yp[k], emax2);
+                } else {
+                    for (int k = 0; k < mine; ++k) {
+                        uint32_t ydummy = 0;
+                        phase_a(f, k, ydummy, emax2);
+                    }
+                }
+            }
+            unsigned long long acc = 0;
+            const bool fresh = n0 == 0 && f == t;   // the open buffer starts here
+            const int n1 = n0 + (f - t) + 1;
+            if (resident) {
+#pragma unroll
+                for (int k = 0; k < MAXT; ++k)
+                    if (k < mine) fold(f, k, first + k, fresh, n1, acc);
+            } else {
+                for (int k = 0; k < mine; ++k) fold(f, k, first + k, fresh, n1, acc);
+            }
+            uint32_t em = max(emax2 & 0xFFFFu, emax2 >> 16);
+            block_reduce(acc, em);
+            if (tid == 0) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(&a.partA[(long)r * SCAN_FW + (f - t)]),
+                          acc);
+                if (fresh_frame) atomicMax(&a.partM[f], (int)em);
+            }
+        }
+        horizon = max(horizon, w + 1);
+        // publish the round, wait for the clip's other CTAs, replay decisions
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(&a.count[r], 1u);
+            int ok = wait_round(a, r, G) ? 1 : 0;
+            int ndec = 0, last = DEC_JOIN;
+            if (ok) {
+                __threadfence();
+                const bool lead = lb == 0;
+                for (int f = t; f <= w; ++f) {
+                    const long long A = (long long)__ldcg(reinterpret_cast<const unsigned long long *>(
+                        &a.partA[(long)r * SCAN_FW + (f - t)]));
+                    const int m = __ldcg(&a.partM[f]);
+                    if (lead && a.A_out) {
+                        a.A_out[f] = A;
+                        a.M_out[f] = m;
+                    }
+                    last = decide(st, A, m, f, a, lead);
+                    ++ndec;
+                    if (last == DEC_FLUSH) break;
+                }
+            }
+            s_ok = ok;
+            s_ndec = ndec;
+            s_last = last;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        const int fend = t + s_ndec;   // first frame not yet decided
+        if (s_last == DEC_FLUSH) {
+            // frame fend-1 starts a new buffer: the closed one is S1 minus the
+            // energies of frames fend-1..w; S1/S2 restart from e_{fend-1}
+            const int f = fend - 1;
+            write_e0(st.nb - 1, f, w + 1);
+            for (int k = 0; k < mine; ++k) {
+                const int tile = first + k;
+                uint4 *S1p, *S2p;
+                state_ptrs(k, tile, S1p, S2p);
+                const uint2 e = ering[(long)(f % SCAN_FW) * eslot + (long)tile * SCAN_THREADS + tid];
+                const uint32_t ev[4] = {e.x & 0xFFFFu, e.y & 0xFFFFu, e.x >> 16, e.y >> 16};
+                *S1p = make_uint4(ev[0], ev[1], ev[2], ev[3]);
+                *S2p = make_uint4(ev[0] * ev[0], ev[1] * ev[1], ev[2] * ev[2], ev[3] * ev[3]);
+            }
+        } else if (s_last == DEC_CLOSE) {
+            write_e0(st.nb - 1, w + 1, w + 1);   // the buffer ending with frame w
+        }
+        __syncthreads();
+        t = fend;
+        ++r;
+    }
+    // the buffer still open at the clip end
+    if (st.n > 0) write_e0(st.nb, T, T);
+    if (lb == 0 && tid == 0) {
+        int nb = st.nb;
+        if (st.n > 0) a.starts[nb++] = st.start;
+        a.starts[nb] = T;
+        *a.n_buffers = nb;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_scan_wt, the warp-tile variant for one clip whose state stays on chip.
+// Tile ownership: a tile is 8 rows x 128 columns and belongs to one warp for
+// the whole clip; lane l holds columns 4l .. 4l+3 of every row of it.  Warp gw
+// of a clip (CTA lb, warp w: gw = lb * WT_WARPS + w) owns the tiles
+// [gw * tpw, (gw + 1) * tpw), tpw = ceil(tiles / warps).  With one tile a warp
+// the running sums S1, S2 of its pixels stay in shared memory and the previous
+// frame's luma in registers ("resident"); with more they live in global memory.
+constexpr int WT_THREADS = 128;
+constexpr int WT_WARPS = WT_THREADS / 32;
+constexpr size_t WT_SMEM = (size_t)WT_WARPS * TR * 2 * 32 * sizeof(uint4);   // 32 KB
+
+// One clip per launch (tab == NULL, every CTA works on a0) or one clip per
+// range of CTAs (clip of CTA x = tab[block_clip[x]], CTAs [cta0, cta0 + G)).
+//
+// Rounds: a round takes the next frames [t, w] (at most SCAN_FW, never past
+// the frame where the open buffer reaches t_max, never past T - 1) and folds
+// each into S1/S2 as if it joined the open buffer, publishing every frame's
+// A_t.  After one device-wide wait every CTA replays the decisions of Eq. 9 in
+// frame order on the same integers.  Up to the first frame that exceeds the
+// threshold the guess was right.  At that frame f a new buffer starts: the
+// closed buffer's sum is S1 minus the energies of frames f..w, S1/S2 restart
+// from e_f, and the next round re-evaluates frames f+1..w from their stored
+// energies.
+__global__ void __launch_bounds__(WT_THREADS, 5)
+k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ block_clip) {
+    extern __shared__ __align__(16) uint4 sstate[];   // [WT_WARPS][TR][2][32] S1, S2
+    __shared__ ScanArgs a;
+    __shared__ unsigned long long red_a[WT_WARPS];
+    __shared__ uint32_t red_m[WT_WARPS];
     __shared__ DecState st;
     __shared__ int s_ok, s_ndec, s_last;
 
@@ -267,9 +678,9 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
     const int lb = blockIdx.x - a.cta0;   // CTA index within the clip's range
     const int tiles_x = (W + TC - 1) / TC;
     const int ntiles = ((H + TR - 1) / TR) * tiles_x;
-    const int nwarps = G * SCAN_WARPS;
+    const int nwarps = G * WT_WARPS;
     const int tpw = (ntiles + nwarps - 1) / nwarps;
-    const int gw = lb * SCAN_WARPS + w;
+    const int gw = lb * WT_WARPS + w;
     const int first = gw * tpw;
     const int mine = max(0, min(tpw, ntiles - first));
     const bool resident = tpw <= 1;
@@ -449,7 +860,7 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
         if (tid == 0) {
             unsigned long long A = 0;
             uint32_t m = 0;
-            for (int q = 0; q < SCAN_WARPS; ++q) { A += red_a[q]; m = max(m, red_m[q]); }
+            for (int q = 0; q < WT_WARPS; ++q) { A += red_a[q]; m = max(m, red_m[q]); }
             acc = A;
             em = m;
         }
@@ -596,6 +1007,7 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
     }
 }
 
+
 }  // namespace
 
 cudaError_t launch_energy_api(const uint8_t *rgb, int T, int H, int W, int wg, int wm,
@@ -608,20 +1020,50 @@ cudaError_t launch_energy_api(const uint8_t *rgb, int T, int H, int W, int wg, i
 }
 
 // Co-resident CTAs for the cooperative scan: all SMs' worth, lowered so that
-// every warp owns the same number of tiles.
+// every CTA owns the same number of tiles.
 int scan_grid_size(int H, int W, int *err_out) {
     const int cap = scan_capacity(err_out);
     if (*err_out || cap < 1) return 0;
     const long ntiles = (long)((H + TR - 1) / TR) * ((W + TC - 1) / TC);
-    const long tpw = (ntiles + (long)cap * SCAN_WARPS - 1) / ((long)cap * SCAN_WARPS);
-    return (int)((ntiles + tpw * SCAN_WARPS - 1) / (tpw * SCAN_WARPS));
+    const long tpc = (ntiles + cap - 1) / cap;
+    return (int)((ntiles + tpc - 1) / tpc);
 }
+
+namespace {
+
+// Co-resident CTAs of the warp-tile variant, and whether a clip's tiles fit
+// one per warp (so that its running sums stay in shared memory).
+int scan_capacity_wt(int *err_out) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_scan_wt, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)WT_SMEM);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_scan_wt, WT_THREADS, WT_SMEM);
+    if (e != cudaSuccess) { *err_out = (int)e; return 0; }
+    *err_out = 0;
+    return sms * per_sm;
+}
+
+}  // namespace
 
 cudaError_t launch_scan(const ScanArgs &a, int grid, cudaStream_t s) {
     ScanArgs copy = a;
     const ScanArgs *tab = nullptr;
     const int *bc = nullptr;
     void *args[] = {&copy, &tab, &bc};
+    // one clip alone: the warp-tile variant when every warp can own a single
+    // tile (each warp walks its tile's rows; its state stays on chip)
+    int err = 0;
+    const long ntiles = (long)scan_tiles(a.H, a.W);
+    const int cap_wt = scan_capacity_wt(&err);
+    if (!err && (long)cap_wt * WT_WARPS >= ntiles) {
+        const int g = (int)((ntiles + WT_WARPS - 1) / WT_WARPS);
+        return cudaLaunchCooperativeKernel((const void *)k_scan_wt, dim3(g), dim3(WT_THREADS),
+                                           args, WT_SMEM, s);
+    }
     cudaError_t e = cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)SCAN_SMEM);
     if (e != cudaSuccess) return e;
@@ -656,7 +1098,7 @@ int scan_capacity(int *err_out) {
 }
 
 int scan_tiles(int H, int W) { return ((H + TR - 1) / TR) * ((W + TC - 1) / TC); }
-int scan_tile_warps() { return SCAN_WARPS; }
+int scan_tile_warps() { return 1; }   // a CTA works on one tile at a time
 
 long scan_state_px(int H, int W) { return (long)scan_tiles(H, W) * TR * TC; }
 

@@ -96,6 +96,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *mbar, unsigned parity, int *
     return true;
 }
 
+// Programmatic dependent launch (the DP and update kernels of a carving loop
+// are launched with programmatic stream serialisation): a kernel lets its
+// dependent start launching at once, and waits for its predecessor's results
+// before its first read of them.
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Committed view of a buffer's state (applies a pending iteration).
 __device__ __forceinline__ void committed(const BufState &s, int &W, int &slot, int &removed) {
     if (s.k_eff > 0) {
