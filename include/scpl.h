@@ -13,7 +13,7 @@
  *    return as soon as the work is queued.
  *  - Every entry point returns an scpl_status; nothing throws.  On a non-zero
  *    status scpl_last_error() describes it.  After SCPL_EINVAL, SCPL_ENOMEM,
- *    SCPL_EOVERFLOW or SCPL_ETIMEOUT the handle stays usable.  After
+ *    SCPL_EOVERFLOW, SCPL_ETIMEOUT or SCPL_ECANCELED the handle stays usable.  After
  *    SCPL_ECUDA it is usable unless the CUDA context itself was lost.
  *  - A handle is not thread-safe: one host thread at a time per handle.
  */
@@ -34,7 +34,8 @@ typedef enum {
     SCPL_ENOMEM = 2,    /* a workspace could not be allocated                  */
     SCPL_ECUDA = 3,     /* a CUDA call failed                                  */
     SCPL_ETIMEOUT = 4,  /* a bounded device-side wait ran out                  */
-    SCPL_EOVERFLOW = 5  /* the sizes could overflow the exact integer sums     */
+    SCPL_EOVERFLOW = 5, /* the sizes could overflow the exact integer sums     */
+    SCPL_ECANCELED = 6  /* a server job was cancelled (scpl_server_cancel)     */
 } scpl_status;
 
 /* Parameters of the method.
@@ -107,6 +108,39 @@ scpl_status scpl_scan(scpl_handle h, const uint8_t *frames, int T, int H, int W,
  * Synchronises the stream. */
 scpl_status scpl_scan_stats(scpl_handle h, const uint8_t *frames, int T, int H, int W,
                             int32_t *buffer_starts, int *n_buffers, int64_t *A, int32_t *emax);
+
+/* scpl_scan on frames that are still arriving (streaming ingest): the buffer
+ * decisions start while a producer is still copying later frames in.  The
+ * producer announces each chunk of `chunk` frames by raising a device counter
+ * to the number of chunks complete; the scan reads frame t only once
+ * *arrived >= t / chunk + 1.
+ *   arrived  [device] uint32, raised by the producer on another stream with
+ *            scpl_signal_arrival after each chunk's copy.  (A stream memory
+ *            operation needs no SM; a kernel on another stream may not be
+ *            scheduled while the scan's persistent grid holds every SM.)
+ *   chunk    frames per announcement, >= 1
+ * The result equals scpl_scan's on the complete frames.  A wait for a frame
+ * is bounded by the handle's wait limit (scpl_set_wait_limit): a counter that
+ * stops short ends the call with SCPL_ETIMEOUT, buffer_starts unwritten, and
+ * the handle stays usable.  Synchronises the stream. */
+scpl_status scpl_scan_arrivals(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                               const uint32_t *arrived, int chunk, int32_t *buffer_starts,
+                               int *n_buffers);
+
+/* Enqueue on `stream` (a cudaStream_t, NULL = the legacy default stream) a
+ * write of `value` to the device word *counter, after the stream's earlier
+ * work and a memory fence: the announcement scpl_scan_arrivals waits for.
+ * Needs no handle.  SCPL_EINVAL for a NULL counter, SCPL_ECUDA if the driver
+ * lacks stream memory operations. */
+scpl_status scpl_signal_arrival(void *stream, uint32_t *counter, uint32_t value);
+
+/* Bound, in nanoseconds, of each device-wide wait of the handle's buffer
+ * scans: the per-round reduction across the scan's CTAs and the waits for
+ * arriving frames (default 2e9).  A wait that runs out makes its call return
+ * SCPL_ETIMEOUT instead of hanging.  (The carving kernels wait only within a
+ * thread-block cluster, under a fixed 2 s bound.)  SCPL_EINVAL outside
+ * [1e5, 6e10]. */
+scpl_status scpl_set_wait_limit(scpl_handle h, uint64_t ns);
 
 /* One SCPL iteration on an energy map (Sec. 3.1, Eq. 4-6): the cumulative
  * energy DP carrying each pixel's row-0 parent (lowest column on ties), the
@@ -308,6 +342,18 @@ size_t scpl_job_footprint_per_buffer(const scpl_job *job);
  *  scpl_server_poll     up to max completed jobs since the last poll: their
  *                       tickets and statuses; returns how many.
  *  scpl_server_drain    progress until every submitted job has completed.
+ *  scpl_server_cancel   a queued job completes at once with SCPL_ECANCELED;
+ *                       an admitted job takes no further stage and completes
+ *                       with SCPL_ECANCELED once the launches already made
+ *                       for it have finished (its out buffer is then
+ *                       unspecified, and may be written until it completes).
+ *                       SCPL_EINVAL if the ticket is unknown or the job has
+ *                       already finished or failed.
+ * Faults are contained per job: a job that cannot fit the budget, or whose
+ * device memory the allocator refuses while nothing else runs, completes with
+ * SCPL_ENOMEM (a refusal while other jobs run delays it until they release
+ * memory); a device-side wait that runs out fails the jobs of that launch with
+ * SCPL_ETIMEOUT.  The server stays usable after each.
  * A server is not thread-safe: one host thread drives it. */
 typedef struct scpl_server_s *scpl_server;
 
@@ -320,6 +366,7 @@ typedef struct {
     long long graphs_built;
     long long kernel_launches;   /* kernels of this library, graph nodes included */
     size_t reserved_bytes, peak_reserved_bytes, budget_bytes;
+    long long cancelled;         /* jobs that ended with SCPL_ECANCELED         */
 } scpl_server_stats;
 
 /* Counters of the handle's batch engine (zeros before the first
@@ -334,6 +381,12 @@ scpl_status scpl_server_set_autotune(scpl_server s, int on);
 scpl_status scpl_server_progress(scpl_server s, int wait, int *n_active, int *n_queued);
 int scpl_server_poll(scpl_server s, long long *tickets, int *statuses, int max);
 scpl_status scpl_server_drain(scpl_server s);
+scpl_status scpl_server_cancel(scpl_server s, long long ticket);
+/* Fault injection for testing the paths above: after `skip` more device
+ * allocations of the server succeed, the next `count` are refused as if the
+ * device were out of memory (count = 0 turns it off).  Host-side only: no
+ * device work is affected. */
+scpl_status scpl_server_refuse_allocations(scpl_server s, long long skip, int count);
 scpl_status scpl_server_get_stats(scpl_server s, scpl_server_stats *out);
 const char *scpl_server_last_error(scpl_server s);
 void scpl_server_destroy(scpl_server s);

@@ -208,6 +208,7 @@ struct Pass {
     cudaEvent_t ready = nullptr;   // src complete (null: ordered on the main stream)
     int group = -1;
     int frame_off = 0;
+    bool item = false;          // its buffers are items of its carving group
     long long e0_off = 0;       // element offset of its summed-energy planes
     int nb = 0, item0 = 0;
     std::vector<int> starts;
@@ -275,6 +276,9 @@ struct scpl_server_s {
     scpl_server_stats st{};
     int active_jobs = 0;
     bool autotune = false;
+    bool hold = false;          // admission waits for running work after a refusal
+    long long refuse_skip = 0;  // injected allocator refusals (testing)
+    int refuse_n = 0;
 };
 
 namespace {
@@ -301,9 +305,37 @@ scpl_status sfail(Srv *s, scpl_status code, const char *fmt, ...) {
         }                                                                                  \
     } while (0)
 
+// An allocation: a refusal returns SCPL_ENOMEM and leaves the server usable.
+#define SRV_ALLOC(s, call)                                                                  \
+    do {                                                                                   \
+        cudaError_t ea_ = (call);                                                          \
+        if (ea_ == cudaErrorMemoryAllocation)                                              \
+            return sfail(s, SCPL_ENOMEM, "%s: refused (%s:%d)", #call, __FILE__, __LINE__);  \
+        SRV_CUDA(s, ea_);                                                                  \
+    } while (0)
+
+// Device allocation from the engine's pool.  A refusal (the pool or the
+// device is out of memory, or an injected refusal) leaves the server usable:
+// the callers below delay or fail only the jobs that needed the memory.
 cudaError_t dalloc(Srv *s, void **p, size_t bytes, cudaStream_t st) {
-    return cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 256), s->mpool, st);
+    *p = nullptr;
+    if (s->refuse_n > 0) {
+        if (s->refuse_skip > 0) {
+            --s->refuse_skip;
+        } else {
+            --s->refuse_n;
+            return cudaErrorMemoryAllocation;
+        }
+    }
+    cudaError_t e = cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 256), s->mpool, st);
+    if (e == cudaErrorMemoryAllocation) cudaGetLastError();   // not sticky
+    return e;
 }
+
+// Work in flight whose completion releases memory (or reports a job).
+bool in_flight(Srv *s);
+struct Group;
+scpl_status free_group(Srv *s, Group &G);
 
 void add_reserved(Srv *s, long long delta) {
     s->reserved = (size_t)((long long)s->reserved + delta);
@@ -337,11 +369,11 @@ scpl_status start_job(Srv *s, int jid) {
     };
     if (j.on_host) {
         uint8_t *in = nullptr;
-        SRV_CUDA(s, own(rgb_bytes(j.T, j.H, j.W), &in));
+        SRV_ALLOC(s, own(rgb_bytes(j.T, j.H, j.W), &in));
         SRV_CUDA(s, cudaMemcpyAsync(in, j.frames, rgb_bytes(j.T, j.H, j.W),
                                     cudaMemcpyHostToDevice, m));
         J.in_dev = in;
-        SRV_CUDA(s, own(rgb_bytes(j.T, j.target_H, j.target_W), &J.out_dev));
+        SRV_ALLOC(s, own(rgb_bytes(j.T, j.target_H, j.target_W), &J.out_dev));
     } else {
         J.in_dev = j.frames;
         J.out_dev = j.out;
@@ -366,10 +398,10 @@ scpl_status start_job(Srv *s, int jid) {
     }
     const bool both = J.npass == 2;
     const bool height_only = !both && d[0].W == j.H && j.target_H < j.H;
-    if (both) SRV_CUDA(s, own(rgb_bytes(j.T, j.H, j.target_W), &J.mid));
+    if (both) SRV_ALLOC(s, own(rgb_bytes(j.T, j.H, j.target_W), &J.mid));
     if (j.target_H < j.H) {
-        SRV_CUDA(s, own(rgb_bytes(j.T, j.target_W, j.H), &J.tr_in));
-        SRV_CUDA(s, own(rgb_bytes(j.T, j.target_W, j.target_H), &J.tr_out));
+        SRV_ALLOC(s, own(rgb_bytes(j.T, j.target_W, j.H), &J.tr_in));
+        SRV_ALLOC(s, own(rgb_bytes(j.T, j.target_W, j.target_H), &J.tr_out));
     }
     Pass P;
     P.job = jid;
@@ -392,10 +424,36 @@ scpl_status start_job(Srv *s, int jid) {
     return SCPL_OK;
 }
 
+// A job that ends without running (or without running further): reported at
+// the next poll.
+void complete_now(Srv *s, Job &J, int status) {
+    J.status = status;
+    J.state = J_DONE;
+    s->completed.push_back({J.ticket, status});
+    if (status == SCPL_ECANCELED) s->st.cancelled++;
+    else s->st.failed++;
+    if (J.user) J.user->status = status;
+}
+
+// Undo a start_job whose allocations were refused: the job is queued again.
+void unstart_job(Srv *s, Job &J) {
+    for (void *p : J.owned) cudaFreeAsync(p, s->main);   // after its queued copies
+    J.owned.clear();
+    J.in_dev = nullptr;
+    J.out_dev = J.mid = J.tr_in = J.tr_out = nullptr;
+    if (J.done) cudaEventDestroy(J.done);
+    J.done = nullptr;
+    add_reserved(s, -(long long)J.reserved);
+    J.reserved = 0;
+    J.state = J_QUEUED;
+    s->active_jobs--;
+}
+
 // Admit queued jobs in arrival order while they fit.
 scpl_status admit(Srv *s, bool *any) {
     for (auto &g : s->groups)
         if (g && g->phase == 1) return SCPL_OK;   // a group waits for memory
+    if (s->hold) return SCPL_OK;                  // the allocator refused: wait
     while (!s->queue.empty()) {
         const int jid = s->queue.front();
         Job &J = *s->jobs[jid];
@@ -404,11 +462,7 @@ scpl_status admit(Srv *s, bool *any) {
             if (s->active_jobs > 0) break;   // wait for memory to free up
             if (fp > s->budget) {            // can never fit
                 s->queue.pop_front();
-                J.status = SCPL_ENOMEM;
-                J.state = J_DONE;
-                s->completed.push_back({J.ticket, J.status});
-                s->st.failed++;
-                if (J.user) J.user->status = J.status;
+                complete_now(s, J, SCPL_ENOMEM);
                 *any = true;
                 continue;
             }
@@ -418,6 +472,19 @@ scpl_status admit(Srv *s, bool *any) {
         add_reserved(s, (long long)fp);
         s->active_jobs++;
         scpl_status st = start_job(s, jid);
+        if (st == SCPL_ENOMEM && !s->broken) {
+            // the allocator refused the job's own buffers: wait for running
+            // work to release memory, or fail the job if nothing runs
+            unstart_job(s, J);
+            if (in_flight(s) || s->active_jobs > 0) {
+                s->queue.push_front(jid);
+                s->hold = true;
+                return SCPL_OK;
+            }
+            complete_now(s, J, SCPL_ENOMEM);
+            *any = true;
+            continue;
+        }
         if (st != SCPL_OK) return st;
         *any = true;
     }
@@ -425,9 +492,12 @@ scpl_status admit(Srv *s, bool *any) {
 }
 
 // ---- scan waves ---------------------------------------------------------------
-scpl_status launch_wave(Srv *s) {
+scpl_status launch_wave(Srv *s, bool *launched) {
+    *launched = false;
     if (s->pending_scan.empty()) return SCPL_OK;
+    TraceRange trace("scpl.server.wave");
     std::unique_ptr<Wave> W(new Wave());
+    const size_t g0 = s->groups.size();
     // a cooperative launch starts only when all its CTAs fit at once: while
     // groups are carving, a wave takes half the GPU so that it can start
     // beside them instead of waiting for the whole GPU to drain
@@ -439,6 +509,28 @@ scpl_status launch_wave(Srv *s) {
     for (int pid : s->pending_scan) ((int)take.size() < cap ? take : rest).push_back(pid);
     s->pending_scan = rest;
     W->passes = take;
+    // the allocator refused the wave's memory: its passes go back to the
+    // queue until running work releases memory, or fail if nothing runs
+    auto refused = [&]() -> scpl_status {
+        for (size_t g = g0; g < s->groups.size(); ++g)
+            if (s->groups[g]->ypool) cudaFreeAsync(s->groups[g]->ypool, s->main);
+        s->st.groups -= (long long)(s->groups.size() - g0);
+        s->groups.resize(g0);
+        for (int pid : take) {
+            s->passes[pid].group = -1;
+            s->passes[pid].frame_off = 0;
+        }
+        std::vector<int> back = take;
+        back.insert(back.end(), rest.begin(), rest.end());
+        s->pending_scan = back;
+        if (in_flight(s)) return SCPL_OK;
+        for (int pid : take) {
+            Job &J = *s->jobs[s->passes[pid].job];
+            if (J.status == SCPL_OK) J.status = SCPL_ENOMEM;
+        }
+        *launched = true;   // the failed jobs are reaped next
+        return SCPL_OK;
+    };
     const int wid = (int)s->waves.size();
 
     // groups: passes of one (H, W) in this wave
@@ -483,7 +575,9 @@ scpl_status launch_wave(Srv *s) {
         }
         G.ypool_bytes += e0;
         void *p = nullptr;
-        SRV_CUDA(s, dalloc(s, &p, G.ypool_bytes, m));
+        const cudaError_t ea = dalloc(s, &p, G.ypool_bytes, m);
+        if (ea == cudaErrorMemoryAllocation) return refused();
+        SRV_CUDA(s, ea);
         G.ypool = static_cast<uint8_t *>(p);
     }
 
@@ -528,7 +622,9 @@ scpl_status launch_wave(Srv *s) {
     const size_t bc_off = o;
     o = a256(o + (size_t)total * 4);
     void *slab = nullptr;
-    SRV_CUDA(s, dalloc(s, &slab, o, m));
+    const cudaError_t ea = dalloc(s, &slab, o, m);
+    if (ea == cudaErrorMemoryAllocation) return refused();
+    SRV_CUDA(s, ea);
     W->slab = static_cast<char *>(slab);
     char *base = W->slab;
 
@@ -612,6 +708,7 @@ scpl_status launch_wave(Srv *s) {
     SRV_CUDA(s, cudaEventRecord(W->ev, m));
     s->waves.push_back(std::move(W));
     s->st.scan_waves++;
+    *launched = true;
     return SCPL_OK;
 }
 
@@ -624,6 +721,7 @@ int chunk_len(long v) {
 }
 
 scpl_status launch_chunk(Srv *s, Group &G, int q) {
+    TraceRange trace("scpl.server.chunk");
     cudaGraphExec_t ge = nullptr;
     auto it = G.graphs.find(q);
     if (it != G.graphs.end()) {
@@ -678,6 +776,7 @@ int next_chunk(const Group &G) {
 
 // Items, workspace and the first launches of a group whose scan finished.
 scpl_status setup_group(Srv *s, int gid) {
+    TraceRange trace("scpl.server.group");
     Group &G = *s->groups[gid];
     std::vector<int> ok;
     for (int pid : G.passes)
@@ -691,10 +790,7 @@ scpl_status setup_group(Srv *s, int gid) {
         klog = std::max(klog, P.d.W - P.d.target);
     }
     G.nb = nb;
-    if (nb == 0) {
-        G.phase = 3;
-        return SCPL_OK;
-    }
+    if (nb == 0) return free_group(s, G);   // every pass failed or was cancelled
     CarveWs &ws = G.ws;
     ws = CarveWs{};
     ws.H = G.H;
@@ -737,6 +833,21 @@ scpl_status setup_group(Srv *s, int gid) {
         G.phase = 1;
         return SCPL_OK;
     }
+    void *p = nullptr;
+    SRV_CUDA(s, cudaStreamWaitEvent(G.stream, s->waves[G.wave]->ev, 0));
+    const cudaError_t ea = dalloc(s, &p, bytes, G.stream);
+    if (ea == cudaErrorMemoryAllocation) {
+        // refused: wait for running work to release memory, or fail the
+        // group's jobs if nothing else runs
+        G.phase = 1;
+        if (in_flight(s)) return SCPL_OK;
+        for (int pid : ok) {
+            Job &J = *s->jobs[s->passes[pid].job];
+            if (J.status == SCPL_OK) J.status = SCPL_ENOMEM;
+        }
+        return free_group(s, G);
+    }
+    SRV_CUDA(s, ea);
     G.phase = 2;
     for (int pid : ok) {
         Pass &P = s->passes[pid];
@@ -744,10 +855,8 @@ scpl_status setup_group(Srv *s, int gid) {
         const long long add = (long long)(P.nb - 1) * (long long)item_bytes(P.d, kc);
         s->jobs[P.job]->reserved += add;
         add_reserved(s, add);
+        P.item = true;
     }
-    void *p = nullptr;
-    SRV_CUDA(s, cudaStreamWaitEvent(G.stream, s->waves[G.wave]->ev, 0));
-    SRV_CUDA(s, dalloc(s, &p, bytes, G.stream));
     G.slab = static_cast<char *>(p);
     G.slab_bytes = bytes;
     carve_ws_assign(ws, nb, klog, G.dpc, G.slab);
@@ -820,7 +929,15 @@ scpl_status pass_done(Srv *s, int pid, cudaStream_t gs) {
     Pass P = s->passes[pid];   // a copy: s->passes may grow below
     Job &J = *s->jobs[P.job];
     const scpl_job &j = J.spec;
-    if (J.status != SCPL_OK) return SCPL_OK;
+    if (J.status != SCPL_OK) {
+        // failed or cancelled while the group carved: it ends after the
+        // group's launches that read or write its frames
+        if (J.state == J_ACTIVE && J.done) {
+            SRV_CUDA(s, cudaEventRecord(J.done, gs));
+            J.state = J_FINISHING;
+        }
+        return SCPL_OK;
+    }
     if (P.index == 0 && J.npass == 2) {
         // the height pass works on the transposed output of the width pass
         SRV_CUDA(s, launch_transpose_rgb(J.mid, j.T, j.H, j.target_W, J.tr_in, gs));
@@ -864,10 +981,12 @@ scpl_status free_group(Srv *s, Group &G) {
     add_reserved(s, -(long long)G.held_after);
     G.held_after = 0;
     G.phase = 3;
+    s->hold = false;
     return SCPL_OK;
 }
 
 scpl_status finish_group(Srv *s, int gid) {
+    TraceRange trace("scpl.server.finish");
     Group &G = *s->groups[gid];
     cudaStream_t gs = G.stream;
     if (G.nframes > 0) {
@@ -905,13 +1024,15 @@ scpl_status reap_jobs(Srv *s, bool *any) {
             SRV_CUDA(s, e);
             finished = true;
         } else if (J.status != SCPL_OK) {
-            // failed: done once no scan wave still reads its frames (a failed
-            // pass is never an item of a carving group)
+            // failed or cancelled: done once no scan wave still reads its
+            // frames and no carving group still has its buffers as items (a
+            // group that finishes records J.done after its last launch)
             bool busy = false;
-            for (const Pass &P : s->passes)
-                if (P.job == (int)jid && P.group >= 0 &&
-                    !s->waves[s->groups[P.group]->wave]->done)
-                    busy = true;
+            for (const Pass &P : s->passes) {
+                if (P.job != (int)jid || P.group < 0) continue;
+                const Group &G = *s->groups[P.group];
+                if (!s->waves[G.wave]->done || (P.item && G.phase == 2)) busy = true;
+            }
             if (busy) continue;
             std::vector<int> keep;   // a pass still queued for a scan is dropped
             for (int q : s->pending_scan)
@@ -941,7 +1062,9 @@ scpl_status reap_jobs(Srv *s, bool *any) {
         s->active_jobs--;
         s->completed.push_back({J.ticket, J.status});
         if (J.status == SCPL_OK) s->st.completed++;
+        else if (J.status == SCPL_ECANCELED) s->st.cancelled++;
         else s->st.failed++;
+        s->hold = false;   // memory was released
         if (J.user) {
             J.user->status = J.status;
             J.user->n_buffers = J.spec.n_buffers;
@@ -1034,8 +1157,9 @@ scpl_status round(Srv *s, bool *any) {
     if ((st = reap_jobs(s, any)) != SCPL_OK) return st;
     if ((st = admit(s, any)) != SCPL_OK) return st;
     if (!s->pending_scan.empty()) {
-        if ((st = launch_wave(s)) != SCPL_OK) return st;
-        *any = true;
+        bool launched = false;
+        if ((st = launch_wave(s, &launched)) != SCPL_OK) return st;
+        if (launched) *any = true;
     }
     compact(s);
     return SCPL_OK;
@@ -1160,11 +1284,7 @@ scpl_status submit(Srv *s, const scpl_job *job, scpl_job *user, long long *ticke
     s->st.submitted++;
     const scpl_status v = check_job(s->p, J->spec);
     if (v != SCPL_OK) {   // fails alone, reported at the next poll
-        J->status = v;
-        J->state = J_DONE;
-        s->completed.push_back({J->ticket, v});
-        s->st.failed++;
-        if (user) user->status = v;
+        complete_now(s, *J, v);
         s->jobs.push_back(std::move(J));
         return SCPL_OK;
     }
@@ -1197,6 +1317,30 @@ scpl_status progress(Srv *s, int wait) {
 }
 
 bool idle(Srv *s) { return s->active_jobs == 0 && s->queue.empty(); }
+
+// Cancel a job: a queued job ends at once; an admitted one stops taking new
+// stages and ends when the launches already made for it have finished.
+scpl_status cancel(Srv *s, long long ticket) {
+    for (size_t jid = 0; jid < s->jobs.size(); ++jid) {
+        Job &J = *s->jobs[jid];
+        if (J.ticket != ticket) continue;
+        if (J.state == J_QUEUED) {
+            for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+                if (*it == (int)jid) {
+                    s->queue.erase(it);
+                    break;
+                }
+            complete_now(s, J, SCPL_ECANCELED);
+            return SCPL_OK;
+        }
+        if (J.state == J_ACTIVE && J.status == SCPL_OK) {
+            J.status = SCPL_ECANCELED;
+            return SCPL_OK;
+        }
+        return sfail(s, SCPL_EINVAL, "job %lld has already finished or failed", ticket);
+    }
+    return sfail(s, SCPL_EINVAL, "no job with ticket %lld", ticket);
+}
 
 bool in_flight(Srv *s) {
     for (auto &W : s->waves)
@@ -1334,6 +1478,18 @@ int scpl_server_poll(scpl_server s, long long *tickets, int *statuses, int max) 
 scpl_status scpl_server_drain(scpl_server s) {
     if (!s) return SCPL_EINVAL;
     return drain(s);
+}
+
+scpl_status scpl_server_cancel(scpl_server s, long long ticket) {
+    if (!s) return SCPL_EINVAL;
+    return cancel(s, ticket);
+}
+
+scpl_status scpl_server_refuse_allocations(scpl_server s, long long skip, int count) {
+    if (!s || skip < 0 || count < 0) return SCPL_EINVAL;
+    s->refuse_skip = skip;
+    s->refuse_n = count;
+    return SCPL_OK;
 }
 
 scpl_status scpl_server_get_stats(scpl_server s, scpl_server_stats *out) {

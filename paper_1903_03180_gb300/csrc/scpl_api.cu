@@ -115,6 +115,7 @@ struct scpl_ctx {
     int dpc_W0 = -1, dpc_H = -1, dpc_R = -1, dpc_WPC = -1;
     bool dpc_ok = false;
     bool autotune = false;
+    unsigned long long wait_ns = SPIN_LIMIT_NS;   // bound of the scan's device-wide waits
     // host-memory path: copy stream, side stream for early gathers, the
     // arrival counter of the frames and its driver entry point
     cudaStream_t cstream = nullptr, gstream = nullptr;
@@ -203,6 +204,7 @@ constexpr int E0_PLANES = 16;   // buffers whose summed energy the scan keeps
 scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
                      std::vector<int> &starts, bool keep_e0, long long *A = nullptr,
                      int *M = nullptr, const unsigned *ready = nullptr, int ready_frames = 1) {
+    TraceRange trace("scpl.scan");
     const long ypitch = round_up(W, 16);
     const long hw = (long)H * W;
     int gerr = 0;
@@ -241,7 +243,7 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     a.wg = h->p.wg; a.wm = h->p.wm; a.alpha = h->p.alpha;
     a.t_max = effective_tmax(h->p); a.maxval_mode = h->p.maxval_mode;
     a.maxval_theory = energy_max(h->p);
-    a.spin_limit_ns = SPIN_LIMIT_NS;
+    a.spin_limit_ns = h->wait_ns;
     a.E0 = h->e0cap ? h->E0.as<int32_t>() : nullptr;
     a.nbcap = h->e0cap;
     a.e0_plane = hw;
@@ -263,7 +265,7 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     SCPL_CUDA(h, cudaStreamSynchronize(s));
     if (hs[0] == DEV_ETIMEOUT)
         return fail(h, SCPL_ETIMEOUT, "buffer scan: a device-wide wait exceeded %llu ns",
-                    SPIN_LIMIT_NS);
+                    h->wait_ns);
     int nb = hs[1];
     if (nb < 1 || nb > T) return fail(h, SCPL_ECUDA, "buffer scan returned %d buffers", nb);
     starts.assign(hs + 2, hs + 2 + nb + 1);
@@ -368,6 +370,7 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
     if ((s = run_scan(h, frames, T, H, W, starts, true, nullptr, nullptr, ready, ready_frames)) != SCPL_OK) return s;
     const int nb = (int)starts.size() - 1;
     const int remove = W - target_W;
+    TraceRange trace("scpl.carve");
     CarveWs ws;
     if ((s = carve_ws(h, nb, H, W, std::min(k, std::max(remove, 1)), ws, remove)) != SCPL_OK)
         return s;
@@ -419,6 +422,7 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
     const size_t frame_out = (size_t)H * target_W * 3;
     auto gather_out = [&](int b) -> scpl_status {
         const int t0 = starts[b], nt = starts[b + 1] - starts[b];
+        TraceRange gtrace("scpl.gather");
         SCPL_CUDA(h, cudaEventRecord(ev_carved, st));
         SCPL_CUDA(h, cudaStreamWaitEvent(h->gstream, ev_carved, 0));
         SCPL_CUDA(h, timed_on(h, K_GATHER, h->gstream, [&] {
@@ -613,6 +617,42 @@ scpl_status scpl_scan(scpl_handle h, const uint8_t *frames, int T, int H, int W,
     if ((s = run_scan(h, frames, T, H, W, starts, false)) != SCPL_OK) return s;
     if (buffer_starts) std::copy(starts.begin(), starts.end(), buffer_starts);
     if (n_buffers) *n_buffers = (int)starts.size() - 1;
+    return SCPL_OK;
+}
+
+scpl_status scpl_scan_arrivals(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                               const uint32_t *arrived, int chunk, int32_t *buffer_starts,
+                               int *n_buffers) {
+    scpl_status s = check_frames(h, frames, T, H, W);
+    if (s != SCPL_OK) return s;
+    if (!arrived) return fail(h, SCPL_EINVAL, "arrived is NULL");
+    if (chunk < 1) return fail(h, SCPL_EINVAL, "chunk=%d must be >= 1", chunk);
+    if ((s = check_overflow(h, T, H)) != SCPL_OK) return s;
+    std::vector<int> starts;
+    if ((s = run_scan(h, frames, T, H, W, starts, false, nullptr, nullptr, arrived, chunk)) !=
+        SCPL_OK)
+        return s;
+    if (buffer_starts) std::copy(starts.begin(), starts.end(), buffer_starts);
+    if (n_buffers) *n_buffers = (int)starts.size() - 1;
+    return SCPL_OK;
+}
+
+scpl_status scpl_signal_arrival(void *stream, uint32_t *counter, uint32_t value) {
+    if (!counter) return SCPL_EINVAL;
+    PFN_cuStreamWriteValue32_v11070 write_value = stream_write_value();
+    if (!write_value) return SCPL_ECUDA;
+    return write_value(reinterpret_cast<CUstream>(stream), reinterpret_cast<CUdeviceptr>(counter),
+                       (cuuint32_t)value, CU_STREAM_WRITE_VALUE_DEFAULT) == CUDA_SUCCESS
+               ? SCPL_OK
+               : SCPL_ECUDA;
+}
+
+scpl_status scpl_set_wait_limit(scpl_handle h, uint64_t ns) {
+    if (!h) return SCPL_EINVAL;
+    if (ns < 100000ull || ns > 60000000000ull)
+        return fail(h, SCPL_EINVAL, "wait limit %llu ns outside [1e5, 6e10]",
+                    (unsigned long long)ns);
+    h->wait_ns = ns;
     return SCPL_OK;
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 namespace scpl {
@@ -11,10 +12,21 @@ constexpr uint64_t KEY_INF = ~0ull;
 constexpr uint64_t KEY_DIR_MASK = 0xFFull << 24;   // tie-break / direction byte of a DP key
 constexpr uint32_t LABEL_MASK = 0xFFFFFFu;         // 24-bit parent label of a DP key
 
-// Status words written by kernels (mirror scpl_status).
+// Status words written by kernels (DEV_OK and DEV_ETIMEOUT have the values of
+// the matching scpl_status; the host maps DEV_EINTERNAL to SCPL_ECUDA).
 constexpr int DEV_OK = 0;
 constexpr int DEV_ETIMEOUT = 4;
 constexpr int DEV_EINTERNAL = 6;   // an internal table held an out-of-range column
+
+// A named NVTX range over a host scope: the library's stages on a profiler's
+// timeline (scan, carve, gather, server waves, groups and chunks, tuning).
+// Without an attached tool the push and pop return at once.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
 
 // Per-buffer carving state, one per spatiotemporal buffer, in device memory.
 // An iteration's seams are selected by k_dp_select (k_eff > 0 = "pending");

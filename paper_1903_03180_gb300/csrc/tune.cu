@@ -96,6 +96,7 @@ void tuning_apply(int H, int W, CarveWs &ws, bool *use_dpc) {
 
 scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
     if (H < 1 || W < 4 || k < 1) return SCPL_EINVAL;
+    TraceRange trace("scpl.tune");
     const int remove = std::min(W - 2, 4 * k);
     const int kcap = std::max(1, std::min(k, remove));
     scpl_tuning t{};

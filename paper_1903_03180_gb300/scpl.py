@@ -17,9 +17,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libscpl.so")
 _lib = None
 
-SCPL_OK, SCPL_EINVAL, SCPL_ENOMEM, SCPL_ECUDA, SCPL_ETIMEOUT, SCPL_EOVERFLOW = range(6)
+(SCPL_OK, SCPL_EINVAL, SCPL_ENOMEM, SCPL_ECUDA, SCPL_ETIMEOUT, SCPL_EOVERFLOW,
+ SCPL_ECANCELED) = range(7)
 STATUS_NAMES = {0: "SCPL_OK", 1: "SCPL_EINVAL", 2: "SCPL_ENOMEM", 3: "SCPL_ECUDA",
-                4: "SCPL_ETIMEOUT", 5: "SCPL_EOVERFLOW"}
+                4: "SCPL_ETIMEOUT", 5: "SCPL_EOVERFLOW", 6: "SCPL_ECANCELED"}
 
 # every symbol the header declares, with (restype, argtypes)
 _P, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
@@ -58,7 +59,8 @@ class ServerStats(ctypes.Structure):
                 ("scan_waves", ctypes.c_longlong), ("groups", ctypes.c_longlong),
                 ("chunks", ctypes.c_longlong), ("graphs_built", ctypes.c_longlong),
                 ("kernel_launches", ctypes.c_longlong), ("reserved_bytes", ctypes.c_size_t),
-                ("peak_reserved_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t)]
+                ("peak_reserved_bytes", ctypes.c_size_t), ("budget_bytes", ctypes.c_size_t),
+                ("cancelled", ctypes.c_longlong)]
 
 
 class Tuning(ctypes.Structure):
@@ -78,6 +80,9 @@ SIGNATURES = {
     "scpl_energy": (_I, [_P, _P, _I, _I, _I, _P]),
     "scpl_scan": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "scpl_scan_stats": (_I, [_P, _P, _I, _I, _I, _P, _P, _P, _P]),
+    "scpl_scan_arrivals": (_I, [_P, _P, _I, _I, _I, _P, _I, _P, _P]),
+    "scpl_signal_arrival": (_I, [_P, _P, ctypes.c_uint32]),
+    "scpl_set_wait_limit": (_I, [_P, ctypes.c_uint64]),
     "scpl_seams": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "scpl_carve": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
     "scpl_carve_host": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
@@ -99,6 +104,8 @@ SIGNATURES = {
     "scpl_server_progress": (_I, [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "scpl_server_poll": (_I, [_P, ctypes.POINTER(_LL), ctypes.POINTER(_I), _I]),
     "scpl_server_drain": (_I, [_P]),
+    "scpl_server_cancel": (_I, [_P, _LL]),
+    "scpl_server_refuse_allocations": (_I, [_P, _LL, _I]),
     "scpl_server_get_stats": (_I, [_P, ctypes.POINTER(ServerStats)]),
     "scpl_server_last_error": (ctypes.c_char_p, [_P]),
     "scpl_server_destroy": (None, [_P]),
@@ -224,6 +231,44 @@ def scpl_scan_stats(h, frames):
     _check(h, load().scpl_scan_stats(h, fp, T, H, W, starts.ctypes.data_as(_P), ctypes.byref(nb),
                                      A.ctypes.data_as(_P), M.ctypes.data_as(_P)))
     return starts[: nb.value + 1].copy(), A, M
+
+
+def scpl_scan_arrivals(h, frames, arrived, chunk: int) -> np.ndarray:
+    """scpl_scan on frames a producer is still copying in: arrived is a cuda
+    int32/uint32 tensor of one element, raised (scpl_signal_arrival) to the
+    number of complete chunks of `chunk` frames.  Raises SCPLError with
+    status SCPL_ETIMEOUT if the counter stops short."""
+    import torch
+    fp = _dev_ptr(frames, torch.uint8, 4, "frames")
+    ap = _counter_ptr(arrived)
+    T, H, W, _ = frames.shape
+    starts = np.zeros(T + 1, np.int32)
+    nb = ctypes.c_int()
+    _check(h, load().scpl_scan_arrivals(h, fp, T, H, W, ap, int(chunk),
+                                        starts.ctypes.data_as(_P), ctypes.byref(nb)))
+    return starts[: nb.value + 1].copy()
+
+
+def scpl_signal_arrival(stream, counter, value: int):
+    """Enqueue on `stream` (a torch.cuda.Stream, a raw handle, or None for
+    torch's current stream) the write of `value` to the one-element cuda
+    counter tensor."""
+    st = load().scpl_signal_arrival(ctypes.c_void_p(_stream_ptr(stream)), _counter_ptr(counter),
+                                    int(value))
+    if st != SCPL_OK:
+        raise SCPLError(st, "scpl_signal_arrival failed")
+
+
+def scpl_set_wait_limit(h, ns: int):
+    _check(h, load().scpl_set_wait_limit(h, int(ns)))
+
+
+def _counter_ptr(t):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.numel() == 1
+            and t.dtype in (torch.int32, torch.uint32)):
+        raise ValueError("counter must be a one-element cuda int32/uint32 tensor")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def scpl_seams(h, energy, k: int, cols) -> int:
@@ -494,6 +539,14 @@ class Server:
 
     def drain(self):
         self._err(self.lib.scpl_server_drain(self.s))
+
+    def cancel(self, ticket: int):
+        """Cancel a job; it completes with SCPL_ECANCELED (reported by poll)."""
+        self._err(self.lib.scpl_server_cancel(self.s, int(ticket)))
+
+    def refuse_allocations(self, skip: int, count: int):
+        """Fault injection: refuse `count` device allocations after `skip`."""
+        self._err(self.lib.scpl_server_refuse_allocations(self.s, int(skip), int(count)))
 
     def stats(self) -> dict:
         st = ServerStats()
