@@ -8,8 +8,10 @@ buffer and the colour gather, inputs resident in HBM.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
---impl reference times the CPU oracle (single-threaded C) on a bounded sample
-of the same workload; that is this project's reference arm.  Under torchrun
+--impl reference times the CPU oracle (C, one process per host core, each
+carving its own sub-clip) on a bounded sample of the same workload; that is
+this project's reference arm.  --compare-raw adds the paper's comparison with
+raw seam carving (classic, frame by frame) on the GPU and in the oracle.  Under torchrun
 every rank carves its own clip (weak scaling, no collective on the data
 path); rank 0 prints the line.
 """
@@ -133,38 +135,179 @@ def cpu_baseline(name: str, frames: np.ndarray, n_frames: int) -> dict:
                       f"single-threaded C oracle ({dt:.1f} s)"}
 
 
+def _oracle_warm(_):
+    import oracle
+    oracle._load()
+    return os.getpid()
+
+
+def _oracle_carve(task):
+    """One process of the all-cores oracle run: carve frames [a, b) of the
+    memory-mapped workload as a clip of its own; returns the seconds taken."""
+    path, a, b, target, k, wg, wm, use_buffer = task
+    import oracle
+    sub = np.ascontiguousarray(np.load(path, mmap_mode="r")[a:b])
+    t0 = time.perf_counter()
+    oracle.carve(sub, target, k, wg=wg, wm=wm, use_buffer=use_buffer)
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """The oracle on every host core: `procs` spawned processes, each carving
+    an independent sub-clip of the workload (clips are independent units of
+    the method, so this is the oracle as it stands, run side by side)."""
+
+    def __init__(self, name: str, frames: np.ndarray, procs: int = 0):
+        import multiprocessing as mp
+        import oracle
+        oracle.build()
+        self.name = name
+        self.T = frames.shape[0]
+        self.procs = procs or os.cpu_count() or 1
+        self.dir = tempfile.mkdtemp(prefix="scpl_oracle_")
+        self.path = os.path.join(self.dir, "frames.npy")
+        np.save(self.path, frames)
+        self.pool = mp.get_context("spawn").Pool(self.procs)
+        self.pool.map(_oracle_warm, range(self.procs))
+
+    def run(self, n: int) -> dict:
+        T, H, W, target, k, _, (wg, wm), use_buffer = WORKLOADS[self.name]
+        n = max(1, min(n, self.T))
+        span = max(self.T - n + 1, 1)
+        tasks = [(self.path, (p * n) % span, (p * n) % span + n, target, k, wg, wm, use_buffer)
+                 for p in range(self.procs)]
+        t0 = time.perf_counter()
+        per = self.pool.map(_oracle_carve, tasks, chunksize=1)
+        wall = time.perf_counter() - t0
+        return {"frames": n * self.procs, "wall_s": wall, "max_proc_s": max(per)}
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+        os.unlink(self.path)
+        os.rmdir(self.dir)
+
+
+def _oracle_batch_job(task):
+    """One process of the batched workload's oracle run: the first n frames
+    of one job (its own size, targets and k) carved by the oracle."""
+    spec, n = task
+    import oracle
+
+    from paper_1903_03180_gb300 import synth
+    sub = np.ascontiguousarray(synth.batch_clip(spec)[:n])
+    t0 = time.perf_counter()
+    oracle.carve_job(sub, spec["target_W"], spec["target_H"], spec["k"])
+    return time.perf_counter() - t0, len(sub)
+
+
+def cpu_baseline_batch(specs: list, n_frames: int) -> dict:
+    """The oracle on every host core for the batched workload: process p
+    carves the first n_frames frames of job p."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    procs = min(os.cpu_count() or 1, len(specs))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        pool.map(_oracle_warm, range(procs))
+        t0 = time.perf_counter()
+        per = pool.map(_oracle_batch_job, [(specs[p], n_frames) for p in range(procs)],
+                       chunksize=1)
+        wall = time.perf_counter() - t0
+    frames = sum(n for _, n in per)
+    busy = sum(t for t, _ in per)
+    sizes = sorted({f"{sp['W']}x{sp['H']}" for sp in specs[:procs]})
+    return {"value": round(frames / wall, 4), "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": f"{procs} processes (one per host core), process p carving the first "
+                      f"{n_frames} frames of job p ({', '.join(sizes)}) with the C oracle "
+                      f"({wall:.1f} s wall)",
+            "one_core_value": round(frames / busy, 4),
+            "one_core_note": "frames / summed per-process seconds, measured while all cores ran"}
+
+
+def cpu_baseline_all_cores(name: str, frames: np.ndarray, n_frames: int) -> dict:
+    pool = OraclePool(name, frames)
+    try:
+        r = pool.run(n_frames)
+    finally:
+        pool.close()
+    return {"value": round(r["frames"] / r["wall_s"], 4), "unit": UNIT, "cores": pool.procs,
+            "kind": "oracle",
+            "sample": f"{pool.procs} processes (one per host core), each carving its own "
+                      f"{n_frames}-frame sub-clip of {name} as a clip with the C oracle "
+                      f"({r['wall_s']:.1f} s wall)"}
+
+
 def run_reference(args) -> None:
     ws, rank, _ = _dist()
     if rank != 0:
         return
-    import oracle
-    oracle.build()
     name = args.workload
     frames = make_frames(name)
     n = args.ref_frames
-    for _ in range(args.warmup):
-        cpu_baseline(name, frames, n)
-    vals = []
-    t_all = time.perf_counter()
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        cpu_baseline(name, frames, n)
-        vals.append(time.perf_counter() - t0)
-    total = time.perf_counter() - t_all
-    value = n * args.steps / total
-    sample = (f"each step: first {n} frames of {name} (energy, buffer scan, carving) by the "
-              f"single-threaded C oracle")
+    pool = OraclePool(name, frames, args.ref_procs)
+    try:
+        for _ in range(args.warmup):
+            pool.run(n)
+        t_all = time.perf_counter()
+        done = 0
+        for _ in range(args.steps):
+            done += pool.run(n)["frames"]
+        total = time.perf_counter() - t_all
+    finally:
+        pool.close()
+    value = done / total
+    sample = (f"each step: {pool.procs} processes (one per host core), each carving its own "
+              f"{n}-frame sub-clip of {name} (energy, buffer scan, carving) with the C oracle")
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1000 * total / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": name, "frames_per_step": n},
-            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": 1,
+            "config": {"workload": name, "frames_per_step": n * pool.procs},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": pool.procs,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def raw_comparison(frames, frames_np, name: str, scpl_ms: float, cpu_frames: int,
+                   cpu_scpl: dict | None) -> dict:
+    """The paper's comparison of SCPL with raw seam carving (classic seam
+    carving frame by frame: k = 1, no buffer, the same energy) on this
+    hardware: the same clip carved both ways through the same kernels, and
+    the oracle both ways on a sample."""
+    import torch
+
+    from paper_1903_03180_gb300 import scpl
+    T, H, W, target, k, _, (wg, wm), use_buffer = WORKLOADS[name]
+    raw = scpl.Retargeter(wg=wg, wm=wm, use_buffer=False, stream=torch.cuda.current_stream())
+    out = torch.empty((frames.shape[0], H, target, 3), dtype=torch.uint8, device="cuda")
+    scpl.scpl_carve(raw.h, frames, target, 1, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    scpl.scpl_carve(raw.h, frames, target, 1, out)
+    e1.record()
+    torch.cuda.synchronize()
+    raw_ms = e0.elapsed_time(e1)
+    raw.close()
+    res = {"what": "raw = classic seam carving per frame (k = 1, no buffer, same energy)",
+           "gpu_scpl_ms_per_clip": round(scpl_ms, 3), "gpu_raw_ms_per_clip": round(raw_ms, 3),
+           "gpu_reduction": round(1.0 - scpl_ms / raw_ms, 4)}
+    import oracle
+    sub = np.ascontiguousarray(frames_np[:cpu_frames])
+    t0 = time.perf_counter()
+    oracle.carve(sub, target, 1, wg=wg, wm=wm, use_buffer=False)
+    raw_s = (time.perf_counter() - t0) / len(sub)
+    res["cpu_raw_s_per_frame"] = round(raw_s, 3)
+    res["cpu_sample"] = f"first {len(sub)} frames, single-threaded C oracle"
+    if cpu_scpl:
+        scpl_s = 1.0 / cpu_scpl["value"]
+        res["cpu_scpl_s_per_frame"] = round(scpl_s, 3)
+        res["cpu_reduction"] = round(1.0 - scpl_s / raw_s, 4)
+    return res
 
 
 def run_native(args) -> None:
@@ -284,9 +427,14 @@ def run_native(args) -> None:
                "h2d_bytes_per_step": int(frames_np.nbytes),
                "d2h_bytes_per_step": int(hout_np.nbytes)}
 
-    cpu = None
+    cpu = cpu1 = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(name, frames_np, args.cpu_frames)
+        cpu1 = cpu_baseline(name, frames_np, args.cpu_frames)
+        cpu = cpu_baseline_all_cores(name, frames_np, args.cpu_frames)
+    raw = None
+    if rank == 0 and args.compare_raw:
+        raw = raw_comparison(frames, frames_np, name, total_ms / args.steps,
+                             args.raw_cpu_frames, cpu1)
 
     if rank == 0:
         algo_gb = all_bytes / args.steps / 1e9
@@ -315,7 +463,10 @@ def run_native(args) -> None:
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "cpu_baseline_1core": cpu1,
         }
+        if raw:
+            line["raw_sc"] = raw
         print(json.dumps(line), flush=True)
     r.close()
     if dist:
@@ -374,6 +525,7 @@ def run_batch(args) -> None:
     one_ms = _event_ms(lambda: [scpl.scpl_carve_batch(h, [j]) for j in jobs1])
     identical = all(torch.equal(a, b) for a, b in zip(outs, outs1))
     scpl.scpl_destroy(h)
+    cpu = None if args.no_cpu_baseline else cpu_baseline_batch(specs, args.batch_cpu_frames)
     total = sum(step_ms)
     value = frames * args.steps / (total / 1000.0)
     one = frames / (one_ms / 1000.0)
@@ -404,7 +556,8 @@ def run_batch(args) -> None:
                                 sp["H"] if sp["target_H"] < sp["H"] else sp["W"])
                                for sp in specs})},
             "gpu_launches": int((st1["kernel_launches"] - st0["kernel_launches"]) / steps),
-            "clocks": clk}
+            "clocks": clk,
+            "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
 
@@ -516,9 +669,17 @@ def main():
     ap.add_argument("--out-buffers", type=int, default=6,
                     help="serve: page-locked output buffers per size (requests in flight)")
     ap.add_argument("--ref-frames", type=int, default=8,
-                    help="frames of the workload the oracle carves per reference step")
+                    help="frames each oracle process carves per reference step")
+    ap.add_argument("--ref-procs", type=int, default=0,
+                    help="oracle processes of the reference arm (0: one per host core)")
+    ap.add_argument("--compare-raw", action="store_true",
+                    help="also carve the clip as raw seam carving (k = 1, no buffer)")
+    ap.add_argument("--raw-cpu-frames", type=int, default=1,
+                    help="frames the oracle carves as raw seam carving for --compare-raw")
     ap.add_argument("--cpu-frames", type=int, default=16,
                     help="frames of the workload the oracle carves for cpu_baseline")
+    ap.add_argument("--batch-cpu-frames", type=int, default=4,
+                    help="batch: frames of each job the oracle carves for cpu_baseline")
     ap.add_argument("--frames", type=int, default=0,
                     help="carve only the first N frames of the workload (smaller profiling case)")
     ap.add_argument("--no-e2e", action="store_true")
