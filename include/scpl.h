@@ -245,21 +245,26 @@ scpl_status scpl_get_stats(scpl_handle h, scpl_stats *out);
 
 /* ------------------------------------------------------------------------
  * Autotuning (no counterpart in the paper).  Per frame size (H, W, in carving
- * orientation) the carving kernels have choices that change only the time:
- * the cluster DP's halo depth R (16: 96 columns a warp, a halo exchange every
- * 16 rows; 32: 64 columns a warp, an exchange every 32 rows), its warps per
- * CTA (4 or 8, i.e. how many CTAs carve one frame), the single-CTA DP instead
- * of the cluster, and the rows per update CTA.  A process-wide
- * table holds one choice per size; scpl_carve, scpl_carve_batch and servers
- * use it when an entry exists, and the defaults (R = 32, the most update rows
- * that fit) otherwise. */
+ * orientation) the carving kernels have choices that change only the time.
+ * The cluster DP holds V columns per lane, so a warp holds 32V columns, and
+ * owns 32V - 2R of them with halo depth R (the rows between halo exchanges):
+ * V = 4, R = 32 owns 64; V = 4, R = 16 owns 96; V = 2, R = 16 owns 32 with
+ * half the instructions per row and warp.  Its CTAs have 4 or 8 warps (how
+ * many CTAs carve one frame, and whether two warps share an SM
+ * sub-partition).  The single-CTA DP can replace the cluster, and the update
+ * takes 1, 2 or 4 rows per CTA.  A process-wide table holds one choice per
+ * size; scpl_carve, scpl_carve_batch and servers use it when an entry exists,
+ * and the defaults (R = 32, V = 4, 4 warps, the most update rows that fit)
+ * otherwise. */
 typedef struct {
     int H, W;
     int dpc_halo;        /* 16 or 32: the cluster DP's R; 0: the single-CTA DP        */
-    int dpc_warps;       /* warps per cluster-DP CTA: 4 or 8 (8 halves the CTAs a frame) */
+    int dpc_warps;       /* warps per cluster-DP CTA: 4 or 8                            */
+    int dpc_lane_cols;   /* columns per lane of the cluster DP: 4, or 2 with R = 16     */
     int update_rows;     /* rows per update CTA: 1, 2 or 4                              */
-    float dp_us[5];      /* measured DP times, us (< 0: unusable): R32 x 4 warps, R16 x 4,
-                            R32 x 8, R16 x 8, the single-CTA DP                        */
+    float dp_us[7];      /* measured DP times, us (< 0: unusable): R32 x 4 warps, R16 x 4,
+                            R32 x 8, R16 x 8 (4 columns a lane), the single-CTA DP,
+                            R16 x 4 warps and R16 x 8 warps with 2 columns a lane      */
     float up_us[3];      /* measured update times with 1, 2 and 4 rows, us              */
 } scpl_tuning;
 

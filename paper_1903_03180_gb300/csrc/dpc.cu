@@ -1,18 +1,23 @@
 // k_dpc: one SCPL iteration (Sec. 3.1, Eq. 4-6) of a buffer on a thread-block
 // cluster.
 //
-// DP (Eq. 4 with parental labels, Eq. 5).  Warp g of the cluster owns the 96
-// columns [96g, 96g+96) and holds a 128-column window [96g-16, 96g+112) in
-// registers, 4 consecutive columns per lane.  A row step needs only the
-// neighbours in the adjacent lanes (shuffles); the window's outer columns go
-// stale one column per row (trapezoid), so after 32 rows exactly the owned
-// columns are still exact.  Then every warp sends the 32 owned columns at each
-// of its edges straight into its neighbours' inboxes with st.async (shared or
-// distributed shared memory), which completes on the receiving warp's
-// mbarrier, and refreshes its own 32-column halos from its inbox.  Warps are
-// coupled only to their two neighbours; the DP loop takes no CTA or cluster
-// barrier.  Each warp's energy rows arrive by TMA tensor copies (one
-// 16-row x 128-column box per stage) into its own four-stage ring.
+// DP (Eq. 4 with parental labels, Eq. 5).  Each lane holds V consecutive
+// columns (V = 4 or 2), so a warp holds a window of 32V columns in registers.
+// With halo depth R, warp g owns the 32V - 2R columns in the middle of its
+// window, [g(32V-2R), (g+1)(32V-2R)), and the window starts R columns to the
+// left of them.  (V = 4, R = 32: 64 owned of 128; V = 4, R = 16: 96 of 128;
+// V = 2, R = 16: 32 of 64.)  A row step needs only the neighbours in the
+// adjacent lanes (shuffles); the window's outer columns go stale one column
+// per row (trapezoid), so after R rows exactly the owned columns are still
+// exact.  Then every warp sends the R owned columns at each of its edges
+// straight into its neighbours' inboxes with st.async (shared or distributed
+// shared memory), which completes on the receiving warp's mbarrier, and
+// refreshes its own R-column halos from its inbox.  Warps are coupled only to
+// their two neighbours; the DP loop takes no CTA or cluster barrier.  Each
+// warp's energy rows arrive by TMA tensor copies (one 16-row x 32V-column box
+// per stage) into its own ring.  V = 2 halves a warp's instructions per row,
+// so two warps can share an SM sub-partition and fill each other's dependency
+// stalls.
 //
 // Columns outside [0, W) carry energy 2^31: a real cumulative energy is below
 // 2^31 (checked on the host), so the column next to a real one always ends up
@@ -40,6 +45,9 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <type_traits>
 
 #include "scpl_internal.cuh"
@@ -50,22 +58,22 @@ namespace scpl {
 
 namespace {
 
-constexpr int DPC_V = 4;                         // columns per lane
 constexpr int DPC_S = 16;                        // rows per TMA stage of the energy ring
-// The halo depth R (16 or 32, a template parameter of k_dpc) is also the
-// number of rows between halo refreshes.  A warp's window is always 128
-// columns, so it owns 128 - 2R of them (96 or 64): R trades the exchange
-// frequency against the columns per warp.
-constexpr int DPC_WW = 32 * DPC_V;               // columns of a warp's window: 128
-__host__ __device__ constexpr int dpc_oww(int R) { return DPC_WW - 2 * R; }
-// Warps per CTA (4 or 8, the other template parameter): with 8 the cluster
-// needs half the CTAs and two warps share an SM sub-partition, each warp's
-// energy ring then holding 2 stages instead of 4 to fit shared memory.
-__host__ __device__ constexpr int dpc_nst(int WPC) { return WPC == 8 ? 2 : 4; }
-__host__ __device__ constexpr int dpc_lmax(int R, int WPC) { return WPC * dpc_oww(R); }
-constexpr size_t DPC_WSLOT = (size_t)DPC_S * DPC_WW * 4;   // one warp's stage: 8 KB
-__host__ __device__ constexpr size_t dpc_ring(int WPC) {
-    return (size_t)WPC * dpc_nst(WPC) * DPC_WSLOT;
+// The template parameters of k_dpc: the halo depth R (16 or 32), which is also
+// the number of rows between halo refreshes; the warps per CTA WPC (4 or 8:
+// with 8 the cluster needs half the CTAs and two warps share an SM
+// sub-partition); and the columns per lane V (4 or 2; 2 only with R = 16).
+__host__ __device__ constexpr int dpc_ww(int V) { return 32 * V; }   // a warp's window
+__host__ __device__ constexpr int dpc_oww(int R, int V) { return dpc_ww(V) - 2 * R; }
+// energy stages in flight per warp (8 warps of 128-column windows keep 2 to
+// fit shared memory)
+__host__ __device__ constexpr int dpc_nst(int WPC, int V) { return WPC == 8 && V == 4 ? 2 : 4; }
+__host__ __device__ constexpr int dpc_lmax(int R, int WPC, int V) { return WPC * dpc_oww(R, V); }
+__host__ __device__ constexpr size_t dpc_wslot(int V) {   // one warp's stage: 8 or 4 KB
+    return (size_t)DPC_S * dpc_ww(V) * 4;
+}
+__host__ __device__ constexpr size_t dpc_ring(int WPC, int V) {
+    return (size_t)WPC * dpc_nst(WPC, V) * dpc_wslot(V);
 }
 constexpr size_t DPC_STAGE_BUDGET = 96 * 1024;   // trace-back staging
 constexpr uint32_t BIG = 0x80000000u;            // energy of columns outside [0, W)
@@ -109,13 +117,20 @@ __device__ __forceinline__ uint32_t mapa_u32(uint32_t addr, uint32_t rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
     return r;
 }
-// 16 bytes into (possibly another CTA's) shared memory, completing on that
-// CTA's mbarrier.
-__device__ __forceinline__ void st_async_v4(uint32_t raddr, const uint32_t (&v)[4], uint32_t rmbar) {
+// 16 or 8 bytes into (possibly another CTA's) shared memory, completing on
+// that CTA's mbarrier.
+__device__ __forceinline__ void st_async_v(uint32_t raddr, const uint32_t (&v)[4], uint32_t rmbar) {
     asm volatile(
         "st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::
             "r"(raddr),
         "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(rmbar)
+        : "memory");
+}
+__device__ __forceinline__ void st_async_v(uint32_t raddr, const uint32_t (&v)[2], uint32_t rmbar) {
+    asm volatile(
+        "st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.b32 [%0], {%1, %2}, [%3];" ::"r"(
+            raddr),
+        "r"(v[0]), "r"(v[1]), "r"(rmbar)
         : "memory");
 }
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *tm, int x, int y, int z,
@@ -151,17 +166,21 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t *mbar, unsigned parit
     return true;
 }
 
-template <int R, int WPC>
+template <int R, int WPC, int V>
 __global__ void __launch_bounds__(WPC * 32, 1)
 k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams,
       long seam_stride) {
+    static_assert((V == 4 && (R == 16 || R == 32)) || (V == 2 && R == 16), "window layout");
+    constexpr int DPC_V = V;                      // columns per lane
+    constexpr int DPC_WW = dpc_ww(V);             // columns of a warp's window
+    constexpr size_t DPC_WSLOT = dpc_wslot(V);    // bytes of one warp's stage
     constexpr int DPC_WPC = WPC;                  // warps per CTA
-    constexpr int DPC_NST = dpc_nst(WPC);         // energy stages in flight per warp
+    constexpr int DPC_NST = dpc_nst(WPC, V);      // energy stages in flight per warp
     constexpr int DPC_R = R;                      // rows between halo refreshes (= halo width)
     constexpr int DPC_SPR = DPC_R / DPC_S;        // stages per refresh
     constexpr int DPC_HL = DPC_R / DPC_V;         // halo lanes on each side of a warp
-    constexpr int DPC_OWW = dpc_oww(R);           // owned columns per warp
-    constexpr int DPC_LMAX = dpc_lmax(R, WPC);    // parents a CTA can report
+    constexpr int DPC_OWW = dpc_oww(R, V);        // owned columns per warp
+    constexpr int DPC_LMAX = dpc_lmax(R, WPC, V); // parents a CTA can report
     extern __shared__ __align__(128) unsigned char smraw[];
     // halo inboxes: [parity][warp][value], filled by the neighbouring warps
     __shared__ __align__(16) uint32_t inLc[2][DPC_WPC][DPC_R], inLl[2][DPC_WPC][DPC_R];
@@ -260,9 +279,19 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
     // always a stage's last row (ro = 15) and its last row is ro = 14.
     // Directions are kept per 16-row group G (rows 16G .. 16G+15) as one uint4
     // per 4 columns: component b holds rows 16G+4b .. 16G+4b+3, 2 bits each.
+    // With V = 2 a lane pair holds the 4 columns: the odd lane's bits sit 4
+    // higher, and the pair ORs its words together before the even lane stores.
     uint32_t wq0 = 0, wq1 = 0, wq2 = 0, wq3 = 0;   // the current group's block words
+    const int vsh = V == 2 ? 4 * (lane & 1) : 0;   // bit offset of the lane's columns
+    const bool quad_lane = V == 4 || (lane & 1) == 0;
     auto store_group = [&](int G) {
-        if (owner && cbase >= 0 && cbase < W0) {
+        if constexpr (V == 2) {
+            wq0 |= __shfl_xor_sync(0xffffffffu, wq0, 1);
+            wq1 |= __shfl_xor_sync(0xffffffffu, wq1, 1);
+            wq2 |= __shfl_xor_sync(0xffffffffu, wq2, 1);
+            wq3 |= __shfl_xor_sync(0xffffffffu, wq3, 1);
+        }
+        if (owner && quad_lane && cbase >= 0 && cbase < W0) {
             reinterpret_cast<uint4 *>(dirs)[(long)G * dstride + (cbase >> 2)] =
                 make_uint4(wq0, wq1, wq2, wq3);
             if (((16 * G) % RJ) == 0) Dfirst[(long)((16 * G) / RJ) * dstride + (cbase >> 2)] = wq0;
@@ -278,9 +307,18 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
         for (int ro = 0; ro < DPC_S; ++ro) {
             const int i = ibase + ro;
             if (!GUARD || i < H) {
-                const uint4 ev = *reinterpret_cast<const uint4 *>(rs + ro * DPC_WW);
-                const uint32_t e[DPC_V] = {valid[0] ? ev.x : BIG, valid[1] ? ev.y : BIG,
-                                           valid[2] ? ev.z : BIG, valid[3] ? ev.w : BIG};
+                uint32_t e[DPC_V];
+                if constexpr (V == 4) {
+                    const uint4 ev = *reinterpret_cast<const uint4 *>(rs + ro * DPC_WW);
+                    e[0] = valid[0] ? ev.x : BIG;
+                    e[1] = valid[1] ? ev.y : BIG;
+                    e[2] = valid[2] ? ev.z : BIG;
+                    e[3] = valid[3] ? ev.w : BIG;
+                } else {
+                    const uint2 ev = *reinterpret_cast<const uint2 *>(rs + ro * DPC_WW);
+                    e[0] = valid[0] ? ev.x : BIG;
+                    e[1] = valid[1] ? ev.y : BIG;
+                }
                 const uint32_t lc = __shfl_up_sync(0xffffffffu, cost[DPC_V - 1], 1);
                 const uint32_t ll = __shfl_up_sync(0xffffffffu, lab[DPC_V - 1], 1);
                 const uint32_t rc = __shfl_down_sync(0xffffffffu, cost[0], 1);
@@ -307,7 +345,7 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
                     for (int v = 0; v < DPC_V; ++v)
                         lab[v] = (lab[v] & 0xFFFF0000u) | ((uint32_t)(cbase + v) & 0xFFFFu);
                 }
-                dw |= dbyte << (8 * ((1 + ro) & 3));
+                dw |= dbyte << (8 * ((1 + ro) & 3) + vsh);
                 if (((1 + ro) & 3) == 3) {   // row i closes a 4-row block
                     if (ro == 2) wq0 = dw;
                     if (ro == 6) wq1 = dw;
@@ -343,15 +381,15 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
                 const int tg = g + 1, tr = tg / DPC_WPC, tw = tg % DPC_WPC;
                 const int o = (lane - (32 - 2 * DPC_HL)) * DPC_V;
                 const uint32_t mb = mapa_u32(smem_u32(&minbox[tw][par]), tr);
-                st_async_v4(mapa_u32(smem_u32(&inLc[par][tw][o]), tr), cost, mb);
-                st_async_v4(mapa_u32(smem_u32(&inLl[par][tw][o]), tr), lab, mb);
+                st_async_v(mapa_u32(smem_u32(&inLc[par][tw][o]), tr), cost, mb);
+                st_async_v(mapa_u32(smem_u32(&inLl[par][tw][o]), tr), lab, mb);
             }
             if (lane >= DPC_HL && lane < 2 * DPC_HL && g > 0) {
                 const int tg = g - 1, tr = tg / DPC_WPC, tw = tg % DPC_WPC;
                 const int o = (lane - DPC_HL) * DPC_V;
                 const uint32_t mb = mapa_u32(smem_u32(&minbox[tw][par]), tr);
-                st_async_v4(mapa_u32(smem_u32(&inRc[par][tw][o]), tr), cost, mb);
-                st_async_v4(mapa_u32(smem_u32(&inRl[par][tw][o]), tr), lab, mb);
+                st_async_v(mapa_u32(smem_u32(&inRc[par][tw][o]), tr), cost, mb);
+                st_async_v(mapa_u32(smem_u32(&inRl[par][tw][o]), tr), lab, mb);
             }
             mbar_wait_cluster(&minbox[w][par], (unsigned)(e >> 1) & 1u, ws.err, WAIT_NS);
             if (lane < DPC_HL) {
@@ -593,13 +631,13 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
     }
 }
 
-size_t dpc_smem(int W0, int H, int rj, int kcap, int C, int R, int WPC) {
+size_t dpc_smem(int W0, int H, int rj, int kcap, int C, int R, int WPC, int V) {
     const int nb = (H + rj - 1) / rj;
     const int jstride = (W0 + 7) & ~7;
     const int dstride = (((W0 + 3) / 4) + 3) & ~3;
-    const PostLayout PL(W0, C, kcap, nb, jstride, dstride, dpc_lmax(R, WPC));
+    const PostLayout PL(W0, C, kcap, nb, jstride, dstride, dpc_lmax(R, WPC, V));
     const WalkLayout WL(kcap, (nb + C - 1) / C);
-    size_t m = dpc_ring(WPC);
+    size_t m = dpc_ring(WPC, V);
     m = PL.end > m ? PL.end : m;
     m = WL.end > m ? WL.end : m;
     return m;
@@ -623,13 +661,13 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
     return fn;
 }
 
-// 3-D view of E ([nb*2 planes][H][pitch] int32) with 16-row x 128-column boxes.
-bool make_energy_map(const CarveWs &ws, int nb, CUtensorMap *m) {
+// 3-D view of E ([nb*2 planes][H][pitch] int32) with 16-row x 32V-column boxes.
+bool make_energy_map(const CarveWs &ws, int nb, int V, CUtensorMap *m) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
     if (!fn) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)ws.pitch, (cuuint64_t)ws.H, (cuuint64_t)nb * 2};
     const cuuint64_t strides[2] = {(cuuint64_t)ws.pitch * 4, (cuuint64_t)ws.plane * 4};
-    const cuuint32_t box[3] = {DPC_WW, DPC_S, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)dpc_ww(V), DPC_S, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, ws.E, dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -638,19 +676,20 @@ bool make_energy_map(const CarveWs &ws, int nb, CUtensorMap *m) {
 
 }  // namespace
 
-bool dpc_plan(int W0, int H, int R, int WPC, int *ctas, int *rj, size_t *smem) {
-    if ((R != 16 && R != 32) || (WPC != 4 && WPC != 8)) return false;
-    const int nwarps = (W0 + dpc_oww(R) - 1) / dpc_oww(R);
+bool dpc_plan(int W0, int H, int R, int WPC, int V, int *ctas, int *rj, size_t *smem) {
+    if ((R != 16 && R != 32) || (WPC != 4 && WPC != 8) || (V != 4 && V != 2)) return false;
+    if (V == 2 && R != 16) return false;
+    const int nwarps = (W0 + dpc_oww(R, V) - 1) / dpc_oww(R, V);
     const int C = (nwarps + WPC - 1) / WPC;
     if (C > 16) return false;
     // about four bands per CTA: the walk then takes ~rj rows per CTA
     int r = (H + 4 * C - 1) / (4 * C);
     r = ((r + 15) / 16) * 16;
     if (r < 16) r = 16;
-    size_t bytes = dpc_smem(W0, H, r, W0, C, R, WPC);
+    size_t bytes = dpc_smem(W0, H, r, W0, C, R, WPC, V);
     while (bytes > 220 * 1024 && r < H) {
         r += 16;
-        bytes = dpc_smem(W0, H, r, W0, C, R, WPC);
+        bytes = dpc_smem(W0, H, r, W0, C, R, WPC, V);
     }
     if (bytes > 220 * 1024) return false;
     // the walk stages at least one 16-row group of every band a CTA owns
@@ -665,15 +704,15 @@ bool dpc_plan(int W0, int H, int R, int WPC, int *ctas, int *rj, size_t *smem) {
 
 namespace {
 
-template <int R, int WPC>
+template <int R, int WPC, int V>
 bool dpc_available_t(int W0, int H) {
     int C = 0, rj = 0;
     size_t smem = 0;
-    if (!dpc_plan(W0, H, R, WPC, &C, &rj, &smem)) return false;
-    if (raise_dyn_smem((const void *)k_dpc<R, WPC>, smem) != cudaSuccess) return false;
-    if (C > 8 &&
-        cudaFuncSetAttribute(k_dpc<R, WPC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-            cudaSuccess)
+    if (!dpc_plan(W0, H, R, WPC, V, &C, &rj, &smem)) return false;
+    if (raise_dyn_smem((const void *)k_dpc<R, WPC, V>, smem) != cudaSuccess) return false;
+    if (C > 8 && cudaFuncSetAttribute(k_dpc<R, WPC, V>,
+                                      cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                      1) != cudaSuccess)
         return false;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C);
@@ -687,25 +726,26 @@ bool dpc_available_t(int W0, int H) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, k_dpc<R, WPC>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_dpc<R, WPC, V>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     return clusters > 0;
 }
 
-template <int R, int WPC>
+template <int R, int WPC, int V>
 cudaError_t launch_dpc_t(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                          cudaStream_t s) {
     int C = 0, rj = 0;
     size_t smem = 0;
-    if (!dpc_plan(ws.W0, ws.H, R, WPC, &C, &rj, &smem) || rj != ws.rj)
+    if (!dpc_plan(ws.W0, ws.H, R, WPC, V, &C, &rj, &smem) || rj != ws.rj)
         return cudaErrorInvalidValue;
-    smem = dpc_smem(ws.W0, ws.H, ws.rj, ws.kcap, C, R, WPC);
-    cudaError_t e = raise_dyn_smem((const void *)k_dpc<R, WPC>, smem);
+    smem = dpc_smem(ws.W0, ws.H, ws.rj, ws.kcap, C, R, WPC, V);
+    cudaError_t e = raise_dyn_smem((const void *)k_dpc<R, WPC, V>, smem);
     if (e != cudaSuccess) return e;
     if (C > 8) {
-        e = cudaFuncSetAttribute(k_dpc<R, WPC>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        e = cudaFuncSetAttribute(k_dpc<R, WPC, V>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
     cudaLaunchConfig_t cfg = {};
@@ -723,28 +763,75 @@ cudaError_t launch_dpc_t(const CarveWs &ws, int nb, int k, int16_t *seams, long 
     cfg.attrs = attr;
     cfg.numAttrs = 2;
     CUtensorMap tm;
-    if (!make_energy_map(ws, nb, &tm)) return cudaErrorInvalidValue;
-    e = cudaLaunchKernelEx(&cfg, k_dpc<R, WPC>, tm, ws, k, seams, seam_stride);
+    if (!make_energy_map(ws, nb, V, &tm)) return cudaErrorInvalidValue;
+    e = cudaLaunchKernelEx(&cfg, k_dpc<R, WPC, V>, tm, ws, k, seams, seam_stride);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 }  // namespace
 
-bool dpc_available(int W0, int H, int R, int WPC) {
+bool dpc_available_uncached(int W0, int H, int R, int WPC, int V) {
     if (!encode_tiled()) return false;
-    if (WPC == 4) return R == 16 ? dpc_available_t<16, 4>(W0, H) : R == 32 && dpc_available_t<32, 4>(W0, H);
-    if (WPC == 8) return R == 16 ? dpc_available_t<16, 8>(W0, H) : R == 32 && dpc_available_t<32, 8>(W0, H);
+    if (V == 2) {
+        if (R != 16) return false;
+        return WPC == 8 ? dpc_available_t<16, 8, 2>(W0, H)
+                        : WPC == 4 && dpc_available_t<16, 4, 2>(W0, H);
+    }
+    if (V != 4) return false;
+    if (WPC == 4) return R == 16 ? dpc_available_t<16, 4, 4>(W0, H) : R == 32 && dpc_available_t<32, 4, 4>(W0, H);
+    if (WPC == 8) return R == 16 ? dpc_available_t<16, 8, 4>(W0, H) : R == 32 && dpc_available_t<32, 8, 4>(W0, H);
+    return false;
+}
+
+// Availability depends only on the size, the layout and the device: cached.
+bool dpc_available(int W0, int H, int R, int WPC, int V) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, int, int>, bool> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    const auto key = std::make_tuple(dev, W0, H, R, WPC, V);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    const bool ok = dpc_available_uncached(W0, H, R, WPC, V);
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = ok;
+    return ok;
+}
+
+// The layout for a size: the requested one if this GPU can run it, else the
+// first that it can run of R16 x 4 warps x 2 columns a lane (the fastest
+// where its cluster fits: half the instructions a row of the 4-column
+// layouts), R32 x 4 x 4 and R16 x 4 x 4.  False: use the single-CTA DP.
+bool dpc_select(int W0, int H, CarveWs &ws, bool requested) {
+    if (requested && dpc_available(W0, H, ws.dpc_r, ws.dpc_wpc, ws.dpc_v)) return true;
+    static const int order[3][3] = {{16, 4, 2}, {32, 4, 4}, {16, 4, 4}};
+    for (const auto &o : order)
+        if (dpc_available(W0, H, o[0], o[1], o[2])) {
+            ws.dpc_r = o[0];
+            ws.dpc_wpc = o[1];
+            ws.dpc_v = o[2];
+            return true;
+        }
     return false;
 }
 
 cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                        cudaStream_t s) {
     const int wpc = ws.dpc_wpc == 8 ? 8 : 4;
-    if (ws.dpc_r == 16 && wpc == 4) return launch_dpc_t<16, 4>(ws, nb, k, seams, seam_stride, s);
-    if (ws.dpc_r == 32 && wpc == 4) return launch_dpc_t<32, 4>(ws, nb, k, seams, seam_stride, s);
-    if (ws.dpc_r == 16 && wpc == 8) return launch_dpc_t<16, 8>(ws, nb, k, seams, seam_stride, s);
-    if (ws.dpc_r == 32 && wpc == 8) return launch_dpc_t<32, 8>(ws, nb, k, seams, seam_stride, s);
+    const int v = ws.dpc_v == 2 ? 2 : 4;
+    if (v == 2) {
+        if (ws.dpc_r == 16 && wpc == 8) return launch_dpc_t<16, 8, 2>(ws, nb, k, seams, seam_stride, s);
+        if (ws.dpc_r == 16 && wpc == 4) return launch_dpc_t<16, 4, 2>(ws, nb, k, seams, seam_stride, s);
+        return cudaErrorInvalidValue;
+    }
+    if (ws.dpc_r == 16 && wpc == 4) return launch_dpc_t<16, 4, 4>(ws, nb, k, seams, seam_stride, s);
+    if (ws.dpc_r == 32 && wpc == 4) return launch_dpc_t<32, 4, 4>(ws, nb, k, seams, seam_stride, s);
+    if (ws.dpc_r == 16 && wpc == 8) return launch_dpc_t<16, 8, 4>(ws, nb, k, seams, seam_stride, s);
+    if (ws.dpc_r == 32 && wpc == 8) return launch_dpc_t<32, 8, 4>(ws, nb, k, seams, seam_stride, s);
     return cudaErrorInvalidValue;
 }
 

@@ -268,7 +268,6 @@ struct scpl_server_s {
     std::vector<std::unique_ptr<Wave>> waves;
     std::vector<int> pending_scan;
     std::vector<std::pair<long long, int>> completed;
-    std::map<std::pair<int, int>, bool> dpc_cache;
     PinnedPool pinned;
     std::string err;
     bool broken = false;
@@ -340,15 +339,6 @@ scpl_status free_group(Srv *s, Group &G);
 void add_reserved(Srv *s, long long delta) {
     s->reserved = (size_t)((long long)s->reserved + delta);
     s->peak = std::max(s->peak, s->reserved);
-}
-
-bool dpc_ok(Srv *s, int W, int H, int R, int WPC) {
-    auto key = std::make_pair(W, (H * 64 + R) * 16 + WPC);
-    auto it = s->dpc_cache.find(key);
-    if (it != s->dpc_cache.end()) return it->second;
-    bool ok = dpc_available(W, H, R, WPC);
-    s->dpc_cache[key] = ok;
-    return ok;
 }
 
 void count_launches(Srv *s, long long n) { s->st.kernel_launches += n; }
@@ -798,9 +788,11 @@ scpl_status setup_group(Srv *s, int gid) {
     ws.kcap = kcap;
     ws.dpc_r = 32;
     ws.dpc_wpc = 4;
+    ws.dpc_v = 4;
     bool use_dpc = true;
-    tuning_apply(G.H, G.W, ws, &use_dpc);   // sizes were tuned when their wave finished
-    G.dpc = use_dpc && dpc_ok(s, G.W, G.H, ws.dpc_r, ws.dpc_wpc);
+    // sizes were tuned when their wave finished
+    const bool tuned = tuning_apply(G.H, G.W, ws, &use_dpc);
+    G.dpc = use_dpc && dpc_select(G.W, G.H, ws, tuned);
     const size_t ws_bytes = carve_ws_assign(ws, nb, klog, G.dpc, nullptr);
     // frames of every item, the gather table and the frame-minor luma
     long long yfm_total = 0;

@@ -111,9 +111,6 @@ struct scpl_ctx {
     // host-memory entry point staging
     DevBuf in_frames, out_frames, seams_dev;
     DevBuf Yfm;
-    // cluster-DP availability per (W0, H, halo, warps) last checked
-    int dpc_W0 = -1, dpc_H = -1, dpc_R = -1, dpc_WPC = -1;
-    bool dpc_ok = false;
     bool autotune = false;
     unsigned long long wait_ns = SPIN_LIMIT_NS;   // bound of the scan's device-wide waits
     // host-memory path: copy stream, side stream for early gathers, the
@@ -290,24 +287,19 @@ scpl_status carve_ws(scpl_ctx *h, int nb, int H, int W0, int kcap, CarveWs &ws,
     if (dp_smem_bytes(W0, H, &bb) > 227 * 1024 - 4096 ||
         update_smem_bytes(W0, ws.kcap, &rb) > 200 * 1024)
         return fail(h, SCPL_EINVAL, "width %d exceeds the shared-memory limits", W0);
-    // the tuned choice for this size (halo depth or the single-CTA DP, update
-    // rows), measured first if autotuning is on; R = 32 otherwise
+    // the tuned choice for this size (cluster-DP layout or the single-CTA DP,
+    // update rows), measured first if autotuning is on; the default layout
+    // for the size otherwise
     ws.dpc_r = 32;
     ws.dpc_wpc = 4;
+    ws.dpc_v = 4;
     ws.up_rows = 0;
     bool use_dpc = true;
     if (h->autotune && !tuning_lookup(H, W0, nullptr))
         tune_class(H, W0, ws.kcap, h->stream, nullptr);   // on failure: the defaults
-    tuning_apply(H, W0, ws, &use_dpc);
-    // cluster DP tables (used when the GPU can co-schedule the cluster)
-    if (h->dpc_W0 != W0 || h->dpc_H != H || h->dpc_R != ws.dpc_r || h->dpc_WPC != ws.dpc_wpc) {
-        h->dpc_ok = dpc_available(W0, H, ws.dpc_r, ws.dpc_wpc);
-        h->dpc_W0 = W0;
-        h->dpc_H = H;
-        h->dpc_R = ws.dpc_r;
-        h->dpc_WPC = ws.dpc_wpc;
-    }
-    const bool dpc = use_dpc && h->dpc_ok;
+    const bool tuned = tuning_apply(H, W0, ws, &use_dpc);
+    // cluster DP (used when the GPU can co-schedule the cluster)
+    const bool dpc = use_dpc && dpc_select(W0, H, ws, tuned);
     const size_t bytes = carve_ws_assign(ws, nb, klog_stride, dpc, nullptr);
     SCPL_CUDA(h, h->cws.ensure(bytes));
     carve_ws_assign(ws, nb, klog_stride, dpc, h->cws.as<char>());
@@ -808,6 +800,9 @@ scpl_status scpl_tuning_set(const scpl_tuning *t) {
     if (!t || t->H < 1 || t->W < 1) return SCPL_EINVAL;
     if (t->dpc_halo != 0 && t->dpc_halo != 16 && t->dpc_halo != 32) return SCPL_EINVAL;
     if (t->dpc_halo != 0 && t->dpc_warps != 4 && t->dpc_warps != 8) return SCPL_EINVAL;
+    if (t->dpc_halo != 0 && t->dpc_lane_cols != 4 &&
+        !(t->dpc_lane_cols == 2 && t->dpc_halo == 16))
+        return SCPL_EINVAL;
     if (t->update_rows != 1 && t->update_rows != 2 && t->update_rows != 4) return SCPL_EINVAL;
     tuning_store(*t);
     return SCPL_OK;

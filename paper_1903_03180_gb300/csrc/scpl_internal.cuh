@@ -164,6 +164,7 @@ struct CarveWs {
     uint32_t *Dfirst;   // [nb][nbands][dstride] direction words of every band's first row
     int dpc_r;          // halo depth of the cluster DP (16 or 32); 0: the single-CTA DP
     int dpc_wpc;        // warps per cluster-DP CTA (4 or 8; 0 means 4)
+    int dpc_v;          // columns per lane of the cluster DP (4 or 2, 2 with R = 16; 0 means 4)
     int up_rows;        // rows per k_update CTA (1, 2 or 4); 0: the largest that fits
     int *err;           // device status word (bounded waits)
     const int32_t *E0;  // summed energy planes [H][W0] from the scan (see BufState::e0)
@@ -220,12 +221,17 @@ cudaError_t launch_energy_init(const CarveWs &ws, int nb, cudaStream_t s);
 cudaError_t launch_update(const CarveWs &ws, int nb, cudaStream_t s);
 cudaError_t launch_dp_select(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                              cudaStream_t s);
-// Cluster DP with halo depth R (16 or 32) and WPC warps per CTA (4 or 8):
-// plan (CTAs per cluster, band rows, shared memory) for a width and height;
-// returns false if this GPU cannot run it (then use launch_dp_select).
-// launch_dpc uses ws.dpc_r and ws.dpc_wpc.
-bool dpc_plan(int W0, int H, int R, int WPC, int *ctas, int *rj, size_t *smem);
-bool dpc_available(int W0, int H, int R, int WPC);
+// Cluster DP with halo depth R (16 or 32), WPC warps per CTA (4 or 8) and V
+// columns per lane (4, or 2 with R = 16): plan (CTAs per cluster, band rows,
+// shared memory) for a width and height; returns false if this GPU cannot
+// run it (then use launch_dp_select).  launch_dpc uses ws.dpc_r, ws.dpc_wpc
+// and ws.dpc_v.
+bool dpc_plan(int W0, int H, int R, int WPC, int V, int *ctas, int *rj, size_t *smem);
+bool dpc_available(int W0, int H, int R, int WPC, int V);
+// Sets ws.dpc_r / dpc_wpc / dpc_v to the requested layout (requested = the
+// fields hold a tuned choice) if available, else to the default for the size;
+// false if no cluster layout runs here.
+bool dpc_select(int W0, int H, CarveWs &ws, bool requested);
 cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                        cudaStream_t s);
 cudaError_t launch_identity_O(const CarveWs &ws, int nb, cudaStream_t s);
@@ -262,7 +268,8 @@ namespace scpl {
 bool tuning_lookup(int H, int W, scpl_tuning *out);
 void tuning_store(const scpl_tuning &t);
 void tuning_clear();
-void tuning_apply(int H, int W, CarveWs &ws, bool *use_dpc);
+// true if the table held a choice for (H, W) (then applied to ws)
+bool tuning_apply(int H, int W, CarveWs &ws, bool *use_dpc);
 scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out);
 
 // scpl_carve_batch's engine (engine.cu), owned by a handle.

@@ -1,9 +1,9 @@
 // Autotuning of the carving kernels per frame size (H, W).
 //
-// The choices are the cluster DP's halo depth R (16: 96 columns a warp with a
-// halo exchange every 16 rows; 32: 64 columns a warp, an exchange every 32
-// rows), the single-CTA DP as a third candidate, and the rows per k_update CTA
-// (1, 2 or 4).  The tuner measures every candidate with CUDA events on a
+// The choices are the cluster DP's layout (halo depth R, warps per CTA and
+// columns per lane: R32 x 4 warps, R16 x 4, R32 x 8, R16 x 8 with 4 columns a
+// lane; R16 x 4 and R16 x 8 with 2), the single-CTA DP, and the rows per
+// k_update CTA (1, 2 or 4).  The tuner measures every candidate with CUDA events on a
 // scratch workspace of one buffer of that size with synthetic energy and luma,
 // and records the fastest in a process-wide table.  Every choice computes the
 // same result (the DP and the update are exact), so only the time differs.
@@ -81,17 +81,19 @@ void tuning_clear() {
 }
 
 // Apply the recorded choice for (H, W), if any, to a workspace about to be
-// laid out: the DP's halo depth (or the single-CTA DP) and the update rows.
-void tuning_apply(int H, int W, CarveWs &ws, bool *use_dpc) {
+// laid out: the cluster-DP layout (or the single-CTA DP) and the update rows.
+bool tuning_apply(int H, int W, CarveWs &ws, bool *use_dpc) {
     scpl_tuning t;
-    if (!tuning_lookup(H, W, &t)) return;
+    if (!tuning_lookup(H, W, &t)) return false;
     if (t.dpc_halo == 0) {
         *use_dpc = false;
     } else {
         ws.dpc_r = t.dpc_halo;
         ws.dpc_wpc = t.dpc_warps;
+        ws.dpc_v = t.dpc_lane_cols;
     }
     ws.up_rows = t.update_rows;
+    return true;
 }
 
 scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
@@ -104,6 +106,7 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
     t.W = W;
     t.dpc_halo = 32;
     t.dpc_warps = 4;
+    t.dpc_lane_cols = 4;
     t.update_rows = 0;
     const int tp = 16;   // frames of the scratch buffer
     CarveWs ws{};
@@ -112,17 +115,20 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
     ws.kcap = kcap;
     ws.dpc_r = 32;
     ws.dpc_wpc = 4;
+    ws.dpc_v = 4;
     Scratch sc;
     // one slab big enough for the layout of every candidate (E, SD and O come
     // first and sit at the same offsets in all of them)
     size_t bytes = 0;
     for (int R : {16, 32, 0})
-        for (int wpc : {4, 8}) {
-            CarveWs c = ws;
-            c.dpc_r = R;
-            c.dpc_wpc = wpc;
-            bytes = std::max(bytes, carve_ws_assign(c, 1, remove, R != 0, nullptr));
-        }
+        for (int wpc : {4, 8})
+            for (int v : {4, 2}) {
+                CarveWs c = ws;
+                c.dpc_r = R;
+                c.dpc_wpc = wpc;
+                c.dpc_v = v;
+                bytes = std::max(bytes, carve_ws_assign(c, 1, remove, R != 0, nullptr));
+            }
     if (cudaMalloc(&sc.slab, bytes) != cudaSuccess) return SCPL_ENOMEM;
     const long yfm_bytes = (long)H * W * tp;
     if (cudaMalloc(&sc.yfm, (size_t)yfm_bytes) != cudaSuccess) return SCPL_ENOMEM;
@@ -152,13 +158,16 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
     };
     const int reps = 3;
     // time one DP candidate (the state is reset before every run)
-    auto time_dp = [&](int kind, int wpc) -> float {   // kind 16, 32: cluster halo; 0: one CTA
+    // kind 16, 32: cluster halo; 0: one CTA
+    auto time_dp = [&](int kind, int wpc, int lane_cols) -> float {
         CarveWs v = ws;
         v.dpc_r = kind;
         v.dpc_wpc = wpc;
-        if (kind != 0 && !dpc_available(W, H, kind, wpc)) return -1.0f;
+        v.dpc_v = lane_cols;
+        if (kind != 0 && !dpc_available(W, H, kind, wpc, lane_cols)) return -1.0f;
         carve_ws_assign(v, 1, remove, kind != 0, static_cast<char *>(sc.slab));
-        if (kind != 0 && (v.dpc_r != kind || v.dpc_wpc != wpc)) return -1.0f;
+        if (kind != 0 && (v.dpc_r != kind || v.dpc_wpc != wpc || v.dpc_v != lane_cols))
+            return -1.0f;
         if (kind == 0) {
             int bb = 0;
             if (dp_smem_bytes(W, H, &bb) > 227 * 1024 - 4096) return -1.0f;
@@ -180,15 +189,18 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
         }
         return best * 1000.0f;
     };
-    const int kinds[5] = {32, 16, 32, 16, 0}, warps[5] = {4, 4, 8, 8, 4};
-    for (int i = 0; i < 5; ++i) t.dp_us[i] = time_dp(kinds[i], warps[i]);
+    constexpr int NC = 7;
+    const int kinds[NC] = {32, 16, 32, 16, 0, 16, 16}, warps[NC] = {4, 4, 8, 8, 4, 4, 8};
+    const int cols[NC] = {4, 4, 4, 4, 4, 2, 2};
+    for (int i = 0; i < NC; ++i) t.dp_us[i] = time_dp(kinds[i], warps[i], cols[i]);
     // the fastest DP; then leave one pending iteration for the update timing
     float best = 1e30f;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < NC; ++i)
         if (t.dp_us[i] > 0.0f && t.dp_us[i] < best) {
             best = t.dp_us[i];
             t.dpc_halo = kinds[i];
             t.dpc_warps = warps[i];
+            t.dpc_lane_cols = cols[i];
         }
     scpl_status result = SCPL_OK;
     if (best >= 1e29f) {
@@ -197,6 +209,7 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
         CarveWs v = ws;   // any exact DP leaves the same pending iteration
         v.dpc_r = t.dp_us[0] > 0 ? 32 : 0;
         v.dpc_wpc = 4;
+        v.dpc_v = 4;
         carve_ws_assign(v, 1, remove, v.dpc_r != 0, static_cast<char *>(sc.slab));
         cudaError_t e = reset();
         if (e == cudaSuccess)

@@ -66,8 +66,9 @@ class ServerStats(ctypes.Structure):
 class Tuning(ctypes.Structure):
     """scpl_tuning: the kernel choices for one frame size and their times."""
     _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("dpc_halo", ctypes.c_int),
-                ("dpc_warps", ctypes.c_int), ("update_rows", ctypes.c_int),
-                ("dp_us", ctypes.c_float * 5), ("up_us", ctypes.c_float * 3)]
+                ("dpc_warps", ctypes.c_int), ("dpc_lane_cols", ctypes.c_int),
+                ("update_rows", ctypes.c_int),
+                ("dp_us", ctypes.c_float * 7), ("up_us", ctypes.c_float * 3)]
 
 
 _LL = ctypes.c_longlong
@@ -431,9 +432,10 @@ def make_job(frames, target_W: int, target_H: int, k: int, out, starts=None) -> 
 
 def _tuning_dict(t: Tuning) -> dict:
     return {"H": t.H, "W": t.W, "dpc_halo": t.dpc_halo, "dpc_warps": t.dpc_warps,
-            "update_rows": t.update_rows,
+            "dpc_lane_cols": t.dpc_lane_cols, "update_rows": t.update_rows,
             "dp_us": {"r32w4": t.dp_us[0], "r16w4": t.dp_us[1], "r32w8": t.dp_us[2],
-                      "r16w8": t.dp_us[3], "single": t.dp_us[4]},
+                      "r16w8": t.dp_us[3], "single": t.dp_us[4], "r16w4v2": t.dp_us[5],
+                      "r16w8v2": t.dp_us[6]},
             "update_us": {1: t.up_us[0], 2: t.up_us[1], 4: t.up_us[2]}}
 
 
@@ -444,12 +446,15 @@ def scpl_tune(h, H: int, W: int, k: int) -> dict:
     return _tuning_dict(t)
 
 
-def scpl_tuning_set(H: int, W: int, dpc_halo: int, update_rows: int, dpc_warps: int = 4):
+def scpl_tuning_set(H: int, W: int, dpc_halo: int, update_rows: int, dpc_warps: int = 4,
+                    dpc_lane_cols: int = 4):
     t = Tuning()
-    t.H, t.W, t.dpc_halo, t.update_rows, t.dpc_warps = H, W, dpc_halo, update_rows, dpc_warps
+    t.H, t.W, t.dpc_halo, t.update_rows = H, W, dpc_halo, update_rows
+    t.dpc_warps, t.dpc_lane_cols = dpc_warps, dpc_lane_cols
     st = load().scpl_tuning_set(ctypes.byref(t))
     if st != SCPL_OK:
-        raise SCPLError(st, "scpl_tuning_set: halo must be 0, 16 or 32 and rows 1, 2 or 4")
+        raise SCPLError(st, "scpl_tuning_set: halo must be 0, 16 or 32, warps 4 or 8, "
+                            "columns a lane 4 (or 2 with halo 16) and rows 1, 2 or 4")
 
 
 def scpl_tuning_get(H: int, W: int) -> dict | None:

@@ -92,5 +92,9 @@ def test_tuning_table_host_only(lib):
         scpl.scpl_tuning_set(10, 20, 8, 2)
     with pytest.raises(scpl.SCPLError):
         scpl.scpl_tuning_set(10, 20, 32, 3)
+    with pytest.raises(scpl.SCPLError):
+        scpl.scpl_tuning_set(10, 20, 32, 2, 4, 2)   # 2 columns a lane needs halo 16
+    scpl.scpl_tuning_set(10, 20, 16, 2, 8, 2)
+    assert scpl.scpl_tuning_get(10, 20)["dpc_lane_cols"] == 2
     scpl.scpl_tuning_clear()
     assert scpl.scpl_tuning_get(10, 20) is None

@@ -1,6 +1,7 @@
 """Autotuning: every kernel choice the tuner can make (cluster DP with halo
-depth 16 or 32, the single-CTA DP, 1/2/4 update rows) gives the oracle's
-result bit for bit; the tuner measures and records a choice."""
+depth 16 or 32, 4 or 8 warps a CTA, 4 or 2 columns a lane; the single-CTA DP;
+1/2/4 update rows) gives the oracle's result bit for bit; the tuner measures
+and records a choice."""
 from __future__ import annotations
 
 import numpy as np
@@ -30,14 +31,18 @@ def synth():
     return s
 
 
-CHOICES = [(32, 4, 4), (32, 1, 8), (16, 2, 4), (16, 4, 8), (0, 1, 4), (0, 4, 4)]
+# (halo, update rows, warps a CTA, columns a lane)
+CHOICES = [(32, 4, 4, 4), (32, 1, 8, 4), (16, 2, 4, 4), (16, 4, 8, 4), (16, 2, 8, 2),
+           (16, 1, 4, 2), (0, 1, 4, 4), (0, 4, 4, 4)]
 
 
-@pytest.mark.parametrize("halo,rows,warps", CHOICES)
+@pytest.mark.parametrize("halo,rows,warps,cols", CHOICES)
 @pytest.mark.parametrize("T,H,W,target,k,seed", [(6, 70, 300, 220, 16, 81),
-                                                 (4, 50, 1000, 900, 32, 82)])
-def test_every_choice_is_exact(orc, lib, synth, halo, rows, warps, T, H, W, target, k, seed):
-    lib.scpl_tuning_set(H, W, halo, rows, warps)
+                                                 (4, 50, 1000, 900, 32, 82),
+                                                 (3, 37, 131, 100, 8, 83)])
+def test_every_choice_is_exact(orc, lib, synth, halo, rows, warps, cols, T, H, W, target, k,
+                               seed):
+    lib.scpl_tuning_set(H, W, halo, rows, warps, cols)
     f = synth.clip(T, H, W, seed=seed, cuts=(2, 3))
     ref_out, ref_starts, ref_seams = orc.carve(f, target, k)
     r = lib.Retargeter()
@@ -54,7 +59,9 @@ def test_tune_measures_and_records(lib):
     h = lib.scpl_create()
     t = lib.scpl_tune(h, 1080, 1920, 32)
     lib.scpl_destroy(h)
-    assert all(t["dp_us"][k] > 0 for k in ("r32w4", "r16w4", "r32w8", "r16w8"))
+    assert all(t["dp_us"][k] > 0 for k in ("r32w4", "r16w4", "r32w8", "r16w8", "r16w4v2",
+                                           "r16w8v2"))
+    assert t["dpc_lane_cols"] in (2, 4)
     assert all(v > 0 for v in t["update_us"].values())
     assert t["dpc_halo"] in (0, 16, 32) and t["update_rows"] in (1, 2, 4)
     rec = lib.scpl_tuning_get(1080, 1920)
