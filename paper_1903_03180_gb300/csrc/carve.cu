@@ -160,15 +160,21 @@ __global__ void __launch_bounds__(EN_QT) k_energy_init(CarveWs ws) {
 // ---------------------------------------------------------------------------
 // k_update: grid (ceil(H/RB), nb), UP_THREADS threads, dynamic shared memory
 // (see update_smem_bytes).
+//   0. One thread stages the CTA's rows into shared memory with bulk copies:
+//      the origin map of rows i0-1 .. i0+RB and the summed energy of rows
+//      i0 .. i0+RB-1, at the committed width.
 //   1. O and E are compacted: each thread gathers 8 consecutive output pixels
-//      (all loads first) and writes them as vectors.
+//      from the staged rows and writes them as vectors.
 //   2. The changed pixels of the rows are marked in a bitmap and listed.
 //   3. Each changed pixel's summed gradient is recomputed from the frame-minor
-//      luma copy written by k_energy_init.
+//      luma copy written by k_energy_init (its neighbours' origins come from
+//      the staged rows).
+constexpr unsigned long long UP_WAIT_NS = 2000000000ull;   // bound of the staging wait
 
 __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int s_cnt;
+    __shared__ __align__(8) uint64_t s_mbar;
     pdl_launch_dependents();
     pdl_wait();   // the DP's selection and removal lists
     const int b = blockIdx.y;
@@ -191,7 +197,29 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
     uint32_t *bm = reinterpret_cast<uint32_t *>(smraw + off);   // [RB][nwords0]
     off += (size_t)RB * nwords0 * 4;
     uint32_t *list = reinterpret_cast<uint32_t *>(smraw + off);  // [list_cap] (row << 16 | old column)
+    off = (off + (size_t)list_cap * 4 + 15) & ~(size_t)15;
+    const int W8 = (ws.W0 + 7) & ~7, W4 = (ws.W0 + 3) & ~3;     // staged row strides
+    uint16_t *Os = reinterpret_cast<uint16_t *>(smraw + off);    // [RB+2][W8] O of rows i0-1..
+    off += (size_t)(RB + 2) * W8 * 2;
+    int32_t *Es = reinterpret_cast<int32_t *>(smraw + off);      // [RB][W4] E of rows i0..
     const uint16_t *rem = ws.rem + (long)b * H * kcap;
+    const uint16_t *__restrict__ Oin = ws.O + ((long)b * 2 + s_in) * plane;
+    const int32_t *__restrict__ Ein = ws.E + ((long)b * 2 + s_in) * plane;
+    if (tid == 0) {
+        // rows start 64-byte aligned (pitch is a multiple of 32) and the
+        // rounded widths stay within the pitch
+        const unsigned obytes = (unsigned)((Wc + 7) & ~7) * 2u;
+        const unsigned ebytes = (unsigned)((Wc + 3) & ~3) * 4u;
+        mbar_init(&s_mbar, 1);
+        fence_mbar_init();
+        mbar_expect_tx(&s_mbar, (unsigned)(nrows + 2) * obytes + (need_e ? (unsigned)nrows * ebytes : 0u));
+        for (int r = 0; r < nrows + 2; ++r)
+            bulk_g2s(Os + (size_t)r * W8, Oin + (long)clampi(i0 + r - 1, 0, H - 1) * pitch, obytes,
+                     &s_mbar);
+        if (need_e)
+            for (int r = 0; r < nrows; ++r)
+                bulk_g2s(Es + (size_t)r * W4, Ein + (long)(i0 + r) * pitch, ebytes, &s_mbar);
+    }
 
     for (int x = tid; x < (RB + 2) * keff; x += UP_THREADS) {
         const int r = x / keff, m = x - r * keff;
@@ -200,12 +228,11 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
     }
     for (int x = tid; x < nrows * nwords0; x += UP_THREADS) bm[x] = 0;
     if (tid == 0) s_cnt = 0;
-    __syncthreads();
+    __syncthreads();   // the barrier is initialised before anyone waits on it
+    mbar_wait(&s_mbar, 0u, ws.err, UP_WAIT_NS);
 
     // 1. compaction of the origin map and of the summed energy
-    const uint16_t *__restrict__ Oin = ws.O + ((long)b * 2 + s_in) * plane;
     uint16_t *__restrict__ Oout = ws.O + ((long)b * 2 + s_out) * plane;
-    const int32_t *__restrict__ Ein = ws.E + ((long)b * 2 + s_in) * plane;
     int32_t *__restrict__ Eout = ws.E + ((long)b * 2 + s_out) * plane;
     const int chunks = (Wn + 7) >> 3;
     for (int x = tid; x < nrows * chunks; x += UP_THREADS) {
@@ -230,11 +257,13 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
         }
         uint16_t ov[8];
         int ev[8];
+        const uint16_t *orow = Os + (size_t)(r + 1) * W8;
+        const int32_t *erow = Es + (size_t)r * W4;
 #pragma unroll
-        for (int j = 0; j < 8; ++j) ov[j] = Oin[roff + src[j]];
+        for (int j = 0; j < 8; ++j) ov[j] = orow[src[j]];
         if (need_e) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) ev[j] = __ldg(Ein + roff + src[j]);   // read-only here
+            for (int j = 0; j < 8; ++j) ev[j] = erow[src[j]];
         }
         if (p0 + 8 <= Wn) {
             uint4 o4;
@@ -346,7 +375,7 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
             }
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const int o = Oin[(long)gi * pitch + src[c]];
+                const int o = Os[(size_t)(r + a) * W8 + src[c]];
                 if (a == 1 && c == 1) ocenter = o;
                 nb[a][c] = reinterpret_cast<const uint4 *>(yfm + ((long)gi * ws.W0 + o) * tp);
             }
@@ -758,26 +787,23 @@ size_t dp_smem_bytes(int W0, int H, int *band_blocks) {
     return fixed + 2 * (size_t)bb * dstride * 4;
 }
 
-// Dynamic shared memory of a k_update CTA of `rb` rows.
+// Dynamic shared memory of a k_update CTA of `rb` rows: removal lists, the
+// changed-pixel bitmap and list, and the staged origin and energy rows.
 size_t update_smem_bytes_rows(int W0, int kcap, int rb) {
     const size_t per_row_list = (size_t)(W0 < 15 * kcap ? W0 : 15 * kcap);
     const size_t nwords0 = (size_t)(W0 + 31) / 32;
-    return (((size_t)(rb + 2) * kcap * 2 + 15) & ~(size_t)15) + (size_t)rb * nwords0 * 4 +
-           (size_t)rb * per_row_list * 4;
+    size_t off = (((size_t)(rb + 2) * kcap * 2 + 15) & ~(size_t)15) + (size_t)rb * nwords0 * 4;
+    off = (off + (size_t)rb * per_row_list * 4 + 15) & ~(size_t)15;
+    const size_t w8 = (size_t)(W0 + 7) & ~(size_t)7, w4 = (size_t)(W0 + 3) & ~(size_t)3;
+    return off + (size_t)(rb + 2) * w8 * 2 + (size_t)rb * w4 * 4;
 }
 
-// Rows per k_update CTA and its dynamic shared memory.
+// Rows per k_update CTA (the most, up to 4, that keep three CTAs on an SM;
+// at least 1) and its dynamic shared memory.
 size_t update_smem_bytes(int W0, int kcap, int *rows) {
-    const size_t per_row_list = (size_t)(W0 < 15 * kcap ? W0 : 15 * kcap);
-    const size_t nwords0 = (size_t)(W0 + 31) / 32;
     int rb = 4;
-    size_t bytes = 0;
-    for (; rb >= 1; --rb) {
-        bytes = (((size_t)(rb + 2) * kcap * 2 + 15) & ~(size_t)15) + (size_t)rb * nwords0 * 4 +
-                (size_t)rb * per_row_list * 4;
-        if (bytes <= 200 * 1024) break;
-    }
-    if (rb < 1) rb = 1;
+    size_t bytes = update_smem_bytes_rows(W0, kcap, rb);
+    while (rb > 1 && bytes > 72 * 1024) bytes = update_smem_bytes_rows(W0, kcap, --rb);
     *rows = rb;
     return bytes;
 }

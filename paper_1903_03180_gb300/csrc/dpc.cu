@@ -438,6 +438,15 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
 
     // ---- Eq. 6: per-parent minima -------------------------------------------------
     const PostLayout PL(W0, C, ws.kcap, NB, ws.jstride, dstride, DPC_LMAX);
+    // CTA 0 fetches every band's anchors and first-row directions for the
+    // band trace now, so the copy overlaps the parents' minima
+    if (crank == 0 && tid == 0) {
+        const unsigned jbytes = (unsigned)NB * ws.jstride * 2u;
+        const unsigned dbytes = (unsigned)NB * dstride * 4u;
+        mbar_expect_tx(&mbar[0], jbytes + dbytes);
+        bulk_g2s(smraw + PL.js, J, jbytes, &mbar[0]);
+        bulk_g2s(smraw + PL.ds, Dfirst, dbytes, &mbar[0]);
+    }
     uint64_t *segmin = reinterpret_cast<uint64_t *>(smraw + PL.segmin);
     uint64_t *lkeys = reinterpret_cast<uint64_t *>(smraw + PL.lkeys);
     uint32_t *llabs = reinterpret_cast<uint32_t *>(smraw + PL.llabs);
@@ -488,13 +497,6 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
         int *pos = reinterpret_cast<int *>(smraw + PL.pos);
         uint16_t *Js = reinterpret_cast<uint16_t *>(smraw + PL.js);
         uint32_t *Ds = reinterpret_cast<uint32_t *>(smraw + PL.ds);
-        const unsigned jbytes = (unsigned)NB * ws.jstride * 2u;
-        const unsigned dbytes = (unsigned)NB * dstride * 4u;
-        if (tid == 0) {
-            mbar_expect_tx(&mbar[0], jbytes + dbytes);
-            bulk_g2s(Js, J, jbytes, &mbar[0]);
-            bulk_g2s(Ds, Dfirst, dbytes, &mbar[0]);
-        }
         for (int r = 1; r < C; ++r) {
             const int n = lcnt[r];
             for (int x = tid; x < n; x += NT)
