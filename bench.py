@@ -42,6 +42,11 @@ WORKLOADS = {
 }
 SEEDS = {"clip_1080p_300f": 0x5C9 ^ 3, "clip_360p_64f": 0x5C9 ^ 2, "still_240p": 0x5C9 ^ 1}
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one ncu capture of k_dpc<16,4,2>
+# (16.7 MB for 2 buffers x 1080 rows x ~1900 columns, profiles/k_dpc_clip_1080p_128f.md)
+# per carved pixel; the roofline's traffic scales it by the pixels a launch carves.
+DP_DRAM_BYTES_PER_PX = 4.1
+
 
 def make_frames(name: str, rank: int = 0, frames: int = 0) -> np.ndarray:
     from paper_1903_03180_gb300 import synth
@@ -388,8 +393,13 @@ def run_native(args) -> None:
     avg_ms = d["ms"] / max(d["launches"], 1)
     bytes_per_launch = d["bytes"] / max(d["launches"], 1)
     achieved = bytes_per_launch / (avg_ms / 1000.0) / 1e9
+    traffic = None
+    if dom == "k_dp":   # DRAM bytes per carved pixel of one ncu capture of k_dpc, scaled
+        # carved_px covers the last clip; the launches cover every profiled step
+        traffic = round(DP_DRAM_BYTES_PER_PX * stats["carved_px"] * args.steps /
+                        max(d["launches"], 1))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": None,
+                "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4), "traffic": traffic,
                 "kernel": dom, "peak_source": pk["source"],
                 "avg_launch_ms": round(avg_ms, 4),
                 "alg_bytes_per_launch": round(bytes_per_launch),

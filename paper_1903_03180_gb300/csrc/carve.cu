@@ -163,12 +163,13 @@ __global__ void __launch_bounds__(EN_QT) k_energy_init(CarveWs ws) {
 //   0. One thread stages the CTA's rows into shared memory with bulk copies:
 //      the origin map of rows i0-1 .. i0+RB and the summed energy of rows
 //      i0 .. i0+RB-1, at the committed width.
+//   2. Meanwhile the changed pixels of the rows are marked in a bitmap and
+//      listed.
 //   1. O and E are compacted: each thread gathers 8 consecutive output pixels
 //      from the staged rows and writes them as vectors.
-//   2. The changed pixels of the rows are marked in a bitmap and listed.
 //   3. Each changed pixel's summed gradient is recomputed from the frame-minor
 //      luma copy written by k_energy_init (its neighbours' origins come from
-//      the staged rows).
+//      the staged rows), 16 frames per work item.
 constexpr unsigned long long UP_WAIT_NS = 2000000000ull;   // bound of the staging wait
 
 __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
@@ -202,6 +203,8 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
     uint16_t *Os = reinterpret_cast<uint16_t *>(smraw + off);    // [RB+2][W8] O of rows i0-1..
     off += (size_t)(RB + 2) * W8 * 2;
     int32_t *Es = reinterpret_cast<int32_t *>(smraw + off);      // [RB][W4] E of rows i0..
+    off += (size_t)RB * W4 * 4;
+    int *acc = reinterpret_cast<int *>(smraw + off);             // [list_cap] recomputed sums
     const uint16_t *rem = ws.rem + (long)b * H * kcap;
     const uint16_t *__restrict__ Oin = ws.O + ((long)b * 2 + s_in) * plane;
     const int32_t *__restrict__ Ein = ws.E + ((long)b * 2 + s_in) * plane;
@@ -228,7 +231,61 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
     }
     for (int x = tid; x < nrows * nwords0; x += UP_THREADS) bm[x] = 0;
     if (tid == 0) s_cnt = 0;
-    __syncthreads();   // the barrier is initialised before anyone waits on it
+    __syncthreads();   // lists loaded; the staging barrier is initialised
+
+    // 2. while the rows arrive: old columns within 2 of a removed pixel in
+    //    rows i-1, i, i+1, marked in a bitmap and listed
+    int cnt = 0;
+    if (need_e) {
+        const int per_row = 15 * keff;
+        for (int x = tid; x < nrows * per_row; x += UP_THREADS) {
+            const int r = x / per_row, y = x - r * per_row;
+            const int a = y / (5 * keff), z = y - a * 5 * keff;
+            const int mm = z / 5, d = z - mm * 5 - 2;
+            const int c = (int)rl[(r + a) * kcap + mm] + d;
+            if (c >= 0 && c < Wc) atomicOr(&bm[r * nwords0 + (c >> 5)], 1u << (c & 31));
+        }
+        __syncthreads();
+        for (int x = tid; x < nrows * keff; x += UP_THREADS) {
+            const int r = x / keff, mm = x - r * keff;
+            const int c = rl[(r + 1) * kcap + mm];
+            atomicAnd(&bm[r * nwords0 + (c >> 5)], ~(1u << (c & 31)));
+        }
+        __syncthreads();
+        const int nwords = (Wc + 31) >> 5;
+        const int lane = tid & 31;
+        // every warp reserves room for all its words' bits with one atomic
+        for (int x0 = tid - lane; x0 < nrows * nwords; x0 += UP_THREADS) {
+            const int x = x0 + lane;
+            uint32_t bits = 0;
+            int r = 0, wd = 0;
+            if (x < nrows * nwords) {
+                r = x / nwords;
+                wd = x - r * nwords;
+                bits = bm[r * nwords0 + wd];
+            }
+            const int n = __popc(bits);
+            int pre = n;   // inclusive prefix over the warp
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, pre, o);
+                if (lane >= o) pre += y;
+            }
+            int base = 0;
+            if (lane == 31) base = atomicAdd(&s_cnt, pre);
+            base = __shfl_sync(0xffffffffu, base, 31);
+            int pos = base + pre - n;
+            while (bits) {
+                const int bit = __ffs(bits) - 1;
+                bits &= bits - 1;
+                list[pos++] = ((uint32_t)r << 16) | (uint32_t)(wd * 32 + bit);
+            }
+        }
+        __syncthreads();
+        cnt = s_cnt;
+        for (int e = tid; e < cnt; e += UP_THREADS) acc[e] = 0;
+        if (tid == 0 && ws.dirty_count) atomicAdd(ws.dirty_count + b, (unsigned long long)cnt);
+    }
     mbar_wait(&s_mbar, 0u, ws.err, UP_WAIT_NS);
 
     // 1. compaction of the origin map and of the summed energy
@@ -288,68 +345,22 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
         }
     }
     if (!need_e) return;
-
-    // 2. old columns within 2 of a removed pixel in rows i-1, i, i+1
-    const int per_row = 15 * keff;
-    for (int x = tid; x < nrows * per_row; x += UP_THREADS) {
-        const int r = x / per_row, y = x - r * per_row;
-        const int a = y / (5 * keff), z = y - a * 5 * keff;
-        const int mm = z / 5, d = z - mm * 5 - 2;
-        const int c = (int)rl[(r + a) * kcap + mm] + d;
-        if (c >= 0 && c < Wc) atomicOr(&bm[r * nwords0 + (c >> 5)], 1u << (c & 31));
-    }
-    __syncthreads();
-    for (int x = tid; x < nrows * keff; x += UP_THREADS) {
-        const int r = x / keff, mm = x - r * keff;
-        const int c = rl[(r + 1) * kcap + mm];
-        atomicAnd(&bm[r * nwords0 + (c >> 5)], ~(1u << (c & 31)));
-    }
-    __syncthreads();
-    const int nwords = (Wc + 31) >> 5;
-    const int lane = tid & 31;
-    // every warp reserves room for all its words' bits with one atomic
-    for (int x0 = tid - lane; x0 < nrows * nwords; x0 += UP_THREADS) {
-        const int x = x0 + lane;
-        uint32_t bits = 0;
-        int r = 0, wd = 0;
-        if (x < nrows * nwords) {
-            r = x / nwords;
-            wd = x - r * nwords;
-            bits = bm[r * nwords0 + wd];
-        }
-        const int n = __popc(bits);
-        int pre = n;   // inclusive prefix over the warp
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, pre, o);
-            if (lane >= o) pre += y;
-        }
-        int base = 0;
-        if (lane == 31) base = atomicAdd(&s_cnt, pre);
-        base = __shfl_sync(0xffffffffu, base, 31);
-        int pos = base + pre - n;
-        while (bits) {
-            const int bit = __ffs(bits) - 1;
-            bits &= bits - 1;
-            list[pos++] = ((uint32_t)r << 16) | (uint32_t)(wd * 32 + bit);
-        }
-    }
-    __syncthreads();
-    const int cnt = s_cnt;
-    if (tid == 0 && ws.dirty_count) atomicAdd(ws.dirty_count + b, (unsigned long long)cnt);
+    __syncthreads();   // the compacted energy is written before the changed pixels
 
     // 3. exact recompute of the changed pixels: every frame's Sobel gradient
-    //    from the frame-minor luma copy, 16 frames per vector load, bytes
-    //    widened to 16-bit lanes and |P - N| taken with packed max/min
+    //    from the frame-minor luma copy, one work item per changed pixel and
+    //    16-frame group (one vector load per neighbour), bytes widened to
+    //    16-bit lanes and |P - N| taken with packed max/min; the groups' sums
+    //    meet in shared memory
     const int32_t *SDo = ws.SD + (long)b * plane;
     const uint8_t *yfm = ws.Yfm + st.yfm;
-    const int tp = st.tp;
-    for (int e = tid; e < cnt; e += UP_THREADS) {
+    const int tp = st.tp, ng = tp >> 4;
+    for (int x = tid; x < cnt * ng; x += UP_THREADS) {
+        const int e = x / ng, f = x - e * ng;
         const int r = (int)(list[e] >> 16), q = (int)(list[e] & 0xFFFFu);
         const int i = i0 + r;
         const int p = q - count_less(rl + (r + 1) * kcap, keff, q);
         const uint4 *nb[3][3];
-        int ocenter = 0;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             const int gi = clampi(i + a - 1, 0, H - 1);
@@ -376,39 +387,42 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const int o = Os[(size_t)(r + a) * W8 + src[c]];
-                if (a == 1 && c == 1) ocenter = o;
                 nb[a][c] = reinterpret_cast<const uint4 *>(yfm + ((long)gi * ws.W0 + o) * tp);
             }
         }
-        int acc = 0;
-        for (int f = 0; f < tp / 16; ++f) {
-            const uint4 v00 = __ldg(nb[0][0] + f), v01 = __ldg(nb[0][1] + f), v02 = __ldg(nb[0][2] + f);
-            const uint4 v10 = __ldg(nb[1][0] + f), v12 = __ldg(nb[1][2] + f);
-            const uint4 v20 = __ldg(nb[2][0] + f), v21 = __ldg(nb[2][1] + f), v22 = __ldg(nb[2][2] + f);
-            const uint32_t w00[4] = {v00.x, v00.y, v00.z, v00.w}, w01[4] = {v01.x, v01.y, v01.z, v01.w};
-            const uint32_t w02[4] = {v02.x, v02.y, v02.z, v02.w}, w10[4] = {v10.x, v10.y, v10.z, v10.w};
-            const uint32_t w12[4] = {v12.x, v12.y, v12.z, v12.w}, w20[4] = {v20.x, v20.y, v20.z, v20.w};
-            const uint32_t w21[4] = {v21.x, v21.y, v21.z, v21.w}, w22[4] = {v22.x, v22.y, v22.z, v22.w};
-            uint32_t packed = 0;   // two 16-bit lane sums, at most 8 * 2040 each
+        const uint4 v00 = __ldg(nb[0][0] + f), v01 = __ldg(nb[0][1] + f), v02 = __ldg(nb[0][2] + f);
+        const uint4 v10 = __ldg(nb[1][0] + f), v12 = __ldg(nb[1][2] + f);
+        const uint4 v20 = __ldg(nb[2][0] + f), v21 = __ldg(nb[2][1] + f), v22 = __ldg(nb[2][2] + f);
+        const uint32_t w00[4] = {v00.x, v00.y, v00.z, v00.w}, w01[4] = {v01.x, v01.y, v01.z, v01.w};
+        const uint32_t w02[4] = {v02.x, v02.y, v02.z, v02.w}, w10[4] = {v10.x, v10.y, v10.z, v10.w};
+        const uint32_t w12[4] = {v12.x, v12.y, v12.z, v12.w}, w20[4] = {v20.x, v20.y, v20.z, v20.w};
+        const uint32_t w21[4] = {v21.x, v21.y, v21.z, v21.w}, w22[4] = {v22.x, v22.y, v22.z, v22.w};
+        uint32_t packed = 0;   // two 16-bit lane sums, at most 8 * 2040 each
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < 4; ++k) {
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const uint32_t sel = h ? 0x4342u : 0x4140u;   // bytes (2,3) or (0,1) -> u16 lanes
-                    const uint32_t a00 = __byte_perm(w00[k], 0, sel), a01 = __byte_perm(w01[k], 0, sel);
-                    const uint32_t a02 = __byte_perm(w02[k], 0, sel), a10 = __byte_perm(w10[k], 0, sel);
-                    const uint32_t a12 = __byte_perm(w12[k], 0, sel), a20 = __byte_perm(w20[k], 0, sel);
-                    const uint32_t a21 = __byte_perm(w21[k], 0, sel), a22 = __byte_perm(w22[k], 0, sel);
-                    const uint32_t gxp = a02 + 2u * a12 + a22, gxn = a00 + 2u * a10 + a20;
-                    const uint32_t gyp = a20 + 2u * a21 + a22, gyn = a00 + 2u * a01 + a02;
-                    const uint32_t gx = __vimax3_u16x2(gxp, gxn, 0u) - __vimin3_u16x2(gxp, gxn, 0xFFFFFFFFu);
-                    const uint32_t gy = __vimax3_u16x2(gyp, gyn, 0u) - __vimin3_u16x2(gyp, gyn, 0xFFFFFFFFu);
-                    packed += gx + gy;
-                }
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t sel = h ? 0x4342u : 0x4140u;   // bytes (2,3) or (0,1) -> u16 lanes
+                const uint32_t a00 = __byte_perm(w00[k], 0, sel), a01 = __byte_perm(w01[k], 0, sel);
+                const uint32_t a02 = __byte_perm(w02[k], 0, sel), a10 = __byte_perm(w10[k], 0, sel);
+                const uint32_t a12 = __byte_perm(w12[k], 0, sel), a20 = __byte_perm(w20[k], 0, sel);
+                const uint32_t a21 = __byte_perm(w21[k], 0, sel), a22 = __byte_perm(w22[k], 0, sel);
+                const uint32_t gxp = a02 + 2u * a12 + a22, gxn = a00 + 2u * a10 + a20;
+                const uint32_t gyp = a20 + 2u * a21 + a22, gyn = a00 + 2u * a01 + a02;
+                const uint32_t gx = __vimax3_u16x2(gxp, gxn, 0u) - __vimin3_u16x2(gxp, gxn, 0xFFFFFFFFu);
+                const uint32_t gy = __vimax3_u16x2(gyp, gyn, 0u) - __vimin3_u16x2(gyp, gyn, 0xFFFFFFFFu);
+                packed += gx + gy;
             }
-            acc += (int)(packed & 0xFFFFu) + (int)(packed >> 16);
         }
-        Eout[(long)i * pitch + p] = ws.wg * acc + SDo[(long)i * pitch + ocenter];
+        atomicAdd(&acc[e], (int)(packed & 0xFFFFu) + (int)(packed >> 16));
+    }
+    __syncthreads();
+    for (int e = tid; e < cnt; e += UP_THREADS) {
+        const int r = (int)(list[e] >> 16), q = (int)(list[e] & 0xFFFFu);
+        const int i = i0 + r;
+        const int p = q - count_less(rl + (r + 1) * kcap, keff, q);
+        const int ocenter = Os[(size_t)(r + 1) * W8 + q];   // the pixel's own origin
+        Eout[(long)i * pitch + p] = ws.wg * acc[e] + SDo[(long)i * pitch + ocenter];
     }
 }
 
@@ -788,22 +802,25 @@ size_t dp_smem_bytes(int W0, int H, int *band_blocks) {
 }
 
 // Dynamic shared memory of a k_update CTA of `rb` rows: removal lists, the
-// changed-pixel bitmap and list, and the staged origin and energy rows.
+// changed-pixel bitmap and list, the staged origin and energy rows, and the
+// recomputed sums of the listed pixels.
 size_t update_smem_bytes_rows(int W0, int kcap, int rb) {
     const size_t per_row_list = (size_t)(W0 < 15 * kcap ? W0 : 15 * kcap);
     const size_t nwords0 = (size_t)(W0 + 31) / 32;
     size_t off = (((size_t)(rb + 2) * kcap * 2 + 15) & ~(size_t)15) + (size_t)rb * nwords0 * 4;
     off = (off + (size_t)rb * per_row_list * 4 + 15) & ~(size_t)15;
     const size_t w8 = (size_t)(W0 + 7) & ~(size_t)7, w4 = (size_t)(W0 + 3) & ~(size_t)3;
-    return off + (size_t)(rb + 2) * w8 * 2 + (size_t)rb * w4 * 4;
+    return off + (size_t)(rb + 2) * w8 * 2 + (size_t)rb * w4 * 4 + (size_t)rb * per_row_list * 4;
 }
 
-// Rows per k_update CTA (the most, up to 4, that keep three CTAs on an SM;
-// at least 1) and its dynamic shared memory.
+// Rows per k_update CTA (the most, up to 4, that keep five CTAs on an SM,
+// as many as its registers allow, so that the recompute's gathers keep the
+// L1 that shared memory would take; at least 1) and its dynamic shared
+// memory.
 size_t update_smem_bytes(int W0, int kcap, int *rows) {
     int rb = 4;
     size_t bytes = update_smem_bytes_rows(W0, kcap, rb);
-    while (rb > 1 && bytes > 72 * 1024) bytes = update_smem_bytes_rows(W0, kcap, --rb);
+    while (rb > 1 && bytes > 44 * 1024) bytes = update_smem_bytes_rows(W0, kcap, --rb);
     *rows = rb;
     return bytes;
 }

@@ -460,6 +460,10 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
             }
             if (max_rem == 0) break;
             iters = (max_rem + min_k - 1) / min_k;
+            // host path: look again after a few iterations, so that buffers
+            // that finish early are gathered and copied out while the others
+            // carve on
+            if (host_out) iters = std::min(iters, 8);
         }
     }
     if (host_out) {

@@ -1,5 +1,9 @@
 // Autotuning of the carving kernels per frame size (H, W).
 //
+// Every candidate is timed on a scratch workspace of four buffers carved in
+// one launch, the regime of a clip's first iterations and of batches: a
+// choice that wins on one buffer alone can lose once several run at once.
+//
 // The choices are the cluster DP's layout (halo depth R, warps per CTA and
 // columns per lane: R32 x 4 warps, R16 x 4, R32 x 8, R16 x 8 with 4 columns a
 // lane; R16 x 4 and R16 x 8 with 2), the single-CTA DP, and the rows per
@@ -108,7 +112,8 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
     t.dpc_warps = 4;
     t.dpc_lane_cols = 4;
     t.update_rows = 0;
-    const int tp = 16;   // frames of the scratch buffer
+    const int tp = 16;   // frames of each scratch buffer
+    constexpr int NBT = 4;   // scratch buffers
     CarveWs ws{};
     ws.H = H;
     ws.W0 = W;
@@ -127,13 +132,13 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
                 c.dpc_r = R;
                 c.dpc_wpc = wpc;
                 c.dpc_v = v;
-                bytes = std::max(bytes, carve_ws_assign(c, 1, remove, R != 0, nullptr));
+                bytes = std::max(bytes, carve_ws_assign(c, NBT, remove, R != 0, nullptr));
             }
     if (cudaMalloc(&sc.slab, bytes) != cudaSuccess) return SCPL_ENOMEM;
-    const long yfm_bytes = (long)H * W * tp;
+    const long yfm_bytes = (long)H * W * tp * NBT;
     if (cudaMalloc(&sc.yfm, (size_t)yfm_bytes) != cudaSuccess) return SCPL_ENOMEM;
     if (cudaMalloc(&sc.err, 256) != cudaSuccess) return SCPL_ENOMEM;
-    carve_ws_assign(ws, 1, remove, true, static_cast<char *>(sc.slab));
+    carve_ws_assign(ws, NBT, remove, true, static_cast<char *>(sc.slab));
     ws.Yfm = static_cast<uint8_t *>(sc.yfm);
     ws.err = static_cast<int *>(sc.err);
     ws.wg = 1;
@@ -141,11 +146,16 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
     ws.E0 = nullptr;
     ws.Y = nullptr;
     ws.D = nullptr;
-    const BufState st0{0, tp, W, 0, 0, 0, W - remove, 0, tp, k, 0, -1};
+    BufState st0[NBT];
+    for (int b = 0; b < NBT; ++b)
+        st0[b] = BufState{0, tp, W, 0, 0, 0, W - remove, 0, tp, k, (long long)b * H * W * tp, -1};
     if (cudaMemsetAsync(sc.err, 0, 256, s) != cudaSuccess) return SCPL_ECUDA;
-    if (cudaMemsetAsync(ws.SD, 0, (size_t)ws.plane * 4, s) != cudaSuccess) return SCPL_ECUDA;
-    k_tune_fill<<<304, 256, 0, s>>>(ws.E, ws.pitch, H, W, ws.Yfm, yfm_bytes);
-    k_tune_identity<<<304, 256, 0, s>>>(ws.O, ws.pitch, H, W);
+    if (cudaMemsetAsync(ws.SD, 0, (size_t)NBT * ws.plane * 4, s) != cudaSuccess) return SCPL_ECUDA;
+    for (int b = 0; b < NBT; ++b) {   // slot 0 of every buffer; the luma copy once
+        k_tune_fill<<<304, 256, 0, s>>>(ws.E + (long)b * 2 * ws.plane, ws.pitch, H, W, ws.Yfm,
+                                        b == 0 ? yfm_bytes : 0);
+        k_tune_identity<<<304, 256, 0, s>>>(ws.O + (long)b * 2 * ws.plane, ws.pitch, H, W);
+    }
     if (cudaGetLastError() != cudaSuccess) return SCPL_ECUDA;
 
     cudaEvent_t a = nullptr, b = nullptr;
@@ -154,7 +164,7 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
         return SCPL_ECUDA;
     }
     auto reset = [&]() {
-        return cudaMemcpyAsync(ws.st, &st0, sizeof st0, cudaMemcpyHostToDevice, s);
+        return cudaMemcpyAsync(ws.st, st0, sizeof st0, cudaMemcpyHostToDevice, s);
     };
     const int reps = 3;
     // time one DP candidate (the state is reset before every run)
@@ -165,7 +175,7 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
         v.dpc_wpc = wpc;
         v.dpc_v = lane_cols;
         if (kind != 0 && !dpc_available(W, H, kind, wpc, lane_cols)) return -1.0f;
-        carve_ws_assign(v, 1, remove, kind != 0, static_cast<char *>(sc.slab));
+        carve_ws_assign(v, NBT, remove, kind != 0, static_cast<char *>(sc.slab));
         if (kind != 0 && (v.dpc_r != kind || v.dpc_wpc != wpc || v.dpc_v != lane_cols))
             return -1.0f;
         if (kind == 0) {
@@ -176,8 +186,8 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
         for (int r = 0; r <= reps; ++r) {
             if (reset() != cudaSuccess) return -1.0f;
             cudaEventRecord(a, s);
-            cudaError_t e = kind ? launch_dpc(v, 1, k, nullptr, 0, s)
-                                 : launch_dp_select(v, 1, k, nullptr, 0, s);
+            cudaError_t e = kind ? launch_dpc(v, NBT, k, nullptr, 0, s)
+                                 : launch_dp_select(v, NBT, k, nullptr, 0, s);
             cudaEventRecord(b, s);
             if (e != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
                 cudaGetLastError();
@@ -210,11 +220,11 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
         v.dpc_r = t.dp_us[0] > 0 ? 32 : 0;
         v.dpc_wpc = 4;
         v.dpc_v = 4;
-        carve_ws_assign(v, 1, remove, v.dpc_r != 0, static_cast<char *>(sc.slab));
+        carve_ws_assign(v, NBT, remove, v.dpc_r != 0, static_cast<char *>(sc.slab));
         cudaError_t e = reset();
         if (e == cudaSuccess)
-            e = t.dp_us[0] > 0 ? launch_dpc(v, 1, k, nullptr, 0, s)
-                               : launch_dp_select(v, 1, k, nullptr, 0, s);
+            e = t.dp_us[0] > 0 ? launch_dpc(v, NBT, k, nullptr, 0, s)
+                               : launch_dp_select(v, NBT, k, nullptr, 0, s);
         if (e != cudaSuccess) result = SCPL_ECUDA;
         const int rows[3] = {1, 2, 4};
         float ubest = 1e30f;
@@ -224,7 +234,7 @@ scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out) {
             float tb = 1e30f;
             for (int r = 0; r <= reps; ++r) {
                 cudaEventRecord(a, s);
-                e = launch_update(u, 1, s);   // idempotent on a pending iteration
+                e = launch_update(u, NBT, s);   // idempotent on a pending iteration
                 cudaEventRecord(b, s);
                 if (e != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess) {
                     result = SCPL_ECUDA;
