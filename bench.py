@@ -571,6 +571,86 @@ def run_batch(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+STILLS_METRIC = "still-image retargeting time: SCPL (every parent's seam per iteration) vs seam carving"
+
+
+def run_stills(args) -> None:
+    """The paper's two image experiments (Sec. 4, Figs. 6-7) on synthetic
+    stills: recursive carving to 0.8 of the previous width per loop, and direct
+    carving to several width ratios, each by SCPL with an uncapped k (every
+    parent's lowest seam per iteration, Eq. 6) and by classic seam carving
+    (k = 1), with the gradient energy alone.  Times are CUDA-event medians of
+    3 carves after a warm-up, on the GPU; the oracle repeats both at 640x480."""
+    import torch
+
+    from paper_1903_03180_gb300 import scpl, synth
+    torch.cuda.set_device(0)
+    r = scpl.Retargeter(wg=1, wm=0, use_buffer=False)
+    UNCAPPED = 1 << 20
+
+    def gpu_ms(img, target, k):
+        x = torch.from_numpy(img[None]).cuda()
+        out = torch.empty((1, img.shape[0], target, 3), dtype=torch.uint8, device="cuda")
+        scpl.scpl_carve(r.h, x, target, k, out)
+        ts = []
+        for _ in range(3):
+            ts.append(_event_ms(lambda: scpl.scpl_carve(r.h, x, target, k, out)))
+        return float(np.median(ts)), out[0].cpu().numpy()
+
+    def experiments(img, time_fn, loops=5, ratios=(0.9, 0.8, 0.7, 0.6, 0.5)):
+        H, W = img.shape[:2]
+        rec, cur = [], {"scpl": img, "sc": img}
+        for i in range(loops):
+            row = {"loop": i + 1}
+            for name, k in (("scpl", UNCAPPED), ("sc", 1)):
+                w = cur[name].shape[1]
+                tgt = max(2, int(round(0.8 * w)))
+                t, out = time_fn(cur[name], tgt, k)
+                row[name + "_ms"] = round(t, 3)
+                row["width"] = f"{w}->{tgt}"
+                cur[name] = out
+            row["reduction"] = round(1.0 - row["scpl_ms"] / row["sc_ms"], 4)
+            rec.append(row)
+        direct = []
+        for ratio in ratios:
+            tgt = max(2, int(round(ratio * W)))
+            row = {"ratio": ratio, "width": f"{W}->{tgt}"}
+            for name, k in (("scpl", UNCAPPED), ("sc", 1)):
+                row[name + "_ms"] = round(time_fn(img, tgt, k)[0], 3)
+            row["reduction"] = round(1.0 - row["scpl_ms"] / row["sc_ms"], 4)
+            direct.append(row)
+        return {"recursive": rec, "direct": direct}
+
+    sizes = [(480, 640), (1080, 1920), (2160, 3840)]
+    gpu = {}
+    for H, W in sizes:
+        img = synth.still_frame(H, W, seed=0x5C9 ^ 6 ^ (H * 7919 + W))
+        gpu[f"{W}x{H}"] = experiments(img, gpu_ms)
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+
+        def cpu_ms(img, target, k):
+            t0 = time.perf_counter()
+            out, _, _ = oracle.carve(img[None], target, k, wg=1, wm=0, use_buffer=False)
+            return (time.perf_counter() - t0) * 1e3, out[0]
+
+        img = synth.still_frame(480, 640, seed=0x5C9 ^ 6 ^ (480 * 7919 + 640))
+        cpu = {"640x480": experiments(img, cpu_ms, loops=3, ratios=(0.9, 0.7, 0.5)),
+               "cores": 1, "kind": "oracle"}
+    reds = [row["reduction"] for v in gpu.values() for row in v["direct"]]
+    line = {"metric": STILLS_METRIC, "value": round(100 * float(np.mean(reds)), 2),
+            "unit": "% less time (mean over the direct ratios and sizes)", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "stills", "sizes": [f"{w}x{h}" for h, w in sizes],
+                       "energy": "gradient only (wg = 1, wm = 0)", "scpl_k": "uncapped",
+                       "sc_k": 1},
+            "gpu": gpu, "cpu": cpu}
+    print(json.dumps(line), flush=True)
+    r.close()
+
+
 def run_serve(args) -> None:
     """Serving: Poisson arrivals of host-memory jobs (16-128 frames, 360p to
     2160p, 10-40 % narrower) through one server, rates swept."""
@@ -670,7 +750,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serve"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serve", "stills"],
                     default="clip_1080p_300f")
     ap.add_argument("--clips", type=int, default=256, help="batch: clips")
     ap.add_argument("--rates", default="5,10,20,50,100,200", help="serve: arrivals per s")
@@ -701,6 +781,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "stills":
+        run_stills(args)
     else:
         run_native(args)
 
