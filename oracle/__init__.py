@@ -239,3 +239,35 @@ def carve_job(frames: np.ndarray, target_W: int, target_H: int, k: int, wg: int 
     if starts is None:
         starts = np.array([0, T], np.int32)
     return out, starts
+
+
+def blend_sharpness(frames: np.ndarray, window: int = 4) -> tuple[int, int]:
+    """A numeric stand-in for Fig. 9 (Sec. 4): on a nearly static video, a
+    blend of consecutive retargeted frames stays sharp when the same seams are
+    removed from them and blurs when content moves between frames.
+
+    For every run of `window` consecutive frames t .. t+window-1 (t = 0 ..
+    T-window), the blend B is the sum of their integer BT.601 luma maps.  The
+    numerator adds up the L1 Sobel magnitude |Gx| + |Gy| (3x3, replicate
+    border) of B, and the denominator the same magnitude of each frame of the
+    run.  Sobel is linear, so num <= den, with equality when the frames'
+    gradients agree everywhere; num / den is the blend's sharpness.
+    Returns (num, den) as exact integers."""
+    frames = np.ascontiguousarray(frames, dtype=np.uint8)
+    T = frames.shape[0]
+    if T < window or window < 1:
+        return 0, 0
+    Y = np.stack([luma(f) for f in frames]).astype(np.int64)
+
+    def mag(img):
+        p = np.pad(img, 1, mode="edge")
+        gx = (p[:-2, 2:] + 2 * p[1:-1, 2:] + p[2:, 2:]) - (p[:-2, :-2] + 2 * p[1:-1, :-2] + p[2:, :-2])
+        gy = (p[2:, :-2] + 2 * p[2:, 1:-1] + p[2:, 2:]) - (p[:-2, :-2] + 2 * p[:-2, 1:-1] + p[:-2, 2:])
+        return int(np.abs(gx).sum() + np.abs(gy).sum())
+
+    per_frame = [mag(Y[t]) for t in range(T)]
+    num = den = 0
+    for t in range(T - window + 1):
+        num += mag(Y[t:t + window].sum(axis=0))
+        den += sum(per_frame[t:t + window])
+    return num, den

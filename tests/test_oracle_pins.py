@@ -402,3 +402,53 @@ def test_carve_job_width_only_is_carve(orc):
     out, starts = orc.carve_job(f, 30, 20, 4, t_max=3)
     ref, ref_starts, _ = orc.carve(f, 30, 4, t_max=3)
     assert np.array_equal(out, ref) and np.array_equal(starts, ref_starts)
+
+
+# ------------------------------------ N4: blend sharpness (Sec. 4, Fig. 9 stand-in)
+def _gray(Y):
+    """RGB frame whose integer BT.601 luma is exactly Y (R = G = B)."""
+    Y = np.asarray(Y, np.uint8)
+    return np.repeat(Y[..., None], 3, axis=-1)
+
+
+def test_blend_sharpness_step_edge_closed_form(orc):
+    """One frame, a vertical step of height h at column c: with a replicate
+    border the L1 Sobel gives 4h on the two columns next to the step and 0
+    elsewhere (rows are identical, so Gy = 0): 8 h H in all."""
+    H, W, c, h = 7, 12, 5, 10
+    Y = np.zeros((H, W), np.uint8)
+    Y[:, c:] = h
+    num, den = orc.blend_sharpness(_gray(Y)[None], window=1)
+    assert num == den == 8 * h * H
+
+
+def test_blend_sharpness_static_frames_are_sharp(orc):
+    """Identical frames: the blend is window x the frame and Sobel is linear."""
+    from paper_1903_03180_gb300 import synth
+    f = synth.still_frame(20, 30, seed=41)
+    num, den = orc.blend_sharpness(np.repeat(f[None], 6, axis=0), window=4)
+    assert num == den > 0
+
+
+def test_blend_sharpness_complementary_frames_cancel(orc):
+    """Gray frames alternating g and 255 - g: every blend of 4 is the constant
+    510, so it has no gradient at all while each frame has."""
+    r = np.random.default_rng(42)
+    g = r.integers(0, 256, (9, 13), dtype=np.uint8)
+    frames = np.stack([_gray(g), _gray(255 - g)] * 3)
+    num, den = orc.blend_sharpness(frames, window=4)
+    assert num == 0 and den > 0
+
+
+def test_blend_sharpness_displaced_content_blurs(orc):
+    """A frame and the same frame moved one column: the blend is blurred."""
+    from paper_1903_03180_gb300 import synth
+    f = synth.still_frame(24, 40, seed=43)
+    moved = np.concatenate([f[:, :1], f[:, :-1]], axis=1)
+    num, den = orc.blend_sharpness(np.stack([f, moved]), window=2)
+    assert 0 < num < den
+
+
+def test_blend_sharpness_short_clip_is_empty(orc):
+    f = np.zeros((3, 4, 5, 3), np.uint8)
+    assert orc.blend_sharpness(f, window=4) == (0, 0)
