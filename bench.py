@@ -651,6 +651,46 @@ def run_stills(args) -> None:
     r.close()
 
 
+CONSISTENCY_METRIC = "sharpness of 4-frame blends of a retargeted static clip (Fig. 9 stand-in)"
+
+
+def run_consistency(args) -> None:
+    """Fig. 9 of the paper, measured: a nearly static 64-frame 1920x1080 clip
+    (no pan, no moving objects, noise of +-2) carved by 30 % with SCPL
+    and the spatiotemporal buffer, and with raw seam carving frame by frame.
+    The blend sharpness (num / den of scpl_blend_sharpness over every run of 4
+    consecutive frames) is 1 for perfectly static content."""
+    import torch
+
+    from paper_1903_03180_gb300 import scpl, synth
+    torch.cuda.set_device(0)
+    T, H, W, target = 64, 1080, 1920, 1344
+    f = synth.clip(T, H, W, seed=0x5C9 ^ 7, pan=0, n_ellipses=0, noise=2)
+    x = torch.from_numpy(f).cuda()
+    rs = scpl.Retargeter(wg=1, wm=2)
+    rr = scpl.Retargeter(wg=1, wm=2, use_buffer=False)
+    o_s, starts, _ = rs.carve(x, target, 32)
+    ms_s = _event_ms(lambda: rs.carve(x, target, 32))
+    o_r, _, _ = rr.carve(x, target, 1)
+    ms_r = _event_ms(lambda: rr.carve(x, target, 1))
+
+    def ratio(frames):
+        n, d = scpl.scpl_blend_sharpness(rs.h, frames, 4)
+        return round(n / d, 5) if d else None
+
+    line = {"metric": CONSISTENCY_METRIC, "value": ratio(o_s), "unit": "num / den",
+            "higher_is_better": True, "n_gpus": 1, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": "static_1080p_64f", "T": T, "H": H, "W": W,
+                       "target_W": target, "blend_window": 4},
+            "input": ratio(x), "scpl": {"value": ratio(o_s), "k": 32, "buffers": len(starts) - 1,
+                                        "ms_per_clip": round(ms_s, 3)},
+            "raw_seam_carving": {"value": ratio(o_r), "k": 1, "buffers": T,
+                                 "ms_per_clip": round(ms_r, 3)}}
+    print(json.dumps(line), flush=True)
+    rs.close()
+    rr.close()
+
+
 def run_serve(args) -> None:
     """Serving: Poisson arrivals of host-memory jobs (16-128 frames, 360p to
     2160p, 10-40 % narrower) through one server, rates swept."""
@@ -750,7 +790,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serve", "stills"],
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["batch", "serve", "stills",
+                                                                "consistency"],
                     default="clip_1080p_300f")
     ap.add_argument("--clips", type=int, default=256, help="batch: clips")
     ap.add_argument("--rates", default="5,10,20,50,100,200", help="serve: arrivals per s")
@@ -783,6 +824,8 @@ def main():
         run_serve(args)
     elif args.workload == "stills":
         run_stills(args)
+    elif args.workload == "consistency":
+        run_consistency(args)
     else:
         run_native(args)
 

@@ -134,6 +134,20 @@ scpl_status scpl_scan_arrivals(scpl_handle h, const uint8_t *frames, int T, int 
  * lacks stream memory operations. */
 scpl_status scpl_signal_arrival(void *stream, uint32_t *counter, uint32_t value);
 
+/* Sharpness of blends of consecutive frames (a measure of temporal
+ * consistency; a numeric stand-in for Fig. 9 of Sec. 4): on a nearly static
+ * clip, frames carved with the same seams blend into a sharp image, frames
+ * carved independently into a blurred one.  For every run of `window`
+ * consecutive frames t .. t+window-1 (t = 0 .. T-window), the blend B is the
+ * sum of their integer BT.601 luma maps; *num adds the L1 Sobel magnitude
+ * |Gx|+|Gy| (3x3, replicate border) of B, and *den the same magnitude of each
+ * frame of the run.  num <= den; num / den is 1 for static content.
+ *   frames   [device] uint8 [T][H][W][3]
+ *   num, den [host] exact sums (0 and 0 when T < window)
+ * SCPL_EINVAL for window outside [1, 64].  Synchronises the stream. */
+scpl_status scpl_blend_sharpness(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                                 int window, int64_t *num, int64_t *den);
+
 /* Bound, in nanoseconds, of each device-wide wait of the handle's buffer
  * scans: the per-round reduction across the scan's CTAs and the waits for
  * arriving frames (default 2e9).  A wait that runs out makes its call return

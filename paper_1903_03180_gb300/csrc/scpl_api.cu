@@ -110,6 +110,7 @@ struct scpl_ctx {
     DevBuf cws, bof;
     // host-memory entry point staging
     DevBuf in_frames, out_frames, seams_dev;
+    DevBuf qY, qacc;   // blend sharpness: luma of every frame, the two sums
     DevBuf Yfm;
     bool autotune = false;
     unsigned long long wait_ns = SPIN_LIMIT_NS;   // bound of the scan's device-wide waits
@@ -641,6 +642,29 @@ scpl_status scpl_signal_arrival(void *stream, uint32_t *counter, uint32_t value)
                        (cuuint32_t)value, CU_STREAM_WRITE_VALUE_DEFAULT) == CUDA_SUCCESS
                ? SCPL_OK
                : SCPL_ECUDA;
+}
+
+scpl_status scpl_blend_sharpness(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                                 int window, int64_t *num, int64_t *den) {
+    scpl_status s = check_frames(h, frames, T, H, W);
+    if (s != SCPL_OK) return s;
+    if (!num || !den) return fail(h, SCPL_EINVAL, "num and den must not be NULL");
+    if (window < 1 || window > 64) return fail(h, SCPL_EINVAL, "window=%d outside [1, 64]", window);
+    *num = *den = 0;
+    if (T < window) return SCPL_OK;
+    cudaStream_t st = h->stream;
+    SCPL_CUDA(h, h->qY.ensure((size_t)T * H * W));
+    SCPL_CUDA(h, h->qacc.ensure(16));
+    SCPL_CUDA(h, h->h_small.ensure(16));
+    SCPL_CUDA(h, cudaMemsetAsync(h->qacc.p, 0, 16, st));
+    SCPL_CUDA(h, launch_blend_sharpness(frames, T, H, W, window, h->qY.as<uint8_t>(),
+                                        h->qacc.as<unsigned long long>(), st));
+    unsigned long long *hs = h->h_small.as<unsigned long long>();
+    SCPL_CUDA(h, cudaMemcpyAsync(hs, h->qacc.p, 16, cudaMemcpyDeviceToHost, st));
+    SCPL_CUDA(h, cudaStreamSynchronize(st));
+    *num = (int64_t)hs[0];
+    *den = (int64_t)hs[1];
+    return SCPL_OK;
 }
 
 scpl_status scpl_set_wait_limit(scpl_handle h, uint64_t ns) {

@@ -268,6 +268,11 @@ namespace scpl {
 bool tuning_lookup(int H, int W, scpl_tuning *out);
 void tuning_store(const scpl_tuning &t);
 void tuning_clear();
+// Blend sharpness of a retargeted clip (quality.cu): luma of every frame into
+// Y [T][H][W], then acc[0] += num, acc[1] += den over the runs of `window`.
+cudaError_t launch_blend_sharpness(const uint8_t *frames, int T, int H, int W, int window,
+                                   uint8_t *Y, unsigned long long *acc, cudaStream_t s);
+
 // true if the table held a choice for (H, W) (then applied to ws)
 bool tuning_apply(int H, int W, CarveWs &ws, bool *use_dpc);
 scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out);

@@ -84,6 +84,8 @@ SIGNATURES = {
     "scpl_scan_arrivals": (_I, [_P, _P, _I, _I, _I, _P, _I, _P, _P]),
     "scpl_signal_arrival": (_I, [_P, _P, ctypes.c_uint32]),
     "scpl_set_wait_limit": (_I, [_P, ctypes.c_uint64]),
+    "scpl_blend_sharpness": (_I, [_P, _P, _I, _I, _I, _I, ctypes.POINTER(_LL),
+                                  ctypes.POINTER(_LL)]),
     "scpl_seams": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "scpl_carve": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
     "scpl_carve_host": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
@@ -258,6 +260,18 @@ def scpl_signal_arrival(stream, counter, value: int):
                                     int(value))
     if st != SCPL_OK:
         raise SCPLError(st, "scpl_signal_arrival failed")
+
+
+def scpl_blend_sharpness(h, frames, window: int = 4) -> tuple[int, int]:
+    """(num, den) of the blends of `window` consecutive frames of a cuda
+    uint8 [T,H,W,3] clip; num / den is the blends' sharpness (1 = static)."""
+    import torch
+    fp = _dev_ptr(frames, torch.uint8, 4, "frames")
+    T, H, W, _ = frames.shape
+    n, d = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(h, load().scpl_blend_sharpness(h, fp, T, H, W, int(window), ctypes.byref(n),
+                                          ctypes.byref(d)))
+    return n.value, d.value
 
 
 def scpl_set_wait_limit(h, ns: int):
