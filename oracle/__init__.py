@@ -271,3 +271,43 @@ def blend_sharpness(frames: np.ndarray, window: int = 4) -> tuple[int, int]:
         num += mag(Y[t:t + window].sum(axis=0))
         den += sum(per_frame[t:t + window])
     return num, den
+
+
+def enlarge(frames: np.ndarray, target: int, k: int, wg: int = 1, wm: int = 2,
+            alpha: float = ALPHA, t_max: int = T_MAX, use_buffer: bool = True,
+            maxval_mode: int = 0):
+    """Widen a clip by seam insertion (Sec. 2 retargets in both directions;
+    the insertion rule is Avidan & Shamir's).  To add m = target - W columns,
+    the clip is carved to W - m by SCPL (``carve``); the m seams removed from
+    each spatiotemporal buffer, in original columns, are the ones inserted
+    into every frame of that buffer.  Each row emits its original pixels in
+    order and, after each seam pixel x, a new pixel that is the rounded mean
+    (a + b + 1) >> 1, per channel, of pixel x and pixel x+1 (x itself at the
+    last column).  m must be in [0, W-2].
+
+    Returns (out [T,H,target,3], starts of the buffers)."""
+    frames = np.ascontiguousarray(frames, dtype=np.uint8)
+    T, H, W = frames.shape[:3]
+    m = target - W
+    if m < 0 or m > W - 2:
+        raise ValueError("target must be in [W, 2W-2]")
+    if m == 0:
+        return frames.copy(), np.array([0, T], np.int32)
+    _, starts, seams = carve(frames, W - m, k, wg=wg, wm=wm, alpha=alpha, t_max=t_max,
+                             use_buffer=use_buffer, maxval_mode=maxval_mode)
+    out = np.empty((T, H, target, 3), np.uint8)
+    for b in range(len(starts) - 1):
+        t0, t1 = int(starts[b]), int(starts[b + 1])
+        for i in range(H):
+            cols = set(int(c) for c in seams[b, :, i])
+            left, right = [], []
+            for x in range(W):
+                left.append(x)
+                right.append(x)
+                if x in cols:
+                    left.append(x)
+                    right.append(min(x + 1, W - 1))
+            a = frames[t0:t1, i, left].astype(np.int32)
+            c = frames[t0:t1, i, right].astype(np.int32)
+            out[t0:t1, i] = ((a + c + 1) >> 1).astype(np.uint8)
+    return out, starts

@@ -452,3 +452,62 @@ def test_blend_sharpness_displaced_content_blurs(orc):
 def test_blend_sharpness_short_clip_is_empty(orc):
     f = np.zeros((3, 4, 5, 3), np.uint8)
     assert orc.blend_sharpness(f, window=4) == (0, 0)
+
+
+# ------------------------------------------------ N4: seam insertion (enlarging)
+def _drop_inserted(out: np.ndarray, W: int, inserted_after: list) -> np.ndarray:
+    """Remove, row by row, the pixel that follows each listed original column."""
+    H = out.shape[0]
+    rows = []
+    for i in range(H):
+        keep, p = [], 0
+        for x in range(W):
+            keep.append(p)
+            p += 2 if x in inserted_after[i] else 1
+        rows.append(out[i, keep])
+    return np.stack(rows)
+
+
+def test_enlarge_k1_inserts_the_classic_seams(orc):
+    """k = 1, one frame, gradient energy: the inserted pixels follow exactly
+    the first m seams of classic seam carving, each is the rounded mean of its
+    neighbours, and dropping them gives the original frame back."""
+    from paper_1903_03180_gb300 import synth
+    f = synth.still_frame(16, 24, seed=51)
+    m = 5
+    out, starts = orc.enlarge(f[None], 24 + m, 1, wm=0, use_buffer=False)
+    _, seams = tb.classic_seam_carve(f, m, lambda im: tb.sobel_scipy(orc.luma(im)))
+    inserted = [set(int(s) for s in seams[:, i]) for i in range(16)]
+    assert out.shape == (1, 16, 24 + m, 3)
+    assert np.array_equal(_drop_inserted(out[0], 24, inserted), f)
+    for i in range(16):
+        p = 0
+        for x in range(24):
+            if x in inserted[i]:
+                a = f[i, x].astype(int)
+                b = f[i, min(x + 1, 23)].astype(int)
+                assert np.array_equal(out[0, i, p + 1], (a + b + 1) >> 1)
+                p += 2
+            else:
+                p += 1
+
+
+def test_enlarge_shares_seams_within_a_buffer(orc):
+    """Video: every frame of a buffer gets the same inserted columns (those
+    that carving the clip removes from the buffer), and dropping them gives
+    each frame back."""
+    from paper_1903_03180_gb300 import synth
+    f = synth.clip(6, 14, 20, seed=52, cuts=(3, 3))
+    out, starts = orc.enlarge(f, 27, 4)
+    _, cstarts, seams = orc.carve(f, 13, 4)
+    assert np.array_equal(starts, cstarts)
+    for b in range(len(starts) - 1):
+        inserted = [set(int(s) for s in seams[b, :, i]) for i in range(14)]
+        for t in range(starts[b], starts[b + 1]):
+            assert np.array_equal(_drop_inserted(out[t], 20, inserted), f[t])
+
+
+def test_enlarge_by_nothing_is_identity(orc):
+    f = np.random.default_rng(53).integers(0, 256, (3, 5, 7, 3), dtype=np.uint8)
+    out, starts = orc.enlarge(f, 7, 2)
+    assert np.array_equal(out, f) and list(starts) == [0, 3]
