@@ -134,6 +134,23 @@ scpl_status scpl_scan_arrivals(scpl_handle h, const uint8_t *frames, int T, int 
  * lacks stream memory operations. */
 scpl_status scpl_signal_arrival(void *stream, uint32_t *counter, uint32_t value);
 
+/* Widen a clip by seam insertion (the inverse use of seam carving; the
+ * insertion rule is Avidan & Shamir's).  To add m = target_W - W columns the
+ * clip is carved to W - m by SCPL (as scpl_carve does, on a scratch copy);
+ * the m seams removed from each spatiotemporal buffer, in original columns,
+ * are inserted into every frame of that buffer.  Each row keeps its original
+ * pixels in order and, after each seam pixel x, gets a new pixel that is the
+ * rounded mean (a + b + 1) >> 1, per channel, of pixels x and x+1 (x itself
+ * at the last column).
+ *   frames        [device] uint8 [T][H][W][3]
+ *   out           [device] uint8 [T][H][target_W][3]
+ *   buffer_starts [host] int32 [T+1] or NULL; n_buffers [host] or NULL
+ * W <= target_W <= 2W-2 and W <= 8192 (else SCPL_EINVAL); k >= 1.
+ * Synchronises the stream. */
+scpl_status scpl_enlarge(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                         int target_W, int k, uint8_t *out, int32_t *buffer_starts,
+                         int *n_buffers);
+
 /* Sharpness of blends of consecutive frames (a measure of temporal
  * consistency; a numeric stand-in for Fig. 9 of Sec. 4): on a nearly static
  * clip, frames carved with the same seams blend into a sharp image, frames

@@ -644,6 +644,45 @@ scpl_status scpl_signal_arrival(void *stream, uint32_t *counter, uint32_t value)
                : SCPL_ECUDA;
 }
 
+scpl_status scpl_enlarge(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                         int target_W, int k, uint8_t *out, int32_t *buffer_starts,
+                         int *n_buffers) {
+    scpl_status s = check_frames(h, frames, T, H, W);
+    if (s != SCPL_OK) return s;
+    if (!out) return fail(h, SCPL_EINVAL, "out is NULL");
+    if (k < 1) return fail(h, SCPL_EINVAL, "k=%d must be >= 1", k);
+    const int m = target_W - W;
+    if (m < 0 || m > W - 2)
+        return fail(h, SCPL_EINVAL, "target_W=%d must be in [W, 2W-2] for W=%d", target_W, W);
+    cudaStream_t st = h->stream;
+    if (m == 0) {
+        SCPL_CUDA(h, cudaMemcpyAsync(out, frames, (size_t)T * H * W * 3, cudaMemcpyDeviceToDevice,
+                                     st));
+        SCPL_CUDA(h, cudaStreamSynchronize(st));
+        if (buffer_starts) {
+            buffer_starts[0] = 0;
+            buffer_starts[1] = T;
+        }
+        if (n_buffers) *n_buffers = 1;
+        return SCPL_OK;
+    }
+    // the seams carving removes, from a scratch copy carved to W - m
+    SCPL_CUDA(h, h->out_frames.ensure((size_t)T * H * (W - m) * 3));
+    SCPL_CUDA(h, h->seams_dev.ensure((size_t)T * m * H * sizeof(int16_t)));
+    std::vector<int> starts(T + 1);
+    int nb = 0;
+    if ((s = carve_run(h, frames, T, H, W, W - m, k, h->out_frames.as<uint8_t>(), starts.data(),
+                       &nb, h->seams_dev.as<int16_t>(), nullptr, 1, nullptr)) != SCPL_OK)
+        return s;
+    // h->starts still holds the scan's buffer starts on the device
+    SCPL_CUDA(h, launch_insert_seams(frames, H, W, target_W, h->seams_dev.as<int16_t>(),
+                                     (long)m * H, m, h->starts.as<int>(), nb, out, st));
+    SCPL_CUDA(h, cudaStreamSynchronize(st));
+    if (buffer_starts) std::copy(starts.begin(), starts.begin() + nb + 1, buffer_starts);
+    if (n_buffers) *n_buffers = nb;
+    return SCPL_OK;
+}
+
 scpl_status scpl_blend_sharpness(scpl_handle h, const uint8_t *frames, int T, int H, int W,
                                  int window, int64_t *num, int64_t *den) {
     scpl_status s = check_frames(h, frames, T, H, W);

@@ -273,6 +273,13 @@ void tuning_clear();
 cudaError_t launch_blend_sharpness(const uint8_t *frames, int T, int H, int W, int window,
                                    uint8_t *Y, unsigned long long *acc, cudaStream_t s);
 
+// Seam insertion (insert.cu): every frame of buffer b (frames starts[b] ..
+// starts[b+1]-1) widened from W to target by the m seams of
+// seams[b * seam_stride + s * H + i] (original columns).
+cudaError_t launch_insert_seams(const uint8_t *frames, int H, int W, int target,
+                                const int16_t *seams, long seam_stride, int m,
+                                const int *starts, int nb, uint8_t *out, cudaStream_t s);
+
 // true if the table held a choice for (H, W) (then applied to ws)
 bool tuning_apply(int H, int W, CarveWs &ws, bool *use_dpc);
 scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out);

@@ -84,6 +84,7 @@ SIGNATURES = {
     "scpl_scan_arrivals": (_I, [_P, _P, _I, _I, _I, _P, _I, _P, _P]),
     "scpl_signal_arrival": (_I, [_P, _P, ctypes.c_uint32]),
     "scpl_set_wait_limit": (_I, [_P, ctypes.c_uint64]),
+    "scpl_enlarge": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
     "scpl_blend_sharpness": (_I, [_P, _P, _I, _I, _I, _I, ctypes.POINTER(_LL),
                                   ctypes.POINTER(_LL)]),
     "scpl_seams": (_I, [_P, _P, _I, _I, _I, _P, _P]),
@@ -262,6 +263,22 @@ def scpl_signal_arrival(stream, counter, value: int):
         raise SCPLError(st, "scpl_signal_arrival failed")
 
 
+def scpl_enlarge(h, frames, target_W: int, k: int, out) -> np.ndarray:
+    """Widen cuda uint8 [T,H,W,3] frames to target_W by seam insertion into
+    out [T,H,target_W,3]; returns the buffer starts."""
+    import torch
+    fp = _dev_ptr(frames, torch.uint8, 4, "frames")
+    op = _dev_ptr(out, torch.uint8, 4, "out")
+    T, H, W, _ = frames.shape
+    if tuple(out.shape) != (T, H, target_W, 3):
+        raise ValueError("out must be [T,H,target_W,3]")
+    starts = np.zeros(T + 1, np.int32)
+    nb = ctypes.c_int()
+    _check(h, load().scpl_enlarge(h, fp, T, H, W, int(target_W), int(k), op,
+                                  starts.ctypes.data_as(_P), ctypes.byref(nb)))
+    return starts[: nb.value + 1].copy()
+
+
 def scpl_blend_sharpness(h, frames, window: int = 4) -> tuple[int, int]:
     """(num, den) of the blends of `window` consecutive frames of a cuda
     uint8 [T,H,W,3] clip; num / den is the blends' sharpness (1 = static)."""
@@ -400,6 +417,14 @@ class Retargeter:
         if seams is not None:
             seams = seams[: len(starts) - 1]
         return out, starts, seams
+
+    def enlarge(self, frames, target_W: int, k: int):
+        """Widen frames by seam insertion; returns (out, buffer starts)."""
+        import torch
+        T, H, W, _ = frames.shape
+        out = torch.empty((T, H, target_W, 3), dtype=torch.uint8, device=frames.device)
+        starts = scpl_enlarge(self.h, frames, target_W, k, out)
+        return out, starts
 
     def close(self):
         if self.h is not None:

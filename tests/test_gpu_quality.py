@@ -52,3 +52,43 @@ def test_static_clip_scpl_blends_sharper_than_raw(orc, lib):
     assert r == orc.blend_sharpness(o_raw.cpu().numpy(), 4)
     assert len(starts) - 1 < 24          # SCPL found multi-frame buffers
     assert s[0] / s[1] > r[0] / r[1]     # and its blends are sharper
+
+
+# ------------------------------------------------------------ seam insertion
+@pytest.mark.parametrize("T,H,W,target,k,seed,cuts", [(6, 14, 20, 27, 4, 81, (3, 3)),
+                                                      (5, 33, 70, 120, 8, 82, None),
+                                                      (4, 19, 257, 400, 16, 83, (2, 2)),
+                                                      (3, 40, 64, 100, 32, 84, None)])
+def test_enlarge_matches_oracle(orc, lib, T, H, W, target, k, seed, cuts):
+    from paper_1903_03180_gb300 import synth
+    f = synth.clip(T, H, W, seed=seed, cuts=cuts)
+    r = lib.Retargeter()
+    out, starts = r.enlarge(torch.from_numpy(f).cuda(), target, k)
+    torch.cuda.synchronize()
+    r.close()
+    ref, ref_starts = orc.enlarge(f, target, k)
+    assert np.array_equal(starts, ref_starts)
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_enlarge_still_k1(orc, lib):
+    from paper_1903_03180_gb300 import synth
+    f = synth.still_frame(30, 50, seed=85)[None]
+    r = lib.Retargeter(wg=1, wm=0, use_buffer=False)
+    out, _ = r.enlarge(torch.from_numpy(f).cuda(), 61, 1)
+    torch.cuda.synchronize()
+    r.close()
+    ref, _ = orc.enlarge(f, 61, 1, wm=0, use_buffer=False)
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_enlarge_identity_and_limits(lib):
+    f = torch.randint(0, 256, (2, 6, 9, 3), dtype=torch.uint8, device="cuda")
+    r = lib.Retargeter()
+    out, starts = r.enlarge(f, 9, 4)
+    assert torch.equal(out, f) and list(starts) == [0, 2]
+    with pytest.raises(lib.SCPLError):
+        r.enlarge(f, 17, 4)   # more than 2W-2
+    with pytest.raises(lib.SCPLError):
+        r.enlarge(f, 8, 4)    # narrower: use scpl_carve
+    r.close()
