@@ -222,6 +222,21 @@ scpl_status scpl_carve_host(scpl_handle h, const uint8_t *frames, int T, int H, 
                             int target_W, int k, uint8_t *out, int32_t *buffer_starts,
                             int *n_buffers, int16_t *seams);
 
+/* scpl_carve_host for n clips of one shape, streamed through two device
+ * slots: clip i+1's frames go up on an input stream while clip i carves, and
+ * clip i's carved buffers come back on the copy stream while clip i+1 scans
+ * and carves, so the copies in both directions overlap the kernels.  Every
+ * clip's result equals scpl_carve_host's.  Needs stream memory operations
+ * (else SCPL_ECUDA).
+ *   frames    [host] n pointers to uint8 [T][H][W][3] (page-locked)
+ *   out       [host] n pointers to uint8 [T][H][target_W][3] (page-locked)
+ *   n_buffers [host] int [n] or NULL: each clip's buffer count
+ * Synchronises before returning; on an error the clips before the failing
+ * one are complete. */
+scpl_status scpl_carve_host_many(scpl_handle h, int n, const uint8_t *const *frames, int T,
+                                 int H, int W, int target_W, int k, uint8_t *const *out,
+                                 int *n_buffers);
+
 /* scpl_seams without any memory allocation.  The paper has no counterpart:
  * this exists for callers that must not allocate device memory -- code that is
  * recording a CUDA graph (allocation is not allowed during stream capture), a

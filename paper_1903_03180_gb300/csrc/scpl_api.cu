@@ -111,6 +111,10 @@ struct scpl_ctx {
     // host-memory entry point staging
     DevBuf in_frames, out_frames, seams_dev;
     DevBuf qY, qacc;   // blend sharpness: luma of every frame, the two sums
+    // scpl_carve_host_many: a second input and output slot, the input copy
+    // stream and the second arrival counter
+    DevBuf in2, out2, ready2;
+    cudaStream_t istream = nullptr;
     DevBuf Yfm;
     bool autotune = false;
     unsigned long long wait_ns = SPIN_LIMIT_NS;   // bound of the scan's device-wide waits
@@ -580,11 +584,16 @@ void scpl_destroy(scpl_handle h) {
     cudaStreamSynchronize(h->stream);
     DevBuf *bufs[] = {&h->Y, &h->D, &h->ering, &h->S1, &h->S2, &h->partA, &h->partM,
                       &h->count, &h->starts, &h->nbuf, &h->errw, &h->E0, &h->cws, &h->bof,
-                      &h->in_frames, &h->out_frames, &h->seams_dev, &h->Yfm};
+                      &h->in_frames, &h->out_frames, &h->seams_dev, &h->Yfm, &h->qY,
+                      &h->qacc, &h->in2, &h->out2, &h->ready2};
+    if (h->istream) cudaStreamSynchronize(h->istream);
+    if (h->cstream) cudaStreamSynchronize(h->cstream);
+    if (h->gstream) cudaStreamSynchronize(h->gstream);
     for (DevBuf *b : bufs) b->release();
     engine_destroy(h->engine);
     if (h->cstream) cudaStreamDestroy(h->cstream);
     if (h->gstream) cudaStreamDestroy(h->gstream);
+    if (h->istream) cudaStreamDestroy(h->istream);
     h->ready.release();
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
     h->h_small.release();
@@ -836,6 +845,101 @@ scpl_status scpl_carve_host(scpl_handle h, const uint8_t *frames, int T, int H, 
     SCPL_CUDA(h, cudaStreamSynchronize(st));
     if (buffer_starts) std::copy(starts.begin(), starts.begin() + nb + 1, buffer_starts);
     if (n_buffers) *n_buffers = nb;
+    return SCPL_OK;
+}
+
+scpl_status scpl_carve_host_many(scpl_handle h, int n, const uint8_t *const *frames, int T,
+                                 int H, int W, int target_W, int k, uint8_t *const *out,
+                                 int *n_buffers) {
+    if (!h) return SCPL_EINVAL;
+    if (n < 0 || (n > 0 && (!frames || !out))) return fail(h, SCPL_EINVAL, "bad clip lists");
+    if (n == 0) return SCPL_OK;
+    for (int i = 0; i < n; ++i) {
+        scpl_status s = check_frames(h, frames[i], T, H, W);
+        if (s != SCPL_OK) return s;
+        if (!out[i]) return fail(h, SCPL_EINVAL, "out[%d] is NULL", i);
+    }
+    if (target_W < 2 || target_W > W)
+        return fail(h, SCPL_EINVAL, "target_W=%d must be in [2, W=%d]", target_W, W);
+    PFN_cuStreamWriteValue32_v11070 write_value = stream_write_value();
+    if (!write_value) return fail(h, SCPL_ECUDA, "the driver lacks stream memory operations");
+    const size_t frame_in = (size_t)H * W * 3;
+    const size_t in_bytes = (size_t)T * frame_in, out_bytes = (size_t)T * H * target_W * 3;
+    SCPL_CUDA(h, h->in_frames.ensure(in_bytes));
+    SCPL_CUDA(h, h->in2.ensure(in_bytes));
+    SCPL_CUDA(h, h->out_frames.ensure(out_bytes));
+    SCPL_CUDA(h, h->out2.ensure(out_bytes));
+    SCPL_CUDA(h, h->ready.ensure(sizeof(unsigned)));
+    SCPL_CUDA(h, h->ready2.ensure(sizeof(unsigned)));
+    if (!h->cstream) SCPL_CUDA(h, cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
+    if (!h->gstream) SCPL_CUDA(h, cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+    if (!h->istream) SCPL_CUDA(h, cudaStreamCreateWithFlags(&h->istream, cudaStreamNonBlocking));
+    cudaStream_t st = h->stream;
+    uint8_t *in_slot[2] = {h->in_frames.as<uint8_t>(), h->in2.as<uint8_t>()};
+    uint8_t *out_slot[2] = {h->out_frames.as<uint8_t>(), h->out2.as<uint8_t>()};
+    unsigned *ready_slot[2] = {h->ready.as<unsigned>(), h->ready2.as<unsigned>()};
+    constexpr int CHUNK = 8;
+    // reset[s]: the slot's counter was zeroed on the input stream (the scan of
+    // the clip in the slot waits for it); done[s]: every read of the slot's
+    // input (the gathers) and of its output (the copies back) has finished
+    cudaEvent_t reset[2] = {}, done[2] = {};
+    struct Guard {
+        cudaEvent_t *a, *b;
+        ~Guard() {
+            for (int s = 0; s < 2; ++s) {
+                if (a[s]) cudaEventDestroy(a[s]);
+                if (b[s]) cudaEventDestroy(b[s]);
+            }
+        }
+    } guard{reset, done};
+    for (int s = 0; s < 2; ++s) {
+        SCPL_CUDA(h, cudaEventCreateWithFlags(&reset[s], cudaEventDisableTiming));
+        SCPL_CUDA(h, cudaEventCreateWithFlags(&done[s], cudaEventDisableTiming));
+    }
+    // the caller's earlier work on the handle's stream comes first
+    SCPL_CUDA(h, cudaEventRecord(done[0], st));
+    SCPL_CUDA(h, cudaEventRecord(done[1], st));
+    auto upload = [&](int i) -> scpl_status {   // clip i's frames into slot i & 1
+        const int s = i & 1;
+        SCPL_CUDA(h, cudaStreamWaitEvent(h->istream, done[s], 0));
+        SCPL_CUDA(h, cudaMemsetAsync(ready_slot[s], 0, sizeof(unsigned), h->istream));
+        SCPL_CUDA(h, cudaEventRecord(reset[s], h->istream));
+        for (int c = 0; c * CHUNK < T; ++c) {
+            const int f0 = c * CHUNK, nf = std::min(CHUNK, T - f0);
+            SCPL_CUDA(h, cudaMemcpyAsync(in_slot[s] + f0 * frame_in, frames[i] + f0 * frame_in,
+                                         (size_t)nf * frame_in, cudaMemcpyHostToDevice,
+                                         h->istream));
+            if (write_value(reinterpret_cast<CUstream>(h->istream),
+                            reinterpret_cast<CUdeviceptr>(ready_slot[s]), (cuuint32_t)(c + 1),
+                            CU_STREAM_WRITE_VALUE_DEFAULT) != CUDA_SUCCESS)
+                return fail(h, SCPL_ECUDA, "cuStreamWriteValue32 failed");
+        }
+        return SCPL_OK;
+    };
+    scpl_status s = upload(0);
+    std::vector<int> starts(T + 1);
+    for (int i = 0; i < n && s == SCPL_OK; ++i) {
+        const int sl = i & 1;
+        // the next clip's frames go up while this one carves
+        if (i + 1 < n && (s = upload(i + 1)) != SCPL_OK) break;
+        SCPL_CUDA(h, cudaStreamWaitEvent(st, reset[sl], 0));
+        int nb = 0;
+        s = carve_run(h, in_slot[sl], T, H, W, target_W, k, out_slot[sl], starts.data(), &nb,
+                      nullptr, ready_slot[sl], CHUNK, out[i]);
+        if (s != SCPL_OK) break;
+        if (n_buffers) n_buffers[i] = nb;
+        // the slot is free once the gathers (input) and copies back (output)
+        // end: every gather is followed on the copy stream by its buffer's
+        // copy back, which waits for it
+        SCPL_CUDA(h, cudaEventRecord(done[sl], h->cstream));
+    }
+    cudaError_t e1 = cudaStreamSynchronize(h->istream);
+    cudaError_t e2 = cudaStreamSynchronize(h->gstream);
+    cudaError_t e3 = cudaStreamSynchronize(h->cstream);
+    if (s != SCPL_OK) return s;
+    SCPL_CUDA(h, e1);
+    SCPL_CUDA(h, e2);
+    SCPL_CUDA(h, e3);
     return SCPL_OK;
 }
 

@@ -85,6 +85,7 @@ SIGNATURES = {
     "scpl_signal_arrival": (_I, [_P, _P, ctypes.c_uint32]),
     "scpl_set_wait_limit": (_I, [_P, ctypes.c_uint64]),
     "scpl_enlarge": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
+    "scpl_carve_host_many": (_I, [_P, _I, _P, _I, _I, _I, _I, _I, _P, _P]),
     "scpl_blend_sharpness": (_I, [_P, _P, _I, _I, _I, _I, ctypes.POINTER(_LL),
                                   ctypes.POINTER(_LL)]),
     "scpl_seams": (_I, [_P, _P, _I, _I, _I, _P, _P]),
@@ -261,6 +262,24 @@ def scpl_signal_arrival(stream, counter, value: int):
                                     int(value))
     if st != SCPL_OK:
         raise SCPLError(st, "scpl_signal_arrival failed")
+
+
+def scpl_carve_host_many(h, frames: list, target_W: int, k: int, outs: list) -> list[int]:
+    """Carve host clips of one shape (numpy uint8 [T,H,W,3], page-locked for
+    overlap) into host outputs [T,H,target_W,3], streamed; returns each
+    clip's buffer count."""
+    n = len(frames)
+    if len(outs) != n:
+        raise ValueError("one output per clip")
+    T, H, W, _ = frames[0].shape
+    fps = (ctypes.c_void_p * n)(*[_host_ptr(f, np.uint8, "frames").value for f in frames])
+    ops = (ctypes.c_void_p * n)(*[_host_ptr(o, np.uint8, "out").value for o in outs])
+    for f, o in zip(frames, outs):
+        if f.shape != (T, H, W, 3) or o.shape != (T, H, target_W, 3):
+            raise ValueError("clips of one shape, outputs [T,H,target_W,3]")
+    nbs = (ctypes.c_int * n)()
+    _check(h, load().scpl_carve_host_many(h, n, fps, T, H, W, int(target_W), int(k), ops, nbs))
+    return list(nbs)
 
 
 def scpl_enlarge(h, frames, target_W: int, k: int, out) -> np.ndarray:

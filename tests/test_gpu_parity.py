@@ -317,3 +317,23 @@ def test_carve_host_pipelined_matches_oracle(orc, lib, synth):
     assert np.array_equal(starts, ref_starts)
     assert np.array_equal(seams[: len(starts) - 1], ref_seams)
     assert np.array_equal(out, ref_out)
+
+
+def test_carve_host_many_equals_each_clip_alone(lib):
+    """Streamed host clips (two device slots, copies overlapping the
+    kernels): every clip's result equals scpl_carve_host on that clip."""
+    from paper_1903_03180_gb300 import synth
+    T, H, W, tw, k = 20, 64, 112, 84, 8
+    clips = [torch.from_numpy(synth.clip(T, H, W, seed=90 + i, cuts=(6, 12))).pin_memory().numpy()
+             for i in range(5)]
+    outs = [torch.zeros((T, H, tw, 3), dtype=torch.uint8).pin_memory().numpy() for _ in clips]
+    h = lib.scpl_create()
+    nbs = lib.scpl_carve_host_many(h, clips, tw, k, outs)
+    refs = []
+    for c in clips:
+        o = np.zeros((T, H, tw, 3), np.uint8)
+        refs.append((lib.scpl_carve_host(h, c, tw, k, o), o))
+    lib.scpl_destroy(h)
+    for i, (starts, ref) in enumerate(refs):
+        assert nbs[i] == len(starts) - 1
+        assert np.array_equal(outs[i], ref), i
