@@ -172,11 +172,6 @@ __global__ void __launch_bounds__(EN_QT) k_energy_init(CarveWs ws) {
 //      the staged rows), 16 frames per work item.
 constexpr unsigned long long UP_WAIT_NS = 2000000000ull;   // bound of the staging wait
 
-// Bulk prefetch of global memory into L2 (16-byte aligned, a multiple of 16 bytes).
-__device__ __forceinline__ void prefetch_l2_bulk(const void *p, unsigned bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int s_cnt;
@@ -292,32 +287,6 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
         if (tid == 0 && ws.dirty_count) atomicAdd(ws.dirty_count + b, (unsigned long long)cnt);
     }
     mbar_wait(&s_mbar, 0u, ws.err, UP_WAIT_NS);
-    if (need_e) {
-        // the changed pixels' neighbourhoods of the frame-minor luma are
-        // prefetched into L2 now, so that the recompute after the compaction
-        // finds them there: per pixel and neighbour row, the origins of the
-        // old columns within 2 of the pixel's source (origins increase along
-        // a row, so that is one contiguous range, capped at 8 pixels)
-        const uint8_t *yfm = ws.Yfm + st.yfm;
-        const int tp = st.tp;
-        for (int x = tid; x < cnt * 3; x += UP_THREADS) {
-            const int e = x / 3, a = x - e * 3;
-            const int r = (int)(list[e] >> 16), q = (int)(list[e] & 0xFFFFu);
-            const int xc = min(q - count_less(rl + (r + 1) * kcap, keff, q), Wn - 1);
-            const uint16_t *rr = rl + (r + a) * kcap;
-            int lo = 0, hi = keff;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if ((int)rr[mid] - mid <= xc) lo = mid + 1; else hi = mid;
-            }
-            const int src = xc + lo;   // old column of the pixel's column in row r+a
-            const uint16_t *orow = Os + (size_t)(r + a) * W8;
-            const int o0 = orow[max(src - 2, 0)], o1 = orow[min(src + 2, Wc - 1)];
-            const int n = min(o1 - o0 + 1, 8);
-            const int gi = clampi(i0 + r + a - 1, 0, H - 1);
-            if (n > 0) prefetch_l2_bulk(yfm + ((long)gi * ws.W0 + o0) * tp, (unsigned)(n * tp));
-        }
-    }
 
     // 1. compaction of the origin map and of the summed energy
     uint16_t *__restrict__ Oout = ws.O + ((long)b * 2 + s_out) * plane;
