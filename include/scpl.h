@@ -325,6 +325,10 @@ scpl_status scpl_tuning_set(const scpl_tuning *t);
 /* The recorded choice for (H, W): SCPL_OK, or SCPL_EINVAL if there is none. */
 scpl_status scpl_tuning_get(int H, int W, scpl_tuning *out);
 void scpl_tuning_clear(void);
+/* Copy up to max recorded choices into out (ordered by H, then W); returns
+ * how many the table holds (a caller can save them and restore them with
+ * scpl_tuning_set, e.g. as a tuning cache kept between processes). */
+int scpl_tuning_list(scpl_tuning *out, int max);
 /* on != 0: scpl_carve and scpl_carve_batch tune every size they meet for the
  * first time (once per process) before carving it. */
 scpl_status scpl_set_autotune(scpl_handle h, int on);

@@ -986,6 +986,8 @@ scpl_status scpl_tuning_get(int H, int W, scpl_tuning *out) {
 
 void scpl_tuning_clear(void) { tuning_clear(); }
 
+int scpl_tuning_list(scpl_tuning *out, int max) { return tuning_list(out, max < 0 ? 0 : max); }
+
 scpl_status scpl_set_autotune(scpl_handle h, int on) {
     if (!h) return SCPL_EINVAL;
     h->autotune = on != 0;

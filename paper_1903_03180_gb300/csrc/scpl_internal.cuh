@@ -280,6 +280,8 @@ cudaError_t launch_insert_seams(const uint8_t *frames, int H, int W, int target,
                                 const int16_t *seams, long seam_stride, int m,
                                 const int *starts, int nb, uint8_t *out, cudaStream_t s);
 
+int tuning_list(scpl_tuning *out, int max);
+
 // true if the table held a choice for (H, W) (then applied to ws)
 bool tuning_apply(int H, int W, CarveWs &ws, bool *use_dpc);
 scpl_status tune_class(int H, int W, int k, cudaStream_t s, scpl_tuning *out);

@@ -84,6 +84,16 @@ void tuning_clear() {
     g_table.clear();
 }
 
+int tuning_list(scpl_tuning *out, int max) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    int i = 0;
+    for (const auto &kv : g_table) {   // std::map: ordered by (H, W)
+        if (out && i < max) out[i] = kv.second;
+        ++i;
+    }
+    return i;
+}
+
 // Apply the recorded choice for (H, W), if any, to a workspace about to be
 // laid out: the cluster-DP layout (or the single-CTA DP) and the update rows.
 bool tuning_apply(int H, int W, CarveWs &ws, bool *use_dpc) {

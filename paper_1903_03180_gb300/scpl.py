@@ -99,6 +99,7 @@ SIGNATURES = {
     "scpl_tuning_set": (_I, [ctypes.POINTER(Tuning)]),
     "scpl_tuning_get": (_I, [_I, _I, ctypes.POINTER(Tuning)]),
     "scpl_tuning_clear": (None, []),
+    "scpl_tuning_list": (_I, [ctypes.POINTER(Tuning), _I]),
     "scpl_set_autotune": (_I, [_P, _I]),
     "scpl_server_set_autotune": (_I, [_P, _I]),
     "scpl_job_footprint": (ctypes.c_size_t, [ctypes.POINTER(Params), ctypes.POINTER(Job)]),
@@ -520,6 +521,33 @@ def scpl_tuning_get(H: int, W: int) -> dict | None:
     if load().scpl_tuning_get(H, W, ctypes.byref(t)) != SCPL_OK:
         return None
     return _tuning_dict(t)
+
+
+def scpl_tuning_list() -> list[dict]:
+    """Every recorded choice, ordered by (H, W)."""
+    n = load().scpl_tuning_list(None, 0)
+    arr = (Tuning * max(n, 1))()
+    n = min(n, load().scpl_tuning_list(arr, n))
+    return [_tuning_dict(arr[i]) for i in range(n)]
+
+
+def save_tuning(path: str):
+    """Write the tuning table to a JSON file (a tuning cache)."""
+    import json
+    with open(path, "w") as fh:
+        json.dump([{k: t[k] for k in ("H", "W", "dpc_halo", "dpc_warps", "dpc_lane_cols",
+                                      "update_rows")} for t in scpl_tuning_list()], fh, indent=1)
+
+
+def load_tuning(path: str) -> int:
+    """Restore choices saved by save_tuning; returns how many."""
+    import json
+    with open(path) as fh:
+        entries = json.load(fh)
+    for e in entries:
+        scpl_tuning_set(e["H"], e["W"], e["dpc_halo"], e["update_rows"], e["dpc_warps"],
+                        e["dpc_lane_cols"])
+    return len(entries)
 
 
 def scpl_tuning_clear():

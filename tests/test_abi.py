@@ -98,3 +98,25 @@ def test_tuning_table_host_only(lib):
     assert scpl.scpl_tuning_get(10, 20)["dpc_lane_cols"] == 2
     scpl.scpl_tuning_clear()
     assert scpl.scpl_tuning_get(10, 20) is None
+
+
+def test_tuning_cache_round_trip_host_only(lib, tmp_path):
+    """The tuning table lists its entries in (H, W) order, and a saved table
+    restores the same choices in a cleared one (a tuning cache)."""
+    from paper_1903_03180_gb300 import scpl
+    scpl.scpl_tuning_clear()
+    scpl.scpl_tuning_set(1080, 1920, 16, 4, 4, 2)
+    scpl.scpl_tuning_set(360, 640, 32, 2, 8, 4)
+    scpl.scpl_tuning_set(720, 1280, 0, 1)
+    got = [(t["H"], t["W"]) for t in scpl.scpl_tuning_list()]
+    assert got == [(360, 640), (720, 1280), (1080, 1920)]
+    path = tmp_path / "tuning.json"
+    scpl.save_tuning(str(path))
+    before = scpl.scpl_tuning_list()
+    scpl.scpl_tuning_clear()
+    assert scpl.scpl_tuning_list() == []
+    assert scpl.load_tuning(str(path)) == 3
+    after = scpl.scpl_tuning_list()
+    keys = ("H", "W", "dpc_halo", "dpc_warps", "dpc_lane_cols", "update_rows")
+    assert [{k: t[k] for k in keys} for t in after] == [{k: t[k] for k in keys} for t in before]
+    scpl.scpl_tuning_clear()
