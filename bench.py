@@ -377,6 +377,7 @@ def run_native(args) -> None:
     torch.cuda.synchronize()
     prof_ms = pev[0].elapsed_time(pev[1]) / args.steps
     stats = scpl.scpl_get_stats(h)
+    keff = np.concatenate(scpl.scpl_keff_log(h) or [np.zeros(0, np.int32)])
     scpl.scpl_set_profiling(h, False)
     total_ms = ev[0].elapsed_time(ev[-1])
     if dist:
@@ -472,6 +473,12 @@ def run_native(args) -> None:
                        "mean_buffer_frames": round(T / max(stats["n_buffers"], 1), 2),
                        "iterations_max": stats["iterations_max"],
                        "iterations_total": stats["iterations_total"],
+                       "keff_mean": round(float(keff.mean()), 2) if keff.size else None,
+                       "keff_histogram": {lbl: int(((keff >= lo) & (keff <= hi)).sum())
+                                          for lbl, lo, hi in (("1", 1, 1), ("2-4", 2, 4),
+                                                              ("5-8", 5, 8), ("9-16", 9, 16),
+                                                              ("17-32", 17, 32),
+                                                              (">32", 33, 1 << 30))},
                        "l2": "no flush: the clip (%.2f GB) and its luma are larger than the "
                              "129 MB L2" % (frames_np.nbytes / 1e9),
                        "parallelism": f"replicas{ws}"},

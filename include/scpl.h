@@ -287,6 +287,13 @@ typedef struct {
 } scpl_stats;
 
 scpl_status scpl_set_profiling(scpl_handle h, int on);
+/* The seams removed in every SCPL iteration of the last scpl_carve (or
+ * scpl_carve_host) on the handle: k_eff of buffer 0's iterations in order,
+ * then buffer 1's, and so on (Eq. 6: min(k, parents, remaining)).  Writes up
+ * to max entries to keff and, if iters is not NULL, each buffer's iteration
+ * count to iters [n_buffers]; returns the number of entries (-1 for a NULL
+ * handle). */
+int scpl_keff_log(scpl_handle h, int32_t *keff, int max, int32_t *iters);
 scpl_status scpl_get_stats(scpl_handle h, scpl_stats *out);
 
 /* ------------------------------------------------------------------------

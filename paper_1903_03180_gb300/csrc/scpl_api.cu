@@ -127,6 +127,7 @@ struct scpl_ctx {
     scpl_server_s *engine = nullptr;   // scpl_carve_batch's engine (created on first use)
     // summary of the last scpl_carve call
     int last_nb = 0, last_iter_max = 0;
+    std::vector<int> last_keff, last_iters;   // k_eff of every iteration, per buffer
     long long last_iter_total = 0;
     double last_carved_px = 0;
 };
@@ -485,6 +486,8 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
     h->last_iter_max = 0;
     h->last_iter_total = 0;
     h->last_carved_px = 0;
+    h->last_keff.clear();
+    h->last_iters.assign(nb, 0);
     if (remove > 0) {
         unsigned long long *hdirty = reinterpret_cast<unsigned long long *>(
             h->h_small.as<char>() + 64 + (((size_t)nb * sizeof(BufState) + (size_t)T * sizeof(int) +
@@ -501,6 +504,7 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
                 const int ke = hklog[(long)b * remove + it];
                 const int Wn = Wc - ke;
                 h->last_carved_px += (double)H * Wc;
+                h->last_keff.push_back(ke);
                 if (h->prof.on) {
                     // DP: E read, directions written and read back, lists written
                     h->prof.bytes[K_DP_SELECT] += H * (4.5 * Wc + 2.0 * ke);
@@ -516,6 +520,7 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
             }
             h->last_iter_max = std::max(h->last_iter_max, it);
             h->last_iter_total += it;
+            h->last_iters[b] = it;
             if (h->prof.on) {
                 // first iteration: luma and motion of every frame, O, SDo, E out
                 h->prof.bytes[K_ENERGY_INIT] += H * (2.0 * Tb * W + 10.0 * W);
@@ -985,6 +990,15 @@ scpl_status scpl_tuning_get(int H, int W, scpl_tuning *out) {
 }
 
 void scpl_tuning_clear(void) { tuning_clear(); }
+
+int scpl_keff_log(scpl_handle h, int32_t *keff, int max, int32_t *iters) {
+    if (!h) return -1;
+    const int n = (int)h->last_keff.size();
+    for (int i = 0; keff && i < n && i < max; ++i) keff[i] = h->last_keff[i];
+    if (iters)
+        for (int b = 0; b < (int)h->last_iters.size(); ++b) iters[b] = h->last_iters[b];
+    return n;
+}
 
 int scpl_tuning_list(scpl_tuning *out, int max) { return tuning_list(out, max < 0 ? 0 : max); }
 

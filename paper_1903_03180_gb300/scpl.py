@@ -93,6 +93,7 @@ SIGNATURES = {
     "scpl_carve_host": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
     "scpl_seams_noalloc": (_I, [_P, _I, _I, _I, _P, _P, _P]),
     "scpl_set_profiling": (_I, [_P, _I]),
+    "scpl_keff_log": (_I, [_P, _P, _I, _P]),
     "scpl_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
     "scpl_carve_batch": (_I, [_P, ctypes.POINTER(Job), _I]),
     "scpl_tune": (_I, [_P, _I, _I, _I, ctypes.POINTER(Tuning)]),
@@ -393,6 +394,21 @@ def scpl_seams_noalloc(energy, k: int, cols, stream=None) -> int:
         raise SCPLError(st, "scpl_seams_noalloc failed (sizes beyond its fixed scratch "
                             "give SCPL_EINVAL)")
     return ke.value
+
+
+def scpl_keff_log(h) -> list[np.ndarray]:
+    """k_eff of every iteration of the last carve, one int32 array per buffer."""
+    lib = load()
+    n = lib.scpl_keff_log(h, None, 0, None)
+    nb = scpl_get_stats(h)["n_buffers"]
+    keff = np.zeros(max(n, 1), np.int32)
+    iters = np.zeros(max(nb, 1), np.int32)
+    lib.scpl_keff_log(h, keff.ctypes.data_as(_P), n, iters.ctypes.data_as(_P))
+    out, o = [], 0
+    for b in range(nb):
+        out.append(keff[o:o + iters[b]].copy())
+        o += int(iters[b])
+    return out
 
 
 def scpl_set_profiling(h, on: bool):

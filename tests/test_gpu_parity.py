@@ -337,3 +337,20 @@ def test_carve_host_many_equals_each_clip_alone(lib):
     for i, (starts, ref) in enumerate(refs):
         assert nbs[i] == len(starts) - 1
         assert np.array_equal(outs[i], ref), i
+
+
+def test_keff_log_matches_oracle(orc, lib):
+    """The seams removed per iteration (Eq. 6: min(k, parents, remaining)),
+    buffer by buffer, equal the oracle's."""
+    from paper_1903_03180_gb300 import synth
+    f = synth.clip(9, 40, 90, seed=95, cuts=(4, 5))
+    r = lib.Retargeter()
+    _, starts, _ = r.carve(torch.from_numpy(f).cuda(), 60, 6)
+    log = lib.scpl_keff_log(r.h)
+    r.close()
+    D = orc.motion(f)
+    assert len(log) == len(starts) - 1
+    for b in range(len(starts) - 1):
+        t0, t1 = starts[b], starts[b + 1]
+        _, _, keff = orc.carve_buffer(f[t0:t1], D[t0:t1], 60, 6)
+        assert list(log[b]) == list(keff), b
