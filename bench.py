@@ -439,13 +439,17 @@ def run_native(args) -> None:
                 dt = float(t.item())
             return dt
 
+        ck = ClockSampler(gpu_id)
+        ck.start()
+        time.sleep(0.3)
         dt = timed_host(lambda: scpl.scpl_carve_host_many(
             h, [hin_np] * args.steps, target, k, [hout_np[i % 2] for i in range(args.steps)]))
+        e2e_clk = ck.stop()
         e2e = {"value": round(T * ws * args.steps / dt, 2), "unit": UNIT,
                "h2d_bytes_per_step": int(frames_np.nbytes),
                "d2h_bytes_per_step": int(hout_np[0].nbytes),
                "api": "scpl_carve_host_many: the steps' clips streamed through two device "
-                      "slots, copies overlapping the kernels"}
+                      "slots, copies overlapping the kernels", "clocks": e2e_clk}
         dt1 = timed_host(lambda: [scpl.scpl_carve_host(h, hin_np, target, k, hout_np[0])
                                   for _ in range(args.steps)])
         e2e_single = {"value": round(T * ws * args.steps / dt1, 2), "unit": UNIT,
