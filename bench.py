@@ -439,6 +439,21 @@ def run_native(args) -> None:
                 dt = float(t.item())
             return dt
 
+        # the machine's host<->device copy bandwidth right now (pinned, one stream
+        # each way), reported beside the end-to-end figures
+        dtmp = torch.empty_like(frames)
+        otmp = torch.empty((T, H, target, 3), dtype=torch.uint8, device="cuda")
+
+        def copy_gbs(dst, src):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            return src.numel() / (time.perf_counter() - t0) / 1e9
+
+        copy_bw = {"h2d_gbs": round(copy_gbs(dtmp, hin), 1),
+                   "d2h_gbs": round(copy_gbs(houts[0], otmp), 1)}
+        del dtmp, otmp
         ck = ClockSampler(gpu_id)
         ck.start()
         time.sleep(0.3)
@@ -449,7 +464,8 @@ def run_native(args) -> None:
                "h2d_bytes_per_step": int(frames_np.nbytes),
                "d2h_bytes_per_step": int(hout_np[0].nbytes),
                "api": "scpl_carve_host_many: the steps' clips streamed through two device "
-                      "slots, copies overlapping the kernels", "clocks": e2e_clk}
+                      "slots, copies overlapping the kernels", "clocks": e2e_clk,
+               "copy_bandwidth": copy_bw}
         dt1 = timed_host(lambda: [scpl.scpl_carve_host(h, hin_np, target, k, hout_np[0])
                                   for _ in range(args.steps)])
         e2e_single = {"value": round(T * ws * args.steps / dt1, 2), "unit": UNIT,
