@@ -103,3 +103,85 @@ def test_random_enlarge_matches_oracle(orc, lib, case):
     r.close()
     assert np.array_equal(starts, ref_starts)
     assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def _job_mix(r, n):
+    """n small jobs: sizes shared by some (so they group), width, height or both
+    reduced, mixed k."""
+    sizes = [(int(r.integers(2, 40)), int(r.integers(4, 120))) for _ in range(3)]
+    jobs = []
+    for j in range(n):
+        H, W = sizes[int(r.integers(0, len(sizes)))]
+        T = int(r.integers(1, 7))
+        tw = int(r.integers(2, W + 1)) if r.integers(0, 3) else W
+        th = int(r.integers(2, H + 1)) if r.integers(0, 3) else H
+        k = int(r.choice([1, 2, int(r.integers(3, 20))]))
+        jobs.append((T, H, W, tw, th, k, int(r.integers(0, 1 << 30))))
+    return jobs
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_batch_matches_oracle(orc, lib, seed):
+    from paper_1903_03180_gb300 import synth
+    r = np.random.default_rng(0xBA7C + seed)
+    spec = _job_mix(r, int(r.integers(3, 12)))
+    frames = [synth.clip(T, H, W, seed=s, cuts=(2, 3) if T >= 4 else None)
+              for (T, H, W, tw, th, k, s) in spec]
+    outs = [torch.zeros((T, th, tw, 3), dtype=torch.uint8, device="cuda")
+            for (T, H, W, tw, th, k, s) in spec]
+    dev = [torch.from_numpy(f).cuda() for f in frames]
+    jobs = [lib.make_job(dev[i], tw, th, k, outs[i]) for i, (T, H, W, tw, th, k, s)
+            in enumerate(spec)]
+    h = lib.scpl_create()
+    res = lib.scpl_carve_batch(h, jobs)
+    torch.cuda.synchronize()
+    lib.scpl_destroy(h)
+    for i, (T, H, W, tw, th, k, s) in enumerate(spec):
+        ref, _ = orc.carve_job(frames[i], tw, th, k)
+        assert res[i][0] == lib.SCPL_OK
+        assert np.array_equal(outs[i].cpu().numpy(), ref), (i, spec[i])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_server_order_and_cancels(orc, lib, seed):
+    """Jobs submitted at random points between scheduling rounds, some
+    cancelled: every job that completes OK equals the oracle, cancelled ones
+    report SCPL_ECANCELED, and nothing stays reserved."""
+    from paper_1903_03180_gb300 import synth
+    r = np.random.default_rng(0x5E4 + seed)
+    spec = _job_mix(r, 10)
+    frames = [synth.clip(T, H, W, seed=s) for (T, H, W, tw, th, k, s) in spec]
+    outs = [torch.zeros((T, th, tw, 3), dtype=torch.uint8, device="cuda")
+            for (T, H, W, tw, th, k, s) in spec]
+    dev = [torch.from_numpy(f).cuda() for f in frames]
+    srv = lib.Server(hbm_budget=int(r.integers(1, 4)) * 8 * 1024 * 1024)
+    tickets, done, cancelled = {}, {}, set()
+    for i, (T, H, W, tw, th, k, s) in enumerate(spec):
+        tickets[srv.submit(dev[i], tw, th, k, outs[i])] = i
+        for _ in range(int(r.integers(0, 3))):
+            srv.progress(wait=False)
+            for t, st in srv.poll():
+                done[tickets[t]] = st
+        if r.integers(0, 5) == 0:
+            victim = list(tickets)[int(r.integers(0, len(tickets)))]
+            try:
+                srv.cancel(victim)
+                cancelled.add(tickets[victim])
+            except lib.SCPLError:
+                pass
+    while len(done) < len(spec):
+        srv.progress(wait=True)
+        for t, st in srv.poll():
+            done[tickets[t]] = st
+    st = srv.stats()
+    srv.close()
+    assert st["reserved_bytes"] == 0
+    torch.cuda.synchronize()
+    for i, (T, H, W, tw, th, k, s) in enumerate(spec):
+        if done[i] == lib.SCPL_ECANCELED:
+            assert i in cancelled
+            continue
+        assert done[i] in (lib.SCPL_OK, lib.SCPL_ENOMEM), (i, done[i])
+        if done[i] == lib.SCPL_OK:
+            ref, _ = orc.carve_job(frames[i], tw, th, k)
+            assert np.array_equal(outs[i].cpu().numpy(), ref), (i, spec[i])
