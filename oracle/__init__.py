@@ -59,8 +59,11 @@ def _load():
     lib.orc_threshold.restype = dbl
     lib.orc_exceeds.argtypes = [i64, i32, i64, i32, i32, dbl]
     lib.orc_scan.argtypes = [P, i32, i32, i32, dbl, i32, i32, i64, P, P]
-    lib.orc_carve_buffer.argtypes = [P, P, i32, i32, i32, i32, i32, i32, i32, P, P, P]
-    lib.orc_carve.argtypes = [P, i32, i32, i32, i32, i32, i32, i32, dbl, i32, i32, i32, P, P, P, P]
+    lib.orc_forward_terms.argtypes = [P, i32, i32, P, P, P]
+    lib.orc_dp_fwd.argtypes = [P, P, P, i32, i32, i32, P, P, P]
+    lib.orc_carve_buffer.argtypes = [P, P, i32, i32, i32, i32, i32, i32, i32, i32, P, P, P]
+    lib.orc_carve.argtypes = [P, i32, i32, i32, i32, i32, i32, i32, i32, dbl, i32, i32, i32, P, P,
+                              P, P]
     _lib = lib
     return lib
 
@@ -122,6 +125,33 @@ def dp(E: np.ndarray):
     return CE, L, d
 
 
+def forward_terms(Y: np.ndarray):
+    """Forward terms of one luma frame [H,W] (R14, after the forward energy of
+    the related work, Sec. 2): (CU, A, B) int32, the luma differences a seam
+    creates in its own row (CU), and between rows i-1 and i when it arrives
+    from the upper left (A) or upper right (B)."""
+    Y = np.ascontiguousarray(Y, dtype=np.uint8)
+    H, W = Y.shape
+    CU, A, B = (np.empty((H, W), np.int32) for _ in range(3))
+    _check(_load().orc_forward_terms(_ptr(Y), H, W, _ptr(CU), _ptr(A), _ptr(B)))
+    return CU, A, B
+
+
+def dp_fwd(E: np.ndarray, A: np.ndarray, B: np.ndarray, wf: int):
+    """Eq. 4 with parental labels where the diagonal moves cost wf*A (from the
+    upper left) and wf*B (from the upper right) extra (R14).  E holds the
+    per-pixel part.  Returns (CE int64, labels int32, dir uint8)."""
+    E = np.ascontiguousarray(E, dtype=np.int32)
+    A = np.ascontiguousarray(A, dtype=np.int32)
+    B = np.ascontiguousarray(B, dtype=np.int32)
+    H, W = E.shape
+    CE = np.empty((H, W), np.int64)
+    L = np.empty((H, W), np.int32)
+    d = np.empty((H, W), np.uint8)
+    _check(_load().orc_dp_fwd(_ptr(E), _ptr(A), _ptr(B), wf, H, W, _ptr(CE), _ptr(L), _ptr(d)))
+    return CE, L, d
+
+
 def select(ce_last: np.ndarray, lab_last: np.ndarray, cap: int) -> np.ndarray:
     """Eq. 6 per-parent argmin, then the `cap` lowest by (CE, column)."""
     ce_last = np.ascontiguousarray(ce_last, dtype=np.int64)
@@ -180,15 +210,17 @@ def scan(e: np.ndarray, alpha: float = ALPHA, t_max: int = T_MAX, maxval_mode: i
 
 
 def carve_buffer(frames: np.ndarray, D: np.ndarray, target: int, k: int, wg: int = 1,
-                 wm: int = 2):
-    """Carve one fixed buffer (Sec. 3.1/3.2).  Returns (out, seams, k_eff list)."""
+                 wm: int = 2, wf: int = 0):
+    """Carve one fixed buffer (Sec. 3.1/3.2; forward terms of weight wf, R14).
+    Returns (out, seams, k_eff list)."""
     frames = np.ascontiguousarray(frames, dtype=np.uint8)
     D = np.ascontiguousarray(D, dtype=np.uint8)
     Tb, H, W0 = frames.shape[:3]
     out = np.empty((Tb, H, target, 3), np.uint8)
     seams = np.empty((max(W0 - target, 1), H), np.int16)
     keff = np.zeros(max(W0 - target, 1), np.int32)
-    n = _load().orc_carve_buffer(_ptr(frames), _ptr(D), Tb, H, W0, target, k, wg, wm, _ptr(out),
+    n = _load().orc_carve_buffer(_ptr(frames), _ptr(D), Tb, H, W0, target, k, wg, wm, wf,
+                                 _ptr(out),
                                  _ptr(seams), _ptr(keff))
     if n < 0:
         raise RuntimeError(f"oracle error {-n}")
@@ -197,8 +229,9 @@ def carve_buffer(frames: np.ndarray, D: np.ndarray, target: int, k: int, wg: int
 
 def carve(frames: np.ndarray, target: int, k: int, wg: int = 1, wm: int = 2,
           alpha: float = ALPHA, t_max: int = T_MAX, use_buffer: bool = True,
-          maxval_mode: int = 0):
-    """Whole clip: energy, buffer scan, per-buffer carving.
+          maxval_mode: int = 0, wf: int = 0):
+    """Whole clip: energy, buffer scan, per-buffer carving (with forward
+    terms of weight wf in the seam cost when wf > 0, R14).
 
     Returns (out [T,H,target,3], starts [n_buffers+1], seams [n_buffers, W0-target, H])."""
     frames = np.ascontiguousarray(frames, dtype=np.uint8)
@@ -207,7 +240,7 @@ def carve(frames: np.ndarray, target: int, k: int, wg: int = 1, wm: int = 2,
     starts = np.empty(T + 1, np.int32)
     nb = np.zeros(1, np.int32)
     seams = np.empty((T, max(W0 - target, 1), H), np.int16)
-    _check(_load().orc_carve(_ptr(frames), T, H, W0, target, k, wg, wm, alpha, t_max,
+    _check(_load().orc_carve(_ptr(frames), T, H, W0, target, k, wg, wm, wf, alpha, t_max,
                              int(use_buffer), maxval_mode, _ptr(out), _ptr(starts), _ptr(nb),
                              _ptr(seams)))
     n = int(nb[0])
@@ -216,7 +249,7 @@ def carve(frames: np.ndarray, target: int, k: int, wg: int = 1, wm: int = 2,
 
 def carve_job(frames: np.ndarray, target_W: int, target_H: int, k: int, wg: int = 1,
               wm: int = 2, alpha: float = ALPHA, t_max: int = T_MAX, use_buffer: bool = True,
-              maxval_mode: int = 0):
+              maxval_mode: int = 0, wf: int = 0):
     """A retarget job to target_H x target_W.  Seams are vertical or horizontal
     (Sec. 2).  The width is carved first with vertical seams (``carve``).  The
     height is then carved as vertical seams of the transposed result, with its
@@ -227,7 +260,7 @@ def carve_job(frames: np.ndarray, target_W: int, target_H: int, k: int, wg: int 
     T, H, W = frames.shape[:3]
     out, starts = frames, None
     kw = dict(wg=wg, wm=wm, alpha=alpha, t_max=t_max, use_buffer=use_buffer,
-              maxval_mode=maxval_mode)
+              maxval_mode=maxval_mode, wf=wf)
     if target_W < W:
         out, starts, _ = carve(out, target_W, k, **kw)
     if target_H < H:
@@ -275,7 +308,7 @@ def blend_sharpness(frames: np.ndarray, window: int = 4) -> tuple[int, int]:
 
 def enlarge(frames: np.ndarray, target: int, k: int, wg: int = 1, wm: int = 2,
             alpha: float = ALPHA, t_max: int = T_MAX, use_buffer: bool = True,
-            maxval_mode: int = 0):
+            maxval_mode: int = 0, wf: int = 0):
     """Widen a clip by seam insertion (Sec. 2 retargets in both directions;
     the insertion rule is Avidan & Shamir's).  To add m = target - W columns,
     the clip is carved to W - m by SCPL (``carve``); the m seams removed from
@@ -294,7 +327,7 @@ def enlarge(frames: np.ndarray, target: int, k: int, wg: int = 1, wm: int = 2,
     if m == 0:
         return frames.copy(), np.array([0, T], np.int32)
     _, starts, seams = carve(frames, W - m, k, wg=wg, wm=wm, alpha=alpha, t_max=t_max,
-                             use_buffer=use_buffer, maxval_mode=maxval_mode)
+                             use_buffer=use_buffer, maxval_mode=maxval_mode, wf=wf)
     out = np.empty((T, H, target, 3), np.uint8)
     for b in range(len(starts) - 1):
         t0, t1 = int(starts[b]), int(starts[b + 1])

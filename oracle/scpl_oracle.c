@@ -31,6 +31,14 @@
  *       Sec. 3.2 up to a positive factor, which changes no comparison).
  *   R9  carving: per iteration the gradient is recomputed on the carved frames,
  *       the motion term is carved along with the frames (Sec. 3.2, 3.3).
+ *   R14 forward energy (Sec. 2, the forward energy of the related work): the
+ *       cost of a seam is also charged, with integer weight wf, the luma
+ *       differences its removal creates between pixels that become neighbours,
+ *       summed over the buffer's frames.  Entering (i,j) costs the horizontal
+ *       term CU = |Y(i,j+1) - Y(i,j-1)| (0 in the first and last column, where
+ *       no pair is created); coming from (i-1,j-1) adds |Y(i-1,j) - Y(i,j-1)|,
+ *       from (i-1,j+1) adds |Y(i-1,j) - Y(i,j+1)|, from (i-1,j) nothing.  The
+ *       buffer scan keeps the backward energy e of Sec. 3.3.
  */
 #include <math.h>
 #include <stdint.h>
@@ -137,6 +145,59 @@ int orc_dp(const int32_t *E, int H, int W, int64_t *CE, int32_t *L, uint8_t *dir
             }
             long p = (long)i * W + j;
             CE[p] = (int64_t)E[p] + up[best_j];
+            L[p] = L[(long)(i - 1) * W + best_j];
+            dir[p] = (uint8_t)(best_j - j + 1);
+        }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------- */
+/* R14: forward terms of one luma frame [H][W]:
+ *   CU(i,j) = |Y(i,j+1) - Y(i,j-1)| for 0 < j < W-1, else 0
+ *   A(i,j)  = |Y(i-1,j) - Y(i,j-1)| for i >= 1 and j >= 1, else 0
+ *   B(i,j)  = |Y(i-1,j) - Y(i,j+1)| for i >= 1 and j <= W-2, else 0
+ * CU is the pair a seam through (i,j) joins in row i; A (B) the pair it joins
+ * between rows i-1 and i when it arrives from the upper left (right).        */
+int orc_forward_terms(const uint8_t *Y, int H, int W, int32_t *CU, int32_t *A, int32_t *B) {
+    if (H < 1 || W < 1) return ORC_EINVAL;
+    for (int i = 0; i < H; ++i) {
+        const uint8_t *r = Y + (long)i * W;
+        const uint8_t *u = i > 0 ? Y + (long)(i - 1) * W : NULL;
+        for (int j = 0; j < W; ++j) {
+            long p = (long)i * W + j;
+            CU[p] = (j > 0 && j < W - 1) ? abs((int)r[j + 1] - (int)r[j - 1]) : 0;
+            A[p] = (u && j >= 1) ? abs((int)u[j] - (int)r[j - 1]) : 0;
+            B[p] = (u && j <= W - 2) ? abs((int)u[j] - (int)r[j + 1]) : 0;
+        }
+    }
+    return ORC_OK;
+}
+
+/* R4/R5 with R14: the DP of Eq. 4 with parental labels where the move from
+ * (i-1,j-1) costs wf*A(i,j) extra and the move from (i-1,j+1) wf*B(i,j); E
+ * already holds the per-pixel part (backward energy + wf*CU).
+ *   CE(i,j) = E(i,j) + min( CE(i-1,j-1) + wf*A(i,j), CE(i-1,j), CE(i-1,j+1) + wf*B(i,j) )
+ * over the neighbours inside the row, lowest j' on ties, labels and
+ * indicators as in orc_dp.  With wf = 0 this is orc_dp.                      */
+int orc_dp_fwd(const int32_t *E, const int32_t *A, const int32_t *B, int wf, int H, int W,
+               int64_t *CE, int32_t *L, uint8_t *dir) {
+    if (H < 1 || W < 1) return ORC_EINVAL;
+    for (int j = 0; j < W; ++j) { CE[j] = E[j]; L[j] = j; dir[j] = 1; }
+    for (int i = 1; i < H; ++i) {
+        const int64_t *up = CE + (long)(i - 1) * W;
+        for (int j = 0; j < W; ++j) {
+            long p = (long)i * W + j;
+            int best_j = -1;
+            int64_t best = 0;
+            for (int jj = j - 1; jj <= j + 1; ++jj) {
+                if (jj < 0 || jj >= W) continue;
+                int64_t c = up[jj];
+                if (jj == j - 1) c += (int64_t)wf * A[p];
+                if (jj == j + 1) c += (int64_t)wf * B[p];
+                if (best_j < 0 || c < best) { best_j = jj; best = c; } /* lowest column on ties */
+            }
+            CE[p] = (int64_t)E[p] + best;
             L[p] = L[(long)(i - 1) * W + best_j];
             dir[p] = (uint8_t)(best_j - j + 1);
         }
@@ -307,8 +368,10 @@ int orc_scan(const int32_t *e, int T, int H, int W, double alpha, int t_max, int
  *   k_eff:  per-iteration seam counts (up to W0-target entries); may be NULL
  * Returns the number of iterations, or a negative error.                    */
 int orc_carve_buffer(const uint8_t *frames, const uint8_t *D, int Tb, int H, int W0, int target,
-                     int k, int wg, int wm, uint8_t *out, int16_t *seams, int32_t *k_eff_out) {
-    if (Tb < 1 || H < 1 || W0 < 1 || target < 1 || target > W0 || k < 1) return -ORC_EINVAL;
+                     int k, int wg, int wm, int wf, uint8_t *out, int16_t *seams,
+                     int32_t *k_eff_out) {
+    if (Tb < 1 || H < 1 || W0 < 1 || target < 1 || target > W0 || k < 1 || wf < 0)
+        return -ORC_EINVAL;
     long hw0 = (long)H * W0;
     uint8_t *rgb = (uint8_t *)malloc(3 * hw0 * Tb);   /* carved colour frames  */
     uint8_t *dm = (uint8_t *)malloc(hw0 * Tb);        /* carved motion maps    */
@@ -322,8 +385,15 @@ int orc_carve_buffer(const uint8_t *frames, const uint8_t *D, int Tb, int H, int
     uint8_t *kill = (uint8_t *)malloc(hw0);
     int32_t *cols = (int32_t *)malloc(sizeof(int32_t) * W0);
     int32_t *path = (int32_t *)malloc(sizeof(int32_t) * H);
+    /* R14: one frame's forward terms, and the buffer's sums of A and B */
+    int32_t *fcu = (int32_t *)malloc(sizeof(int32_t) * hw0);
+    int32_t *fa = (int32_t *)malloc(sizeof(int32_t) * hw0);
+    int32_t *fb = (int32_t *)malloc(sizeof(int32_t) * hw0);
+    int32_t *sa = (int32_t *)malloc(sizeof(int32_t) * hw0);
+    int32_t *sb = (int32_t *)malloc(sizeof(int32_t) * hw0);
     int rc = 0;
-    if (!rgb || !dm || !orig || !E || !G || !Y || !CE || !L || !dir || !kill || !cols || !path) {
+    if (!rgb || !dm || !orig || !E || !G || !Y || !CE || !L || !dir || !kill || !cols || !path ||
+        !fcu || !fa || !fb || !sa || !sb) {
         rc = -ORC_ENOMEM;
         goto done;
     }
@@ -337,12 +407,23 @@ int orc_carve_buffer(const uint8_t *frames, const uint8_t *D, int Tb, int H, int
         long hw = (long)H * W;
         /* uniform energy of the buffer at the current width (R8, R9) */
         memset(E, 0, sizeof(int32_t) * hw);
+        memset(sa, 0, sizeof(int32_t) * hw);
+        memset(sb, 0, sizeof(int32_t) * hw);
         for (int t = 0; t < Tb; ++t) {
             orc_luma(rgb + 3 * (long)t * hw, H, W, Y);
             orc_sobel(Y, H, W, G);
             for (long p = 0; p < hw; ++p) E[p] += wg * G[p] + wm * (int)dm[(long)t * hw + p];
+            if (wf > 0) {   /* R14, summed over the buffer like the energy (R8) */
+                orc_forward_terms(Y, H, W, fcu, fa, fb);
+                for (long p = 0; p < hw; ++p) {
+                    E[p] += wf * fcu[p];
+                    sa[p] += fa[p];
+                    sb[p] += fb[p];
+                }
+            }
         }
-        orc_dp(E, H, W, CE, L, dir);
+        if (wf > 0) orc_dp_fwd(E, sa, sb, wf, H, W, CE, L, dir);
+        else orc_dp(E, H, W, CE, L, dir);
         int cap = k < W - target ? k : W - target;
         int k_eff = orc_select(CE + (long)(H - 1) * W, L + (long)(H - 1) * W, W, cap, cols);
         if (k_eff < 1) { rc = -ORC_EINVAL; goto done; }
@@ -393,20 +474,22 @@ int orc_carve_buffer(const uint8_t *frames, const uint8_t *D, int Tb, int H, int
     rc = iters;
 done:
     free(rgb); free(dm); free(orig); free(E); free(G); free(Y); free(CE); free(L);
-    free(dir); free(kill); free(cols); free(path);
+    free(dir); free(kill); free(cols); free(path); free(fcu); free(fa); free(fb); free(sa);
+    free(sb);
     return rc;
 }
 
 /* ------------------------------------------------------------------------- */
 /* The whole clip: energy (Sec. 3.3), buffer scan (Sec. 3.2), then every fixed
- * buffer carved to `target` (Sec. 3.1/3.2).  use_buffer = 0 gives per-frame
+ * buffer carved to `target` (Sec. 3.1/3.2), with forward terms of weight wf
+ * in the seam cost when wf > 0 (R14).  use_buffer = 0 gives per-frame
  * SCPL (every frame its own buffer); with k = 1 that is classic seam carving
  * applied frame by frame (the paper's "raw" comparison).
  *   out:   [T][H][target][3]
  *   starts: [T+1] buffer starts, n_buffers receives the count
  *   seams: [n_buffers][W0-target][H] or NULL                                 */
 int orc_carve(const uint8_t *frames, int T, int H, int W0, int target, int k, int wg, int wm,
-              double alpha, int t_max, int use_buffer, int maxval_mode, uint8_t *out,
+              int wf, double alpha, int t_max, int use_buffer, int maxval_mode, uint8_t *out,
               int32_t *starts, int *n_buffers, int16_t *seams) {
     if (T < 1 || H < 1 || W0 < 1 || target < 1 || target > W0 || k < 1) return ORC_EINVAL;
     long hw = (long)H * W0;
@@ -423,7 +506,7 @@ int orc_carve(const uint8_t *frames, int T, int H, int W0, int target, int k, in
     for (int b = 0; rc == ORC_OK && b < *n_buffers; ++b) {
         int t0 = starts[b], tb = starts[b + 1] - starts[b];
         int it = orc_carve_buffer(frames + 3 * (long)t0 * hw, D + (long)t0 * hw, tb, H, W0, target,
-                                  k, wg, wm, out + 3 * (long)t0 * H * target,
+                                  k, wg, wm, wf, out + 3 * (long)t0 * H * target,
                                   seams ? seams + (long)b * (W0 - target) * H : NULL, NULL);
         if (it < 0) rc = -it;
     }

@@ -511,3 +511,108 @@ def test_enlarge_by_nothing_is_identity(orc):
     f = np.random.default_rng(53).integers(0, 256, (3, 5, 7, 3), dtype=np.uint8)
     out, starts = orc.enlarge(f, 7, 2)
     assert np.array_equal(out, f) and list(starts) == [0, 3]
+
+
+# ------------------------------------------------------ N3: forward energy (R14)
+def _inserted_luma(Y: np.ndarray, seam) -> int:
+    """Luma differences between the pixels that become neighbours when `seam`
+    (one column per row) is cut out of the luma frame Y: pairs that sit side by
+    side, or one above the other, in the carved frame but did not in Y."""
+    H, W = Y.shape
+    orig = [[j for j in range(W) if j != seam[i]] for i in range(H)]
+    total = 0
+    for i in range(H):
+        for c in range(W - 2):
+            a, b = orig[i][c], orig[i][c + 1]
+            if b - a != 1:
+                total += abs(int(Y[i, b]) - int(Y[i, a]))
+        if i > 0:
+            for c in range(W - 1):
+                a, b = orig[i - 1][c], orig[i][c]
+                if a != b:
+                    total += abs(int(Y[i - 1, a]) - int(Y[i, b]))
+    return total
+
+
+def _forward_cost(orc, f, seam, wg, wm, wf):
+    """Backward energy of the buffer along the seam plus wf times the luma
+    differences its removal creates in every frame."""
+    E = orc.energy(f, wg, wm).sum(0)
+    Y = [orc.luma(f[t]) for t in range(f.shape[0])]
+    return (int(sum(E[i, c] for i, c in enumerate(seam))) +
+            wf * sum(_inserted_luma(y, seam) for y in Y))
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_forward_seam_is_the_least_costly_of_all_seams(orc, seed):
+    """Brute force over every seam of a tiny buffer: the seam the forward DP
+    removes has the least backward energy plus wf times the differences its
+    removal really creates.  Half the cases carry no backward energy, so the
+    created differences alone decide; some use a coarse palette, which makes
+    ties common."""
+    r = np.random.default_rng(900 + seed)
+    T, H, W = int(r.integers(1, 4)), int(r.integers(2, 6)), int(r.integers(3, 8))
+    wg, wm, wf = int(r.integers(0, 3)), int(r.integers(0, 3)), int(r.integers(1, 4))
+    if seed % 2 == 0:
+        wg = wm = 0
+    levels = np.array([0, 60, 200, 255], np.uint8) if seed % 3 == 0 else np.arange(256, dtype=np.uint8)
+    f = levels[r.integers(0, len(levels), (T, H, W, 3))]
+    _, seams, _ = orc.carve_buffer(f, orc.motion(f), W - 1, 1, wg=wg, wm=wm, wf=wf)
+    best = min(_forward_cost(orc, f, s, wg, wm, wf) for s in tb.all_seams(H, W))
+    assert _forward_cost(orc, f, seams[0], wg, wm, wf) == best
+
+
+def test_forward_iterations_recompute_on_the_carved_frames(orc):
+    """k = 1 over four iterations: each removed seam is the least costly of the
+    frames as carved so far (brute force on the carved frames each time)."""
+    r = np.random.default_rng(911)
+    f = r.integers(0, 256, (2, 4, 7, 3), dtype=np.uint8)
+    out, seams, keff = orc.carve_buffer(f, np.zeros((2, 4, 7), np.uint8), 3, 1, wg=1, wm=0, wf=2)
+    assert list(keff) == [1, 1, 1, 1]
+    cur = f.copy()
+    orig = np.tile(np.arange(7), (4, 1))
+    for s in range(4):
+        W = cur.shape[2]
+        seam = [int(np.nonzero(orig[i] == seams[s, i])[0][0]) for i in range(4)]
+        best = min(_forward_cost(orc, cur, p, 1, 0, 2) for p in tb.all_seams(4, W))
+        assert _forward_cost(orc, cur, seam, 1, 0, 2) == best
+        keep = [[j for j in range(W) if j != seam[i]] for i in range(4)]
+        cur = np.stack([np.stack([cur[t, i, keep[i]] for i in range(4)]) for t in range(2)])
+        orig = np.stack([orig[i, keep[i]] for i in range(4)])
+    assert np.array_equal(cur, out)
+
+
+def test_forward_terms_of_a_ramp(orc):
+    """Y = 3j: the horizontal term is 6 inside and 0 in the border columns, each
+    diagonal move costs 3; with no backward energy the straight seam down the
+    first column creates no new pair and is removed."""
+    H, W = 5, 8
+    ramp = np.tile((np.arange(W) * 3).astype(np.uint8), (H, 1))
+    CU, A, B = orc.forward_terms(ramp)
+    assert (CU[:, 1:-1] == 6).all() and not CU[:, [0, -1]].any()
+    assert (A[1:, 1:] == 3).all() and (B[1:, :-1] == 3).all() and not A[0].any()
+    f = np.stack([ramp] * 3, -1)[None]   # grey, so the luma is the ramp itself
+    _, seams, _ = orc.carve_buffer(f, np.zeros((1, H, W), np.uint8), W - 1, 1, wg=0, wm=0, wf=1)
+    assert (seams[0] == 0).all()
+
+
+def test_forward_dp_with_zero_weight_is_the_plain_dp(orc):
+    r = np.random.default_rng(912)
+    E = r.integers(0, 50, (9, 13)).astype(np.int32)
+    A, B = (r.integers(0, 255, (9, 13)).astype(np.int32) for _ in range(2))
+    for x, y in zip(orc.dp_fwd(E, A, B, 0), orc.dp(E)):
+        assert np.array_equal(x, y)
+
+
+def test_forward_weight_shifts_seams_off_created_edges(orc):
+    """One frame, no backward energy: a dark vertical bar two columns wide in
+    a bright frame.  A seam through the bar joins bar and bright pixels, one
+    beside it joins only bright ones; the forward cost sees the difference."""
+    H, W = 6, 9
+    img = np.full((H, W), 200, np.uint8)
+    img[:, 3:5] = 20
+    f = np.stack([img] * 3, -1)[None]
+    _, seams, _ = orc.carve_buffer(f, np.zeros((1, H, W), np.uint8), W - 1, 1, wg=0, wm=0, wf=1)
+    s = seams[0]
+    assert _forward_cost(orc, f, s, 0, 0, 1) == 0
+    assert not np.isin(s, [2, 3, 4, 5]).any()
