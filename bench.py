@@ -126,14 +126,14 @@ def _dist():
     return ws, rank, local
 
 
-def cpu_baseline(name: str, frames: np.ndarray, n_frames: int) -> dict:
+def cpu_baseline(name: str, frames: np.ndarray, n_frames: int, wf: int = 0) -> dict:
     """The oracle as it stands (single thread) on the first `n_frames` frames
     of the workload: energy, buffer scan and carving of that sub-clip."""
     import oracle
     T, H, W, target, k, _, (wg, wm), use_buffer = WORKLOADS[name]
     sub = np.ascontiguousarray(frames[:n_frames])
     t0 = time.perf_counter()
-    oracle.carve(sub, target, k, wg=wg, wm=wm, use_buffer=use_buffer)
+    oracle.carve(sub, target, k, wg=wg, wm=wm, use_buffer=use_buffer, wf=wf)
     dt = time.perf_counter() - t0
     return {"value": round(len(sub) / dt, 4), "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"first {len(sub)} frames of {name} carved as one clip by the "
@@ -149,11 +149,11 @@ def _oracle_warm(_):
 def _oracle_carve(task):
     """One process of the all-cores oracle run: carve frames [a, b) of the
     memory-mapped workload as a clip of its own; returns the seconds taken."""
-    path, a, b, target, k, wg, wm, use_buffer = task
+    path, a, b, target, k, wg, wm, use_buffer, wf = task
     import oracle
     sub = np.ascontiguousarray(np.load(path, mmap_mode="r")[a:b])
     t0 = time.perf_counter()
-    oracle.carve(sub, target, k, wg=wg, wm=wm, use_buffer=use_buffer)
+    oracle.carve(sub, target, k, wg=wg, wm=wm, use_buffer=use_buffer, wf=wf)
     return time.perf_counter() - t0
 
 
@@ -162,11 +162,12 @@ class OraclePool:
     an independent sub-clip of the workload (clips are independent units of
     the method, so this is the oracle as it stands, run side by side)."""
 
-    def __init__(self, name: str, frames: np.ndarray, procs: int = 0):
+    def __init__(self, name: str, frames: np.ndarray, procs: int = 0, wf: int = 0):
         import multiprocessing as mp
         import oracle
         oracle.build()
         self.name = name
+        self.wf = wf
         self.T = frames.shape[0]
         self.procs = procs or os.cpu_count() or 1
         self.dir = tempfile.mkdtemp(prefix="scpl_oracle_")
@@ -179,8 +180,8 @@ class OraclePool:
         T, H, W, target, k, _, (wg, wm), use_buffer = WORKLOADS[self.name]
         n = max(1, min(n, self.T))
         span = max(self.T - n + 1, 1)
-        tasks = [(self.path, (p * n) % span, (p * n) % span + n, target, k, wg, wm, use_buffer)
-                 for p in range(self.procs)]
+        tasks = [(self.path, (p * n) % span, (p * n) % span + n, target, k, wg, wm, use_buffer,
+                  self.wf) for p in range(self.procs)]
         t0 = time.perf_counter()
         per = self.pool.map(_oracle_carve, tasks, chunksize=1)
         wall = time.perf_counter() - t0
@@ -230,8 +231,8 @@ def cpu_baseline_batch(specs: list, n_frames: int) -> dict:
             "one_core_note": "frames / summed per-process seconds, measured while all cores ran"}
 
 
-def cpu_baseline_all_cores(name: str, frames: np.ndarray, n_frames: int) -> dict:
-    pool = OraclePool(name, frames)
+def cpu_baseline_all_cores(name: str, frames: np.ndarray, n_frames: int, wf: int = 0) -> dict:
+    pool = OraclePool(name, frames, wf=wf)
     try:
         r = pool.run(n_frames)
     finally:
@@ -250,7 +251,7 @@ def run_reference(args) -> None:
     name = args.workload
     frames = make_frames(name)
     n = args.ref_frames
-    pool = OraclePool(name, frames, args.ref_procs)
+    pool = OraclePool(name, frames, args.ref_procs, wf=args.wf)
     try:
         for _ in range(args.warmup):
             pool.run(n)
@@ -269,7 +270,7 @@ def run_reference(args) -> None:
             "ms_per_step": round(1000 * total / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": name, "frames_per_step": n * pool.procs},
+            "config": {"workload": name, "frames_per_step": n * pool.procs, "wf": args.wf},
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": pool.procs,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -334,7 +335,7 @@ def run_native(args) -> None:
     frames = torch.from_numpy(frames_np).cuda()
     out = torch.empty((T, H, target, 3), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    r = scpl.Retargeter(wg=wg, wm=wm, use_buffer=use_buffer, stream=stream)
+    r = scpl.Retargeter(wg=wg, wm=wm, use_buffer=use_buffer, stream=stream, wf=args.wf)
     h = r.h
 
     for _ in range(max(args.warmup, 0)):
@@ -395,7 +396,7 @@ def run_native(args) -> None:
     bytes_per_launch = d["bytes"] / max(d["launches"], 1)
     achieved = bytes_per_launch / (avg_ms / 1000.0) / 1e9
     traffic = None
-    if dom == "k_dp":   # DRAM bytes per carved pixel of one ncu capture of k_dpc, scaled
+    if dom == "k_dp" and args.wf == 0:   # DRAM bytes per carved pixel of one ncu capture of k_dpc, scaled
         # carved_px covers the last clip; the launches cover every profiled step
         traffic = round(DP_DRAM_BYTES_PER_PX * stats["carved_px"] * args.steps /
                         max(d["launches"], 1))
@@ -473,8 +474,8 @@ def run_native(args) -> None:
 
     cpu = cpu1 = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu1 = cpu_baseline(name, frames_np, args.cpu_frames)
-        cpu = cpu_baseline_all_cores(name, frames_np, args.cpu_frames)
+        cpu1 = cpu_baseline(name, frames_np, args.cpu_frames, args.wf)
+        cpu = cpu_baseline_all_cores(name, frames_np, args.cpu_frames, args.wf)
     raw = None
     if rank == 0 and args.compare_raw:
         raw = raw_comparison(frames, frames_np, name, total_ms / args.steps,
@@ -488,7 +489,7 @@ def run_native(args) -> None:
             "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": name if not args.frames else f"{name}[:{T}]", "T": T, "H": H, "W": W, "target_W": target, "k": k,
-                       "seams": W - target, "wg": wg, "wm": wm, "alpha": 0.2,
+                       "seams": W - target, "wg": wg, "wm": wm, "wf": args.wf, "alpha": 0.2,
                        "use_buffer": use_buffer, "buffers": stats["n_buffers"],
                        "mean_buffer_frames": round(T / max(stats["n_buffers"], 1), 2),
                        "iterations_max": stats["iterations_max"],
@@ -854,6 +855,9 @@ def main():
                     help="batch: frames of each job the oracle carves for cpu_baseline")
     ap.add_argument("--frames", type=int, default=0,
                     help="carve only the first N frames of the workload (smaller profiling case)")
+    ap.add_argument("--wf", type=int, default=0,
+                    help="weight of the forward terms in the seam cost (0: the paper's "
+                         "backward energy)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -46,17 +46,30 @@ typedef enum {
  *  use_buffer   0: every frame is its own buffer (per-frame SCPL; with k = 1
  *               this is classic seam carving frame by frame).
  *  maxval_mode  Eq. 9's maxval: 0 = running maximum of the buffered energy
- *               maps, 1 = the energy function's maximum 255*(8*wg + wm).     */
+ *               maps, 1 = the energy function's maximum 255*(8*wg + wm).
+ *  wf           weight of the forward terms in the seam cost (0..255; 0 =
+ *               the paper's backward energy only).  With wf > 0 a seam also
+ *               pays, per frame of its buffer, wf times the luma differences
+ *               its removal creates between pixels that become neighbours
+ *               (the forward energy the paper's Sec. 2 names): in its own
+ *               row |Y(i,j+1) - Y(i,j-1)| (nothing in the first and last
+ *               column), and between rows i-1 and i |Y(i-1,j) - Y(i,j-1)|
+ *               when it arrives from the upper left, |Y(i-1,j) - Y(i,j+1)|
+ *               from the upper right.  The buffer scan (Eq. 7-9) keeps the
+ *               backward energy.  wf > 0 needs buffers of at most 256 frames
+ *               (t_max <= 256, or use_buffer 0) and carves with the
+ *               single-CTA DP.                                               */
 typedef struct {
     double alpha;
     int wg, wm;
     int t_max;
     int use_buffer;
     int maxval_mode;
+    int wf;
 } scpl_params;
 
 /* Fill p with the defaults: alpha 0.20, wg 1, wm 2, t_max 128, buffer on,
- * maxval_mode 0. */
+ * maxval_mode 0, wf 0. */
 void scpl_default_params(scpl_params *p);
 
 /* Create a handle bound to the current CUDA device and to `stream`

@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(EN_QT) k_energy_init(CarveWs ws) {
 //      the staged rows), 16 frames per work item.
 constexpr unsigned long long UP_WAIT_NS = 2000000000ull;   // bound of the staging wait
 
+template <bool FWD>
 __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
     extern __shared__ __align__(16) unsigned char smraw[];
     __shared__ int s_cnt;
@@ -205,6 +206,10 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
     int32_t *Es = reinterpret_cast<int32_t *>(smraw + off);      // [RB][W4] E of rows i0..
     off += (size_t)RB * W4 * 4;
     int *acc = reinterpret_cast<int *>(smraw + off);             // [list_cap] recomputed sums
+    // forward terms: the listed pixels' recomputed row terms and diagonal sums
+    constexpr bool fwd = FWD;
+    int *accu = acc + list_cap;                                  // [list_cap] (fwd only)
+    uint32_t *accp = reinterpret_cast<uint32_t *>(accu + list_cap);   // [list_cap] (fwd only)
     const uint16_t *rem = ws.rem + (long)b * H * kcap;
     const uint16_t *__restrict__ Oin = ws.O + ((long)b * 2 + s_in) * plane;
     const int32_t *__restrict__ Ein = ws.E + ((long)b * 2 + s_in) * plane;
@@ -284,6 +289,11 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
         __syncthreads();
         cnt = s_cnt;
         for (int e = tid; e < cnt; e += UP_THREADS) acc[e] = 0;
+        if constexpr (fwd)
+            for (int e = tid; e < cnt; e += UP_THREADS) {
+                accu[e] = 0;
+                accp[e] = 0;
+            }
         if (tid == 0 && ws.dirty_count) atomicAdd(ws.dirty_count + b, (unsigned long long)cnt);
     }
     mbar_wait(&s_mbar, 0u, ws.err, UP_WAIT_NS);
@@ -321,6 +331,13 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
         if (need_e) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) ev[j] = erow[src[j]];
+        }
+        if (fwd && need_e) {   // the diagonal sums move with their pixels
+            const uint32_t *prow = ws.P + ((long)b * 2 + s_in) * plane + roff;
+            uint32_t *pout = ws.P + ((long)b * 2 + s_out) * plane + roff;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (p0 + j < Wn) pout[p0 + j] = __ldg(prow + src[j]);
         }
         if (p0 + 8 <= Wn) {
             uint4 o4;
@@ -415,6 +432,21 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
             }
         }
         atomicAdd(&acc[e], (int)(packed & 0xFFFFu) + (int)(packed >> 16));
+        if (fwd) {
+            // forward terms of the group's 16 frames: left L = (i, p-1), right
+            // R = (i, p+1), above U = (i-1, p); the row term is 0 in the first
+            // and last column, the diagonal sums stay below 2^16 a pixel
+            const uint32_t *wL = w10, *wR = w12, *wU = w01;
+            uint32_t cu = 0, da = 0, db = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                cu += __vsadu4(wR[k], wL[k]);
+                da += __vsadu4(wU[k], wL[k]);
+                db += __vsadu4(wU[k], wR[k]);
+            }
+            if (p > 0 && p < Wn - 1) atomicAdd(&accu[e], (int)cu);
+            atomicAdd(&accp[e], da | (db << 16));
+        }
     }
     __syncthreads();
     for (int e = tid; e < cnt; e += UP_THREADS) {
@@ -422,8 +454,49 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
         const int i = i0 + r;
         const int p = q - count_less(rl + (r + 1) * kcap, keff, q);
         const int ocenter = Os[(size_t)(r + 1) * W8 + q];   // the pixel's own origin
-        Eout[(long)i * pitch + p] = ws.wg * acc[e] + SDo[(long)i * pitch + ocenter];
+        int ev = ws.wg * acc[e] + SDo[(long)i * pitch + ocenter];
+        if (fwd) {
+            ev += ws.wf * accu[e];
+            ws.P[((long)b * 2 + s_out) * plane + (long)i * pitch + p] = accp[e];
+        }
+        Eout[(long)i * pitch + p] = ev;
     }
+}
+
+// ---------------------------------------------------------------------------
+// k_forward_init: grid (ceil(W0 / FW_T), H, nb), FW_T threads, one pixel
+// each.  The forward terms of a buffer at its original width, summed over its
+// frames from the frame-minor luma copy, 16 frames per vector (per-byte
+// absolute differences added by __vsadu4; frames past the buffer are zero in
+// every pixel and add nothing): the row term CU = |Y(i,j+1) - Y(i,j-1)| (0 in
+// the first and last column) goes into E with weight wf, the diagonal terms
+// A = |Y(i-1,j) - Y(i,j-1)| and B = |Y(i-1,j) - Y(i,j+1)| into P.  Terms that
+// no move reads (A in column 0, B in the last column, both in row 0) come from
+// clamped neighbours.
+constexpr int FW_T = 128;
+
+__global__ void __launch_bounds__(FW_T) k_forward_init(CarveWs ws) {
+    const int b = blockIdx.z, i = blockIdx.y;
+    const int j = blockIdx.x * FW_T + threadIdx.x;
+    const int W0 = ws.W0;
+    if (j >= W0) return;
+    const BufState st = ws.st[b];
+    const int tp = st.tp;
+    const uint8_t *yfm = ws.Yfm + st.yfm;
+    const uint4 *L = reinterpret_cast<const uint4 *>(yfm + ((long)i * W0 + max(j - 1, 0)) * tp);
+    const uint4 *R = reinterpret_cast<const uint4 *>(yfm + ((long)i * W0 + min(j + 1, W0 - 1)) * tp);
+    const uint4 *U = reinterpret_cast<const uint4 *>(yfm + ((long)max(i - 1, 0) * W0 + j) * tp);
+    uint32_t cu = 0, da = 0, db = 0;
+    for (int g = 0; g < (tp >> 4); ++g) {
+        const uint4 l = __ldg(L + g), r = __ldg(R + g), u = __ldg(U + g);
+        cu += __vsadu4(r.x, l.x) + __vsadu4(r.y, l.y) + __vsadu4(r.z, l.z) + __vsadu4(r.w, l.w);
+        da += __vsadu4(u.x, l.x) + __vsadu4(u.y, l.y) + __vsadu4(u.z, l.z) + __vsadu4(u.w, l.w);
+        db += __vsadu4(u.x, r.x) + __vsadu4(u.y, r.y) + __vsadu4(u.z, r.z) + __vsadu4(u.w, r.w);
+    }
+    if (j == 0 || j == W0 - 1) cu = 0;
+    const long o = (long)b * 2 * ws.plane + (long)i * ws.pitch + j;   // slot 0
+    ws.E[o] += ws.wf * (int)cu;
+    ws.P[o] = da | (db << 16);
 }
 
 // ---------------------------------------------------------------------------
@@ -439,7 +512,11 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
 //
 // Directions: 2 bits per pixel, one u32 word per 4 rows x 4 columns:
 // word [i/4][j/4], bits 8*(i%4) + 2*(j%4).
-template <int V>
+//
+// FWD (forward terms): the move from the upper left also costs wf * A and
+// the move from the upper right wf * B, both read from the P plane of the
+// pixel; a neighbour outside the row (cost INF32) stays INF32.
+template <int V, bool FWD>
 __global__ void __launch_bounds__(DP_MAX_WARPS * 32, 1)
 k_dp(CarveWs ws, int k, int16_t *seams, long seam_stride, int band_blocks) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -467,6 +544,18 @@ k_dp(CarveWs ws, int k, int16_t *seams, long seam_stride, int band_blocks) {
     const int dstride = ws.dstride;
     uint32_t *dirs = ws.dirs + (long)b * ws.dbuf;
     const bool vec = ((pitch & 3) == 0) && ((reinterpret_cast<uintptr_t>(E) & 15) == 0);
+    const uint32_t *Pd = FWD ? ws.P + ((long)b * 2 + s_slot) * ws.plane : nullptr;
+    const uint32_t wf = FWD ? (uint32_t)ws.wf : 0u;
+    auto loadP = [&](int i, uint32_t (&dst)[V]) {   // the diagonal sums of row i
+#pragma unroll
+        for (int v = 0; v < V; ++v) dst[v] = 0;
+        if (FWD && i < H && base < W) {
+            const uint32_t *row = Pd + (long)i * pitch + base;
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (base + v < W) dst[v] = __ldcg(row + v);
+        }
+    };
 
     auto loadE = [&](int i, int (&dst)[V]) {
 #pragma unroll
@@ -504,6 +593,11 @@ k_dp(CarveWs ws, int k, int16_t *seams, long seam_stride, int band_blocks) {
     int ering[DP_PF][V];
 #pragma unroll
     for (int u = 0; u < DP_PF; ++u) loadE(1 + u, ering[u]);
+    uint32_t pring[FWD ? DP_PF : 1][V];
+    if constexpr (FWD) {
+#pragma unroll
+        for (int u = 0; u < DP_PF; ++u) loadP(1 + u, pring[u]);
+    }
     uint32_t dw[V / 4];
 #pragma unroll
     for (int g = 0; g < V / 4; ++g) dw[g] = 0;
@@ -531,10 +625,16 @@ k_dp(CarveWs ws, int k, int16_t *seams, long seam_stride, int band_blocks) {
                 uint32_t nc[V], nl[V];
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
-                    const uint32_t c0 = v == 0 ? lc : cost[v - 1];
+                    uint32_t c0 = v == 0 ? lc : cost[v - 1];
                     const uint32_t l0 = v == 0 ? ll : lab[v - 1];
-                    const uint32_t c2 = v == V - 1 ? rc : cost[v + 1];
+                    uint32_t c2 = v == V - 1 ? rc : cost[v + 1];
                     const uint32_t l2 = v == V - 1 ? rl : lab[v + 1];
+                    if constexpr (FWD) {
+                        // real cumulative costs stay below 2^31 (checked on the host)
+                        const uint32_t pw = pring[u][v];
+                        if (c0 < 0x80000000u) c0 += wf * (pw & 0xFFFFu);
+                        if (c2 < 0x80000000u) c2 += wf * (pw >> 16);
+                    }
                     uint32_t m = c0, l = l0, d = 0;
                     if (cost[v] < m) { m = cost[v]; l = lab[v]; d = 1; }
                     if (c2 < m) { m = c2; l = l2; d = 2; }
@@ -557,6 +657,7 @@ k_dp(CarveWs ws, int k, int16_t *seams, long seam_stride, int band_blocks) {
                 if (lane == 0) { bnd_c[i & 1][w][0] = cost[0]; bnd_l[i & 1][w][0] = lab[0]; }
                 if (lane == 31) { bnd_c[i & 1][w][1] = cost[V - 1]; bnd_l[i & 1][w][1] = lab[V - 1]; }
                 loadE(i + DP_PF, ering[u]);
+                if constexpr (FWD) loadP(i + DP_PF, pring[u]);
                 __syncthreads();
             }
         }
@@ -775,11 +876,17 @@ cudaError_t launch_dp_t(const CarveWs &ws, int nb, int k, int16_t *seams, long s
                         cudaStream_t s) {
     int band_blocks = 0;
     size_t smem = dp_smem_bytes(ws.W0, ws.H, &band_blocks);
-    cudaError_t e =
-        raise_dyn_smem((const void *)k_dp<V>, smem);
-    if (e != cudaSuccess) return e;
     const int nw = (ws.W0 + 32 * V - 1) / (32 * V);
-    k_dp<V><<<nb, 32 * nw, smem, s>>>(ws, k, seams, seam_stride, band_blocks);
+    if (ws.wf > 0) {
+        if (!ws.P) return cudaErrorInvalidValue;
+        cudaError_t e = raise_dyn_smem((const void *)k_dp<V, true>, smem);
+        if (e != cudaSuccess) return e;
+        k_dp<V, true><<<nb, 32 * nw, smem, s>>>(ws, k, seams, seam_stride, band_blocks);
+        return cudaGetLastError();
+    }
+    cudaError_t e = raise_dyn_smem((const void *)k_dp<V, false>, smem);
+    if (e != cudaSuccess) return e;
+    k_dp<V, false><<<nb, 32 * nw, smem, s>>>(ws, k, seams, seam_stride, band_blocks);
     return cudaGetLastError();
 }
 
@@ -804,23 +911,24 @@ size_t dp_smem_bytes(int W0, int H, int *band_blocks) {
 // Dynamic shared memory of a k_update CTA of `rb` rows: removal lists, the
 // changed-pixel bitmap and list, the staged origin and energy rows, and the
 // recomputed sums of the listed pixels.
-size_t update_smem_bytes_rows(int W0, int kcap, int rb) {
+size_t update_smem_bytes_rows(int W0, int kcap, int rb, bool fwd) {
     const size_t per_row_list = (size_t)(W0 < 15 * kcap ? W0 : 15 * kcap);
     const size_t nwords0 = (size_t)(W0 + 31) / 32;
     size_t off = (((size_t)(rb + 2) * kcap * 2 + 15) & ~(size_t)15) + (size_t)rb * nwords0 * 4;
     off = (off + (size_t)rb * per_row_list * 4 + 15) & ~(size_t)15;
     const size_t w8 = (size_t)(W0 + 7) & ~(size_t)7, w4 = (size_t)(W0 + 3) & ~(size_t)3;
-    return off + (size_t)(rb + 2) * w8 * 2 + (size_t)rb * w4 * 4 + (size_t)rb * per_row_list * 4;
+    return off + (size_t)(rb + 2) * w8 * 2 + (size_t)rb * w4 * 4 +
+           (size_t)rb * per_row_list * 4 * (fwd ? 3 : 1);
 }
 
 // Rows per k_update CTA (the most, up to 4, that keep five CTAs on an SM,
 // as many as its registers allow, so that the recompute's gathers keep the
 // L1 that shared memory would take; at least 1) and its dynamic shared
 // memory.
-size_t update_smem_bytes(int W0, int kcap, int *rows) {
+size_t update_smem_bytes(int W0, int kcap, int *rows, bool fwd) {
     int rb = 4;
-    size_t bytes = update_smem_bytes_rows(W0, kcap, rb);
-    while (rb > 1 && bytes > 44 * 1024) bytes = update_smem_bytes_rows(W0, kcap, --rb);
+    size_t bytes = update_smem_bytes_rows(W0, kcap, rb, fwd);
+    while (rb > 1 && bytes > 44 * 1024) bytes = update_smem_bytes_rows(W0, kcap, --rb, fwd);
     *rows = rb;
     return bytes;
 }
@@ -828,18 +936,26 @@ size_t update_smem_bytes(int W0, int kcap, int *rows) {
 cudaError_t launch_energy_init(const CarveWs &ws, int nb, cudaStream_t s) {
     dim3 grid((ws.W0 + 4 * EN_QT - 1) / (4 * EN_QT), ws.H, nb);
     k_energy_init<<<grid, EN_QT, 0, s>>>(ws);
+    if (ws.wf > 0) {
+        if (!ws.P) return cudaErrorInvalidValue;
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        k_forward_init<<<dim3((ws.W0 + FW_T - 1) / FW_T, ws.H, nb), FW_T, 0, s>>>(ws);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_update(const CarveWs &ws, int nb, cudaStream_t s) {
     int rb = 8;
-    size_t smem = update_smem_bytes(ws.W0, ws.kcap, &rb);
+    const bool fwd = ws.wf > 0;
+    if (fwd && !ws.P) return cudaErrorInvalidValue;
+    size_t smem = update_smem_bytes(ws.W0, ws.kcap, &rb, fwd);
     if (ws.up_rows >= 1 && ws.up_rows < rb) {
         rb = ws.up_rows;
-        smem = update_smem_bytes_rows(ws.W0, ws.kcap, rb);
+        smem = update_smem_bytes_rows(ws.W0, ws.kcap, rb, fwd);
     }
-    cudaError_t e =
-        raise_dyn_smem((const void *)k_update, smem);
+    const void *fn = fwd ? (const void *)k_update<true> : (const void *)k_update<false>;
+    cudaError_t e = raise_dyn_smem(fn, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((ws.H + rb - 1) / rb, nb);
@@ -851,7 +967,8 @@ cudaError_t launch_update(const CarveWs &ws, int nb, cudaStream_t s) {
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_update, ws, rb);
+    e = fwd ? cudaLaunchKernelEx(&cfg, k_update<true>, ws, rb)
+            : cudaLaunchKernelEx(&cfg, k_update<false>, ws, rb);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -968,6 +1085,7 @@ size_t carve_ws_assign(CarveWs &ws, int nb, int klog_stride, bool dpc, char *bas
         ws.colbot = reinterpret_cast<uint16_t *>(take((size_t)nb * ws.nbands * ws.kcap * 2));
         ws.dpx = reinterpret_cast<int *>(take((size_t)nb * (1 + ws.kcap) * 4));
     }
+    ws.P = ws.wf > 0 ? reinterpret_cast<uint32_t *>(take((size_t)nb * 2 * ws.plane * 4)) : nullptr;
     return off;
 }
 

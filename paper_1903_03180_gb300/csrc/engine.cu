@@ -106,19 +106,20 @@ size_t scan_state_bytes(const PassDims &d) {
 // k_energy_init from the luma and motion maps).
 int e0_planes(const PassDims &d) { return std::min(d.T, 4); }
 size_t e0_bytes(const PassDims &d) { return a256((size_t)e0_planes(d) * d.H * d.W * 4); }
-size_t item_bytes(const PassDims &d, int kcap) {
+size_t item_bytes(const PassDims &d, int kcap, int wf) {
     CarveWs ws{};
     ws.H = d.H;
     ws.W0 = d.W;
     ws.kcap = kcap;
+    ws.wf = wf;
     return carve_ws_assign(ws, 1, d.W - d.target, true, nullptr);
 }
-size_t pass_bytes(const PassDims &d, int k) {
+size_t pass_bytes(const PassDims &d, int k, int wf) {
     const size_t yp = (size_t)rup(d.W, 16);
     const size_t ypool = 2 * (size_t)d.T * d.H * yp;
     const size_t yfm = (size_t)d.H * d.W * rup(d.T, 16);
     const int kcap = std::max(1, std::min(k, d.W - d.target));
-    return ypool + e0_bytes(d) + scan_state_bytes(d) + item_bytes(d, kcap) + yfm +
+    return ypool + e0_bytes(d) + scan_state_bytes(d) + item_bytes(d, kcap, wf) + yfm +
            (size_t)d.T * 32;
 }
 
@@ -161,11 +162,11 @@ scpl_status check_job(const scpl_params &p, const scpl_job &j) {
     const long long tb = std::min<long long>(j.T, tmax_of(p));
     if (em >= 65536 || (long long)tmax_of(p) * em * em >= (1LL << 32)) return SCPL_EOVERFLOW;
     for (int i = 0; i < n; ++i) {
-        if (em * tb * d[i].H >= (1LL << 31)) return SCPL_EOVERFLOW;
+        if (dp_row_max(em, tb, p.wf) * d[i].H >= (1LL << 31)) return SCPL_EOVERFLOW;
         int bb = 0, rb = 0;
         const int kcap = std::max(1, std::min(j.k, d[i].W - d[i].target));
         if (dp_smem_bytes(d[i].W, d[i].H, &bb) > 227 * 1024 - 4096 ||
-            update_smem_bytes(d[i].W, kcap, &rb) > 200 * 1024)
+            update_smem_bytes(d[i].W, kcap, &rb, p.wf > 0) > 200 * 1024)
             return SCPL_EINVAL;
     }
     return SCPL_OK;
@@ -176,7 +177,7 @@ size_t footprint(const scpl_params &p, const scpl_job &j) {
     PassDims d[2];
     const int n = job_passes(j, d);
     size_t b = job_own_bytes(j);
-    for (int i = 0; i < n; ++i) b += pass_bytes(d[i], j.k);
+    for (int i = 0; i < n; ++i) b += pass_bytes(d[i], j.k, p.wf);
     return b;
 }
 
@@ -792,6 +793,8 @@ scpl_status setup_group(Srv *s, int gid) {
     bool use_dpc = true;
     // sizes were tuned when their wave finished
     const bool tuned = tuning_apply(G.H, G.W, ws, &use_dpc);
+    ws.wf = s->p.wf;   // forward terms: their planes and the single-CTA DP
+    if (ws.wf > 0) use_dpc = false;
     G.dpc = use_dpc && dpc_select(G.W, G.H, ws, tuned);
     const size_t ws_bytes = carve_ws_assign(ws, nb, klog, G.dpc, nullptr);
     // frames of every item, the gather table and the frame-minor luma
@@ -816,7 +819,7 @@ scpl_status setup_group(Srv *s, int gid) {
     for (int pid : ok) {
         Pass &P = s->passes[pid];
         const int kc = std::max(1, std::min(P.k, P.d.W - P.d.target));
-        const long long add = (long long)(P.nb - 1) * (long long)item_bytes(P.d, kc);
+        const long long add = (long long)(P.nb - 1) * (long long)item_bytes(P.d, kc, s->p.wf);
         extra += add;
     }
     // wait until memory frees up (admission pauses meanwhile), unless this
@@ -844,7 +847,7 @@ scpl_status setup_group(Srv *s, int gid) {
     for (int pid : ok) {
         Pass &P = s->passes[pid];
         const int kc = std::max(1, std::min(P.k, P.d.W - P.d.target));
-        const long long add = (long long)(P.nb - 1) * (long long)item_bytes(P.d, kc);
+        const long long add = (long long)(P.nb - 1) * (long long)item_bytes(P.d, kc, s->p.wf);
         s->jobs[P.job]->reserved += add;
         add_reserved(s, add);
         P.item = true;
@@ -1204,7 +1207,8 @@ scpl_status create(const scpl_params *p, size_t budget, void *stream, Srv **out)
     scpl_default_params(&def);
     if (!p) p = &def;
     if (!(p->alpha >= 0.0) || p->alpha > 1e6 || p->wg < 0 || p->wm < 0 || p->wg + p->wm == 0 ||
-        p->t_max < 1 || p->t_max > 1024 || (p->maxval_mode != 0 && p->maxval_mode != 1))
+        p->t_max < 1 || p->t_max > 1024 || (p->maxval_mode != 0 && p->maxval_mode != 1) ||
+        !forward_params_ok(*p))
         return SCPL_EINVAL;
     std::unique_ptr<Srv> s(new Srv());
     s->p = *p;
@@ -1426,7 +1430,7 @@ size_t scpl_job_footprint_per_buffer(const scpl_job *job) {
     const int n = job_passes(*job, d);
     size_t b = 0;
     for (int i = 0; i < n; ++i)
-        b = std::max(b, item_bytes(d[i], std::max(1, std::min(job->k, d[i].W - d[i].target))));
+        b = std::max(b, item_bytes(d[i], std::max(1, std::min(job->k, d[i].W - d[i].target)), 0));
     return b;
 }
 

@@ -177,6 +177,7 @@ scpl_status check_params(const scpl_params *p) {
     if (p->wg < 0 || p->wm < 0 || p->wg + p->wm == 0) return SCPL_EINVAL;
     if (p->t_max < 1 || p->t_max > 1024) return SCPL_EINVAL;
     if (p->maxval_mode != 0 && p->maxval_mode != 1) return SCPL_EINVAL;
+    if (!forward_params_ok(*p)) return SCPL_EINVAL;
     return SCPL_OK;
 }
 
@@ -191,9 +192,9 @@ scpl_status check_overflow(scpl_ctx *h, int T, int H) {
     long long em = energy_max(h->p);
     long long tb = std::min<long long>(T, effective_tmax(h->p));
     if (em >= 65536) return fail(h, SCPL_EOVERFLOW, "energy maximum %lld exceeds 16 bits", em);
-    if (em * tb * H >= (1LL << 31))
-        return fail(h, SCPL_EOVERFLOW, "cumulative energy %lld*%lld*%d can exceed 2^31", em, tb,
-                    H);
+    if (dp_row_max(em, tb, h->p.wf) * H >= (1LL << 31))
+        return fail(h, SCPL_EOVERFLOW, "cumulative energy %lld*%d can exceed 2^31",
+                    dp_row_max(em, tb, h->p.wf), H);
     if ((long long)effective_tmax(h->p) * em * em >= (1LL << 32))
         return fail(h, SCPL_EOVERFLOW, "t_max*emax^2 can exceed 2^32");
     return SCPL_OK;
@@ -291,7 +292,7 @@ scpl_status carve_ws(scpl_ctx *h, int nb, int H, int W0, int kcap, CarveWs &ws,
     ws.err = h->errw.as<int>();
     int bb = 0, rb = 0;
     if (dp_smem_bytes(W0, H, &bb) > 227 * 1024 - 4096 ||
-        update_smem_bytes(W0, ws.kcap, &rb) > 200 * 1024)
+        update_smem_bytes(W0, ws.kcap, &rb, h->p.wf > 0) > 200 * 1024)
         return fail(h, SCPL_EINVAL, "width %d exceeds the shared-memory limits", W0);
     // the tuned choice for this size (cluster-DP layout or the single-CTA DP,
     // update rows), measured first if autotuning is on; the default layout
@@ -304,6 +305,9 @@ scpl_status carve_ws(scpl_ctx *h, int nb, int H, int W0, int kcap, CarveWs &ws,
     if (h->autotune && !tuning_lookup(H, W0, nullptr))
         tune_class(H, W0, ws.kcap, h->stream, nullptr);   // on failure: the defaults
     const bool tuned = tuning_apply(H, W0, ws, &use_dpc);
+    // forward terms: the single-CTA DP and the planes of the terms
+    ws.wf = h->p.wf;
+    if (ws.wf > 0) use_dpc = false;
     // cluster DP (used when the GPU can co-schedule the cluster)
     const bool dpc = use_dpc && dpc_select(W0, H, ws, tuned);
     const size_t bytes = carve_ws_assign(ws, nb, klog_stride, dpc, nullptr);
@@ -497,6 +501,7 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
         SCPL_CUDA(h, cudaMemcpyAsync(hdirty, ws.dirty_count, (size_t)nb * sizeof(unsigned long long),
                                      cudaMemcpyDeviceToHost, st));
         SCPL_CUDA(h, cudaStreamSynchronize(st));
+        const bool fwd = h->p.wf > 0;
         for (int b = 0; b < nb; ++b) {
             const double Tb = hb[b].nt;
             int Wc = W, it = 0;
@@ -507,11 +512,13 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
                 h->last_keff.push_back(ke);
                 if (h->prof.on) {
                     // DP: E read, directions written and read back, lists written
-                    h->prof.bytes[K_DP_SELECT] += H * (4.5 * Wc + 2.0 * ke);
+                    // (forward terms: the diagonal sums read too)
+                    h->prof.bytes[K_DP_SELECT] += H * ((fwd ? 8.5 : 4.5) * Wc + 2.0 * ke);
                     // update: O and E read (gathered) and written at the new width,
                     // the removal lists of each row and its two neighbours
+                    // (forward terms: the diagonal sums as well)
                     if (Wn > target_W)
-                        h->prof.bytes[K_ENERGY_ITER] += H * (12.0 * Wn + 6.0 * ke);
+                        h->prof.bytes[K_ENERGY_ITER] += H * ((fwd ? 20.0 : 12.0) * Wn + 6.0 * ke);
                     else
                         h->prof.bytes[K_ENERGY_ITER] += H * (4.0 * Wn + 6.0 * ke);
                 }
@@ -523,9 +530,13 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
             h->last_iters[b] = it;
             if (h->prof.on) {
                 // first iteration: luma and motion of every frame, O, SDo, E out
-                h->prof.bytes[K_ENERGY_INIT] += H * (2.0 * Tb * W + 10.0 * W);
-                // recomputed pixels: 3 luma bytes of every frame, SDo read, E write
-                h->prof.bytes[K_ENERGY_ITER] += (double)hdirty[b] * (3.0 * Tb + 8.0);
+                // (forward terms: the frame-minor luma read back, E read and
+                // written again, the diagonal sums written)
+                h->prof.bytes[K_ENERGY_INIT] +=
+                    H * (2.0 * Tb * W + 10.0 * W) + (fwd ? H * (Tb * W + 12.0 * W) : 0.0);
+                // recomputed pixels: 3 luma bytes of every frame, SDo read, E
+                // write (and the diagonal sums)
+                h->prof.bytes[K_ENERGY_ITER] += (double)hdirty[b] * (3.0 * Tb + (fwd ? 12.0 : 8.0));
             }
         }
     }
@@ -557,6 +568,7 @@ void scpl_default_params(scpl_params *p) {
     p->t_max = 128;
     p->use_buffer = 1;
     p->maxval_mode = 0;
+    p->wf = 0;
 }
 
 scpl_status scpl_create(const scpl_params *p, void *stream, scpl_handle *out) {
@@ -753,6 +765,7 @@ scpl_status scpl_seams(scpl_handle h, const int32_t *energy, int H, int W, int k
     CarveWs ws;
     int kc = std::min(k, W);
     if ((s = carve_ws(h, 1, H, W, kc, ws)) != SCPL_OK) return s;
+    ws.wf = 0;   // a caller's energy map comes without frames: no forward terms
     cudaStream_t st = h->stream;
     SCPL_CUDA(h, cudaMemsetAsync(ws.err, 0, sizeof(int), st));
     SCPL_CUDA(h, cudaMemcpy2DAsync(ws.E, ws.pitch * sizeof(int32_t), energy,

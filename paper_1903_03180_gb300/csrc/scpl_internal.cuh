@@ -168,6 +168,12 @@ struct CarveWs {
     int up_rows;        // rows per k_update CTA (1, 2 or 4); 0: the largest that fits
     int *err;           // device status word (bounded waits)
     const int32_t *E0;  // summed energy planes [H][W0] from the scan (see BufState::e0)
+    // forward terms (wf > 0): E then also holds wf * sum_t CU, and P holds the
+    // buffer's sums of the two diagonal terms, A in the low and B in the high
+    // 16 bits; the DP charges wf * A (wf * B) for a move from the upper left
+    // (right)
+    int wf = 0;
+    uint32_t *P = nullptr;   // [nb][2][plane], slots as in E
 };
 
 constexpr int SCAN_FW = 8;   // frames per round of the buffer scan
@@ -296,6 +302,19 @@ scpl_status engine_stats(scpl_server_s *eng, scpl_server_stats *out);
 // with a larger launch of the same kernel stays launchable.
 cudaError_t raise_dyn_smem(const void *func, size_t bytes);
 size_t dp_smem_bytes(int W0, int H, int *band_blocks);
-size_t update_smem_bytes(int W0, int kcap, int *rows);
+size_t update_smem_bytes(int W0, int kcap, int *rows, bool fwd = false);
+
+// Forward terms: wf in [0, 255]; with wf > 0 a buffer holds at most 256
+// frames, so a pixel's sums of the diagonal terms (255 a frame) fit 16 bits.
+inline bool forward_params_ok(const scpl_params &p) {
+    if (p.wf < 0 || p.wf > 255) return false;
+    return p.wf == 0 || (p.use_buffer ? p.t_max : 1) <= 256;
+}
+// Largest step of a column's cumulative energy from one row to the next:
+// the summed energy of tb frames plus, with forward terms, wf times the row's
+// term and a diagonal term (255 each a frame).
+inline long long dp_row_max(long long emax, long long tb, int wf) {
+    return emax * tb + 2LL * 255 * wf * tb;
+}
 
 }  // namespace scpl

@@ -27,10 +27,11 @@ _P, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
 
 
 class Params(ctypes.Structure):
-    """scpl_params (Sec. 3.2 alpha, Sec. 3.3 weights, buffer cap and mode)."""
+    """scpl_params (Sec. 3.2 alpha, Sec. 3.3 weights, buffer cap and mode, and
+    the weight of the forward terms in the seam cost)."""
     _fields_ = [("alpha", ctypes.c_double), ("wg", ctypes.c_int), ("wm", ctypes.c_int),
                 ("t_max", ctypes.c_int), ("use_buffer", ctypes.c_int),
-                ("maxval_mode", ctypes.c_int)]
+                ("maxval_mode", ctypes.c_int), ("wf", ctypes.c_int)]
 
 
 class KernelStat(ctypes.Structure):
@@ -435,10 +436,10 @@ class Retargeter:
     device."""
 
     def __init__(self, alpha: float = 0.20, wg: int = 1, wm: int = 2, t_max: int = 128,
-                 use_buffer: bool = True, maxval_mode: int = 0, stream=None):
+                 use_buffer: bool = True, maxval_mode: int = 0, stream=None, wf: int = 0):
         p = scpl_default_params()
         p.alpha, p.wg, p.wm, p.t_max = alpha, wg, wm, t_max
-        p.use_buffer, p.maxval_mode = int(use_buffer), maxval_mode
+        p.use_buffer, p.maxval_mode, p.wf = int(use_buffer), maxval_mode, wf
         self.params = p
         self.h = scpl_create(p, stream)
 

@@ -45,7 +45,37 @@ def test_binding_covers_the_header(lib):
 def test_default_params_host_only(lib):
     from paper_1903_03180_gb300 import scpl
     p = scpl.scpl_default_params()
-    assert (p.alpha, p.wg, p.wm, p.t_max, p.use_buffer, p.maxval_mode) == (0.2, 1, 2, 128, 1, 0)
+    assert (p.alpha, p.wg, p.wm, p.t_max, p.use_buffer, p.maxval_mode, p.wf) == \
+        (0.2, 1, 2, 128, 1, 0, 0)
+
+
+def test_forward_params_are_checked_without_a_gpu(lib):
+    """Forward terms: wf in [0, 255], and buffers of at most 256 frames, so a
+    pixel's diagonal sums fit 16 bits; the check comes before any CUDA call."""
+    import ctypes
+    from paper_1903_03180_gb300 import scpl
+    for wf, t_max, use_buffer in [(256, 128, 1), (-1, 128, 1), (1, 257, 1)]:
+        p = scpl.scpl_default_params()
+        p.wf, p.t_max, p.use_buffer = wf, t_max, use_buffer
+        h = ctypes.c_void_p()
+        assert lib.scpl_create(ctypes.byref(p), None, ctypes.byref(h)) == scpl.SCPL_EINVAL
+        srv = ctypes.c_void_p()
+        assert lib.scpl_server_create(ctypes.byref(p), 0, None, ctypes.byref(srv)) == \
+            scpl.SCPL_EINVAL
+
+
+def test_forward_footprint_adds_the_diagonal_planes(lib):
+    """With forward terms a buffer's workspace holds two more 32-bit planes
+    (the diagonal sums of both slots), padded rows as the energy planes."""
+    from paper_1903_03180_gb300 import scpl
+    j = scpl.Job()
+    j.frames, j.out = 1, 1   # never dereferenced
+    j.T, j.H, j.W, j.target_W, j.target_H, j.k = 16, 270, 481, 400, 270, 8
+    p = scpl.scpl_default_params()
+    base = scpl.scpl_job_footprint(p, j)
+    p.wf = 3
+    pitch = (481 + 31) // 32 * 32
+    assert scpl.scpl_job_footprint(p, j) - base == 2 * 270 * pitch * 4
 
 
 def test_null_handle_is_rejected_without_a_gpu(lib):
