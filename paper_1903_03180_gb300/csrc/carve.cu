@@ -1054,7 +1054,8 @@ size_t carve_ws_assign(CarveWs &ws, int nb, int klog_stride, bool dpc, char *bas
         if (ws.dpc_r != 16 && ws.dpc_r != 32) ws.dpc_r = 32;
         if (ws.dpc_wpc != 8) ws.dpc_wpc = 4;
         if (ws.dpc_v != 2 || ws.dpc_r != 16) ws.dpc_v = 4;
-        if (!dpc_plan(W0, H, ws.dpc_r, ws.dpc_wpc, ws.dpc_v, &C, &rj, &smem)) dpc = false;
+        if (!dpc_plan(W0, H, ws.dpc_r, ws.dpc_wpc, ws.dpc_v, &C, &rj, &smem, ws.wf > 0))
+            dpc = false;
         else {
             ws.rj = rj;
             ws.nbands = (H + rj - 1) / rj;

@@ -19,6 +19,12 @@
 // so two warps can share an SM sub-partition and fill each other's dependency
 // stalls.
 //
+// Forward terms (FWD): each stage also brings the 16 x 32V box of the P plane
+// (the pixel's summed diagonal terms A | B << 16) by TMA on the same mbarrier,
+// and the moves from the upper left and right cost wf * A and wf * B more.
+// Outside [0, W) both are taken as 0, so a column next to a real one still
+// ends up at 2^31 or more.
+//
 // Columns outside [0, W) carry energy 2^31: a real cumulative energy is below
 // 2^31 (checked on the host), so the column next to a real one always ends up
 // at 2^31 or more and is never chosen, whatever lies further out.  Among equal
@@ -67,13 +73,17 @@ __host__ __device__ constexpr int dpc_ww(int V) { return 32 * V; }   // a warp's
 __host__ __device__ constexpr int dpc_oww(int R, int V) { return dpc_ww(V) - 2 * R; }
 // energy stages in flight per warp (8 warps of 128-column windows keep 2 to
 // fit shared memory)
-__host__ __device__ constexpr int dpc_nst(int WPC, int V) { return WPC == 8 && V == 4 ? 2 : 4; }
+// (8 warps of 128-column windows, or 4 with the forward terms' second ring,
+// keep 2 to fit shared memory)
+__host__ __device__ constexpr int dpc_nst(int WPC, int V, bool FWD = false) {
+    return V == 4 && (WPC == 8 || FWD) ? 2 : 4;
+}
 __host__ __device__ constexpr int dpc_lmax(int R, int WPC, int V) { return WPC * dpc_oww(R, V); }
 __host__ __device__ constexpr size_t dpc_wslot(int V) {   // one warp's stage: 8 or 4 KB
     return (size_t)DPC_S * dpc_ww(V) * 4;
 }
-__host__ __device__ constexpr size_t dpc_ring(int WPC, int V) {
-    return (size_t)WPC * dpc_nst(WPC, V) * dpc_wslot(V);
+__host__ __device__ constexpr size_t dpc_ring(int WPC, int V, bool FWD = false) {
+    return (size_t)WPC * dpc_nst(WPC, V, FWD) * dpc_wslot(V);   // per plane
 }
 constexpr size_t DPC_STAGE_BUDGET = 96 * 1024;   // trace-back staging
 constexpr uint32_t BIG = 0x80000000u;            // energy of columns outside [0, W)
@@ -166,16 +176,16 @@ __device__ __forceinline__ bool mbar_wait_cluster(uint64_t *mbar, unsigned parit
     return true;
 }
 
-template <int R, int WPC, int V>
+template <int R, int WPC, int V, bool FWD>
 __global__ void __launch_bounds__(WPC * 32, 1)
-k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams,
-      long seam_stride) {
+k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmP,
+      CarveWs ws, int k, int16_t *seams, long seam_stride) {
     static_assert((V == 4 && (R == 16 || R == 32)) || (V == 2 && R == 16), "window layout");
     constexpr int DPC_V = V;                      // columns per lane
     constexpr int DPC_WW = dpc_ww(V);             // columns of a warp's window
     constexpr size_t DPC_WSLOT = dpc_wslot(V);    // bytes of one warp's stage
     constexpr int DPC_WPC = WPC;                  // warps per CTA
-    constexpr int DPC_NST = dpc_nst(WPC, V);      // energy stages in flight per warp
+    constexpr int DPC_NST = dpc_nst(WPC, V, FWD); // energy stages in flight per warp
     constexpr int DPC_R = R;                      // rows between halo refreshes (= halo width)
     constexpr int DPC_SPR = DPC_R / DPC_S;        // stages per refresh
     constexpr int DPC_HL = DPC_R / DPC_V;         // halo lanes on each side of a warp
@@ -226,15 +236,22 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
     // ---- per-warp energy ring: stage s holds rows 1+16s .. 16+16s of the
     //      warp's 128-column window ---------------------------------------------
     uint32_t *wring = reinterpret_cast<uint32_t *>(smraw) + (size_t)w * DPC_NST * DPC_S * DPC_WW;
+    // forward terms: the P boxes, in a second ring after the energy ring
+    uint32_t *pring = reinterpret_cast<uint32_t *>(smraw + dpc_ring(WPC, V, FWD)) +
+                      (size_t)w * DPC_NST * DPC_S * DPC_WW;
+    const uint32_t wfw = FWD ? (uint32_t)ws.wf : 0u;
     const int wx = g * DPC_OWW - DPC_R;   // first column of the warp's window
     const int zplane = b * 2 + slot;
     const int nstages = (H - 1 + DPC_S - 1) / DPC_S;
     auto issue = [&](int s) {   // lane 0 of the warp
         if (s >= nstages) return;
         uint64_t *mb = &mring[w][s % DPC_NST];
-        mbar_expect_tx(mb, (unsigned)DPC_WSLOT);
+        mbar_expect_tx(mb, (unsigned)DPC_WSLOT * (FWD ? 2u : 1u));
         tma_load_3d(wring + (size_t)(s % DPC_NST) * DPC_S * DPC_WW, &tmE, wx, 1 + s * DPC_S,
                     zplane, mb);
+        if constexpr (FWD)
+            tma_load_3d(pring + (size_t)(s % DPC_NST) * DPC_S * DPC_WW, &tmP, wx, 1 + s * DPC_S,
+                        zplane, mb);
     };
     // halo bytes a warp receives per refresh: 32 costs and 32 labels per neighbour
     const unsigned in_bytes =
@@ -301,6 +318,7 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
     auto stage_rows = [&](int s, auto guarded) {
         constexpr bool GUARD = decltype(guarded)::value;
         const uint32_t *rs = wring + (size_t)(s % DPC_NST) * DPC_S * DPC_WW + lane * DPC_V;
+        const uint32_t *ps = pring + (size_t)(s % DPC_NST) * DPC_S * DPC_WW + lane * DPC_V;
         const int ibase = 1 + DPC_S * s;
         const bool band_edge = ((ibase + DPC_S - 1) % RJ) == 0;   // row 16s+16 starts a band
 #pragma unroll
@@ -319,6 +337,20 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
                     e[0] = valid[0] ? ev.x : BIG;
                     e[1] = valid[1] ? ev.y : BIG;
                 }
+                [[maybe_unused]] uint32_t pw[DPC_V];   // forward terms of the row's pixels (0 outside [0, W))
+                if constexpr (FWD) {
+                    if constexpr (V == 4) {
+                        const uint4 pv = *reinterpret_cast<const uint4 *>(ps + ro * DPC_WW);
+                        pw[0] = valid[0] ? pv.x : 0u;
+                        pw[1] = valid[1] ? pv.y : 0u;
+                        pw[2] = valid[2] ? pv.z : 0u;
+                        pw[3] = valid[3] ? pv.w : 0u;
+                    } else {
+                        const uint2 pv = *reinterpret_cast<const uint2 *>(ps + ro * DPC_WW);
+                        pw[0] = valid[0] ? pv.x : 0u;
+                        pw[1] = valid[1] ? pv.y : 0u;
+                    }
+                }
                 const uint32_t lc = __shfl_up_sync(0xffffffffu, cost[DPC_V - 1], 1);
                 const uint32_t ll = __shfl_up_sync(0xffffffffu, lab[DPC_V - 1], 1);
                 const uint32_t rc = __shfl_down_sync(0xffffffffu, cost[0], 1);
@@ -326,10 +358,16 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
                 uint32_t nc[DPC_V], nl[DPC_V], dbyte = 0;
 #pragma unroll
                 for (int v = 0; v < DPC_V; ++v) {
-                    const uint32_t c0 = v == 0 ? lc : cost[v - 1];
+                    uint32_t c0 = v == 0 ? lc : cost[v - 1];
                     const uint32_t l0 = v == 0 ? ll : lab[v - 1];
-                    const uint32_t c2 = v == DPC_V - 1 ? rc : cost[v + 1];
+                    uint32_t c2 = v == DPC_V - 1 ? rc : cost[v + 1];
                     const uint32_t l2 = v == DPC_V - 1 ? rl : lab[v + 1];
+                    if constexpr (FWD) {
+                        // real cumulative costs with a move's term stay below
+                        // 2^31 (checked on the host); 2^31 and up stays put
+                        if (c0 < BIG) c0 += wfw * (pw[v] & 0xFFFFu);
+                        if (c2 < BIG) c2 += wfw * (pw[v] >> 16);
+                    }
                     // the cost chain is two integer mins; the first index that
                     // attains the minimum (lowest column) is chosen off the chain
                     const uint32_t m = __vimin3_u32(c0, cost[v], c2);
@@ -633,13 +671,13 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, CarveWs ws, int k, int16_t *seams
     }
 }
 
-size_t dpc_smem(int W0, int H, int rj, int kcap, int C, int R, int WPC, int V) {
+size_t dpc_smem(int W0, int H, int rj, int kcap, int C, int R, int WPC, int V, bool fwd) {
     const int nb = (H + rj - 1) / rj;
     const int jstride = (W0 + 7) & ~7;
     const int dstride = (((W0 + 3) / 4) + 3) & ~3;
     const PostLayout PL(W0, C, kcap, nb, jstride, dstride, dpc_lmax(R, WPC, V));
     const WalkLayout WL(kcap, (nb + C - 1) / C);
-    size_t m = dpc_ring(WPC, V);
+    size_t m = dpc_ring(WPC, V, fwd) * (fwd ? 2 : 1);
     m = PL.end > m ? PL.end : m;
     m = WL.end > m ? WL.end : m;
     return m;
@@ -663,24 +701,27 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
     return fn;
 }
 
-// 3-D view of E ([nb*2 planes][H][pitch] int32) with 16-row x 32V-column boxes.
-bool make_energy_map(const CarveWs &ws, int nb, int V, CUtensorMap *m) {
+// 3-D view of E, or of P ([nb*2 planes][H][pitch], 32-bit) with 16-row x
+// 32V-column boxes.
+bool make_energy_map(const CarveWs &ws, const void *plane0, int nb, int V, CUtensorMap *m) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
     if (!fn) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)ws.pitch, (cuuint64_t)ws.H, (cuuint64_t)nb * 2};
     const cuuint64_t strides[2] = {(cuuint64_t)ws.pitch * 4, (cuuint64_t)ws.plane * 4};
     const cuuint32_t box[3] = {(cuuint32_t)dpc_ww(V), DPC_S, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, ws.E, dims, strides, box, estr,
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT32, 3, const_cast<void *>(plane0), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace
 
-bool dpc_plan(int W0, int H, int R, int WPC, int V, int *ctas, int *rj, size_t *smem) {
+bool dpc_plan(int W0, int H, int R, int WPC, int V, int *ctas, int *rj, size_t *smem, bool fwd) {
     if ((R != 16 && R != 32) || (WPC != 4 && WPC != 8) || (V != 4 && V != 2)) return false;
     if (V == 2 && R != 16) return false;
+    // forward terms: the layouts built with them (R16 x 4 x 2, R32 x 4 x 4)
+    if (fwd && !(WPC == 4 && ((R == 16 && V == 2) || (R == 32 && V == 4)))) return false;
     const int nwarps = (W0 + dpc_oww(R, V) - 1) / dpc_oww(R, V);
     const int C = (nwarps + WPC - 1) / WPC;
     if (C > 16) return false;
@@ -688,10 +729,10 @@ bool dpc_plan(int W0, int H, int R, int WPC, int V, int *ctas, int *rj, size_t *
     int r = (H + 4 * C - 1) / (4 * C);
     r = ((r + 15) / 16) * 16;
     if (r < 16) r = 16;
-    size_t bytes = dpc_smem(W0, H, r, W0, C, R, WPC, V);
+    size_t bytes = dpc_smem(W0, H, r, W0, C, R, WPC, V, fwd);
     while (bytes > 220 * 1024 && r < H) {
         r += 16;
-        bytes = dpc_smem(W0, H, r, W0, C, R, WPC, V);
+        bytes = dpc_smem(W0, H, r, W0, C, R, WPC, V, fwd);
     }
     if (bytes > 220 * 1024) return false;
     // the walk stages at least one 16-row group of every band a CTA owns
@@ -706,13 +747,13 @@ bool dpc_plan(int W0, int H, int R, int WPC, int V, int *ctas, int *rj, size_t *
 
 namespace {
 
-template <int R, int WPC, int V>
+template <int R, int WPC, int V, bool FWD>
 bool dpc_available_t(int W0, int H) {
     int C = 0, rj = 0;
     size_t smem = 0;
-    if (!dpc_plan(W0, H, R, WPC, V, &C, &rj, &smem)) return false;
-    if (raise_dyn_smem((const void *)k_dpc<R, WPC, V>, smem) != cudaSuccess) return false;
-    if (C > 8 && cudaFuncSetAttribute(k_dpc<R, WPC, V>,
+    if (!dpc_plan(W0, H, R, WPC, V, &C, &rj, &smem, FWD)) return false;
+    if (raise_dyn_smem((const void *)k_dpc<R, WPC, V, FWD>, smem) != cudaSuccess) return false;
+    if (C > 8 && cudaFuncSetAttribute(k_dpc<R, WPC, V, FWD>,
                                       cudaFuncAttributeNonPortableClusterSizeAllowed,
                                       1) != cudaSuccess)
         return false;
@@ -728,25 +769,25 @@ bool dpc_available_t(int W0, int H) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&clusters, k_dpc<R, WPC, V>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&clusters, k_dpc<R, WPC, V, FWD>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     return clusters > 0;
 }
 
-template <int R, int WPC, int V>
+template <int R, int WPC, int V, bool FWD>
 cudaError_t launch_dpc_t(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                          cudaStream_t s) {
     int C = 0, rj = 0;
     size_t smem = 0;
-    if (!dpc_plan(ws.W0, ws.H, R, WPC, V, &C, &rj, &smem) || rj != ws.rj)
+    if (!dpc_plan(ws.W0, ws.H, R, WPC, V, &C, &rj, &smem, FWD) || rj != ws.rj)
         return cudaErrorInvalidValue;
-    smem = dpc_smem(ws.W0, ws.H, ws.rj, ws.kcap, C, R, WPC, V);
-    cudaError_t e = raise_dyn_smem((const void *)k_dpc<R, WPC, V>, smem);
+    smem = dpc_smem(ws.W0, ws.H, ws.rj, ws.kcap, C, R, WPC, V, FWD);
+    cudaError_t e = raise_dyn_smem((const void *)k_dpc<R, WPC, V, FWD>, smem);
     if (e != cudaSuccess) return e;
     if (C > 8) {
-        e = cudaFuncSetAttribute(k_dpc<R, WPC, V>,
+        e = cudaFuncSetAttribute(k_dpc<R, WPC, V, FWD>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
     }
@@ -764,41 +805,52 @@ cudaError_t launch_dpc_t(const CarveWs &ws, int nb, int k, int16_t *seams, long 
     attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 2;
-    CUtensorMap tm;
-    if (!make_energy_map(ws, nb, V, &tm)) return cudaErrorInvalidValue;
-    e = cudaLaunchKernelEx(&cfg, k_dpc<R, WPC, V>, tm, ws, k, seams, seam_stride);
+    CUtensorMap tm, tp;
+    if (!make_energy_map(ws, ws.E, nb, V, &tm)) return cudaErrorInvalidValue;
+    if (FWD && (!ws.P || !make_energy_map(ws, ws.P, nb, V, &tp))) return cudaErrorInvalidValue;
+    e = cudaLaunchKernelEx(&cfg, k_dpc<R, WPC, V, FWD>, tm, FWD ? tp : tm, ws, k, seams,
+                           seam_stride);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
 }  // namespace
 
-bool dpc_available_uncached(int W0, int H, int R, int WPC, int V) {
+bool dpc_available_uncached(int W0, int H, int R, int WPC, int V, bool fwd) {
     if (!encode_tiled()) return false;
+    if (fwd) {   // the layouts built with the forward terms
+        if (WPC == 4 && R == 16 && V == 2) return dpc_available_t<16, 4, 2, true>(W0, H);
+        if (WPC == 4 && R == 32 && V == 4) return dpc_available_t<32, 4, 4, true>(W0, H);
+        return false;
+    }
     if (V == 2) {
         if (R != 16) return false;
-        return WPC == 8 ? dpc_available_t<16, 8, 2>(W0, H)
-                        : WPC == 4 && dpc_available_t<16, 4, 2>(W0, H);
+        return WPC == 8 ? dpc_available_t<16, 8, 2, false>(W0, H)
+                        : WPC == 4 && dpc_available_t<16, 4, 2, false>(W0, H);
     }
     if (V != 4) return false;
-    if (WPC == 4) return R == 16 ? dpc_available_t<16, 4, 4>(W0, H) : R == 32 && dpc_available_t<32, 4, 4>(W0, H);
-    if (WPC == 8) return R == 16 ? dpc_available_t<16, 8, 4>(W0, H) : R == 32 && dpc_available_t<32, 8, 4>(W0, H);
+    if (WPC == 4)
+        return R == 16 ? dpc_available_t<16, 4, 4, false>(W0, H)
+                       : R == 32 && dpc_available_t<32, 4, 4, false>(W0, H);
+    if (WPC == 8)
+        return R == 16 ? dpc_available_t<16, 8, 4, false>(W0, H)
+                       : R == 32 && dpc_available_t<32, 8, 4, false>(W0, H);
     return false;
 }
 
 // Availability depends only on the size, the layout and the device: cached.
-bool dpc_available(int W0, int H, int R, int WPC, int V) {
+bool dpc_available(int W0, int H, int R, int WPC, int V, bool fwd) {
     static std::mutex mu;
-    static std::map<std::tuple<int, int, int, int, int, int>, bool> cache;
+    static std::map<std::tuple<int, int, int, int, int, int, bool>, bool> cache;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    const auto key = std::make_tuple(dev, W0, H, R, WPC, V);
+    const auto key = std::make_tuple(dev, W0, H, R, WPC, V, fwd);
     {
         std::lock_guard<std::mutex> lock(mu);
         auto it = cache.find(key);
         if (it != cache.end()) return it->second;
     }
-    const bool ok = dpc_available_uncached(W0, H, R, WPC, V);
+    const bool ok = dpc_available_uncached(W0, H, R, WPC, V, fwd);
     std::lock_guard<std::mutex> lock(mu);
     cache[key] = ok;
     return ok;
@@ -807,8 +859,21 @@ bool dpc_available(int W0, int H, int R, int WPC, int V) {
 // The layout for a size: the requested one if this GPU can run it, else the
 // first that it can run of R16 x 4 warps x 2 columns a lane (the fastest
 // where its cluster fits: half the instructions a row of the 4-column
-// layouts), R32 x 4 x 4 and R16 x 4 x 4.  False: use the single-CTA DP.
+// layouts), R32 x 4 x 4 and R16 x 4 x 4.  With the forward terms (ws.wf > 0)
+// the first of R16 x 4 x 2 and R32 x 4 x 4 that runs, whatever was requested
+// (the tuner times the plain kernels).  False: use the single-CTA DP.
 bool dpc_select(int W0, int H, CarveWs &ws, bool requested) {
+    if (ws.wf > 0) {
+        static const int fwd_order[2][3] = {{16, 4, 2}, {32, 4, 4}};
+        for (const auto &o : fwd_order)
+            if (dpc_available(W0, H, o[0], o[1], o[2], true)) {
+                ws.dpc_r = o[0];
+                ws.dpc_wpc = o[1];
+                ws.dpc_v = o[2];
+                return true;
+            }
+        return false;
+    }
     if (requested && dpc_available(W0, H, ws.dpc_r, ws.dpc_wpc, ws.dpc_v)) return true;
     static const int order[3][3] = {{16, 4, 2}, {32, 4, 4}, {16, 4, 4}};
     for (const auto &o : order)
@@ -825,15 +890,24 @@ cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long se
                        cudaStream_t s) {
     const int wpc = ws.dpc_wpc == 8 ? 8 : 4;
     const int v = ws.dpc_v == 2 ? 2 : 4;
-    if (v == 2) {
-        if (ws.dpc_r == 16 && wpc == 8) return launch_dpc_t<16, 8, 2>(ws, nb, k, seams, seam_stride, s);
-        if (ws.dpc_r == 16 && wpc == 4) return launch_dpc_t<16, 4, 2>(ws, nb, k, seams, seam_stride, s);
+    if (ws.wf > 0) {
+        if (ws.dpc_r == 16 && wpc == 4 && v == 2)
+            return launch_dpc_t<16, 4, 2, true>(ws, nb, k, seams, seam_stride, s);
+        if (ws.dpc_r == 32 && wpc == 4 && v == 4)
+            return launch_dpc_t<32, 4, 4, true>(ws, nb, k, seams, seam_stride, s);
         return cudaErrorInvalidValue;
     }
-    if (ws.dpc_r == 16 && wpc == 4) return launch_dpc_t<16, 4, 4>(ws, nb, k, seams, seam_stride, s);
-    if (ws.dpc_r == 32 && wpc == 4) return launch_dpc_t<32, 4, 4>(ws, nb, k, seams, seam_stride, s);
-    if (ws.dpc_r == 16 && wpc == 8) return launch_dpc_t<16, 8, 4>(ws, nb, k, seams, seam_stride, s);
-    if (ws.dpc_r == 32 && wpc == 8) return launch_dpc_t<32, 8, 4>(ws, nb, k, seams, seam_stride, s);
+    if (v == 2) {
+        if (ws.dpc_r == 16 && wpc == 8)
+            return launch_dpc_t<16, 8, 2, false>(ws, nb, k, seams, seam_stride, s);
+        if (ws.dpc_r == 16 && wpc == 4)
+            return launch_dpc_t<16, 4, 2, false>(ws, nb, k, seams, seam_stride, s);
+        return cudaErrorInvalidValue;
+    }
+    if (ws.dpc_r == 16 && wpc == 4) return launch_dpc_t<16, 4, 4, false>(ws, nb, k, seams, seam_stride, s);
+    if (ws.dpc_r == 32 && wpc == 4) return launch_dpc_t<32, 4, 4, false>(ws, nb, k, seams, seam_stride, s);
+    if (ws.dpc_r == 16 && wpc == 8) return launch_dpc_t<16, 8, 4, false>(ws, nb, k, seams, seam_stride, s);
+    if (ws.dpc_r == 32 && wpc == 8) return launch_dpc_t<32, 8, 4, false>(ws, nb, k, seams, seam_stride, s);
     return cudaErrorInvalidValue;
 }
 

@@ -793,8 +793,8 @@ scpl_status setup_group(Srv *s, int gid) {
     bool use_dpc = true;
     // sizes were tuned when their wave finished
     const bool tuned = tuning_apply(G.H, G.W, ws, &use_dpc);
-    ws.wf = s->p.wf;   // forward terms: their planes and the single-CTA DP
-    if (ws.wf > 0) use_dpc = false;
+    ws.wf = s->p.wf;   // forward terms: their planes and the cluster-DP layouts built with them
+    if (ws.wf > 0) use_dpc = true;
     G.dpc = use_dpc && dpc_select(G.W, G.H, ws, tuned);
     const size_t ws_bytes = carve_ws_assign(ws, nb, klog, G.dpc, nullptr);
     // frames of every item, the gather table and the frame-minor luma

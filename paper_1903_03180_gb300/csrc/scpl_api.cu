@@ -305,9 +305,9 @@ scpl_status carve_ws(scpl_ctx *h, int nb, int H, int W0, int kcap, CarveWs &ws,
     if (h->autotune && !tuning_lookup(H, W0, nullptr))
         tune_class(H, W0, ws.kcap, h->stream, nullptr);   // on failure: the defaults
     const bool tuned = tuning_apply(H, W0, ws, &use_dpc);
-    // forward terms: the single-CTA DP and the planes of the terms
+    // forward terms: their planes, and the cluster-DP layouts built with them
     ws.wf = h->p.wf;
-    if (ws.wf > 0) use_dpc = false;
+    if (ws.wf > 0) use_dpc = true;
     // cluster DP (used when the GPU can co-schedule the cluster)
     const bool dpc = use_dpc && dpc_select(W0, H, ws, tuned);
     const size_t bytes = carve_ws_assign(ws, nb, klog_stride, dpc, nullptr);

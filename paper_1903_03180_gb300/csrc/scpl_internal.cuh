@@ -232,8 +232,9 @@ cudaError_t launch_dp_select(const CarveWs &ws, int nb, int k, int16_t *seams, l
 // shared memory) for a width and height; returns false if this GPU cannot
 // run it (then use launch_dp_select).  launch_dpc uses ws.dpc_r, ws.dpc_wpc
 // and ws.dpc_v.
-bool dpc_plan(int W0, int H, int R, int WPC, int V, int *ctas, int *rj, size_t *smem);
-bool dpc_available(int W0, int H, int R, int WPC, int V);
+bool dpc_plan(int W0, int H, int R, int WPC, int V, int *ctas, int *rj, size_t *smem,
+              bool fwd = false);
+bool dpc_available(int W0, int H, int R, int WPC, int V, bool fwd = false);
 // Sets ws.dpc_r / dpc_wpc / dpc_v to the requested layout (requested = the
 // fields hold a tuned choice) if available, else to the default for the size;
 // false if no cluster layout runs here.

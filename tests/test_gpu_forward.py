@@ -72,8 +72,19 @@ def test_forward_per_frame_and_gradient_only(orc, lib):
     assert np.array_equal(seams, ref_seams)
 
 
+def test_forward_second_cluster_layout(orc, lib):
+    """2049 to 4096 columns: too wide for the 2-column-lane cluster, so the
+    forward terms go through the 32-deep-halo, 4-column-lane layout."""
+    from paper_1903_03180_gb300 import synth
+    f = synth.clip(2, 6, 3000, seed=15)
+    out, starts, seams = _carve(lib, f, 2990, 4, wf=2)
+    ref, ref_starts, ref_seams = orc.carve(f, 2990, 4, wf=2)
+    assert np.array_equal(starts, ref_starts) and np.array_equal(out, ref)
+    assert np.array_equal(seams, ref_seams)
+
+
 def test_forward_wide_frame_layout(orc, lib):
-    """More than 4096 columns: the DP's 8-column lanes."""
+    """More than 4096 columns: the single-CTA DP's 8-column lanes."""
     from paper_1903_03180_gb300 import synth
     f = synth.clip(2, 3, 4500, seed=13)
     out, starts, seams = _carve(lib, f, 4488, 4, wf=1)
