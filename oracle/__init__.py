@@ -344,3 +344,27 @@ def enlarge(frames: np.ndarray, target: int, k: int, wg: int = 1, wm: int = 2,
             c = frames[t0:t1, i, right].astype(np.int32)
             out[t0:t1, i] = ((a + c + 1) >> 1).astype(np.uint8)
     return out, starts
+
+
+def enlarge_job(frames: np.ndarray, target_W: int, target_H: int, k: int, wg: int = 1,
+                wm: int = 2, alpha: float = ALPHA, t_max: int = T_MAX, use_buffer: bool = True,
+                maxval_mode: int = 0, wf: int = 0):
+    """Enlarge a clip to target_H x target_W (R12 in both directions; Sec. 2
+    retargets along either axis).  The width grows first (``enlarge``); the
+    height then grows as the width of the transposed result, its horizontal
+    seams being the vertical seams of the transposed frames (R10), and the
+    result is transposed back.  Each target lies in [size, 2*size - 2].
+
+    Returns out [T,target_H,target_W,3]."""
+    frames = np.ascontiguousarray(frames, dtype=np.uint8)
+    T, H, W = frames.shape[:3]
+    kw = dict(wg=wg, wm=wm, alpha=alpha, t_max=t_max, use_buffer=use_buffer,
+              maxval_mode=maxval_mode, wf=wf)
+    out = frames
+    if target_W > W:
+        out, _ = enlarge(out, target_W, k, **kw)
+    if target_H > H:
+        tr = np.ascontiguousarray(out.transpose(0, 2, 1, 3))
+        o2, _ = enlarge(tr, target_H, k, **kw)
+        out = np.ascontiguousarray(o2.transpose(0, 2, 1, 3))
+    return out.copy() if out is frames else out

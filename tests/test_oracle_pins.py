@@ -616,3 +616,64 @@ def test_forward_weight_shifts_seams_off_created_edges(orc):
     s = seams[0]
     assert _forward_cost(orc, f, s, 0, 0, 1) == 0
     assert not np.isin(s, [2, 3, 4, 5]).any()
+
+
+# ------------------------------------- N4: insertion along the height (Sec. 2)
+def _drop_inserted_rows(out: np.ndarray, H: int, inserted_after: list) -> np.ndarray:
+    """Remove, column by column, the pixel that follows each listed original row."""
+    return _drop_inserted(out.transpose(1, 0, 2), H, inserted_after).transpose(1, 0, 2)
+
+
+def test_enlarge_job_height_inserts_the_classic_horizontal_seams(orc):
+    """k = 1, one frame, gradient energy: the rows inserted into each column
+    follow the horizontal seams of classic seam carving (found here as the
+    vertical seams of the transposed frame, whose gradient is the transposed
+    gradient), each new pixel is the rounded mean of the pixels above and
+    below it, and dropping them gives the frame back."""
+    from paper_1903_03180_gb300 import synth
+    f = synth.still_frame(20, 15, seed=61)
+    m = 4
+    out = orc.enlarge_job(f[None], 15, 20 + m, 1, wm=0, use_buffer=False)
+    assert out.shape == (1, 20 + m, 15, 3)
+    ft = np.ascontiguousarray(f.transpose(1, 0, 2))
+    _, seams = tb.classic_seam_carve(ft, m, lambda im: tb.sobel_scipy(orc.luma(im)))
+    inserted = [set(int(s) for s in seams[:, j]) for j in range(15)]
+    assert np.array_equal(_drop_inserted_rows(out[0], 20, inserted), f)
+    for j in range(15):
+        p = 0
+        for x in range(20):
+            if x in inserted[j]:
+                a = f[x, j].astype(int)
+                b = f[min(x + 1, 19), j].astype(int)
+                assert np.array_equal(out[0, p + 1, j], (a + b + 1) >> 1)
+                p += 2
+            else:
+                p += 1
+
+
+def test_enlarge_job_both_drops_back_to_the_clip(orc):
+    """Both dimensions on a multi-buffer clip: dropping the rows that the
+    height stage inserted gives the width stage's result, and dropping the
+    columns it inserted gives the clip back, frame by frame."""
+    from paper_1903_03180_gb300 import synth
+    f = synth.clip(6, 12, 18, seed=62, cuts=(3, 3))
+    out = orc.enlarge_job(f, 23, 16, 3)
+    mid, _ = orc.enlarge(f, 23, 3)
+    assert np.array_equal(out, orc.enlarge_job(mid, 23, 16, 3))
+    tr = np.ascontiguousarray(mid.transpose(0, 2, 1, 3))
+    _, starts, seams = orc.carve(tr, 12 - 4, 3)
+    _, wstarts, wseams = orc.carve(f, 18 - 5, 3)
+    for b in range(len(starts) - 1):
+        rows = [set(int(s) for s in seams[b, :, j]) for j in range(23)]
+        for t in range(starts[b], starts[b + 1]):
+            assert np.array_equal(_drop_inserted_rows(out[t], 12, rows), mid[t])
+    for b in range(len(wstarts) - 1):
+        cols = [set(int(s) for s in wseams[b, :, i]) for i in range(12)]
+        for t in range(wstarts[b], wstarts[b + 1]):
+            assert np.array_equal(_drop_inserted(mid[t], 18, cols), f[t])
+
+
+def test_enlarge_job_identity_and_width_only(orc):
+    f = np.random.default_rng(63).integers(0, 256, (3, 6, 9, 3), dtype=np.uint8)
+    assert np.array_equal(orc.enlarge_job(f, 9, 6, 2), f)
+    assert np.array_equal(orc.enlarge_job(f, 13, 6, 2), orc.enlarge(f, 13, 2)[0])
