@@ -164,6 +164,21 @@ scpl_status scpl_enlarge(scpl_handle h, const uint8_t *frames, int T, int H, int
                          int target_W, int k, uint8_t *out, int32_t *buffer_starts,
                          int *n_buffers);
 
+/* Enlarge a clip along both axes (Sec. 2 retargets either way): the width
+ * grows first, exactly as scpl_enlarge does; the height then grows as the
+ * width of the transposed result (its horizontal seams are the vertical seams
+ * of the transposed frames, found by the same SCPL carving with its own buffer
+ * scan), and the result is transposed back.  A target equal to its size adds
+ * nothing along that axis.
+ *   frames [device] uint8 [T][H][W][3]
+ *   out    [device] uint8 [T][target_H][target_W][3]
+ * W <= target_W <= max(W, 2W-2), H <= target_H <= max(H, 2H-2), W <= 8192,
+ * and H <= 8192 when the height grows (else SCPL_EINVAL); k >= 1.  Scratch
+ * copies of the intermediate clips are the handle's.  Synchronises the
+ * stream. */
+scpl_status scpl_enlarge_job(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                             int target_W, int target_H, int k, uint8_t *out);
+
 /* Sharpness of blends of consecutive frames (a measure of temporal
  * consistency; a numeric stand-in for Fig. 9 of Sec. 4): on a nearly static
  * clip, frames carved with the same seams blend into a sharp image, frames

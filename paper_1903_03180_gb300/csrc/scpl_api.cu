@@ -111,6 +111,7 @@ struct scpl_ctx {
     // host-memory entry point staging
     DevBuf in_frames, out_frames, seams_dev;
     DevBuf qY, qacc;   // blend sharpness: luma of every frame, the two sums
+    DevBuf ej_mid, ej_tin, ej_tout;   // scpl_enlarge_job: widened, transposed, enlarged
     // scpl_carve_host_many: a second input and output slot, the input copy
     // stream and the second arrival counter
     DevBuf in2, out2, ready2;
@@ -602,7 +603,8 @@ void scpl_destroy(scpl_handle h) {
     DevBuf *bufs[] = {&h->Y, &h->D, &h->ering, &h->S1, &h->S2, &h->partA, &h->partM,
                       &h->count, &h->starts, &h->nbuf, &h->errw, &h->E0, &h->cws, &h->bof,
                       &h->in_frames, &h->out_frames, &h->seams_dev, &h->Yfm, &h->qY,
-                      &h->qacc, &h->in2, &h->out2, &h->ready2};
+                      &h->qacc, &h->in2, &h->out2, &h->ready2, &h->ej_mid, &h->ej_tin,
+                      &h->ej_tout};
     if (h->istream) cudaStreamSynchronize(h->istream);
     if (h->cstream) cudaStreamSynchronize(h->cstream);
     if (h->gstream) cudaStreamSynchronize(h->gstream);
@@ -706,6 +708,40 @@ scpl_status scpl_enlarge(scpl_handle h, const uint8_t *frames, int T, int H, int
     SCPL_CUDA(h, cudaStreamSynchronize(st));
     if (buffer_starts) std::copy(starts.begin(), starts.begin() + nb + 1, buffer_starts);
     if (n_buffers) *n_buffers = nb;
+    return SCPL_OK;
+}
+
+scpl_status scpl_enlarge_job(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                             int target_W, int target_H, int k, uint8_t *out) {
+    scpl_status s = check_frames(h, frames, T, H, W);
+    if (s != SCPL_OK) return s;
+    if (!out) return fail(h, SCPL_EINVAL, "out is NULL");
+    if (k < 1) return fail(h, SCPL_EINVAL, "k=%d must be >= 1", k);
+    if (target_W < W || target_W > std::max(W, 2 * W - 2))
+        return fail(h, SCPL_EINVAL, "target_W=%d must be in [W, 2W-2] for W=%d", target_W, W);
+    if (target_H < H || target_H > std::max(H, 2 * H - 2))
+        return fail(h, SCPL_EINVAL, "target_H=%d must be in [H, 2H-2] for H=%d", target_H, H);
+    if (target_H == H) return scpl_enlarge(h, frames, T, H, W, target_W, k, out, nullptr, nullptr);
+    if (H > 8192) return fail(h, SCPL_EINVAL, "H=%d exceeds 8192 for a height enlargement", H);
+    cudaStream_t st = h->stream;
+    // the width first, into a scratch clip
+    const uint8_t *mid = frames;
+    if (target_W > W) {
+        SCPL_CUDA(h, h->ej_mid.ensure((size_t)T * H * target_W * 3));
+        if ((s = scpl_enlarge(h, frames, T, H, W, target_W, k, h->ej_mid.as<uint8_t>(), nullptr,
+                              nullptr)) != SCPL_OK)
+            return s;
+        mid = h->ej_mid.as<uint8_t>();
+    }
+    // the height as the width of the transposed clip, then back
+    SCPL_CUDA(h, h->ej_tin.ensure((size_t)T * target_W * H * 3));
+    SCPL_CUDA(h, h->ej_tout.ensure((size_t)T * target_W * target_H * 3));
+    SCPL_CUDA(h, launch_transpose_rgb(mid, T, H, target_W, h->ej_tin.as<uint8_t>(), st));
+    if ((s = scpl_enlarge(h, h->ej_tin.as<uint8_t>(), T, target_W, H, target_H, k,
+                          h->ej_tout.as<uint8_t>(), nullptr, nullptr)) != SCPL_OK)
+        return s;
+    SCPL_CUDA(h, launch_transpose_rgb(h->ej_tout.as<uint8_t>(), T, target_W, target_H, out, st));
+    SCPL_CUDA(h, cudaStreamSynchronize(st));
     return SCPL_OK;
 }
 

@@ -86,6 +86,7 @@ SIGNATURES = {
     "scpl_signal_arrival": (_I, [_P, _P, ctypes.c_uint32]),
     "scpl_set_wait_limit": (_I, [_P, ctypes.c_uint64]),
     "scpl_enlarge": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P]),
+    "scpl_enlarge_job": (_I, [_P, _P, _I, _I, _I, _I, _I, _I, _P]),
     "scpl_carve_host_many": (_I, [_P, _I, _P, _I, _I, _I, _I, _I, _P, _P]),
     "scpl_blend_sharpness": (_I, [_P, _P, _I, _I, _I, _I, ctypes.POINTER(_LL),
                                   ctypes.POINTER(_LL)]),
@@ -301,6 +302,18 @@ def scpl_enlarge(h, frames, target_W: int, k: int, out) -> np.ndarray:
     return starts[: nb.value + 1].copy()
 
 
+def scpl_enlarge_job(h, frames, target_W: int, target_H: int, k: int, out):
+    """Seam insertion along both axes: width first, then the height on the
+    transposed clip.  frames [T,H,W,3] uint8 (device), out [T,target_H,target_W,3]."""
+    import torch
+    fp = _dev_ptr(frames, torch.uint8, 4, "frames")
+    op = _dev_ptr(out, torch.uint8, 4, "out")
+    T, H, W, _ = frames.shape
+    if tuple(out.shape) != (T, target_H, target_W, 3):
+        raise ValueError("out must be [T,target_H,target_W,3]")
+    _check(h, load().scpl_enlarge_job(h, fp, T, H, W, int(target_W), int(target_H), int(k), op))
+
+
 def scpl_blend_sharpness(h, frames, window: int = 4) -> tuple[int, int]:
     """(num, den) of the blends of `window` consecutive frames of a cuda
     uint8 [T,H,W,3] clip; num / den is the blends' sharpness (1 = static)."""
@@ -462,6 +475,14 @@ class Retargeter:
         out = torch.empty((T, H, target_W, 3), dtype=torch.uint8, device=frames.device)
         starts = scpl_enlarge(self.h, frames, target_W, k, out)
         return out, starts
+
+    def enlarge_job(self, frames, target_W: int, target_H: int, k: int):
+        """Enlarge frames along both axes by seam insertion; returns out."""
+        import torch
+        T = frames.shape[0]
+        out = torch.empty((T, target_H, target_W, 3), dtype=torch.uint8, device=frames.device)
+        scpl_enlarge_job(self.h, frames, target_W, target_H, k, out)
+        return out
 
     def close(self):
         if self.h is not None:

@@ -92,3 +92,29 @@ def test_enlarge_identity_and_limits(lib):
     with pytest.raises(lib.SCPLError):
         r.enlarge(f, 8, 4)    # narrower: use scpl_carve
     r.close()
+
+
+# ------------------------------------------------ insertion along both axes
+@pytest.mark.parametrize("T,H,W,tw,th,k,seed,cuts", [(5, 14, 20, 20, 23, 4, 91, (2, 3)),
+                                                     (4, 12, 18, 23, 16, 3, 92, (2, 2)),
+                                                     (3, 33, 40, 60, 50, 8, 93, None),
+                                                     (2, 9, 300, 300, 13, 16, 94, None)])
+def test_enlarge_job_matches_oracle(orc, lib, T, H, W, tw, th, k, seed, cuts):
+    from paper_1903_03180_gb300 import synth
+    f = synth.clip(T, H, W, seed=seed, cuts=cuts)
+    r = lib.Retargeter()
+    out = r.enlarge_job(torch.from_numpy(f).cuda(), tw, th, k)
+    torch.cuda.synchronize()
+    r.close()
+    assert np.array_equal(out.cpu().numpy(), orc.enlarge_job(f, tw, th, k))
+
+
+def test_enlarge_job_limits(lib):
+    f = torch.randint(0, 256, (2, 6, 9, 3), dtype=torch.uint8, device="cuda")
+    r = lib.Retargeter()
+    assert torch.equal(r.enlarge_job(f, 9, 6, 4), f)
+    with pytest.raises(lib.SCPLError):
+        r.enlarge_job(f, 9, 11, 4)   # more than 2H-2
+    with pytest.raises(lib.SCPLError):
+        r.enlarge_job(f, 9, 5, 4)    # shorter: carve instead
+    r.close()
