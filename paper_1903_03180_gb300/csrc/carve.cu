@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
     const long pitch = ws.pitch, plane = ws.plane;
     const int kcap = ws.kcap;
     const int nwords0 = (ws.W0 + 31) >> 5;
-    const int list_cap = RB * min(ws.W0, 15 * kcap);
+    const int list_cap = RB * min(ws.W0, 9 * kcap);
     uint16_t *rl = reinterpret_cast<uint16_t *>(smraw);   // [RB+2][kcap] lists of rows i0-1..i0+RB
     size_t off = ((size_t)(RB + 2) * kcap * 2 + 15) & ~(size_t)15;
     uint32_t *bm = reinterpret_cast<uint32_t *>(smraw + off);   // [RB][nwords0]
@@ -238,15 +238,19 @@ __global__ void __launch_bounds__(UP_THREADS) k_update(CarveWs ws, int RB) {
     if (tid == 0) s_cnt = 0;
     __syncthreads();   // lists loaded; the staging barrier is initialised
 
-    // 2. while the rows arrive: old columns within 2 of a removed pixel in
-    //    rows i-1, i, i+1, marked in a bitmap and listed
+    // 2. while the rows arrive: old columns within 1 of a removed pixel in
+    //    rows i-1, i, i+1, marked in a bitmap and listed.  No other pixel
+    //    changes: seams move at most one column a row, so the new 3x3
+    //    neighbourhood of a pixel x (and so its gradient and forward terms)
+    //    holds the same original pixels unless some row i-1 .. i+1 lost a
+    //    pixel in x-1 .. x+1
     int cnt = 0;
     if (need_e) {
-        const int per_row = 15 * keff;
+        const int per_row = 9 * keff;
         for (int x = tid; x < nrows * per_row; x += UP_THREADS) {
             const int r = x / per_row, y = x - r * per_row;
-            const int a = y / (5 * keff), z = y - a * 5 * keff;
-            const int mm = z / 5, d = z - mm * 5 - 2;
+            const int a = y / (3 * keff), z = y - a * 3 * keff;
+            const int mm = z / 3, d = z - mm * 3 - 1;
             const int c = (int)rl[(r + a) * kcap + mm] + d;
             if (c >= 0 && c < Wc) atomicOr(&bm[r * nwords0 + (c >> 5)], 1u << (c & 31));
         }
@@ -912,7 +916,7 @@ size_t dp_smem_bytes(int W0, int H, int *band_blocks) {
 // changed-pixel bitmap and list, the staged origin and energy rows, and the
 // recomputed sums of the listed pixels.
 size_t update_smem_bytes_rows(int W0, int kcap, int rb, bool fwd) {
-    const size_t per_row_list = (size_t)(W0 < 15 * kcap ? W0 : 15 * kcap);
+    const size_t per_row_list = (size_t)(W0 < 9 * kcap ? W0 : 9 * kcap);
     const size_t nwords0 = (size_t)(W0 + 31) / 32;
     size_t off = (((size_t)(rb + 2) * kcap * 2 + 15) & ~(size_t)15) + (size_t)rb * nwords0 * 4;
     off = (off + (size_t)rb * per_row_list * 4 + 15) & ~(size_t)15;
