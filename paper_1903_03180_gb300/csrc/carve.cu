@@ -37,17 +37,6 @@ constexpr uint32_t INF32 = 0xFFFFFFFFu;
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 
-// Source column (at the old width) of carved column p, given the ascending
-// removal list r[0..k) of the row: p + #{m : r[m] - m <= p}.
-__device__ __forceinline__ int src_col(const uint16_t *__restrict__ r, int k, int p) {
-    int lo = 0, hi = k;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if ((int)r[mid] - mid <= p) lo = mid + 1; else hi = mid;
-    }
-    return p + lo;
-}
-
 // #{m : r[m] < q} for an ascending list.
 __device__ __forceinline__ int count_less(const uint16_t *__restrict__ r, int k, int q) {
     int lo = 0, hi = k;
