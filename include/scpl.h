@@ -57,8 +57,10 @@ typedef enum {
  *               when it arrives from the upper left, |Y(i-1,j) - Y(i,j+1)|
  *               from the upper right.  The buffer scan (Eq. 7-9) keeps the
  *               backward energy.  wf > 0 needs buffers of at most 256 frames
- *               (t_max <= 256, or use_buffer 0) and carves with the
- *               single-CTA DP.                                               */
+ *               (t_max <= 256, or use_buffer 0); widths up to 4096 carve
+ *               with the cluster DP, wider ones with the single-CTA DP.
+ *               scpl_seams and scpl_seams_noalloc take a caller's energy map
+ *               and charge no forward terms.                                */
 typedef struct {
     double alpha;
     int wg, wm;
@@ -414,7 +416,9 @@ scpl_status scpl_carve_batch(scpl_handle h, scpl_job *jobs, int n_jobs);
  * copies of host frames and outputs, the transposed frames of a horizontal
  * pass, the luma and motion maps, the scan state and the carving workspace of
  * one spatiotemporal buffer.  Each further buffer the scan finds adds
- * scpl_job_footprint_per_buffer bytes when it is found.  0 for an invalid job. */
+ * scpl_job_footprint_per_buffer bytes when it is found (with forward terms,
+ * p->wf > 0, also two 32-bit planes of the pass's padded frame size).  0 for
+ * an invalid job. */
 size_t scpl_job_footprint(const scpl_params *p, const scpl_job *job);
 size_t scpl_job_footprint_per_buffer(const scpl_job *job);
 
