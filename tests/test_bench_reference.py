@@ -26,3 +26,14 @@ def test_reference_arm_json_line():
     assert d["config"]["frames_per_step"] == 2
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_forward_weight():
+    """--wf reaches the oracle of the reference arm and its config."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--workload", "still_240p", "--steps", "1", "--warmup", "1",
+                        "--ref-frames", "1", "--ref-procs", "2", "--wf", "2"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([l for l in r.stdout.splitlines() if l.startswith("{")][0])
+    assert d["impl"] == "reference" and d["config"]["wf"] == 2 and d["value"] > 0
