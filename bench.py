@@ -396,7 +396,9 @@ def run_native(args) -> None:
     bytes_per_launch = d["bytes"] / max(d["launches"], 1)
     achieved = bytes_per_launch / (avg_ms / 1000.0) / 1e9
     traffic = None
-    if dom == "k_dp" and args.wf == 0:   # DRAM bytes per carved pixel of one ncu capture of k_dpc, scaled
+    # DRAM bytes per carved pixel of one ncu capture of the plain k_dpc, scaled
+    # (the forward-energy DP was not captured)
+    if dom == "k_dp" and args.wf == 0:
         # carved_px covers the last clip; the launches cover every profiled step
         traffic = round(DP_DRAM_BYTES_PER_PX * stats["carved_px"] * args.steps /
                         max(d["launches"], 1))
