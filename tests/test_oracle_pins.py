@@ -677,3 +677,35 @@ def test_enlarge_job_identity_and_width_only(orc):
     f = np.random.default_rng(63).integers(0, 256, (3, 6, 9, 3), dtype=np.uint8)
     assert np.array_equal(orc.enlarge_job(f, 9, 6, 2), f)
     assert np.array_equal(orc.enlarge_job(f, 13, 6, 2), orc.enlarge(f, 13, 2)[0])
+
+
+@pytest.mark.parametrize("wf", [1, 4])
+def test_forward_multi_seam_invariants(orc, wf):
+    """Forward terms with several seams an iteration on a multi-buffer clip:
+    the removed pixels are disjoint and narrow every row, each seam is
+    8-connected at the width it was removed at, and the output is the input
+    minus the seams' pixels (the DP's moves cost more, the structure stays)."""
+    from paper_1903_03180_gb300 import synth
+    c = synth.clip(6, 26, 44, seed=913, cuts=(3, 3))
+    target = 30
+    out, starts, seams = orc.carve(c, target, 5, wf=wf, t_max=4)
+    _check_carve_invariants(c, out, starts, seams, target)
+    for b in range(len(starts) - 1):
+        cur = _current_columns(seams[b], 26, 44)
+        assert (np.abs(np.diff(cur, axis=1)) <= 1).all()
+
+
+def test_forward_kbig_removes_one_seam_per_parent(orc):
+    """The uncapped variant with forward terms: the first iteration removes one
+    seam for every parent the forward DP's last row holds (capped by what is
+    left to remove)."""
+    from paper_1903_03180_gb300 import synth
+    f = synth.still_frame(18, 36, seed=914, n_rects=3)
+    D = np.zeros((1, 18, 36), np.uint8)
+    out, seams, keff = orc.carve_buffer(f[None], D, 26, 1000, wg=1, wm=0, wf=2)
+    Y = orc.luma(f)
+    CU, A, B = orc.forward_terms(Y)
+    E = orc.energy(f[None], 1, 0)[0] + 2 * CU
+    CE, L, d = orc.dp_fwd(E, A, B, 2)
+    assert keff[0] == min(len(np.unique(L[-1])), 10)
+    assert keff.sum() == 10
