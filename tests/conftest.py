@@ -15,6 +15,18 @@ def pytest_configure(config):
 
 @pytest.fixture(scope="session")
 def orc():
+    """The oracle; SCPL_ORACLE_DIR names another copy of the oracle package
+    (the mutation test runs the pins against copies with a planted error)."""
+    path = os.environ.get("SCPL_ORACLE_DIR")
+    if path:
+        import importlib.util
+        spec = importlib.util.spec_from_file_location(
+            "oracle_under_test", os.path.join(path, "__init__.py"),
+            submodule_search_locations=[path])
+        mod = importlib.util.module_from_spec(spec)
+        spec.loader.exec_module(mod)
+        mod.build()
+        return mod
     import oracle
     oracle.build()
     return oracle

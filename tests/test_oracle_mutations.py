@@ -1,0 +1,83 @@
+"""The pins catch plausible mistakes in the oracle: each case copies the oracle
+package, plants one error in its C source (on the CPU, in the copy only), and
+runs the pin suite against the copy, which must fail.  An unmodified copy must
+pass, so a failure means the planted error, not the harness."""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
+
+# (name, text in scpl_oracle.c, planted replacement)
+MUTATIONS = [
+    ("luma weights swapped",
+     "return (77 * (int)px[0] + 150 * (int)px[1] + 29 * (int)px[2] + 128) >> 8;",
+     "return (29 * (int)px[0] + 150 * (int)px[1] + 77 * (int)px[2] + 128) >> 8;"),
+    ("Sobel centre weight 1",
+     "int gx = (y[0][2] + 2 * y[1][2] + y[2][2]) - (y[0][0] + 2 * y[1][0] + y[2][0]);",
+     "int gx = (y[0][2] + y[1][2] + y[2][2]) - (y[0][0] + y[1][0] + y[2][0]);"),
+    ("first frame has motion", "D[p] = 0;", "D[p] = 7;"),
+    ("DP ties to the highest column",
+     "if (best_j < 0 || up[jj] < up[best_j]) best_j = jj;",
+     "if (best_j < 0 || up[jj] <= up[best_j]) best_j = jj;"),
+    ("selection ties to the highest column",
+     "return a->ce < b->ce || (a->ce == b->ce && a->col < b->col);",
+     "return a->ce < b->ce || (a->ce == b->ce && a->col > b->col);"),
+    ("backtrack mirrored",
+     "path[i - 1] = path[i] + (int)dir[(long)i * W + path[i]] - 1;",
+     "path[i - 1] = path[i] - (int)dir[(long)i * W + path[i]] + 1;"),
+    ("sqrt(n) for sqrt(n-1)", "thr = thr * sqrt((double)(n - 1));",
+     "thr = thr * sqrt((double)n);"),
+    ("no t_max cap", "if (n == t_max) {", "if (n == t_max + 1) {"),
+    ("motion of the first frame only",
+     "E[p] += wg * G[p] + wm * (int)dm[(long)t * hw + p];",
+     "E[p] += wg * G[p] + wm * (int)dm[p];"),
+    ("forward diagonal terms swapped",
+     "if (jj == j - 1) c += (int64_t)wf * A[p];\n                if (jj == j + 1) c += (int64_t)wf * B[p];",
+     "if (jj == j - 1) c += (int64_t)wf * B[p];\n                if (jj == j + 1) c += (int64_t)wf * A[p];"),
+    ("forward row term clamped at the border",
+     "CU[p] = (j > 0 && j < W - 1) ? abs((int)r[j + 1] - (int)r[j - 1]) : 0;",
+     "CU[p] = abs((int)r[j + 1 < W ? j + 1 : j] - (int)r[j > 0 ? j - 1 : 0]);"),
+    ("forward diagonal term from the wrong column",
+     "A[p] = (u && j >= 1) ? abs((int)u[j] - (int)r[j - 1]) : 0;",
+     "A[p] = (u && j >= 1) ? abs((int)u[j - 1] - (int)r[j - 1]) : 0;"),
+]
+
+
+def _copy(tmp_path, name, old=None, new=None) -> str:
+    dst = os.path.join(str(tmp_path), name)
+    shutil.copytree(os.path.join(ROOT, "oracle"), dst,
+                    ignore=shutil.ignore_patterns("*.so", "*.tmp*", "__pycache__"))
+    if old is not None:
+        src = os.path.join(dst, "scpl_oracle.c")
+        with open(src) as fh:
+            text = fh.read()
+        assert text.count(old) == 1, f"mutation target not unique: {old[:40]}"
+        with open(src, "w") as fh:
+            fh.write(text.replace(old, new))
+    return dst
+
+
+def _run_pins(path: str) -> subprocess.CompletedProcess:
+    env = dict(os.environ, SCPL_ORACLE_DIR=path)
+    return subprocess.run([sys.executable, "-m", "pytest", PINS, "-x", "-q", "-p",
+                           "no:cacheprovider"], capture_output=True, text=True, env=env,
+                          cwd=ROOT, timeout=600)
+
+
+def test_unmodified_copy_passes(tmp_path):
+    r = _run_pins(_copy(tmp_path, "oracle_copy"))
+    assert r.returncode == 0, r.stdout[-2000:]
+
+
+@pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_error_fails_a_pin(tmp_path, name, old, new):
+    r = _run_pins(_copy(tmp_path, "oracle_mut", old, new))
+    assert r.returncode == 1, (name, r.returncode, r.stdout[-2000:])
+    assert "failed" in r.stdout

@@ -232,6 +232,21 @@ def test_multi_seam_invariants(orc):
         assert (np.abs(np.diff(cur, axis=1)) <= 1).all()
 
 
+@pytest.mark.parametrize("seed", range(8))
+def test_buffer_seam_is_least_costly_with_motion(orc, seed):
+    """Brute force over every seam of a small multi-frame buffer (R8): the seam
+    removed first has the least sum, along it, of every frame's energy
+    wg*G_t + wm*D_t (the energies from `orc.energy`, pinned against scipy)."""
+    r = np.random.default_rng(700 + seed)
+    T, H, W = int(r.integers(2, 4)), int(r.integers(3, 6)), int(r.integers(4, 8))
+    wg, wm = int(r.integers(0, 2)), int(r.integers(1, 4))
+    f = r.integers(0, 256, (T, H, W, 3), dtype=np.uint8)
+    _, seams, _ = orc.carve_buffer(f, orc.motion(f), W - 1, 1, wg=wg, wm=wm)
+    E = orc.energy(f, wg, wm).sum(0)
+    cost = lambda s: int(sum(E[i, c] for i, c in enumerate(s)))
+    assert cost(seams[0]) == min(cost(s) for s in tb.all_seams(H, W))
+
+
 def test_kbig_removes_one_seam_per_parent(orc):
     from paper_1903_03180_gb300 import synth
     f = synth.still_frame(20, 40, seed=14, n_rects=3)
