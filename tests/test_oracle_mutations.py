@@ -14,7 +14,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
 
-# (name, text in scpl_oracle.c, planted replacement)
+# (name, text in scpl_oracle.c, planted replacement); names ending in "(py)" plant
+# the error in the wrapper module __init__.py instead
 MUTATIONS = [
     ("luma weights swapped",
      "return (77 * (int)px[0] + 150 * (int)px[1] + 29 * (int)px[2] + 128) >> 8;",
@@ -47,15 +48,21 @@ MUTATIONS = [
     ("forward diagonal term from the wrong column",
      "A[p] = (u && j >= 1) ? abs((int)u[j] - (int)r[j - 1]) : 0;",
      "A[p] = (u && j >= 1) ? abs((int)u[j - 1] - (int)r[j - 1]) : 0;"),
+    ("insertion mean rounds down (py)", "out[t0:t1, i] = ((a + c + 1) >> 1).astype(np.uint8)",
+     "out[t0:t1, i] = ((a + c) >> 1).astype(np.uint8)"),
+    ("inserted pixel blends with the left neighbour (py)",
+     "right.append(min(x + 1, W - 1))", "right.append(max(x - 1, 0))"),
+    ("blend of one frame fewer (py)", "num += mag(Y[t:t + window].sum(axis=0))",
+     "num += mag(Y[t:t + window - 1].sum(axis=0))"),
 ]
 
 
 def _copy(tmp_path, name, old=None, new=None) -> str:
-    dst = os.path.join(str(tmp_path), name)
+    dst = os.path.join(str(tmp_path), "oracle_copy")
     shutil.copytree(os.path.join(ROOT, "oracle"), dst,
                     ignore=shutil.ignore_patterns("*.so", "*.tmp*", "__pycache__"))
     if old is not None:
-        src = os.path.join(dst, "scpl_oracle.c")
+        src = os.path.join(dst, "__init__.py" if name.endswith("(py)") else "scpl_oracle.c")
         with open(src) as fh:
             text = fh.read()
         assert text.count(old) == 1, f"mutation target not unique: {old[:40]}"
@@ -78,6 +85,6 @@ def test_unmodified_copy_passes(tmp_path):
 
 @pytest.mark.parametrize("name,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
 def test_planted_error_fails_a_pin(tmp_path, name, old, new):
-    r = _run_pins(_copy(tmp_path, "oracle_mut", old, new))
+    r = _run_pins(_copy(tmp_path, name, old, new))
     assert r.returncode == 1, (name, r.returncode, r.stdout[-2000:])
     assert "failed" in r.stdout
