@@ -48,6 +48,17 @@ MUTATIONS = [
     ("forward diagonal term from the wrong column",
      "A[p] = (u && j >= 1) ? abs((int)u[j] - (int)r[j - 1]) : 0;",
      "A[p] = (u && j >= 1) ? abs((int)u[j - 1] - (int)r[j - 1]) : 0;"),
+    ("label of the previous row's column",
+     "CE[p] = (int64_t)E[p] + up[best_j];\n            L[p] = L[(long)(i - 1) * W + best_j];",
+     "CE[p] = (int64_t)E[p] + up[best_j];\n            L[p] = best_j;"),
+    ("no cap on k", "int cap = k < W - target ? k : W - target;", "int cap = k;"),
+    ("flush starts after the crossing frame", "            start = f;",
+     "            start = f + 1;"),
+    ("maxval kept across a flush", "M = maxval_mode == 1 ? maxval_theory : emax;",
+     "M = maxval_mode == 1 ? maxval_theory : M1;"),
+    ("spread scaled by 128, not 256",
+     "int64_t Q = (int64_t)n1 * a2 - a1 * a1;\n            A += (int64_t)isqrt_floor((uint64_t)Q << 16);",
+     "int64_t Q = (int64_t)n1 * a2 - a1 * a1;\n            A += (int64_t)isqrt_floor((uint64_t)Q << 14);"),
     ("insertion mean rounds down (py)", "out[t0:t1, i] = ((a + c + 1) >> 1).astype(np.uint8)",
      "out[t0:t1, i] = ((a + c) >> 1).astype(np.uint8)"),
     ("inserted pixel blends with the left neighbour (py)",
@@ -75,7 +86,7 @@ def _run_pins(path: str) -> subprocess.CompletedProcess:
     env = dict(os.environ, SCPL_ORACLE_DIR=path)
     return subprocess.run([sys.executable, "-m", "pytest", PINS, "-x", "-q", "-p",
                            "no:cacheprovider"], capture_output=True, text=True, env=env,
-                          cwd=ROOT, timeout=600)
+                          cwd=ROOT, timeout=300)
 
 
 def test_unmodified_copy_passes(tmp_path):

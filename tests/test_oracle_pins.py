@@ -387,6 +387,17 @@ def test_new_buffer_keeps_its_first_frames_maximum(orc):
     assert np.array_equal(orc.scan(e, alpha=0.2), [0, 3, 5])
 
 
+def test_new_buffer_does_not_inherit_the_closed_buffers_maximum(orc):
+    """Eq. 9's maxval belongs to the open buffer: frame 0 peaks at 2550 and the
+    zero frame 1 flushes it, so buffer 2 starts with maxval 0.  Frame 2 at 10
+    spreads it by 10 per pixel (STD sum 10*H*W) against 0.2*10*H*W, so frame 2
+    starts buffer 3; had the closed buffer's 2550 carried over (threshold
+    510*H*W) it would have joined."""
+    e = np.zeros((3, 3, 4), np.int32)
+    e[0], e[2] = 2550, 10
+    assert np.array_equal(orc.scan(e, alpha=0.2), [0, 1, 2, 3])
+
+
 # ------------------------------------------------ C12: horizontal seams (Sec. 2)
 def test_carve_job_height_is_classic_horizontal_seam_carving(orc):
     """k = 1, one frame, gradient energy: the job's height pass removes the
