@@ -59,6 +59,17 @@ MUTATIONS = [
     ("spread scaled by 128, not 256",
      "int64_t Q = (int64_t)n1 * a2 - a1 * a1;\n            A += (int64_t)isqrt_floor((uint64_t)Q << 16);",
      "int64_t Q = (int64_t)n1 * a2 - a1 * a1;\n            A += (int64_t)isqrt_floor((uint64_t)Q << 14);"),
+    ("first child per parent instead of the least",
+     "if (best[a].col < 0 || cand_less(&c, &best[a])) best[a] = c;",
+     "if (best[a].col < 0) best[a] = c;"),
+    ("seams recorded at the current column",
+     "if (seams) seams[(long)(removed + s) * H + i] = (int16_t)orig[p];",
+     "if (seams) seams[(long)(removed + s) * H + i] = (int16_t)path[i];"),
+    ("every buffer carved from the clip's first frames",
+     "int it = orc_carve_buffer(frames + 3 * (long)t0 * hw, D + (long)t0 * hw, tb, H, W0, target,",
+     "int it = orc_carve_buffer(frames, D + (long)t0 * hw, tb, H, W0, target,"),
+    ("one-sided frame difference", "D[(long)t * hw + p] = (uint8_t)abs(a - b);",
+     "D[(long)t * hw + p] = (uint8_t)(a > b ? a - b : 0);"),
     ("insertion mean rounds down (py)", "out[t0:t1, i] = ((a + c + 1) >> 1).astype(np.uint8)",
      "out[t0:t1, i] = ((a + c) >> 1).astype(np.uint8)"),
     ("inserted pixel blends with the left neighbour (py)",
