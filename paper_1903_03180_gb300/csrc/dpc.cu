@@ -71,10 +71,8 @@ constexpr int DPC_S = 16;                        // rows per TMA stage of the en
 // sub-partition); and the columns per lane V (4 or 2; 2 only with R = 16).
 __host__ __device__ constexpr int dpc_ww(int V) { return 32 * V; }   // a warp's window
 __host__ __device__ constexpr int dpc_oww(int R, int V) { return dpc_ww(V) - 2 * R; }
-// energy stages in flight per warp (8 warps of 128-column windows keep 2 to
-// fit shared memory)
-// (8 warps of 128-column windows, or 4 with the forward terms' second ring,
-// keep 2 to fit shared memory)
+// energy stages in flight per warp (8 warps of 128-column windows, or 4 with
+// the forward terms' second ring, keep 2 to fit shared memory)
 __host__ __device__ constexpr int dpc_nst(int WPC, int V, bool FWD = false) {
     return V == 4 && (WPC == 8 || FWD) ? 2 : 4;
 }
