@@ -150,3 +150,24 @@ def test_tuning_cache_round_trip_host_only(lib, tmp_path):
     keys = ("H", "W", "dpc_halo", "dpc_warps", "dpc_lane_cols", "update_rows")
     assert [{k: t[k] for k in keys} for t in after] == [{k: t[k] for k in keys} for t in before]
     scpl.scpl_tuning_clear()
+
+
+def test_forward_terms_enter_the_overflow_rule(lib):
+    """A column's cumulative cost must stay below 2^31 with the forward terms
+    too: each row adds at most the buffer's summed energy plus wf times a row
+    term and a diagonal term (255 each a frame).  At 1080 rows and 128-frame
+    buffers that holds for wf = 0 but not for wf = 255, and admission (host
+    arithmetic, no GPU) refuses the job."""
+    from paper_1903_03180_gb300 import scpl
+    j = scpl.Job()
+    j.frames, j.out = 1, 1   # never dereferenced
+    j.T, j.H, j.W, j.target_W, j.target_H, j.k = 128, 1080, 1920, 1440, 1080, 32
+    p = scpl.scpl_default_params()
+    assert scpl.scpl_job_footprint(p, j) > 0
+    em, tb = 255 * (8 * p.wg + p.wm), 128
+    p.wf = 255
+    assert (em * tb + 2 * 255 * 255 * tb) * 1080 >= 2 ** 31
+    assert scpl.scpl_job_footprint(p, j) == 0
+    p.wf = 1
+    assert (em * tb + 2 * 255 * 1 * tb) * 1080 < 2 ** 31
+    assert scpl.scpl_job_footprint(p, j) > 0
