@@ -268,11 +268,11 @@ scpl_status scpl_carve_host_many(scpl_handle h, int n, const uint8_t *const *fra
                                  int *n_buffers);
 
 /* scpl_seams without any memory allocation.  The paper has no counterpart:
- * this exists for callers that must not allocate device memory -- code that is
- * recording a CUDA graph (allocation is not allowed during stream capture), a
- * real-time frame loop that cannot take cudaMalloc's implicit synchronisation
- * of the device, or a host application that hands out all device memory from
- * its own fixed pool.  It computes exactly what scpl_seams computes (one SCPL
+ * this exists for callers that must not allocate device memory -- a real-time
+ * frame loop that cannot take cudaMalloc's implicit synchronisation of the
+ * device, or a host application that hands out all device memory from its
+ * own fixed pool and lets no library allocate after start-up.  It computes
+ * exactly what scpl_seams computes (one SCPL
  * iteration: Eq. 4 DP with parental labels, Eq. 6 per-parent argmin, the
  * k_eff lowest children traced back), needs no handle, and calls no
  * cudaMalloc, cudaFree or allocating library routine.
@@ -282,7 +282,7 @@ scpl_status scpl_carve_host_many(scpl_handle h, int n, const uint8_t *const *fra
  *   stream  cudaStream_t as void* (NULL = legacy default stream)
  * Its scratch is one fixed array of about 9 MiB in device memory, reserved on
  * every GPU that loads the library and held until the process exits.  Limits
- * (else SCPL_EINVAL): H*W <= 2^21, W <= 4096, k <= 64.  The first call on a
+ * (else SCPL_EINVAL): H*W <= 2^21, W <= 4096, H <= 65535, k <= 64.  The first call on a
  * device looks up the array's device address (once per device, with that
  * device current); make that first call before any stream capture.  All calls
  * share the one array: calls whose work overlaps on the GPU (other streams,

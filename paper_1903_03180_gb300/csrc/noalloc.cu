@@ -1,14 +1,15 @@
 // scpl_seams_noalloc: one SCPL iteration on a caller's energy map that
 // allocates no memory at all.
 //
-// Who needs it: code that may not call cudaMalloc -- a caller recording work
-// into a CUDA graph (allocation is not allowed while a stream is being
-// captured), a real-time frame loop that cannot afford cudaMalloc's implicit
-// device-wide synchronisation, or a host application that owns all device
-// memory through its own fixed pool and forbids libraries from allocating
-// after start-up.  scpl_seams grows handle-owned workspaces with cudaMalloc;
-// this entry point instead works in one fixed scratch array that the library
-// reserves in device memory when it is loaded.
+// Who needs it: code that may not call cudaMalloc -- a real-time frame loop
+// that cannot afford cudaMalloc's implicit device-wide synchronisation (it
+// stalls every stream of the device until the allocation is done), or a host
+// application that owns all device memory through its own fixed pool and
+// forbids libraries from allocating after start-up, so that a long-running
+// process can never fail half-way for lack of memory.  scpl_seams grows
+// handle-owned workspaces with cudaMalloc; this entry point instead works in
+// one fixed scratch array that the library reserves in device memory when it
+// is loaded.
 //
 // The scratch is the file-scope __device__ array below.  Every GPU that loads
 // the library holds it until the process exits.  In host code `g_scratch` is

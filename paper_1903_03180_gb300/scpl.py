@@ -391,7 +391,8 @@ def scpl_carve_host(h, frames, target_W: int, k: int, out, seams=None) -> np.nda
 
 def scpl_seams_noalloc(energy, k: int, cols, stream=None) -> int:
     """scpl_seams for callers that may not allocate device memory: works in
-    the library's fixed scratch array (H*W <= 2^21, W <= 4096, k <= 64).
+    the library's fixed scratch array (H*W <= 2^21, W <= 4096, H <= 65535,
+    k <= 64).
     energy: cuda int32 [H,W]; cols: cuda int16 [k,H] (written).  Returns k_eff."""
     import torch
     ep = _dev_ptr(energy, torch.int32, 2, "energy")

@@ -1,7 +1,9 @@
 """scpl_seams_noalloc -- the entry point for callers that may not allocate
-device memory (graph capture, real-time loops, applications with their own
-fixed memory pool) -- must give exactly what scpl_seams gives, call after
-call, although every call reuses the same fixed scratch array.
+device memory (a real-time frame loop that cannot take cudaMalloc's
+device-wide synchronisation, an application that hands out all device memory
+from its own fixed pool) -- must give exactly what scpl_seams gives, call
+after call, although every call reuses the same fixed scratch array, and must
+take no device memory of its own.
 
 This file is named to be collected last, so that a failure here comes after
 every other test has run."""
@@ -74,3 +76,46 @@ def test_sizes_beyond_the_scratch_are_rejected(lib):
     with pytest.raises(lib.SCPLError) as ei:
         lib.scpl_seams_noalloc(big_k, 65, cols65)
     assert ei.value.status == lib.SCPL_EINVAL
+    # H * W one row of 1024 beyond 2^21
+    tall = torch.zeros((2049, 1024), dtype=torch.int32, device="cuda")
+    cols_t = torch.zeros((4, 2049), dtype=torch.int16, device="cuda")
+    with pytest.raises(lib.SCPLError) as ei:
+        lib.scpl_seams_noalloc(tall, 4, cols_t)
+    assert ei.value.status == lib.SCPL_EINVAL
+    # more rows than the removal lists index, although H * W fits
+    high = torch.zeros((65536, 1), dtype=torch.int32, device="cuda")
+    cols_h = torch.zeros((1, 65536), dtype=torch.int16, device="cuda")
+    with pytest.raises(lib.SCPLError) as ei:
+        lib.scpl_seams_noalloc(high, 1, cols_h)
+    assert ei.value.status == lib.SCPL_EINVAL
+
+
+def test_calls_take_no_device_memory(lib):
+    """After one call has loaded the kernels, further calls leave the free
+    device memory unchanged: nothing is allocated, not even temporarily kept."""
+    r = np.random.default_rng(7)
+    E = torch.from_numpy(r.integers(0, 2551, (1080, 1920)).astype(np.int32)).cuda()
+    cols = torch.full((32, 1080), -1, dtype=torch.int16, device="cuda")
+    lib.scpl_seams_noalloc(E, 32, cols)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(8):
+        lib.scpl_seams_noalloc(E, 32, cols)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+
+
+def test_on_a_side_stream(lib):
+    """A call on a stream other than the default one gives the same seams."""
+    r = np.random.default_rng(11)
+    E = torch.from_numpy(r.integers(0, 300, (333, 1500)).astype(np.int32)).cuda()
+    ref_k, ref = _seams_with_workspace(lib, E, 24)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        cols = torch.full((24, 333), -1, dtype=torch.int16, device="cuda")
+        ke = lib.scpl_seams_noalloc(E, 24, cols, stream=side)
+    side.synchronize()
+    assert ke == ref_k
+    assert np.array_equal(cols.cpu().numpy()[:ke], ref)
