@@ -191,3 +191,27 @@ def batch_spec(n_clips: int = 256, T: int = 32, seed: int = SEED_BASE ^ 4):
 def batch_clip(spec: dict) -> np.ndarray:
     """Frames of one clip of the batched workload (one scene, no cuts)."""
     return clip(spec["T"], spec["H"], spec["W"], spec["seed"])
+
+
+SERVE_SIZES = ((360, 640, 16), (720, 1280, 32), (1080, 1920, 32), (2160, 3840, 64))
+
+
+def serve_jobs(n_jobs: int = 20, seed: int = SEED_BASE ^ 5):
+    """A fixed list of served retarget jobs at the serving workload's sizes,
+    without frames: for job j its size (H, W, k drawn uniformly from
+    SERVE_SIZES), its length T ~ U[16, 128], its target width (a width
+    reduction ~ U[10 %, 40 %], rounded) and the seed of its frames."""
+    r = _rng(seed)
+    out = []
+    for j in range(n_jobs):
+        H, W, k = SERVE_SIZES[int(r.integers(0, len(SERVE_SIZES)))]
+        T = int(r.integers(16, 129))
+        red = float(r.uniform(0.10, 0.40))
+        out.append({"job": j, "T": T, "H": H, "W": W, "target_W": W - int(round(W * red)),
+                    "target_H": H, "k": k, "seed": (seed * 1000003 + j) & 0xFFFFFFFF})
+    return out
+
+
+def serve_clip(spec: dict) -> np.ndarray:
+    """Frames of one served job: a clip with scene cuts every 40-90 frames."""
+    return clip(spec["T"], spec["H"], spec["W"], spec["seed"], cuts=(40, 90))
