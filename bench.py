@@ -427,50 +427,83 @@ def run_native(args) -> None:
         houts = [torch.empty((T, H, target, 3), dtype=torch.uint8).pin_memory() for _ in range(2)]
         hin_np, hout_np = hin.numpy(), [o.numpy() for o in houts]
 
-        def timed_host(fn):
+        def timed_host(fn, reps=1):
+            """Wall time of fn() (host memory in and out, synchronised), after
+            one untimed call; the median of `reps` timed calls, max over ranks."""
             fn()
             torch.cuda.synchronize()
-            if dist:
-                dist.barrier()
-            t0 = time.perf_counter()
-            fn()
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            if dist:
-                t = torch.tensor([dt], device="cuda")
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                dt = float(t.item())
-            return dt
+            times = []
+            for _ in range(reps):
+                if dist:
+                    dist.barrier()
+                t0 = time.perf_counter()
+                fn()
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                if dist:
+                    t = torch.tensor([dt], device="cuda")
+                    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                    dt = float(t.item())
+                times.append(dt)
+            return float(np.median(times)), times
 
-        # the machine's host<->device copy bandwidth right now (pinned, one stream
-        # each way), reported beside the end-to-end figures
+        # the box's host<->device copy rates right now (page-locked, one
+        # stream each way): the library's link copy (scpl_copy), which the
+        # host paths use, and the copy engines (torch's copy_) for context
         dtmp = torch.empty_like(frames)
         otmp = torch.empty((T, H, target, 3), dtype=torch.uint8, device="cuda")
 
-        def copy_gbs(dst, src):
+        def rate(fn, nbytes):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            dst.copy_(src, non_blocking=True)
+            fn()
             torch.cuda.synchronize()
-            return src.numel() / (time.perf_counter() - t0) / 1e9
+            return nbytes / (time.perf_counter() - t0) / 1e9
 
-        copy_bw = {"h2d_gbs": round(copy_gbs(dtmp, hin), 1),
-                   "d2h_gbs": round(copy_gbs(houts[0], otmp), 1)}
-        del dtmp, otmp
+        def copy_rates():
+            return {
+                "link_h2d_gbs": round(rate(lambda: scpl.scpl_copy(dtmp, hin), hin.nbytes), 1),
+                "link_d2h_gbs": round(rate(lambda: scpl.scpl_copy(houts[0], otmp),
+                                           houts[0].nbytes), 1),
+                "engine_h2d_gbs": round(rate(lambda: dtmp.copy_(hin, non_blocking=True),
+                                             hin.nbytes), 1),
+                "engine_d2h_gbs": round(rate(lambda: houts[0].copy_(otmp, non_blocking=True),
+                                             houts[0].nbytes), 1)}
+
+        copy_bw = copy_rates()
         ck = ClockSampler(gpu_id)
         ck.start()
         time.sleep(0.3)
-        dt = timed_host(lambda: scpl.scpl_carve_host_many(
-            h, [hin_np] * args.steps, target, k, [hout_np[i % 2] for i in range(args.steps)]))
+        n_clips = max(args.steps, 2)
+        dt, reps = timed_host(lambda: scpl.scpl_carve_host_many(
+            h, [hin_np] * n_clips, target, k, [hout_np[i % 2] for i in range(n_clips)]),
+            reps=args.e2e_reps)
         e2e_clk = ck.stop()
-        e2e = {"value": round(T * ws * args.steps / dt, 2), "unit": UNIT,
+        dt_one, _ = timed_host(lambda: scpl.scpl_carve_host_many(h, [hin_np], target, k,
+                                                                 [hout_np[0]]), reps=3)
+        copy_bw_after = copy_rates()
+        del dtmp, otmp
+        steady_ms = (dt - dt_one) / (n_clips - 1) * 1e3
+        dev_ms = total_ms / args.steps
+        copies_ms = (hin.nbytes / copy_bw["link_h2d_gbs"] +
+                     houts[0].nbytes / copy_bw["link_d2h_gbs"]) / 1e6
+        e2e = {"value": round(T * ws * n_clips / dt, 2), "unit": UNIT,
                "h2d_bytes_per_step": int(frames_np.nbytes),
                "d2h_bytes_per_step": int(hout_np[0].nbytes),
-               "api": "scpl_carve_host_many: the steps' clips streamed through two device "
-                      "slots, copies overlapping the kernels", "clocks": e2e_clk,
-               "copy_bandwidth": copy_bw}
-        dt1 = timed_host(lambda: [scpl.scpl_carve_host(h, hin_np, target, k, hout_np[0])
-                                  for _ in range(args.steps)])
+               "api": "scpl_carve_host_many: %d clips streamed from page-locked host memory "
+                      "through two device slots, uploads and copies back by scpl_copy "
+                      "overlapping the kernels" % n_clips,
+               "repetitions_s": [round(x, 4) for x in reps],
+               "statistic": "median of %d timed calls after one untimed call" % len(reps),
+               "one_clip_ms": round(dt_one * 1e3, 2),
+               "steady_clip_ms": round(steady_ms, 2),
+               "device_resident_clip_ms": round(dev_ms, 2),
+               "copies_alone_ms": round(copies_ms, 2),
+               "copies_hidden": round((dev_ms + copies_ms - steady_ms) / copies_ms, 3),
+               "clocks": e2e_clk,
+               "copy_bandwidth": copy_bw, "copy_bandwidth_after": copy_bw_after}
+        dt1, _ = timed_host(lambda: [scpl.scpl_carve_host(h, hin_np, target, k, hout_np[0])
+                                     for _ in range(args.steps)])
         e2e_single = {"value": round(T * ws * args.steps / dt1, 2), "unit": UNIT,
                       "api": "scpl_carve_host, one call per clip"}
 
@@ -861,6 +894,8 @@ def main():
                     help="weight of the forward terms in the seam cost (0: the paper's "
                          "backward energy)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-reps", type=int, default=3,
+                    help="timed repetitions of the end-to-end call (the median is reported)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

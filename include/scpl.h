@@ -195,6 +195,19 @@ scpl_status scpl_enlarge_job(scpl_handle h, const uint8_t *frames, int T, int H,
 scpl_status scpl_blend_sharpness(scpl_handle h, const uint8_t *frames, int T, int H, int W,
                                  int window, int64_t *num, int64_t *den);
 
+/* The integer square root of the buffer decision (Sec. 3.2, Eq. 7-8): the
+ * scan adds floor(sqrt(65536 * Q)) over the pixels, with Q = n*S2 - S1^2 the
+ * scaled spread of a pixel's energy over the n buffered frames.  This runs the
+ * scan's own device routine on caller values, so that it can be checked
+ * against an exact integer square root at its edges.
+ *   x [device] uint64 [n], each below 2^53 (the scan's values stay below
+ *     2^51; larger values give an unspecified result, never a fault)
+ *   r [device] uint32 [n], written: r[i] = floor(sqrt(x[i]))
+ *   stream cudaStream_t as void* (NULL = legacy default stream); asynchronous
+ * SCPL_EINVAL for n < 0 or NULL arrays with n > 0; SCPL_ECUDA if the launch
+ * fails. */
+scpl_status scpl_isqrt(const uint64_t *x, uint32_t *r, long n, void *stream);
+
 /* Bound, in nanoseconds, of each device-wide wait of the handle's buffer
  * scans: the per-round reduction across the scan's CTAs and the waits for
  * arriving frames (default 2e9).  A wait that runs out makes its call return
@@ -237,13 +250,11 @@ scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W
                        int16_t *seams);
 
 /* scpl_carve on host memory, through library-owned device buffers.  The
- * copies overlap the work: frames go up in chunks of 8 on a copy stream and
- * the buffer scan reads each chunk as soon as it has arrived (a stream memory
- * operation raises a device counter after every chunk; the scan's wait for it
- * is bounded and ends in SCPL_ETIMEOUT); every spatiotemporal buffer is
- * gathered and copied back as soon as it is carved, while the others carve
- * on.  Page-locked host memory makes the copies asynchronous; pageable memory
- * works too, without the overlap.
+ * frames go up by scpl_copy before the buffer scan reads them; every
+ * spatiotemporal buffer is gathered and copied back (scpl_copy, on a copy
+ * stream) as soon as it is carved, while the others carve on.  Page-locked
+ * host memory is read and written by the copy kernel; pageable memory works
+ * too, through the copy engines.
  *   frames [host] uint8 [T][H][W][3]   out [host] uint8 [T][H][target_W][3]
  *   seams  [host] int16 [n_buffers][W - target_W][H] or NULL (size it for T
  *          buffers when the count is not known in advance)
@@ -253,11 +264,12 @@ scpl_status scpl_carve_host(scpl_handle h, const uint8_t *frames, int T, int H, 
                             int *n_buffers, int16_t *seams);
 
 /* scpl_carve_host for n clips of one shape, streamed through two device
- * slots: clip i+1's frames go up on an input stream while clip i carves, and
- * clip i's carved buffers come back on the copy stream while clip i+1 scans
- * and carves, so the copies in both directions overlap the kernels.  Every
- * clip's result equals scpl_carve_host's.  Needs stream memory operations
- * (else SCPL_ECUDA).
+ * slots: clip i+1's frames go up on an input stream once clip i's buffer scan
+ * has finished, so the upload runs beside clip i's carving; clip i's carved
+ * buffers come back on the copy stream while the rest of clip i and then clip
+ * i+1 run.  Both directions use scpl_copy.  Clip i+1's scan waits for its
+ * upload through stream order only.  Every clip's result equals
+ * scpl_carve_host's.
  *   frames    [host] n pointers to uint8 [T][H][W][3] (page-locked)
  *   out       [host] n pointers to uint8 [T][H][target_W][3] (page-locked)
  *   n_buffers [host] int [n] or NULL: each clip's buffer count
@@ -266,6 +278,21 @@ scpl_status scpl_carve_host(scpl_handle h, const uint8_t *frames, int T, int H, 
 scpl_status scpl_carve_host_many(scpl_handle h, int n, const uint8_t *const *frames, int T,
                                  int H, int W, int target_W, int k, uint8_t *const *out,
                                  int *n_buffers);
+
+/* The bulk transfer of the host-memory entry points (the paper has no
+ * counterpart: it moves frames between host and device memory).  Copies
+ * `bytes` from src to dst, asynchronously on `stream` (a cudaStream_t as
+ * void*, NULL = legacy default stream), where either side may be device
+ * memory or page-locked host memory.  When both are addressable by the device
+ * and share their offset within 16 bytes, a kernel of 48 CTAs reads or writes
+ * the host side over the CPU-GPU link with 16-byte accesses (on a
+ * Grace-attached GB300 that holds about 210 GB/s up and 192 GB/s down, where
+ * the copy engines were seen to fall to 25-60 GB/s for seconds at a time);
+ * otherwise it is cudaMemcpyAsync.  The caller keeps both buffers alive and
+ * unchanged until the stream has passed the copy.
+ * SCPL_EINVAL for a NULL pointer with bytes > 0; SCPL_ECUDA if the launch or
+ * the copy fails. */
+scpl_status scpl_copy(void *dst, const void *src, size_t bytes, void *stream);
 
 /* scpl_seams without any memory allocation.  The paper has no counterpart:
  * this exists for callers that must not allocate device memory -- a real-time

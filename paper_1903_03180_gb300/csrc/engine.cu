@@ -361,8 +361,7 @@ scpl_status start_job(Srv *s, int jid) {
     if (j.on_host) {
         uint8_t *in = nullptr;
         SRV_ALLOC(s, own(rgb_bytes(j.T, j.H, j.W), &in));
-        SRV_CUDA(s, cudaMemcpyAsync(in, j.frames, rgb_bytes(j.T, j.H, j.W),
-                                    cudaMemcpyHostToDevice, m));
+        SRV_CUDA(s, link_copy(in, j.frames, rgb_bytes(j.T, j.H, j.W), m));
         J.in_dev = in;
         SRV_ALLOC(s, own(rgb_bytes(j.T, j.target_H, j.target_W), &J.out_dev));
     } else {
@@ -376,8 +375,7 @@ scpl_status start_job(Srv *s, int jid) {
         SRV_CUDA(s, cudaMemcpyAsync(J.out_dev, J.in_dev, rgb_bytes(j.T, j.H, j.W),
                                     cudaMemcpyDeviceToDevice, m));
         if (j.on_host)
-            SRV_CUDA(s, cudaMemcpyAsync(j.out, J.out_dev, rgb_bytes(j.T, j.H, j.W),
-                                        cudaMemcpyDeviceToHost, m));
+            SRV_CUDA(s, link_copy(j.out, J.out_dev, rgb_bytes(j.T, j.H, j.W), m));
         if (j.buffer_starts) {
             j.buffer_starts[0] = 0;
             j.buffer_starts[1] = j.T;
@@ -956,8 +954,7 @@ scpl_status pass_done(Srv *s, int pid, cudaStream_t gs) {
         count_launches(s, 1);
     }
     if (j.on_host)
-        SRV_CUDA(s, cudaMemcpyAsync(j.out, J.out_dev, rgb_bytes(j.T, j.target_H, j.target_W),
-                                    cudaMemcpyDeviceToHost, gs));
+        SRV_CUDA(s, link_copy(j.out, J.out_dev, rgb_bytes(j.T, j.target_H, j.target_W), gs));
     SRV_CUDA(s, cudaEventRecord(J.done, gs));
     J.state = J_FINISHING;
     return SCPL_OK;

@@ -1007,8 +1007,23 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
     }
 }
 
+// r[i] = floor(sqrt(x[i])) by the routine the scan applies to 65536 Q of
+// every pixel (Eq. 7-8); exposed so that it can be checked at its edges.
+__global__ void k_isqrt_check(const unsigned long long *x, uint32_t *r, long n) {
+    const long stride = (long)gridDim.x * blockDim.x;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += stride)
+        r[i] = isqrt53(x[i]);
+}
 
 }  // namespace
+
+cudaError_t launch_isqrt_check(const unsigned long long *x, uint32_t *r, long n,
+                               cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const long blocks = (n + 255) / 256;
+    k_isqrt_check<<<(int)(blocks < 1216 ? blocks : 1216), 256, 0, s>>>(x, r, n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_energy_api(const uint8_t *rgb, int T, int H, int W, int wg, int wm,
                               int32_t *energy, cudaStream_t s) {

@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -112,17 +113,15 @@ struct scpl_ctx {
     DevBuf in_frames, out_frames, seams_dev;
     DevBuf qY, qacc;   // blend sharpness: luma of every frame, the two sums
     DevBuf ej_mid, ej_tin, ej_tout;   // scpl_enlarge_job: widened, transposed, enlarged
-    // scpl_carve_host_many: a second input and output slot, the input copy
-    // stream and the second arrival counter
-    DevBuf in2, out2, ready2;
+    // scpl_carve_host_many: a second input and output slot and the input copy
+    // stream
+    DevBuf in2, out2;
     cudaStream_t istream = nullptr;
     DevBuf Yfm;
     bool autotune = false;
     unsigned long long wait_ns = SPIN_LIMIT_NS;   // bound of the scan's device-wide waits
-    // host-memory path: copy stream, side stream for early gathers, the
-    // arrival counter of the frames and its driver entry point
+    // host-memory path: copy stream and side stream for early gathers
     cudaStream_t cstream = nullptr, gstream = nullptr;
-    DevBuf ready;
     HostBuf h_small;   // starts + n_buffers + states readback
     Profiler prof;
     scpl_server_s *engine = nullptr;   // scpl_carve_batch's engine (created on first use)
@@ -353,14 +352,16 @@ PFN_cuStreamWriteValue32_v11070 stream_write_value() {
     return fn;
 }
 
-// scpl_carve with two options of the host-memory path: `ready` (frames still
-// arriving, see ScanArgs::ready) and `host_out` (every buffer's output frames
+// scpl_carve with the options of the host-memory paths: `ready` (frames still
+// arriving, see ScanArgs::ready), `host_out` (every buffer's output frames
 // are gathered as soon as the buffer is carved and copied to host_out on the
-// copy stream while the other buffers carve on).
+// copy stream while the other buffers carve on) and `after_scan` (called
+// once the scan has finished, before the carving is issued).
 scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, int target_W,
                       int k, uint8_t *out, int32_t *buffer_starts, int *n_buffers,
                       int16_t *seams, const unsigned *ready, int ready_frames,
-                      uint8_t *host_out) {
+                      uint8_t *host_out,
+                      const std::function<scpl_status()> &after_scan = nullptr) {
     scpl_status s = check_frames(h, frames, T, H, W);
     if (s != SCPL_OK) return s;
     if (!out) return fail(h, SCPL_EINVAL, "out is NULL");
@@ -371,6 +372,9 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
 
     std::vector<int> starts;
     if ((s = run_scan(h, frames, T, H, W, starts, true, nullptr, nullptr, ready, ready_frames)) != SCPL_OK) return s;
+    // the scan has finished (its starts are on the host): work that must not
+    // share the GPU with the scan's device-wide waits may be issued now
+    if (after_scan && (s = after_scan()) != SCPL_OK) return s;
     const int nb = (int)starts.size() - 1;
     const int remove = W - target_W;
     TraceRange trace("scpl.carve");
@@ -434,8 +438,8 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
                   }));
         SCPL_CUDA(h, cudaEventRecord(ev_gathered, h->gstream));
         SCPL_CUDA(h, cudaStreamWaitEvent(h->cstream, ev_gathered, 0));
-        SCPL_CUDA(h, cudaMemcpyAsync(host_out + (size_t)t0 * frame_out, out + (size_t)t0 * frame_out,
-                                     (size_t)nt * frame_out, cudaMemcpyDeviceToHost, h->cstream));
+        SCPL_CUDA(h, link_copy(host_out + (size_t)t0 * frame_out, out + (size_t)t0 * frame_out,
+                               (size_t)nt * frame_out, h->cstream));
         gathered[b] = 1;
         return SCPL_OK;
     };
@@ -603,7 +607,7 @@ void scpl_destroy(scpl_handle h) {
     DevBuf *bufs[] = {&h->Y, &h->D, &h->ering, &h->S1, &h->S2, &h->partA, &h->partM,
                       &h->count, &h->starts, &h->nbuf, &h->errw, &h->E0, &h->cws, &h->bof,
                       &h->in_frames, &h->out_frames, &h->seams_dev, &h->Yfm, &h->qY,
-                      &h->qacc, &h->in2, &h->out2, &h->ready2, &h->ej_mid, &h->ej_tin,
+                      &h->qacc, &h->in2, &h->out2, &h->ej_mid, &h->ej_tin,
                       &h->ej_tout};
     if (h->istream) cudaStreamSynchronize(h->istream);
     if (h->cstream) cudaStreamSynchronize(h->cstream);
@@ -613,7 +617,6 @@ void scpl_destroy(scpl_handle h) {
     if (h->cstream) cudaStreamDestroy(h->cstream);
     if (h->gstream) cudaStreamDestroy(h->gstream);
     if (h->istream) cudaStreamDestroy(h->istream);
-    h->ready.release();
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
     h->h_small.release();
     delete h;
@@ -768,6 +771,14 @@ scpl_status scpl_blend_sharpness(scpl_handle h, const uint8_t *frames, int T, in
     return SCPL_OK;
 }
 
+scpl_status scpl_isqrt(const uint64_t *x, uint32_t *r, long n, void *stream) {
+    if (n < 0 || (n > 0 && (!x || !r))) return SCPL_EINVAL;
+    if (launch_isqrt_check(reinterpret_cast<const unsigned long long *>(x), r, n,
+                           static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return SCPL_ECUDA;
+    return SCPL_OK;
+}
+
 scpl_status scpl_set_wait_limit(scpl_handle h, uint64_t ns) {
     if (!h) return SCPL_EINVAL;
     if (ns < 100000ull || ns > 60000000000ull)
@@ -853,40 +864,15 @@ scpl_status scpl_carve_host(scpl_handle h, const uint8_t *frames, int T, int H, 
     if (!h->cstream) SCPL_CUDA(h, cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
     if (!h->gstream) SCPL_CUDA(h, cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
     cudaStream_t st = h->stream;
-    // The frames go up in chunks on the copy stream; after each chunk a
-    // stream memory operation raises the arrival counter, and the scan reads a
-    // frame only once its chunk has arrived.  The carved frames come back per
-    // buffer as the buffers finish.
-    PFN_cuStreamWriteValue32_v11070 write_value = stream_write_value();
-    const unsigned *ready = nullptr;
-    constexpr int CHUNK = 8;
-    SCPL_CUDA(h, h->ready.ensure(sizeof(unsigned)));
-    SCPL_CUDA(h, cudaMemsetAsync(h->ready.p, 0, sizeof(unsigned), st));
-    cudaEvent_t ev = nullptr;
-    SCPL_CUDA(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    SCPL_CUDA(h, cudaEventRecord(ev, st));
-    SCPL_CUDA(h, cudaStreamWaitEvent(h->cstream, ev, 0));   // no copy before the reset
-    cudaEventDestroy(ev);
-    if (write_value) {
-        for (int c = 0; c * CHUNK < T; ++c) {
-            const int f0 = c * CHUNK, nf = std::min(CHUNK, T - f0);
-            SCPL_CUDA(h, cudaMemcpyAsync(h->in_frames.as<uint8_t>() + f0 * frame_in,
-                                         frames + f0 * frame_in, (size_t)nf * frame_in,
-                                         cudaMemcpyHostToDevice, h->cstream));
-            if (write_value(reinterpret_cast<CUstream>(h->cstream),
-                            reinterpret_cast<CUdeviceptr>(h->ready.p), (cuuint32_t)(c + 1),
-                            CU_STREAM_WRITE_VALUE_DEFAULT) != CUDA_SUCCESS)
-                return fail(h, SCPL_ECUDA, "cuStreamWriteValue32 failed");
-        }
-        ready = h->ready.as<unsigned>();
-    } else {   // no stream memory operations: copy everything first
-        SCPL_CUDA(h, cudaMemcpyAsync(h->in_frames.p, frames, in_bytes, cudaMemcpyHostToDevice, st));
-    }
+    // The frames go up by the link-copy kernel before the scan reads them (no
+    // kernel here waits on another); the carved frames come back per buffer as
+    // the buffers finish, by the same kernel on the copy stream.
+    SCPL_CUDA(h, link_copy(h->in_frames.p, frames, in_bytes, st));
     int nb = 0;
     std::vector<int> starts(T + 1);
     s = carve_run(h, h->in_frames.as<uint8_t>(), T, H, W, target_W, k,
                   h->out_frames.as<uint8_t>(), starts.data(), &nb,
-                  seams ? h->seams_dev.as<int16_t>() : nullptr, ready, CHUNK, out);
+                  seams ? h->seams_dev.as<int16_t>() : nullptr, nullptr, 1, out);
     cudaError_t e1 = cudaStreamSynchronize(h->cstream);
     cudaError_t e2 = cudaStreamSynchronize(h->gstream);
     if (s != SCPL_OK) return s;
@@ -915,28 +901,22 @@ scpl_status scpl_carve_host_many(scpl_handle h, int n, const uint8_t *const *fra
     }
     if (target_W < 2 || target_W > W)
         return fail(h, SCPL_EINVAL, "target_W=%d must be in [2, W=%d]", target_W, W);
-    PFN_cuStreamWriteValue32_v11070 write_value = stream_write_value();
-    if (!write_value) return fail(h, SCPL_ECUDA, "the driver lacks stream memory operations");
     const size_t frame_in = (size_t)H * W * 3;
     const size_t in_bytes = (size_t)T * frame_in, out_bytes = (size_t)T * H * target_W * 3;
     SCPL_CUDA(h, h->in_frames.ensure(in_bytes));
     SCPL_CUDA(h, h->in2.ensure(in_bytes));
     SCPL_CUDA(h, h->out_frames.ensure(out_bytes));
     SCPL_CUDA(h, h->out2.ensure(out_bytes));
-    SCPL_CUDA(h, h->ready.ensure(sizeof(unsigned)));
-    SCPL_CUDA(h, h->ready2.ensure(sizeof(unsigned)));
     if (!h->cstream) SCPL_CUDA(h, cudaStreamCreateWithFlags(&h->cstream, cudaStreamNonBlocking));
     if (!h->gstream) SCPL_CUDA(h, cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
     if (!h->istream) SCPL_CUDA(h, cudaStreamCreateWithFlags(&h->istream, cudaStreamNonBlocking));
     cudaStream_t st = h->stream;
     uint8_t *in_slot[2] = {h->in_frames.as<uint8_t>(), h->in2.as<uint8_t>()};
     uint8_t *out_slot[2] = {h->out_frames.as<uint8_t>(), h->out2.as<uint8_t>()};
-    unsigned *ready_slot[2] = {h->ready.as<unsigned>(), h->ready2.as<unsigned>()};
-    constexpr int CHUNK = 8;
-    // reset[s]: the slot's counter was zeroed on the input stream (the scan of
-    // the clip in the slot waits for it); done[s]: every read of the slot's
-    // input (the gathers) and of its output (the copies back) has finished
-    cudaEvent_t reset[2] = {}, done[2] = {};
+    // up[s]: the clip in slot s is on the device; done[s]: every read of the
+    // slot's input (the gathers) and of its output (the copies back) has
+    // finished, so the slot may take the next clip
+    cudaEvent_t up[2] = {}, done[2] = {};
     struct Guard {
         cudaEvent_t *a, *b;
         ~Guard() {
@@ -945,46 +925,41 @@ scpl_status scpl_carve_host_many(scpl_handle h, int n, const uint8_t *const *fra
                 if (b[s]) cudaEventDestroy(b[s]);
             }
         }
-    } guard{reset, done};
+    } guard{up, done};
     for (int s = 0; s < 2; ++s) {
-        SCPL_CUDA(h, cudaEventCreateWithFlags(&reset[s], cudaEventDisableTiming));
+        SCPL_CUDA(h, cudaEventCreateWithFlags(&up[s], cudaEventDisableTiming));
         SCPL_CUDA(h, cudaEventCreateWithFlags(&done[s], cudaEventDisableTiming));
     }
     // the caller's earlier work on the handle's stream comes first
     SCPL_CUDA(h, cudaEventRecord(done[0], st));
     SCPL_CUDA(h, cudaEventRecord(done[1], st));
-    auto upload = [&](int i) -> scpl_status {   // clip i's frames into slot i & 1
+    // Clip i's frames go up into slot i & 1 by the link-copy kernel on the
+    // input stream.  Clip i+1's upload is issued once clip i's scan has
+    // finished, so it runs beside clip i's carving and never beside a scan;
+    // clip i+1's scan waits for it by an event.  No kernel waits on another.
+    auto upload = [&](int i) -> scpl_status {
         const int s = i & 1;
         SCPL_CUDA(h, cudaStreamWaitEvent(h->istream, done[s], 0));
-        SCPL_CUDA(h, cudaMemsetAsync(ready_slot[s], 0, sizeof(unsigned), h->istream));
-        SCPL_CUDA(h, cudaEventRecord(reset[s], h->istream));
-        for (int c = 0; c * CHUNK < T; ++c) {
-            const int f0 = c * CHUNK, nf = std::min(CHUNK, T - f0);
-            SCPL_CUDA(h, cudaMemcpyAsync(in_slot[s] + f0 * frame_in, frames[i] + f0 * frame_in,
-                                         (size_t)nf * frame_in, cudaMemcpyHostToDevice,
-                                         h->istream));
-            if (write_value(reinterpret_cast<CUstream>(h->istream),
-                            reinterpret_cast<CUdeviceptr>(ready_slot[s]), (cuuint32_t)(c + 1),
-                            CU_STREAM_WRITE_VALUE_DEFAULT) != CUDA_SUCCESS)
-                return fail(h, SCPL_ECUDA, "cuStreamWriteValue32 failed");
-        }
+        SCPL_CUDA(h, link_copy(in_slot[s], frames[i], in_bytes, h->istream));
+        SCPL_CUDA(h, cudaEventRecord(up[s], h->istream));
         return SCPL_OK;
     };
     scpl_status s = upload(0);
     std::vector<int> starts(T + 1);
     for (int i = 0; i < n && s == SCPL_OK; ++i) {
         const int sl = i & 1;
-        // the next clip's frames go up while this one carves
-        if (i + 1 < n && (s = upload(i + 1)) != SCPL_OK) break;
-        SCPL_CUDA(h, cudaStreamWaitEvent(st, reset[sl], 0));
+        SCPL_CUDA(h, cudaStreamWaitEvent(st, up[sl], 0));
         int nb = 0;
+        const std::function<scpl_status()> next = [&]() -> scpl_status {
+            return i + 1 < n ? upload(i + 1) : SCPL_OK;
+        };
         s = carve_run(h, in_slot[sl], T, H, W, target_W, k, out_slot[sl], starts.data(), &nb,
-                      nullptr, ready_slot[sl], CHUNK, out[i]);
+                      nullptr, nullptr, 1, out[i], next);
         if (s != SCPL_OK) break;
         if (n_buffers) n_buffers[i] = nb;
-        // the slot is free once the gathers (input) and copies back (output)
-        // end: every gather is followed on the copy stream by its buffer's
-        // copy back, which waits for it
+        // every gather is followed on the copy stream by its buffer's copy
+        // back, which waits for it: the slot is free once the copy stream
+        // reaches this point
         SCPL_CUDA(h, cudaEventRecord(done[sl], h->cstream));
     }
     cudaError_t e1 = cudaStreamSynchronize(h->istream);

@@ -214,6 +214,9 @@ cudaError_t launch_energy_api(const uint8_t *rgb, int T, int H, int W, int wg, i
                               int32_t *energy, cudaStream_t s);
 int scan_grid_size(int H, int W, int *err_out);
 cudaError_t launch_scan(const ScanArgs &a, int grid, cudaStream_t s);
+// floor(sqrt(x)) of n values (device arrays) by the scan's own routine.
+cudaError_t launch_isqrt_check(const unsigned long long *x, uint32_t *r, long n,
+                               cudaStream_t s);
 // Several clips in one cooperative launch: tab (device) holds each clip's
 // arguments with its CTA range, block_clip (device) the clip of every CTA.
 cudaError_t launch_scan_multi(const ScanArgs *tab, const int *block_clip, int grid,
@@ -261,6 +264,11 @@ cudaError_t launch_gather_frames(const CarveWs &ws, const GatherFrame *tab, int 
 // [T][H][W][3] -> [T][W][H][3]
 cudaError_t launch_transpose_rgb(const uint8_t *src, int T, int H, int W, uint8_t *dst,
                                  cudaStream_t s);
+// Bulk copy between page-locked host memory and device memory (either way) by
+// a kernel of a few dozen CTAs that reads or writes the host side over the
+// CPU-GPU link (hostcopy.cu); memory the device cannot address goes through
+// cudaMemcpyAsync instead.
+cudaError_t link_copy(void *dst, const void *src, size_t bytes, cudaStream_t s);
 // Carving workspace of nb buffers in one slab: sets ws's geometry (from ws.H,
 // ws.W0, ws.kcap) and, when base is not NULL, its array pointers into base.
 // Returns the slab size in bytes.  dpc: also the cluster-DP tables.

@@ -94,6 +94,8 @@ SIGNATURES = {
     "scpl_carve": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
     "scpl_carve_host": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
     "scpl_seams_noalloc": (_I, [_P, _I, _I, _I, _P, _P, _P]),
+    "scpl_copy": (_I, [_P, _P, ctypes.c_size_t, _P]),
+    "scpl_isqrt": (_I, [_P, _P, ctypes.c_long, _P]),
     "scpl_set_profiling": (_I, [_P, _I]),
     "scpl_keff_log": (_I, [_P, _P, _I, _P]),
     "scpl_get_stats": (_I, [_P, ctypes.POINTER(Stats)]),
@@ -286,6 +288,34 @@ def scpl_carve_host_many(h, frames: list, target_W: int, k: int, outs: list) -> 
     return list(nbs)
 
 
+def scpl_copy(dst, src, stream=None):
+    """Copy src into dst (same number of bytes) with the library's host/device
+    transfer; each side a torch tensor (CUDA, or CPU page-locked) or a numpy
+    array (page-locked).  Asynchronous on `stream` (default: the current
+    torch stream)."""
+    import torch
+
+    def ptr_bytes(a):
+        if isinstance(a, torch.Tensor):
+            if not a.is_contiguous():
+                raise ValueError("tensors must be contiguous")
+            return a.data_ptr(), a.numel() * a.element_size()
+        a = np.asarray(a)
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data, a.nbytes
+    dp, dn = ptr_bytes(dst)
+    sp, sn = ptr_bytes(src)
+    if dn != sn:
+        raise ValueError(f"dst holds {dn} bytes, src {sn}")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    status = load().scpl_copy(ctypes.c_void_p(dp), ctypes.c_void_p(sp), sn, ctypes.c_void_p(st))
+    if status != SCPL_OK:
+        raise SCPLError(status, "scpl_copy failed")
+
+
 def scpl_enlarge(h, frames, target_W: int, k: int, out) -> np.ndarray:
     """Widen cuda uint8 [T,H,W,3] frames to target_W by seam insertion into
     out [T,H,target_W,3]; returns the buffer starts."""
@@ -324,6 +354,24 @@ def scpl_blend_sharpness(h, frames, window: int = 4) -> tuple[int, int]:
     _check(h, load().scpl_blend_sharpness(h, fp, T, H, W, int(window), ctypes.byref(n),
                                           ctypes.byref(d)))
     return n.value, d.value
+
+
+def scpl_isqrt(x, r, stream=None):
+    """r = floor(sqrt(x)) by the buffer scan's device routine (Eq. 7-8):
+    x cuda int64/uint64 [n] (values below 2^53), r cuda int32/uint32 [n]."""
+    import torch
+    if x.device.type != "cuda" or r.device.type != "cuda" or x.numel() != r.numel():
+        raise ValueError("x and r: CUDA tensors of the same length")
+    if x.element_size() != 8 or r.element_size() != 4 or not (x.is_contiguous() and
+                                                              r.is_contiguous()):
+        raise ValueError("x: contiguous 64-bit, r: contiguous 32-bit")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    status = load().scpl_isqrt(ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(r.data_ptr()),
+                               x.numel(), ctypes.c_void_p(st))
+    if status != SCPL_OK:
+        raise SCPLError(status, "scpl_isqrt failed")
 
 
 def scpl_set_wait_limit(h, ns: int):
