@@ -284,7 +284,7 @@ scpl_status scpl_carve_host_many(scpl_handle h, int n, const uint8_t *const *fra
  * `bytes` from src to dst, asynchronously on `stream` (a cudaStream_t as
  * void*, NULL = legacy default stream), where either side may be device
  * memory or page-locked host memory.  When both are addressable by the device
- * and share their offset within 16 bytes, a kernel of 48 CTAs reads or writes
+ * and share their offset within 16 bytes, a kernel of 16 CTAs reads or writes
  * the host side over the CPU-GPU link with 16-byte accesses (on a
  * Grace-attached GB300 that holds about 210 GB/s up and 192 GB/s down, where
  * the copy engines were seen to fall to 25-60 GB/s for seconds at a time);
@@ -321,8 +321,24 @@ scpl_status scpl_seams_noalloc(const int32_t *energy, int H, int W, int k, int16
 /* Per-kernel accounting of the handle's launches (not part of the paper: a
  * measurement aid).  While profiling is on, every kernel launch of the handle
  * is bracketed by CUDA events on the handle's stream, and every scpl_carve
- * call adds its kernels' algorithmic bytes (the bytes the method has to move,
- * by the model stated beside each kernel in the library's design notes).
+ * call adds its kernels' algorithmic bytes, the bytes the method has to move.
+ * Per launch, with H rows, W_c the width a buffer is carved at, W_n the width
+ * after the iteration, k_e its seam count and T_b its frames:
+ *   k_scan        28 per pixel and frame (RGB 3, luma and motion out 2, the
+ *                 previous luma 1, S1 and S2 read and written 16, energy 6)
+ *   k_energy_init H*(2*T_b*W + 10*W) per buffer (luma and motion of every
+ *                 frame, origin map, summed and per-pixel energy out)
+ *   k_dp          H*(4.5*W_c + 2*k_e) per buffer (energy read, directions
+ *                 written and read back, removal lists)
+ *   k_update      H*(12*W_n + 6*k_e) per buffer (origin map and energy read
+ *                 and written at the new width, the lists of a row and its
+ *                 neighbours; 4*W_n in a buffer's last iteration, which
+ *                 compacts only the origin map), plus (3*T_b + 8) per
+ *                 recomputed pixel
+ *   k_gather      H*target_W*(6*T + 2*n_buffers) per clip (colour in and
+ *                 out, the origin map of each buffer)
+ * With forward terms (wf > 0) the DP adds 4*W_c per row, the update 8*W_n
+ * per row and 4 per recomputed pixel, the initialisation H*(T_b*W + 12*W).
  *   scpl_set_profiling(h, 1) clears the counters and turns accounting on;
  *   scpl_set_profiling(h, 0) turns it off.
  *   scpl_get_stats synchronises the stream and fills *out. */

@@ -5,11 +5,11 @@
 // about 210 GB/s to 25-60 GB/s for seconds at a time once copies have run for
 // a while, and device-to-host copies follow at times.  Loads and stores issued
 // by SMs over the same link hold 209-211 GB/s (up) and 192 GB/s (down) the
-// whole time, and about 40 CTAs already reach those rates.  So every bulk
+// whole time, and a few dozen SMs already reach those rates.  So every bulk
 // frame copy of the host-memory paths goes through k_link_copy; the rest of
-// the GPU stays free for the carving kernels and the scan.  A host pointer that the device
-// cannot address (pageable memory without a mapping) falls back to
-// cudaMemcpyAsync.
+// the GPU stays free for the carving kernels and the scan.  A host pointer
+// that the device cannot address (pageable memory without a mapping) falls
+// back to cudaMemcpyAsync.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -21,20 +21,21 @@ namespace scpl {
 
 namespace {
 
-// One thin CTA per SM (152 x 128 threads, at most 32 registers a thread:
-// 4096 registers).  That is what an SM has left beside a full buffer scan
-// (5 CTAs x 128 threads x 96 registers), so a copy still running when a scan
-// is launched never keeps the scan's cooperative grid from becoming resident.
-// With 4 loads of 16 bytes in flight per thread, 152 such CTAs keep about 1.2 MB
-// in flight, which saturates the link both ways.
-constexpr int LINK_CTAS = 152;
-constexpr int LINK_THREADS = 128;
+// 16 CTAs of 1024 threads.  Such a copy holds the link's rate both ways
+// (4 loads of 16 bytes in flight per thread, about 1 MB in all) while it
+// shares only 16 SMs with the kernels it overlaps.  Measured on the streamed
+// 1080p clips (page-locked in and out, one GB300), the steady time per clip
+// was 19.5 ms against 18.9 ms with no copies at all; copies spread over more
+// SMs disturbed the carving more (48 x 512: 27.3 ms, 152 x 128: 30.3 ms,
+// 24 x 512: 21.0 ms), and fewer SMs could not keep up (6 x 1024: 26.3 ms).
+constexpr int LINK_CTAS = 16;
+constexpr int LINK_THREADS = 1024;
 
 // dst[0, n) = src[0, n).  When both pointers share their offset within 16
 // bytes, the bytes up to the first 16-byte boundary go singly, the body as
 // 16-byte streaming loads and stores, and the tail singly; otherwise every
 // byte goes singly.  Every index stays below n.
-__global__ void __launch_bounds__(LINK_THREADS, 16)
+__global__ void __launch_bounds__(LINK_THREADS)
 k_link_copy(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst, size_t n) {
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t nth = (size_t)gridDim.x * blockDim.x;

@@ -7,9 +7,9 @@
 // The choices are the cluster DP's layout (halo depth R, warps per CTA and
 // columns per lane: R32 x 4 warps, R16 x 4, R32 x 8, R16 x 8 with 4 columns a
 // lane; R16 x 4 and R16 x 8 with 2), the single-CTA DP, and the rows per
-// k_update CTA (1, 2 or 4).  The tuner measures every candidate with CUDA events on a
-// scratch workspace of one buffer of that size with synthetic energy and luma,
-// and records the fastest in a process-wide table.  Every choice computes the
+// k_update CTA (1, 2 or 4).  The scratch buffers hold synthetic energy and
+// luma of that size; each candidate is timed with CUDA events, and the
+// fastest is recorded in a process-wide table.  Every choice computes the
 // same result (the DP and the update are exact), so only the time differs.
 #include <cuda_runtime.h>
 
