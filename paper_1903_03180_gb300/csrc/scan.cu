@@ -15,6 +15,8 @@
 //
 // Several clips can share one launch: a table gives each clip its own range
 // of CTAs, and the waits and reductions above then run among that range only.
+#include <algorithm>
+
 #include "scpl_internal.cuh"
 
 namespace scpl {
@@ -617,15 +619,19 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
 
 // ---------------------------------------------------------------------------
 // k_scan_wt, the warp-tile variant for one clip whose state stays on chip.
-// Tile ownership: a tile is 8 rows x 128 columns and belongs to one warp for
+// Tile ownership: a tile is WT_TR rows x 128 columns and belongs to one warp for
 // the whole clip; lane l holds columns 4l .. 4l+3 of every row of it.  Warp gw
 // of a clip (CTA lb, warp w: gw = lb * WT_WARPS + w) owns the tiles
 // [gw * tpw, (gw + 1) * tpw), tpw = ceil(tiles / warps).  With one tile a warp
 // the running sums S1, S2 of its pixels stay in shared memory and the previous
 // frame's luma in registers ("resident"); with more they live in global memory.
+// Tiles of 6 rows: at 1080p that is 2700 tiles, so that 675 of the 760
+// co-resident CTAs have work (8-row tiles left a third of them idle) and each
+// warp's chain of rows per frame is a quarter shorter.
+constexpr int WT_TR = 6;
 constexpr int WT_THREADS = 128;
 constexpr int WT_WARPS = WT_THREADS / 32;
-constexpr size_t WT_SMEM = (size_t)WT_WARPS * TR * 2 * 32 * sizeof(uint4);   // 32 KB
+constexpr size_t WT_SMEM = (size_t)WT_WARPS * WT_TR * 2 * 32 * sizeof(uint4);   // 24 KB
 
 // One clip per launch (tab == NULL, every CTA works on a0) or one clip per
 // range of CTAs (clip of CTA x = tab[block_clip[x]], CTAs [cta0, cta0 + G)).
@@ -641,10 +647,10 @@ constexpr size_t WT_SMEM = (size_t)WT_WARPS * TR * 2 * 32 * sizeof(uint4);   // 
 // energies.
 __global__ void __launch_bounds__(WT_THREADS, 5)
 k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ block_clip) {
-    extern __shared__ __align__(16) uint4 sstate[];   // [WT_WARPS][TR][2][32] S1, S2
+    extern __shared__ __align__(16) uint4 sstate[];   // [WT_WARPS][WT_TR][2][32] S1, S2
     __shared__ ScanArgs a;
-    __shared__ unsigned long long red_a[WT_WARPS];
-    __shared__ uint32_t red_m[WT_WARPS];
+    __shared__ unsigned long long red_a[SCAN_FW][WT_WARPS];   // per frame of the round
+    __shared__ uint32_t red_m[SCAN_FW][WT_WARPS];
     __shared__ DecState st;
     __shared__ int s_ok, s_ndec, s_last;
 
@@ -677,7 +683,7 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
     const int G = a.G;
     const int lb = blockIdx.x - a.cta0;   // CTA index within the clip's range
     const int tiles_x = (W + TC - 1) / TC;
-    const int ntiles = ((H + TR - 1) / TR) * tiles_x;
+    const int ntiles = ((H + WT_TR - 1) / WT_TR) * tiles_x;
     const int nwarps = G * WT_WARPS;
     const int tpw = (ntiles + nwarps - 1) / nwarps;
     const int gw = lb * WT_WARPS + w;
@@ -688,24 +694,24 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
     const bool pf_ok = (reinterpret_cast<uintptr_t>(rgb) & 15) == 0;   // prefetch needs 16-byte bases
     const long hw3 = (long)H * W * 3;
     const long yplane = (long)H * ypitch;
-    const long eslot = (long)ntiles * TR * 32;           // uint2 entries per ring slot
-    uint2 *ering = reinterpret_cast<uint2 *>(a.ering);  // [SCAN_FW][ntiles][TR][32] e quads
-    uint32_t yp[TR];   // resident path: previous frame's luma quad of every row
+    const long eslot = (long)ntiles * WT_TR * 32;           // uint2 entries per ring slot
+    uint2 *ering = reinterpret_cast<uint2 *>(a.ering);  // [SCAN_FW][ntiles][WT_TR][32] e quads
+    uint32_t yp[WT_TR];   // resident path: previous frame's luma quad of every row
 #pragma unroll
-    for (int r = 0; r < TR; ++r) yp[r] = 0;
+    for (int r = 0; r < WT_TR; ++r) yp[r] = 0;
 
     auto state_ptrs = [&](int tile, int r, uint4 *&S1p, uint4 *&S2p) {
         if (resident) {
-            S1p = &sstate[((w * TR + r) * 2) * 32 + lane];
-            S2p = &sstate[((w * TR + r) * 2 + 1) * 32 + lane];
+            S1p = &sstate[((w * WT_TR + r) * 2) * 32 + lane];
+            S2p = &sstate[((w * WT_TR + r) * 2 + 1) * 32 + lane];
         } else {
-            const long sidx = ((long)tile * TR + r) * 32 + lane;
+            const long sidx = ((long)tile * WT_TR + r) * 32 + lane;
             S1p = reinterpret_cast<uint4 *>(S1g) + sidx;
             S2p = reinterpret_cast<uint4 *>(S2g) + sidx;
         }
     };
     auto ering_at = [&](int f, int tile, int r) -> uint2 & {
-        return ering[(long)(f % SCAN_FW) * eslot + ((long)tile * TR + r) * 32 + lane];
+        return ering[(long)(f % SCAN_FW) * eslot + ((long)tile * WT_TR + r) * 32 + lane];
     };
 
     // fold one row's energy quad into S1/S2 (restart when `fresh`) and add
@@ -742,12 +748,12 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
     auto tile_frame = [&](int f, int tile, bool fresh_frame, bool fresh, int n1,
                           unsigned long long &acc, uint32_t &emax2) {
         const int ty = tile / tiles_x;
-        const int r0 = ty * TR, c0 = (tile - ty * tiles_x) * TC;
+        const int r0 = ty * WT_TR, c0 = (tile - ty * tiles_x) * TC;
         const int col = c0 + 4 * lane;
         const int nvq = max(0, min(4, W - col));
         if (!fresh_frame) {
 #pragma unroll
-            for (int r = 0; r < TR; ++r) {
+            for (int r = 0; r < WT_TR; ++r) {
                 const int nv = r0 + r < H ? nvq : 0;
                 const uint2 e = ering_at(f, tile, r);
                 fold(tile, r, e.x, e.y, nv, fresh, n1, acc);
@@ -758,7 +764,7 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
         // the tile's rows of the next frame into L2 now, so that its loads
         // wait for L2 instead of DRAM; ranges rounded inwards to 16 bytes
         // and kept inside the clip
-        if (pf_ok && lane < TR + 2 && f + 1 < T) {
+        if (pf_ok && lane < WT_TR + 2 && f + 1 < T) {
             const int row = clampi(r0 - 1 + lane, 0, H - 1);
             const long base = ((long)(f + 1) * H + row) * W * 3;
             const long lo = (base + 3L * max(c0 - 1, 0)) & ~15L;
@@ -812,7 +818,7 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
             window(xa, qa, a0, a1);
             window(xb, qb, b0, b1);
 #pragma unroll
-            for (int r = 0; r < TR; ++r) {
+            for (int r = 0; r < WT_TR; ++r) {
                 const int i = r0 + r;
                 const Raw xn = fetch(i + 2);   // two rows ahead
                 uint32_t qc, c0w, c1w;
@@ -848,23 +854,15 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
         }
     };
 
-    // block sum of acc and maximum of em (thread 0 receives them)
-    auto block_reduce = [&](unsigned long long &acc, uint32_t &em) {
+    // warp sum of acc and maximum of em into the round's slot i of this warp
+    // (thread 0 adds the warps up once the round's frames are done)
+    auto warp_reduce = [&](int i, unsigned long long acc, uint32_t em) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             acc += __shfl_xor_sync(0xffffffffu, acc, o);
             em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
         }
-        if (lane == 0) { red_a[w] = acc; red_m[w] = em; }
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long A = 0;
-            uint32_t m = 0;
-            for (int q = 0; q < WT_WARPS; ++q) { A += red_a[q]; m = max(m, red_m[q]); }
-            acc = A;
-            em = m;
-        }
-        __syncthreads();
+        if (lane == 0) { red_a[i][w] = acc; red_m[i][w] = em; }
     };
 
     // summed energy of buffer bi (the E0 plane) for the valid pixels of my tiles:
@@ -874,9 +872,9 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
         for (int k = 0; k < mine; ++k) {
             const int tile = first + k;
             const int ty = tile / tiles_x;
-            const int r0 = ty * TR, col = (tile - ty * tiles_x) * TC + 4 * lane;
+            const int r0 = ty * WT_TR, col = (tile - ty * tiles_x) * TC + 4 * lane;
             const int nvq = max(0, min(4, W - col));
-            for (int r = 0; r < TR; ++r) {
+            for (int r = 0; r < WT_TR; ++r) {
                 if (r0 + r >= H || nvq == 0) continue;
                 uint4 *S1p, *S2p;
                 state_ptrs(tile, r, S1p, S2p);
@@ -935,13 +933,22 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
             const bool fresh = n0 == 0 && f == t;   // the open buffer starts here
             const int n1 = n0 + (f - t) + 1;
             for (int k = 0; k < mine; ++k) tile_frame(f, first + k, fresh_frame, fresh, n1, acc, emax2);
-            uint32_t em = max(emax2 & 0xFFFFu, emax2 >> 16);
-            block_reduce(acc, em);
-            if (tid == 0) {
+            warp_reduce(f - t, acc, max(emax2 & 0xFFFFu, emax2 >> 16));
+        }
+        // the CTA's share of every frame of the round: one barrier per round
+        __syncthreads();
+        if (tid == 0) {
+            for (int f = t; f <= wend; ++f) {
+                unsigned long long A = 0;
+                uint32_t m = 0;
+                for (int q = 0; q < WT_WARPS; ++q) {
+                    A += red_a[f - t][q];
+                    m = max(m, red_m[f - t][q]);
+                }
                 atomicAdd(reinterpret_cast<unsigned long long *>(
                               &a.partA[(long)rnd * SCAN_FW + (f - t)]),
-                          acc);
-                if (fresh_frame) atomicMax(&a.partM[f], (int)em);
+                          A);
+                if (f >= horizon) atomicMax(&a.partM[f], (int)m);
             }
         }
         horizon = max(horizon, wend + 1);
@@ -981,7 +988,7 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
             write_e0(st.nb - 1, f, wend + 1);
             for (int k = 0; k < mine; ++k) {
                 const int tile = first + k;
-                for (int r = 0; r < TR; ++r) {
+                for (int r = 0; r < WT_TR; ++r) {
                     uint4 *S1p, *S2p;
                     state_ptrs(tile, r, S1p, S2p);
                     const uint2 e = ering_at(f, tile, r);
@@ -1072,7 +1079,7 @@ cudaError_t launch_scan(const ScanArgs &a, int grid, cudaStream_t s) {
     // one clip alone: the warp-tile variant when every warp can own a single
     // tile (each warp walks its tile's rows; its state stays on chip)
     int err = 0;
-    const long ntiles = (long)scan_tiles(a.H, a.W);
+    const long ntiles = (long)scan_tiles_wt(a.H, a.W);
     const int cap_wt = scan_capacity_wt(&err);
     if (!err && (long)cap_wt * WT_WARPS >= ntiles) {
         const int g = (int)((ntiles + WT_WARPS - 1) / WT_WARPS);
@@ -1113,8 +1120,13 @@ int scan_capacity(int *err_out) {
 }
 
 int scan_tiles(int H, int W) { return ((H + TR - 1) / TR) * ((W + TC - 1) / TC); }
+int scan_tiles_wt(int H, int W) { return ((H + WT_TR - 1) / WT_TR) * ((W + TC - 1) / TC); }
 int scan_tile_warps() { return 1; }   // a CTA works on one tile at a time
 
-long scan_state_px(int H, int W) { return (long)scan_tiles(H, W) * TR * TC; }
+// pixels of the tile-major state, enough for either layout's tiles
+long scan_state_px(int H, int W) {
+    const long rows = std::max((long)((H + TR - 1) / TR) * TR, (long)((H + WT_TR - 1) / WT_TR) * WT_TR);
+    return rows * ((W + TC - 1) / TC) * TC;
+}
 
 }  // namespace scpl

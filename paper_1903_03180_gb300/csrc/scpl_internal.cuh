@@ -223,6 +223,7 @@ cudaError_t launch_scan_multi(const ScanArgs *tab, const int *block_clip, int gr
                               cudaStream_t s);
 int scan_capacity(int *err_out);   // co-resident scan CTAs on this GPU
 int scan_tiles(int H, int W);      // 8x128 tiles of one frame
+int scan_tiles_wt(int H, int W);   // 6x128 tiles of the single-clip warp-tile layout
 int scan_tile_warps();             // tile-owning warps per scan CTA
 long scan_state_px(int H, int W);  // pixels of the tile-major scan state
 
