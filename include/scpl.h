@@ -249,6 +249,26 @@ scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W
                        int k, uint8_t *out, int32_t *buffer_starts, int *n_buffers,
                        int16_t *seams);
 
+/* Carve one fixed spatiotemporal buffer on its own (Sec. 3.2: once a buffer
+ * is fixed, its seams depend on its own frames only, and the same seams are
+ * removed from every frame of it).  This is how a clip's buffers are dealt to
+ * several GPUs after one scan: a rank carves the frames [t0, t1) of buffer b
+ * and gets exactly what scpl_carve gives for those frames of the whole clip.
+ * No flush decision is taken: the T frames are one buffer.
+ *   frames     [device] uint8 [T][H][W][3]: the buffer's frames
+ *   prev_frame [device] uint8 [H][W][3]: the clip's frame t0 - 1, from which
+ *              the motion term of the buffer's first frame is taken (R3:
+ *              D_t = |Y_t - Y_{t-1}|), or NULL when the buffer starts the clip
+ *              (D = 0 there)
+ *   out        [device] uint8 [T][H][target_W][3], written
+ *   seams      [device] int16 [1][W - target_W][H] or NULL
+ * T <= t_max of the handle's parameters (a buffer never holds more; else
+ * SCPL_EINVAL); the other limits and errors are scpl_carve's.  Synchronises
+ * the stream. */
+scpl_status scpl_carve_buffer(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                              const uint8_t *prev_frame, int target_W, int k, uint8_t *out,
+                              int16_t *seams);
+
 /* scpl_carve on host memory, through library-owned device buffers.  The
  * frames go up by scpl_copy before the buffer scan reads them; every
  * spatiotemporal buffer is gathered and copied back (scpl_copy, on a copy

@@ -326,6 +326,7 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
     const long e0_plane = a.e0_plane;
     const unsigned *ready = a.ready;
     const int ready_frames = a.ready_frames;
+    const uint8_t *__restrict__ Yprev = a.Yprev;
     const bool words = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(rgb) & 3) == 0;
     const int G = a.G;
     const int lb = blockIdx.x - a.cta0;   // CTA index within the clip's range
@@ -389,9 +390,12 @@ k_scan(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__ bl
         if (!resident && t > 0 && c.nvalid > 0)
             yprv = *reinterpret_cast<const uint32_t *>(Yo + (long)(t - 1) * yplane +
                                                        (long)c.row * ypitch + c.col);
+        if (t == 0 && Yprev && c.nvalid > 0)
+            yprv = *reinterpret_cast<const uint32_t *>(Yprev + (long)c.row * ypitch + c.col);
         // motion |Y_t - Y_{t-1}| on the u16 halves the energy uses
-        const uint32_t d02 = t > 0 ? absdiff16(even16(ycur), even16(yprv)) : 0u;
-        const uint32_t d13 = t > 0 ? absdiff16(odd16(ycur), odd16(yprv)) : 0u;
+        const bool moves = t > 0 || Yprev;
+        const uint32_t d02 = moves ? absdiff16(even16(ycur), even16(yprv)) : 0u;
+        const uint32_t d13 = moves ? absdiff16(odd16(ycur), odd16(yprv)) : 0u;
         const uint32_t dq = __byte_perm(d02, d13, 0x6240);   // back to 4 bytes
         const uint32_t e02 = wg * g02 + wm * d02;
         const uint32_t e13 = wg * g13 + wm * d13;
@@ -680,6 +684,7 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
     const long e0_plane = a.e0_plane;
     const unsigned *ready = a.ready;
     const int ready_frames = a.ready_frames;
+    const uint8_t *__restrict__ Yprev = a.Yprev;
     const int G = a.G;
     const int lb = blockIdx.x - a.cta0;   // CTA index within the clip's range
     const int tiles_x = (W + TC - 1) / TC;
@@ -830,9 +835,12 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
                 if (!resident && f > 0 && nv > 0)
                     yprv = *reinterpret_cast<const uint32_t *>(Yo + (long)(f - 1) * yplane +
                                                                (long)i * ypitch + col);
+                if (f == 0 && Yprev && nv > 0)
+                    yprv = *reinterpret_cast<const uint32_t *>(Yprev + (long)i * ypitch + col);
                 // motion |Y_t - Y_{t-1}| on the u16 halves the energy uses
-                const uint32_t d02 = f > 0 ? absdiff16(even16(qb), even16(yprv)) : 0u;
-                const uint32_t d13 = f > 0 ? absdiff16(odd16(qb), odd16(yprv)) : 0u;
+                const bool moves = f > 0 || Yprev;
+                const uint32_t d02 = moves ? absdiff16(even16(qb), even16(yprv)) : 0u;
+                const uint32_t d13 = moves ? absdiff16(odd16(qb), odd16(yprv)) : 0u;
                 const uint32_t dq = __byte_perm(d02, d13, 0x6240);   // back to 4 bytes
                 const uint32_t e02 = wg * g02 + wm * d02;
                 const uint32_t e13 = wg * g13 + wm * d13;
@@ -1014,6 +1022,18 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
     }
 }
 
+// out[i][j] = luma of pixel (i, j) of one frame, rows ypitch apart; the
+// padding past W is left as it is (the scan reads it only for pixels that do
+// not exist, whose energy counts nowhere)
+__global__ void k_luma_plane(const uint8_t *rgb, int H, int W, long ypitch, uint8_t *out) {
+    const long n = (long)H * W;
+    for (long q = blockIdx.x * (long)blockDim.x + threadIdx.x; q < n;
+         q += (long)gridDim.x * blockDim.x) {
+        const long i = q / W, j = q - i * W;
+        out[i * ypitch + j] = (uint8_t)luma_px(rgb + q * 3);
+    }
+}
+
 // r[i] = floor(sqrt(x[i])) by the routine the scan applies to 65536 Q of
 // every pixel (Eq. 7-8); exposed so that it can be checked at its edges.
 __global__ void k_isqrt_check(const unsigned long long *x, uint32_t *r, long n) {
@@ -1023,6 +1043,15 @@ __global__ void k_isqrt_check(const unsigned long long *x, uint32_t *r, long n) 
 }
 
 }  // namespace
+
+cudaError_t launch_luma_plane(const uint8_t *rgb, int H, int W, long ypitch, uint8_t *out,
+                              cudaStream_t s) {
+    const long n = (long)H * W;
+    if (n <= 0) return cudaSuccess;
+    const long blocks = (n + 255) / 256;
+    k_luma_plane<<<(int)(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(rgb, H, W, ypitch, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_isqrt_check(const unsigned long long *x, uint32_t *r, long n,
                                cudaStream_t s) {

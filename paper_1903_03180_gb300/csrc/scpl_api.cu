@@ -116,6 +116,7 @@ struct scpl_ctx {
     // scpl_carve_host_many: a second input and output slot and the input copy
     // stream
     DevBuf in2, out2;
+    DevBuf Yprev;   // scpl_carve_buffer: luma of the frame before the buffer
     cudaStream_t istream = nullptr;
     DevBuf Yfm;
     bool autotune = false;
@@ -205,9 +206,12 @@ constexpr int E0_PLANES = 16;   // buffers whose summed energy the scan keeps
 // Runs the buffer scan; leaves Y, D (original luma / motion) and the summed
 // energy of the first E0_PLANES buffers in the handle and the starts on the
 // host.  A and M (host, or NULL) receive every frame's A_t and maximum e_t.
+// prev_rgb (device [H][W][3], or NULL) is the frame before frame 0, for frame
+// 0's motion term; `fixed` makes the T frames one buffer (no flush decision).
 scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
                      std::vector<int> &starts, bool keep_e0, long long *A = nullptr,
-                     int *M = nullptr, const unsigned *ready = nullptr, int ready_frames = 1) {
+                     int *M = nullptr, const unsigned *ready = nullptr, int ready_frames = 1,
+                     const uint8_t *prev_rgb = nullptr, bool fixed = false) {
     TraceRange trace("scpl.scan");
     const long ypitch = round_up(W, 16);
     const long hw = (long)H * W;
@@ -234,6 +238,10 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     SCPL_CUDA(h, cudaMemsetAsync(h->count.p, 0, (size_t)T * sizeof(unsigned), s));
     SCPL_CUDA(h, cudaMemsetAsync(h->partA.p, 0, accb + (size_t)T * 4, s));
     SCPL_CUDA(h, cudaMemsetAsync(h->errw.p, 0, sizeof(int), s));
+    if (prev_rgb) {
+        SCPL_CUDA(h, h->Yprev.ensure((size_t)H * ypitch));
+        SCPL_CUDA(h, launch_luma_plane(prev_rgb, H, W, ypitch, h->Yprev.as<uint8_t>(), s));
+    }
     ScanArgs a;
     a.rgb = frames; a.T = T; a.H = H; a.W = W; a.ypitch = ypitch;
     a.Y = h->Y.as<uint8_t>(); a.D = h->D.as<uint8_t>();
@@ -255,6 +263,14 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     a.M_out = nullptr;
     a.ready = ready;
     a.ready_frames = ready_frames;
+    a.Yprev = prev_rgb ? h->Yprev.as<uint8_t>() : nullptr;
+    if (fixed) {
+        // one buffer of all T frames: the cap at T closes it at the end, and
+        // with alpha = 1e6 no spread can exceed the threshold (A is at most
+        // 128 n M H W, the threshold 2.56e8 M sqrt(n-1) H W)
+        a.alpha = 1e6;
+        a.t_max = T;
+    }
     if (A) {   // diagnostics after the accumulators in the same allocation
         a.M_out = reinterpret_cast<int *>(h->partA.as<char>() + accb + (size_t)T * 4);
         a.A_out = reinterpret_cast<long long *>(h->partA.as<char>() + accb + (size_t)T * 8);
@@ -361,7 +377,8 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
                       int k, uint8_t *out, int32_t *buffer_starts, int *n_buffers,
                       int16_t *seams, const unsigned *ready, int ready_frames,
                       uint8_t *host_out,
-                      const std::function<scpl_status()> &after_scan = nullptr) {
+                      const std::function<scpl_status()> &after_scan = nullptr,
+                      const uint8_t *prev_rgb = nullptr, bool fixed = false) {
     scpl_status s = check_frames(h, frames, T, H, W);
     if (s != SCPL_OK) return s;
     if (!out) return fail(h, SCPL_EINVAL, "out is NULL");
@@ -371,7 +388,9 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
     if ((s = check_overflow(h, T, H)) != SCPL_OK) return s;
 
     std::vector<int> starts;
-    if ((s = run_scan(h, frames, T, H, W, starts, true, nullptr, nullptr, ready, ready_frames)) != SCPL_OK) return s;
+    if ((s = run_scan(h, frames, T, H, W, starts, true, nullptr, nullptr, ready, ready_frames,
+                      prev_rgb, fixed)) != SCPL_OK)
+        return s;
     // the scan has finished (its starts are on the host): work that must not
     // share the GPU with the scan's device-wide waits may be issued now
     if (after_scan && (s = after_scan()) != SCPL_OK) return s;
@@ -607,7 +626,7 @@ void scpl_destroy(scpl_handle h) {
     DevBuf *bufs[] = {&h->Y, &h->D, &h->ering, &h->S1, &h->S2, &h->partA, &h->partM,
                       &h->count, &h->starts, &h->nbuf, &h->errw, &h->E0, &h->cws, &h->bof,
                       &h->in_frames, &h->out_frames, &h->seams_dev, &h->Yfm, &h->qY,
-                      &h->qacc, &h->in2, &h->out2, &h->ej_mid, &h->ej_tin,
+                      &h->qacc, &h->in2, &h->out2, &h->Yprev, &h->ej_mid, &h->ej_tin,
                       &h->ej_tout};
     if (h->istream) cudaStreamSynchronize(h->istream);
     if (h->cstream) cudaStreamSynchronize(h->cstream);
@@ -845,6 +864,17 @@ scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W
                        int16_t *seams) {
     return carve_run(h, frames, T, H, W, target_W, k, out, buffer_starts, n_buffers, seams,
                      nullptr, 1, nullptr);
+}
+
+scpl_status scpl_carve_buffer(scpl_handle h, const uint8_t *frames, int T, int H, int W,
+                              const uint8_t *prev_frame, int target_W, int k, uint8_t *out,
+                              int16_t *seams) {
+    if (!h) return SCPL_EINVAL;
+    if (T > effective_tmax(h->p))
+        return fail(h, SCPL_EINVAL, "a fixed buffer holds at most t_max = %d frames, not %d",
+                    effective_tmax(h->p), T);
+    return carve_run(h, frames, T, H, W, target_W, k, out, nullptr, nullptr, seams, nullptr, 1,
+                     nullptr, nullptr, prev_frame, true);
 }
 
 scpl_status scpl_carve_host(scpl_handle h, const uint8_t *frames, int T, int H, int W,

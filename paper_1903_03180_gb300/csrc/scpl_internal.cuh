@@ -207,6 +207,10 @@ struct ScanArgs {
     // f / ready_frames; a copy stream raises it after every chunk it copies
     const unsigned *ready;
     int ready_frames;
+    // luma of the frame just before frame 0 ([H][ypitch], or NULL): frame 0's
+    // motion term is taken against it instead of being 0 (a buffer carved on
+    // its own, away from the start of its clip)
+    const uint8_t *Yprev;
 };
 
 // Launchers (return the CUDA error of the launch).
@@ -214,6 +218,9 @@ cudaError_t launch_energy_api(const uint8_t *rgb, int T, int H, int W, int wg, i
                               int32_t *energy, cudaStream_t s);
 int scan_grid_size(int H, int W, int *err_out);
 cudaError_t launch_scan(const ScanArgs &a, int grid, cudaStream_t s);
+// Integer BT.601 luma of one RGB frame [H][W][3] into out [H][ypitch].
+cudaError_t launch_luma_plane(const uint8_t *rgb, int H, int W, long ypitch, uint8_t *out,
+                              cudaStream_t s);
 // floor(sqrt(x)) of n values (device arrays) by the scan's own routine.
 cudaError_t launch_isqrt_check(const unsigned long long *x, uint32_t *r, long n,
                                cudaStream_t s);

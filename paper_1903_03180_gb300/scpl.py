@@ -93,6 +93,7 @@ SIGNATURES = {
     "scpl_seams": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "scpl_carve": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
     "scpl_carve_host": (_I, [_P, _P, _I, _I, _I, _I, _I, _P, _P, _P, _P]),
+    "scpl_carve_buffer": (_I, [_P, _P, _I, _I, _I, _P, _I, _I, _P, _P]),
     "scpl_seams_noalloc": (_I, [_P, _I, _I, _I, _P, _P, _P]),
     "scpl_copy": (_I, [_P, _P, ctypes.c_size_t, _P]),
     "scpl_isqrt": (_I, [_P, _P, ctypes.c_long, _P]),
@@ -419,6 +420,30 @@ def scpl_carve(h, frames, target_W: int, k: int, out, seams=None) -> np.ndarray:
     _check(h, load().scpl_carve(h, fp, T, H, W, target_W, k, op, starts.ctypes.data_as(_P),
                                 ctypes.byref(nb), sp))
     return starts[: nb.value + 1].copy()
+
+
+def scpl_carve_buffer(h, frames, target_W: int, k: int, out, prev_frame=None, seams=None):
+    """Carve cuda uint8 [T,H,W,3] frames as one fixed buffer into out
+    [T,H,target_W,3]; prev_frame (cuda uint8 [H,W,3] or None) is the clip's
+    frame before them, for the first frame's motion term.  seams: optional
+    cuda int16 [1, W-target_W, H]."""
+    import torch
+    fp = _dev_ptr(frames, torch.uint8, 4, "frames")
+    T, H, W, _ = frames.shape
+    op = _dev_ptr(out, torch.uint8, 4, "out")
+    if tuple(out.shape) != (T, H, target_W, 3):
+        raise ValueError("out must be [T,H,target_W,3]")
+    pp = None
+    if prev_frame is not None:
+        pp = _dev_ptr(prev_frame, torch.uint8, 3, "prev_frame")
+        if tuple(prev_frame.shape) != (H, W, 3):
+            raise ValueError("prev_frame must be [H,W,3]")
+    sp = None
+    if seams is not None:
+        sp = _dev_ptr(seams, torch.int16, 3, "seams")
+        if tuple(seams.shape[1:]) != (W - target_W, H):
+            raise ValueError("seams must be [1, W-target_W, H]")
+    _check(h, load().scpl_carve_buffer(h, fp, T, H, W, pp, target_W, k, op, sp))
 
 
 def scpl_carve_host(h, frames, target_W: int, k: int, out, seams=None) -> np.ndarray:
