@@ -507,6 +507,37 @@ def run_native(args) -> None:
         e2e_single = {"value": round(T * ws * args.steps / dt1, 2), "unit": UNIT,
                       "api": "scpl_carve_host, one call per clip"}
 
+    # the batched and served workloads, briefly, so that this line records
+    # them too: one timed batched step of all 256 clips against the same jobs
+    # one clip per call, and a short Poisson sweep through the server
+    summaries = None
+    if rank == 0 and ws == 1 and not args.no_summaries:
+        b = measure_batch(256, steps=2, warmup=1)
+        rates = [float(x) for x in args.summary_rates.split(",")]
+        sv = measure_serve(rates, args.summary_duration, args.max_requests, args.out_buffers)
+        summaries = {
+            "batch_256x32": {
+                "frames_per_s": round(b["value"], 1),
+                "ms_per_step": round(sum(b["step_ms"]) / len(b["step_ms"]), 2),
+                "one_clip_at_a_time_frames_per_s": round(b["one"], 1),
+                "batched_over_one_at_a_time": round(b["value"] / b["one"], 3),
+                "identical_output": b["identical"],
+                "gpu_launches_per_step": int(b["engine"]["kernel_launches"]),
+                "steps": len(b["step_ms"]), "clocks": b["clocks"],
+                "what": "256 device-resident clips of 32 frames (426x240 to 1920x1080, "
+                        "1:1/4:3/21:9 targets) in one scpl_carve_batch per step, against "
+                        "the same jobs one call per clip"},
+            "serve_poisson": {
+                "sweep": [{"rate_per_s": x["rate_per_s"], "requests": x["requests"],
+                           "failed": x["failed"], "frames_per_s": round(x["frames_per_s"], 1),
+                           "p50_ms": None if x["p50_ms"] is None else round(x["p50_ms"], 2),
+                           "p99_ms": None if x["p99_ms"] is None else round(x["p99_ms"], 2)}
+                          for x in sv["results"]],
+                "duration_s_per_rate": args.summary_duration,
+                "what": "Poisson arrivals of page-locked host jobs (16-128 frames, 640x360 to "
+                        "3840x2160, 10-40 % narrower) through one server; latency from "
+                        "arrival to the result in host memory"}}
+
     cpu = cpu1 = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu1 = cpu_baseline(name, frames_np, args.cpu_frames, args.wf)
@@ -552,6 +583,8 @@ def run_native(args) -> None:
             "cpu_baseline": cpu,
             "cpu_baseline_1core": cpu1,
         }
+        if summaries:
+            line["workload_summaries"] = summaries
         if raw:
             line["raw_sc"] = raw
         print(json.dumps(line), flush=True)
@@ -576,18 +609,26 @@ def _event_ms(fn):
     return a.elapsed_time(b)
 
 
-def run_batch(args) -> None:
+def _generate(fn, specs) -> list:
+    """Frames of every spec, generated by spawned processes (no CUDA state is
+    forked)."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(16, os.cpu_count() or 4)) as pool:
+        return pool.map(fn, specs, chunksize=2)
+
+
+def measure_batch(n_clips: int, steps: int, warmup: int, cpu_frames: int = 0) -> dict:
     """The batched workload: every clip device-resident, one scpl_carve_batch
     per step; then the same jobs one clip per call, outputs compared."""
     import torch
 
     from paper_1903_03180_gb300 import scpl, synth
     torch.cuda.set_device(0)
-    specs = synth.batch_spec(n_clips=args.clips)
+    specs = synth.batch_spec(n_clips=n_clips)
     t_gen = time.perf_counter()
     dev, outs, outs1 = [], [], []
-    for sp in specs:
-        dev.append(torch.from_numpy(synth.batch_clip(sp)).cuda())
+    for sp, f in zip(specs, _generate(synth.batch_clip, specs)):
+        dev.append(torch.from_numpy(f).cuda())
         shape = (sp["T"], sp["target_H"], sp["target_W"], 3)
         outs.append(torch.zeros(shape, dtype=torch.uint8, device="cuda"))
         outs1.append(torch.zeros(shape, dtype=torch.uint8, device="cuda"))
@@ -599,52 +640,65 @@ def run_batch(args) -> None:
     frames = sum(sp["T"] for sp in specs)
     h = scpl.scpl_create()
     scpl.scpl_set_autotune(h, True)   # every size is tuned once, during the warm-up
-    for _ in range(max(args.warmup, 0)):
+    for _ in range(max(warmup, 1)):
         scpl.scpl_carve_batch(h, jobs)
     st0 = scpl.scpl_batch_stats(h)
     clocks = ClockSampler("0")
     clocks.start()
     time.sleep(0.3)
-    step_ms = [_event_ms(lambda: scpl.scpl_carve_batch(h, jobs)) for _ in range(args.steps)]
+    step_ms = [_event_ms(lambda: scpl.scpl_carve_batch(h, jobs)) for _ in range(steps)]
     clk = clocks.stop()
     st1 = scpl.scpl_batch_stats(h)
     # one clip per call through the same engine and kernels
     one_ms = _event_ms(lambda: [scpl.scpl_carve_batch(h, [j]) for j in jobs1])
     identical = all(torch.equal(a, b) for a, b in zip(outs, outs1))
+    tuning = {f"{hh}x{w}": scpl.scpl_tuning_get(hh, w) for hh, w in
+              sorted({(sp["H"], sp["W"]) for sp in specs} |
+                     {(sp["W"] if sp["target_H"] < sp["H"] else sp["H"],
+                       sp["H"] if sp["target_H"] < sp["H"] else sp["W"]) for sp in specs})}
     scpl.scpl_destroy(h)
-    cpu = None if args.no_cpu_baseline else cpu_baseline_batch(specs, args.batch_cpu_frames)
+    in_gb = sum(d.numel() for d in dev) / 1e9
+    del dev, outs, outs1, jobs, jobs1
+    torch.cuda.empty_cache()
+    cpu = cpu_baseline_batch(specs, cpu_frames) if cpu_frames else None
     total = sum(step_ms)
-    value = frames * args.steps / (total / 1000.0)
+    steps = max(steps, 1)
+    value = frames * steps / (total / 1000.0)
     one = frames / (one_ms / 1000.0)
+    return {"value": value, "frames": frames, "clips": len(specs), "step_ms": step_ms,
+            "one_ms": one_ms, "one": one, "identical": bool(identical), "clocks": clk,
+            "t_gen": t_gen, "in_gb": in_gb, "tuning": tuning, "cpu": cpu,
+            "engine": {k: (st1[k] - st0[k]) / steps for k in
+                       ("scan_waves", "groups", "chunks", "kernel_launches")}}
+
+
+def run_batch(args) -> None:
+    from paper_1903_03180_gb300 import synth
+    m = measure_batch(args.clips, args.steps, args.warmup,
+                      0 if args.no_cpu_baseline else args.batch_cpu_frames)
     steps = max(args.steps, 1)
-    line = {"metric": BATCH_METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": 1,
+    line = {"metric": BATCH_METRIC, "value": round(m["value"], 2), "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(total / steps, 3), "higher_is_better": True,
+            "ms_per_step": round(sum(m["step_ms"]) / steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"batch_{args.clips}x32", "clips": len(specs),
-                       "frames": frames, "sizes": [f"{w}x{hh}" for hh, w in synth.BATCH_SIZES],
+            "config": {"workload": f"batch_{args.clips}x32", "clips": m["clips"],
+                       "frames": m["frames"], "sizes": [f"{w}x{hh}" for hh, w in synth.BATCH_SIZES],
                        "aspects": list(synth.BATCH_ASPECTS), "wg": 1, "wm": 2,
-                       "l2": "no flush: %.1f GB of clips, far above the 129 MB L2" %
-                             (sum(d.numel() for d in dev) / 1e9),
-                       "generation_s": round(t_gen, 1)},
-            "latency_ms": {"p50": round(float(np.percentile(step_ms, 50)), 3),
-                           "p99": round(float(np.percentile(step_ms, 99)), 3),
+                       "l2": "no flush: %.1f GB of clips, far above the 129 MB L2" % m["in_gb"],
+                       "generation_s": round(m["t_gen"], 1)},
+            "latency_ms": {"p50": round(float(np.percentile(m["step_ms"], 50)), 3),
+                           "p99": round(float(np.percentile(m["step_ms"], 99)), 3),
                            "what": "one batched step (all clips)"},
-            "one_clip_at_a_time": {"value": round(one, 2), "unit": UNIT,
-                                   "ms": round(one_ms, 3),
+            "one_clip_at_a_time": {"value": round(m["one"], 2), "unit": UNIT,
+                                   "ms": round(m["one_ms"], 3),
                                    "what": "the same jobs, one scpl_carve_batch call per clip"},
-            "batched_over_one_at_a_time": round(value / one, 3),
-            "identical_output": bool(identical),
-            "engine_per_step": {k: (st1[k] - st0[k]) / steps for k in
-                                ("scan_waves", "groups", "chunks", "kernel_launches")},
-            "tuning": {f"{hh}x{w}": scpl.scpl_tuning_get(hh, w) for hh, w in
-                       sorted({(sp["H"], sp["W"]) for sp in specs} |
-                              {(sp["W"] if sp["target_H"] < sp["H"] else sp["H"],
-                                sp["H"] if sp["target_H"] < sp["H"] else sp["W"])
-                               for sp in specs})},
-            "gpu_launches": int((st1["kernel_launches"] - st0["kernel_launches"]) / steps),
-            "clocks": clk,
-            "cpu_baseline": cpu}
+            "batched_over_one_at_a_time": round(m["value"] / m["one"], 3),
+            "identical_output": m["identical"],
+            "engine_per_step": m["engine"],
+            "tuning": m["tuning"],
+            "gpu_launches": int(m["engine"]["kernel_launches"]),
+            "clocks": m["clocks"],
+            "cpu_baseline": m["cpu"]}
     print(json.dumps(line), flush=True)
 
 
@@ -768,26 +822,34 @@ def run_consistency(args) -> None:
     rr.close()
 
 
-def run_serve(args) -> None:
+def _serve_source(i):
+    """The 128-frame source clip of serving size i (cuts every 40-90 frames)."""
+    from paper_1903_03180_gb300 import synth
+    H, W, _ = SERVE_SIZES[i]
+    return synth.clip(128, H, W, seed=(0x5C9 ^ 5) * 1000003 + i, cuts=(40, 90))
+
+
+SERVE_SIZES = [(360, 640, 16), (720, 1280, 32), (1080, 1920, 32), (2160, 3840, 64)]
+
+
+def measure_serve(rates: list, duration: float, max_requests: int, out_buffers: int) -> dict:
     """Serving: Poisson arrivals of host-memory jobs (16-128 frames, 360p to
     2160p, 10-40 % narrower) through one server, rates swept."""
     import torch
 
-    from paper_1903_03180_gb300 import scpl, serve, synth
+    from paper_1903_03180_gb300 import scpl, serve
     torch.cuda.set_device(0)
-    sizes = [(360, 640, 16), (720, 1280, 32), (1080, 1920, 32), (2160, 3840, 64)]
+    sizes = SERVE_SIZES
     t_gen = time.perf_counter()
-    pool = []   # one 128-frame source clip per size, page-locked
-    for i, (H, W, k) in enumerate(sizes):
-        f = synth.clip(128, H, W, seed=(0x5C9 ^ 5) * 1000003 + i, cuts=(40, 90))
-        pool.append(torch.from_numpy(f).pin_memory().numpy())
-        del f
+    # one 128-frame source clip per size, page-locked
+    pool = [torch.from_numpy(f).pin_memory().numpy()
+            for f in _generate(_serve_source, list(range(len(sizes))))]
     t_gen = time.perf_counter() - t_gen
-    # page-locked output buffers, allocated before timing: args.out_buffers per
+    # page-locked output buffers, allocated before timing: out_buffers per
     # size, each big enough for 128 frames at full width
     t_pin = time.perf_counter()
     free_out = {i: [torch.empty(128 * H * W * 3, dtype=torch.uint8).pin_memory().numpy()
-                    for _ in range(args.out_buffers)] for i, (H, W, k) in enumerate(sizes)}
+                    for _ in range(out_buffers)] for i, (H, W, k) in enumerate(sizes)}
     t_pin = time.perf_counter() - t_pin
 
     def get_out(si, T, H, tw):
@@ -803,11 +865,10 @@ def run_serve(args) -> None:
     th = scpl.scpl_create()
     tuning = {f"{W}x{H}": scpl.scpl_tune(th, H, W, k) for H, W, k in sizes}
     scpl.scpl_destroy(th)
-    rates = [float(x) for x in args.rates.split(",")]
     for ri, rate in enumerate(rates):
         r = np.random.default_rng(1000 + ri)
-        arrivals = serve.poisson_arrivals(rate, args.duration, seed=2000 + ri,
-                                          max_requests=args.max_requests)
+        arrivals = serve.poisson_arrivals(rate, duration, seed=2000 + ri,
+                                          max_requests=max_requests)
         reqs = []
         for _ in arrivals:
             si = int(r.integers(0, len(sizes)))
@@ -835,18 +896,25 @@ def run_serve(args) -> None:
         results.append(res)
     st = srv.stats()
     srv.close()
+    return {"results": results, "server": st, "tuning": tuning, "t_gen": t_gen, "t_pin": t_pin}
+
+
+def run_serve(args) -> None:
+    rates = [float(x) for x in args.rates.split(",")]
+    m = measure_serve(rates, args.duration, args.max_requests, args.out_buffers)
+    results, st, tuning = m["results"], m["server"], m["tuning"]
     best = max(results, key=lambda x: x["frames_per_s"])
     line = {"metric": SERVE_METRIC, "value": round(best["frames_per_s"], 2), "unit": UNIT,
             "n_gpus": 1, "steps": len(rates), "warmup": 0, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": "serve_poisson", "sizes": [f"{w}x{h}" for h, w, _ in sizes],
+            "config": {"workload": "serve_poisson", "sizes": [f"{w}x{h}" for h, w, _ in SERVE_SIZES],
                        "frames": "U[16,128]", "width_reduction": "U[10%,40%]",
                        "k": "16/32/32/64 by size", "duration_s_per_rate": args.duration,
                        "max_requests_per_rate": args.max_requests,
                        "source_clips": "one seeded 128-frame clip per size, requests take its "
                                        "first T frames (page-locked host memory)",
                        "output_buffers_per_size": args.out_buffers,
-                       "generation_s": round(t_gen, 1), "pinning_s": round(t_pin, 1)},
+                       "generation_s": round(m["t_gen"], 1), "pinning_s": round(m["t_pin"], 1)},
             "latency_ms": {"p50": round(best["p50_ms"], 2), "p99": round(best["p99_ms"], 2),
                            "what": "arrival to result in host memory, at the best rate"},
             "sweep": [{k: (round(v, 3) if isinstance(v, float) else v) for k, v in x.items()}
@@ -894,6 +962,12 @@ def main():
                     help="weight of the forward terms in the seam cost (0: the paper's "
                          "backward energy)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-summaries", action="store_true",
+                    help="skip the short batch and serving measurements of the default run")
+    ap.add_argument("--summary-rates", default="20,100",
+                    help="arrival rates of the default run's serving summary")
+    ap.add_argument("--summary-duration", type=float, default=2.0,
+                    help="seconds per rate of the default run's serving summary")
     ap.add_argument("--e2e-reps", type=int, default=3,
                     help="timed repetitions of the end-to-end call (the median is reported)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
