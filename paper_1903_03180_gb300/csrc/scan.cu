@@ -25,7 +25,7 @@ namespace {
 
 constexpr int TR = 8, TC = 128, SCAN_THREADS = 256;
 constexpr int LUMW = TC + 8;   // luma tile row: TC + 2 columns, padded to whole words
-enum { DEC_JOIN = 0, DEC_FLUSH = 1, DEC_CLOSE = 2 };
+enum { DEC_JOIN = 0, DEC_FLUSH = 1, DEC_CLOSE = 2, DEC_UNSURE = 3 };
 
 __device__ __forceinline__ int luma_px(const uint8_t *p) {
     return (77 * (int)p[0] + 150 * (int)p[1] + 29 * (int)p[2] + 128) >> 8;
@@ -90,19 +90,28 @@ struct DecState {
 // Buffer decision for frame t given the device-wide A_t and max e_t (all CTAs
 // evaluate it identically).  Eq. 9: phi(n) = alpha*M*sqrt(n-1)/n, and
 // ASDE > phi(n)  <=>  A > 256*alpha*M*sqrt(n-1)*H*W, products left to right.
+// The threshold of Eq. 9 for a buffer of n1 frames with maxval M1, scaled:
+// 256*alpha*M1*sqrt(n1-1)*H*W, products left to right.
+__device__ double threshold(const ScanArgs &a, long long M1, int n1) {
+    double thr = __dmul_rn(256.0, a.alpha);
+    thr = __dmul_rn(thr, __ll2double_rn(M1));
+    thr = __dmul_rn(thr, __dsqrt_rn(__int2double_rn(n1 - 1)));
+    thr = __dmul_rn(thr, __int2double_rn(a.H));
+    thr = __dmul_rn(thr, __int2double_rn(a.W));
+    return thr;
+}
+
+// maxval of the open buffer once frame t (maximum emax) joins it
+__device__ long long next_maxval(const DecState &s, long long emax, const ScanArgs &a) {
+    return a.maxval_mode == 1 ? a.maxval_theory : (emax > s.M ? emax : s.M);
+}
+
 __device__ int decide(DecState &s, long long A, long long emax, int t, const ScanArgs &a,
                       bool write) {
     int n1 = s.n + 1;
-    long long M1 = a.maxval_mode == 1 ? a.maxval_theory : (emax > s.M ? emax : s.M);
+    long long M1 = next_maxval(s, emax, a);
     bool exceeds = false;
-    if (n1 >= 2) {
-        double thr = __dmul_rn(256.0, a.alpha);
-        thr = __dmul_rn(thr, __ll2double_rn(M1));
-        thr = __dmul_rn(thr, __dsqrt_rn(__int2double_rn(n1 - 1)));
-        thr = __dmul_rn(thr, __int2double_rn(a.H));
-        thr = __dmul_rn(thr, __int2double_rn(a.W));
-        exceeds = __ll2double_rn(A) > thr;
-    }
+    if (n1 >= 2) exceeds = __ll2double_rn(A) > threshold(a, M1, n1);
     if (exceeds) {
         if (write) a.starts[s.nb] = s.start;
         s.nb += 1;
@@ -654,7 +663,9 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
     extern __shared__ __align__(16) uint4 sstate[];   // [WT_WARPS][WT_TR][2][32] S1, S2
     __shared__ ScanArgs a;
     __shared__ unsigned long long red_a[SCAN_FW][WT_WARPS];   // per frame of the round
+    __shared__ double red_f[SCAN_FW][WT_WARPS];               // (bounded rounds)
     __shared__ uint32_t red_m[SCAN_FW][WT_WARPS];
+    __shared__ int s_exact;   // this round sums the exact floor(sqrt) (else a bounded float)
     __shared__ DecState st;
     __shared__ int s_ok, s_ndec, s_last;
 
@@ -668,6 +679,7 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
             a.G = gridDim.x;
         }
         st.n = 0; st.M = 0; st.start = 0; st.nb = 0;
+        s_exact = a.A_out != nullptr;   // the diagnostics report every exact A_t
     }
     __syncthreads();
     // the clip's arguments live in shared memory; the hot loops use register
@@ -721,8 +733,11 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
 
     // fold one row's energy quad into S1/S2 (restart when `fresh`) and add
     // floor(sqrt(65536 (n S2 - S1^2))) of its valid pixels to acc
+    // exact: acc += floor(sqrt(65536 Q)) per pixel, the integers Eq. 7-8 define;
+    // otherwise accf += sqrt(Q) in single precision, an estimate whose error is
+    // bounded (see the decisions below)
     auto fold = [&](int tile, int r, uint32_t e02, uint32_t e13, int nv, bool fresh, int n1,
-                    unsigned long long &acc) {
+                    bool exact, unsigned long long &acc, float &accf) {
         uint4 *S1p, *S2p;
         state_ptrs(tile, r, S1p, S2p);
         const uint32_t ev[4] = {e02 & 0xFFFFu, e13 & 0xFFFFu, e02 >> 16, e13 >> 16};
@@ -739,7 +754,12 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
             if (v < nv) {
                 const unsigned long long Q =
                     (unsigned long long)n1 * S2v[v] - (unsigned long long)S1v[v] * S1v[v];
-                acc += isqrt53(Q << 16);
+                if (exact) {
+                    acc += isqrt53(Q << 16);
+                } else {
+                    const float qf = __ull2float_rz(Q);
+                    accf += qf > 0.0f ? qf * rsqrtf(qf) : 0.0f;
+                }
             }
         }
         *S1p = s1;
@@ -750,8 +770,8 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
     // frame, luma and motion written out, the energy kept in the ring; then
     // every row folded into the running sums.  Rows are software-pipelined:
     // the raw bytes of row i+2 are loaded while row i is computed.
-    auto tile_frame = [&](int f, int tile, bool fresh_frame, bool fresh, int n1,
-                          unsigned long long &acc, uint32_t &emax2) {
+    auto tile_frame = [&](int f, int tile, bool fresh_frame, bool fresh, int n1, bool exact,
+                          unsigned long long &acc, float &accf, uint32_t &emax2) {
         const int ty = tile / tiles_x;
         const int r0 = ty * WT_TR, c0 = (tile - ty * tiles_x) * TC;
         const int col = c0 + 4 * lane;
@@ -761,7 +781,7 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
             for (int r = 0; r < WT_TR; ++r) {
                 const int nv = r0 + r < H ? nvq : 0;
                 const uint2 e = ering_at(f, tile, r);
-                fold(tile, r, e.x, e.y, nv, fresh, n1, acc);
+                fold(tile, r, e.x, e.y, nv, fresh, n1, exact, acc, accf);
             }
             return;
         }
@@ -855,7 +875,7 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
                 }
                 ering_at(f, tile, r) = make_uint2(e02, e13);
                 yp[r] = qb;
-                fold(tile, r, e02, e13, nv, fresh, n1, acc);
+                fold(tile, r, e02, e13, nv, fresh, n1, exact, acc, accf);
                 a0 = b0; a1 = b1; b0 = c0w; b1 = c1w; qb = qc;
                 xc = xn;
             }
@@ -864,13 +884,19 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
 
     // warp sum of acc and maximum of em into the round's slot i of this warp
     // (thread 0 adds the warps up once the round's frames are done)
-    auto warp_reduce = [&](int i, unsigned long long acc, uint32_t em) {
+    auto warp_reduce = [&](int i, bool exact, unsigned long long acc, float accf, uint32_t em) {
+        double accd = accf;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (exact) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            else accd += __shfl_xor_sync(0xffffffffu, accd, o);
             em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
         }
-        if (lane == 0) { red_a[i][w] = acc; red_m[i][w] = em; }
+        if (lane == 0) {
+            red_a[i][w] = acc;
+            red_f[i][w] = accd;
+            red_m[i][w] = em;
+        }
     };
 
     // summed energy of buffer bi (the E0 plane) for the valid pixels of my tiles:
@@ -909,6 +935,7 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
         // the round's frames: up to SCAN_FW, ending where the open buffer
         // would reach t_max, and at the clip end
         const int n0 = st.n;
+        const bool exact = s_exact;
         int wend = min(t + SCAN_FW - 1, T - 1);
         wend = min(wend, t + (a.t_max - n0) - 1);
         for (int f = t; f <= wend; ++f) {
@@ -937,25 +964,31 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
                 if (!s_ok) return;
             }
             unsigned long long acc = 0;
+            float accf = 0.0f;
             uint32_t emax2 = 0;
             const bool fresh = n0 == 0 && f == t;   // the open buffer starts here
             const int n1 = n0 + (f - t) + 1;
-            for (int k = 0; k < mine; ++k) tile_frame(f, first + k, fresh_frame, fresh, n1, acc, emax2);
-            warp_reduce(f - t, acc, max(emax2 & 0xFFFFu, emax2 >> 16));
+            for (int k = 0; k < mine; ++k)
+                tile_frame(f, first + k, fresh_frame, fresh, n1, exact, acc, accf, emax2);
+            warp_reduce(f - t, exact, acc, accf, max(emax2 & 0xFFFFu, emax2 >> 16));
         }
         // the CTA's share of every frame of the round: one barrier per round
         __syncthreads();
         if (tid == 0) {
             for (int f = t; f <= wend; ++f) {
                 unsigned long long A = 0;
+                double Af = 0.0;
                 uint32_t m = 0;
                 for (int q = 0; q < WT_WARPS; ++q) {
                     A += red_a[f - t][q];
+                    Af += red_f[f - t][q];
                     m = max(m, red_m[f - t][q]);
                 }
-                atomicAdd(reinterpret_cast<unsigned long long *>(
-                              &a.partA[(long)rnd * SCAN_FW + (f - t)]),
-                          A);
+                long long *slot = &a.partA[(long)rnd * SCAN_FW + (f - t)];
+                if (exact)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(slot), A);
+                else   // the slot (zeroed) holds a double in a bounded round
+                    atomicAdd(reinterpret_cast<double *>(slot), Af);
                 if (f >= horizon) atomicMax(&a.partM[f], (int)m);
             }
         }
@@ -970,12 +1003,39 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
                 __threadfence();
                 const bool lead = lb == 0;
                 for (int f = t; f <= wend; ++f) {
-                    const long long A = (long long)__ldcg(reinterpret_cast<const unsigned long long *>(
-                        &a.partA[(long)rnd * SCAN_FW + (f - t)]));
+                    const long long *slot = &a.partA[(long)rnd * SCAN_FW + (f - t)];
                     const int m = __ldcg(&a.partM[f]);
-                    if (lead && a.A_out) {
-                        a.A_out[f] = A;
-                        a.M_out[f] = m;
+                    long long A;
+                    if (exact) {
+                        A = (long long)__ldcg(reinterpret_cast<const unsigned long long *>(slot));
+                        if (lead && a.A_out) {
+                            a.A_out[f] = A;
+                            a.M_out[f] = m;
+                        }
+                    } else {
+                        // S = 256 sum sqrt(Q) in floats: each sqrt within 2^-21.4 of
+                        // its value, a thread's sum of at most 24 of them within
+                        // 2^-19.5, the double sums beyond that within 2^-32.  So
+                        // the exact A = sum floor(256 sqrt(Q)) lies in
+                        // [S (1 - e) - H W, S (1 + e)] with e = 2^-16 (about
+                        // 6x the bound).  A threshold outside that range is
+                        // decided as the exact A would decide it; one inside it
+                        // sends the frame back to be summed exactly.
+                        const double S = 256.0 * __ldcg(reinterpret_cast<const double *>(slot));
+                        constexpr double EPS = 1.52587890625e-05;   // 2^-16
+                        A = 0;
+                        const int n1 = st.n + 1;
+                        if (n1 >= 2) {
+                            const double thr = threshold(a, next_maxval(st, m, a), n1);
+                            const double lo = S * (1.0 - EPS) - (double)a.H * (double)a.W;
+                            const double hi = S * (1.0 + EPS);
+                            if (lo > thr) {
+                                A = 0x7FFFFFFFFFFFFFFFll;   // certainly above the threshold
+                            } else if (!(hi <= thr)) {
+                                last = DEC_UNSURE;
+                                break;
+                            }
+                        }
                     }
                     last = decide(st, A, m, f, a, lead);
                     ++ndec;
@@ -985,6 +1045,8 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
             s_ok = ok;
             s_ndec = ndec;
             s_last = last;
+            // a frame too close to call is summed exactly in the next round
+            s_exact = last == DEC_UNSURE || a.A_out != nullptr;
         }
         __syncthreads();
         if (!s_ok) return;
@@ -1007,6 +1069,28 @@ k_scan_wt(ScanArgs a0, const ScanArgs *__restrict__ tab, const int *__restrict__
             }
         } else if (s_last == DEC_CLOSE) {
             write_e0(st.nb - 1, wend + 1, wend + 1);   // the buffer ending with frame wend
+        } else if (s_last == DEC_UNSURE) {
+            // frames fend..wend leave S1/S2 again (the open buffer as it was
+            // before frame fend); the next round folds them back in from the
+            // ring and sums their spread exactly
+            for (int k = 0; k < mine; ++k) {
+                const int tile = first + k;
+                for (int r = 0; r < WT_TR; ++r) {
+                    uint4 *S1p, *S2p;
+                    state_ptrs(tile, r, S1p, S2p);
+                    uint4 s1 = *S1p, s2 = *S2p;
+                    for (int g = fend; g <= wend; ++g) {
+                        const uint2 e = ering_at(g, tile, r);
+                        const uint32_t ev[4] = {e.x & 0xFFFFu, e.y & 0xFFFFu, e.x >> 16,
+                                                e.y >> 16};
+                        s1.x -= ev[0]; s1.y -= ev[1]; s1.z -= ev[2]; s1.w -= ev[3];
+                        s2.x -= ev[0] * ev[0]; s2.y -= ev[1] * ev[1];
+                        s2.z -= ev[2] * ev[2]; s2.w -= ev[3] * ev[3];
+                    }
+                    *S1p = s1;
+                    *S2p = s2;
+                }
+            }
         }
         __syncthreads();
         t = fend;

@@ -226,16 +226,20 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
     SCPL_CUDA(h, h->S2.ensure(spx * sizeof(uint32_t)));
     h->e0cap = keep_e0 ? std::min(T, E0_PLANES) : 0;
     if (h->e0cap) SCPL_CUDA(h, h->E0.ensure((size_t)h->e0cap * hw * sizeof(int32_t)));
-    // per-round A_t [T][SCAN_FW], frame maxima [T], then the diagnostics M_t, A_t
-    const size_t accb = (size_t)T * SCAN_FW * 8;
+    // per-round A_t [rounds][SCAN_FW], frame maxima [T], then the diagnostics
+    // M_t, A_t.  A round decides at least one frame, except a round whose
+    // first frame is too close to call on its bounded sum; the round after it
+    // is exact and decides at least one: 2T rounds at most.
+    const size_t rounds = 2 * (size_t)T;
+    const size_t accb = rounds * SCAN_FW * 8;
     SCPL_CUDA(h, h->partA.ensure(accb + (size_t)T * 16));
-    SCPL_CUDA(h, h->count.ensure((size_t)T * sizeof(unsigned)));
+    SCPL_CUDA(h, h->count.ensure(rounds * sizeof(unsigned)));
     SCPL_CUDA(h, h->starts.ensure((size_t)(T + 1) * sizeof(int)));
     SCPL_CUDA(h, h->nbuf.ensure(sizeof(int)));
     SCPL_CUDA(h, h->errw.ensure(sizeof(int)));
     SCPL_CUDA(h, h->h_small.ensure((size_t)(T + 4) * sizeof(int)));
     cudaStream_t s = h->stream;
-    SCPL_CUDA(h, cudaMemsetAsync(h->count.p, 0, (size_t)T * sizeof(unsigned), s));
+    SCPL_CUDA(h, cudaMemsetAsync(h->count.p, 0, rounds * sizeof(unsigned), s));
     SCPL_CUDA(h, cudaMemsetAsync(h->partA.p, 0, accb + (size_t)T * 4, s));
     SCPL_CUDA(h, cudaMemsetAsync(h->errw.p, 0, sizeof(int), s));
     if (prev_rgb) {
