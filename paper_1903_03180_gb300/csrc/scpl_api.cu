@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -487,17 +488,22 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
                     if (!gathered[b] && hb[b].W - hb[b].k_eff <= target_W) {
                         if ((s = gather_out(b)) != SCPL_OK) return s;
                     }
-            int max_rem = 0, min_k = k;
+            // the next chunk: enough iterations for every buffer at the mean
+            // number of seams it has removed per iteration so far, at most 32
+            // (a buffer's last k_eff swings from 2 to 16 and overshot by a
+            // fifth of the launches; a launch past a buffer's target costs a
+            // few microseconds, a read-back between chunks a few tens)
+            int next = 0;
             for (int b = 0; b < nb; ++b) {
-                int Wc = hb[b].W - hb[b].k_eff;
-                int r = Wc - target_W;
+                const int Wc = hb[b].W - hb[b].k_eff;
+                const int r = Wc - target_W;
                 if (r > 0) {
-                    max_rem = std::max(max_rem, r);
-                    min_k = std::min(min_k, std::max(hb[b].k_eff, 1));
+                    const double mean = std::max(1.0, (double)(W - Wc) / std::max(hb[b].iters, 1));
+                    next = std::max(next, (int)std::ceil(r / mean));
                 }
             }
-            if (max_rem == 0) break;
-            iters = (max_rem + min_k - 1) / min_k;
+            if (next == 0) break;
+            iters = std::min(std::max(next, 1), 32);
             // host path: look again after a few iterations, so that buffers
             // that finish early are gathered and copied out while the others
             // carve on
