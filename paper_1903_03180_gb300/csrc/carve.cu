@@ -1070,12 +1070,10 @@ size_t carve_ws_assign(CarveWs &ws, int nb, int klog_stride, bool dpc, char *bas
     ws.st = reinterpret_cast<BufState *>(take((size_t)nb * sizeof(BufState)));
     ws.klog = reinterpret_cast<int *>(take((size_t)nb * ws.klog_stride * 4));
     ws.J = nullptr;
-    ws.Dfirst = nullptr;
     ws.colbot = nullptr;
     ws.dpx = nullptr;
     if (dpc) {
         ws.J = reinterpret_cast<uint16_t *>(take((size_t)nb * ws.nbands * ws.jstride * 2));
-        ws.Dfirst = reinterpret_cast<uint32_t *>(take((size_t)nb * ws.nbands * ws.dstride * 4));
         ws.colbot = reinterpret_cast<uint16_t *>(take((size_t)nb * ws.nbands * ws.kcap * 2));
         ws.dpx = reinterpret_cast<int *>(take((size_t)nb * (1 + ws.kcap) * 4));
     }

@@ -32,18 +32,19 @@
 // with a strict "<"), which keeps paths non-crossing.
 //
 // Every pixel carries (label << 16 | anchor): the label is the row-0 column of
-// its path (Eq. 5); the anchor is the path's column at the first row of the
-// current trace-back band of rj rows.  At each band's last row the anchors of
-// the owned columns are stored (J), so the trace back can jump a whole band in
-// one look-up.
+// its path (Eq. 5); the anchor is the path's column in the row just above the
+// current trace-back band of rj rows (the parent it took at the band's first
+// row; in band 0 its row-0 column).  At each band's last row the anchors of
+// the owned columns are stored (J): the column at the last row of the band
+// above, so the trace back goes from band to band in one look-up.
 //
 // Selection (Eq. 6): each CTA min-reduces (CE << 32 | column) per label over
 // its owned last-row columns and pushes the short list of its parents' minima
 // into CTA 0, which merges them, ranks them and keeps the k_eff lowest.
 //
 // Trace back: CTA 0 follows every selected seam from band to band through J
-// and the band-first-row directions (both bulk-copied into shared memory) and
-// records the seam's column at every band's last row; then each CTA walks all
+// (bulk-copied into shared memory) and records the seam's column at every
+// band's last row; then each CTA walks all
 // seams through its share of the bands at once (one thread per seam and band),
 // the bands' directions bulk-copied into shared memory, and writes the
 // per-row removal lists.
@@ -92,9 +93,8 @@ __host__ __device__ inline size_t al16(size_t v) { return (v + 15) & ~(size_t)15
 
 // Shared-memory layout after the DP (aliases the energy ring).
 struct PostLayout {
-    size_t segmin, lkeys, llabs, lcnt, cand, sel, pos, js, ds, end;
-    __host__ __device__ PostLayout(int W0, int C, int kcap, int nb, int jstride, int dstride,
-                                   int DPC_LMAX) {
+    size_t segmin, lkeys, llabs, lcnt, cand, sel, pos, js, end;
+    __host__ __device__ PostLayout(int W0, int C, int kcap, int nb, int jstride, int DPC_LMAX) {
         size_t o = 0;
         segmin = o; o = al16(o + (size_t)W0 * 8);
         lkeys = o;  o = al16(o + (size_t)C * DPC_LMAX * 8);
@@ -104,7 +104,6 @@ struct PostLayout {
         sel = o;    o = al16(o + (size_t)kcap * 4);
         pos = o;    o = al16(o + (size_t)kcap * 4);
         js = o;     o = al16(o + (size_t)nb * jstride * 2);
-        ds = o;     o = al16(o + (size_t)nb * dstride * 4);
         end = o;
     }
 };
@@ -229,7 +228,6 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
     const int dstride = ws.dstride;
     uint32_t *dirs = ws.dirs + (long)b * ws.dbuf;
     uint16_t *J = ws.J + (long)b * NB * ws.jstride;
-    uint32_t *Dfirst = ws.Dfirst + (long)b * NB * dstride;
 
     // ---- per-warp energy ring: stage s holds rows 1+16s .. 16+16s of the
     //      warp's 128-column window ---------------------------------------------
@@ -309,7 +307,6 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
         if (owner && quad_lane && cbase >= 0 && cbase < W0) {
             reinterpret_cast<uint4 *>(dirs)[(long)G * dstride + (cbase >> 2)] =
                 make_uint4(wq0, wq1, wq2, wq3);
-            if (((16 * G) % RJ) == 0) Dfirst[(long)((16 * G) / RJ) * dstride + (cbase >> 2)] = wq0;
         }
         wq0 = wq1 = wq2 = wq3 = 0;
     };
@@ -377,9 +374,13 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
 #pragma unroll
                 for (int v = 0; v < DPC_V; ++v) { cost[v] = nc[v]; lab[v] = nl[v]; }
                 if (ro == DPC_S - 1 && band_edge) {
+                    // a band's first row: the anchor becomes the parent's
+                    // column in the row above (the direction just chosen)
 #pragma unroll
                     for (int v = 0; v < DPC_V; ++v)
-                        lab[v] = (lab[v] & 0xFFFF0000u) | ((uint32_t)(cbase + v) & 0xFFFFu);
+                        lab[v] = (lab[v] & 0xFFFF0000u) |
+                                 ((uint32_t)(cbase + v + (int)((dbyte >> (2 * v)) & 3u) - 1) &
+                                  0xFFFFu);
                 }
                 dw |= dbyte << (8 * ((1 + ro) & 3) + vsh);
                 if (((1 + ro) & 3) == 3) {   // row i closes a 4-row block
@@ -473,15 +474,13 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
     cluster.sync();   // every CTA is done with its energy ring
 
     // ---- Eq. 6: per-parent minima -------------------------------------------------
-    const PostLayout PL(W0, C, ws.kcap, NB, ws.jstride, dstride, DPC_LMAX);
-    // CTA 0 fetches every band's anchors and first-row directions for the
-    // band trace now, so the copy overlaps the parents' minima
+    const PostLayout PL(W0, C, ws.kcap, NB, ws.jstride, DPC_LMAX);
+    // CTA 0 fetches every band's anchors for the band trace now, so the
+    // copy overlaps the parents' minima
     if (crank == 0 && tid == 0) {
         const unsigned jbytes = (unsigned)NB * ws.jstride * 2u;
-        const unsigned dbytes = (unsigned)NB * dstride * 4u;
-        mbar_expect_tx(&mbar[0], jbytes + dbytes);
+        mbar_expect_tx(&mbar[0], jbytes);
         bulk_g2s(smraw + PL.js, J, jbytes, &mbar[0]);
-        bulk_g2s(smraw + PL.ds, Dfirst, dbytes, &mbar[0]);
     }
     uint64_t *segmin = reinterpret_cast<uint64_t *>(smraw + PL.segmin);
     uint64_t *lkeys = reinterpret_cast<uint64_t *>(smraw + PL.lkeys);
@@ -532,7 +531,6 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
         int *sel = reinterpret_cast<int *>(smraw + PL.sel);
         int *pos = reinterpret_cast<int *>(smraw + PL.pos);
         uint16_t *Js = reinterpret_cast<uint16_t *>(smraw + PL.js);
-        uint32_t *Ds = reinterpret_cast<uint32_t *>(smraw + PL.ds);
         for (int r = 1; r < C; ++r) {
             const int n = lcnt[r];
             for (int x = tid; x < n; x += NT)
@@ -573,16 +571,11 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
         // only come from a fault, which is reported instead of followed)
         for (int s = tid; s < keff; s += NT) {
             int col = sel[s];
-            for (int q = NB - 1; q >= 0; --q) {
-                colbot[(long)q * ws.kcap + s] = (uint16_t)col;
-                int top = Js[(long)q * ws.jstride + col];
-                if (top >= W) { atomicExch(ws.err, DEV_EINTERNAL); top = W - 1; }
-                if (q > 0) {
-                    const int r0 = q * RJ;
-                    const uint32_t word = Ds[(long)q * dstride + (top >> 2)];
-                    col = top + (int)((word >> (8 * (r0 & 3) + 2 * (top & 3))) & 3u) - 1;
-                    if (col < 0 || col >= W) { atomicExch(ws.err, DEV_EINTERNAL); col = min(max(col, 0), W - 1); }
-                }
+            colbot[(long)(NB - 1) * ws.kcap + s] = (uint16_t)col;
+            for (int q = NB - 1; q > 0; --q) {
+                col = Js[(long)q * ws.jstride + col];   // the band above's last row
+                if (col >= W) { atomicExch(ws.err, DEV_EINTERNAL); col = W - 1; }
+                colbot[(long)(q - 1) * ws.kcap + s] = (uint16_t)col;
             }
         }
     }
@@ -672,8 +665,7 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
 size_t dpc_smem(int W0, int H, int rj, int kcap, int C, int R, int WPC, int V, bool fwd) {
     const int nb = (H + rj - 1) / rj;
     const int jstride = (W0 + 7) & ~7;
-    const int dstride = (((W0 + 3) / 4) + 3) & ~3;
-    const PostLayout PL(W0, C, kcap, nb, jstride, dstride, dpc_lmax(R, WPC, V));
+    const PostLayout PL(W0, C, kcap, nb, jstride, dpc_lmax(R, WPC, V));
     const WalkLayout WL(kcap, (nb + C - 1) / C);
     size_t m = dpc_ring(WPC, V, fwd) * (fwd ? 2 : 1);
     m = PL.end > m ? PL.end : m;

@@ -110,7 +110,6 @@ extern "C" scpl_status scpl_seams_noalloc(const int32_t *energy, int H, int W, i
     ws.E0 = nullptr;
     ws.err = nullptr;
     ws.J = nullptr;
-    ws.Dfirst = nullptr;
     ws.colbot = nullptr;
     ws.dpx = nullptr;
     ws.rj = 0;

@@ -156,12 +156,12 @@ struct CarveWs {
     // cluster DP (k_dpc) only
     int rj;             // rows per trace-back band
     int nbands;         // ceil(H / rj)
-    uint16_t *J;        // [nb][nbands][W0]  column at the band's first row of the path
-                        //                   through (band's last row, j)
+    uint16_t *J;        // [nb][nbands][W0]  column, at the last row of the band above, of
+                        //                   the path through (band's last row, j); band
+                        //                   0: the path's row-0 column
     uint16_t *colbot;   // [nb][nbands][kcap] column of each seam at each band's last row
     int *dpx;           // [nb][1 + kcap]     k_eff, then each seam's rank by column
     int jstride;        // row stride of J (W0 rounded up to 8)
-    uint32_t *Dfirst;   // [nb][nbands][dstride] direction words of every band's first row
     int dpc_r;          // halo depth of the cluster DP (16 or 32); 0: the single-CTA DP
     int dpc_wpc;        // warps per cluster-DP CTA (4 or 8; 0 means 4)
     int dpc_v;          // columns per lane of the cluster DP (4 or 2, 2 with R = 16; 0 means 4)
