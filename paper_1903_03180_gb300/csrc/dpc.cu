@@ -39,15 +39,16 @@
 // above, so the trace back goes from band to band in one look-up.
 //
 // Selection (Eq. 6): each CTA min-reduces (CE << 32 | column) per label over
-// its owned last-row columns and pushes the short list of its parents' minima
-// into CTA 0, which merges them, ranks them and keeps the k_eff lowest.
+// its owned last-row columns and writes each parent's minimum, once, into its
+// list in CTA 0 (distributed shared memory); CTA 0 merges the short lists,
+// ranks the parents' minima and keeps the k_eff lowest.
 //
 // Trace back: CTA 0 follows every selected seam from band to band through J
 // (bulk-copied into shared memory) and records the seam's column at every
-// band's last row; then each CTA walks all
-// seams through its share of the bands at once (one thread per seam and band),
-// the bands' directions bulk-copied into shared memory, and writes the
-// per-row removal lists.
+// band's last row; then the other CTAs (CTA 0 alone in a one-CTA cluster)
+// walk all seams through their share of the bands at once (one thread per
+// seam and band), the bands' directions bulk-copied into shared memory while
+// the selection runs, and write the per-row removal lists.
 #include <cooperative_groups.h>
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -91,29 +92,34 @@ constexpr unsigned long long WAIT_NS = 2000000000ull;
 
 __host__ __device__ inline size_t al16(size_t v) { return (v + 15) & ~(size_t)15; }
 
-// Shared-memory layout after the DP (aliases the energy ring).
+// Shared-memory layout after the DP (aliases the energy ring).  segmin comes
+// first in every CTA; the rest is CTA 0's: the other CTAs' lists of their
+// parents' minima (keys, labels and counts per CTA), the candidates, the
+// selection and the band anchors.
 struct PostLayout {
-    size_t segmin, lkeys, llabs, lcnt, cand, sel, pos, js, end;
-    __host__ __device__ PostLayout(int W0, int C, int kcap, int nb, int jstride, int DPC_LMAX) {
+    size_t segmin, cand, sel, pos, js, lkeys, llabs, lcnt, end;
+    __host__ __device__ PostLayout(int W0, int C, int kcap, int nb, int jstride, int lmax) {
         size_t o = 0;
         segmin = o; o = al16(o + (size_t)W0 * 8);
-        lkeys = o;  o = al16(o + (size_t)C * DPC_LMAX * 8);
-        llabs = o;  o = al16(o + (size_t)C * DPC_LMAX * 4);
-        lcnt = o;   o = al16(o + (size_t)C * 4);
         cand = o;   o = al16(o + (size_t)W0 * 8);
         sel = o;    o = al16(o + (size_t)kcap * 4);
         pos = o;    o = al16(o + (size_t)kcap * 4);
         js = o;     o = al16(o + (size_t)nb * jstride * 2);
+        lkeys = o;  o = al16(o + (size_t)C * lmax * 8);
+        llabs = o;  o = al16(o + (size_t)C * lmax * 4);
+        lcnt = o;   o = al16(o + (size_t)C * 4);
         end = o;
     }
 };
 
-// Trace-back walk layout (aliases everything before it).
+// Trace-back walk layout: after segmin, so that the walking CTAs can stage
+// their bands' directions while the parents' minima are still being taken
+// (it aliases the rest of CTA 0's layout, which a walk starts only after).
 struct WalkLayout {
     size_t stage, cur, pos, end;
-    __host__ __device__ WalkLayout(int kcap, int nbq_max) {
-        stage = 0;
-        cur = al16(DPC_STAGE_BUDGET);
+    __host__ __device__ WalkLayout(int W0, int kcap, int nbq_max) {
+        stage = al16((size_t)W0 * 8);
+        cur = al16(stage + DPC_STAGE_BUDGET);
         pos = al16(cur + (size_t)nbq_max * kcap * 4);
         end = al16(pos + (size_t)kcap * 4);
     }
@@ -471,10 +477,43 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
     }
     // directions, anchors and band rows are read back through the async proxy
     fence_proxy_async();
+    const PostLayout PL(W0, C, ws.kcap, NB, ws.jstride, DPC_LMAX);
+    uint64_t *segmin = reinterpret_cast<uint64_t *>(smraw + PL.segmin);
     cluster.sync();   // every CTA is done with its energy ring
 
+    // the walk's bands (every CTA but CTA 0 when there are several) and the
+    // staging of their direction words, issued now for the first round
+    const int nwalk = C > 1 ? C - 1 : 1, wr = C > 1 ? crank - 1 : crank;
+    const int q0 = wr >= 0 ? (wr * NB) / nwalk : 0, q1 = wr >= 0 ? ((wr + 1) * NB) / nwalk : 0;
+    const int nbq = q1 - q0;
+    const WalkLayout WL(W0, ws.kcap, (NB + nwalk - 1) / nwalk);
+    uint32_t *stage = reinterpret_cast<uint32_t *>(smraw + WL.stage);
+    const int gpb = RJ / 16;   // 16-row direction groups of a full band
+    int cb = nbq > 0 ? (int)(DPC_STAGE_BUDGET / ((size_t)nbq * dstride * 16)) : 1;
+    cb = max(1, min(cb, gpb));
+    const int rounds = (gpb + cb - 1) / cb;
+    auto issue_walk = [&](int j) {   // thread 0: round j's direction words
+        unsigned total = 0;
+        for (int qq = 0; qq < nbq; ++qq) {
+            const int q = q0 + qq;
+            const int glo = q * gpb, ghi = (min((q + 1) * RJ, H) + 15) >> 4;
+            const int shi = ghi - j * cb, slo = max(glo, shi - cb);
+            if (shi > slo) total += (unsigned)(shi - slo) * dstride * 16u;
+        }
+        mbar_expect_tx(&mbar[1], total);
+        for (int qq = 0; qq < nbq; ++qq) {
+            const int q = q0 + qq;
+            const int glo = q * gpb, ghi = (min((q + 1) * RJ, H) + 15) >> 4;
+            const int shi = ghi - j * cb, slo = max(glo, shi - cb);
+            if (shi > slo)
+                bulk_g2s(stage + (size_t)qq * cb * dstride * 4, dirs + (long)slo * dstride * 4,
+                         (unsigned)(shi - slo) * dstride * 16u, &mbar[1]);
+        }
+    };
+    const bool early = C > 1 && nbq > 0;
+    if (early && tid == 0) issue_walk(0);
+
     // ---- Eq. 6: per-parent minima -------------------------------------------------
-    const PostLayout PL(W0, C, ws.kcap, NB, ws.jstride, DPC_LMAX);
     // CTA 0 fetches every band's anchors for the band trace now, so the
     // copy overlaps the parents' minima
     if (crank == 0 && tid == 0) {
@@ -482,7 +521,6 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
         mbar_expect_tx(&mbar[0], jbytes);
         bulk_g2s(smraw + PL.js, J, jbytes, &mbar[0]);
     }
-    uint64_t *segmin = reinterpret_cast<uint64_t *>(smraw + PL.segmin);
     uint64_t *lkeys = reinterpret_cast<uint64_t *>(smraw + PL.lkeys);
     uint32_t *llabs = reinterpret_cast<uint32_t *>(smraw + PL.llabs);
     int *lcnt = reinterpret_cast<int *>(smraw + PL.lcnt);
@@ -509,18 +547,28 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
     }
     __syncthreads();
     if (crank != 0) {
-        // push this CTA's parents' minima into CTA 0's list for this rank
+        // this CTA's minimum of each parent into its list in CTA 0, once per
+        // label: at every warp's first owned column and wherever the label
+        // changes along the row (labels do not decrease along the row); a
+        // label that two warps share appears twice, which the merge absorbs
         uint64_t *rk = cluster.map_shared_rank(lkeys, 0) + (size_t)crank * DPC_LMAX;
         uint32_t *rl = cluster.map_shared_rank(llabs, 0) + (size_t)crank * DPC_LMAX;
-        for (int a = tid; a < W; a += NT) {
-            const uint64_t v = segmin[a];
-            if (v != ~0ull) {
-                const int idx = atomicAdd(&s_cnt, 1);
-                if (idx < DPC_LMAX) { rk[idx] = v; rl[idx] = (uint32_t)a; }
+        const uint32_t lprev = __shfl_up_sync(0xffffffffu, lab[DPC_V - 1], 1) >> 16;
+        if (owner) {
+#pragma unroll
+            for (int v = 0; v < DPC_V; ++v) {
+                const int c = cbase + v;
+                const uint32_t l = lab[v] >> 16;
+                const uint32_t pl = v == 0 ? lprev : (lab[v > 0 ? v - 1 : 0] >> 16);
+                if (c < W && ((v == 0 && lane == DPC_HL) || l != pl)) {
+                    const int idx = atomicAdd(&s_cnt, 1);   // < owned columns
+                    rk[idx] = segmin[l];
+                    rl[idx] = l;
+                }
             }
         }
         __syncthreads();
-        if (tid == 0) *cluster.map_shared_rank(lcnt + crank, 0) = min(s_cnt, DPC_LMAX);
+        if (tid == 0) *cluster.map_shared_rank(lcnt + crank, 0) = s_cnt;
     }
     cluster.sync();
 
@@ -531,12 +579,16 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
         int *sel = reinterpret_cast<int *>(smraw + PL.sel);
         int *pos = reinterpret_cast<int *>(smraw + PL.pos);
         uint16_t *Js = reinterpret_cast<uint16_t *>(smraw + PL.js);
-        for (int r = 1; r < C; ++r) {
-            const int n = lcnt[r];
-            for (int x = tid; x < n; x += NT)
-                atomicMin(reinterpret_cast<unsigned long long *>(
-                              &segmin[llabs[(size_t)r * DPC_LMAX + x]]),
-                          (unsigned long long)lkeys[(size_t)r * DPC_LMAX + x]);
+        // the other CTAs' lists, merged in parallel (entry e of the lists
+        // laid end to end)
+        int total = 0;
+        for (int r = 1; r < C; ++r) total += lcnt[r];
+        for (int e = tid; e < total; e += NT) {
+            int r = 1, x = e;
+            while (x >= lcnt[r]) x -= lcnt[r++];
+            atomicMin(reinterpret_cast<unsigned long long *>(
+                          &segmin[llabs[(size_t)r * DPC_LMAX + x]]),
+                      (unsigned long long)lkeys[(size_t)r * DPC_LMAX + x]);
         }
         __syncthreads();
         for (int a = tid; a < W; a += NT) {
@@ -583,9 +635,6 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
 
     // ---- trace back: every CTA walks all seams through its bands at once -------
     const int keff = __ldcg(dpx);
-    const int q0 = (crank * NB) / C, q1 = ((crank + 1) * NB) / C, nbq = q1 - q0;
-    const WalkLayout WL(ws.kcap, (NB + C - 1) / C);
-    uint32_t *stage = reinterpret_cast<uint32_t *>(smraw + WL.stage);
     int *cur = reinterpret_cast<int *>(smraw + WL.cur);
     int *pos_s = reinterpret_cast<int *>(smraw + WL.pos);
     const uint16_t *Ocur = ws.O + ((long)b * 2 + slot) * ws.plane;
@@ -596,31 +645,9 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
             const int qq = x / keff, s = x - qq * keff;
             cur[x] = __ldcg(colbot + (long)(q0 + qq) * ws.kcap + s);
         }
-        const int gpb = RJ / 16;   // 16-row direction groups of a full band
-        int cb = (int)(DPC_STAGE_BUDGET / ((size_t)nbq * dstride * 16));
-        cb = max(1, min(cb, gpb));
-        const int rounds = (gpb + cb - 1) / cb;
         for (int j = 0; j < rounds; ++j) {
             __syncthreads();   // the previous round's staging is consumed
-            if (tid == 0) {
-                unsigned total = 0;
-                for (int qq = 0; qq < nbq; ++qq) {
-                    const int q = q0 + qq;
-                    const int glo = q * gpb, ghi = (min((q + 1) * RJ, H) + 15) >> 4;
-                    const int shi = ghi - j * cb, slo = max(glo, shi - cb);
-                    if (shi > slo) total += (unsigned)(shi - slo) * dstride * 16u;
-                }
-                mbar_expect_tx(&mbar[1], total);
-                for (int qq = 0; qq < nbq; ++qq) {
-                    const int q = q0 + qq;
-                    const int glo = q * gpb, ghi = (min((q + 1) * RJ, H) + 15) >> 4;
-                    const int shi = ghi - j * cb, slo = max(glo, shi - cb);
-                    if (shi > slo)
-                        bulk_g2s(stage + (size_t)qq * cb * dstride * 4,
-                                 dirs + (long)slo * dstride * 4,
-                                 (unsigned)(shi - slo) * dstride * 16u, &mbar[1]);
-                }
-            }
+            if (tid == 0 && !(early && j == 0)) issue_walk(j);
             mbar_wait(&mbar[1], (unsigned)j & 1u, ws.err, WAIT_NS);
             for (int x = tid; x < nbq * keff; x += NT) {
                 const int qq = x / keff, s = x - qq * keff;
@@ -666,7 +693,8 @@ size_t dpc_smem(int W0, int H, int rj, int kcap, int C, int R, int WPC, int V, b
     const int nb = (H + rj - 1) / rj;
     const int jstride = (W0 + 7) & ~7;
     const PostLayout PL(W0, C, kcap, nb, jstride, dpc_lmax(R, WPC, V));
-    const WalkLayout WL(kcap, (nb + C - 1) / C);
+    const int nwalk = C > 1 ? C - 1 : 1;
+    const WalkLayout WL(W0, kcap, (nb + nwalk - 1) / nwalk);
     size_t m = dpc_ring(WPC, V, fwd) * (fwd ? 2 : 1);
     m = PL.end > m ? PL.end : m;
     m = WL.end > m ? WL.end : m;
@@ -728,7 +756,8 @@ bool dpc_plan(int W0, int H, int R, int WPC, int V, int *ctas, int *rj, size_t *
     // the walk stages at least one 16-row group of every band a CTA owns
     const int nbands = (H + r - 1) / r;
     const size_t dstride = (size_t)((((W0 + 3) / 4) + 3) & ~3);
-    if ((size_t)((nbands + C - 1) / C) * dstride * 16 > DPC_STAGE_BUDGET) return false;
+    const int nwalk = C > 1 ? C - 1 : 1;
+    if ((size_t)((nbands + nwalk - 1) / nwalk) * dstride * 16 > DPC_STAGE_BUDGET) return false;
     *ctas = C;
     *rj = r;
     *smem = bytes;
