@@ -16,10 +16,15 @@
 //          Their spatiotemporal buffers become the items of one carving
 //          workspace, so one k_energy_init, one DP launch and one k_update
 //          launch per iteration serve every buffer of every clip in the group.
-//   carve  iterations in chunks of q DP + update launches, captured once per
-//          (group, q) as a CUDA graph and replayed; after a chunk the item
-//          states are read back to size the next chunk.  Items that reach
-//          their target width become no-ops in later launches.
+//   carve  one launch of a CUDA graph whose conditional WHILE node repeats a
+//          body of LOOP_ITERS DP + update launches followed by a one-thread
+//          kernel that reads the item states and sets the loop's condition
+//          (some item still above its target, no device error), so the GPU
+//          runs the group's iterations to the end with no host in the loop.
+//          Items that reach their target width become no-ops in later
+//          launches.  Where conditional nodes are unavailable, chunks of q
+//          iterations are captured once per (group, q), and the item states
+//          are read back after each chunk to size the next.
 //   gather one launch per group for the colour frames of all its passes, then
 //          transposes for horizontal passes and the copy back for host jobs.
 // Each group runs on one of 16 streams, so groups of different sizes, and jobs
@@ -50,6 +55,7 @@ namespace {
 
 constexpr int N_STREAMS = 16;
 constexpr int MAX_CHUNK = 16;
+constexpr int LOOP_ITERS = 4;   // DP + update pairs per body of the device-side loop
 constexpr unsigned long long SPIN_NS = 2000000000ull;   // bounded device-wide waits
 
 long rup(long v, long m) { return (v + m - 1) / m * m; }
@@ -232,7 +238,8 @@ struct Group {
     Pinned hb;                  // states + err readback / upload staging
     cudaEvent_t ev = nullptr;
     int phase = 0;              // 0 scanning, 1 waiting for memory, 2 carving, 3 finished
-    std::map<int, cudaGraphExec_t> graphs;
+    std::map<int, cudaGraphExec_t> graphs;   // q > 0: chunks; 0: the device-side loop
+    bool looped = false;        // the carving ran as the device-side loop
     size_t held_after = 0;      // bytes of completed jobs still held by this group
     int wave = -1;
     size_t gt_off = 0;          // gather table in the slab
@@ -709,6 +716,94 @@ int chunk_len(long v) {
     return q;
 }
 
+// Condition of a group's device-side carving loop: 1 while some item is still
+// wider than its target after the body's iterations (and no device wait or
+// check failed), else 0.  One thread; launched inside the loop's body.
+__global__ void k_loop_more(cudaGraphConditionalHandle h, const BufState *st, int nb,
+                            const int *err) {
+    unsigned more = 0;
+    if (*(volatile const int *)err == DEV_OK)
+        for (int b = 0; b < nb; ++b)
+            if (st[b].W - st[b].k_eff > st[b].target) {
+                more = 1;
+                break;
+            }
+    cudaGraphSetConditional(h, more);
+}
+
+// The group's carving as one graph: a WHILE node (condition set to 1 at every
+// launch) around LOOP_ITERS DP + update launches and k_loop_more.  False when
+// this CUDA runtime or driver cannot build it (the chunks are used instead).
+bool build_loop(Srv *s, Group &G, cudaGraphExec_t *out) {
+    cudaGraph_t g = nullptr;
+    if (cudaGraphCreate(&g, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    bool ok = false;
+    cudaGraphConditionalHandle h;
+    cudaGraphNodeParams np = {};
+    cudaGraphNode_t node = nullptr;
+    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess) {
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            if (cudaStreamBeginCaptureToGraph(G.stream, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+                cudaError_t e = cudaSuccess;
+                for (int i = 0; i < LOOP_ITERS && e == cudaSuccess; ++i) {
+                    e = G.dpc ? launch_dpc(G.ws, G.nb, 1, nullptr, 0, G.stream)
+                              : launch_dp_select(G.ws, G.nb, 1, nullptr, 0, G.stream);
+                    if (e == cudaSuccess) e = launch_update(G.ws, G.nb, G.stream);
+                }
+                if (e == cudaSuccess) {
+                    k_loop_more<<<1, 1, 0, G.stream>>>(h, G.ws.st, G.nb, G.ws.err);
+                    e = cudaGetLastError();
+                }
+                cudaGraph_t captured = nullptr;
+                const cudaError_t e2 = cudaStreamEndCapture(G.stream, &captured);
+                ok = e == cudaSuccess && e2 == cudaSuccess &&
+                     cudaGraphInstantiate(out, g, 0) == cudaSuccess;
+            }
+        }
+    }
+    cudaGraphDestroy(g);
+    if (!ok) cudaGetLastError();
+    (void)s;
+    return ok;
+}
+
+// Launches the group's device-side loop (built once per group) and queues the
+// read-back of the item states and the error word behind it.  False when the
+// loop cannot be built here.
+scpl_status launch_loop(Srv *s, Group &G, bool *used) {
+    TraceRange trace("scpl.server.chunk");
+    *used = false;
+    cudaGraphExec_t ge = nullptr;
+    auto it = G.graphs.find(0);
+    if (it != G.graphs.end()) {
+        ge = it->second;
+    } else {
+        if (!build_loop(s, G, &ge)) return SCPL_OK;
+        G.graphs[0] = ge;
+        s->st.graphs_built++;
+    }
+    SRV_CUDA(s, cudaGraphLaunch(ge, G.stream));
+    G.looped = true;
+    *used = true;
+    s->st.chunks++;
+    BufState *hst = static_cast<BufState *>(G.hb.p);
+    int *herr = reinterpret_cast<int *>(hst + G.nb);
+    SRV_CUDA(s, cudaMemcpyAsync(hst, G.ws.st, (size_t)G.nb * sizeof(BufState),
+                                cudaMemcpyDeviceToHost, G.stream));
+    SRV_CUDA(s, cudaMemcpyAsync(herr, G.ws.err, 4, cudaMemcpyDeviceToHost, G.stream));
+    SRV_CUDA(s, cudaEventRecord(G.ev, G.stream));
+    return SCPL_OK;
+}
+
 scpl_status launch_chunk(Srv *s, Group &G, int q) {
     TraceRange trace("scpl.server.chunk");
     cudaGraphExec_t ge = nullptr;
@@ -914,6 +1009,9 @@ scpl_status setup_group(Srv *s, int gid) {
         rem_max = std::max<long>(rem_max, P.d.W - P.d.target);
         kmax = std::max(kmax, std::min(P.k, P.d.W - P.d.target));
     }
+    bool looped = false;
+    scpl_status st = launch_loop(s, G, &looped);
+    if (st != SCPL_OK || looped) return st;
     return launch_chunk(s, G, chunk_len((rem_max + kmax - 1) / kmax));
 }
 
@@ -1143,6 +1241,17 @@ scpl_status round(Srv *s, bool *any) {
         if (q > 0) {
             if ((st = launch_chunk(s, G, q)) != SCPL_OK) return st;
         } else {
+            if (G.looped) {
+                // the loop ran bodies of LOOP_ITERS DP + update launches and
+                // one condition kernel each, up to the longest item's
+                // iterations (the items' selecting DP launches)
+                const BufState *hst = static_cast<const BufState *>(G.hb.p);
+                int it = 0;
+                for (int b = 0; b < G.nb; ++b) it = std::max(it, hst[b].iters);
+                const long long bodies = std::max(1, (it + LOOP_ITERS - 1) / LOOP_ITERS);
+                count_launches(s, bodies * (2LL * LOOP_ITERS + 1));
+                G.looped = false;
+            }
             if ((st = finish_group(s, (int)g)) != SCPL_OK) return st;
         }
     }
