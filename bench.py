@@ -366,6 +366,9 @@ def run_native(args) -> None:
         dist.barrier()
     clk = clocks.stop()
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    # kernel launches of the timed region: every call launches the same ones
+    # (the carving iterations run as a graph that loops on the device)
+    timed_launches = int(scpl.scpl_get_stats(h)["launches"]) * args.steps
     # per-kernel region: the same number of steps with every launch bracketed
     # by CUDA events on its stream, for the roofline of each kernel
     scpl.scpl_set_profiling(h, True)
@@ -576,7 +579,11 @@ def run_native(args) -> None:
             "hbm_fraction_whole_step": round(algo_gb / (total_ms / args.steps / 1000) /
                                              pk["hbm_gbs"], 4),
             "kernels": per_kernel,
-            "gpu_launches": launches,
+            "kernels_region": "per-launch CUDA events over the %d steps after the timed region, "
+                              "with the carving iterations launched from the host in chunks "
+                              "(%d launches); the timed region runs them as a graph that "
+                              "loops on the device" % (args.steps, launches),
+            "gpu_launches": timed_launches,
             "clocks": clk,
             "e2e": e2e,
             "e2e_single_clip": e2e_single,

@@ -377,6 +377,9 @@ typedef struct {
                                    H * (width before the iteration)         */
     int n_kernels;
     scpl_kernel_stat kernel[8];
+    long long launches;         /* kernel launches of the last scpl_carve call,
+                                   every iteration of its device-side loop
+                                   included (profiled or not)               */
 } scpl_stats;
 
 scpl_status scpl_set_profiling(scpl_handle h, int on);

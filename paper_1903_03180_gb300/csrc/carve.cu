@@ -966,6 +966,61 @@ cudaError_t launch_update(const CarveWs &ws, int nb, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+namespace {
+// Condition of the device-side carving loop: 1 while some buffer is still
+// wider than its target after the body's iterations and no device wait or
+// check has failed, else 0.  One thread, launched inside the loop's body.
+__global__ void k_loop_more(cudaGraphConditionalHandle h, const BufState *st, int nb,
+                            const int *err) {
+    unsigned more = 0;
+    if (*(volatile const int *)err == DEV_OK)
+        for (int b = 0; b < nb; ++b)
+            if (st[b].W - st[b].k_eff > st[b].target) {
+                more = 1;
+                break;
+            }
+    cudaGraphSetConditional(h, more);
+}
+}  // namespace
+
+cudaError_t build_carve_loop(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
+                             int per_body, cudaStream_t s, cudaGraphExec_t *out) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    cudaGraphNodeParams np = {};
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(s, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) {
+        for (int i = 0; i < per_body && e == cudaSuccess; ++i) {
+            e = ws.J ? launch_dpc(ws, nb, k, seams, seam_stride, s)
+                     : launch_dp_select(ws, nb, k, seams, seam_stride, s);
+            if (e == cudaSuccess) e = launch_update(ws, nb, s);
+        }
+        if (e == cudaSuccess) {
+            k_loop_more<<<1, 1, 0, s>>>(h, ws.st, nb, ws.err);
+            e = cudaGetLastError();
+        }
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(s, &captured);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
 cudaError_t launch_dp_select(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                              cudaStream_t s) {
     if (dp_lanes_cols(ws.W0) == 4) return launch_dp_t<4>(ws, nb, k, seams, seam_stride, s);

@@ -716,66 +716,6 @@ int chunk_len(long v) {
     return q;
 }
 
-// Condition of a group's device-side carving loop: 1 while some item is still
-// wider than its target after the body's iterations (and no device wait or
-// check failed), else 0.  One thread; launched inside the loop's body.
-__global__ void k_loop_more(cudaGraphConditionalHandle h, const BufState *st, int nb,
-                            const int *err) {
-    unsigned more = 0;
-    if (*(volatile const int *)err == DEV_OK)
-        for (int b = 0; b < nb; ++b)
-            if (st[b].W - st[b].k_eff > st[b].target) {
-                more = 1;
-                break;
-            }
-    cudaGraphSetConditional(h, more);
-}
-
-// The group's carving as one graph: a WHILE node (condition set to 1 at every
-// launch) around LOOP_ITERS DP + update launches and k_loop_more.  False when
-// this CUDA runtime or driver cannot build it (the chunks are used instead).
-bool build_loop(Srv *s, Group &G, cudaGraphExec_t *out) {
-    cudaGraph_t g = nullptr;
-    if (cudaGraphCreate(&g, 0) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    bool ok = false;
-    cudaGraphConditionalHandle h;
-    cudaGraphNodeParams np = {};
-    cudaGraphNode_t node = nullptr;
-    if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) == cudaSuccess) {
-        np.type = cudaGraphNodeTypeConditional;
-        np.conditional.handle = h;
-        np.conditional.type = cudaGraphCondTypeWhile;
-        np.conditional.size = 1;
-        if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) == cudaSuccess) {
-            cudaGraph_t body = np.conditional.phGraph_out[0];
-            if (cudaStreamBeginCaptureToGraph(G.stream, body, nullptr, nullptr, 0,
-                                              cudaStreamCaptureModeRelaxed) == cudaSuccess) {
-                cudaError_t e = cudaSuccess;
-                for (int i = 0; i < LOOP_ITERS && e == cudaSuccess; ++i) {
-                    e = G.dpc ? launch_dpc(G.ws, G.nb, 1, nullptr, 0, G.stream)
-                              : launch_dp_select(G.ws, G.nb, 1, nullptr, 0, G.stream);
-                    if (e == cudaSuccess) e = launch_update(G.ws, G.nb, G.stream);
-                }
-                if (e == cudaSuccess) {
-                    k_loop_more<<<1, 1, 0, G.stream>>>(h, G.ws.st, G.nb, G.ws.err);
-                    e = cudaGetLastError();
-                }
-                cudaGraph_t captured = nullptr;
-                const cudaError_t e2 = cudaStreamEndCapture(G.stream, &captured);
-                ok = e == cudaSuccess && e2 == cudaSuccess &&
-                     cudaGraphInstantiate(out, g, 0) == cudaSuccess;
-            }
-        }
-    }
-    cudaGraphDestroy(g);
-    if (!ok) cudaGetLastError();
-    (void)s;
-    return ok;
-}
-
 // Launches the group's device-side loop (built once per group) and queues the
 // read-back of the item states and the error word behind it.  False when the
 // loop cannot be built here.
@@ -787,7 +727,11 @@ scpl_status launch_loop(Srv *s, Group &G, bool *used) {
     if (it != G.graphs.end()) {
         ge = it->second;
     } else {
-        if (!build_loop(s, G, &ge)) return SCPL_OK;
+        if (build_carve_loop(G.ws, G.nb, 1, nullptr, 0, LOOP_ITERS, G.stream, &ge) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return SCPL_OK;   // conditional nodes unavailable: chunks
+        }
         G.graphs[0] = ge;
         s->st.graphs_built++;
     }

@@ -98,6 +98,8 @@ struct Profiler {
 
 long round_up(long v, long m) { return (v + m - 1) / m * m; }
 
+constexpr int CARVE_LOOP_ITERS = 8;   // DP + update pairs per body of the device-side loop
+
 }  // namespace
 
 struct scpl_ctx {
@@ -126,9 +128,21 @@ struct scpl_ctx {
     cudaStream_t cstream = nullptr, gstream = nullptr;
     HostBuf h_small;   // starts + n_buffers + states readback
     Profiler prof;
+    // the carving loop as a graph that runs on the device until every buffer
+    // reaches its target, kept for the next call with the same workspace and
+    // arguments (the key: the workspace's bytes, nb, k, seams, their stride)
+    cudaGraphExec_t loop = nullptr;
+    unsigned char loop_ws[sizeof(CarveWs)] = {};
+    int loop_nb = 0, loop_k = 0;
+    int16_t *loop_seams = nullptr;
+    long loop_stride = 0;
+    bool loop_unavailable = false;   // conditional graph nodes cannot be built here
+    cudaStream_t lstream = nullptr;  // capture stream of the loop (the handle's may be the
+                                     // legacy default stream, which cannot be captured)
     scpl_server_s *engine = nullptr;   // scpl_carve_batch's engine (created on first use)
     // summary of the last scpl_carve call
     int last_nb = 0, last_iter_max = 0;
+    long long last_launches = 0;   // kernel launches of the last scpl_carve call
     std::vector<int> last_keff, last_iters;   // k_eff of every iteration, per buffer
     long long last_iter_total = 0;
     double last_carved_px = 0;
@@ -305,7 +319,7 @@ scpl_status run_scan(scpl_ctx *h, const uint8_t *frames, int T, int H, int W,
 // Workspace of the carving stage for nb buffers (one grow-only slab).
 scpl_status carve_ws(scpl_ctx *h, int nb, int H, int W0, int kcap, CarveWs &ws,
                      int klog_stride = 1) {
-    ws = CarveWs{};
+    std::memset(&ws, 0, sizeof ws);   // every byte set: the device loop compares workspaces
     ws.H = H;
     ws.W0 = W0;
     ws.kcap = std::max(kcap, 1);
@@ -392,6 +406,11 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
     if (k < 1) return fail(h, SCPL_EINVAL, "k=%d must be >= 1", k);
     if ((s = check_overflow(h, T, H)) != SCPL_OK) return s;
 
+    // kernel launches of this call: the scan (with the luma of the frame
+    // before a lone buffer), the initialisation, the iterations, the gathers
+    long long launched = 1 + (prev_rgb ? 1 : 0);
+    bool carve_looped = false;
+    int loop_iters = 0;
     std::vector<int> starts;
     if ((s = run_scan(h, frames, T, H, W, starts, true, nullptr, nullptr, ready, ready_frames,
                       prev_rgb, fixed)) != SCPL_OK)
@@ -472,7 +491,41 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
     } else {
         SCPL_CUDA(h, timed(h, K_ENERGY_INIT, [&] { return launch_energy_init(ws, nb, st); }));
         int iters = (remove + k - 1) / k;
-        for (int guard = 0; guard <= remove; ++guard) {
+        launched += 1 + (h->p.wf > 0 ? 1 : 0);   // k_energy_init (+ k_forward_init)
+        // device-resident clips (not profiled per kernel): the iterations as
+        // one graph that loops on the device until every buffer is carved
+        bool looped = false;
+        if (!host_out && !h->prof.on && !h->loop_unavailable) {
+            const bool same = h->loop && h->loop_nb == nb && h->loop_k == k &&
+                              h->loop_seams == seams && h->loop_stride == seam_stride &&
+                              std::memcmp(h->loop_ws, &ws, sizeof ws) == 0;
+            if (!same) {
+                if (h->loop) SCPL_CUDA(h, cudaGraphExecDestroy(h->loop));
+                h->loop = nullptr;
+                cudaGraphExec_t ge = nullptr;
+                if (!h->lstream)
+                    SCPL_CUDA(h, cudaStreamCreateWithFlags(&h->lstream, cudaStreamNonBlocking));
+                if (build_carve_loop(ws, nb, k, seams, seam_stride, CARVE_LOOP_ITERS, h->lstream,
+                                     &ge) == cudaSuccess) {
+                    h->loop = ge;
+                    h->loop_nb = nb;
+                    h->loop_k = k;
+                    h->loop_seams = seams;
+                    h->loop_stride = seam_stride;
+                    std::memcpy(h->loop_ws, &ws, sizeof ws);
+                } else {
+                    cudaGetLastError();
+                    h->loop_unavailable = true;   // conditional nodes unavailable: chunks
+                }
+            }
+            if (h->loop) {
+                SCPL_CUDA(h, cudaGraphLaunch(h->loop, st));
+                looped = true;
+            }
+        }
+        carve_looped = looped;
+        for (int guard = 0; guard <= remove && !looped; ++guard) {
+            launched += 2LL * iters;
             for (int q = 0; q < iters; ++q) {
                 SCPL_CUDA(h, timed(h, K_DP_SELECT, [&] {
                               return ws.J ? launch_dpc(ws, nb, k, seams, seam_stride, st)
@@ -521,6 +574,7 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
 
     // iteration summary (and the algorithmic bytes while profiling)
     h->last_nb = nb;
+    launched += remove == 0 ? 1 : (host_out ? nb : 1);   // identity O or the colour gathers
     h->last_iter_max = 0;
     h->last_iter_total = 0;
     h->last_carved_px = 0;
@@ -562,6 +616,7 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
             h->last_iter_max = std::max(h->last_iter_max, it);
             h->last_iter_total += it;
             h->last_iters[b] = it;
+            loop_iters = std::max(loop_iters, it);
             if (h->prof.on) {
                 // first iteration: luma and motion of every frame, O, SDo, E out
                 // (forward terms: the frame-minor luma read back, E read and
@@ -578,6 +633,12 @@ scpl_status carve_run(scpl_ctx *h, const uint8_t *frames, int T, int H, int W, i
         h->prof.bytes[K_GATHER] += (double)H * target_W * (6.0 * T + 2.0 * nb);
         if (remove == 0) h->prof.bytes[K_IDENTITY] += 2.0 * H * W * nb;
     }
+    // the device-side loop ran whole bodies of CARVE_LOOP_ITERS DP + update
+    // launches and one condition kernel, up to the longest buffer's iterations
+    if (carve_looped)
+        launched += (long long)std::max(1, (loop_iters + CARVE_LOOP_ITERS - 1) / CARVE_LOOP_ITERS) *
+                    (2LL * CARVE_LOOP_ITERS + 1);
+    h->last_launches = launched;
     int *herr = reinterpret_cast<int *>(h->h_small.as<char>());
     SCPL_CUDA(h, cudaMemcpyAsync(herr, ws.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     SCPL_CUDA(h, cudaStreamSynchronize(st));
@@ -647,6 +708,8 @@ void scpl_destroy(scpl_handle h) {
     if (h->gstream) cudaStreamDestroy(h->gstream);
     if (h->istream) cudaStreamDestroy(h->istream);
     for (cudaEvent_t e : h->prof.pool) cudaEventDestroy(e);
+    if (h->loop) cudaGraphExecDestroy(h->loop);
+    if (h->lstream) cudaStreamDestroy(h->lstream);
     h->h_small.release();
     delete h;
 }
@@ -1099,6 +1162,7 @@ scpl_status scpl_get_stats(scpl_handle h, scpl_stats *out) {
     out->iterations_max = h->last_iter_max;
     out->iterations_total = h->last_iter_total;
     out->carved_px = h->last_carved_px;
+    out->launches = h->last_launches;
     int n = 0;
     for (int i = 0; i < K_COUNT && n < 8; ++i) {
         if (pr.launches[i] == 0 && pr.bytes[i] == 0) continue;

@@ -253,6 +253,13 @@ bool dpc_select(int W0, int H, CarveWs &ws, bool requested);
 cudaError_t launch_dpc(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
                        cudaStream_t s);
 cudaError_t launch_identity_O(const CarveWs &ws, int nb, cudaStream_t s);
+// The carving iterations as one graph that runs on its own until every
+// buffer reaches its target: a conditional WHILE node around `per_body` DP +
+// update launches (the cluster DP when ws.J is set) and a one-thread kernel
+// that sets the loop's condition from the buffer states and the status word.
+// The graph's kernels get exactly these arguments.
+cudaError_t build_carve_loop(const CarveWs &ws, int nb, int k, int16_t *seams, long seam_stride,
+                             int per_body, cudaStream_t s, cudaGraphExec_t *out);
 cudaError_t launch_gather(const CarveWs &ws, const uint8_t *rgb, int T, const int *buf_of_frame,
                           int target, uint8_t *out, cudaStream_t s);
 // The colour gather of frames [t0, t0 + nt) only.

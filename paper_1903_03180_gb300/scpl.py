@@ -42,7 +42,8 @@ class KernelStat(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("n_buffers", ctypes.c_int), ("iterations_max", ctypes.c_int),
                 ("iterations_total", ctypes.c_longlong), ("carved_px", ctypes.c_double),
-                ("n_kernels", ctypes.c_int), ("kernel", KernelStat * 8)]
+                ("n_kernels", ctypes.c_int), ("kernel", KernelStat * 8),
+                ("launches", ctypes.c_longlong)]
 
 
 class Job(ctypes.Structure):
@@ -515,7 +516,7 @@ def scpl_get_stats(h) -> dict:
                                     "bytes": float(k.bytes)}
     return {"n_buffers": st.n_buffers, "iterations_max": st.iterations_max,
             "iterations_total": int(st.iterations_total), "carved_px": float(st.carved_px),
-            "kernels": kernels}
+            "launches": int(st.launches), "kernels": kernels}
 
 
 class Retargeter:

@@ -189,6 +189,33 @@ def test_repeat_calls_identical(lib, synth):
     r.close()
 
 
+def test_device_loop_follows_changing_calls(lib, synth):
+    """One handle carves a sequence of clips whose size, k and seam output
+    change from call to call, then repeats the first: the graph that loops
+    over the iterations on the device is rebuilt whenever the workspace or
+    the arguments change, and every result equals the same call on a
+    profiled handle, whose iterations are launched from the host in chunks."""
+    clips = [synth.clip(12, 40, 150, seed=31, cuts=(6, 9)),
+             synth.clip(9, 56, 210, seed=32, cuts=(4, 7)),
+             synth.clip(12, 40, 150, seed=33, cuts=(5, 8))]
+    calls = [(0, 110, 8, False), (1, 140, 16, True), (0, 110, 8, True), (0, 110, 3, False),
+             (2, 120, 8, False), (0, 110, 8, False)]
+    r = lib.Retargeter()
+    ref = lib.Retargeter()
+    lib.scpl_set_profiling(ref.h, True)
+    for ci, target, k, with_seams in calls:
+        f = torch.from_numpy(clips[ci]).cuda()
+        a = r.carve(f, target, k, with_seams=with_seams)
+        b = ref.carve(f, target, k, with_seams=with_seams)
+        torch.cuda.synchronize()
+        assert torch.equal(a[0], b[0]), (ci, target, k, with_seams)
+        assert np.array_equal(a[1], b[1])
+        if with_seams:
+            assert torch.equal(a[2], b[2])
+    r.close()
+    ref.close()
+
+
 def test_errors(lib):
     h = lib.scpl_create()
     f = torch.zeros((1, 4, 4, 3), dtype=torch.uint8, device="cuda")
