@@ -322,12 +322,26 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
         const uint32_t *ps = pring + (size_t)(s % DPC_NST) * DPC_S * DPC_WW + lane * DPC_V;
         const int ibase = 1 + DPC_S * s;
         const bool band_edge = ((ibase + DPC_S - 1) % RJ) == 0;   // row 16s+16 starts a band
+        // with 2 columns a lane (plain energy) the stage's 16 rows of energy
+        // are read into registers first, off the rows' dependency chain
+        constexpr bool PRE = V == 2 && !FWD;
+        [[maybe_unused]] uint2 epre[PRE ? DPC_S : 1];
+        if constexpr (PRE) {
+#pragma unroll
+            for (int ro = 0; ro < DPC_S; ++ro) {
+                const uint2 ev = *reinterpret_cast<const uint2 *>(rs + ro * DPC_WW);
+                epre[ro] = make_uint2(valid[0] ? ev.x : BIG, valid[1] ? ev.y : BIG);
+            }
+        }
 #pragma unroll
         for (int ro = 0; ro < DPC_S; ++ro) {
             const int i = ibase + ro;
             if (!GUARD || i < H) {
                 uint32_t e[DPC_V];
-                if constexpr (V == 4) {
+                if constexpr (PRE) {
+                    e[0] = epre[ro].x;
+                    e[DPC_V - 1] = epre[ro].y;
+                } else if constexpr (V == 4) {
                     const uint4 ev = *reinterpret_cast<const uint4 *>(rs + ro * DPC_WW);
                     e[0] = valid[0] ? ev.x : BIG;
                     e[1] = valid[1] ? ev.y : BIG;
