@@ -322,15 +322,31 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
         const uint32_t *ps = pring + (size_t)(s % DPC_NST) * DPC_S * DPC_WW + lane * DPC_V;
         const int ibase = 1 + DPC_S * s;
         const bool band_edge = ((ibase + DPC_S - 1) % RJ) == 0;   // row 16s+16 starts a band
-        // with 2 columns a lane (plain energy) the stage's 16 rows of energy
-        // are read into registers first, off the rows' dependency chain
+        // with plain energy the stage's 16 rows are read into registers
+        // first, off the rows' dependency chain (with the forward terms the
+        // extra registers made the DP slower)
         constexpr bool PRE = V == 2 && !FWD;
+        constexpr bool PRE4 = V == 4 && !FWD;
         [[maybe_unused]] uint2 epre[PRE ? DPC_S : 1];
+        [[maybe_unused]] uint2 ppre[PRE && FWD ? DPC_S : 1];
+        [[maybe_unused]] uint4 epre4[PRE4 ? DPC_S : 1];
+        if constexpr (PRE4) {
+#pragma unroll
+            for (int ro = 0; ro < DPC_S; ++ro) {
+                const uint4 ev = *reinterpret_cast<const uint4 *>(rs + ro * DPC_WW);
+                epre4[ro] = make_uint4(valid[0] ? ev.x : BIG, valid[1] ? ev.y : BIG,
+                                       valid[2] ? ev.z : BIG, valid[3] ? ev.w : BIG);
+            }
+        }
         if constexpr (PRE) {
 #pragma unroll
             for (int ro = 0; ro < DPC_S; ++ro) {
                 const uint2 ev = *reinterpret_cast<const uint2 *>(rs + ro * DPC_WW);
                 epre[ro] = make_uint2(valid[0] ? ev.x : BIG, valid[1] ? ev.y : BIG);
+                if constexpr (FWD) {
+                    const uint2 pv = *reinterpret_cast<const uint2 *>(ps + ro * DPC_WW);
+                    ppre[ro] = make_uint2(valid[0] ? pv.x : 0u, valid[1] ? pv.y : 0u);
+                }
             }
         }
 #pragma unroll
@@ -341,6 +357,11 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
                 if constexpr (PRE) {
                     e[0] = epre[ro].x;
                     e[DPC_V - 1] = epre[ro].y;
+                } else if constexpr (PRE4) {
+                    e[0] = epre4[ro].x;
+                    e[1 % DPC_V] = epre4[ro].y;
+                    e[2 % DPC_V] = epre4[ro].z;
+                    e[3 % DPC_V] = epre4[ro].w;
                 } else if constexpr (V == 4) {
                     const uint4 ev = *reinterpret_cast<const uint4 *>(rs + ro * DPC_WW);
                     e[0] = valid[0] ? ev.x : BIG;
@@ -353,7 +374,10 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
                     e[1] = valid[1] ? ev.y : BIG;
                 }
                 [[maybe_unused]] uint32_t pw[DPC_V];   // forward terms of the row's pixels (0 outside [0, W))
-                if constexpr (FWD) {
+                if constexpr (FWD && PRE) {
+                    pw[0] = ppre[ro].x;
+                    pw[DPC_V - 1] = ppre[ro].y;
+                } else if constexpr (FWD) {
                     if constexpr (V == 4) {
                         const uint4 pv = *reinterpret_cast<const uint4 *>(ps + ro * DPC_WW);
                         pw[0] = valid[0] ? pv.x : 0u;
