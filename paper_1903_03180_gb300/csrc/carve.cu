@@ -805,17 +805,89 @@ __device__ __forceinline__ void gather_row(const uint16_t *__restrict__ O,
     }
 }
 
-// Final colour gather: out[t][i][p] = rgb[t][i][O[i][p]].  grid (H, frames),
-// frame t = t0 + blockIdx.y.
-__global__ void k_gather(CarveWs ws, const uint8_t *__restrict__ rgb, const int *buf_of_frame,
-                         int target, uint8_t *__restrict__ out, int t0) {
-    const int i = blockIdx.x, t = t0 + blockIdx.y;
-    const int b = buf_of_frame[t];
-    int W, slot, removed;
-    committed(ws.st[b], W, slot, removed);
-    const uint16_t *O = ws.O + ((long)b * 2 + slot) * ws.plane + (long)i * ws.pitch;
-    gather_row(O, rgb + ((long)t * ws.H + i) * ws.W0 * 3,
-               out + ((long)t * ws.H + i) * (long)target * 3, target);
+// Final colour gather: out[t][i][p] = rgb[t][i][O[i][p]].  grid (H, ceil(nt /
+// GA_FRAMES)), GA_THREADS threads: the CTA takes row i of GA_FRAMES
+// consecutive frames [t0 + GA_FRAMES * blockIdx.y, ...), GA_PAR at a time, so
+// each thread's origin quad is read once for all of them and their source
+// bytes are in flight together (frames of one buffer share the origin map; a
+// group that spans two buffers reads each frame's own).
+constexpr int GA_FRAMES = 8;
+constexpr int GA_PAR = 2;
+constexpr int GA_THREADS = 128;
+__global__ void __launch_bounds__(GA_THREADS) k_gather(CarveWs ws, const uint8_t *__restrict__ rgb,
+                                                      const int *buf_of_frame, int target,
+                                                      uint8_t *__restrict__ out, int t0, int nt) {
+    const int i = blockIdx.x;
+    const int fa = t0 + GA_FRAMES * blockIdx.y, fb = min(fa + GA_FRAMES, t0 + nt);
+    const long rowb = (long)ws.W0 * 3, outb = (long)target * 3;
+    for (int t = fa; t < fb; t += GA_PAR) {
+        if (t + GA_PAR > fb) {   // the last frames of the clip, one at a time
+            for (int u = t; u < fb; ++u) {
+                const int b = buf_of_frame[u];
+                int W, slot, removed;
+                committed(ws.st[b], W, slot, removed);
+                gather_row(ws.O + ((long)b * 2 + slot) * ws.plane + (long)i * ws.pitch,
+                           rgb + ((long)u * ws.H + i) * rowb, out + ((long)u * ws.H + i) * outb,
+                           target);
+            }
+            break;
+        }
+        const uint16_t *O[GA_PAR];
+        const uint8_t *src[GA_PAR];
+        uint8_t *dst[GA_PAR];
+        bool words = true;
+#pragma unroll
+        for (int u = 0; u < GA_PAR; ++u) {
+            const int b = buf_of_frame[t + u];
+            int W, slot, removed;
+            committed(ws.st[b], W, slot, removed);
+            O[u] = ws.O + ((long)b * 2 + slot) * ws.plane + (long)i * ws.pitch;
+            src[u] = rgb + ((long)(t + u) * ws.H + i) * rowb;
+            dst[u] = out + ((long)(t + u) * ws.H + i) * outb;
+            words = words && (reinterpret_cast<uintptr_t>(dst[u]) & 3) == 0;
+        }
+        for (int p = 4 * threadIdx.x; p < target; p += 4 * GA_THREADS) {
+            const int n = min(4, target - p);
+            int o[GA_PAR][4];
+#pragma unroll
+            for (int u = 0; u < GA_PAR; ++u) {
+                // O rows are 8-byte aligned; frames of one buffer share the row
+                const uint2 q = u > 0 && O[u] == O[u - 1] ? make_uint2(0, 0)
+                                                          : *reinterpret_cast<const uint2 *>(O[u] + p);
+                if (u > 0 && O[u] == O[u - 1]) {
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) o[u][j] = o[u - 1][j];
+                } else {
+                    o[u][0] = (int)(q.x & 0xFFFF);
+                    o[u][1] = (int)(q.x >> 16);
+                    o[u][2] = (int)(q.y & 0xFFFF);
+                    o[u][3] = (int)(q.y >> 16);
+                }
+            }
+            if (n == 4 && words) {
+                uint32_t x[GA_PAR][12];
+#pragma unroll
+                for (int u = 0; u < GA_PAR; ++u)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) x[u][3 * j + c] = src[u][o[u][j] * 3 + c];
+#pragma unroll
+                for (int u = 0; u < GA_PAR; ++u) {
+                    uint32_t *d = reinterpret_cast<uint32_t *>(dst[u] + p * 3);
+#pragma unroll
+                    for (int w = 0; w < 3; ++w)
+                        d[w] = x[u][4 * w] | (x[u][4 * w + 1] << 8) | (x[u][4 * w + 2] << 16) |
+                               (x[u][4 * w + 3] << 24);
+                }
+            } else {
+                for (int u = 0; u < GA_PAR; ++u)
+                    for (int j = 0; j < n; ++j)
+                        for (int c = 0; c < 3; ++c)
+                            dst[u][(p + j) * 3 + c] = src[u][o[u][j] * 3 + c];
+            }
+        }
+    }
 }
 
 // Final colour gather of frames listed in a table (frames of several clips
@@ -1037,7 +1109,8 @@ cudaError_t launch_gather_range(const CarveWs &ws, const uint8_t *rgb, int t0, i
                                 cudaStream_t s) {
     for (int f = 0; f < nt; f += 65535) {
         const int n = nt - f < 65535 ? nt - f : 65535;
-        k_gather<<<dim3(ws.H, n), 256, 0, s>>>(ws, rgb, buf_of_frame, target, out, t0 + f);
+        k_gather<<<dim3(ws.H, (n + GA_FRAMES - 1) / GA_FRAMES), GA_THREADS, 0, s>>>(
+            ws, rgb, buf_of_frame, target, out, t0 + f, n);
     }
     return cudaGetLastError();
 }
