@@ -805,14 +805,58 @@ __device__ __forceinline__ void gather_row(const uint16_t *__restrict__ O,
     }
 }
 
+// One output row of two frames at once: dst_u[p] = src_u[O_u[p]] for p <
+// target (u = a, b).  Each thread's origin quad is read once when both frames
+// share their origin row (frames of one buffer), and the source bytes of both
+// frames are in flight together.  NT: threads of the CTA.
+template <int NT>
+__device__ __forceinline__ void gather_pair(const uint16_t *__restrict__ Oa,
+                                            const uint16_t *__restrict__ Ob,
+                                            const uint8_t *__restrict__ srca,
+                                            const uint8_t *__restrict__ srcb,
+                                            uint8_t *__restrict__ dsta, uint8_t *__restrict__ dstb,
+                                            int target) {
+    const bool words = ((reinterpret_cast<uintptr_t>(dsta) & 3) == 0) &&
+                       ((reinterpret_cast<uintptr_t>(dstb) & 3) == 0);
+    for (int p = 4 * threadIdx.x; p < target; p += 4 * NT) {
+        const int n = min(4, target - p);
+        const uint2 qa = *reinterpret_cast<const uint2 *>(Oa + p);   // O rows are 8-byte aligned
+        const uint2 qb = Oa == Ob ? qa : *reinterpret_cast<const uint2 *>(Ob + p);
+        const int oa[4] = {(int)(qa.x & 0xFFFF), (int)(qa.x >> 16), (int)(qa.y & 0xFFFF),
+                           (int)(qa.y >> 16)};
+        const int ob[4] = {(int)(qb.x & 0xFFFF), (int)(qb.x >> 16), (int)(qb.y & 0xFFFF),
+                           (int)(qb.y >> 16)};
+        if (n == 4 && words) {
+            uint32_t x[12], y[12];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    x[3 * j + c] = srca[oa[j] * 3 + c];
+                    y[3 * j + c] = srcb[ob[j] * 3 + c];
+                }
+            uint32_t *da = reinterpret_cast<uint32_t *>(dsta + p * 3);
+            uint32_t *db = reinterpret_cast<uint32_t *>(dstb + p * 3);
+#pragma unroll
+            for (int w = 0; w < 3; ++w) {
+                da[w] = x[4 * w] | (x[4 * w + 1] << 8) | (x[4 * w + 2] << 16) | (x[4 * w + 3] << 24);
+                db[w] = y[4 * w] | (y[4 * w + 1] << 8) | (y[4 * w + 2] << 16) | (y[4 * w + 3] << 24);
+            }
+        } else {
+            for (int j = 0; j < n; ++j)
+                for (int c = 0; c < 3; ++c) {
+                    dsta[(p + j) * 3 + c] = srca[oa[j] * 3 + c];
+                    dstb[(p + j) * 3 + c] = srcb[ob[j] * 3 + c];
+                }
+        }
+    }
+}
+
 // Final colour gather: out[t][i][p] = rgb[t][i][O[i][p]].  grid (H, ceil(nt /
 // GA_FRAMES)), GA_THREADS threads: the CTA takes row i of GA_FRAMES
-// consecutive frames [t0 + GA_FRAMES * blockIdx.y, ...), GA_PAR at a time, so
-// each thread's origin quad is read once for all of them and their source
-// bytes are in flight together (frames of one buffer share the origin map; a
-// group that spans two buffers reads each frame's own).
+// consecutive frames [t0 + GA_FRAMES * blockIdx.y, ...), two at a time
+// (gather_pair; a lone last frame through gather_row).
 constexpr int GA_FRAMES = 8;
-constexpr int GA_PAR = 2;
 constexpr int GA_THREADS = 128;
 __global__ void __launch_bounds__(GA_THREADS) k_gather(CarveWs ws, const uint8_t *__restrict__ rgb,
                                                       const int *buf_of_frame, int target,
@@ -820,89 +864,66 @@ __global__ void __launch_bounds__(GA_THREADS) k_gather(CarveWs ws, const uint8_t
     const int i = blockIdx.x;
     const int fa = t0 + GA_FRAMES * blockIdx.y, fb = min(fa + GA_FRAMES, t0 + nt);
     const long rowb = (long)ws.W0 * 3, outb = (long)target * 3;
-    for (int t = fa; t < fb; t += GA_PAR) {
-        if (t + GA_PAR > fb) {   // the last frames of the clip, one at a time
-            for (int u = t; u < fb; ++u) {
-                const int b = buf_of_frame[u];
-                int W, slot, removed;
-                committed(ws.st[b], W, slot, removed);
-                gather_row(ws.O + ((long)b * 2 + slot) * ws.plane + (long)i * ws.pitch,
-                           rgb + ((long)u * ws.H + i) * rowb, out + ((long)u * ws.H + i) * outb,
-                           target);
-            }
-            break;
-        }
-        const uint16_t *O[GA_PAR];
-        const uint8_t *src[GA_PAR];
-        uint8_t *dst[GA_PAR];
-        bool words = true;
-#pragma unroll
-        for (int u = 0; u < GA_PAR; ++u) {
-            const int b = buf_of_frame[t + u];
-            int W, slot, removed;
-            committed(ws.st[b], W, slot, removed);
-            O[u] = ws.O + ((long)b * 2 + slot) * ws.plane + (long)i * ws.pitch;
-            src[u] = rgb + ((long)(t + u) * ws.H + i) * rowb;
-            dst[u] = out + ((long)(t + u) * ws.H + i) * outb;
-            words = words && (reinterpret_cast<uintptr_t>(dst[u]) & 3) == 0;
-        }
-        for (int p = 4 * threadIdx.x; p < target; p += 4 * GA_THREADS) {
-            const int n = min(4, target - p);
-            int o[GA_PAR][4];
-#pragma unroll
-            for (int u = 0; u < GA_PAR; ++u) {
-                // O rows are 8-byte aligned; frames of one buffer share the row
-                const uint2 q = u > 0 && O[u] == O[u - 1] ? make_uint2(0, 0)
-                                                          : *reinterpret_cast<const uint2 *>(O[u] + p);
-                if (u > 0 && O[u] == O[u - 1]) {
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) o[u][j] = o[u - 1][j];
-                } else {
-                    o[u][0] = (int)(q.x & 0xFFFF);
-                    o[u][1] = (int)(q.x >> 16);
-                    o[u][2] = (int)(q.y & 0xFFFF);
-                    o[u][3] = (int)(q.y >> 16);
-                }
-            }
-            if (n == 4 && words) {
-                uint32_t x[GA_PAR][12];
-#pragma unroll
-                for (int u = 0; u < GA_PAR; ++u)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j)
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) x[u][3 * j + c] = src[u][o[u][j] * 3 + c];
-#pragma unroll
-                for (int u = 0; u < GA_PAR; ++u) {
-                    uint32_t *d = reinterpret_cast<uint32_t *>(dst[u] + p * 3);
-#pragma unroll
-                    for (int w = 0; w < 3; ++w)
-                        d[w] = x[u][4 * w] | (x[u][4 * w + 1] << 8) | (x[u][4 * w + 2] << 16) |
-                               (x[u][4 * w + 3] << 24);
-                }
-            } else {
-                for (int u = 0; u < GA_PAR; ++u)
-                    for (int j = 0; j < n; ++j)
-                        for (int c = 0; c < 3; ++c)
-                            dst[u][(p + j) * 3 + c] = src[u][o[u][j] * 3 + c];
-            }
-        }
+    auto orow = [&](int t) {
+        const int b = buf_of_frame[t];
+        int W, slot, removed;
+        committed(ws.st[b], W, slot, removed);
+        return ws.O + ((long)b * 2 + slot) * ws.plane + (long)i * ws.pitch;
+    };
+    for (int t = fa; t < fb; t += 2) {
+        const uint8_t *src = rgb + ((long)t * ws.H + i) * rowb;
+        uint8_t *dst = out + ((long)t * ws.H + i) * outb;
+        if (t + 1 < fb)
+            gather_pair<GA_THREADS>(orow(t), orow(t + 1), src, src + (long)ws.H * rowb, dst,
+                        dst + (long)ws.H * outb, target);
+        else
+            gather_row(orow(t), src, dst, target);
     }
 }
 
 // Final colour gather of frames listed in a table (frames of several clips
-// that share one (H, W0) workspace).  grid (H, frames).
-__global__ void k_gather_frames(CarveWs ws, const GatherFrame *__restrict__ tab) {
+// that share one (H, W0) workspace).  grid (H, ceil(nframes / GA_FRAMES)),
+// GA_THREADS threads: entries [GA_FRAMES * blockIdx.y, ...), two at a time
+// when both have the same target width.
+__global__ void __launch_bounds__(GA_THREADS) k_gather_frames(CarveWs ws,
+                                                             const GatherFrame *__restrict__ tab,
+                                                             int nframes) {
     const int i = blockIdx.x;
-    const GatherFrame g = tab[blockIdx.y];
-    int W, slot, removed;
-    committed(ws.st[g.b], W, slot, removed);
-    if (W != g.target) {   // carving did not reach the target: report, copy nothing
-        if (i == 0 && threadIdx.x == 0) atomicExch(ws.err, DEV_EINTERNAL);
-        return;
+    const int fa = GA_FRAMES * blockIdx.y, fb = min(fa + GA_FRAMES, nframes);
+    // the entry's origin row, or NULL (reported) if its buffer missed its target
+    auto orow = [&](const GatherFrame &g) -> const uint16_t * {
+        int W, slot, removed;
+        committed(ws.st[g.b], W, slot, removed);
+        if (W != g.target) {   // carving did not reach the target: report, copy nothing
+            if (i == 0 && threadIdx.x == 0) atomicExch(ws.err, DEV_EINTERNAL);
+            return nullptr;
+        }
+        return ws.O + ((long)g.b * 2 + slot) * ws.plane + (long)i * ws.pitch;
+    };
+    for (int e = fa; e < fb;) {
+        const GatherFrame g = tab[e];
+        const uint16_t *O = orow(g);
+        if (e + 1 < fb && tab[e + 1].target == g.target) {
+            const GatherFrame h = tab[e + 1];
+            const uint16_t *O2 = orow(h);
+            if (O && O2)
+                gather_pair<GA_THREADS>(O, O2, g.src + (long)i * ws.W0 * 3, h.src + (long)i * ws.W0 * 3,
+                            g.dst + (long)i * g.target * 3, h.dst + (long)i * h.target * 3,
+                            g.target);
+            else if (O)
+                gather_row(O, g.src + (long)i * ws.W0 * 3, g.dst + (long)i * g.target * 3,
+                           g.target);
+            else if (O2)
+                gather_row(O2, h.src + (long)i * ws.W0 * 3, h.dst + (long)i * h.target * 3,
+                           h.target);
+            e += 2;
+        } else {
+            if (O)
+                gather_row(O, g.src + (long)i * ws.W0 * 3, g.dst + (long)i * g.target * 3,
+                           g.target);
+            e += 1;
+        }
     }
-    const uint16_t *O = ws.O + ((long)g.b * 2 + slot) * ws.plane + (long)i * ws.pitch;
-    gather_row(O, g.src + (long)i * ws.W0 * 3, g.dst + (long)i * g.target * 3, g.target);
 }
 
 // dst[t][j][i] = src[t][i][j] for RGB pixels: [T][H][W][3] -> [T][W][H][3].
@@ -1124,7 +1145,8 @@ cudaError_t launch_gather_frames(const CarveWs &ws, const GatherFrame *tab, int 
                                  cudaStream_t s) {
     for (int f0 = 0; f0 < nframes; f0 += 65535) {
         const int n = nframes - f0 < 65535 ? nframes - f0 : 65535;
-        k_gather_frames<<<dim3(ws.H, n), 256, 0, s>>>(ws, tab + f0);
+        k_gather_frames<<<dim3(ws.H, (n + GA_FRAMES - 1) / GA_FRAMES), GA_THREADS, 0, s>>>(
+            ws, tab + f0, n);
     }
     return cudaGetLastError();
 }
