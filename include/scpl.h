@@ -244,7 +244,11 @@ scpl_status scpl_seams(scpl_handle h, const int32_t *energy, int H, int W, int k
  * Limits: 1 <= T, 1 <= H <= 65535, 2 <= target_W <= W <= 8192, 1 <= k;
  * 255*(8*wg + wm)*min(T, t_max)*H < 2^31 and t_max*(255*(8*wg+wm))^2 < 2^32
  * (else SCPL_EOVERFLOW).  Synchronises the stream (the buffer count decides
- * the launch shapes). */
+ * the launch shapes).  The iterations run as one CUDA graph that loops on the
+ * device until every buffer is carved (a conditional WHILE node); the handle
+ * keeps that graph and builds a new one when the workspace, the buffer count,
+ * k or the seam output changes.  With profiling on (scpl_set_profiling) the
+ * iterations are launched from the host instead, each bracketed by events. */
 scpl_status scpl_carve(scpl_handle h, const uint8_t *frames, int T, int H, int W, int target_W,
                        int k, uint8_t *out, int32_t *buffer_starts, int *n_buffers,
                        int16_t *seams);
@@ -472,7 +476,9 @@ typedef struct {
 /* Carve every job; returns when all have completed (host-synchronous).  The
  * work starts after everything queued before on the handle's stream.  The
  * handle keeps the engine and its device memory pool between calls (freed by
- * scpl_destroy).
+ * scpl_destroy).  Each group of same-size passes carves in one launch of a
+ * CUDA graph that loops on the device until all of the group's buffers reach
+ * their targets (servers carve in chunks with a read-back between them).
  * Returns SCPL_OK if every job succeeded, else the first failing job's status
  * (each job's own result is in jobs[i].status; a job with bad arguments
  * fails alone with SCPL_EINVAL). */
