@@ -216,6 +216,29 @@ def test_device_loop_follows_changing_calls(lib, synth):
     ref.close()
 
 
+def test_launch_count_of_a_carve(lib, synth):
+    """scpl_get_stats reports the kernels the last carve launched: with the
+    iterations looping on the device, the scan, the initialisation, whole
+    loop bodies (8 DP + 8 update launches and one condition kernel, up to the
+    longest buffer's iterations) and the gather; profiled, the scan, the
+    initialisation, the DP and update launches of the host's chunks and the
+    gather."""
+    f = torch.from_numpy(synth.clip(10, 40, 120, seed=41, cuts=(5, 8))).cuda()
+    h = lib.scpl_create()
+    out = torch.empty((10, 40, 80, 3), dtype=torch.uint8, device="cuda")
+    lib.scpl_carve(h, f, 80, 4, out)
+    torch.cuda.synchronize()
+    st = lib.scpl_get_stats(h)
+    bodies = max(1, -(-st["iterations_max"] // 8))
+    assert st["launches"] == 3 + bodies * 17, st
+    lib.scpl_set_profiling(h, True)
+    lib.scpl_carve(h, f, 80, 4, out)
+    st = lib.scpl_get_stats(h)
+    assert st["launches"] == sum(k["launches"] for k in st["kernels"].values()), st
+    lib.scpl_set_profiling(h, False)
+    lib.scpl_destroy(h)
+
+
 def test_errors(lib):
     h = lib.scpl_create()
     f = torch.zeros((1, 4, 4, 3), dtype=torch.uint8, device="cuda")
