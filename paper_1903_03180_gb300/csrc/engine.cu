@@ -721,8 +721,9 @@ int chunk_len(long v) {
 }
 
 // Launches the group's device-side loop (built once per group) and queues the
-// read-back of the item states and the error word behind it.  False when the
-// loop cannot be built here.
+// read-back of the item states and the error word behind it.  *used stays
+// false (and nothing is launched) for servers and where the loop cannot be
+// built; the caller then carves in chunks.
 scpl_status launch_loop(Srv *s, Group &G, bool *used) {
     TraceRange trace("scpl.server.chunk");
     *used = false;
