@@ -316,12 +316,16 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
         }
         wq0 = wq1 = wq2 = wq3 = 0;
     };
+    // band edges by countdown (rj is a multiple of 16): the stage whose last
+    // row starts a band, and the index of the band that ends one row above
+    const int spb = RJ / DPC_S;
+    int bleft = spb, bq = 0;
+    bool band_edge = false;
     auto stage_rows = [&](int s, auto guarded) {
         constexpr bool GUARD = decltype(guarded)::value;
         const uint32_t *rs = wring + (size_t)(s % DPC_NST) * DPC_S * DPC_WW + lane * DPC_V;
         const uint32_t *ps = pring + (size_t)(s % DPC_NST) * DPC_S * DPC_WW + lane * DPC_V;
         const int ibase = 1 + DPC_S * s;
-        const bool band_edge = ((ibase + DPC_S - 1) % RJ) == 0;   // row 16s+16 starts a band
         // with plain energy the stage's 16 rows are read into registers
         // first, off the rows' dependency chain (with the forward terms the
         // extra registers made the DP slower)
@@ -436,7 +440,7 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
                     if (ro == 14) store_group(s);   // rows 16s .. 16s+15 are complete
                 }
                 if (ro == DPC_S - 2 && band_edge && owner) {   // a band's last row
-                    uint16_t *Jrow = J + (long)(i / RJ) * ws.jstride;
+                    uint16_t *Jrow = J + (long)bq * ws.jstride;
 #pragma unroll
                     for (int v = 0; v < DPC_V; ++v) {
                         const int c = cbase + v;
@@ -446,49 +450,60 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
             }
         }
     };
+    // After a stage's rows: the edge strips go out to the neighbours first
+    // (they wait for them), then lane 0 refills the ring slot and arms the
+    // inbox that the previous refresh emptied, then the warp waits for its
+    // own inbox.  Each of the three is one divergent region of the warp.
+    int arm = -1;   // inbox parity to re-arm at the next stage (-1: none)
     for (int s = 0; s < nstages; ++s) {
         mbar_wait(&mring[w][s % DPC_NST], (unsigned)(s / DPC_NST) & 1u, ws.err, WAIT_NS);
         const int ibase = 1 + DPC_S * s;
+        band_edge = --bleft == 0;   // row 16s+16 starts a band
         if (ibase + DPC_S - 1 < H) stage_rows(s, std::false_type{});
         else stage_rows(s, std::true_type{});
-        __syncwarp();
-        if (lane == 0) issue(s + DPC_NST);   // the warp is done with this slot
+        if (band_edge) { bleft = spb; ++bq; }
         const int ilast = ibase + DPC_S - 1;   // the stage's last row
-        if ((s + 1) % DPC_SPR == 0 && ilast < H - 1) {
-            // refresh e: send the owned edge strips to the neighbours' inboxes,
-            // then wait for the own inbox and reload the halos from it
-            const int e = (s + 1) / DPC_SPR - 1, par = e & 1;
-            if (lane >= 32 - 2 * DPC_HL && lane < 32 - DPC_HL && g + 1 < nwarps) {
-                const int tg = g + 1, tr = tg / DPC_WPC, tw = tg % DPC_WPC;
-                const int o = (lane - (32 - 2 * DPC_HL)) * DPC_V;
+        const bool refresh = (s + 1) % DPC_SPR == 0 && ilast < H - 1;
+        const int e = (s + 1) / DPC_SPR - 1, par = e & 1;
+        if (refresh) {
+            // refresh e: lanes [32-2HL, 32-HL) send to the right neighbour's
+            // left inbox, lanes [HL, 2HL) to the left neighbour's right inbox
+            const bool toR = lane >= 32 - 2 * DPC_HL && lane < 32 - DPC_HL;
+            const bool toL = lane >= DPC_HL && lane < 2 * DPC_HL;
+            if ((toR && g + 1 < nwarps) || (toL && g > 0)) {
+                const int tg = toR ? g + 1 : g - 1, tr = tg / DPC_WPC, tw = tg % DPC_WPC;
+                const int o = (toR ? lane - (32 - 2 * DPC_HL) : lane - DPC_HL) * DPC_V;
+                uint32_t *cb = toR ? &inLc[par][tw][o] : &inRc[par][tw][o];
+                uint32_t *lb = toR ? &inLl[par][tw][o] : &inRl[par][tw][o];
                 const uint32_t mb = mapa_u32(smem_u32(&minbox[tw][par]), tr);
-                st_async_v(mapa_u32(smem_u32(&inLc[par][tw][o]), tr), cost, mb);
-                st_async_v(mapa_u32(smem_u32(&inLl[par][tw][o]), tr), lab, mb);
+                st_async_v(mapa_u32(smem_u32(cb), tr), cost, mb);
+                st_async_v(mapa_u32(smem_u32(lb), tr), lab, mb);
             }
-            if (lane >= DPC_HL && lane < 2 * DPC_HL && g > 0) {
-                const int tg = g - 1, tr = tg / DPC_WPC, tw = tg % DPC_WPC;
-                const int o = (lane - DPC_HL) * DPC_V;
-                const uint32_t mb = mapa_u32(smem_u32(&minbox[tw][par]), tr);
-                st_async_v(mapa_u32(smem_u32(&inRc[par][tw][o]), tr), cost, mb);
-                st_async_v(mapa_u32(smem_u32(&inRl[par][tw][o]), tr), lab, mb);
-            }
+        }
+        __syncwarp();   // every lane has read the slot's rows
+        if (lane == 0) {
+            issue(s + DPC_NST);
+            // the inbox of parity `arm` (its refresh already waited for)
+            // serves the refresh two later, which a neighbour sends only
+            // after it has this warp's refresh e strips (sent above)
+            if (arm >= 0) mbar_expect_tx(&minbox[w][arm], in_bytes);
+        }
+        arm = -1;
+        if (refresh) {
             mbar_wait_cluster(&minbox[w][par], (unsigned)(e >> 1) & 1u, ws.err, WAIT_NS);
-            if (lane < DPC_HL) {
+            if (lane < DPC_HL || lane >= 32 - DPC_HL) {
+                const bool left = lane < DPC_HL;
+                const int o = (left ? lane : lane - (32 - DPC_HL)) * DPC_V;
+                const uint32_t *cs = left ? &inLc[par][w][o] : &inRc[par][w][o];
+                const uint32_t *ls = left ? &inLl[par][w][o] : &inRl[par][w][o];
+                const bool edge = left ? g == 0 : g == nwarps - 1;
 #pragma unroll
                 for (int v = 0; v < DPC_V; ++v) {
-                    cost[v] = g == 0 ? INF32 : inLc[par][w][lane * DPC_V + v];
-                    lab[v] = inLl[par][w][lane * DPC_V + v];
+                    cost[v] = edge ? INF32 : cs[v];
+                    lab[v] = ls[v];
                 }
             }
-            if (lane >= 32 - DPC_HL) {
-#pragma unroll
-                for (int v = 0; v < DPC_V; ++v) {
-                    cost[v] = g == nwarps - 1 ? INF32 : inRc[par][w][(lane - (32 - DPC_HL)) * DPC_V + v];
-                    lab[v] = inRl[par][w][(lane - (32 - DPC_HL)) * DPC_V + v];
-                }
-            }
-            __syncwarp();
-            if (lane == 0) mbar_expect_tx(&minbox[w][par], in_bytes);   // arm refresh e+2
+            arm = par;
         }
     }
     // the last row: a partial 4-row block, group and band are stored here
