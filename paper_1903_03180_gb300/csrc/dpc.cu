@@ -485,7 +485,10 @@ k_dpc(const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorM
             issue(s + DPC_NST);
             // the inbox of parity `arm` (its refresh already waited for)
             // serves the refresh two later, which a neighbour sends only
-            // after it has this warp's refresh e strips (sent above)
+            // after it has this warp's refresh e strips (sent above).  Bytes
+            // that land before this arrive only take the barrier's
+            // transaction count below zero for a while; the phase cannot
+            // complete before the arrive, which adds the expected bytes.
             if (arm >= 0) mbar_expect_tx(&minbox[w][arm], in_bytes);
         }
         arm = -1;
